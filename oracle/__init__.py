@@ -1,0 +1,266 @@
+"""Python face of the FP64 CPU oracle (test infrastructure).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never does.
+
+The arithmetic lives in ``vt_oracle.c``; this module compiles it with gcc
+(``-O2 -fopenmp -ffp-contract=off``, no fast-math) into ``oracle/_build`` and
+marshals numpy arrays through ctypes.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = [os.path.join(_HERE, "vt_oracle.c"), os.path.join(_HERE, "vt_oracle.h")]
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if its sources are newer than the library."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_SO) or any(
+        os.path.getmtime(s) > os.path.getmtime(_SO) for s in _SRC)
+    if stale:
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, _SRC[0], "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Section(C.Structure):
+    _fields_ = [("n_views", C.c_int32), ("W", C.c_int32), ("H", C.c_int32),
+                ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("poses", C.c_void_p), ("depth", C.c_void_p), ("n", C.c_int64),
+                ("src", C.c_void_p), ("colour", C.c_void_p), ("opacity", C.c_void_p),
+                ("radius", C.c_void_p)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("pose", C.c_double * 12), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("W", C.c_int32), ("H", C.c_int32)]
+
+
+class _Image(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("sil", C.c_void_p),
+                ("T_final", C.c_void_p), ("n_added", C.c_void_p), ("margin", C.c_void_p),
+                ("margin_T", C.c_void_p), ("margin_clamp", C.c_void_p),
+                ("lists", C.c_void_p), ("list_cap", C.c_int32)]
+
+
+class _Upstream(C.Structure):
+    _fields_ = [("g_rgb", C.c_void_p), ("g_depth", C.c_void_p), ("g_sil", C.c_void_p)]
+
+
+class _Grads(C.Structure):
+    _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
+                ("twist", C.c_double * 6), ("mat", C.c_double * 12)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_render.restype = C.c_int
+            L.orc_render.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
+            L.orc_backward.restype = C.c_int
+            L.orc_backward.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                       C.c_void_p]
+            L.orc_zkeys.restype = None
+            L.orc_zkeys.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_backproject.restype = C.c_int64
+            L.orc_backproject.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_float,
+                                          C.c_float, C.c_float, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]
+            L.orc_section_init.restype = C.c_int64
+            L.orc_section_init.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                           C.c_int32, C.c_float, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+@dataclasses.dataclass
+class Section:
+    """A section as the oracle sees it (all arrays host numpy).
+
+    poses: (V, 3, 4) float64 camera-to-world; depth: (V, H, W) float32;
+    src: (n,) uint32 = (view*H + v)*W + u, strictly increasing;
+    colour (n, 3), opacity (n,), radius (n,) float64."""
+    W: int
+    H: int
+    K: tuple          # (fx, fy, cx, cy) float32-representable
+    poses: np.ndarray
+    depth: np.ndarray
+    src: np.ndarray
+    colour: np.ndarray
+    opacity: np.ndarray
+    radius: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.src.shape[0])
+
+    def _c(self, keep: list) -> _Section:
+        arrs = dict(poses=pose12(self.poses),
+                    depth=np.ascontiguousarray(self.depth, np.float32),
+                    src=np.ascontiguousarray(self.src, np.uint32),
+                    colour=np.ascontiguousarray(self.colour, np.float64).reshape(-1, 3),
+                    opacity=np.ascontiguousarray(self.opacity, np.float64),
+                    radius=np.ascontiguousarray(self.radius, np.float64))
+        keep.append(arrs)
+        s = _Section()
+        s.n_views = int(self.depth.shape[0])
+        s.W, s.H = int(self.W), int(self.H)
+        s.fx, s.fy, s.cx, s.cy = (float(np.float32(k)) for k in self.K)
+        s.poses = _ptr(arrs["poses"])
+        s.depth = _ptr(arrs["depth"])
+        s.n = self.n
+        s.src = _ptr(arrs["src"])
+        s.colour = _ptr(arrs["colour"])
+        s.opacity = _ptr(arrs["opacity"])
+        s.radius = _ptr(arrs["radius"])
+        return s
+
+
+def pose12(poses) -> np.ndarray:
+    """(V, 3, 4) camera-to-world poses -> (V, 12): R row-major, then t."""
+    p = np.asarray(poses, np.float64).reshape(-1, 3, 4)
+    return np.ascontiguousarray(np.concatenate([p[:, :, :3].reshape(-1, 9), p[:, :, 3]], axis=1))
+
+
+def _camera(pose, K, W, H) -> _Camera:
+    c = _Camera()
+    flat = pose12(pose)[0]
+    for i in range(12):
+        c.pose[i] = float(flat[i])
+    c.fx, c.fy, c.cx, c.cy = (float(np.float32(k)) for k in K)
+    c.W, c.H = int(W), int(H)
+    return c
+
+
+def _sections(secs):
+    if isinstance(secs, Section):
+        secs = [secs]
+    keep = []
+    arr = (_Section * len(secs))()
+    for i, s in enumerate(secs):
+        arr[i] = s._c(keep)
+    return list(secs), arr, keep
+
+
+def render(secs, pose, K, W, H, binned=True, list_cap=0):
+    """Forward render.  Returns a dict of float64 images (rgb (3,H,W), depth,
+    sil, T_final), n_added (int32), the relative decision margins (margin for
+    the inclusion tests, margin_T for termination, margin_clamp for the 0.99
+    clamp) and, if list_cap > 0, the ids each pixel added front to back
+    (H, W, list_cap; -1 padded)."""
+    secs, arr, keep = _sections(secs)
+    out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
+               T_final=np.zeros((H, W)), n_added=np.zeros((H, W), np.int32),
+               margin=np.zeros((H, W)), margin_T=np.zeros((H, W)),
+               margin_clamp=np.zeros((H, W)))
+    lists = np.full((H, W, list_cap), -1, np.int64) if list_cap > 0 else None
+    img = _Image(_ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["sil"]), _ptr(out["T_final"]),
+                 _ptr(out["n_added"]), _ptr(out["margin"]), _ptr(out["margin_T"]),
+                 _ptr(out["margin_clamp"]), _ptr(lists), int(list_cap))
+    cam = _camera(pose, K, W, H)
+    rc = lib().orc_render(C.byref(arr), len(secs), C.byref(cam), int(bool(binned)), C.byref(img))
+    if rc != 0:
+        raise RuntimeError("oracle render failed")
+    if lists is not None:
+        out["lists"] = lists
+    return out
+
+
+def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=True):
+    """Gradients of <g_rgb, rgb> + <g_depth, depth> + <g_sil, sil>.
+
+    Returns dict(colour=[(n,3)], opacity=[(n,)], radius=[(n,)] per section,
+    twist (6,) and mat (12,) float64)."""
+    secs, arr, keep = _sections(secs)
+    ups = [None if g is None else np.ascontiguousarray(g, np.float64) for g in (g_rgb, g_depth, g_sil)]
+    up = _Upstream(*[_ptr(u) for u in ups])
+    dcol = [np.zeros((s.n, 3)) for s in secs]
+    dop = [np.zeros(s.n) for s in secs]
+    drad = [np.zeros(s.n) for s in secs]
+    pc = (C.c_void_p * len(secs))(*[_ptr(a) for a in dcol])
+    po = (C.c_void_p * len(secs))(*[_ptr(a) for a in dop])
+    pr = (C.c_void_p * len(secs))(*[_ptr(a) for a in drad])
+    g = _Grads(C.cast(pc, C.c_void_p), C.cast(po, C.c_void_p), C.cast(pr, C.c_void_p))
+    cam = _camera(pose, K, W, H)
+    rc = lib().orc_backward(C.byref(arr), len(secs), C.byref(cam), int(bool(binned)), C.byref(up),
+                            C.byref(g))
+    if rc != 0:
+        raise RuntimeError("oracle backward failed")
+    return dict(colour=dcol, opacity=dop, radius=drad, twist=np.array(g.twist[:]),
+                mat=np.array(g.mat[:]))
+
+
+def zkeys(sec: Section, pose, K, W, H):
+    """FP32 depth keys and validity of every Gaussian of one section."""
+    _, arr, keep = _sections([sec])
+    z = np.zeros(sec.n, np.float32)
+    ok = np.zeros(sec.n, np.uint8)
+    cam = _camera(pose, K, W, H)
+    lib().orc_zkeys(C.byref(arr), C.byref(cam), _ptr(z), _ptr(ok))
+    return z, ok.astype(bool)
+
+
+def backproject(depth, K, pose):
+    """Centres (n, 3) float64 and raster pixel indices (n,) uint32."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    H, W = depth.shape
+    cen = np.zeros((H * W, 3))
+    pix = np.zeros(H * W, np.uint32)
+    flat = pose12(pose)[0]
+    fx, fy, cx, cy = (float(np.float32(k)) for k in K)
+    n = lib().orc_backproject(_ptr(depth), W, H, fx, fy, cx, cy, _ptr(flat), _ptr(cen), _ptr(pix))
+    return cen[:n].copy(), pix[:n].copy()
+
+
+def section_init(depth, rgb, K, poses) -> Section:
+    """One Gaussian per valid depth pixel: colour = V(u,v), opacity 0.9,
+    radius = D / fx.  depth (V,H,W) f32, rgb (V,3,H,W) f32, poses (V,3,4)."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    rgb = np.ascontiguousarray(rgb, np.float32)
+    V, H, W = depth.shape
+    cap = V * H * W
+    src = np.zeros(cap, np.uint32)
+    col = np.zeros((cap, 3))
+    op = np.zeros(cap)
+    rad = np.zeros(cap)
+    fx = float(np.float32(K[0]))
+    n = lib().orc_section_init(_ptr(depth), _ptr(rgb), V, W, H, fx, _ptr(src), _ptr(col),
+                               _ptr(op), _ptr(rad))
+    return Section(W, H, tuple(float(np.float32(k)) for k in K),
+                   np.asarray(poses, np.float64).reshape(V, 3, 4).copy(), depth,
+                   src[:n].copy(), col[:n].copy(), op[:n].copy(), rad[:n].copy())

@@ -1,0 +1,109 @@
+/* Plain FP64 CPU oracle of view-tied isotropic Gaussian splatting.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load or call this library.  It shares
+ * no code with the CUDA path.
+ *
+ * What it computes (paper Sec. 3.2, Eq. 1 text, supplementary Eq. for r):
+ * every Gaussian is tied to one valid depth pixel of a source view and has a
+ * colour c, an opacity o and an isotropic radius r (a standard deviation in
+ * metres).  Its centre is the back-projection of that depth pixel with the
+ * source view's pose.  A target camera (pose, intrinsics, W x H) is rendered
+ * per pixel by front-to-back alpha compositing with
+ *     q     = ((px*z - x)^2 + (py*z - y)^2) / r^2     (isotropic footprint)
+ *     ahat  = o * exp(-q/2),  included iff q <= 9 and ahat >= 1/255
+ *     alpha = min(0.99, ahat),
+ * ordered by (z_key, id) and stopped before the Gaussian whose inclusion
+ * would drop the transmittance below 1e-4.  Outputs: colour, depth
+ * (sum w*z) and silhouette (sum w).  Thresholds are the FP32 constants the
+ * kernels compare against (1.0f/255.0f, 0.99f, 1e-4f, z_near 0.1f).
+ */
+#ifndef VT_ORACLE_H
+#define VT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t n_views, W, H;
+    float fx, fy, cx, cy;        /* source-view intrinsics (shared by the section) */
+    const double *poses;         /* n_views x 12: R row-major (camera-to-world), then t */
+    const float *depth;          /* n_views x H x W, metres; <=0 or non-finite = invalid */
+    int64_t n;                   /* number of Gaussians */
+    const uint32_t *src;         /* n: (view*H + v)*W + u, strictly increasing */
+    const double *colour;        /* n x 3 */
+    const double *opacity;       /* n */
+    const double *radius;        /* n */
+} orc_section;
+
+typedef struct {
+    double pose[12];             /* target camera-to-world: R row-major then t */
+    float fx, fy, cx, cy;
+    int32_t W, H;
+} orc_camera;
+
+typedef struct {
+    double *rgb;                 /* 3 x H x W */
+    double *depth;               /* H x W */
+    double *sil;                 /* H x W */
+    double *T_final;             /* H x W */
+    int32_t *n_added;            /* H x W */
+    double *margin;              /* H x W: smallest relative distance of an inclusion test
+                                    (q <= 9, ahat >= 1/255) to its threshold */
+    double *margin_T;            /* H x W: same for the termination test T' < 1e-4 */
+    double *margin_clamp;        /* H x W: same for the clamp ahat vs 0.99 (gradient only) */
+    int64_t *lists;              /* H x W x list_cap ids added front to back, -1 padded (may be NULL) */
+    int32_t list_cap;
+} orc_image;
+
+typedef struct {
+    const double *g_rgb;         /* 3 x H x W (NULL = 0) */
+    const double *g_depth;       /* H x W (NULL = 0) */
+    const double *g_sil;         /* H x W (NULL = 0) */
+} orc_upstream;
+
+typedef struct {
+    double **d_colour;           /* per section, n x 3 (entries may be NULL) */
+    double **d_opacity;          /* per section, n */
+    double **d_radius;           /* per section, n */
+    double twist[6];             /* dL/d(rho, phi) for P(xi) = P * Exp(xi) */
+    double mat[12];              /* dL/dR (row-major 3x3) then dL/dt */
+} orc_grads;
+
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
+/* FP32 depth keys of every Gaussian for the target pose; valid[i]=0 marks a
+ * Gaussian with invalid depth or z_key < 0.1f. */
+void orc_zkeys(const orc_section *sec, const orc_camera *cam, float *zkey, uint8_t *valid);
+
+/* Render; binned = 0 evaluates every Gaussian at every pixel (brute force),
+ * binned = 1 takes candidates from 16x16 pixel bins of conservative disc
+ * boxes.  Returns 0 on success. */
+int orc_render(const orc_section *secs, int n_secs, const orc_camera *cam, int binned,
+               orc_image *out);
+
+/* Gradients of L = <g_rgb, rgb> + <g_depth, depth> + <g_sil, sil>; the
+ * included sets and their order are held fixed.  Accumulates (+=) into the
+ * per-Gaussian arrays; twist and mat are overwritten. */
+int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int binned,
+                 const orc_upstream *up, orc_grads *g);
+
+/* Centres of the Gaussians of one depth map: mu = R (D * K^-1 [u v 1]) + t
+ * for every valid pixel in raster order.  Returns the count. */
+int64_t orc_backproject(const float *depth, int32_t W, int32_t H, float fx, float fy,
+                        float cx, float cy, const double *pose12, double *centres,
+                        uint32_t *pix);
+
+/* Section initialisation from RGB-D views: one Gaussian per valid depth
+ * pixel, colour = V(u,v), opacity = 0.9, radius = D / fx.  Returns n. */
+int64_t orc_section_init(const float *depth, const float *rgb, int32_t n_views, int32_t W,
+                         int32_t H, float fx, uint32_t *src, double *colour,
+                         double *opacity, double *radius);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
