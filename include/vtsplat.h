@@ -1,0 +1,205 @@
+/* vtsplat: differentiable splatting of view-tied isotropic 3D Gaussians on
+ * GB300 (sm_103a).  C ABI.
+ *
+ * The operations follow VTGaussian-SLAM (arXiv 2506.02741):
+ *   - a Gaussian has only a colour c (3), an opacity o and an isotropic
+ *     radius r, and is tied to one valid depth pixel of one view; its centre
+ *     is that pixel back-projected with the view's pose (Sec. 3.2);
+ *   - a section groups the Gaussians of N consecutive views (Sec. 3.2);
+ *   - splat(gaussians, pose) renders colour and depth (Eq. 1 text) and the
+ *     silhouette used to find uncovered pixels (Sec. 3.4);
+ *   - tracking differentiates the render with respect to the camera pose,
+ *     mapping with respect to colour, opacity and radius (Sec. 3.3, Eq. 1;
+ *     Sec. 3.4, Eq. 2).
+ * The splatting definition implemented here (per target pixel (u, v) at
+ * normalised position p = ((u-cx)/fx, (v-cy)/fy), Gaussian centre x = (x,y,z)
+ * in the target camera):
+ *   q = ((p_x z - x)^2 + (p_y z - y)^2) / r^2, ahat = o exp(-q/2),
+ *   included iff z_key >= 0.1, q <= 9 and ahat >= 1/255, alpha = min(0.99, ahat),
+ *   front to back by (z_key, id), stop before a Gaussian that would make the
+ *   transmittance T < 1e-4;  C = sum w c, D = sum w z, S = sum w, w = alpha T.
+ * id = (section index, position in the section); z_key = FP32 camera depth
+ * of the centre computed with a fixed operation order.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are CUDA global memory on the current device,
+ *     owned by the caller; the library never frees or keeps them beyond the
+ *     call (except that vt_render_backward reads the buffers of the
+ *     preceding vt_render on the same context, which must still be alive).
+ *   - Structs passed by pointer (vt_section arrays, vt_grads arrays) are host
+ *     memory, read during the call only.
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and is asynchronous; no call synchronises the stream
+ *     except vt_ctx_sync_status and vt_ctx_debug_copy, which say so.
+ *   - Poses are camera-to-world 3x4 [R | t] as 12 doubles: R row-major, then t.
+ *   - Images are float32, planar: rgb is 3 x H x W (channel-major), depth and
+ *     silhouette H x W.
+ *   - Errors are returned as vt_status; vt_last_error() gives a message for
+ *     the calling thread.  Argument errors are found on the host before any
+ *     launch.  A shortage of instance capacity is found on the device: the
+ *     call returns VT_OK, the results of that render are undefined, and
+ *     vt_ctx_sync_status reports VT_ERR_CAPACITY with the size needed.
+ */
+#ifndef VTSPLAT_H
+#define VTSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *vt_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    VT_OK = 0,
+    VT_ERR_INVALID_ARG = 1, /* a size, pointer or value is out of range */
+    VT_ERR_OOM = 2,         /* device memory for the workspace could not be allocated */
+    VT_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    VT_ERR_CAPACITY = 4,    /* more tile instances than the workspace holds */
+    VT_ERR_TIMEOUT = 5,     /* a bounded wait expired */
+    VT_ERR_STATE = 6        /* backward without a matching render */
+} vt_status;
+
+typedef struct {
+    float fx, fy, cx, cy; /* pinhole intrinsics in pixels */
+} vt_intrinsics;
+
+typedef enum {
+    VT_F32 = 0, /* colour, opacity, radius stored as float32 */
+    VT_F16 = 1  /* stored as IEEE half; all arithmetic stays float32 */
+} vt_precision;
+
+/* One section (Sec. 3.2): the Gaussians tied to the valid depth pixels of
+ * n_views views of one camera.  Every pointer is device memory. */
+typedef struct {
+    int32_t n_views, W, H;  /* views share size W x H and intrinsics K */
+    vt_intrinsics K;
+    const double *poses;    /* n_views x 12 camera-to-world */
+    const float *depth;     /* n_views x H x W metres; <= 0 or non-finite = no Gaussian */
+    int64_t n;              /* number of Gaussians */
+    const uint32_t *src;    /* n: (view*H + v)*W + u, strictly increasing (canonical id order) */
+    vt_precision prec;
+    const void *colour;     /* n x 3 */
+    const void *opacity;    /* n, activated value in (0, 1] */
+    const void *radius;     /* n, activated value > 0 (metres, a standard deviation) */
+} vt_section;
+
+/* Per-section gradient buffers (device float32, accumulated with +=).  A
+ * NULL pointer skips that gradient; a section whose three pointers are NULL
+ * is frozen (only the learnable section gets gradients, Sec. 3.2 / Eq. 2). */
+typedef struct {
+    float *d_colour;  /* n x 3 */
+    float *d_opacity; /* n */
+    float *d_radius;  /* n */
+} vt_grads;
+
+typedef enum {
+    VT_GRAD_ATTR = 1, /* colour, opacity, radius (mapping, Eq. 2) */
+    VT_GRAD_POSE = 2  /* target camera pose (tracking, Eq. 1) */
+} vt_grad_mode;
+
+/* Opaque render context: the library-owned workspace (projected Gaussians,
+ * tile lists, per-pixel state) kept from a render for its backward. */
+typedef struct vt_ctx vt_ctx;
+
+/* Create / destroy a context on the current CUDA device.  Destroy frees the
+ * workspace after the work queued on the context's last stream. */
+vt_status vt_ctx_create(vt_ctx **ctx);
+void vt_ctx_destroy(vt_ctx *ctx);
+
+/* Reserve workspace for renders of up to n_gaussians Gaussians into W x H
+ * images with up to n_instances (Gaussian, tile) pairs, so that later calls
+ * allocate nothing (needed before capturing renders in a CUDA graph).
+ * n_instances <= 0 picks 4 * n_gaussians + 65536.  Allocates on `stream`. */
+vt_status vt_ctx_reserve(vt_ctx *ctx, int64_t n_gaussians, int32_t W, int32_t H,
+                         int64_t n_instances, vt_stream stream);
+
+/* Workspace bytes a reserve of those sizes needs. */
+size_t vt_workspace_bytes(int64_t n_gaussians, int32_t W, int32_t H, int64_t n_instances);
+
+/* Synchronises `stream`, then reports the status word of the last render on
+ * this context: VT_OK, or VT_ERR_CAPACITY with *needed_instances set to the
+ * count that render required (reserve at least that much and render again).
+ * needed_instances may be NULL. */
+vt_status vt_ctx_sync_status(vt_ctx *ctx, vt_stream stream, int64_t *needed_instances);
+
+/* Back-projection (Sec. 3.2): the world centre mu = R (D K^-1 [u v 1]^T) + t
+ * of every valid depth pixel, in raster order.  depth: device H x W;
+ * pose12: device; centres: device float32 3 x cap (x,y,z interleaved);
+ * pix: device uint32 cap (v*W + u); n_out: device int64, receives the number
+ * of valid pixels (entries beyond cap are counted but not written). */
+vt_status vt_backproject(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                         const double *pose12, float *centres, uint32_t *pix, int64_t cap,
+                         int64_t *n_out, vt_stream stream);
+
+/* Section initialisation (Sec. 3.2 and supplementary r = D/f): one Gaussian
+ * per valid depth pixel of n_views views, in canonical order, with
+ * colour = V(u, v), opacity = 0.9 and radius = D / fx.  depth: device
+ * n_views x H x W; rgb: device n_views x 3 x H x W float32 in [0, 1];
+ * outputs (device, capacity cap): src, colour (cap x 3), opacity, radius in
+ * precision `prec`; n_out (device int64) receives the count. */
+vt_status vt_section_init(const float *depth, const float *rgb, int32_t n_views, int32_t W,
+                          int32_t H, vt_intrinsics K, vt_precision prec, uint32_t *src,
+                          void *colour, void *opacity, void *radius, int64_t cap,
+                          int64_t *n_out, vt_stream stream);
+
+/* Render sections [secs, secs + n_secs) (their concatenation, as in the
+ * multi-section render of Sec. 3.4) from the camera pose12 (device, 12
+ * doubles) with intrinsics K into W x H images.  rgb (3 x H x W), depth and
+ * silhouette (H x W) are device float32; any of them may be NULL.  The
+ * context keeps what vt_render_backward needs. */
+vt_status vt_render(vt_ctx *ctx, const vt_section *secs, int32_t n_secs, const double *pose12,
+                    vt_intrinsics K, int32_t W, int32_t H, float *rgb, float *depth,
+                    float *silhouette, vt_stream stream);
+
+/* Backward of the last vt_render on ctx for L with upstream gradients
+ * dL_drgb (3 x H x W), dL_ddepth, dL_dsil (H x W; each device, NULL = 0).
+ * mode is a combination of vt_grad_mode bits.
+ *   VT_GRAD_ATTR: grads[s] (host array of n_secs entries) receive
+ *     dL/dcolour, dL/dopacity, dL/dradius of section s (+=, float32).
+ *   VT_GRAD_POSE: d_twist (device, 6 doubles) += dL/d(rho, phi) for the
+ *     right perturbation P exp(xi), xi = (rho, phi); d_mat (device, 12
+ *     doubles) += dL/dR (row-major) and dL/dt.  The pose sums are reduced in
+ *     FP64 in a fixed order (bit-reproducible).
+ * The included sets and their order are those of the render (piecewise
+ * constant).  Returns VT_ERR_STATE when ctx holds no render. */
+vt_status vt_render_backward(vt_ctx *ctx, const float *dL_drgb, const float *dL_ddepth,
+                             const float *dL_dsil, int32_t mode, const vt_grads *grads,
+                             double *d_twist, double *d_mat, vt_stream stream);
+
+/* Per-kernel timing of the context's launches with CUDA events on the
+ * launching stream (enable != 0).  vt_ctx_timing synchronises the stream
+ * and writes, for up to n_max kernels, their names (static strings), the
+ * number of launches and the summed milliseconds since the last reset;
+ * returns the number of kernels. */
+vt_status vt_ctx_set_timing(vt_ctx *ctx, int32_t enable);
+int32_t vt_ctx_timing(vt_ctx *ctx, vt_stream stream, const char **names, int64_t *launches,
+                      double *ms, int32_t n_max, int32_t reset);
+
+/* Number of kernels launched by the library on this context since it was
+ * created (host-side counter). */
+int64_t vt_ctx_launch_count(const vt_ctx *ctx);
+
+/* Test and inspection hook: synchronises `stream` and copies an internal
+ * array of the last render to host memory dst (bytes <= capacity).
+ * what: 0 = depth keys (float32 x n, 0 for culled), 1 = tile offsets
+ * (uint32 x tiles+1), 2 = sorted tile lists (uint32 x instances, Gaussian
+ * ids), 3 = per-pixel list end (uint32 x H*W, relative to the tile start),
+ * 4 = per-pixel count of added Gaussians (uint32 x H*W), 5 = per-pixel final
+ * transmittance (float32 x H*W).  Returns the number of bytes copied, or a
+ * negative vt_status. */
+int64_t vt_ctx_debug_copy(vt_ctx *ctx, int32_t what, void *dst, int64_t capacity,
+                          vt_stream stream);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *vt_last_error(void);
+
+/* Library version string. */
+const char *vt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

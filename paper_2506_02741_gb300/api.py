@@ -1,0 +1,278 @@
+"""PyTorch-facing binding of the vtsplat C ABI.
+
+Argument marshalling only: tensors are checked for device, dtype and shape
+and their pointers are handed to the CUDA library on the current torch
+stream.  Every step of the splatting path runs in the library's kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _intr(K) -> L.Intrinsics:
+    fx, fy, cx, cy = (float(np.float32(k)) for k in K)
+    return L.Intrinsics(fx, fy, cx, cy)
+
+
+def _cuda(t: torch.Tensor, dtype, name: str, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def pose12(P, device="cuda") -> torch.Tensor:
+    """(3, 4) or (V, 3, 4) camera-to-world pose(s) -> (12,) / (V, 12) float64
+    on the device: R row-major, then t."""
+    if isinstance(P, torch.Tensor):
+        P = P.detach().to("cpu", torch.float64).numpy()
+    p = np.asarray(P, np.float64)
+    single = p.ndim == 2
+    p = p.reshape(-1, 3, 4)
+    flat = np.concatenate([p[:, :, :3].reshape(-1, 9), p[:, :, 3]], axis=1)
+    t = torch.from_numpy(np.ascontiguousarray(flat)).to(device)
+    return t[0].contiguous() if single else t.contiguous()
+
+
+def matrix_of(p12) -> np.ndarray:
+    """(12,) pose vector -> (3, 4) numpy matrix."""
+    v = p12.detach().cpu().numpy() if isinstance(p12, torch.Tensor) else np.asarray(p12)
+    return np.hstack([v[:9].reshape(3, 3), v[9:12].reshape(3, 1)])
+
+
+@dataclasses.dataclass
+class Section:
+    """A device-resident section (Sec. 3.2): the Gaussians tied to the valid
+    depth pixels of ``n_views`` views of one camera.
+
+    poses (V, 12) float64, depth (V, H, W) float32, src (n,) int32 holding
+    the uint32 source index (view*H + v)*W + u in increasing order,
+    colour (n, 3), opacity (n,), radius (n,) in float32 or float16."""
+    poses: torch.Tensor
+    depth: torch.Tensor
+    K: tuple
+    src: torch.Tensor
+    colour: torch.Tensor
+    opacity: torch.Tensor
+    radius: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.src.shape[0])
+
+    @property
+    def n_views(self) -> int:
+        return int(self.depth.shape[0])
+
+    @property
+    def prec(self) -> int:
+        return L.VT_F16 if self.colour.dtype == torch.float16 else L.VT_F32
+
+    def validate(self):
+        V, H, W = self.depth.shape
+        _cuda(self.poses, torch.float64, "poses", (V, 12))
+        _cuda(self.depth, torch.float32, "depth")
+        _cuda(self.src, torch.int32, "src", (self.n,))
+        dt = self.colour.dtype
+        if dt not in (torch.float32, torch.float16):
+            raise TypeError("attributes must be float32 or float16")
+        _cuda(self.colour, dt, "colour", (self.n, 3))
+        _cuda(self.opacity, dt, "opacity", (self.n,))
+        _cuda(self.radius, dt, "radius", (self.n,))
+
+    def c_struct(self) -> L.SectionC:
+        self.validate()
+        V, H, W = self.depth.shape
+        return L.SectionC(V, W, H, _intr(self.K), _ptr(self.poses), _ptr(self.depth), self.n,
+                          _ptr(self.src), self.prec, _ptr(self.colour), _ptr(self.opacity),
+                          _ptr(self.radius))
+
+    @staticmethod
+    def from_rgbd(depth: torch.Tensor, rgb: torch.Tensor, K, poses, precision: str = "f32",
+                  stream=None) -> "Section":
+        """Initialise a section on the device (one Gaussian per valid depth
+        pixel, colour = V(u,v), opacity 0.9, radius D/fx).  Synchronises once
+        to learn the count."""
+        depth = _cuda(depth, torch.float32, "depth")
+        V, H, W = depth.shape
+        rgb = _cuda(rgb, torch.float32, "rgb", (V, 3, H, W))
+        P = poses if isinstance(poses, torch.Tensor) and poses.dtype == torch.float64 and \
+            poses.is_cuda else pose12(poses, depth.device)
+        P = P.reshape(V, 12).contiguous()
+        dt = torch.float16 if precision == "f16" else torch.float32
+        cap = V * H * W
+        dev = depth.device
+        src = torch.empty(cap, dtype=torch.int32, device=dev)
+        col = torch.empty(cap, 3, dtype=dt, device=dev)
+        op = torch.empty(cap, dtype=dt, device=dev)
+        rad = torch.empty(cap, dtype=dt, device=dev)
+        n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+        L.check(L.lib().vt_section_init(_ptr(depth), _ptr(rgb), V, W, H, _intr(K),
+                                        L.VT_F16 if dt == torch.float16 else L.VT_F32,
+                                        _ptr(src), _ptr(col), _ptr(op), _ptr(rad), cap,
+                                        _ptr(n_out), _stream(stream)), "vt_section_init")
+        n = int(n_out.item())
+        return Section(P, depth, tuple(float(np.float32(k)) for k in K), src[:n].contiguous(),
+                       col[:n].contiguous(), op[:n].contiguous(), rad[:n].contiguous())
+
+
+def backproject(depth: torch.Tensor, K, pose, stream=None):
+    """World centres (n, 3) float32 and raster pixel indices (n,) of the valid
+    pixels of one depth map (synchronises once to learn n)."""
+    depth = _cuda(depth, torch.float32, "depth")
+    H, W = depth.shape
+    P = pose if isinstance(pose, torch.Tensor) else pose12(pose, depth.device)
+    cap = H * W
+    cen = torch.empty(cap, 3, dtype=torch.float32, device=depth.device)
+    pix = torch.empty(cap, dtype=torch.int32, device=depth.device)
+    n_out = torch.zeros(1, dtype=torch.int64, device=depth.device)
+    L.check(L.lib().vt_backproject(_ptr(depth), W, H, _intr(K), _ptr(P), _ptr(cen), _ptr(pix),
+                                   cap, _ptr(n_out), _stream(stream)), "vt_backproject")
+    n = int(n_out.item())
+    return cen[:n], pix[:n]
+
+
+class Renderer:
+    """Owns one vt_ctx (the library's render workspace) on the current device."""
+
+    def __init__(self):
+        self._lib = L.lib()
+        h = C.c_void_p()
+        L.check(self._lib.vt_ctx_create(C.byref(h)), "vt_ctx_create")
+        self._ctx = h
+        self.last = None
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.vt_ctx_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- workspace ---------------------------------------------------------
+    def reserve(self, n_gaussians: int, W: int, H: int, n_instances: int = 0, stream=None):
+        L.check(self._lib.vt_ctx_reserve(self._ctx, int(n_gaussians), int(W), int(H),
+                                         int(n_instances), _stream(stream)), "vt_ctx_reserve")
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return the tile-instance count of the last render;
+        raises VTError(VT_ERR_CAPACITY) if the workspace was too small."""
+        need = C.c_int64(0)
+        L.check(self._lib.vt_ctx_sync_status(self._ctx, _stream(stream), C.byref(need)),
+                "render status")
+        return int(need.value)
+
+    # -- render --------------------------------------------------------------
+    def render(self, sections, pose, K, W: int, H: int, rgb=None, depth=None, sil=None,
+               stream=None, checked: bool = False):
+        """Render (the concatenation of) ``sections`` from ``pose`` ((12,)
+        float64 device tensor).  Returns (rgb (3,H,W), depth (H,W),
+        silhouette (H,W)) float32.  With ``checked`` the call synchronises,
+        grows the workspace if the instance capacity was short and renders
+        again."""
+        if isinstance(sections, Section):
+            sections = [sections]
+        pose = _cuda(pose, torch.float64, "pose", (12,))
+        dev = pose.device
+        rgb = torch.empty(3, H, W, device=dev) if rgb is None else _cuda(rgb, torch.float32, "rgb", (3, H, W))
+        depth = torch.empty(H, W, device=dev) if depth is None else _cuda(depth, torch.float32, "depth", (H, W))
+        sil = torch.empty(H, W, device=dev) if sil is None else _cuda(sil, torch.float32, "sil", (H, W))
+        arr = (L.SectionC * max(1, len(sections)))(*[s.c_struct() for s in sections])
+        args = (self._ctx, arr, len(sections), _ptr(pose), _intr(K), int(W), int(H), _ptr(rgb),
+                _ptr(depth), _ptr(sil), _stream(stream))
+        L.check(self._lib.vt_render(*args), "vt_render")
+        self.last = (sections, pose, tuple(K), W, H)
+        if checked:
+            try:
+                self.status(stream)
+            except L.VTError as e:
+                if e.status != L.VT_ERR_CAPACITY:
+                    raise
+                need = C.c_int64(0)
+                self._lib.vt_ctx_sync_status(self._ctx, _stream(stream), C.byref(need))
+                n = sum(s.n for s in sections)
+                self.reserve(n, W, H, int(need.value * 1.25) + 1024, stream)
+                L.check(self._lib.vt_render(*args), "vt_render")
+                self.status(stream)
+        return rgb, depth, sil
+
+    def backward(self, d_rgb=None, d_depth=None, d_sil=None, attr_grads=None, pose_grad=False,
+                 d_twist=None, d_mat=None, stream=None):
+        """Backward of the last render.  attr_grads: per section a tuple
+        (d_colour (n,3), d_opacity (n,), d_radius (n,)) float32 device tensors
+        or None (frozen section); gradients are accumulated (+=).  With
+        pose_grad, d_twist (6,) and d_mat (12,) float64 device tensors are
+        accumulated (created as zeros if not given).  Returns (d_twist, d_mat)."""
+        mode = 0
+        grads = None
+        if attr_grads is not None:
+            mode |= L.VT_GRAD_ATTR
+            gl = []
+            for g in attr_grads:
+                if g is None:
+                    gl.append(L.GradsC(None, None, None))
+                else:
+                    dc, do, dr = g
+                    gl.append(L.GradsC(_ptr(dc), _ptr(do), _ptr(dr)))
+            grads = (L.GradsC * len(gl))(*gl)
+        if pose_grad:
+            mode |= L.VT_GRAD_POSE
+            dev = self.last[1].device if self.last else "cuda"
+            if d_twist is None:
+                d_twist = torch.zeros(6, dtype=torch.float64, device=dev)
+            if d_mat is None:
+                d_mat = torch.zeros(12, dtype=torch.float64, device=dev)
+        L.check(self._lib.vt_render_backward(self._ctx, _ptr(d_rgb), _ptr(d_depth), _ptr(d_sil),
+                                             mode, grads, _ptr(d_twist), _ptr(d_mat),
+                                             _stream(stream)), "vt_render_backward")
+        return d_twist, d_mat
+
+    # -- instrumentation -----------------------------------------------------
+    def set_timing(self, on: bool = True):
+        L.check(self._lib.vt_ctx_set_timing(self._ctx, int(bool(on))), "vt_ctx_set_timing")
+
+    def timing(self, reset: bool = True, stream=None) -> dict:
+        n = 16
+        names = (C.c_char_p * n)()
+        launches = (C.c_int64 * n)()
+        ms = (C.c_double * n)()
+        k = self._lib.vt_ctx_timing(self._ctx, _stream(stream), names, launches, ms, n,
+                                    int(bool(reset)))
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(k)}
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.vt_ctx_launch_count(self._ctx))
+
+    def debug(self, what: int, count: int, dtype=np.uint32, stream=None) -> np.ndarray:
+        out = np.zeros(count, dtype)
+        r = self._lib.vt_ctx_debug_copy(self._ctx, int(what), out.ctypes.data_as(C.c_void_p),
+                                        out.nbytes, _stream(stream))
+        if r < 0:
+            raise L.VTError(-r, "vt_ctx_debug_copy")
+        return out[: r // out.itemsize]

@@ -1,0 +1,599 @@
+// C ABI of the vtsplat library: argument checks, the render context and its
+// workspace, kernel launches, back-projection and section initialisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vt_common.cuh"
+
+using namespace vt;
+
+namespace {
+
+thread_local std::string g_err;
+
+vt_status fail(vt_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+vt_status fail(vt_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+vt_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(VT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define VT_CUDA(call, what)                         \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr int kSortSmemN = 6144;  // tile lists up to this length are sorted in shared memory
+constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 16 * 256 * 4;
+
+enum KernelId {
+    K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
+    K_SECTION_INIT, K_COUNT, K_NUM
+};
+const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
+                                   "k_emit",          "k_sort_tiles",    "k_composite_fwd",
+                                   "k_composite_bwd", "k_pose_finalize", "k_backproject",
+                                   "k_section_init",  "k_count_valid"};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+bool finite(float x) { return std::isfinite(x); }
+
+}  // namespace
+
+struct vt_ctx {
+    int device = 0;
+    // capacities
+    int64_t cap_g = 0, cap_i = 0, cap_p = 0, cap_t = 0, cap_v = 0, cap_tab = 0;
+    int64_t reserved_i = 0;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    float4 *geo = nullptr, *app = nullptr;
+    uint4 *info = nullptr;
+    uint32_t *tile_count = nullptr, *tile_off = nullptr, *tile_cursor = nullptr;
+    unsigned long long *bucket = nullptr, *alt = nullptr;
+    uint32_t *sorted = nullptr;
+    uint32_t *pix_last = nullptr, *pix_nadd = nullptr;
+    float *pix_T = nullptr;
+    Status *status = nullptr;
+    ViewXf *views = nullptr;
+    TabRow *tab = nullptr;
+    double *pose_partials = nullptr, *pose_copy = nullptr;
+    // last render
+    bool has_render = false;
+    SecTable table{};
+    Camera cam{};
+    int n_tiles = 0;
+    cudaStream_t stream = nullptr;
+    // instrumentation
+    int64_t launches = 0;
+    bool timing = false;
+    struct Pending {
+        int kernel;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t t_launches[K_NUM] = {0};
+    double t_ms[K_NUM] = {0};
+};
+
+namespace {
+
+cudaEvent_t get_event(vt_ctx *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one launch with events when timing is on.
+struct LaunchScope {
+    vt_ctx *c;
+    int k;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    LaunchScope(vt_ctx *c_, int k_, cudaStream_t s_) : c(c_), k(k_), s(s_) {
+        if (c->timing) {
+            a = get_event(c);
+            cudaEventRecord(a, s);
+        }
+        c->launches++;
+    }
+    ~LaunchScope() {
+        if (c->timing) {
+            cudaEvent_t b = get_event(c);
+            cudaEventRecord(b, s);
+            c->pending.push_back({k, a, b});
+        }
+    }
+};
+
+void free_arena(vt_ctx *c, cudaStream_t s) {
+    if (c->arena) cudaFreeAsync(c->arena, s);
+    c->arena = nullptr;
+    c->arena_bytes = 0;
+}
+
+size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, int64_t tab) {
+    size_t b = 0;
+    b += align_up(sizeof(float4) * 2 * g);               // geo
+    b += align_up(sizeof(float4) * g);                   // app
+    b += align_up(sizeof(uint4) * g);                    // info
+    b += 3 * align_up(sizeof(uint32_t) * (t + 1));       // tile count/off/cursor
+    b += 2 * align_up(sizeof(unsigned long long) * i);   // bucket, alt
+    b += align_up(sizeof(uint32_t) * i);                 // sorted
+    b += 3 * align_up(sizeof(uint32_t) * p);             // last, nadd, T
+    b += align_up(sizeof(Status));
+    b += align_up(sizeof(ViewXf) * v);
+    b += align_up(sizeof(TabRow) * tab);
+    b += align_up(sizeof(double) * 12 * t);              // pose partials
+    b += align_up(sizeof(double) * 12);                  // pose copy
+    return b;
+}
+
+vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, int64_t tab,
+                 cudaStream_t s) {
+    if (g <= c->cap_g && i <= c->cap_i && p <= c->cap_p && t <= c->cap_t && v <= c->cap_v &&
+        tab <= c->cap_tab && c->arena)
+        return VT_OK;
+    g = std::max(g, c->cap_g);
+    i = std::max(i, c->cap_i);
+    p = std::max(p, c->cap_p);
+    t = std::max(t, c->cap_t);
+    v = std::max(v, c->cap_v);
+    tab = std::max(tab, c->cap_tab);
+    const size_t bytes = arena_bytes_for(g, i, p, t, v, tab);
+    free_arena(c, s);
+    void *a = nullptr;
+    cudaError_t e = cudaMallocAsync(&a, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_g = c->cap_i = c->cap_p = c->cap_t = c->cap_v = c->cap_tab = 0;
+        c->has_render = false;
+        return fail(VT_ERR_OOM, "workspace allocation of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    c->arena = a;
+    c->arena_bytes = bytes;
+    char *q = static_cast<char *>(a);
+    auto take = [&](size_t n) {
+        char *r = q;
+        q += align_up(n);
+        return r;
+    };
+    c->geo = reinterpret_cast<float4 *>(take(sizeof(float4) * 2 * g));
+    c->app = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
+    c->info = reinterpret_cast<uint4 *>(take(sizeof(uint4) * g));
+    c->tile_count = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
+    c->tile_off = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
+    c->tile_cursor = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
+    c->bucket = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * i));
+    c->alt = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * i));
+    c->sorted = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * i));
+    c->pix_last = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * p));
+    c->pix_nadd = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * p));
+    c->pix_T = reinterpret_cast<float *>(take(sizeof(float) * p));
+    c->status = reinterpret_cast<Status *>(take(sizeof(Status)));
+    c->views = reinterpret_cast<ViewXf *>(take(sizeof(ViewXf) * v));
+    c->tab = reinterpret_cast<TabRow *>(take(sizeof(TabRow) * tab));
+    c->pose_partials = reinterpret_cast<double *>(take(sizeof(double) * 12 * t));
+    c->pose_copy = reinterpret_cast<double *>(take(sizeof(double) * 12));
+    c->cap_g = g;
+    c->cap_i = i;
+    c->cap_p = p;
+    c->cap_t = t;
+    c->cap_v = v;
+    c->cap_tab = tab;
+    c->has_render = false;
+    VT_CUDA(cudaMemsetAsync(c->status, 0, sizeof(Status), s), "status init");
+    return VT_OK;
+}
+
+int64_t default_instances(int64_t g) { return 4 * g + 65536; }
+
+vt_status check_intrinsics(const vt_intrinsics &K, const char *who) {
+    if (!finite_pos(K.fx) || !finite_pos(K.fy) || !finite(K.cx) || !finite(K.cy))
+        return fail(VT_ERR_INVALID_ARG, "%s: intrinsics must be finite with fx, fy > 0", who);
+    return VT_OK;
+}
+
+vt_status check_image(int32_t W, int32_t H, const char *who) {
+    if (W <= 0 || H <= 0 || (int64_t)W * H > (int64_t)1 << 31 || W > 16 * 65535 ||
+        H > 16 * 65535)
+        return fail(VT_ERR_INVALID_ARG, "%s: image size %d x %d out of range", who, W, H);
+    return VT_OK;
+}
+
+bool sort_attr_set = false;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *vt_last_error(void) { return g_err.c_str(); }
+
+const char *vt_version(void) { return "vtsplat 0.1 (sm_103a)"; }
+
+vt_status vt_ctx_create(vt_ctx **ctx) {
+    if (!ctx) return fail(VT_ERR_INVALID_ARG, "vt_ctx_create: ctx is NULL");
+    vt_ctx *c = new (std::nothrow) vt_ctx();
+    if (!c) return fail(VT_ERR_OOM, "vt_ctx_create: out of host memory");
+    cudaGetDevice(&c->device);
+    *ctx = c;
+    return VT_OK;
+}
+
+void vt_ctx_destroy(vt_ctx *c) {
+    if (!c) return;
+    free_arena(c, c->stream);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+size_t vt_workspace_bytes(int64_t n_gaussians, int32_t W, int32_t H, int64_t n_instances) {
+    if (n_gaussians < 0 || W <= 0 || H <= 0) return 0;
+    if (n_instances <= 0) n_instances = default_instances(n_gaussians);
+    const int64_t tiles = (int64_t)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+    return arena_bytes_for(n_gaussians, n_instances, (int64_t)W * H, tiles, 0, 0);
+}
+
+vt_status vt_ctx_reserve(vt_ctx *c, int64_t n_gaussians, int32_t W, int32_t H,
+                         int64_t n_instances, vt_stream stream) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_ctx_reserve: ctx is NULL");
+    if (n_gaussians < 0) return fail(VT_ERR_INVALID_ARG, "vt_ctx_reserve: n_gaussians < 0");
+    vt_status st = check_image(W, H, "vt_ctx_reserve");
+    if (st) return st;
+    if (n_instances <= 0) n_instances = default_instances(n_gaussians);
+    c->reserved_i = std::max(c->reserved_i, n_instances);
+    const int64_t tiles = (int64_t)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+    c->stream = stream;
+    return ensure(c, std::max<int64_t>(n_gaussians, 1), n_instances, (int64_t)W * H, tiles,
+                  std::max<int64_t>(c->cap_v, 1), std::max<int64_t>(c->cap_tab, 1), stream);
+}
+
+vt_status vt_ctx_sync_status(vt_ctx *c, vt_stream stream, int64_t *needed) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_ctx_sync_status: ctx is NULL");
+    VT_CUDA(cudaStreamSynchronize(stream), "vt_ctx_sync_status");
+    if (!c->status) {
+        if (needed) *needed = 0;
+        return VT_OK;
+    }
+    Status h;
+    VT_CUDA(cudaMemcpy(&h, c->status, sizeof h, cudaMemcpyDeviceToHost), "status copy");
+    if (needed) *needed = (int64_t)h.n_instances;
+    if (h.flags & kFlagCapacity)
+        return fail(VT_ERR_CAPACITY, "render needed %llu tile instances, workspace holds %lld",
+                    h.n_instances, (long long)c->cap_i);
+    return VT_OK;
+}
+
+vt_status vt_ctx_set_timing(vt_ctx *c, int32_t enable) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_ctx_set_timing: ctx is NULL");
+    c->timing = enable != 0;
+    return VT_OK;
+}
+
+int32_t vt_ctx_timing(vt_ctx *c, vt_stream stream, const char **names, int64_t *launches,
+                      double *ms, int32_t n_max, int32_t reset) {
+    if (!c) return -VT_ERR_INVALID_ARG;
+    cudaStreamSynchronize(stream);
+    for (auto &p : c->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+            c->t_ms[p.kernel] += t;
+            c->t_launches[p.kernel] += 1;
+        }
+        c->event_pool.push_back(p.a);
+        c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+    int32_t n = 0;
+    for (int k = 0; k < K_NUM && n < n_max; ++k) {
+        if (names) names[n] = kKernelNames[k];
+        if (launches) launches[n] = c->t_launches[k];
+        if (ms) ms[n] = c->t_ms[k];
+        ++n;
+    }
+    if (reset)
+        for (int k = 0; k < K_NUM; ++k) {
+            c->t_ms[k] = 0;
+            c->t_launches[k] = 0;
+        }
+    return n;
+}
+
+int64_t vt_ctx_launch_count(const vt_ctx *c) { return c ? c->launches : 0; }
+
+vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const double *pose12,
+                    vt_intrinsics K, int32_t W, int32_t H, float *rgb, float *depth,
+                    float *silhouette, vt_stream stream) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_render: ctx is NULL");
+    if (!pose12) return fail(VT_ERR_INVALID_ARG, "vt_render: pose is NULL");
+    if (n_secs < 0 || n_secs > kMaxSecs || (n_secs > 0 && !secs))
+        return fail(VT_ERR_INVALID_ARG, "vt_render: n_secs must be in [0, %d]", kMaxSecs);
+    vt_status st = check_intrinsics(K, "vt_render");
+    if (st) return st;
+    if ((st = check_image(W, H, "vt_render"))) return st;
+    SecTable T{};
+    T.n = n_secs;
+    int64_t total = 0, views = 0, tabrows = 0;
+    for (int s = 0; s < n_secs; ++s) {
+        const vt_section &S = secs[s];
+        if (S.n < 0) return fail(VT_ERR_INVALID_ARG, "vt_render: section %d has n < 0", s);
+        if (S.n_views <= 0 || S.W <= 0 || S.H <= 0 ||
+            (int64_t)S.n_views * S.W * S.H > (int64_t)0xffffffffll)
+            return fail(VT_ERR_INVALID_ARG, "vt_render: section %d views/size out of range", s);
+        if (S.prec != VT_F32 && S.prec != VT_F16)
+            return fail(VT_ERR_INVALID_ARG, "vt_render: section %d precision %d unknown", s,
+                        (int)S.prec);
+        if ((st = check_intrinsics(S.K, "vt_render section"))) return st;
+        if (S.n > 0 && (!S.poses || !S.depth || !S.src || !S.colour || !S.opacity || !S.radius))
+            return fail(VT_ERR_INVALID_ARG, "vt_render: section %d has a NULL array", s);
+        SecDesc &D = T.s[s];
+        D.poses = S.poses;
+        D.depth = S.depth;
+        D.src = S.src;
+        D.colour = S.colour;
+        D.opacity = S.opacity;
+        D.radius = S.radius;
+        D.d_colour = D.d_opacity = D.d_radius = nullptr;
+        D.gbase = total;
+        D.n = S.n;
+        D.tab_base = tabrows;
+        D.view_base = (int32_t)views;
+        D.n_views = S.n_views;
+        D.W = S.W;
+        D.H = S.H;
+        D.prec = (int32_t)S.prec;
+        D.fx = S.K.fx;
+        D.fy = S.K.fy;
+        D.cx = S.K.cx;
+        D.cy = S.K.cy;
+        total += S.n;
+        views += S.n_views;
+        tabrows += (int64_t)S.n_views * (S.W + S.H);
+    }
+    if (total >= (int64_t)0xffffffffll)
+        return fail(VT_ERR_INVALID_ARG, "vt_render: %lld Gaussians exceed 2^32 - 1",
+                    (long long)total);
+    T.n_total = total;
+    Camera cam;
+    cam.fx = K.fx;
+    cam.fy = K.fy;
+    cam.cx = K.cx;
+    cam.cy = K.cy;
+    cam.W = W;
+    cam.H = H;
+    cam.tiles_x = (W + kTile - 1) / kTile;
+    cam.tiles_y = (H + kTile - 1) / kTile;
+    const int n_tiles = cam.tiles_x * cam.tiles_y;
+    const int64_t want_i = std::max(c->reserved_i, default_instances(total));
+    c->stream = stream;
+    if ((st = ensure(c, std::max<int64_t>(total, 1), std::max(want_i, c->cap_i), (int64_t)W * H,
+                     n_tiles, std::max<int64_t>(views, 1), std::max<int64_t>(tabrows, 1), stream)))
+        return st;
+    if (!sort_attr_set) {
+        VT_CUDA(cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSortSmemBytes),
+                "sort smem attribute");
+        sort_attr_set = true;
+    }
+    c->has_render = false;
+    VT_CUDA(cudaMemsetAsync(c->tile_count, 0, sizeof(uint32_t) * (n_tiles + 1), stream),
+            "tile count reset");
+    if (views > 0) {
+        LaunchScope ls(c, K_SETUP, stream);
+        k_setup<<<(unsigned)views, 256, 0, stream>>>(T, cam, pose12, c->views, c->tab,
+                                                    c->pose_copy);
+    } else {
+        VT_CUDA(cudaMemcpyAsync(c->pose_copy, pose12, 12 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, stream),
+                "pose copy");
+    }
+    const unsigned gblocks = (unsigned)((total + 255) / 256);
+    if (total > 0) {
+        LaunchScope ls(c, K_PREPROCESS, stream);
+        k_preprocess<<<gblocks, 256, 0, stream>>>(T, cam, c->views, c->tab, c->geo, c->app,
+                                                  c->info, c->tile_count);
+    }
+    {
+        LaunchScope ls(c, K_SCAN, stream);
+        k_scan_tiles<<<1, 1024, 0, stream>>>(c->tile_count, n_tiles, c->tile_off, c->tile_cursor,
+                                             c->status, (unsigned long long)c->cap_i);
+    }
+    if (total > 0) {
+        LaunchScope ls(c, K_EMIT, stream);
+        k_emit<<<gblocks, 256, 0, stream>>>(total, c->info, cam, c->tile_cursor, c->bucket,
+                                            c->status);
+    }
+    {
+        LaunchScope ls(c, K_SORT, stream);
+        k_sort_tiles<<<n_tiles, 512, kSortSmemBytes, stream>>>(c->tile_off, n_tiles, c->bucket,
+                                                               c->alt, c->sorted, c->status,
+                                                               kSortSmemN);
+    }
+    {
+        LaunchScope ls(c, K_FWD, stream);
+        k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(cam, c->tile_off, c->sorted, c->geo,
+                                                           c->app, rgb, depth, silhouette,
+                                                           c->pix_last, c->pix_nadd, c->pix_T,
+                                                           c->status);
+    }
+    VT_CUDA(cudaGetLastError(), "vt_render launch");
+    c->table = T;
+    c->cam = cam;
+    c->n_tiles = n_tiles;
+    c->has_render = true;
+    return VT_OK;
+}
+
+vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_ddepth,
+                             const float *dL_dsil, int32_t mode, const vt_grads *grads,
+                             double *d_twist, double *d_mat, vt_stream stream) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_render_backward: ctx is NULL");
+    if (!c->has_render) return fail(VT_ERR_STATE, "vt_render_backward: no render on this context");
+    if (mode & ~(VT_GRAD_ATTR | VT_GRAD_POSE))
+        return fail(VT_ERR_INVALID_ARG, "vt_render_backward: unknown mode bits 0x%x", mode);
+    if ((mode & VT_GRAD_ATTR) && !grads && c->table.n > 0)
+        return fail(VT_ERR_INVALID_ARG, "vt_render_backward: ATTR mode needs grads");
+    if ((mode & VT_GRAD_POSE) && !d_twist && !d_mat)
+        return fail(VT_ERR_INVALID_ARG, "vt_render_backward: POSE mode needs d_twist or d_mat");
+    if (!mode) return VT_OK;
+    SecTable T = c->table;
+    for (int s = 0; s < T.n; ++s) {
+        if (mode & VT_GRAD_ATTR) {
+            T.s[s].d_colour = grads[s].d_colour;
+            T.s[s].d_opacity = grads[s].d_opacity;
+            T.s[s].d_radius = grads[s].d_radius;
+        }
+    }
+    {
+        LaunchScope ls(c, K_BWD, stream);
+        k_composite_bwd<<<c->n_tiles, kBlockPix, 0, stream>>>(
+            T, c->cam, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, dL_drgb,
+            dL_ddepth, dL_dsil, mode, c->pose_partials, c->status);
+    }
+    if (mode & VT_GRAD_POSE) {
+        LaunchScope ls(c, K_POSE, stream);
+        k_pose_finalize<<<1, 384, 0, stream>>>(c->pose_partials, c->n_tiles, c->pose_copy, d_twist,
+                                               d_mat);
+    }
+    VT_CUDA(cudaGetLastError(), "vt_render_backward launch");
+    return VT_OK;
+}
+
+// Ordered compaction scratch: per-block counts and offsets, stream-ordered
+// allocation released on the same stream after the launches.
+static vt_status compaction_scratch(int64_t total, uint32_t **counts, uint32_t **offs,
+                                    int64_t *nb, cudaStream_t s) {
+    *nb = (total + kInitBlock - 1) / kInitBlock;
+    void *p = nullptr;
+    const size_t bytes = sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(*nb, 1);
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VT_ERR_OOM, "compaction scratch of %zu bytes: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    *counts = static_cast<uint32_t *>(p);
+    *offs = *counts + std::max<int64_t>(*nb, 1);
+    return VT_OK;
+}
+
+vt_status vt_backproject(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                         const double *pose12, float *centres, uint32_t *pix, int64_t cap,
+                         int64_t *n_out, vt_stream stream) {
+    vt_status st = check_image(W, H, "vt_backproject");
+    if (st) return st;
+    if ((st = check_intrinsics(K, "vt_backproject"))) return st;
+    if (!depth || !pose12 || !n_out || cap < 0 || (cap > 0 && (!centres || !pix)))
+        return fail(VT_ERR_INVALID_ARG, "vt_backproject: NULL pointer or negative capacity");
+    const int64_t total = (int64_t)W * H;
+    uint32_t *counts, *offs;
+    int64_t nb;
+    if ((st = compaction_scratch(total, &counts, &offs, &nb, stream))) return st;
+    k_count_valid<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, total, counts);
+    k_scan_counts<<<1, 1024, 0, stream>>>(counts, nb, offs, reinterpret_cast<long long *>(n_out));
+    k_backproject<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, W, H, K, pose12, offs, centres,
+                                                           pix, cap);
+    cudaFreeAsync(counts, stream);
+    VT_CUDA(cudaGetLastError(), "vt_backproject launch");
+    return VT_OK;
+}
+
+vt_status vt_section_init(const float *depth, const float *rgb, int32_t n_views, int32_t W,
+                          int32_t H, vt_intrinsics K, vt_precision prec, uint32_t *src,
+                          void *colour, void *opacity, void *radius, int64_t cap,
+                          int64_t *n_out, vt_stream stream) {
+    vt_status st = check_image(W, H, "vt_section_init");
+    if (st) return st;
+    if ((st = check_intrinsics(K, "vt_section_init"))) return st;
+    if (n_views <= 0 || (int64_t)n_views * W * H > (int64_t)0xffffffffll)
+        return fail(VT_ERR_INVALID_ARG, "vt_section_init: n_views out of range");
+    if (prec != VT_F32 && prec != VT_F16)
+        return fail(VT_ERR_INVALID_ARG, "vt_section_init: unknown precision");
+    if (!depth || !rgb || !n_out || cap < 0 ||
+        (cap > 0 && (!src || !colour || !opacity || !radius)))
+        return fail(VT_ERR_INVALID_ARG, "vt_section_init: NULL pointer or negative capacity");
+    const int64_t plane = (int64_t)W * H, total = plane * n_views;
+    uint32_t *counts, *offs;
+    int64_t nb;
+    if ((st = compaction_scratch(total, &counts, &offs, &nb, stream))) return st;
+    k_count_valid<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, total, counts);
+    k_scan_counts<<<1, 1024, 0, stream>>>(counts, nb, offs, reinterpret_cast<long long *>(n_out));
+    k_section_init<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, rgb, plane, total, K.fx,
+                                                            (int)prec, offs, src, colour,
+                                                            opacity, radius, cap);
+    cudaFreeAsync(counts, stream);
+    VT_CUDA(cudaGetLastError(), "vt_section_init launch");
+    return VT_OK;
+}
+
+int64_t vt_ctx_debug_copy(vt_ctx *c, int32_t what, void *dst, int64_t capacity,
+                          vt_stream stream) {
+    if (!c || !dst || capacity < 0) return -VT_ERR_INVALID_ARG;
+    if (!c->has_render) return -VT_ERR_STATE;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return -VT_ERR_CUDA;
+    Status h;
+    if (cudaMemcpy(&h, c->status, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -VT_ERR_CUDA;
+    const int64_t P = (int64_t)c->cam.W * c->cam.H;
+    const void *src = nullptr;
+    int64_t bytes = 0;
+    std::vector<uint4> tmp;
+    switch (what) {
+        case 0: {
+            const int64_t n = c->table.n_total;
+            bytes = n * 4;
+            if (bytes > capacity) return -VT_ERR_INVALID_ARG;
+            tmp.resize(n);
+            if (n && cudaMemcpy(tmp.data(), c->info, n * sizeof(uint4), cudaMemcpyDeviceToHost) !=
+                         cudaSuccess)
+                return -VT_ERR_CUDA;
+            uint32_t *o = static_cast<uint32_t *>(dst);
+            for (int64_t i = 0; i < n; ++i) o[i] = tmp[i].z;
+            return bytes;
+        }
+        case 1: src = c->tile_off; bytes = 4 * (int64_t)(c->n_tiles + 1); break;
+        case 2: src = c->sorted; bytes = 4 * std::min<int64_t>(h.n_instances, c->cap_i); break;
+        case 3: src = c->pix_last; bytes = 4 * P; break;
+        case 4: src = c->pix_nadd; bytes = 4 * P; break;
+        case 5: src = c->pix_T; bytes = 4 * P; break;
+        default: return -VT_ERR_INVALID_ARG;
+    }
+    if (bytes > capacity) return -VT_ERR_INVALID_ARG;
+    if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -VT_ERR_CUDA;
+    return bytes;
+}
+
+}  // extern "C"

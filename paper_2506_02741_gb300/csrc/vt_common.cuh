@@ -1,0 +1,204 @@
+// Shared device definitions of the vtsplat CUDA library (sm_103a).
+//
+// Layout of the workspace a render keeps (all in HBM, library-owned):
+//   geo[g]   : float4 x 2 per Gaussian  {iu, fu, iv, fv} {kx, ky, z, o}
+//   app[g]   : float4 per Gaussian      {c0, c1, c2, r}
+//   info[g]  : uint4 per Gaussian       {tx0 | ty0<<16, tx1 | ty1<<16, zkey bits, n_tiles}
+//   bucket   : uint64 per instance      (zkey << 32 | gid), unsorted per tile
+//   sorted   : uint32 per instance      Gaussian ids, per tile in (zkey, gid) order
+//   per pixel: list end, count added, final transmittance
+// The projected centre of a Gaussian in pixels is iu + fu (integer part and
+// a float remainder), accurate to ~1e-7 px, because footprints are only
+// about one pixel wide while centres lie hundreds of pixels from the origin.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vtsplat.h"
+
+namespace vt {
+
+constexpr int kTile = 16;          // tile edge in pixels
+constexpr int kBlockPix = 256;     // threads of a compositing block (one per pixel)
+constexpr int kBatch = 256;        // Gaussians staged in shared memory per step
+constexpr int kMaxSecs = 16;       // sections per render
+constexpr float kQMax = 9.0f;      // 3-sigma disc
+constexpr float kZNear = 0.1f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaClamp = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+// Status flags written on the device.
+constexpr int kFlagCapacity = 1;
+
+struct SecDesc {
+    const double *poses;    // n_views x 12 camera-to-world
+    const float *depth;
+    const uint32_t *src;
+    const void *colour, *opacity, *radius;
+    float *d_colour, *d_opacity, *d_radius;  // backward only
+    int64_t gbase, n;       // global id range [gbase, gbase + n)
+    int64_t tab_base;       // first table row of view 0
+    int32_t view_base;      // first ViewXf of this section
+    int32_t n_views, W, H, prec;
+    float fx, fy, cx, cy;
+};
+
+struct SecTable {
+    int32_t n;
+    int64_t n_total;
+    SecDesc s[kMaxSecs];
+};
+
+struct Camera {
+    float fx, fy, cx, cy;
+    int32_t W, H, tiles_x, tiles_y;
+};
+
+// Per source view, per render: FP32 composite transform for the depth key
+// and the float-float offsets of the projection numerators.
+struct ViewXf {
+    float Mf[12];            // R^T R_k (row-major) then R^T (t_k - t), rounded to FP32
+    float2 mu, mv, mz;       // fx m0 + cx m2, fy m1 + cy m2, m2 (float-float)
+    float pad[2];
+};
+
+// One table row: three float-float values (u numerator, v numerator, z).
+struct TabRow {
+    float2 a, b, c;
+};
+
+struct Status {
+    int32_t flags;
+    int32_t pad;
+    unsigned long long n_instances;
+    unsigned long long n_overflow_tiles;
+};
+
+// ---------------------------------------------------------------------------
+// float-float ("double-single") arithmetic: Knuth's TwoSum, Dekker's
+// FastTwoSum and the FMA-based exact product.  Every operation uses the
+// explicit round-to-nearest intrinsics so that no contraction or
+// reassociation can break the error-free transformations.
+
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return ff_fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return ff_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_from_double(double d) {
+    float hi = __double2float_rn(d);
+    float lo = __double2float_rn(__dsub_rn(d, (double)hi));
+    return {hi, lo};
+}
+
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    ff p = ff_mul_f(b, q1);
+    ff r = ff_add(a, ff{-p.hi, -p.lo});
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return ff_fast_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ ff ff_from(float2 v) { return {v.x, v.y}; }
+
+// ---------------------------------------------------------------------------
+// Shared per-pair footprint: q = du^2 kx + dv^2 ky with explicit rounding so
+// that the forward and backward kernels take bit-identical decisions.
+__device__ __forceinline__ float pair_q(int px, int py, const float4 &g0, const float4 &g1,
+                                        float &du, float &dv) {
+    du = __fsub_rn((float)(px - __float_as_int(g0.x)), g0.y);
+    dv = __fsub_rn((float)(py - __float_as_int(g0.z)), g0.w);
+    float a = __fmul_rn(__fmul_rn(du, du), g1.x);
+    return __fmaf_rn(__fmul_rn(dv, dv), g1.y, a);
+}
+
+__device__ __forceinline__ float pair_gauss(float q) { return __expf(__fmul_rn(-0.5f, q)); }
+
+// Attribute loads in either storage precision.
+__device__ __forceinline__ float ld_attr(const void *p, int prec, int64_t i) {
+    if (prec == VT_F16) return __half2float(reinterpret_cast<const __half *>(p)[i]);
+    return reinterpret_cast<const float *>(p)[i];
+}
+
+__device__ __forceinline__ int find_section(const SecTable &T, int64_t gid) {
+    int s = 0;
+#pragma unroll 1
+    for (int k = 1; k < T.n; ++k)
+        if (gid >= T.s[k].gbase) s = k;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel entry points (defined in the .cu files, launched from vt_api.cu).
+
+__global__ void k_setup(SecTable T, Camera cam, const double *pose12, ViewXf *views, TabRow *tab,
+                        double *pose_copy);
+__global__ void k_preprocess(SecTable T, Camera cam, const ViewXf *views, const TabRow *tab,
+                             float4 *geo, float4 *app, uint4 *info, uint32_t *tile_count);
+__global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *tile_off,
+                             uint32_t *tile_cursor, Status *st, unsigned long long cap);
+__global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
+                       unsigned long long *bucket, const Status *st);
+__global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,
+                             unsigned long long *alt, uint32_t *sorted, Status *st, int smem_n);
+__global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
+                                const float4 *geo, const float4 *app, float *rgb, float *depth,
+                                float *sil, uint32_t *pix_last, uint32_t *pix_nadd,
+                                float *pix_T, const Status *st);
+__global__ void k_composite_bwd(SecTable T, Camera cam, const uint32_t *tile_off,
+                                const uint32_t *sorted, const float4 *geo, const float4 *app,
+                                const uint32_t *pix_last, const float *pix_T,
+                                const float *g_rgb, const float *g_depth, const float *g_sil,
+                                int mode, double *pose_partials, const Status *st);
+__global__ void k_pose_finalize(const double *partials, int n_parts, const double *pose_copy,
+                                double *d_twist, double *d_mat);
+__global__ void k_count_valid(const float *depth, int64_t total, uint32_t *block_counts);
+__global__ void k_scan_counts(const uint32_t *counts, int64_t n, uint32_t *offs,
+                              long long *n_out);
+__global__ void k_backproject(const float *depth, int W, int H, vt_intrinsics K,
+                              const double *pose12, const uint32_t *offs, float *centres,
+                              uint32_t *pix, int64_t cap);
+__global__ void k_section_init(const float *depth, const float *rgb, int64_t plane,
+                               int64_t total, float fx, int prec, const uint32_t *offs,
+                               uint32_t *src, void *colour, void *opacity, void *radius,
+                               int64_t cap);
+
+constexpr int kInitBlock = 256;
+
+}  // namespace vt

@@ -1,0 +1,464 @@
+// Projection, tile binning and per-tile depth sort: the forward steps before
+// compositing.  sm_103a; no tensor cores (nothing here is a contraction).
+#include "vt_common.cuh"
+
+namespace vt {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// k_setup: one block per source view.  Thread 0 forms in FP64 the composite
+// transform of the view into the target camera, M = R^T R_k and
+// m = R^T (t_k - t), in the fixed operation order that defines the depth key
+// (each product and sum rounded on its own), plus the projection rows
+// U = fx M0 + cx M2, V = fy M1 + cy M2, Z = M2 and offsets as float-float.
+// The block then fills the view's float-float tables, column u:
+// (U0, V0, Z0) * a_u and row v: (U1, V1, Z1) * b_v + (U2, V2, Z2), with
+// a_u = (u - cx_k)/fx_k, b_v = (v - cy_k)/fy_k, so that the projected centre's
+// numerators are D * (A[u] + B[v]) + (mu, mv, mz).
+__global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const double *pose12,
+                                               ViewXf *views, TabRow *tab, double *pose_copy) {
+    __shared__ ff rows[9];  // U0 U1 U2 V0 V1 V2 Z0 Z1 Z2
+    const int gv = blockIdx.x;
+    int s = 0;
+    for (int j = 1; j < T.n; ++j)
+        if (gv >= T.s[j].view_base) s = j;
+    const SecDesc &S = T.s[s];
+    const int k = gv - S.view_base;
+    if (threadIdx.x == 0) {
+        const double *R = pose12, *t = pose12 + 9;
+        const double *Rk = S.poses + 12 * k, *tk = Rk + 9;
+        double M[9], m[3];
+        const double d0 = __dsub_rn(tk[0], t[0]), d1 = __dsub_rn(tk[1], t[1]),
+                     d2 = __dsub_rn(tk[2], t[2]);
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) {
+                double acc = __dmul_rn(R[0 * 3 + a], Rk[0 * 3 + b]);
+                acc = __dadd_rn(acc, __dmul_rn(R[1 * 3 + a], Rk[1 * 3 + b]));
+                acc = __dadd_rn(acc, __dmul_rn(R[2 * 3 + a], Rk[2 * 3 + b]));
+                M[a * 3 + b] = acc;
+            }
+            double acc = __dmul_rn(R[0 * 3 + a], d0);
+            acc = __dadd_rn(acc, __dmul_rn(R[1 * 3 + a], d1));
+            acc = __dadd_rn(acc, __dmul_rn(R[2 * 3 + a], d2));
+            m[a] = acc;
+        }
+        ViewXf X;
+        for (int i = 0; i < 9; ++i) X.Mf[i] = __double2float_rn(M[i]);
+        for (int i = 0; i < 3; ++i) X.Mf[9 + i] = __double2float_rn(m[i]);
+        const double fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
+        for (int b = 0; b < 3; ++b) {
+            rows[0 + b] = ff_from_double(fx * M[0 * 3 + b] + cx * M[2 * 3 + b]);
+            rows[3 + b] = ff_from_double(fy * M[1 * 3 + b] + cy * M[2 * 3 + b]);
+            rows[6 + b] = ff_from_double(M[2 * 3 + b]);
+        }
+        ff mu = ff_from_double(fx * m[0] + cx * m[2]);
+        ff mv = ff_from_double(fy * m[1] + cy * m[2]);
+        ff mz = ff_from_double(m[2]);
+        X.mu = make_float2(mu.hi, mu.lo);
+        X.mv = make_float2(mv.hi, mv.lo);
+        X.mz = make_float2(mz.hi, mz.lo);
+        X.pad[0] = X.pad[1] = 0.f;
+        views[gv] = X;
+        if (gv == 0)
+            for (int i = 0; i < 12; ++i) pose_copy[i] = pose12[i];
+    }
+    __syncthreads();
+    const int W = S.W, H = S.H;
+    TabRow *tb = tab + S.tab_base + (int64_t)k * (W + H);
+    for (int i = threadIdx.x; i < W + H; i += blockDim.x) {
+        TabRow out;
+        if (i < W) {
+            ff a = ff_div(ff_two_sum((float)i, -S.cx), ff{S.fx, 0.f});
+            ff pu = ff_mul(rows[0], a), pv = ff_mul(rows[3], a), pz = ff_mul(rows[6], a);
+            out.a = make_float2(pu.hi, pu.lo);
+            out.b = make_float2(pv.hi, pv.lo);
+            out.c = make_float2(pz.hi, pz.lo);
+        } else {
+            ff b = ff_div(ff_two_sum((float)(i - W), -S.cy), ff{S.fy, 0.f});
+            ff pu = ff_add(ff_mul(rows[1], b), rows[2]);
+            ff pv = ff_add(ff_mul(rows[4], b), rows[5]);
+            ff pz = ff_add(ff_mul(rows[7], b), rows[8]);
+            out.a = make_float2(pu.hi, pu.lo);
+            out.b = make_float2(pv.hi, pv.lo);
+            out.c = make_float2(pz.hi, pz.lo);
+        }
+        tb[i] = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-aggregated visit of the tiles of each lane's tile rectangle: lanes
+// that hit the same tile in the same step share one atomic.  fn(tile, peers,
+// rank) is called by every active lane; the lowest lane of each peer group
+// is the leader.
+template <class Fn>
+__device__ __forceinline__ void for_each_tile(uint32_t r0, uint32_t r1, uint32_t nt, int tiles_x,
+                                              Fn &&fn) {
+    const int lane = threadIdx.x & 31;
+    const unsigned maxnt = __reduce_max_sync(kFull, nt);
+    const uint32_t tx0 = r0 & 0xffffu, ty0 = r0 >> 16, tx1 = r1 & 0xffffu;
+    const uint32_t w = tx1 - tx0 + 1;
+    for (unsigned j = 0; j < maxnt; ++j) {
+        const bool act = j < nt;
+        const unsigned am = __ballot_sync(kFull, act);
+        if (act) {
+            const uint32_t jy = j / w, jx = j - jy * w;
+            const uint32_t t = (ty0 + jy) * (uint32_t)tiles_x + tx0 + jx;
+            const unsigned peers = __match_any_sync(am, t);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            fn(t, peers, rank);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_preprocess: one thread per Gaussian.  Gathers its depth pixel, computes
+// the FP32 depth key (fixed operation order, identical to the definition),
+// culls invalid depth, z_key < 0.1 and opacity < 1/255, projects the centre
+// in float-float, derives the footprint coefficients kx = (z / (fx r))^2,
+// ky = (z / (fy r))^2 (q = du^2 kx + dv^2 ky in pixels) and the conservative
+// pixel box of the disc q <= min(9, 2 ln(255 o)), and counts its tiles.
+__global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, const ViewXf *views,
+                                                    const TabRow *tab, float4 *geo, float4 *app,
+                                                    uint4 *info, uint32_t *tile_count) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t r0 = 0, r1 = 0, nt = 0, zbits = 0;
+    if (gid < T.n_total) {
+        const int s = find_section(T, gid);
+        const SecDesc &S = T.s[s];
+        const int64_t li = gid - S.gbase;
+        const uint32_t src = S.src[li];
+        const uint32_t plane = (uint32_t)S.W * (uint32_t)S.H;
+        const uint32_t k = src / plane;
+        const uint32_t pix = src - k * plane;
+        const uint32_t v = pix / (uint32_t)S.W;
+        const uint32_t u = pix - v * (uint32_t)S.W;
+        const bool in_range = k < (uint32_t)S.n_views;   // src beyond the views: no Gaussian
+        const float D = in_range ? S.depth[src] : 0.f;
+        const float o = ld_attr(S.opacity, S.prec, li);
+        const float r = ld_attr(S.radius, S.prec, li);
+        bool ok = in_range && isfinite(D) && D > 0.f && o >= kAlphaMin && r > 0.f && isfinite(r);
+        const ViewXf &X = views[S.view_base + (ok ? k : 0)];
+        float zkey = 0.f;
+        if (ok) {
+            // depth key: a = (u - cx)/fx, b = (v - cy)/fy, X = D a, Y = D b,
+            // z = ((M20 X + M21 Y) + M22 D) + m2, every step rounded to FP32.
+            const float a = __fdiv_rn(__fsub_rn((float)u, S.cx), S.fx);
+            const float b = __fdiv_rn(__fsub_rn((float)v, S.cy), S.fy);
+            const float Xc = __fmul_rn(D, a), Yc = __fmul_rn(D, b);
+            float z = __fmul_rn(X.Mf[6], Xc);
+            z = __fadd_rn(z, __fmul_rn(X.Mf[7], Yc));
+            z = __fadd_rn(z, __fmul_rn(X.Mf[8], D));
+            zkey = __fadd_rn(z, X.Mf[11]);
+            ok = zkey >= kZNear;
+        }
+        if (ok) {
+            const TabRow *tb = tab + S.tab_base + (int64_t)k * (S.W + S.H);
+            const TabRow A = tb[u], B = tb[S.W + v];
+            const ff hu = ff_add(ff_from(A.a), ff_from(B.a));
+            const ff hv = ff_add(ff_from(A.b), ff_from(B.b));
+            const ff hz = ff_add(ff_from(A.c), ff_from(B.c));
+            const ff nu = ff_add(ff_mul_f(hu, D), ff_from(X.mu));
+            const ff nv = ff_add(ff_mul_f(hv, D), ff_from(X.mv));
+            const ff nz = ff_add(ff_mul_f(hz, D), ff_from(X.mz));
+            const ff uc = ff_div(nu, nz), vc = ff_div(nv, nz);
+            const float z = nz.hi;
+            const float tx = __fdiv_rn(z, __fmul_rn(cam.fx, r));
+            const float ty = __fdiv_rn(z, __fmul_rn(cam.fy, r));
+            const float kx = __fmul_rn(tx, tx), ky = __fmul_rn(ty, ty);
+            float qlim = kQMax;
+            const float qo = 2.f * logf(255.f * o);
+            if (qo < qlim) qlim = qo;
+            qlim = qlim * 1.0001f + 1e-4f;
+            const float ex = sqrtf(qlim / kx) + 1e-3f, ey = sqrtf(qlim / ky) + 1e-3f;
+            ok = z > 0.f && kx > 0.f && ky > 0.f && isfinite(kx) && isfinite(ky) &&
+                 fabsf(uc.hi) < 16777216.f && fabsf(vc.hi) < 16777216.f;
+            if (ok) {
+                const float u0 = fmaxf(ceilf(uc.hi - ex), 0.f);
+                const float u1 = fminf(floorf(uc.hi + ex), (float)(cam.W - 1));
+                const float v0 = fmaxf(ceilf(vc.hi - ey), 0.f);
+                const float v1 = fminf(floorf(vc.hi + ey), (float)(cam.H - 1));
+                ok = u0 <= u1 && v0 <= v1;
+                if (ok) {
+                    const uint32_t tx0 = (uint32_t)u0 / kTile, tx1 = (uint32_t)u1 / kTile;
+                    const uint32_t ty0 = (uint32_t)v0 / kTile, ty1 = (uint32_t)v1 / kTile;
+                    r0 = tx0 | (ty0 << 16);
+                    r1 = tx1 | (ty1 << 16);
+                    nt = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+                    zbits = __float_as_uint(zkey);
+                    const int iu = __float2int_rn(uc.hi), iv = __float2int_rn(vc.hi);
+                    const float fu = __fadd_rn(__fsub_rn(uc.hi, (float)iu), uc.lo);
+                    const float fv = __fadd_rn(__fsub_rn(vc.hi, (float)iv), vc.lo);
+                    geo[2 * gid] = make_float4(__int_as_float(iu), fu, __int_as_float(iv), fv);
+                    geo[2 * gid + 1] = make_float4(kx, ky, z, o);
+                    const float c0 = ld_attr(S.colour, S.prec, 3 * li + 0);
+                    const float c1 = ld_attr(S.colour, S.prec, 3 * li + 1);
+                    const float c2 = ld_attr(S.colour, S.prec, 3 * li + 2);
+                    app[gid] = make_float4(c0, c1, c2, r);
+                }
+            }
+        }
+        info[gid] = make_uint4(r0, r1, zbits, nt);
+    }
+    for_each_tile(r0, r1, nt, cam.tiles_x, [&](uint32_t t, unsigned peers, int rank) {
+        if (rank == 0) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
+    });
+}
+
+// ---------------------------------------------------------------------------
+// k_scan_tiles: one block; exclusive prefix sum of the per-tile counts into
+// tile offsets (tile_off[n_tiles] = instance total) and insertion cursors.
+// Flags a capacity shortage instead of letting later kernels overrun.
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count, int n_tiles,
+                                                     uint32_t *tile_off, uint32_t *tile_cursor,
+                                                     Status *st, unsigned long long cap) {
+    __shared__ unsigned long long warp_sums[32];
+    __shared__ unsigned long long carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_tiles; base += 1024) {
+        const int i = base + tid;
+        const unsigned long long c = i < n_tiles ? tile_count[i] : 0ull;
+        unsigned long long x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = warp_sums[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long excl = carry + (warp ? warp_sums[warp - 1] : 0ull) + x - c;
+        if (i < n_tiles) {
+            tile_off[i] = (uint32_t)excl;
+            tile_cursor[i] = (uint32_t)excl;
+        }
+        __syncthreads();
+        if (tid == 1023) carry = excl + c;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        tile_off[n_tiles] = (uint32_t)carry;
+        st->n_instances = carry;
+        st->n_overflow_tiles = 0;
+        st->flags = carry > cap || carry >= 0xffffffffull ? kFlagCapacity : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_emit: one thread per Gaussian; appends (zkey << 32 | gid) to the bucket of
+// every tile of its rectangle (the same tiles counted in k_preprocess).
+__global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Camera cam,
+                                              uint32_t *tile_cursor,
+                                              unsigned long long *bucket, const Status *st) {
+    if (st->flags) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint4 in = make_uint4(0, 0, 0, 0);
+    if (gid < n) in = info[gid];
+    const unsigned long long key = ((unsigned long long)in.z << 32) | (unsigned long long)gid;
+    const int lane = threadIdx.x & 31;
+    for_each_tile(in.x, in.y, in.w, cam.tiles_x, [&](uint32_t t, unsigned peers, int rank) {
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&tile_cursor[t], (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        bucket[base + rank] = key;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Per-tile stable LSD radix sort (one block of 512 threads per tile).
+//
+// Keys are 64-bit.  Pass A sorts by the depth key only: (zkey - zmin) sits in
+// the high word and only its significant bits are sorted.  If two entries
+// then share a depth key, pass B re-sorts by (zrel << bits_g | gid - gmin),
+// which orders ties by Gaussian id.  Lists of up to smem_n entries are
+// sorted in shared memory; longer ones in place in the tile's own range of
+// the bucket and its twin buffer.
+
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigned long long *out,
+                                           int n, int shift, int nbits, uint32_t *hist) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned dmask = (1u << nbits) - 1u;
+    const int per = (n + kSortWarps - 1) / kSortWarps;
+    const int lo = min(n, warp * per), hi = min(n, lo + per);
+    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) hist[i] = 0;
+    __syncthreads();
+    uint32_t *h = hist + warp * 256;
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < hi;
+        const unsigned d = valid ? (unsigned)(in[i] >> shift) & dmask : 0u;
+        const unsigned am = __ballot_sync(kFull, valid);
+        if (valid) {
+            const unsigned peers = __match_any_sync(am, d);
+            if (lane == __ffs(peers) - 1) h[d] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive scan in (digit, warp) order
+    __shared__ uint32_t dsum[256];
+    if (tid < 256) {
+        uint32_t run = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = hist[w * 256 + tid];
+            hist[w * 256 + tid] = run;
+            run += c;
+        }
+        dsum[tid] = run;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        uint32_t v[8], tot = 0;
+        for (int j = 0; j < 8; ++j) {
+            v[j] = dsum[tid * 8 + j];
+            tot += v[j];
+        }
+        uint32_t x = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (tid >= o) x += y;
+        }
+        uint32_t run = x - tot;
+        for (int j = 0; j < 8; ++j) {
+            dsum[tid * 8 + j] = run;
+            run += v[j];
+        }
+    }
+    __syncthreads();
+    if (tid < 256)
+        for (int w = 0; w < kSortWarps; ++w) hist[w * 256 + tid] += dsum[tid];
+    __syncthreads();
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < hi;
+        unsigned long long key = 0;
+        unsigned d = 0;
+        if (valid) {
+            key = in[i];
+            d = (unsigned)(key >> shift) & dmask;
+        }
+        const unsigned am = __ballot_sync(kFull, valid);
+        unsigned peers = 0;
+        if (valid) {
+            peers = __match_any_sync(am, d);
+            const uint32_t pos = h[d] + __popc(peers & ((1u << lane) - 1u));
+            out[pos] = key;
+        }
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned bits_of(uint32_t span) { return span ? 32 - __clz(span) : 0; }
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *tile_off,
+                                                             int n_tiles,
+                                                             unsigned long long *bucket,
+                                                             unsigned long long *alt,
+                                                             uint32_t *sorted, Status *st,
+                                                             int smem_n) {
+    extern __shared__ unsigned long long sm[];
+    __shared__ uint32_t red[4][kSortWarps];
+    if (st->flags) return;
+    const int t = blockIdx.x;
+    const uint32_t start = tile_off[t];
+    const int n = (int)(tile_off[t + 1] - start);
+    if (n == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (n == 1) {
+        if (tid == 0) sorted[start] = (uint32_t)bucket[start];
+        return;
+    }
+    const bool big = n > smem_n;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(sm + 2 * smem_n);
+    unsigned long long *A = big ? bucket + start : sm;
+    unsigned long long *B = big ? alt + start : sm + smem_n;
+    if (big && tid == 0) atomicAdd(&st->n_overflow_tiles, 1ull);
+    uint32_t zmin = 0xffffffffu, zmax = 0, gmin = 0xffffffffu, gmax = 0;
+    for (int i = tid; i < n; i += kSortThreads) {
+        const unsigned long long k = bucket[start + i];
+        if (!big) A[i] = k;
+        const uint32_t z = (uint32_t)(k >> 32), g = (uint32_t)k;
+        zmin = min(zmin, z);
+        zmax = max(zmax, z);
+        gmin = min(gmin, g);
+        gmax = max(gmax, g);
+    }
+    zmin = __reduce_min_sync(kFull, zmin);
+    zmax = __reduce_max_sync(kFull, zmax);
+    gmin = __reduce_min_sync(kFull, gmin);
+    gmax = __reduce_max_sync(kFull, gmax);
+    if (lane == 0) {
+        red[0][warp] = zmin;
+        red[1][warp] = zmax;
+        red[2][warp] = gmin;
+        red[3][warp] = gmax;
+    }
+    __syncthreads();
+    zmin = red[0][0];
+    zmax = red[1][0];
+    gmin = red[2][0];
+    gmax = red[3][0];
+    for (int w = 1; w < kSortWarps; ++w) {
+        zmin = min(zmin, red[0][w]);
+        zmax = max(zmax, red[1][w]);
+        gmin = min(gmin, red[2][w]);
+        gmax = max(gmax, red[3][w]);
+    }
+    const unsigned bz = bits_of(zmax - zmin), bg = bits_of(gmax - gmin);
+    // pass A: depth key relative to the tile minimum in the high word
+    for (int i = tid; i < n; i += kSortThreads) {
+        const unsigned long long k = A[i];
+        A[i] = ((unsigned long long)((uint32_t)(k >> 32) - zmin) << 32) | (k & 0xffffffffull);
+    }
+    __syncthreads();
+    unsigned long long *cur = A, *oth = B;
+    for (unsigned b = 0; b < bz; b += 8) {
+        radix_pass(cur, oth, n, 32 + b, min(8u, bz - b), hist);
+        unsigned long long *tmp = cur;
+        cur = oth;
+        oth = tmp;
+    }
+    int tie = 0;
+    for (int i = tid + 1; i < n; i += kSortThreads)
+        tie |= (uint32_t)(cur[i] >> 32) == (uint32_t)(cur[i - 1] >> 32);
+    tie = __syncthreads_or(tie);
+    if (!tie) {
+        for (int i = tid; i < n; i += kSortThreads) sorted[start + i] = (uint32_t)cur[i];
+        return;
+    }
+    // pass B: (zrel, gid - gmin) packed into bz + bg <= 64 bits
+    for (int i = tid; i < n; i += kSortThreads) {
+        const unsigned long long k = cur[i];
+        const unsigned long long zr = k >> 32, gr = (uint32_t)k - gmin;
+        cur[i] = (bg == 64 ? 0ull : (zr << bg)) | gr;
+    }
+    __syncthreads();
+    const unsigned tot = bz + bg;
+    for (unsigned b = 0; b < tot; b += 8) {
+        radix_pass(cur, oth, n, b, min(8u, tot - b), hist);
+        unsigned long long *tmp = cur;
+        cur = oth;
+        oth = tmp;
+    }
+    const unsigned long long gm = bg >= 64 ? ~0ull : ((1ull << bg) - 1ull);
+    for (int i = tid; i < n; i += kSortThreads) sorted[start + i] = gmin + (uint32_t)(cur[i] & gm);
+}
+
+}  // namespace vt

@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (the benchmark spec): FP32 forward within 1e-5 relative (floor 1 for
+colour/silhouette, 4 m for depth); gradients within 1e-4 relative (per-tensor
+L2 and per element with a floor of 1e-3 of the largest magnitude).  Integer
+and index results (section ids, depth keys, per-pixel counts, list order) are
+bit-exact.  Pixels where an FP32 decision sits within a relative margin of
+its threshold (the oracle reports the margins) are excluded and counted.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_02741_gb300 import api
+from paper_2506_02741_gb300 import synthetic as syn
+from tests import _gpu as G
+from tests import _helpers as h
+
+pytestmark = pytest.mark.gpu
+
+IDENT = syn.identity_pose()
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _render(osecs, target, K, W, H, prec="f32", R=None):
+    dsecs = [G.to_device(s, prec) for s in osecs]
+    R = R or api.Renderer()
+    out = R.render(dsecs, api.pose12(target), K, W, H, checked=True)
+    torch.cuda.synchronize()
+    return R, dsecs, out
+
+
+def _upstream(shape, seed, mask):
+    H, W = shape
+    rng = np.random.default_rng(seed)
+    gR = (rng.normal(0, 1, (3, H, W)) * mask).astype(np.float32)
+    gD = (rng.normal(0, 1, (H, W)) * mask).astype(np.float32)
+    gS = (rng.normal(0, 1, (H, W)) * mask).astype(np.float32)
+    return gR, gD, gS
+
+
+def _cases():
+    return {
+        "tiny": lambda: (lambda s, t, K: ([G.quantise(s)], t, K.astuple(), K.W, K.H))(*h.tiny_section()),
+        "qqvga_2views": lambda: (lambda K: (lambda s, t: ([G.quantise(s)], t, K.astuple(), K.W, K.H))(
+            *h.multiview_section(K, n_views=2)))(syn.scaled_intrinsics(160, 120)),
+        "ragged_3views": lambda: (lambda K: (lambda s, t: ([G.quantise(s)], t, K.astuple(), 203, 131))(
+            *h.multiview_section(K, n_views=3, seed=9)))(syn.scaled_intrinsics(200, 130)),
+    }
+
+
+# ---------------------------------------------------------------------------
+
+
+def test_section_init_bitexact(dev):
+    room, fr, _ = syn.tiny_workload()
+    K = syn.TINY
+    depth = fr.depth.copy()
+    depth[0, 3, 4] = 0.0
+    depth[0, 10, 11] = np.nan
+    depth[0, 20, 21] = -2.0
+    ref = oracle.section_init(depth, fr.rgb, K.astuple(), np.stack(fr.poses))
+    for prec in ("f32", "f16"):
+        s = api.Section.from_rgbd(torch.from_numpy(depth).to(dev), torch.from_numpy(fr.rgb).to(dev),
+                                  K.astuple(), np.stack(fr.poses), precision=prec)
+        assert s.n == ref.n
+        np.testing.assert_array_equal(s.src.cpu().numpy().view(np.uint32), ref.src)
+        dt = np.float16 if prec == "f16" else np.float32
+        np.testing.assert_array_equal(s.colour.cpu().numpy(), ref.colour.astype(np.float32).astype(dt))
+        np.testing.assert_array_equal(s.opacity.cpu().numpy(), np.full(ref.n, 0.9, np.float32).astype(dt))
+        r32 = depth.reshape(-1)[ref.src] / np.float32(K.fx)     # IEEE FP32 division
+        np.testing.assert_array_equal(s.radius.cpu().numpy(), r32.astype(dt))
+
+
+def test_backproject(dev):
+    room = syn.make_room()
+    K = syn.scaled_intrinsics(96, 72)
+    P = syn.trajectory(9)[8]
+    depth, _ = syn.raycast(room, K, P)
+    depth[5, 7] = 0.0
+    cen_ref, pix_ref = oracle.backproject(depth, K.astuple(), P)
+    cen, pix = api.backproject(torch.from_numpy(depth).to(dev), K.astuple(), api.pose12(P))
+    np.testing.assert_array_equal(pix.cpu().numpy().view(np.uint32), pix_ref)
+    np.testing.assert_allclose(cen.cpu().numpy(), cen_ref, rtol=0, atol=4 * 2.0 ** -24 * 8)
+
+
+@pytest.mark.parametrize("case", ["tiny", "qqvga_2views", "ragged_3views"])
+def test_depth_keys_and_tile_order(dev, case):
+    osecs, target, K, W, H = _cases()[case]()
+    R, dsecs, out = _render(osecs, target, K, W, H)
+    z_ref, ok = oracle.zkeys(osecs[0], target, K, W, H)
+    z = R.debug(0, osecs[0].n, np.float32)
+    # bit-exact depth keys for every Gaussian that survives culling
+    np.testing.assert_array_equal(z.view(np.uint32)[ok & (z != 0)], z_ref.view(np.uint32)[ok & (z != 0)])
+    assert np.all(z[~ok] == 0)
+    tiles_x = (W + 15) // 16
+    n_tiles = tiles_x * ((H + 15) // 16)
+    off = R.debug(1, n_tiles + 1)
+    lists = R.debug(2, int(off[-1]))
+    zk = z.view(np.uint32).astype(np.uint64)
+    for t in range(n_tiles):
+        l = lists[off[t]:off[t + 1]].astype(np.int64)
+        if l.size > 1:
+            key = (zk[l] << np.uint64(32)) | l.astype(np.uint64)
+            assert np.all(key[1:] > key[:-1]), t
+    # every pixel's added Gaussians appear in its tile list in the oracle's order
+    ref = oracle.render(osecs, target, K, W, H, list_cap=256)
+    clean = G.clean_mask(ref)
+    last = R.debug(3, W * H).reshape(H, W)
+    nadd = R.debug(4, W * H).reshape(H, W)
+    np.testing.assert_array_equal(nadd[clean], ref["n_added"][clean])
+    rng = np.random.default_rng(0)
+    ys, xs = np.nonzero(clean)
+    for k in rng.choice(ys.size, min(300, ys.size), replace=False):
+        y, x = ys[k], xs[k]
+        t = (y // 16) * tiles_x + x // 16
+        l = lists[off[t]:off[t] + last[y, x]].astype(np.int64)
+        want = ref["lists"][y, x, : ref["n_added"][y, x]]
+        where = {g: i for i, g in enumerate(l)}
+        idx = [where.get(int(g), -1) for g in want]
+        assert all(i >= 0 for i in idx) and idx == sorted(idx), (y, x)
+        if want.size:
+            assert l[-1] == want[-1]
+
+
+@pytest.mark.parametrize("case", ["tiny", "qqvga_2views", "ragged_3views"])
+def test_forward_parity(dev, case):
+    osecs, target, K, W, H = _cases()[case]()
+    R, dsecs, out = _render(osecs, target, K, W, H)
+    ref = oracle.render(osecs, target, K, W, H)
+    clean = G.clean_mask(ref)
+    assert (~clean).sum() <= max(3, 2e-3 * W * H), (~clean).sum()
+    G.assert_forward_close(out, ref, clean)
+    T = R.debug(5, W * H, np.float32).reshape(H, W)
+    np.testing.assert_allclose(T[clean], ref["T_final"][clean], rtol=2e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("case", ["tiny", "qqvga_2views", "ragged_3views"])
+def test_backward_parity(dev, case):
+    osecs, target, K, W, H = _cases()[case]()
+    R, dsecs, out = _render(osecs, target, K, W, H)
+    ref = oracle.render(osecs, target, K, W, H)
+    clean = G.clean_mask(ref, tau_clamp=1e-4)
+    gR, gD, gS = _upstream((H, W), 31, clean)
+    want = oracle.backward(osecs, target, K, W, H, g_rgb=gR, g_depth=gD, g_sil=gS)
+    grads = [(torch.zeros(s.n, 3, device=dev), torch.zeros(s.n, device=dev),
+              torch.zeros(s.n, device=dev)) for s in osecs]
+    t = lambda a: torch.from_numpy(a).to(dev)
+    dtw, dmat = R.backward(t(gR), t(gD), t(gS), attr_grads=grads, pose_grad=True)
+    torch.cuda.synchronize()
+    G.assert_grad_close(grads[0][0].cpu().numpy(), want["colour"][0], name="colour")
+    G.assert_grad_close(grads[0][1].cpu().numpy(), want["opacity"][0], name="opacity")
+    G.assert_grad_close(grads[0][2].cpu().numpy(), want["radius"][0], name="radius")
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist")
+    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat")
+
+
+def test_pose_only_and_attr_only_modes_agree(dev):
+    osecs, target, K, W, H = _cases()["tiny"]()
+    R, dsecs, out = _render(osecs, target, K, W, H)
+    ref = oracle.render(osecs, target, K, W, H)
+    gR, gD, gS = (torch.from_numpy(a).to(dev) for a in _upstream((H, W), 5, G.clean_mask(ref)))
+    n = osecs[0].n
+    g1 = [(torch.zeros(n, 3, device=dev), torch.zeros(n, device=dev), torch.zeros(n, device=dev))]
+    g2 = [(torch.zeros(n, 3, device=dev), torch.zeros(n, device=dev), torch.zeros(n, device=dev))]
+    R.backward(gR, gD, gS, attr_grads=g1)
+    tw1, m1 = R.backward(gR, gD, gS, pose_grad=True)
+    tw2, m2 = R.backward(gR, gD, gS, attr_grads=g2, pose_grad=True)
+    torch.cuda.synchronize()
+    assert torch.equal(tw1, tw2) and torch.equal(m1, m2)     # fixed-order FP64 reduction
+    for a, b in zip(g1[0], g2[0]):
+        torch.testing.assert_close(a, b, rtol=1e-6, atol=1e-9)
+
+
+def test_closed_forms_gpu(dev):
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+    W, H, f = 16, 12, 20.0
+    K = (f, f, 7.5, 5.5)
+    col = np.array([[0.2, 0.5, 0.9]])
+    sec = G.quantise(h.hand_section([(IDENT, {(8, 6): 2.0})], W, H, K, colour=col))
+    R, _, (rgb, depth, sil) = _render([sec], IDENT, K, W, H)
+    for c in gold["single_gaussian"]["cases"]:
+        du, dv = c["offset"]
+        a = c["alpha"]
+        assert sil[6 + dv, 8 + du].item() == pytest.approx(a, rel=2e-6, abs=1e-9)
+        np.testing.assert_allclose(rgb[:, 6 + dv, 8 + du].cpu().numpy(), sec.colour[0] * a, rtol=3e-6,
+                                   atol=1e-9)
+    g = gold["termination"]
+    rng = np.random.default_rng(11)
+    depths = 1.0 + 0.1 * rng.permutation(g["n"])
+    sec = G.quantise(h.hand_section([(IDENT, {(8, 6): float(d)}) for d in depths], W, H, K,
+                                    colour=rng.uniform(0, 1, (g["n"], 3)),
+                                    opacity=np.full(g["n"], g["opacity"])))
+    R, _, (rgb, depth, sil) = _render([sec], IDENT, K, W, H)
+    assert R.debug(4, W * H).reshape(H, W)[6, 8] == g["n_added"]
+    assert sil[6, 8].item() == g["silhouette"]
+    assert R.debug(5, W * H, np.float32).reshape(H, W)[6, 8] == np.float32(g["T_final"])
+
+
+def test_multi_section_with_frozen(dev):
+    K = syn.scaled_intrinsics(128, 96)
+    full, target = h.multiview_section(K, n_views=3, seed=12)
+    plane = full.W * full.H
+    view = full.src // plane
+    parts = []
+    for k in range(3):
+        m = view == k
+        parts.append(G.quantise(oracle.Section(full.W, full.H, full.K, full.poses[k:k + 1],
+                                               full.depth[k:k + 1],
+                                               (full.src[m] - k * plane).astype(np.uint32),
+                                               full.colour[m], full.opacity[m], full.radius[m])))
+    Kt = K.astuple()
+    R, dsecs, out = _render(parts, target, Kt, K.W, K.H)
+    ref = oracle.render(parts, target, Kt, K.W, K.H)
+    clean = G.clean_mask(ref, tau_clamp=1e-4)
+    G.assert_forward_close(out, ref, clean)
+    gR, gD, gS = _upstream((K.H, K.W), 8, clean)
+    want = oracle.backward(parts, target, Kt, K.W, K.H, g_rgb=gR, g_depth=gD, g_sil=gS)
+    grads = [None, (torch.zeros(parts[1].n, 3, device=dev), torch.zeros(parts[1].n, device=dev),
+                    torch.zeros(parts[1].n, device=dev)), None]
+    t = lambda a: torch.from_numpy(a).to(dev)
+    R.backward(t(gR), t(gD), t(gS), attr_grads=grads)
+    torch.cuda.synchronize()
+    G.assert_grad_close(grads[1][0].cpu().numpy(), want["colour"][1], name="colour")
+    G.assert_grad_close(grads[1][1].cpu().numpy(), want["opacity"][1], name="opacity")
+    G.assert_grad_close(grads[1][2].cpu().numpy(), want["radius"][1], name="radius")
+
+
+def test_fp16_attributes(dev):
+    K = syn.scaled_intrinsics(160, 120)
+    sec, target = h.multiview_section(K, n_views=2, seed=3)
+    q = G.quantise(sec, "f16")
+    Kt = K.astuple()
+    R, dsecs, out = _render([q], target, Kt, K.W, K.H, prec="f16")
+    ref = oracle.render([q], target, Kt, K.W, K.H)
+    G.assert_forward_close(out, ref, G.clean_mask(ref))
+    # against the FP64 render of the unrounded attributes: colour max-abs <= 2e-3
+    ref32 = oracle.render([G.quantise(sec)], target, Kt, K.W, K.H)
+    assert np.max(np.abs(out[0].cpu().numpy() - ref32["rgb"])) <= 2e-3
+
+
+def test_empty_and_degenerate(dev):
+    K = (20.0, 20.0, 7.5, 5.5)
+    # empty section: background everywhere
+    sec = G.quantise(h.hand_section([(IDENT, {})], 16, 12, K))
+    R, _, (rgb, depth, sil) = _render([sec], IDENT, K, 16, 12)
+    assert sec.n == 0 and float(rgb.abs().max()) == 0.0 and float(sil.abs().max()) == 0.0
+    # everything behind the camera or closer than z_near: culled
+    sec = G.quantise(h.hand_section([(IDENT, {(3, 3): 0.05, (8, 6): 1.0})], 16, 12, K))
+    back = np.hstack([np.diag([1.0, 1.0, 1.0]), np.array([[0.0], [0.0], [2.0]])])
+    R, _, (rgb, depth, sil) = _render([sec], back, K, 16, 12)
+    assert float(sil.abs().max()) == 0.0
+    # 1x1 and 17x1 images, one huge Gaussian covering everything
+    for W, H in ((1, 1), (17, 1), (33, 47)):
+        Kc = (20.0, 20.0, (W - 1) / 2, (H - 1) / 2)
+        s = G.quantise(h.hand_section([(IDENT, {(0, 0): 1.0})], 1, 1, (20.0, 20.0, 0.0, 0.0),
+                                      radius=[5.0], opacity=[0.5]))
+        R, _, out = _render([s], IDENT, Kc, W, H)
+        ref = oracle.render([s], IDENT, Kc, W, H)
+        G.assert_forward_close(out, ref, G.clean_mask(ref))
+        assert float(out[2].min()) > 0.4
+
+
+def test_capacity_overflow_reported_and_recovered(dev):
+    osecs, target, K, W, H = _cases()["qqvga_2views"]()
+    dsecs = [G.to_device(s) for s in osecs]
+    R = api.Renderer()
+    R.reserve(osecs[0].n, W, H, n_instances=1000)
+    R.render(dsecs, api.pose12(target), K, W, H)
+    from paper_2506_02741_gb300 import _lib as L
+    with pytest.raises(L.VTError) as ei:
+        R.status()
+    assert ei.value.status == L.VT_ERR_CAPACITY
+    out = R.render(dsecs, api.pose12(target), K, W, H, checked=True)
+    ref = oracle.render(osecs, target, K, W, H)
+    G.assert_forward_close(out, ref, G.clean_mask(ref))
+
+
+def test_determinism(dev):
+    osecs, target, K, W, H = _cases()["qqvga_2views"]()
+    R, dsecs, a = _render(osecs, target, K, W, H)
+    a = [x.clone() for x in a]
+    b = R.render(dsecs, api.pose12(target), K, W, H)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    g = torch.ones(3, H, W, device=dev)
+    t1, m1 = R.backward(g, None, None, pose_grad=True)
+    t2, m2 = R.backward(g, None, None, pose_grad=True)
+    assert torch.equal(t1, t2) and torch.equal(m1, m2)
+
+
+def test_bad_arguments_rejected(dev):
+    from paper_2506_02741_gb300 import _lib as L
+    osecs, target, K, W, H = _cases()["tiny"]()
+    d = G.to_device(osecs[0])
+    R = api.Renderer()
+    with pytest.raises(L.VTError) as ei:
+        R.render([d], api.pose12(target), (0.0, 1.0, 0.0, 0.0), W, H)
+    assert ei.value.status == L.VT_ERR_INVALID_ARG
+    with pytest.raises(L.VTError) as ei:
+        R.render([d], api.pose12(target), K, 0, H)
+    assert ei.value.status == L.VT_ERR_INVALID_ARG
+    R2 = api.Renderer()
+    with pytest.raises(L.VTError) as ei:
+        R2.backward(torch.ones(3, H, W, device=dev), pose_grad=True)
+    assert ei.value.status == L.VT_ERR_STATE
