@@ -273,7 +273,7 @@ vt_status vt_ctx_reserve(vt_ctx *c, int64_t n_gaussians, int32_t W, int32_t H,
     vt_status st = check_image(W, H, "vt_ctx_reserve");
     if (st) return st;
     if (n_instances <= 0) n_instances = default_instances(n_gaussians);
-    c->reserved_i = std::max(c->reserved_i, n_instances);
+    c->reserved_i = std::max(c->reserved_i, n_instances);  // later renders keep this capacity
     const int64_t tiles = (int64_t)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
     c->stream = stream;
     return ensure(c, std::max<int64_t>(n_gaussians, 1), n_instances, (int64_t)W * H, tiles,
@@ -396,9 +396,9 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     cam.tiles_x = (W + kTile - 1) / kTile;
     cam.tiles_y = (H + kTile - 1) / kTile;
     const int n_tiles = cam.tiles_x * cam.tiles_y;
-    const int64_t want_i = std::max(c->reserved_i, default_instances(total));
+    const int64_t want_i = c->reserved_i > 0 ? c->reserved_i : default_instances(total);
     c->stream = stream;
-    if ((st = ensure(c, std::max<int64_t>(total, 1), std::max(want_i, c->cap_i), (int64_t)W * H,
+    if ((st = ensure(c, std::max<int64_t>(total, 1), want_i, (int64_t)W * H,
                      n_tiles, std::max<int64_t>(views, 1), std::max<int64_t>(tabrows, 1), stream)))
         return st;
     if (!sort_attr_set) {

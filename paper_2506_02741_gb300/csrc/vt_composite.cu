@@ -112,6 +112,14 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
 // and the sums A, B of w c and w z behind the current one:
 //   dL/dc_i     = gC w_i
 //   dL/dalpha_i = T_i (gC.c_i + gD z_i) - (gC.A + gD B - gS T_final) / (1 - alpha_i)
+// Evaluated as written in FP32, T_i z_i and B / (1 - alpha_i) cancel almost
+// completely when the Gaussians lie on one surface (depths agree to ~1e-3),
+// so the sums are kept relative to the pixel's last added Gaussian (c_r, z_r):
+// with S = sum_{j>i} w_j, A' = sum w_j (c_j - c_r), B' = sum w_j (z_j - z_r)
+// and T_{i+1} = S + T_final the same derivative is
+//   [gC.(c_i T_final + (c_i - c_r) S - A') + gD (z_i T_final + (z_i - z_r) S - B')
+//    + gS T_final] / (1 - alpha_i),
+// whose terms are all of the size of the result.
 //   below the clamp: dL/do = dL/dalpha exp(-q/2),  dL/dq = -ahat/2 dL/dalpha
 //   dL/dr = dL/dq (-2q/r)
 //   camera-space centre: with e = (p_x z - x, p_y z - y) = z (du/fx, dv/fy),
@@ -184,7 +192,9 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     __syncthreads();
     const uint32_t tile_last = s_last;
 
-    float T = Tfin, A0 = 0.f, A1 = 0.f, A2 = 0.f, Bd = 0.f;
+    float T = Tfin, A0 = 0.f, A1 = 0.f, A2 = 0.f, Bd = 0.f, Sb = 0.f;
+    float cr0 = 0.f, cr1 = 0.f, cr2 = 0.f, zr = 0.f;
+    bool have_ref = false;
     PoseAcc acc;
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc.a[i] = 0.f;
@@ -234,9 +244,21 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                                     const float w = al * Ti;
                                     const float4 a = s_a[j];
                                     const float z = g1.z, r = a.w;
-                                    const float dal =
-                                        Ti * (gC0 * a.x + gC1 * a.y + gC2 * a.z + gD * z) -
-                                        (gC0 * A0 + gC1 * A1 + gC2 * A2 + gD * Bd - gS * Tfin) / om;
+                                    if (!have_ref) {
+                                        have_ref = true;
+                                        cr0 = a.x;
+                                        cr1 = a.y;
+                                        cr2 = a.z;
+                                        zr = z;
+                                    }
+                                    const float e0 = a.x - cr0, e1 = a.y - cr1, e2 = a.z - cr2,
+                                                ez = z - zr;
+                                    const float num =
+                                        gC0 * (a.x * Tfin + e0 * Sb - A0) +
+                                        gC1 * (a.y * Tfin + e1 * Sb - A1) +
+                                        gC2 * (a.z * Tfin + e2 * Sb - A2) +
+                                        gD * (z * Tfin + ez * Sb - Bd) + gS * Tfin;
+                                    const float dal = num / om;
                                     dc0 = gC0 * w;
                                     dc1 = gC1 * w;
                                     dc2 = gC2 * w;
@@ -265,10 +287,11 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                                         acc.a[10] += gy;
                                         acc.a[11] += gz;
                                     }
-                                    A0 = __fmaf_rn(w, a.x, A0);
-                                    A1 = __fmaf_rn(w, a.y, A1);
-                                    A2 = __fmaf_rn(w, a.z, A2);
-                                    Bd = __fmaf_rn(w, z, Bd);
+                                    A0 = __fmaf_rn(w, e0, A0);
+                                    A1 = __fmaf_rn(w, e1, A1);
+                                    A2 = __fmaf_rn(w, e2, A2);
+                                    Bd = __fmaf_rn(w, ez, Bd);
+                                    Sb += w;
                                     T = Ti;
                                 }
                             }

@@ -30,10 +30,12 @@ def to_device(sec: "oracle.Section", prec: str = "f32", device="cuda") -> api.Se
                        t(sec.radius).contiguous())
 
 
-def clean_mask(ref: dict, tau_incl=2e-5, tau_T=2e-4, tau_clamp=None) -> np.ndarray:
+def clean_mask(ref: dict, tau_incl=1e-5, tau_T=2e-4, tau_clamp=None) -> np.ndarray:
     """Pixels whose every inclusion / termination decision is farther than the
     given relative margins from its threshold: there FP32 and FP64 must take
-    the same decisions."""
+    the same decisions.  The FP32 kernels compute q to ~6e-7 and ahat to
+    ~3e-6 relative (exp of an argument up to 4.5), and the transmittance to
+    ~1e-4 after many steps near the 0.99 clamp, hence the default margins."""
     m = (ref["margin"] > tau_incl) & (ref["margin_T"] > tau_T)
     if tau_clamp is not None:
         m &= ref["margin_clamp"] > tau_clamp
