@@ -1,0 +1,410 @@
+"""Benchmark: camera tracking with view-tied Gaussian splatting on GB300.
+
+One step = one tracking iteration of the 640x480 workload (a section of 8
+keyframes = 2,457,600 view-tied Gaussians, FP32): render colour/depth/
+silhouette, Eq. 1 L1 loss and its image gradient, pose backward, Adam step
+on the pose.  Target frames change every 40 iterations (50 frames x 40
+iterations = 2000 iterations for the whole workload).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vtsplat|reference]
+
+Prints one JSON line (rank 0).  ``value`` is fwd+bwd splat Mpix/s over all
+ranks (W*H*iterations / max-over-ranks time); ranks track independent
+frames (weak scaling, no collective on the data path).  ``--impl reference``
+times the FP64 CPU oracle (binned form, all host cores) on a bounded crop of
+the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd splat Mpix/s & tracking iters/s vs plain FP32; serve p50/p99 ms"
+WORKLOAD = "tracking_640x480_8kf_fp32"
+ITERS_PER_FRAME = 40
+FP32_FLOPS_PER_PAIR_FWD = 21      # per included pixel-Gaussian pair (20 FP32 ops + 1 exp)
+FP32_FLOPS_PER_PAIR_BWD = 63      # about 3x the forward
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="vtsplat", choices=["vtsplat", "reference"])
+    p.add_argument("--frames", type=int, default=4, help="distinct target frames to cycle")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+
+
+def make_workload(rank: int, n_frames: int):
+    from paper_2506_02741_gb300 import synthetic as syn
+    K = syn.VGA
+    room = syn.make_room(syn.SCENE_SEED)
+    n_key, every = 8, 5
+    path = syn.trajectory(n_key * every + 4 + n_frames * 3 + 3 * rank)
+    keys = [path[i * every] for i in range(n_key)]
+    section = syn.render_frames(room, K, keys)
+    tframes = [(n_key - 1) * every + 2 + 3 * rank + 3 * j for j in range(n_frames)]
+    targets = syn.render_frames(room, K, [path[i] for i in tframes])
+    rng = np.random.default_rng(syn.POSE_NOISE_SEED + rank)
+    starts = [syn.perturb_pose(path[i], rng) for i in tframes]
+    return K, keys, section, targets, starts
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SRC = {
+    "k_composite_fwd": ["paper_2506_02741_gb300/csrc/vt_composite.cu",
+                        "paper_2506_02741_gb300/csrc/vt_common.cuh"],
+    "k_composite_bwd": ["paper_2506_02741_gb300/csrc/vt_composite.cu",
+                        "paper_2506_02741_gb300/csrc/vt_common.cuh"],
+    "k_sort_tiles": ["paper_2506_02741_gb300/csrc/vt_raster.cu",
+                     "paper_2506_02741_gb300/csrc/vt_common.cuh"],
+    "k_preprocess": ["paper_2506_02741_gb300/csrc/vt_raster.cu",
+                     "paper_2506_02741_gb300/csrc/vt_common.cuh"],
+    "k_emit": ["paper_2506_02741_gb300/csrc/vt_raster.cu",
+               "paper_2506_02741_gb300/csrc/vt_common.cuh"],
+}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    sources are unchanged since it was taken."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t[WORKLOAD][kernel]
+        if e.get("source_sha") == source_hash(KERNEL_SRC[kernel]):
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+
+
+def oracle_crop_sample(seconds: float, W=640, H=480, max_steps: int = 1 << 30):
+    """Time the FP64 oracle (binned, all host threads) on a crop of the
+    tracking workload: forward + backward per step.  Returns (Mpix/s, info)."""
+    import oracle
+    from paper_2506_02741_gb300 import synthetic as syn
+    K, keys, section, targets, starts = make_workload(0, 1)
+    osec = oracle.section_init(section.depth, section.rgb, K.astuple(), np.stack(keys))
+    osec.colour = osec.colour.astype(np.float32).astype(np.float64)
+    osec.radius = osec.radius.astype(np.float32).astype(np.float64)
+    cw, ch = 160, 120                      # crop: same camera, shifted principal point
+    x0, y0 = (W - cw) // 2, (H - ch) // 2
+    Kc = (K.fx, K.fy, K.cx - x0, K.cy - y0)
+    obs_rgb = targets.rgb[0][:, y0:y0 + ch, x0:x0 + cw]
+    obs_d = targets.depth[0][y0:y0 + ch, x0:x0 + cw]
+    pose = starts[0]
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        out = oracle.render(osec, pose, Kc, cw, ch)
+        mask = ((obs_d > 0) & (out["sil"] > 0.99)).astype(np.float64)
+        P = cw * ch
+        g_rgb = 0.5 * np.sign(out["rgb"] - obs_rgb) * mask / (3 * P)
+        g_d = 0.025 * np.sign(out["depth"] - obs_d) * mask / P
+        oracle.backward(osec, pose, Kc, cw, ch, g_rgb=g_rgb, g_depth=g_d)
+        n += 1
+        if time.perf_counter() - t0 >= seconds or n >= max_steps:
+            break
+    dt = time.perf_counter() - t0
+    info = {"kind": "oracle", "cores": oracle.get_threads(),
+            "sample": f"{n} fwd+bwd iterations of a {cw}x{ch} crop of the 640x480 8-keyframe "
+                      f"section ({osec.n} Gaussians), FP64, binned"}
+    return (cw * ch * n) / dt / 1e6, info
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores; one
+    step = one fwd+bwd iteration of a 160x120 crop (at most 90 s of steps)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    val, info = oracle_crop_sample(90.0, max_steps=max(1, args.steps))
+    wall = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 160 * 120 / (val * 1e6) * 1e3 if val else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "crop": "160x120", "global_batch": 1,
+                       "parallelism": "host cores"},
+            "cpu_baseline": dict(info, value=val, unit="Mpix/s"),
+            "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_02741_gb300 import api
+    from paper_2506_02741_gb300.tracking import PoseTracker
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    K, keys, section, targets, starts = make_workload(rank, args.frames)
+    Kt = K.astuple()
+    sec = api.Section.from_rgbd(torch.from_numpy(section.depth).to(dev),
+                                torch.from_numpy(section.rgb).to(dev), Kt, np.stack(keys))
+    tgt_rgb = [torch.from_numpy(targets.rgb[i]).to(dev) for i in range(args.frames)]
+    tgt_d = [torch.from_numpy(targets.depth[i]).to(dev) for i in range(args.frames)]
+    R = api.Renderer()
+    tr = PoseTracker(R, [sec], Kt, K.W, K.H, starts[0], device=dev)
+    tr.set_target(tgt_rgb[0], tgt_d[0])
+    R.render([sec], tr.pose, Kt, K.W, K.H, checked=True)     # size the workspace
+    n_inst = R.status()
+    R.reserve(sec.n, K.W, K.H, int(n_inst * 1.5) + 65536)
+
+    def frame_for(i):
+        f = (i // ITERS_PER_FRAME) % args.frames
+        if i % ITERS_PER_FRAME == 0:
+            tr.set_target(tgt_rgb[f], tgt_d[f])
+            tr.pose.copy_(api.pose12(starts[f], dev))
+            tr.reset_optimiser()
+
+    for i in range(args.warmup):
+        frame_for(i)
+        tr.step()
+    torch.cuda.synchronize()
+    R.status()
+    # included pairs of a representative render (for the ALU roofline)
+    tr.pose.copy_(api.pose12(starts[0], dev))
+    R.render([sec], tr.pose, Kt, K.W, K.H)
+    pairs_fwd = int(R.debug(4, K.W * K.H).astype(np.int64).sum())
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    R.set_timing(True)
+    R.timing(reset=True)
+    launches0 = R.launches
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall0 = time.perf_counter()
+        ev0.record()
+        for i in range(args.steps):
+            frame_for(i)
+            tr.step()
+        ev1.record()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    launches = R.launches - launches0
+    ms = ev0.elapsed_time(ev1)
+    per_kernel = R.timing(reset=True)
+    R.set_timing(False)
+    R.status()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    P = K.W * K.H
+    value = world * P * args.steps / (ms / 1e3) / 1e6
+    iters_s = world * args.steps / (ms / 1e3)
+
+    # end to end through the public API: host frame in, pose + loss out, per step
+    n_e2e = min(args.steps, 200)
+    pin_rgb = [targets.rgb[i % args.frames] for i in range(args.frames)]
+    h_rgb = [torch.from_numpy(x).pin_memory() for x in pin_rgb]
+    h_d = [torch.from_numpy(targets.depth[i]).pin_memory() for i in range(args.frames)]
+    d_rgb = torch.empty(3, K.H, K.W, device=dev)
+    d_d = torch.empty(K.H, K.W, device=dev)
+    out_host = torch.empty(13, dtype=torch.float64).pin_memory()
+    tr.set_target(d_rgb, d_d)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        f = (i // ITERS_PER_FRAME) % args.frames
+        d_rgb.copy_(h_rgb[f], non_blocking=True)
+        d_d.copy_(h_d[f], non_blocking=True)
+        loss = tr.step()
+        res = torch.cat([tr.pose, loss.reshape(1).double()])
+        out_host.copy_(res, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * P * n_e2e / e2e_s / 1e6, "unit": "Mpix/s",
+           "h2d_bytes_per_step": int(h_rgb[0].numel() * 4 + h_d[0].numel() * 4),
+           "d2h_bytes_per_step": int(out_host.numel() * 8), "steps": n_e2e}
+
+    # roofline of the dominant kernel (CUDA-event durations inside the timed region)
+    pk = {k: v for k, v in per_kernel.items() if v[0] > 0}
+    dom = max(pk, key=lambda k: pk[k][1])
+    n_l, tot_ms = pk[dom]
+    avg_s = tot_ms / n_l / 1e3
+    mp = peaks()
+    clocks = clk.summary()
+    if dom in ("k_composite_fwd", "k_composite_bwd"):
+        flops = pairs_fwd * (FP32_FLOPS_PER_PAIR_FWD if dom == "k_composite_fwd"
+                             else FP32_FLOPS_PER_PAIR_BWD)
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "algorithmic": f"{pairs_fwd} included pairs x "
+                               f"{flops // max(pairs_fwd, 1)} FP32 flops"}
+    else:
+        per_g = {"k_preprocess": 28, "k_emit": 16, "k_sort_tiles": 0}.get(dom, 28)
+        inst = n_inst
+        byts = sec.n * per_g if dom != "k_sort_tiles" else inst * (8 + 4)
+        peak = float(mp.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "achieved": byts / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if mp else "fallback 6.8 TB/s",
+                "algorithmic": f"{byts} bytes per launch"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["avg_launch_ms"] = avg_s * 1e3
+    roof["traffic"] = traffic_for(dom)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            v, info = oracle_crop_sample(args.cpu_seconds)
+            cpu = dict(info, value=v, unit="Mpix/s")
+        except Exception as e:  # the baseline is context, never the product path
+            cpu = {"error": repr(e)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "W": K.W, "H": K.H, "gaussians_per_gpu": sec.n,
+                       "keyframes": 8, "iters_per_frame": ITERS_PER_FRAME,
+                       "global_batch": world, "parallelism": f"replicas x{world}",
+                       "l2": "no flush: per-step working set (attributes 69 MB + workspace "
+                             "~0.3 GB) exceeds the 129 MB L2",
+                       "instances": n_inst},
+            "tracking_iters_per_s": iters_s,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items()},
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -67,6 +67,7 @@ class _Upstream(C.Structure):
 
 class _Grads(C.Structure):
     _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
+                ("a_colour", C.c_void_p), ("a_opacity", C.c_void_p), ("a_radius", C.c_void_p),
                 ("twist", C.c_double * 6), ("mat", C.c_double * 12)]
 
 
@@ -205,24 +206,27 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     """Gradients of <g_rgb, rgb> + <g_depth, depth> + <g_sil, sil>.
 
     Returns dict(colour=[(n,3)], opacity=[(n,)], radius=[(n,)] per section,
-    twist (6,) and mat (12,) float64)."""
+    twist (6,) and mat (12,) float64, and abs_colour/abs_opacity/abs_radius:
+    per element the sum of the magnitudes of its per-pixel terms)."""
     secs, arr, keep = _sections(secs)
     ups = [None if g is None else np.ascontiguousarray(g, np.float64) for g in (g_rgb, g_depth, g_sil)]
     up = _Upstream(*[_ptr(u) for u in ups])
     dcol = [np.zeros((s.n, 3)) for s in secs]
     dop = [np.zeros(s.n) for s in secs]
     drad = [np.zeros(s.n) for s in secs]
-    pc = (C.c_void_p * len(secs))(*[_ptr(a) for a in dcol])
-    po = (C.c_void_p * len(secs))(*[_ptr(a) for a in dop])
-    pr = (C.c_void_p * len(secs))(*[_ptr(a) for a in drad])
-    g = _Grads(C.cast(pc, C.c_void_p), C.cast(po, C.c_void_p), C.cast(pr, C.c_void_p))
+    acol = [np.zeros((s.n, 3)) for s in secs]
+    aop = [np.zeros(s.n) for s in secs]
+    arad = [np.zeros(s.n) for s in secs]
+    arrs = [(C.c_void_p * len(secs))(*[_ptr(a) for a in lst])
+            for lst in (dcol, dop, drad, acol, aop, arad)]
+    g = _Grads(*[C.cast(a, C.c_void_p) for a in arrs])
     cam = _camera(pose, K, W, H)
     rc = lib().orc_backward(C.byref(arr), len(secs), C.byref(cam), int(bool(binned)), C.byref(up),
                             C.byref(g))
     if rc != 0:
         raise RuntimeError("oracle backward failed")
     return dict(colour=dcol, opacity=dop, radius=drad, twist=np.array(g.twist[:]),
-                mat=np.array(g.mat[:]))
+                mat=np.array(g.mat[:]), abs_colour=acol, abs_opacity=aop, abs_radius=arad)
 
 
 def zkeys(sec: Section, pose, K, W, H):

@@ -468,6 +468,14 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
                     }
                     if (dop_ && dop_[G->sec]) atomic_add(&dop_[G->sec][G->local], dop);
                     if (drad && drad[G->sec]) atomic_add(&drad[G->sec][G->local], dr);
+                    /* magnitude of every per-pixel term: the condition of each sum */
+                    if (gr->a_colour && gr->a_colour[G->sec])
+                        for (int c = 0; c < 3; ++c)
+                            atomic_add(&gr->a_colour[G->sec][3 * G->local + c], fabs(gC[c] * w));
+                    if (gr->a_opacity && gr->a_opacity[G->sec])
+                        atomic_add(&gr->a_opacity[G->sec][G->local], fabs(dop));
+                    if (gr->a_radius && gr->a_radius[G->sec])
+                        atomic_add(&gr->a_radius[G->sec][G->local], fabs(dr));
                     double gv[3] = {gx, gy, gz};
                     const double *x = G->x;
                     ltw[0] -= gx;

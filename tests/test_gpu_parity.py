@@ -159,9 +159,12 @@ def test_backward_parity(dev, case):
     t = lambda a: torch.from_numpy(a).to(dev)
     dtw, dmat = R.backward(t(gR), t(gD), t(gS), attr_grads=grads, pose_grad=True)
     torch.cuda.synchronize()
-    G.assert_grad_close(grads[0][0].cpu().numpy(), want["colour"][0], name="colour")
-    G.assert_grad_close(grads[0][1].cpu().numpy(), want["opacity"][0], name="opacity")
-    G.assert_grad_close(grads[0][2].cpu().numpy(), want["radius"][0], name="radius")
+    G.assert_grad_close(grads[0][0].cpu().numpy(), want["colour"][0], name="colour",
+                        abs_ref=want["abs_colour"][0])
+    G.assert_grad_close(grads[0][1].cpu().numpy(), want["opacity"][0], name="opacity",
+                        abs_ref=want["abs_opacity"][0])
+    G.assert_grad_close(grads[0][2].cpu().numpy(), want["radius"][0], name="radius",
+                        abs_ref=want["abs_radius"][0])
     G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist")
     G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat")
 
@@ -233,9 +236,12 @@ def test_multi_section_with_frozen(dev):
     t = lambda a: torch.from_numpy(a).to(dev)
     R.backward(t(gR), t(gD), t(gS), attr_grads=grads)
     torch.cuda.synchronize()
-    G.assert_grad_close(grads[1][0].cpu().numpy(), want["colour"][1], name="colour")
-    G.assert_grad_close(grads[1][1].cpu().numpy(), want["opacity"][1], name="opacity")
-    G.assert_grad_close(grads[1][2].cpu().numpy(), want["radius"][1], name="radius")
+    G.assert_grad_close(grads[1][0].cpu().numpy(), want["colour"][1], name="colour",
+                        abs_ref=want["abs_colour"][1])
+    G.assert_grad_close(grads[1][1].cpu().numpy(), want["opacity"][1], name="opacity",
+                        abs_ref=want["abs_opacity"][1])
+    G.assert_grad_close(grads[1][2].cpu().numpy(), want["radius"][1], name="radius",
+                        abs_ref=want["abs_radius"][1])
 
 
 def test_fp16_attributes(dev):

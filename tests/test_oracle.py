@@ -360,3 +360,18 @@ def test_zkey_is_fp32_camera_depth():
     z2, ok2 = oracle.zkeys(sec, P, K.astuple(), K.W, K.H)
     assert 0 < ok2.sum() < ok2.size
     assert np.all(z2[ok2] >= np.float32(0.1)) and np.all(z2[~ok2] < np.float32(0.1))
+
+
+def test_gradient_term_magnitudes_bound_the_gradients():
+    """abs_* (sum over pixels of |term|) bounds |gradient| element-wise and
+    equals it when every term has one sign (all upstream gradients >= 0 and
+    a colour gradient is w * gC)."""
+    sec, target, K = h.tiny_section()
+    args = (K.astuple(), K.W, K.H)
+    rng = np.random.default_rng(2)
+    g = oracle.backward(sec, target, *args, g_rgb=rng.normal(0, 1, (3, K.H, K.W)),
+                        g_depth=rng.normal(0, 1, (K.H, K.W)), g_sil=rng.normal(0, 1, (K.H, K.W)))
+    for k in ("colour", "opacity", "radius"):
+        assert np.all(g["abs_" + k][0] >= np.abs(g[k][0]) * (1 - 1e-12))
+    g = oracle.backward(sec, target, *args, g_rgb=np.abs(rng.normal(0, 1, (3, K.H, K.W))))
+    np.testing.assert_allclose(g["abs_colour"][0], g["colour"][0], rtol=1e-12)
