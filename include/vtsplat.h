@@ -182,6 +182,24 @@ int32_t vt_ctx_timing(vt_ctx *ctx, vt_stream stream, const char **names, int64_t
  * created (host-side counter). */
 int64_t vt_ctx_launch_count(const vt_ctx *ctx);
 
+/* Per-pixel lists.  By default every render keeps, for each pixel, the ids
+ * of the first `cap` Gaussians it added (4 * cap bytes per pixel, cap = 256),
+ * so that the backward walks each pixel's own Gaussians; pixels that add
+ * more, and renders where the lists do not fit the workspace budget, fall
+ * back to replaying the tile lists (same results).  cap = 0 never keeps
+ * lists.  Takes effect at the next vt_render. */
+vt_status vt_ctx_set_list_capacity(vt_ctx *ctx, int32_t cap);
+
+/* Upper bound in bytes on the context's workspace; 0 = unbounded.  When the
+ * per-pixel lists of a render would exceed it, that render keeps none. */
+vt_status vt_ctx_set_workspace_budget(vt_ctx *ctx, size_t bytes);
+
+/* Device bytes the context currently holds. */
+size_t vt_ctx_workspace_bytes(const vt_ctx *ctx);
+
+/* 1 if the last render on ctx kept per-pixel lists, else 0. */
+int32_t vt_ctx_used_lists(const vt_ctx *ctx);
+
 /* Test and inspection hook: synchronises `stream` and copies an internal
  * array of the last render to host memory dst (bytes <= capacity).
  * what: 0 = depth keys (float32 x n, 0 for culled), 1 = tile offsets

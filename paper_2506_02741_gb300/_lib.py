@@ -66,6 +66,10 @@ def _declare(L):
         "vt_ctx_timing": (C.c_int32, [_P, _P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_double), C.c_int32, C.c_int32]),
         "vt_ctx_launch_count": (C.c_int64, [_P]),
+        "vt_ctx_set_list_capacity": (C.c_int, [_P, C.c_int32]),
+        "vt_ctx_set_workspace_budget": (C.c_int, [_P, C.c_size_t]),
+        "vt_ctx_workspace_bytes": (C.c_size_t, [_P]),
+        "vt_ctx_used_lists": (C.c_int32, [_P]),
         "vt_ctx_debug_copy": (C.c_int64, [_P, C.c_int32, _P, C.c_int64, _P]),
         "vt_last_error": (C.c_char_p, []),
         "vt_version": (C.c_char_p, []),
@@ -81,7 +85,8 @@ def _declare(L):
 EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_bytes",
            "vt_ctx_sync_status", "vt_backproject", "vt_section_init", "vt_render",
            "vt_render_backward", "vt_ctx_set_timing", "vt_ctx_timing", "vt_ctx_launch_count",
-           "vt_ctx_debug_copy", "vt_last_error", "vt_version"]
+           "vt_ctx_debug_copy", "vt_last_error", "vt_version", "vt_ctx_set_list_capacity",
+           "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists"]
 
 
 def lib_path() -> str:

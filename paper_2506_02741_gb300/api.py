@@ -179,6 +179,22 @@ class Renderer:
         L.check(self._lib.vt_ctx_reserve(self._ctx, int(n_gaussians), int(W), int(H),
                                          int(n_instances), _stream(stream)), "vt_ctx_reserve")
 
+    def set_list_capacity(self, cap: int):
+        """Per-pixel list capacity for the backward (0 = always replay tiles)."""
+        L.check(self._lib.vt_ctx_set_list_capacity(self._ctx, int(cap)), "set_list_capacity")
+
+    def set_budget(self, nbytes: int):
+        """Workspace budget in bytes (0 = unbounded)."""
+        L.check(self._lib.vt_ctx_set_workspace_budget(self._ctx, int(nbytes)), "set_budget")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.vt_ctx_workspace_bytes(self._ctx))
+
+    @property
+    def used_lists(self) -> bool:
+        return bool(self._lib.vt_ctx_used_lists(self._ctx))
+
     def status(self, stream=None) -> int:
         """Synchronise and return the tile-instance count of the last render;
         raises VTError(VT_ERR_CAPACITY) if the workspace was too small."""

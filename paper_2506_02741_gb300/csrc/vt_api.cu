@@ -44,12 +44,13 @@ constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 
 
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
-    K_SECTION_INIT, K_COUNT, K_NUM
+    K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
                                    "k_composite_bwd", "k_pose_finalize", "k_backproject",
-                                   "k_section_init",  "k_count_valid"};
+                                   "k_section_init",  "k_count_valid",   "k_composite_bwd_list"};
+constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -76,6 +77,13 @@ struct vt_ctx {
     ViewXf *views = nullptr;
     TabRow *tab = nullptr;
     double *pose_partials = nullptr, *pose_copy = nullptr;
+    uint32_t *tile_ovf = nullptr;
+    // per-pixel lists of added Gaussians (separate allocation)
+    int list_cap = kDefaultListCap;
+    uint32_t *plist = nullptr;
+    size_t plist_bytes = 0;
+    size_t budget = (size_t)-1;
+    bool used_lists = false;
     // last render
     bool has_render = false;
     SecTable table{};
@@ -150,6 +158,7 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += align_up(sizeof(TabRow) * tab);
     b += align_up(sizeof(double) * 12 * t);              // pose partials
     b += align_up(sizeof(double) * 12);                  // pose copy
+    b += align_up(sizeof(uint32_t) * (t + 1));           // tile overflow flags
     return b;
 }
 
@@ -200,6 +209,7 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->tab = reinterpret_cast<TabRow *>(take(sizeof(TabRow) * tab));
     c->pose_partials = reinterpret_cast<double *>(take(sizeof(double) * 12 * t));
     c->pose_copy = reinterpret_cast<double *>(take(sizeof(double) * 12));
+    c->tile_ovf = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
     c->cap_g = g;
     c->cap_i = i;
     c->cap_p = p;
@@ -250,6 +260,7 @@ vt_status vt_ctx_create(vt_ctx **ctx) {
 void vt_ctx_destroy(vt_ctx *c) {
     if (!c) return;
     free_arena(c, c->stream);
+    if (c->plist) cudaFreeAsync(c->plist, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
@@ -333,6 +344,26 @@ int32_t vt_ctx_timing(vt_ctx *c, vt_stream stream, const char **names, int64_t *
 
 int64_t vt_ctx_launch_count(const vt_ctx *c) { return c ? c->launches : 0; }
 
+vt_status vt_ctx_set_list_capacity(vt_ctx *c, int32_t cap) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_ctx_set_list_capacity: ctx is NULL");
+    if (cap < 0 || cap > 65536)
+        return fail(VT_ERR_INVALID_ARG, "vt_ctx_set_list_capacity: %d out of [0, 65536]", cap);
+    c->list_cap = cap;
+    return VT_OK;
+}
+
+vt_status vt_ctx_set_workspace_budget(vt_ctx *c, size_t bytes) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_ctx_set_workspace_budget: ctx is NULL");
+    c->budget = bytes ? bytes : (size_t)-1;
+    return VT_OK;
+}
+
+size_t vt_ctx_workspace_bytes(const vt_ctx *c) {
+    return c ? c->arena_bytes + c->plist_bytes : 0;
+}
+
+int32_t vt_ctx_used_lists(const vt_ctx *c) { return c && c->has_render && c->used_lists; }
+
 vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const double *pose12,
                     vt_intrinsics K, int32_t W, int32_t H, float *rgb, float *depth,
                     float *silhouette, vt_stream stream) {
@@ -408,6 +439,27 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         sort_attr_set = true;
     }
     c->has_render = false;
+    // Per-pixel lists for the backward, unless they would exceed the budget
+    // (then the backward replays the tile lists instead).
+    c->used_lists = false;
+    if (c->list_cap > 0) {
+        const size_t need = sizeof(uint32_t) * (size_t)c->list_cap * (size_t)W * (size_t)H;
+        if (c->arena_bytes + need <= c->budget) {
+            if (need > c->plist_bytes) {
+                if (c->plist) cudaFreeAsync(c->plist, stream);
+                c->plist = nullptr;
+                c->plist_bytes = 0;
+                void *q = nullptr;
+                if (cudaMallocAsync(&q, need, stream) == cudaSuccess) {
+                    c->plist = static_cast<uint32_t *>(q);
+                    c->plist_bytes = need;
+                } else {
+                    cudaGetLastError();   // fall back to the tile replay
+                }
+            }
+            c->used_lists = c->plist != nullptr;
+        }
+    }
     VT_CUDA(cudaMemsetAsync(c->tile_count, 0, sizeof(uint32_t) * (n_tiles + 1), stream),
             "tile count reset");
     if (views > 0) {
@@ -443,10 +495,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     }
     {
         LaunchScope ls(c, K_FWD, stream);
-        k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(cam, c->tile_off, c->sorted, c->geo,
-                                                           c->app, rgb, depth, silhouette,
-                                                           c->pix_last, c->pix_nadd, c->pix_T,
-                                                           c->status);
+        k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(
+            cam, c->tile_off, c->sorted, c->geo, c->app, rgb, depth, silhouette, c->pix_last,
+            c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap, c->tile_ovf,
+            c->status);
     }
     VT_CUDA(cudaGetLastError(), "vt_render launch");
     c->table = T;
@@ -476,11 +528,17 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
             T.s[s].d_radius = grads[s].d_radius;
         }
     }
-    {
+    if (c->used_lists) {
+        LaunchScope ls(c, K_BWD_LIST, stream);
+        k_composite_bwd_list<<<c->n_tiles, kBlockPix, 0, stream>>>(
+            T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->tile_ovf,
+            dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->status);
+    }
+    {   // tiles without complete per-pixel lists (all of them when none were kept)
         LaunchScope ls(c, K_BWD, stream);
         k_composite_bwd<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, dL_drgb,
-            dL_ddepth, dL_dsil, mode, c->pose_partials, c->status);
+            dL_ddepth, dL_dsil, mode, c->pose_partials, c->tile_ovf, c->status);
     }
     if (mode & VT_GRAD_POSE) {
         LaunchScope ls(c, K_POSE, stream);

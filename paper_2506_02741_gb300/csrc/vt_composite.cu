@@ -24,11 +24,22 @@ __device__ __forceinline__ bool disc_touches(const float4 &g0, const float4 &g1,
     return dx * dx * g1.x + dy * dy * g1.y <= kQMax;
 }
 
+// Forward.  Each warp streams through its tile's depth-sorted list on its
+// own (no block barriers): the 32 lanes load the next 32 list entries and
+// their records into registers one round ahead, test them against the warp's
+// 8x4 pixel block, stage the round in warp-private shared memory and walk the
+// relevant ones in order.  A warp leaves as soon as all its pixels have
+// terminated.  With plist != NULL every pixel also records the ids of the
+// Gaussians it added (up to plist_cap, pixel-major), which the backward
+// replays instead of the tile list; tiles where a pixel added more are
+// flagged in tile_ovf.
 __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, float *rgb, float *depth, float *sil, uint32_t *pix_last,
-    uint32_t *pix_nadd, float *pix_T, const Status *st) {
-    __shared__ float4 s_g0[kBatch], s_g1[kBatch], s_a[kBatch];
+    uint32_t *pix_nadd, float *pix_T, uint32_t *plist, int plist_cap, uint32_t *tile_ovf,
+    const Status *st) {
+    __shared__ float4 s_g0[kBlockPix / 32][32], s_g1[kBlockPix / 32][32], s_a[kBlockPix / 32][32];
+    __shared__ uint32_t s_gid[kBlockPix / 32][32];
     if (st->flags) return;
     const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
@@ -38,61 +49,79 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     const bool inside = px < cam.W && py < cam.H;
     const float rx0 = (float)bx0, rx1 = (float)min(bx0 + 7, cam.W - 1);
     const float ry0 = (float)by0, ry1 = (float)min(by0 + 3, cam.H - 1);
-    const uint32_t start = tile_off[tile], end = tile_off[tile + 1];
+    const uint32_t start = tile_off[tile];
+    const int n = (int)(tile_off[tile + 1] - start);
+    const size_t p = inside ? (size_t)py * cam.W + px : 0;
+    uint32_t *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
     uint32_t last = 0, nadd = 0;
     bool done = !inside;
-    for (uint32_t b0 = start; b0 < end; b0 += kBatch) {
-        if (__syncthreads_and(done)) break;
-        const uint32_t i = b0 + threadIdx.x;
-        if (i < end) {
-            const uint32_t g = sorted[i];
-            s_g0[threadIdx.x] = geo[2 * (size_t)g];
-            s_g1[threadIdx.x] = geo[2 * (size_t)g + 1];
-            s_a[threadIdx.x] = app[g];
+    float4 (&g0s)[32] = s_g0[warp];
+    float4 (&g1s)[32] = s_g1[warp];
+    float4 (&as)[32] = s_a[warp];
+    uint32_t (&ids)[32] = s_gid[warp];
+
+    uint32_t gid_n = 0;
+    float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
+    if (!__all_sync(kFullMask, done) && lane < n) {
+        gid_n = sorted[start + lane];
+        g0n = geo[2 * (size_t)gid_n];
+        g1n = geo[2 * (size_t)gid_n + 1];
+        an = app[gid_n];
+    }
+    for (int base = 0; base < n; base += 32) {
+        if (__all_sync(kFullMask, done)) break;
+        const uint32_t gid = gid_n;
+        const float4 g0 = g0n, g1 = g1n, a = an;
+        const bool valid = base + lane < n;
+        const int inext = base + 32 + lane;
+        if (inext < n) {   // prefetch the next round while this one is composited
+            gid_n = sorted[start + inext];
+            g0n = geo[2 * (size_t)gid_n];
+            g1n = geo[2 * (size_t)gid_n + 1];
+            an = app[gid_n];
         }
-        __syncthreads();
-        const int nb = (int)min((uint32_t)kBatch, end - b0);
-        bool wdone = __all_sync(kFullMask, done);
-        for (int j0 = 0; j0 < nb && !wdone; j0 += 32) {
-            const int jj = j0 + lane;
-            bool rel = false;
-            if (jj < nb) rel = disc_touches(s_g0[jj], s_g1[jj], rx0, rx1, ry0, ry1);
-            unsigned mask = __ballot_sync(kFullMask, rel);
-            while (mask) {
-                const int j = j0 + __ffs(mask) - 1;
-                mask &= mask - 1;
-                if (done) continue;
-                const float4 g0 = s_g0[j], g1 = s_g1[j];
-                float du, dv;
-                const float q = pair_q(px, py, g0, g1, du, dv);
-                if (!(q <= kQMax)) continue;
-                const float ah = __fmul_rn(g1.w, pair_gauss(q));
-                if (!(ah >= kAlphaMin)) continue;
-                const float al = fminf(ah, kAlphaClamp);
-                const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
-                if (Tn < kTMin) {
-                    done = true;
-                    continue;
-                }
-                const float w = __fmul_rn(al, T);
-                const float4 a = s_a[j];
-                c0 = __fmaf_rn(w, a.x, c0);
-                c1 = __fmaf_rn(w, a.y, c1);
-                c2 = __fmaf_rn(w, a.z, c2);
-                dd = __fmaf_rn(w, g1.z, dd);
-                ss = __fadd_rn(ss, w);
-                T = Tn;
-                last = b0 - start + (uint32_t)j + 1u;
-                ++nadd;
+        const bool rel = valid && disc_touches(g0, g1, rx0, rx1, ry0, ry1);
+        unsigned mask = __ballot_sync(kFullMask, rel);
+        if (!mask) continue;
+        __syncwarp();
+        g0s[lane] = g0;
+        g1s[lane] = g1;
+        as[lane] = a;
+        ids[lane] = gid;
+        __syncwarp();
+        while (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1;
+            if (done) continue;
+            const float4 h0 = g0s[j], h1 = g1s[j];
+            float du, dv;
+            const float q = pair_q(px, py, h0, h1, du, dv);
+            if (!(q <= kQMax)) continue;
+            const float ah = __fmul_rn(h1.w, pair_gauss(q));
+            if (!(ah >= kAlphaMin)) continue;
+            const float al = fminf(ah, kAlphaClamp);
+            const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
+            if (Tn < kTMin) {
+                done = true;
+                continue;
             }
-            wdone = __all_sync(kFullMask, done);
+            const float w = __fmul_rn(al, T);
+            const float4 c = as[j];
+            c0 = __fmaf_rn(w, c.x, c0);
+            c1 = __fmaf_rn(w, c.y, c1);
+            c2 = __fmaf_rn(w, c.z, c2);
+            dd = __fmaf_rn(w, h1.z, dd);
+            ss = __fadd_rn(ss, w);
+            T = Tn;
+            last = (uint32_t)(base + j) + 1u;
+            if (mylist && nadd < (uint32_t)plist_cap) mylist[nadd] = ids[j];
+            ++nadd;
         }
-        __syncthreads();
     }
     if (inside) {
-        const size_t p = (size_t)py * cam.W + px, HW = (size_t)cam.W * cam.H;
+        const size_t HW = (size_t)cam.W * cam.H;
         if (rgb) {
             rgb[p] = c0;
             rgb[HW + p] = c1;
@@ -103,6 +132,10 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
         pix_last[p] = last;
         pix_nadd[p] = nadd;
         pix_T[p] = T;
+    }
+    if (tile_ovf) {
+        const int ovf = __syncthreads_or(plist != nullptr && nadd > (uint32_t)plist_cap);
+        if (threadIdx.x == 0) tile_ovf[tile] = plist ? (uint32_t)ovf : 1u;
     }
 }
 
@@ -130,9 +163,6 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
 // needs only A = sum x g^T and s = sum g, kept per lane in FP32, summed over
 // the warp and the block in FP64 and written as one partial per tile.
 
-struct PoseAcc {
-    float a[12];  // a[3*i + j] = sum x_i g_j ; a[9 + j] = sum g_j
-};
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -146,17 +176,146 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+struct PoseAcc {
+    float a[12];  // a[3*i + j] = sum x_i g_j ; a[9 + j] = sum g_j
+};
+
+// Per-pixel state of the back-to-front walk (see the derivation above).
+struct BwdPixel {
+    float gC0, gC1, gC2, gD, gS, Tfin, pxn, pyn;
+    float T, A0, A1, A2, Bd, Sb, cr0, cr1, cr2, zr;
+    bool have_ref;
+};
+
+__device__ __forceinline__ void bwd_pixel_init(BwdPixel &P, float Tfin, float gC0, float gC1,
+                                               float gC2, float gD, float gS, int px, int py,
+                                               const Camera &cam) {
+    P.gC0 = gC0;
+    P.gC1 = gC1;
+    P.gC2 = gC2;
+    P.gD = gD;
+    P.gS = gS;
+    P.Tfin = Tfin;
+    P.pxn = ((float)px - cam.cx) / cam.fx;
+    P.pyn = ((float)py - cam.cy) / cam.fy;
+    P.T = Tfin;
+    P.A0 = P.A1 = P.A2 = P.Bd = P.Sb = 0.f;
+    P.cr0 = P.cr1 = P.cr2 = P.zr = 0.f;
+    P.have_ref = false;
+}
+
+// One added Gaussian of the pixel, visited back to front.  Returns its
+// colour / opacity / radius gradient terms and adds its pose terms to acc.
+__device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const float4 &g1,
+                                         const float4 &a, float q, float du, float dv, float G,
+                                         float ah, const Camera &cam, bool want_pose,
+                                         PoseAcc &acc, float &dc0, float &dc1, float &dc2,
+                                         float &dop, float &drd) {
+    const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
+    const float al = fminf(ah, kAlphaClamp);
+    const float om = 1.f - al;
+    const float Ti = P.T / om;
+    const float w = al * Ti;
+    const float z = g1.z, r = a.w;
+    if (!P.have_ref) {
+        P.have_ref = true;
+        P.cr0 = a.x;
+        P.cr1 = a.y;
+        P.cr2 = a.z;
+        P.zr = z;
+    }
+    const float e0 = a.x - P.cr0, e1 = a.y - P.cr1, e2 = a.z - P.cr2, ez = z - P.zr;
+    const float num = P.gC0 * (a.x * P.Tfin + e0 * P.Sb - P.A0) +
+                      P.gC1 * (a.y * P.Tfin + e1 * P.Sb - P.A1) +
+                      P.gC2 * (a.z * P.Tfin + e2 * P.Sb - P.A2) +
+                      P.gD * (z * P.Tfin + ez * P.Sb - P.Bd) + P.gS * P.Tfin;
+    const float dal = num / om;
+    dc0 = P.gC0 * w;
+    dc1 = P.gC1 * w;
+    dc2 = P.gC2 * w;
+    float dq = 0.f;
+    dop = 0.f;
+    if (ah < kAlphaClamp) {
+        dop = dal * G;
+        dq = -0.5f * ah * dal;
+    }
+    drd = dq * (-2.f * q / r);
+    if (want_pose) {
+        const float ir2 = 1.f / (r * r);
+        const float ex = z * du * ifx, ey = z * dv * ify;
+        const float gx = dq * (-2.f * ex * ir2);
+        const float gy = dq * (-2.f * ey * ir2);
+        const float gz = dq * (2.f * (P.pxn * ex + P.pyn * ey) * ir2) + P.gD * w;
+        const float uc = (float)__float_as_int(g0.x) + g0.y;
+        const float vc = (float)__float_as_int(g0.z) + g0.w;
+        const float X[3] = {z * (uc - cam.cx) * ifx, z * (vc - cam.cy) * ify, z};
+        const float Gv[3] = {gx, gy, gz};
+#pragma unroll
+        for (int a_ = 0; a_ < 3; ++a_)
+#pragma unroll
+            for (int b_ = 0; b_ < 3; ++b_)
+                acc.a[3 * a_ + b_] = __fmaf_rn(X[a_], Gv[b_], acc.a[3 * a_ + b_]);
+        acc.a[9] += gx;
+        acc.a[10] += gy;
+        acc.a[11] += gz;
+    }
+    P.A0 = __fmaf_rn(w, e0, P.A0);
+    P.A1 = __fmaf_rn(w, e1, P.A1);
+    P.A2 = __fmaf_rn(w, e2, P.A2);
+    P.Bd = __fmaf_rn(w, ez, P.Bd);
+    P.Sb += w;
+    P.T = Ti;
+}
+
+__device__ __forceinline__ void add_attr_grads(const SecTable &Tab, int64_t g, float dc0,
+                                               float dc1, float dc2, float dop, float drd) {
+    const int s = find_section(Tab, g);
+    const SecDesc &S = Tab.s[s];
+    const int64_t li = g - S.gbase;
+    if (S.d_colour) {
+        atomicAdd(S.d_colour + 3 * li + 0, dc0);
+        atomicAdd(S.d_colour + 3 * li + 1, dc1);
+        atomicAdd(S.d_colour + 3 * li + 2, dc2);
+    }
+    if (S.d_opacity) atomicAdd(S.d_opacity + li, dop);
+    if (S.d_radius) atomicAdd(S.d_radius + li, drd);
+}
+
+// Block sum of the per-lane pose terms in FP64, in a fixed order, written as
+// the tile's partial.
+__device__ __forceinline__ void write_pose_partial(const PoseAcc &acc, double (*s_pose)[12],
+                                                   double *pose_partials, int tile) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        const double v = warp_sum_d((double)acc.a[i]);
+        if (lane == 0) s_pose[warp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        double v = 0.0;
+        for (int w = 0; w < kBlockPix / 32; ++w) v += s_pose[w][threadIdx.x];
+        pose_partials[(size_t)tile * 12 + threadIdx.x] = v;
+    }
+}
+
+// Tile replay: the block walks its tile's list from the largest list end of
+// its pixels back to the front in shared-memory batches; each warp visits the
+// Gaussians whose disc touches its 8x4 block.  Used when no per-pixel lists
+// were kept (memory budget) and for tiles whose lists overflowed (tile_mask:
+// only tiles with tile_mask[t] != 0; NULL = all tiles).
 __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     SecTable Tab, Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, const uint32_t *pix_last, const float *pix_T, const float *g_rgb,
-    const float *g_depth, const float *g_sil, int mode, double *pose_partials, const Status *st) {
+    const float *g_depth, const float *g_sil, int mode, double *pose_partials,
+    const uint32_t *tile_mask, const Status *st) {
     __shared__ float4 s_g0[kBatch], s_g1[kBatch], s_a[kBatch];
-    __shared__ float2 s_xy[kBatch];
     __shared__ uint32_t s_gid[kBatch];
     __shared__ double s_pose[kBlockPix / 32][12];
     __shared__ uint32_t s_last;
     if (st->flags) return;
     const int tile = blockIdx.x;
+    if (tile_mask && !tile_mask[tile]) return;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
@@ -170,7 +329,6 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t p = inside ? (size_t)py * cam.W + px : 0;
     uint32_t my_last = inside ? pix_last[p] : 0u;
-    const float Tfin = inside ? pix_T[p] : 1.f;
     float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gS = 0.f;
     if (inside) {
         if (g_rgb) {
@@ -182,8 +340,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
         if (g_sil) gS = g_sil[p];
     }
     if (gC0 == 0.f && gC1 == 0.f && gC2 == 0.f && gD == 0.f && gS == 0.f) my_last = 0;
-    const float pxn = ((float)px - cam.cx) / cam.fx, pyn = ((float)py - cam.cy) / cam.fy;
-    const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
+    BwdPixel P;
+    bwd_pixel_init(P, inside ? pix_T[p] : 1.f, gC0, gC1, gC2, gD, gS, px, py, cam);
 
     if (threadIdx.x == 0) s_last = 0;
     __syncthreads();
@@ -192,9 +350,6 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     __syncthreads();
     const uint32_t tile_last = s_last;
 
-    float T = Tfin, A0 = 0.f, A1 = 0.f, A2 = 0.f, Bd = 0.f, Sb = 0.f;
-    float cr0 = 0.f, cr1 = 0.f, cr2 = 0.f, zr = 0.f;
-    bool have_ref = false;
     PoseAcc acc;
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc.a[i] = 0.f;
@@ -204,15 +359,10 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
             const int nb = (int)min((uint32_t)kBatch, tile_last - (uint32_t)b0);
             if ((int)threadIdx.x < nb) {
                 const uint32_t g = sorted[start + b0 + threadIdx.x];
-                const float4 g0 = geo[2 * (size_t)g], g1 = geo[2 * (size_t)g + 1];
-                s_g0[threadIdx.x] = g0;
-                s_g1[threadIdx.x] = g1;
+                s_g0[threadIdx.x] = geo[2 * (size_t)g];
+                s_g1[threadIdx.x] = geo[2 * (size_t)g + 1];
                 s_a[threadIdx.x] = app[g];
                 s_gid[threadIdx.x] = g;
-                const float uc = (float)__float_as_int(g0.x) + g0.y;
-                const float vc = (float)__float_as_int(g0.z) + g0.w;
-                s_xy[threadIdx.x] = make_float2(g1.z * (uc - cam.cx) * ifx,
-                                                g1.z * (vc - cam.cy) * ify);
             }
             __syncthreads();
             if (wl > (uint32_t)b0) {
@@ -226,10 +376,9 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                         const int bit = 31 - __clz(mask);
                         mask &= ~(1u << bit);
                         const int j = j0 + bit;
-                        const uint32_t idx = (uint32_t)(b0 + j);
                         float dc0 = 0.f, dc1 = 0.f, dc2 = 0.f, dop = 0.f, drd = 0.f;
                         bool contrib = false;
-                        if (idx < my_last) {
+                        if ((uint32_t)(b0 + j) < my_last) {
                             const float4 g0 = s_g0[j], g1 = s_g1[j];
                             float du, dv;
                             const float q = pair_q(px, py, g0, g1, du, dv);
@@ -238,61 +387,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                                 const float ah = __fmul_rn(g1.w, G);
                                 if (ah >= kAlphaMin) {
                                     contrib = true;
-                                    const float al = fminf(ah, kAlphaClamp);
-                                    const float om = 1.f - al;
-                                    const float Ti = T / om;
-                                    const float w = al * Ti;
-                                    const float4 a = s_a[j];
-                                    const float z = g1.z, r = a.w;
-                                    if (!have_ref) {
-                                        have_ref = true;
-                                        cr0 = a.x;
-                                        cr1 = a.y;
-                                        cr2 = a.z;
-                                        zr = z;
-                                    }
-                                    const float e0 = a.x - cr0, e1 = a.y - cr1, e2 = a.z - cr2,
-                                                ez = z - zr;
-                                    const float num =
-                                        gC0 * (a.x * Tfin + e0 * Sb - A0) +
-                                        gC1 * (a.y * Tfin + e1 * Sb - A1) +
-                                        gC2 * (a.z * Tfin + e2 * Sb - A2) +
-                                        gD * (z * Tfin + ez * Sb - Bd) + gS * Tfin;
-                                    const float dal = num / om;
-                                    dc0 = gC0 * w;
-                                    dc1 = gC1 * w;
-                                    dc2 = gC2 * w;
-                                    float dq = 0.f;
-                                    if (ah < kAlphaClamp) {
-                                        dop = dal * G;
-                                        dq = -0.5f * ah * dal;
-                                    }
-                                    drd = dq * (-2.f * q / r);
-                                    if (want_pose) {
-                                        const float ir2 = 1.f / (r * r);
-                                        const float ex = z * du * ifx, ey = z * dv * ify;
-                                        const float gx = dq * (-2.f * ex * ir2);
-                                        const float gy = dq * (-2.f * ey * ir2);
-                                        const float gz =
-                                            dq * (2.f * (pxn * ex + pyn * ey) * ir2) + gD * w;
-                                        const float2 xy = s_xy[j];
-                                        const float X[3] = {xy.x, xy.y, z}, Gv[3] = {gx, gy, gz};
-#pragma unroll
-                                        for (int a_ = 0; a_ < 3; ++a_)
-#pragma unroll
-                                            for (int b_ = 0; b_ < 3; ++b_)
-                                                acc.a[3 * a_ + b_] =
-                                                    __fmaf_rn(X[a_], Gv[b_], acc.a[3 * a_ + b_]);
-                                        acc.a[9] += gx;
-                                        acc.a[10] += gy;
-                                        acc.a[11] += gz;
-                                    }
-                                    A0 = __fmaf_rn(w, e0, A0);
-                                    A1 = __fmaf_rn(w, e1, A1);
-                                    A2 = __fmaf_rn(w, e2, A2);
-                                    Bd = __fmaf_rn(w, ez, Bd);
-                                    Sb += w;
-                                    T = Ti;
+                                    bwd_pair(P, g0, g1, s_a[j], q, du, dv, G, ah, cam, want_pose,
+                                             acc, dc0, dc1, dc2, dop, drd);
                                 }
                             }
                         }
@@ -302,19 +398,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                             dc2 = warp_sum(dc2);
                             dop = warp_sum(dop);
                             drd = warp_sum(drd);
-                            if (lane == 0) {
-                                const int64_t g = s_gid[j];
-                                const int s = find_section(Tab, g);
-                                const SecDesc &S = Tab.s[s];
-                                const int64_t li = g - S.gbase;
-                                if (S.d_colour) {
-                                    atomicAdd(S.d_colour + 3 * li + 0, dc0);
-                                    atomicAdd(S.d_colour + 3 * li + 1, dc1);
-                                    atomicAdd(S.d_colour + 3 * li + 2, dc2);
-                                }
-                                if (S.d_opacity) atomicAdd(S.d_opacity + li, dop);
-                                if (S.d_radius) atomicAdd(S.d_radius + li, drd);
-                            }
+                            if (lane == 0) add_attr_grads(Tab, s_gid[j], dc0, dc1, dc2, dop, drd);
                         }
                     }
                 }
@@ -322,19 +406,74 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
             __syncthreads();
         }
     }
-    if (want_pose) {
-#pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            const double v = warp_sum_d((double)acc.a[i]);
-            if (lane == 0) s_pose[warp][i] = v;
+    if (want_pose) write_pose_partial(acc, s_pose, pose_partials, tile);
+}
+
+// Per-pixel list replay: every lane walks the ids its pixel added, recorded
+// by the forward, from the last to the first, loading each record one step
+// ahead.  No filtering and no block barriers in the walk; tiles flagged in
+// tile_ovf (a pixel exceeded the list capacity) are left to k_composite_bwd.
+__global__ void __launch_bounds__(kBlockPix) k_composite_bwd_list(
+    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
+    const float *pix_T, const uint32_t *plist, int plist_cap, const uint32_t *tile_ovf,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, const Status *st) {
+    __shared__ double s_pose[kBlockPix / 32][12];
+    if (st->flags) return;
+    const int tile = blockIdx.x;
+    if (tile_ovf[tile]) return;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
+    const int py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    const bool inside = px < cam.W && py < cam.H;
+    const bool want_attr = (mode & VT_GRAD_ATTR) != 0, want_pose = (mode & VT_GRAD_POSE) != 0;
+    const size_t HW = (size_t)cam.W * cam.H;
+    const size_t p = inside ? (size_t)py * cam.W + px : 0;
+    int n = inside ? (int)pix_nadd[p] : 0;
+    float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gS = 0.f;
+    if (inside) {
+        if (g_rgb) {
+            gC0 = g_rgb[p];
+            gC1 = g_rgb[HW + p];
+            gC2 = g_rgb[2 * HW + p];
         }
-        __syncthreads();
-        if (threadIdx.x < 12) {
-            double v = 0.0;
-            for (int w = 0; w < kBlockPix / 32; ++w) v += s_pose[w][threadIdx.x];
-            pose_partials[(size_t)tile * 12 + threadIdx.x] = v;
-        }
+        if (g_depth) gD = g_depth[p];
+        if (g_sil) gS = g_sil[p];
     }
+    if (gC0 == 0.f && gC1 == 0.f && gC2 == 0.f && gD == 0.f && gS == 0.f) n = 0;
+    BwdPixel P;
+    bwd_pixel_init(P, inside ? pix_T[p] : 1.f, gC0, gC1, gC2, gD, gS, px, py, cam);
+    PoseAcc acc;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc.a[i] = 0.f;
+    const uint32_t *mylist = plist + p * (size_t)plist_cap;
+    uint32_t g_n = 0;
+    float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
+    if (n > 0) {
+        g_n = mylist[n - 1];
+        g0n = geo[2 * (size_t)g_n];
+        g1n = geo[2 * (size_t)g_n + 1];
+        an = app[g_n];
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        const uint32_t g = g_n;
+        const float4 g0 = g0n, g1 = g1n, a = an;
+        if (k > 0) {   // prefetch the next (nearer) Gaussian
+            g_n = mylist[k - 1];
+            g0n = geo[2 * (size_t)g_n];
+            g1n = geo[2 * (size_t)g_n + 1];
+            an = app[g_n];
+        }
+        float du, dv;
+        const float q = pair_q(px, py, g0, g1, du, dv);
+        const float G = pair_gauss(q);
+        const float ah = __fmul_rn(g1.w, G);
+        float dc0, dc1, dc2, dop, drd;
+        bwd_pair(P, g0, g1, a, q, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd);
+        if (want_attr) add_attr_grads(Tab, g, dc0, dc1, dc2, dop, drd);
+    }
+    if (want_pose) write_pose_partial(acc, s_pose, pose_partials, tile);
 }
 
 // Fixed-order FP64 sum of the per-tile partials, then

@@ -288,6 +288,21 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Came
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 
+// Lanes of the warp holding the same nbits-bit digit as this lane (valid lanes
+// only): one ballot per digit bit, cheaper than a general match instruction.
+__device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, bool valid) {
+    unsigned m = __ballot_sync(kFull, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (b < nbits) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned bb = __ballot_sync(kFull, bit);
+            m &= bit ? bb : ~bb;
+        }
+    }
+    return m;
+}
+
 __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigned long long *out,
                                            int n, int shift, int nbits, uint32_t *hist) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -301,11 +316,8 @@ __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigne
         const int i = i0 + lane;
         const bool valid = i < hi;
         const unsigned d = valid ? (unsigned)(in[i] >> shift) & dmask : 0u;
-        const unsigned am = __ballot_sync(kFull, valid);
-        if (valid) {
-            const unsigned peers = __match_any_sync(am, d);
-            if (lane == __ffs(peers) - 1) h[d] += __popc(peers);
-        }
+        const unsigned peers = digit_peers(d, nbits, valid);
+        if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -351,10 +363,8 @@ __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigne
             key = in[i];
             d = (unsigned)(key >> shift) & dmask;
         }
-        const unsigned am = __ballot_sync(kFull, valid);
-        unsigned peers = 0;
+        const unsigned peers = digit_peers(d, nbits, valid);
         if (valid) {
-            peers = __match_any_sync(am, d);
             const uint32_t pos = h[d] + __popc(peers & ((1u << lane) - 1u));
             out[pos] = key;
         }

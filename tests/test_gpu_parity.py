@@ -329,3 +329,38 @@ def test_bad_arguments_rejected(dev):
     with pytest.raises(L.VTError) as ei:
         R2.backward(torch.ones(3, H, W, device=dev), pose_grad=True)
     assert ei.value.status == L.VT_ERR_STATE
+
+
+@pytest.mark.parametrize("cap", [0, 3, 256])
+def test_backward_paths_agree(dev, cap):
+    """Per-pixel list replay (cap 256), tile replay (cap 0) and the mixed case
+    where pixels overflow a tiny list (cap 3) give the oracle's gradients."""
+    osecs, target, K, W, H = _cases()["qqvga_2views"]()
+    R = api.Renderer()
+    R.set_list_capacity(cap)
+    R, dsecs, out = _render(osecs, target, K, W, H, R=R)
+    assert R.used_lists == (cap > 0)
+    ref = oracle.render(osecs, target, K, W, H)
+    clean = G.clean_mask(ref, tau_clamp=1e-4)
+    gR, gD, gS = _upstream((H, W), 77, clean)
+    want = oracle.backward(osecs, target, K, W, H, g_rgb=gR, g_depth=gD, g_sil=gS)
+    n = osecs[0].n
+    grads = [(torch.zeros(n, 3, device=dev), torch.zeros(n, device=dev), torch.zeros(n, device=dev))]
+    t = lambda a: torch.from_numpy(a).to(dev)
+    dtw, dmat = R.backward(t(gR), t(gD), t(gS), attr_grads=grads, pose_grad=True)
+    torch.cuda.synchronize()
+    for k, name in enumerate(("colour", "opacity", "radius")):
+        G.assert_grad_close(grads[0][k].cpu().numpy(), want[name][0], name=name,
+                            abs_ref=want["abs_" + name][0])
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist")
+    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat")
+
+
+def test_budget_disables_lists(dev):
+    osecs, target, K, W, H = _cases()["tiny"]()
+    R = api.Renderer()
+    R.set_budget(1)            # nothing fits: lists are dropped, the render still works
+    R, dsecs, out = _render(osecs, target, K, W, H, R=R)
+    assert not R.used_lists
+    ref = oracle.render(osecs, target, K, W, H)
+    G.assert_forward_close(out, ref, G.clean_mask(ref))
