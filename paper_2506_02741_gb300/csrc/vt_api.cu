@@ -39,17 +39,24 @@ vt_status cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-constexpr int kSortSmemN = 6144;  // tile lists up to this length are sorted in shared memory
+// Tile lists up to kSortSmemN entries are sorted in shared memory by blocks
+// small enough for two per SM; longer ones (up to kSortSmemBig) by a second
+// launch with one large block per SM; longer still in global memory.
+constexpr int kSortSmemN = 6144;
 constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 16 * 256 * 4;
+constexpr int kSortSmemBig = 13312;
+constexpr size_t kSortSmemBigBytes =
+    2 * kSortSmemBig * sizeof(unsigned long long) + 16 * 256 * 4;
 
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
-    K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_NUM
+    K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
                                    "k_composite_bwd", "k_pose_finalize", "k_backproject",
-                                   "k_section_init",  "k_count_valid",   "k_composite_bwd_list"};
+                                   "k_section_init",  "k_count_valid",   "k_composite_bwd_list",
+                                   "k_sort_tiles_long"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -434,7 +441,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         return st;
     if (!sort_attr_set) {
         VT_CUDA(cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSortSmemBytes),
+                                     (int)kSortSmemBigBytes),
                 "sort smem attribute");
         sort_attr_set = true;
     }
@@ -491,7 +498,13 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         LaunchScope ls(c, K_SORT, stream);
         k_sort_tiles<<<n_tiles, 512, kSortSmemBytes, stream>>>(c->tile_off, n_tiles, c->bucket,
                                                                c->alt, c->sorted, c->status,
-                                                               kSortSmemN);
+                                                               kSortSmemN, 0, kSortSmemN);
+    }
+    {
+        LaunchScope ls(c, K_SORT_BIG, stream);
+        k_sort_tiles<<<n_tiles, 512, kSortSmemBigBytes, stream>>>(
+            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortSmemBig,
+            kSortSmemN, 0x7fffffff);
     }
     {
         LaunchScope ls(c, K_FWD, stream);

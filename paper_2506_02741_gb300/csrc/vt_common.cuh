@@ -177,7 +177,8 @@ __global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *
 __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
                        unsigned long long *bucket, const Status *st);
 __global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,
-                             unsigned long long *alt, uint32_t *sorted, Status *st, int smem_n);
+                             unsigned long long *alt, uint32_t *sorted, Status *st, int smem_n,
+                             int lo, int hi);
 __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
                                 const float4 *geo, const float4 *app, float *rgb, float *depth,
                                 float *sil, uint32_t *pix_last, uint32_t *pix_nadd,

@@ -281,9 +281,10 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Came
 // Keys are 64-bit.  Pass A sorts by the depth key only: (zkey - zmin) sits in
 // the high word and only its significant bits are sorted.  If two entries
 // then share a depth key, pass B re-sorts by (zrel << bits_g | gid - gmin),
-// which orders ties by Gaussian id.  Lists of up to smem_n entries are
-// sorted in shared memory; longer ones in place in the tile's own range of
-// the bucket and its twin buffer.
+// which orders ties by Gaussian id.  A launch handles the tiles whose list
+// length lies in (lo, hi]; lists of up to smem_n entries are sorted in shared
+// memory, longer ones in place in the tile's own range of the bucket and its
+// twin buffer.
 
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -382,14 +383,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *til
                                                              unsigned long long *bucket,
                                                              unsigned long long *alt,
                                                              uint32_t *sorted, Status *st,
-                                                             int smem_n) {
+                                                             int smem_n, int lo, int hi) {
     extern __shared__ unsigned long long sm[];
     __shared__ uint32_t red[4][kSortWarps];
     if (st->flags) return;
     const int t = blockIdx.x;
     const uint32_t start = tile_off[t];
     const int n = (int)(tile_off[t + 1] - start);
-    if (n == 0) return;
+    if (n <= lo || n > hi) return;   // another launch sorts this size class
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (n == 1) {
         if (tid == 0) sorted[start] = (uint32_t)bucket[start];
@@ -445,11 +446,36 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *til
         cur = oth;
         oth = tmp;
     }
-    int tie = 0;
-    for (int i = tid + 1; i < n; i += kSortThreads)
-        tie |= (uint32_t)(cur[i] >> 32) == (uint32_t)(cur[i - 1] >> 32);
-    tie = __syncthreads_or(tie);
-    if (!tie) {
+    // Runs of equal depth keys (a few per tile: ~2700 FP32 keys over a depth
+    // range of some 2^22 values collide) are ordered by id in place, each by
+    // the thread at its start; only a run longer than kMaxRun (e.g. a
+    // fronto-parallel wall seen from its own view) needs pass B.  Threads
+    // only move the low words inside their own run, so the depth keys other
+    // threads read stay fixed.
+    constexpr int kMaxRun = 32;
+    int long_run = 0;
+    for (int i = tid; i < n; i += kSortThreads) {
+        const uint32_t zi = (uint32_t)(cur[i] >> 32);
+        const bool first = i == 0 || (uint32_t)(cur[i - 1] >> 32) != zi;
+        if (!first || i + 1 >= n || (uint32_t)(cur[i + 1] >> 32) != zi) continue;
+        int e = i + 1;
+        while (e < n && e - i <= kMaxRun && (uint32_t)(cur[e] >> 32) == zi) ++e;
+        if (e - i > kMaxRun) {
+            long_run = 1;
+            continue;
+        }
+        for (int a = i + 1; a < e; ++a) {   // insertion sort by id
+            const unsigned long long k = cur[a];
+            int b = a - 1;
+            while (b >= i && (uint32_t)cur[b] > (uint32_t)k) {
+                cur[b + 1] = cur[b];
+                --b;
+            }
+            cur[b + 1] = k;
+        }
+    }
+    long_run = __syncthreads_or(long_run);
+    if (!long_run) {
         for (int i = tid; i < n; i += kSortThreads) sorted[start + i] = (uint32_t)cur[i];
         return;
     }
