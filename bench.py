@@ -276,17 +276,19 @@ def main():
         tr.step()
     torch.cuda.synchronize()
     R.status()
+    # the whole step (render, loss, backward, Adam) as one CUDA graph
+    l0 = R.launches
+    tr.capture(warmup=3)
+    per_step_launches = (R.launches - l0) // 4       # 3 warm-up steps + 1 captured
     # included pairs of a representative render (for the ALU roofline)
     tr.pose.copy_(api.pose12(starts[0], dev))
     R.render([sec], tr.pose, Kt, K.W, K.H)
     pairs_fwd = int(R.debug(4, K.W * K.H).astype(np.int64).sum())
+    R.status()
 
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    R.set_timing(True)
-    R.timing(reset=True)
-    launches0 = R.launches
     with ClockSampler(local) as clk:
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -297,14 +299,12 @@ def main():
         ev0.record()
         for i in range(args.steps):
             frame_for(i)
-            tr.step()
+            tr.replay()
         ev1.record()
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
-    launches = R.launches - launches0
+    launches = per_step_launches * args.steps
     ms = ev0.elapsed_time(ev1)
-    per_kernel = R.timing(reset=True)
-    R.set_timing(False)
     R.status()
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
@@ -314,25 +314,37 @@ def main():
     value = world * P * args.steps / (ms / 1e3) / 1e6
     iters_s = world * args.steps / (ms / 1e3)
 
+    # per-kernel CUDA-event durations: the same steps run eagerly (events can
+    # not be read per kernel inside a replayed graph)
+    n_prof = min(args.steps, 200)
+    R.set_timing(True)
+    R.timing(reset=True)
+    for i in range(n_prof):
+        frame_for(i)
+        tr.step()
+    per_kernel = R.timing(reset=True)
+    R.set_timing(False)
+
     # end to end through the public API: host frame in, pose + loss out, per step
     n_e2e = min(args.steps, 200)
-    pin_rgb = [targets.rgb[i % args.frames] for i in range(args.frames)]
-    h_rgb = [torch.from_numpy(x).pin_memory() for x in pin_rgb]
+    h_rgb = [torch.from_numpy(targets.rgb[i]).pin_memory() for i in range(args.frames)]
     h_d = [torch.from_numpy(targets.depth[i]).pin_memory() for i in range(args.frames)]
-    d_rgb = torch.empty(3, K.H, K.W, device=dev)
-    d_d = torch.empty(K.H, K.W, device=dev)
     out_host = torch.empty(13, dtype=torch.float64).pin_memory()
-    tr.set_target(d_rgb, d_d)
+    res = torch.empty(13, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for i in range(n_e2e):
         f = (i // ITERS_PER_FRAME) % args.frames
-        d_rgb.copy_(h_rgb[f], non_blocking=True)
-        d_d.copy_(h_d[f], non_blocking=True)
-        loss = tr.step()
-        res = torch.cat([tr.pose, loss.reshape(1).double()])
+        if i % ITERS_PER_FRAME == 0:
+            tr.pose.copy_(api.pose12(starts[f], dev))
+            tr.reset_optimiser()
+        tr.obs_rgb.copy_(h_rgb[f], non_blocking=True)
+        tr.obs_depth.copy_(h_d[f], non_blocking=True)
+        loss = tr.replay()
+        res[:12].copy_(tr.pose)
+        res[12].copy_(loss)
         out_host.copy_(res, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
@@ -371,6 +383,7 @@ def main():
     roof["kernel"] = dom
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["traffic"] = traffic_for(dom)
+    roof["timing"] = f"CUDA events around each launch, {n_prof} eager steps of the same workload"
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -395,6 +408,7 @@ def main():
             "tracking_iters_per_s": iters_s,
             "e2e": e2e,
             "gpu_launches": int(launches),
+            "graph": "whole step captured in one CUDA graph, replayed per step",
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,

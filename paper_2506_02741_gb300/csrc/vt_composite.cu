@@ -33,7 +33,7 @@ __device__ __forceinline__ bool disc_touches(const float4 &g0, const float4 &g1,
 // Gaussians it added (up to plist_cap, pixel-major), which the backward
 // replays instead of the tile list; tiles where a pixel added more are
 // flagged in tile_ovf.
-__global__ void __launch_bounds__(kBlockPix, 5) k_composite_fwd(
+__global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, float *rgb, float *depth, float *sil, uint32_t *pix_last,
     uint32_t *pix_nadd, float *pix_T, uint32_t *plist, int plist_cap, uint32_t *tile_ovf,

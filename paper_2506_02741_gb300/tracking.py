@@ -66,11 +66,14 @@ class PoseTracker:
         self.depth = torch.empty(H, W, device=device)
         self.sil = torch.empty(H, W, device=device)
         self.loss = torch.zeros((), device=device)
-        self.obs_rgb = None
-        self.obs_depth = None
+        self.obs_rgb = torch.zeros(3, H, W, device=device)
+        self.obs_depth = torch.zeros(H, W, device=device)
+        self.graph = None
 
     def set_target(self, rgb: torch.Tensor, depth: torch.Tensor):
-        self.obs_rgb, self.obs_depth = rgb, depth
+        """Copy the observed frame into the tracker's fixed buffers."""
+        self.obs_rgb.copy_(rgb, non_blocking=True)
+        self.obs_depth.copy_(depth, non_blocking=True)
 
     def reset_optimiser(self):
         self.m.zero_()
@@ -105,6 +108,26 @@ class PoseTracker:
         tm = self.pose[9:]
         new = torch.cat([(Rm @ Rd).reshape(-1), Rm @ td + tm])
         self.pose.copy_(new)
+        return self.loss
+
+    def capture(self, warmup: int = 3):
+        """Record one step() in a CUDA graph (the renderer's workspace must be
+        reserved first: a captured render allocates nothing).  Afterwards
+        replay() runs the step with one launch; the pose, optimiser state and
+        observation buffers are updated in place."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
         return self.loss
 
 
