@@ -134,6 +134,27 @@ vt_status vt_backproject(const float *depth, int32_t W, int32_t H, vt_intrinsics
                          const double *pose12, float *centres, uint32_t *pix, int64_t cap,
                          int64_t *n_out, vt_stream stream);
 
+/* Allocation-free variant of vt_backproject (the paper has no counterpart:
+ * this is a deployment aid).  Same arguments, same results.  For callers
+ * that cannot let the library allocate device memory: code recorded into a
+ * CUDA graph without a memory pool, real-time loops that must not call the
+ * CUDA allocator after start-up, hosts that give all device memory to their
+ * own allocator.  The scratch it needs (per-block counts and offsets) lives
+ * in a fixed 512 KiB array inside the library, present on every GPU that
+ * loads it until the process exits; the call allocates nothing.
+ *   - Depth maps are limited to W * H <= 2^24 pixels; larger ones return
+ *     VT_ERR_INVALID_ARG (use vt_backproject).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the one array: calls that may overlap on the GPU (on
+ *     different streams, or from different threads) race and must be
+ *     serialised by the caller.  No state carries over from one call to the
+ *     next. */
+vt_status vt_backproject_noalloc(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                                 const double *pose12, float *centres, uint32_t *pix,
+                                 int64_t cap, int64_t *n_out, vt_stream stream);
+
 /* Section initialisation (Sec. 3.2 and supplementary r = D/f): one Gaussian
  * per valid depth pixel of n_views views, in canonical order, with
  * colour = V(u, v), opacity = 0.9 and radius = D / fx.  depth: device

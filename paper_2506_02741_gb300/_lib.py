@@ -56,6 +56,8 @@ def _declare(L):
         "vt_ctx_sync_status": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
         "vt_backproject": (C.c_int, [_P, C.c_int32, C.c_int32, Intrinsics, _P, _P, _P, C.c_int64,
                                      _P, _P]),
+        "vt_backproject_noalloc": (C.c_int, [_P, C.c_int32, C.c_int32, Intrinsics, _P, _P, _P,
+                                             C.c_int64, _P, _P]),
         "vt_section_init": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, Intrinsics, C.c_int,
                                       _P, _P, _P, _P, C.c_int64, _P, _P]),
         "vt_render": (C.c_int, [_P, C.POINTER(SectionC), C.c_int32, _P, Intrinsics, C.c_int32,
@@ -86,7 +88,8 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_ctx_sync_status", "vt_backproject", "vt_section_init", "vt_render",
            "vt_render_backward", "vt_ctx_set_timing", "vt_ctx_timing", "vt_ctx_launch_count",
            "vt_ctx_debug_copy", "vt_last_error", "vt_version", "vt_ctx_set_list_capacity",
-           "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists"]
+           "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists",
+           "vt_backproject_noalloc"]
 
 
 def lib_path() -> str:

@@ -66,6 +66,13 @@ bool finite(float x) { return std::isfinite(x); }
 
 }  // namespace
 
+// Lets other translation units of the library report an error message for
+// vt_last_error (not exported).
+__attribute__((visibility("hidden"))) vt_status vt_internal_fail(vt_status s, const char *msg) {
+    g_err = msg;
+    return s;
+}
+
 struct vt_ctx {
     int device = 0;
     // capacities
