@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--frames", type=int, default=4, help="distinct target frames to cycle")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-mapping", action="store_true", help="skip the FP16/FP32 mapping lines")
+    p.add_argument("--mapping-iters", type=int, default=60)
     return p.parse_args()
 
 
@@ -133,6 +135,53 @@ def make_workload(rank: int, n_frames: int):
     rng = np.random.default_rng(syn.POSE_NOISE_SEED + rank)
     starts = [syn.perturb_pose(path[i], rng) for i in tframes]
     return K, keys, section, targets, starts
+
+
+def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
+    """Mapping workload: 1200x680 section of 10 views (8,160,000 Gaussians),
+    colour/opacity/radius in ``prec``, FP32 compositing; one step = render
+    from a random section view + Eq. 2 L1 terms + attribute backward + Adam
+    (+ FP16 write-back).  Returns a summary dict."""
+    import torch
+
+    from paper_2506_02741_gb300 import api
+    from paper_2506_02741_gb300 import synthetic as syn
+    from paper_2506_02741_gb300.mapping import SectionMapper, random_views
+    K = syn.REPLICA
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(10 * 5)
+    keys = [path[i * 5] for i in range(10)]
+    fr = syn.render_frames(room, K, keys)
+    depth = torch.from_numpy(fr.depth).to(dev)
+    rgb = torch.from_numpy(fr.rgb).to(dev)
+    sec = api.Section.from_rgbd(depth, rgb, K.astuple(), np.stack(keys), precision=prec)
+    R = api.Renderer()
+    R.render([sec], sec.poses[0], K.astuple(), K.W, K.H, checked=True)
+    R.reserve(sec.n, K.W, K.H, int(R.status() * 1.5) + 65536)
+    m = SectionMapper(R, sec, rgb)
+    views = random_views(10, warmup + iters, seed=1)
+    for v in views[:warmup]:
+        m.step(v)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    R.set_timing(True)
+    R.timing(reset=True)
+    l0 = float(m.loss)
+    e0.record()
+    for v in views[warmup:]:
+        m.step(v)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pk = R.timing(reset=True)
+    R.set_timing(False)
+    R.status()
+    return {"workload": f"mapping_1200x680_10views_{prec}", "gaussians": sec.n,
+            "iters": iters, "ms_per_step": ms / iters,
+            "mpix_s": K.W * K.H * iters / (ms / 1e3) / 1e6,
+            "loss_first": l0, "loss_last": float(m.loss),
+            "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
 
 
 def source_hash(files):
@@ -385,6 +434,10 @@ def main():
     roof["traffic"] = traffic_for(dom)
     roof["timing"] = f"CUDA events around each launch, {n_prof} eager steps of the same workload"
 
+    mapping = None
+    if rank == 0 and not args.no_mapping:
+        mapping = {prec: run_mapping(dev, prec, args.mapping_iters) for prec in ("f16", "f32")}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -411,6 +464,7 @@ def main():
             "graph": "whole step captured in one CUDA graph, replayed per step",
             "roofline": roof,
             "cpu_baseline": cpu,
+            "mapping": mapping,
             "clocks": clocks,
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items()},
             "wall_s_timed": t_wall,

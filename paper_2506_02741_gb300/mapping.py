@@ -1,0 +1,79 @@
+"""Scene mapping driver (Sec. 3.4): learn the colour, opacity and radius of
+the Gaussians of the current section by rendering it from the views of the
+section and minimising the L1 terms of Eq. 2,
+
+    rho |V - V'|_1 + sigma U |D - D'|_1        (rho = 0.8, sigma = 1.0),
+
+with U masking pixels without valid depth.  The SSIM term of Eq. 2 is not
+part of this driver.  The render and its attribute gradient run in the vtsplat
+kernels; the loss gradient and the Adam step (learning rates of the
+supplementary: colour 0.0025, radius 0.005, opacity 0.05) are torch ops on
+the device.
+
+Attributes may be stored in FP16 (all arithmetic stays FP32): the optimiser
+then keeps FP32 master copies and writes the FP16 storage after each step.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import api
+
+
+class SectionMapper:
+    def __init__(self, renderer: api.Renderer, section: api.Section, frames_rgb: torch.Tensor,
+                 lr_colour: float = 0.0025, lr_opacity: float = 0.05, lr_radius: float = 0.005,
+                 rho: float = 0.8, sigma: float = 1.0):
+        self.R = renderer
+        self.sec = section
+        self.rgb_obs = frames_rgb                      # (V, 3, H, W) float32, device
+        self.depth_obs = section.depth                 # (V, H, W)
+        self.V, self.H, self.W = section.depth.shape
+        self.rho, self.sigma = float(rho), float(sigma)
+        dev = section.colour.device
+        self.master = [section.colour.detach().float().clone(),
+                       section.opacity.detach().float().clone(),
+                       section.radius.detach().float().clone()]
+        for m in self.master:
+            m.grad = torch.zeros_like(m)
+        self.opt = torch.optim.Adam(
+            [{"params": [self.master[0]], "lr": lr_colour},
+             {"params": [self.master[1]], "lr": lr_opacity},
+             {"params": [self.master[2]], "lr": lr_radius}], fused=True)
+        self.rgb = torch.empty(3, self.H, self.W, device=dev)
+        self.depth = torch.empty(self.H, self.W, device=dev)
+        self.sil = torch.empty(self.H, self.W, device=dev)
+        self.loss = torch.zeros((), device=dev)
+
+    def step(self, view: int):
+        """One mapping iteration rendering from section view ``view``."""
+        pose = self.sec.poses[view]
+        K = self.sec.K
+        self.R.render([self.sec], pose, K, self.W, self.H, self.rgb, self.depth, self.sil)
+        P = float(self.W * self.H)
+        V = self.rgb_obs[view]
+        D = self.depth_obs[view]
+        U = (D > 0).float()
+        dr = self.rgb - V
+        dd = self.depth - D
+        self.loss = self.rho * dr.abs().sum() / (3 * P) + self.sigma * (dd.abs() * U).sum() / P
+        g_rgb = (torch.sign(dr) * (self.rho / (3 * P))).contiguous()
+        g_d = (torch.sign(dd) * U * (self.sigma / P)).contiguous()
+        for m in self.master:
+            m.grad.zero_()
+        self.R.backward(g_rgb, g_d, None, attr_grads=[tuple(m.grad for m in self.master)])
+        self.opt.step()
+        with torch.no_grad():
+            self.master[1].clamp_(1e-4, 1.0)
+            self.master[2].clamp_(min=1e-6)
+            self.sec.colour.copy_(self.master[0])
+            self.sec.opacity.copy_(self.master[1])
+            self.sec.radius.copy_(self.master[2])
+        return self.loss
+
+
+def random_views(n_views: int, iters: int, seed: int = 0):
+    """Views to map from, drawn uniformly (Sec. 3.4: a random view of the section)."""
+    return np.random.default_rng(seed).integers(0, n_views, iters).tolist()

@@ -1,0 +1,81 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times: the GPU renders the whole frame, the oracle a crop of it (same camera
+with a shifted principal point, so the crop's pixels are the frame's pixels).
+
+* tracking: 640x480, 8 keyframes = 2,457,600 FP32 Gaussians;
+* mapping: 1200x680, 10 views = 8,160,000 FP16 Gaussians.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_02741_gb300 import api
+from paper_2506_02741_gb300 import synthetic as syn
+from tests import _gpu as G
+
+pytestmark = pytest.mark.gpu
+
+
+def _section(K, n_key, prec):
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(n_key * 5 + 4)
+    keys = [path[i * 5] for i in range(n_key)]
+    fr = syn.render_frames(room, K, keys)
+    osec = oracle.section_init(fr.depth, fr.rgb, K.astuple(), np.stack(keys))
+    return G.quantise(osec, prec), path[(n_key - 1) * 5 + 2]
+
+
+def _crop(K, x0, y0):
+    return (K.fx, K.fy, K.cx - x0, K.cy - y0)
+
+
+@pytest.mark.parametrize("cfg", ["tracking_640x480_fp32", "mapping_1200x680_fp16"])
+def test_fullsize_crop_parity(cfg):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    if cfg.startswith("tracking"):
+        K, n_key, prec = syn.VGA, 8, "f32"
+    else:
+        K, n_key, prec = syn.REPLICA, 10, "f16"
+    osec, target = _section(K, n_key, prec)
+    assert osec.n == n_key * K.W * K.H
+    sec = G.to_device(osec, prec)
+    R = api.Renderer()
+    rgb, depth, sil = R.render([sec], api.pose12(target, dev), K.astuple(), K.W, K.H, checked=True)
+    cw, ch = 96, 80
+    x0, y0 = (K.W - cw) // 2 + 16, (K.H - ch) // 2 - 8
+    Kc = _crop(K, x0, y0)
+    ref = oracle.render([osec], target, Kc, cw, ch)
+    clean = G.clean_mask(ref)
+    assert clean.mean() > 0.95
+    sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
+    out = (rgb[:, sl[0], sl[1]], depth[sl], sil[sl])
+    G.assert_forward_close(out, ref, clean)
+    # backward with the upstream gradient on the crop only
+    gm = G.clean_mask(ref, tau_clamp=1e-4)
+    rng = np.random.default_rng(8)
+    gR = (rng.normal(0, 1, (3, ch, cw)) * gm).astype(np.float32)
+    gD = (rng.normal(0, 1, (ch, cw)) * gm).astype(np.float32)
+    want = oracle.backward([osec], target, Kc, cw, ch, g_rgb=gR, g_depth=gD)
+    full_gR = torch.zeros(3, K.H, K.W, device=dev)
+    full_gD = torch.zeros(K.H, K.W, device=dev)
+    full_gR[:, sl[0], sl[1]] = torch.from_numpy(gR).to(dev)
+    full_gD[sl] = torch.from_numpy(gD).to(dev)
+    n = osec.n
+    grads = [(torch.zeros(n, 3, device=dev), torch.zeros(n, device=dev), torch.zeros(n, device=dev))]
+    dtw, dmat = R.backward(full_gR, full_gD, None, attr_grads=grads, pose_grad=True)
+    torch.cuda.synchronize()
+    touched = np.flatnonzero(want["abs_opacity"][0] > 0)
+    assert touched.size > 1000
+    for k, name in enumerate(("colour", "opacity", "radius")):
+        got = grads[0][k].cpu().numpy()
+        G.assert_grad_close(got[touched], want[name][0][touched], name=name,
+                            abs_ref=want["abs_" + name][0][touched])
+        other = np.ones(n, bool)
+        other[touched] = False
+        assert np.all(got[other] == 0)
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist")
+    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat")
