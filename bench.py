@@ -157,7 +157,7 @@ def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
     sec = api.Section.from_rgbd(depth, rgb, K.astuple(), np.stack(keys), precision=prec)
     R = api.Renderer()
     R.render([sec], sec.poses[0], K.astuple(), K.W, K.H, checked=True)
-    R.reserve(sec.n, K.W, K.H, int(R.status() * 1.5) + 65536)
+    R.reserve(sec.n, K.W, K.H, int(R.status() * 3) + 65536)   # radii may grow
     m = SectionMapper(R, sec, rgb)
     views = random_views(10, warmup + iters, seed=1)
     for v in views[:warmup]:

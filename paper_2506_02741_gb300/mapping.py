@@ -10,8 +10,12 @@ kernels; the loss gradient and the Adam step (learning rates of the
 supplementary: colour 0.0025, radius 0.005, opacity 0.05) are torch ops on
 the device.
 
-Attributes may be stored in FP16 (all arithmetic stays FP32): the optimiser
-then keeps FP32 master copies and writes the FP16 storage after each step.
+The learning rates apply, as in the 3D Gaussian splatting family the paper
+builds on, to logit(opacity) and log(radius) (a reading: the paper gives the
+rates, not the parametrisation); the kernels take and return the activated
+values, and this driver applies the chain rule.  Attributes may be stored in
+FP16 (all arithmetic stays FP32): the optimiser keeps FP32 master copies and
+writes the storage after each step.
 """
 
 from __future__ import annotations
@@ -33,11 +37,13 @@ class SectionMapper:
         self.V, self.H, self.W = section.depth.shape
         self.rho, self.sigma = float(rho), float(sigma)
         dev = section.colour.device
-        self.master = [section.colour.detach().float().clone(),
-                       section.opacity.detach().float().clone(),
-                       section.radius.detach().float().clone()]
+        o = section.opacity.detach().float().clamp(1e-4, 1 - 1e-4)
+        self.master = [section.colour.detach().float().clone(), torch.log(o / (1 - o)),
+                       torch.log(section.radius.detach().float())]
         for m in self.master:
             m.grad = torch.zeros_like(m)
+        self.d_o = torch.zeros_like(self.master[1])
+        self.d_r = torch.zeros_like(self.master[2])
         self.opt = torch.optim.Adam(
             [{"params": [self.master[0]], "lr": lr_colour},
              {"params": [self.master[1]], "lr": lr_opacity},
@@ -61,16 +67,20 @@ class SectionMapper:
         self.loss = self.rho * dr.abs().sum() / (3 * P) + self.sigma * (dd.abs() * U).sum() / P
         g_rgb = (torch.sign(dr) * (self.rho / (3 * P))).contiguous()
         g_d = (torch.sign(dd) * U * (self.sigma / P)).contiguous()
-        for m in self.master:
-            m.grad.zero_()
-        self.R.backward(g_rgb, g_d, None, attr_grads=[tuple(m.grad for m in self.master)])
+        self.master[0].grad.zero_()
+        self.d_o.zero_()
+        self.d_r.zero_()
+        self.R.backward(g_rgb, g_d, None, attr_grads=[(self.master[0].grad, self.d_o, self.d_r)])
+        with torch.no_grad():
+            o = torch.sigmoid(self.master[1])
+            r = torch.exp(self.master[2])
+            torch.mul(self.d_o, o * (1 - o), out=self.master[1].grad)   # d/dlogit
+            torch.mul(self.d_r, r, out=self.master[2].grad)             # d/dlog r
         self.opt.step()
         with torch.no_grad():
-            self.master[1].clamp_(1e-4, 1.0)
-            self.master[2].clamp_(min=1e-6)
             self.sec.colour.copy_(self.master[0])
-            self.sec.opacity.copy_(self.master[1])
-            self.sec.radius.copy_(self.master[2])
+            self.sec.opacity.copy_(torch.sigmoid(self.master[1]))
+            self.sec.radius.copy_(torch.exp(self.master[2]))
         return self.loss
 
 
