@@ -204,7 +204,8 @@ int32_t vt_ctx_timing(vt_ctx *ctx, vt_stream stream, const char **names, int64_t
 int64_t vt_ctx_launch_count(const vt_ctx *ctx);
 
 /* Per-pixel lists.  By default every render keeps, for each pixel, the ids
- * of the first `cap` Gaussians it added (4 * cap bytes per pixel, cap = 256),
+ * of the first `cap` Gaussians it added and the transmittance in front of
+ * each (8 * cap bytes per pixel, cap = 256),
  * so that the backward walks each pixel's own Gaussians; pixels that add
  * more, and renders where the lists do not fit the workspace budget, fall
  * back to replaying the tile lists (same results).  cap = 0 never keeps

@@ -50,13 +50,13 @@ constexpr size_t kSortSmemBigBytes =
 
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
-    K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_NUM
+    K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
                                    "k_composite_bwd", "k_pose_finalize", "k_backproject",
                                    "k_section_init",  "k_count_valid",   "k_composite_bwd_list",
-                                   "k_sort_tiles_long"};
+                                   "k_sort_tiles_long", "k_attr_scatter"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -92,9 +92,11 @@ struct vt_ctx {
     TabRow *tab = nullptr;
     double *pose_partials = nullptr, *pose_copy = nullptr;
     uint32_t *tile_ovf = nullptr;
+    float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
+    float *accr = nullptr;        // and radius, per Gaussian
     // per-pixel lists of added Gaussians (separate allocation)
     int list_cap = kDefaultListCap;
-    uint32_t *plist = nullptr;
+    uint2 *plist = nullptr;       // (id, transmittance in front) per added Gaussian
     size_t plist_bytes = 0;
     size_t budget = (size_t)-1;
     bool used_lists = false;
@@ -173,6 +175,7 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += align_up(sizeof(double) * 12 * t);              // pose partials
     b += align_up(sizeof(double) * 12);                  // pose copy
     b += align_up(sizeof(uint32_t) * (t + 1));           // tile overflow flags
+    b += align_up(sizeof(float4) * g) + align_up(sizeof(float) * g);   // gradient accumulators
     return b;
 }
 
@@ -224,6 +227,8 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->pose_partials = reinterpret_cast<double *>(take(sizeof(double) * 12 * t));
     c->pose_copy = reinterpret_cast<double *>(take(sizeof(double) * 12));
     c->tile_ovf = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
+    c->acc4 = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
+    c->accr = reinterpret_cast<float *>(take(sizeof(float) * g));
     c->cap_g = g;
     c->cap_i = i;
     c->cap_p = p;
@@ -457,7 +462,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     // (then the backward replays the tile lists instead).
     c->used_lists = false;
     if (c->list_cap > 0) {
-        const size_t need = sizeof(uint32_t) * (size_t)c->list_cap * (size_t)W * (size_t)H;
+        const size_t need = sizeof(uint2) * (size_t)c->list_cap * (size_t)W * (size_t)H;
         if (c->arena_bytes + need <= c->budget) {
             if (need > c->plist_bytes) {
                 if (c->plist) cudaFreeAsync(c->plist, stream);
@@ -465,7 +470,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
                 c->plist_bytes = 0;
                 void *q = nullptr;
                 if (cudaMallocAsync(&q, need, stream) == cudaSuccess) {
-                    c->plist = static_cast<uint32_t *>(q);
+                    c->plist = static_cast<uint2 *>(q);
                     c->plist_bytes = need;
                 } else {
                     cudaGetLastError();   // fall back to the tile replay
@@ -548,17 +553,28 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
             T.s[s].d_radius = grads[s].d_radius;
         }
     }
+    const bool attr = (mode & VT_GRAD_ATTR) != 0;
+    if (attr && T.n_total > 0) {
+        VT_CUDA(cudaMemsetAsync(c->acc4, 0, sizeof(float4) * T.n_total, stream), "grad acc reset");
+        VT_CUDA(cudaMemsetAsync(c->accr, 0, sizeof(float) * T.n_total, stream), "grad acc reset");
+    }
     if (c->used_lists) {
         LaunchScope ls(c, K_BWD_LIST, stream);
         k_composite_bwd_list<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->tile_ovf,
-            dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->status);
+            dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->acc4, c->accr, c->status);
     }
     {   // tiles without complete per-pixel lists (all of them when none were kept)
         LaunchScope ls(c, K_BWD, stream);
         k_composite_bwd<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, dL_drgb,
-            dL_ddepth, dL_dsil, mode, c->pose_partials, c->tile_ovf, c->status);
+            dL_ddepth, dL_dsil, mode, c->pose_partials, c->tile_ovf, c->acc4, c->accr,
+            c->status);
+    }
+    if (attr && T.n_total > 0) {
+        LaunchScope ls(c, K_SCATTER, stream);
+        k_attr_scatter<<<(unsigned)((T.n_total + 255) / 256), 256, 0, stream>>>(T, c->acc4,
+                                                                               c->accr);
     }
     if (mode & VT_GRAD_POSE) {
         LaunchScope ls(c, K_POSE, stream);

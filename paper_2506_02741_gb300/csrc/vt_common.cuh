@@ -7,7 +7,8 @@
 //   bucket   : uint64 per instance      (zkey << 32 | gid), unsorted per tile
 //   sorted   : uint32 per instance      Gaussian ids, per tile in (zkey, gid) order
 //   per pixel: list end, count added, final transmittance, and (optional)
-//              the ids of the Gaussians it added, pixel-major, plist_cap each
+//              (id, transmittance in front) of each Gaussian it added,
+//              8 B each, pixel-major, plist_cap per pixel
 // The projected centre of a Gaussian in pixels is iu + fu (integer part and
 // a float remainder), accurate to ~1e-7 px, because footprints are only
 // about one pixel wide while centres lie hundreds of pixels from the origin.
@@ -182,20 +183,22 @@ __global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned lon
 __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
                                 const float4 *geo, const float4 *app, float *rgb, float *depth,
                                 float *sil, uint32_t *pix_last, uint32_t *pix_nadd,
-                                float *pix_T, uint32_t *plist, int plist_cap, uint32_t *tile_ovf,
+                                float *pix_T, uint2 *plist, int plist_cap, uint32_t *tile_ovf,
                                 const Status *st);
 __global__ void k_composite_bwd(SecTable T, Camera cam, const uint32_t *tile_off,
                                 const uint32_t *sorted, const float4 *geo, const float4 *app,
                                 const uint32_t *pix_last, const float *pix_T,
                                 const float *g_rgb, const float *g_depth, const float *g_sil,
                                 int mode, double *pose_partials, const uint32_t *tile_mask,
-                                const Status *st);
+                                float4 *acc4, float *accr, const Status *st);
 __global__ void k_composite_bwd_list(SecTable T, Camera cam, const float4 *geo,
                                      const float4 *app, const uint32_t *pix_nadd,
-                                     const float *pix_T, const uint32_t *plist, int plist_cap,
+                                     const float *pix_T, const uint2 *plist, int plist_cap,
                                      const uint32_t *tile_ovf, const float *g_rgb,
                                      const float *g_depth, const float *g_sil, int mode,
-                                     double *pose_partials, const Status *st);
+                                     double *pose_partials, float4 *acc4, float *accr,
+                                     const Status *st);
+__global__ void k_attr_scatter(SecTable T, const float4 *acc4, const float *accr);
 __global__ void k_pose_finalize(const double *partials, int n_parts, const double *pose_copy,
                                 double *d_twist, double *d_mat);
 __global__ void k_count_valid(const float *depth, int64_t total, uint32_t *block_counts);

@@ -29,14 +29,15 @@ __device__ __forceinline__ bool disc_touches(const float4 &g0, const float4 &g1,
 // their records into registers one round ahead, test them against the warp's
 // 8x4 pixel block, stage the round in warp-private shared memory and walk the
 // relevant ones in order.  A warp leaves as soon as all its pixels have
-// terminated.  With plist != NULL every pixel also records the ids of the
-// Gaussians it added (up to plist_cap, pixel-major), which the backward
+// terminated.  With plist != NULL every pixel also records the id of every
+// Gaussian it added together with the transmittance in front of it (up to
+// plist_cap entries, pixel-major), which the backward
 // replays instead of the tile list; tiles where a pixel added more are
 // flagged in tile_ovf.
 __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, float *rgb, float *depth, float *sil, uint32_t *pix_last,
-    uint32_t *pix_nadd, float *pix_T, uint32_t *plist, int plist_cap, uint32_t *tile_ovf,
+    uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap, uint32_t *tile_ovf,
     const Status *st) {
     __shared__ float4 s_g0[kBlockPix / 32][32], s_g1[kBlockPix / 32][32], s_a[kBlockPix / 32][32];
     __shared__ uint32_t s_gid[kBlockPix / 32][32];
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     const uint32_t start = tile_off[tile];
     const int n = (int)(tile_off[tile + 1] - start);
     const size_t p = inside ? (size_t)py * cam.W + px : 0;
-    uint32_t *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
+    uint2 *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
     uint32_t last = 0, nadd = 0;
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
                 continue;
             }
             const float w = __fmul_rn(al, T);
+            const float T_prev = T;
             const float4 c = as[j];
             c0 = __fmaf_rn(w, c.x, c0);
             c1 = __fmaf_rn(w, c.y, c1);
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
             ss = __fadd_rn(ss, w);
             T = Tn;
             last = (uint32_t)(base + j) + 1u;
-            if (mylist && nadd < (uint32_t)plist_cap) mylist[nadd] = ids[j];
+            if (mylist && nadd < (uint32_t)plist_cap)
+                mylist[nadd] = make_uint2(ids[j], __float_as_uint(T_prev));
             ++nadd;
         }
     }
@@ -206,15 +209,18 @@ __device__ __forceinline__ void bwd_pixel_init(BwdPixel &P, float Tfin, float gC
 
 // One added Gaussian of the pixel, visited back to front.  Returns its
 // colour / opacity / radius gradient terms and adds its pose terms to acc.
+// Ti_fwd >= 0 is the forward's transmittance in front of this Gaussian
+// (recorded in the per-pixel list); otherwise it is recovered by division,
+// which accumulates the rounding of every Gaussian behind.
 __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const float4 &g1,
                                          const float4 &a, float q, float du, float dv, float G,
                                          float ah, const Camera &cam, bool want_pose,
                                          PoseAcc &acc, float &dc0, float &dc1, float &dc2,
-                                         float &dop, float &drd) {
+                                         float &dop, float &drd, float Ti_fwd = -1.f) {
     const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
     const float al = fminf(ah, kAlphaClamp);
     const float om = 1.f - al;
-    const float Ti = P.T / om;
+    const float Ti = Ti_fwd >= 0.f ? Ti_fwd : P.T / om;
     const float w = al * Ti;
     const float z = g1.z, r = a.w;
     if (!P.have_ref) {
@@ -267,18 +273,34 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
     P.T = Ti;
 }
 
+// Attribute gradient terms go to a workspace accumulator indexed by Gaussian
+// id: one 16-byte vector atomic for (colour, opacity) and one for the radius
+// instead of five scalar ones; k_attr_scatter then adds them to the caller's
+// per-section buffers.  Gaussians of frozen sections are skipped.
 __device__ __forceinline__ void add_attr_grads(const SecTable &Tab, int64_t g, float dc0,
-                                               float dc1, float dc2, float dop, float drd) {
-    const int s = find_section(Tab, g);
-    const SecDesc &S = Tab.s[s];
+                                               float dc1, float dc2, float dop, float drd,
+                                               float4 *acc4, float *accr) {
+    const SecDesc &S = Tab.s[find_section(Tab, g)];
+    if (!S.d_colour && !S.d_opacity && !S.d_radius) return;
+    atomicAdd(acc4 + g, make_float4(dc0, dc1, dc2, dop));
+    atomicAdd(accr + g, drd);
+}
+
+__global__ void __launch_bounds__(256) k_attr_scatter(SecTable Tab, const float4 *acc4,
+                                                      const float *accr) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Tab.n_total) return;
+    const SecDesc &S = Tab.s[find_section(Tab, g)];
+    if (!S.d_colour && !S.d_opacity && !S.d_radius) return;
     const int64_t li = g - S.gbase;
+    const float4 v = acc4[g];
     if (S.d_colour) {
-        atomicAdd(S.d_colour + 3 * li + 0, dc0);
-        atomicAdd(S.d_colour + 3 * li + 1, dc1);
-        atomicAdd(S.d_colour + 3 * li + 2, dc2);
+        S.d_colour[3 * li + 0] += v.x;
+        S.d_colour[3 * li + 1] += v.y;
+        S.d_colour[3 * li + 2] += v.z;
     }
-    if (S.d_opacity) atomicAdd(S.d_opacity + li, dop);
-    if (S.d_radius) atomicAdd(S.d_radius + li, drd);
+    if (S.d_opacity) S.d_opacity[li] += v.w;
+    if (S.d_radius) S.d_radius[li] += accr[g];
 }
 
 // Block sum of the per-lane pose terms in FP64, in a fixed order, written as
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     SecTable Tab, Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, const uint32_t *pix_last, const float *pix_T, const float *g_rgb,
     const float *g_depth, const float *g_sil, int mode, double *pose_partials,
-    const uint32_t *tile_mask, const Status *st) {
+    const uint32_t *tile_mask, float4 *acc4, float *accr, const Status *st) {
     __shared__ float4 s_g0[kBatch], s_g1[kBatch], s_a[kBatch];
     __shared__ uint32_t s_gid[kBatch];
     __shared__ double s_pose[kBlockPix / 32][12];
@@ -398,7 +420,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                             dc2 = warp_sum(dc2);
                             dop = warp_sum(dop);
                             drd = warp_sum(drd);
-                            if (lane == 0) add_attr_grads(Tab, s_gid[j], dc0, dc1, dc2, dop, drd);
+                            if (lane == 0)
+                                add_attr_grads(Tab, s_gid[j], dc0, dc1, dc2, dop, drd, acc4, accr);
                         }
                     }
                 }
@@ -415,9 +438,9 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
 // tile_ovf (a pixel exceeded the list capacity) are left to k_composite_bwd.
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
     SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
-    const float *pix_T, const uint32_t *plist, int plist_cap, const uint32_t *tile_ovf,
+    const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *tile_ovf,
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
-    double *pose_partials, const Status *st) {
+    double *pose_partials, float4 *acc4, float *accr, const Status *st) {
     __shared__ double s_pose[kBlockPix / 32][12];
     if (st->flags) return;
     const int tile = blockIdx.x;
@@ -447,31 +470,32 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
     PoseAcc acc;
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc.a[i] = 0.f;
-    const uint32_t *mylist = plist + p * (size_t)plist_cap;
-    uint32_t g_n = 0;
+    const uint2 *mylist = plist + p * (size_t)plist_cap;
+    uint2 e_n = make_uint2(0u, 0u);
     float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
     if (n > 0) {
-        g_n = mylist[n - 1];
-        g0n = geo[2 * (size_t)g_n];
-        g1n = geo[2 * (size_t)g_n + 1];
-        an = app[g_n];
+        e_n = mylist[n - 1];
+        g0n = geo[2 * (size_t)e_n.x];
+        g1n = geo[2 * (size_t)e_n.x + 1];
+        an = app[e_n.x];
     }
     for (int k = n - 1; k >= 0; --k) {
-        const uint32_t g = g_n;
+        const uint32_t g = e_n.x;
+        const float Ti = __uint_as_float(e_n.y);
         const float4 g0 = g0n, g1 = g1n, a = an;
         if (k > 0) {   // prefetch the next (nearer) Gaussian
-            g_n = mylist[k - 1];
-            g0n = geo[2 * (size_t)g_n];
-            g1n = geo[2 * (size_t)g_n + 1];
-            an = app[g_n];
+            e_n = mylist[k - 1];
+            g0n = geo[2 * (size_t)e_n.x];
+            g1n = geo[2 * (size_t)e_n.x + 1];
+            an = app[e_n.x];
         }
         float du, dv;
         const float q = pair_q(px, py, g0, g1, du, dv);
         const float G = pair_gauss(q);
         const float ah = __fmul_rn(g1.w, G);
         float dc0, dc1, dc2, dop, drd;
-        bwd_pair(P, g0, g1, a, q, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd);
-        if (want_attr) add_attr_grads(Tab, g, dc0, dc1, dc2, dop, drd);
+        bwd_pair(P, g0, g1, a, q, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd, Ti);
+        if (want_attr) add_attr_grads(Tab, g, dc0, dc1, dc2, dop, drd, acc4, accr);
     }
     if (want_pose) write_pose_partial(acc, s_pose, pose_partials, tile);
 }
