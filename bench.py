@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-mapping", action="store_true", help="skip the FP16/FP32 mapping lines")
     p.add_argument("--mapping-iters", type=int, default=60)
+    p.add_argument("--no-serving", action="store_true", help="skip the serving load points")
+    p.add_argument("--serving-requests", type=int, default=300)
     return p.parse_args()
 
 
@@ -182,6 +184,68 @@ def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
             "mpix_s": K.W * K.H * iters / (ms / 1e3) / 1e6,
             "loss_first": l0, "loss_last": float(m.loss),
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
+
+
+def run_serving(dev, n_req: int = 300):
+    """Serving workload: 4 resident sections (0.3 M - 8.3 M Gaussians),
+    Poisson render/track requests (70% track) over 320x240 ... 1920x1080.
+    Served form: FP16 attributes, 4 slots, CUDA graphs.  Baseline: FP32
+    attributes, one request at a time, eager.  Returns a summary dict."""
+    import torch
+
+    from paper_2506_02741_gb300 import api, serving
+    from paper_2506_02741_gb300 import synthetic as syn
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(40)
+    specs = ((320, 240, 4), (640, 480, 4), (1280, 720, 3), (1920, 1080, 4))
+    sec16, sec32, poses = [], [], []
+    for k, (W, H, nv) in enumerate(specs):
+        K = syn.scaled_intrinsics(W, H)
+        keys = [path[4 * k + 3 * j] for j in range(nv)]
+        fr = syn.render_frames(room, K, keys)
+        d = torch.from_numpy(fr.depth).to(dev)
+        c = torch.from_numpy(fr.rgb).to(dev)
+        sec16.append(api.Section.from_rgbd(d, c, K.astuple(), np.stack(keys), precision="f16"))
+        sec32.append(api.Section.from_rgbd(d, c, K.astuple(), np.stack(keys), precision="f32"))
+        poses.append([syn.perturb_pose(keys[-1], np.random.default_rng(50 + 7 * k + j))
+                      for j in range(4)])
+    res = [(W, H) for W, H, _ in specs]
+    obs = []
+    for W, H in res:
+        dd, cc = syn.raycast(room, syn.scaled_intrinsics(W, H), path[9])
+        obs.append((torch.from_numpy(cc).to(dev), torch.from_numpy(dd).to(dev)))
+    out = {"sections_gaussians": [s.n for s in sec16], "resolutions": res,
+           "mix": "70% track (fwd + Eq. 1 L1 + pose bwd, pose gradient to host), 30% render "
+                  "(colour image to host)"}
+    served = serving.Server(sec16, res, obs, n_slots=4, graphs=True)
+    base = serving.Server(sec32, res, obs, n_slots=1, graphs=False)
+    burst = serving.poisson_requests(n_req, 1e9, len(sec16), len(res), poses, seed=3)
+    served.warm(burst)
+    base.warm(burst)
+    sat = serving.latency_summary(served.run(burst), res)
+    sat_b = serving.latency_summary(base.run(burst), res)
+    out["saturated"] = {"served_req_s": n_req / sat["span_s"], "served_mpix_s": sat["mpix_s"],
+                        "baseline_req_s": n_req / sat_b["span_s"],
+                        "baseline_mpix_s": sat_b["mpix_s"], "slots": len(served.slots)}
+    loads = {}
+    for frac in (0.5, 0.9):
+        rate = frac * n_req / sat["span_s"]
+        reqs = serving.poisson_requests(n_req, rate, len(sec16), len(res), poses, seed=4)
+        a = serving.latency_summary(served.run(reqs), res)
+        reqs = serving.poisson_requests(n_req, rate, len(sec16), len(res), poses, seed=4)
+        b = serving.latency_summary(base.run(reqs, timeout=300.0), res)
+        loads[f"{int(frac * 100)}pct_of_served_saturation"] = {
+            "rate_req_s": rate, "served": a, "baseline_fp32_one_at_a_time": b}
+    out["load_points"] = loads
+    # matched accuracy: FP16 vs FP32 colour on one request of every section
+    errs = []
+    for k in range(len(sec16)):
+        r = serving.Request(0, "render", k, poses[k][0], 1)
+        (x,) = served.run([r])
+        (y,) = base.run([serving.Request(0, "render", k, poses[k][0], 1)])
+        errs.append(float((x.result - y.result).abs().max()))
+    out["fp16_vs_fp32_colour_maxabs"] = errs
+    return out
 
 
 def source_hash(files):
@@ -438,6 +502,10 @@ def main():
     if rank == 0 and not args.no_mapping:
         mapping = {prec: run_mapping(dev, prec, args.mapping_iters) for prec in ("f16", "f32")}
 
+    serving_line = None
+    if rank == 0 and not args.no_serving:
+        serving_line = run_serving(dev, args.serving_requests)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -465,6 +533,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "mapping": mapping,
+            "serving": serving_line,
             "clocks": clocks,
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items()},
             "wall_s_timed": t_wall,
