@@ -143,6 +143,34 @@ class Server:
         g, p, i = slot.reserved
         return n <= g and W * H <= p and inst <= i
 
+    # -- execution --------------------------------------------------------------
+    def _launch(self, slot, req):
+        key = (req.section, req.bucket, req.kind)
+        work = slot.works.get(key)
+        with torch.cuda.stream(slot.stream):
+            if work is None:
+                if not self._fits(slot, req):
+                    raise RuntimeError("request larger than the slot workspaces sized in warm()")
+                work = _Work(slot, self, req.section, req.bucket, req.kind)
+                slot.works[key] = work
+                if self.graphs:
+                    work.pose.copy_(api.pose12(req.pose, self.device))
+                    work.run()                      # warm-up outside the capture
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=slot.stream):
+                        work.run()
+                    work.graph = g
+            work.pose.copy_(api.pose12(req.pose, self.device), non_blocking=True)
+            if work.graph is not None:
+                work.graph.replay()
+            else:
+                work.run()
+            src = work.rgb if req.kind == "render" else work.d_twist
+            work.host.copy_(src, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+        slot.request, slot.event, slot.work = req, ev, work
+
     def warm(self, requests):
         """Size the slot workspaces and capture the graphs for every
         (slot, section, bucket, kind) the requests use."""
