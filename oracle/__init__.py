@@ -207,7 +207,8 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
 
     Returns dict(colour=[(n,3)], opacity=[(n,)], radius=[(n,)] per section,
     twist (6,) and mat (12,) float64, and abs_colour/abs_opacity/abs_radius:
-    per element the sum of the magnitudes of its per-pixel terms)."""
+    per element the sum over pixels of the componentwise magnitude of each
+    term, i.e. of the absolute values of the products its formula adds)."""
     secs, arr, keep = _sections(secs)
     ups = [None if g is None else np.ascontiguousarray(g, np.float64) for g in (g_rgb, g_depth, g_sil)]
     up = _Upstream(*[_ptr(u) for u in ups])

@@ -468,14 +468,24 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
                     }
                     if (dop_ && dop_[G->sec]) atomic_add(&dop_[G->sec][G->local], dop);
                     if (drad && drad[G->sec]) atomic_add(&drad[G->sec][G->local], dr);
-                    /* magnitude of every per-pixel term: the condition of each sum */
+                    /* Componentwise magnitude of every per-pixel term: the sum of the
+                     * absolute values of the products the derivative formula adds,
+                     * which bounds the floating-point error of evaluating the term
+                     * (the term itself can cancel to far less). */
+                    double mal = Tb[j] * (fabs(gC[0] * G->c[0]) + fabs(gC[1] * G->c[1]) +
+                                          fabs(gC[2] * G->c[2]) + fabs(gD * z)) +
+                                 (fabs(gC[0] * A[0]) + fabs(gC[1] * A[1]) + fabs(gC[2] * A[2]) +
+                                  fabs(gD * Bd) + fabs(gS * Tfin)) / (1.0 - al);
                     if (gr->a_colour && gr->a_colour[G->sec])
                         for (int c = 0; c < 3; ++c)
                             atomic_add(&gr->a_colour[G->sec][3 * G->local + c], fabs(gC[c] * w));
-                    if (gr->a_opacity && gr->a_opacity[G->sec])
-                        atomic_add(&gr->a_opacity[G->sec][G->local], fabs(dop));
-                    if (gr->a_radius && gr->a_radius[G->sec])
-                        atomic_add(&gr->a_radius[G->sec][G->local], fabs(dr));
+                    if (e->ahat < ORC_A_CLAMP) {
+                        if (gr->a_opacity && gr->a_opacity[G->sec])
+                            atomic_add(&gr->a_opacity[G->sec][G->local], mal * e->G);
+                        if (gr->a_radius && gr->a_radius[G->sec])
+                            atomic_add(&gr->a_radius[G->sec][G->local],
+                                       mal * 0.5 * e->ahat * 2.0 * e->q / r);
+                    }
                     double gv[3] = {gx, gy, gz};
                     const double *x = G->x;
                     ltw[0] -= gx;

@@ -68,8 +68,10 @@ typedef struct {
     double **d_colour;           /* per section, n x 3 (entries may be NULL) */
     double **d_opacity;          /* per section, n */
     double **d_radius;           /* per section, n */
-    double **a_colour;           /* optional, per section n x 3: sum over pixels of |term| */
-    double **a_opacity;          /* optional: the same for opacity */
+    double **a_colour;           /* optional, per section n x 3: sum over pixels of the
+                                    componentwise magnitude of each term (|gC w| for colour) */
+    double **a_opacity;          /* optional: the same for opacity (sum of |products| of the
+                                    dL/dalpha formula times dalpha/do) */
     double **a_radius;           /* optional: the same for radius */
     double twist[6];             /* dL/d(rho, phi) for P(xi) = P * Exp(xi) */
     double mat[12];              /* dL/dR (row-major 3x3) then dL/dt */

@@ -65,12 +65,13 @@ def assert_grad_close(g, ref, tol=1e-4, name="", abs_ref=None):
     """Per-tensor relative L2 <= tol, and per element
     |g - ref| <= tol * max(|ref|, 1e-3 max|ref|) + tol * sum|terms|.
 
-    The second term applies the same relative tolerance to each pixel's term
-    (the oracle reports sum|terms| for every element): a gradient element is
-    a sum of per-pixel terms of mixed sign that can cancel, and each FP32 term
-    carries the error of the transmittance product in front of it, about
-    sum_i (alpha_i / (1 - alpha_i)) x 1e-7 (~1e-5 to 1e-4 after 50 Gaussians
-    of alpha ~0.9)."""
+    The second term applies the same relative tolerance to the componentwise
+    magnitude of each pixel's term (the oracle reports, per element, the sum
+    over pixels of the absolute values of the products the derivative formula
+    adds): terms cancel within a pixel's formula and across pixels, and each
+    FP32 product carries the error of the transmittance product in front of
+    it, about sum_i (alpha_i / (1 - alpha_i)) x 1e-7 (~1e-5 to 1e-4 after 50
+    Gaussians of alpha ~0.9)."""
     g = np.asarray(g, np.float64).ravel()
     ref = np.asarray(ref, np.float64).ravel()
     assert rel_l2(g, ref) <= tol, (name, rel_l2(g, ref))
