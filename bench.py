@@ -238,13 +238,19 @@ def run_serving(dev, n_req: int = 300):
             "rate_req_s": rate, "served": a, "baseline_fp32_one_at_a_time": b}
     out["load_points"] = loads
     # matched accuracy: FP16 vs FP32 colour on one request of every section
-    errs = []
+    # The 3-sigma cut and the 1/255 skip are discontinuous: FP16 rounding of o
+    # and r moves a few Gaussians across them (jumps of ~0.01 c), so the
+    # difference is reported as a distribution.
+    diffs = []
     for k in range(len(sec16)):
         r = serving.Request(0, "render", k, poses[k][0], 1)
         (x,) = served.run([r])
         (y,) = base.run([serving.Request(0, "render", k, poses[k][0], 1)])
-        errs.append(float((x.result - y.result).abs().max()))
-    out["fp16_vs_fp32_colour_maxabs"] = errs
+        diffs.append((x.result - y.result).abs().flatten().numpy())
+    d = np.concatenate(diffs)
+    out["fp16_vs_fp32_colour_abs"] = {"max": float(d.max()), "p99": float(np.percentile(d, 99)),
+                                      "p99_9": float(np.percentile(d, 99.9)),
+                                      "frac_above_2e-3": float(np.mean(d > 2e-3))}
     return out
 
 
