@@ -124,9 +124,24 @@ class ClockSampler:
 # workload
 
 
-def make_workload(rank: int, n_frames: int):
+def reduce_max(x: float, world: int, device) -> float:
+    """Max of a per-rank scalar over all ranks (the timing rule: the job is
+    as slow as its slowest rank).  Not on the data path."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(rank: int, n_frames: int, K=None):
+    """Section of 8 keyframes (identical on every rank) and ``n_frames``
+    target frames with perturbed start poses; rank r tracks its own frames
+    (weak scaling: independent problems, no data exchange)."""
     from paper_2506_02741_gb300 import synthetic as syn
-    K = syn.VGA
+    K = K or syn.VGA
     room = syn.make_room(syn.SCENE_SEED)
     n_key, every = 8, 5
     path = syn.trajectory(n_key * every + 4 + n_frames * 3 + 3 * rank)
@@ -425,10 +440,7 @@ def main():
     launches = per_step_launches * args.steps
     ms = ev0.elapsed_time(ev1)
     R.status()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, world, dev)
     P = K.W * K.H
     value = world * P * args.steps / (ms / 1e3) / 1e6
     iters_s = world * args.steps / (ms / 1e3)
@@ -467,10 +479,7 @@ def main():
         out_host.copy_(res, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(e2e_s, world, dev)
     e2e = {"value": world * P * n_e2e / e2e_s / 1e6, "unit": "Mpix/s",
            "h2d_bytes_per_step": int(h_rgb[0].numel() * 4 + h_d[0].numel() * 4),
            "d2h_bytes_per_step": int(out_host.numel() * 8), "steps": n_e2e}
