@@ -45,15 +45,11 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // Quarter-warp q (lanes 8q..8q+7) owns the 4x2 quadrant (q & 1, q >> 1)
-    // of the warp's 8x4 block and steps through the Gaussians relevant to its
-    // quadrant on its own: per round the warp runs as many steps as its
-    // busiest quadrant needs instead of one step per Gaussian relevant to
-    // any pixel of the block.
     const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
-    const int quad = lane >> 3, k8 = lane & 7;
-    const int px = bx0 + (quad & 1) * 4 + (k8 & 3), py = by0 + (quad >> 1) * 2 + (k8 >> 2);
+    const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
     const bool inside = px < cam.W && py < cam.H;
+    const float rx0 = (float)bx0, rx1 = (float)min(bx0 + 7, cam.W - 1);
+    const float ry0 = (float)by0, ry1 = (float)min(by0 + 3, cam.H - 1);
     const uint32_t start = tile_off[tile];
     const int n = (int)(tile_off[tile + 1] - start);
     const size_t p = inside ? (size_t)py * cam.W + px : 0;
@@ -87,30 +83,18 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
             g1n = geo[2 * (size_t)gid_n + 1];
             an = app[gid_n];
         }
-        // relevance of this lane's Gaussian to each of the four quadrants
-        unsigned mq = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int x0 = bx0 + (q & 1) * 4, y0 = by0 + (q >> 1) * 2;
-            const bool r = valid && x0 < cam.W && y0 < cam.H &&
-                           disc_touches(g0, g1, (float)x0, (float)min(x0 + 3, cam.W - 1),
-                                        (float)y0, (float)min(y0 + 1, cam.H - 1));
-            const unsigned b = __ballot_sync(kFullMask, r);
-            if (q == quad) mq = b;
-        }
-        const unsigned live = __ballot_sync(kFullMask, !done);
-        if (((live >> (quad * 8)) & 0xffu) == 0u) mq = 0u;   // quadrant finished
-        if (!__any_sync(kFullMask, mq != 0u)) continue;
+        const bool rel = valid && disc_touches(g0, g1, rx0, rx1, ry0, ry1);
+        unsigned mask = __ballot_sync(kFullMask, rel);
+        if (!mask) continue;
         __syncwarp();
         g0s[lane] = g0;
         g1s[lane] = g1;
         as[lane] = a;
         ids[lane] = gid;
         __syncwarp();
-        while (__any_sync(kFullMask, mq != 0u)) {
-            if (!mq) continue;
-            const int j = __ffs(mq) - 1;
-            mq &= mq - 1;
+        while (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1;
             if (done) continue;
             const float4 h0 = g0s[j], h1 = g1s[j];
             float du, dv;
