@@ -68,7 +68,8 @@ class _Upstream(C.Structure):
 class _Grads(C.Structure):
     _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
                 ("a_colour", C.c_void_p), ("a_opacity", C.c_void_p), ("a_radius", C.c_void_p),
-                ("twist", C.c_double * 6), ("mat", C.c_double * 12)]
+                ("twist", C.c_double * 6), ("mat", C.c_double * 12),
+                ("twist_noise", C.c_double * 6), ("mat_noise", C.c_double * 12)]
 
 
 def lib():
@@ -208,7 +209,10 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     Returns dict(colour=[(n,3)], opacity=[(n,)], radius=[(n,)] per section,
     twist (6,) and mat (12,) float64, and abs_colour/abs_opacity/abs_radius:
     per element the sum over pixels of the componentwise magnitude of each
-    term, i.e. of the absolute values of the products its formula adds)."""
+    term, i.e. of the absolute values of the products its formula adds;
+    twist_noise (6,) and mat_noise (12,): per component
+    sqrt(sum over pixels of n_p m_p^2), n_p the pixel's added Gaussians and
+    m_p the componentwise magnitude of the pixel's contribution)."""
     secs, arr, keep = _sections(secs)
     ups = [None if g is None else np.ascontiguousarray(g, np.float64) for g in (g_rgb, g_depth, g_sil)]
     up = _Upstream(*[_ptr(u) for u in ups])
@@ -227,7 +231,8 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     if rc != 0:
         raise RuntimeError("oracle backward failed")
     return dict(colour=dcol, opacity=dop, radius=drad, twist=np.array(g.twist[:]),
-                mat=np.array(g.mat[:]), abs_colour=acol, abs_opacity=aop, abs_radius=arad)
+                mat=np.array(g.mat[:]), abs_colour=acol, abs_opacity=aop, abs_radius=arad,
+                twist_noise=np.array(g.twist_noise[:]), mat_noise=np.array(g.mat_noise[:]))
 
 
 def zkeys(sec: Section, pose, K, W, H):

@@ -398,11 +398,11 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
     if (binned) build_bins(g, n, cam, &B);
     int64_t HW = (int64_t)cam->W * cam->H;
     const double *R = cam->pose;
-    double tw[6] = {0}, mt[12] = {0};
+    double tw[6] = {0}, mt[12] = {0}, nz[18] = {0};
 #pragma omp parallel num_threads(orc_get_threads())
     {
         scratch_t sc = {0};
-        double ltw[6] = {0}, lmt[12] = {0};
+        double ltw[6] = {0}, lmt[12] = {0}, lnz[18] = {0};
         double *Tb = NULL, *wb = NULL;
         int64_t wcap = 0;
 #pragma omp for schedule(dynamic, 1)
@@ -441,6 +441,7 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
                     T = T * (1.0 - sc.buf[j].alpha);
                 }
                 double A[3] = {0, 0, 0}, Bd = 0;    /* sums over the Gaussians behind */
+                double pm[18] = {0};                 /* componentwise pose magnitudes */
                 for (int64_t j = k - 1; j >= 0; --j) {
                     const inc_t *e = &sc.buf[j];
                     const gpre *G = &g[e->gi];
@@ -498,17 +499,35 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
                         for (int a = 0; a < 3; ++a) lmt[3 * b + a] += G->d[b] * gv[a];
                     for (int b = 0; b < 3; ++b)
                         lmt[9 + b] -= R[3 * b + 0] * gx + R[3 * b + 1] * gy + R[3 * b + 2] * gz;
+                    /* magnitudes: |g| per axis from its products, then the same
+                     * sums as above with every product taken absolute */
+                    double ag[3] = {fabs(gx), fabs(gy),
+                                    fabs(dq * 2.0 * px * e->ex / (r * r)) +
+                                        fabs(dq * 2.0 * py * e->ey / (r * r)) + fabs(gD * w)};
+                    pm[0] += ag[0];
+                    pm[1] += ag[1];
+                    pm[2] += ag[2];
+                    pm[3] += ag[1] * fabs(x[2]) + ag[2] * fabs(x[1]);
+                    pm[4] += ag[2] * fabs(x[0]) + ag[0] * fabs(x[2]);
+                    pm[5] += ag[0] * fabs(x[1]) + ag[1] * fabs(x[0]);
+                    for (int b = 0; b < 3; ++b)
+                        for (int a = 0; a < 3; ++a) pm[6 + 3 * b + a] += fabs(G->d[b]) * ag[a];
+                    for (int b = 0; b < 3; ++b)
+                        pm[15 + b] += fabs(R[3 * b + 0]) * ag[0] + fabs(R[3 * b + 1]) * ag[1] +
+                                      fabs(R[3 * b + 2]) * ag[2];
                     A[0] += w * G->c[0];
                     A[1] += w * G->c[1];
                     A[2] += w * G->c[2];
                     Bd += w * z;
                 }
+                for (int i = 0; i < 18; ++i) lnz[i] += (double)k * pm[i] * pm[i];
             }
         }
 #pragma omp critical
         {
             for (int i = 0; i < 6; ++i) tw[i] += ltw[i];
             for (int i = 0; i < 12; ++i) mt[i] += lmt[i];
+            for (int i = 0; i < 18; ++i) nz[i] += lnz[i];
         }
         free(sc.buf);
         free(Tb);
@@ -516,6 +535,8 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
     }
     memcpy(gr->twist, tw, sizeof tw);
     memcpy(gr->mat, mt, sizeof mt);
+    for (int i = 0; i < 6; ++i) gr->twist_noise[i] = sqrt(nz[i]);
+    for (int i = 0; i < 12; ++i) gr->mat_noise[i] = sqrt(nz[6 + i]);
     if (binned) free_bins(&B);
     free(g);
     return 0;

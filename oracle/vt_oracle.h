@@ -75,6 +75,12 @@ typedef struct {
     double **a_radius;           /* optional: the same for radius */
     double twist[6];             /* dL/d(rho, phi) for P(xi) = P * Exp(xi) */
     double mat[12];              /* dL/dR (row-major 3x3) then dL/dt */
+    double twist_noise[6];       /* sqrt(sum over pixels of n_p m_p^2), n_p the pixel's added
+                                    Gaussians and m_p the componentwise magnitude of its
+                                    contribution to the component: the scale of the rounding
+                                    noise of an evaluation that sums each pixel's terms in a
+                                    short float format and the pixels in a long one */
+    double mat_noise[12];        /* the same for mat */
 } orc_grads;
 
 void orc_set_threads(int n);

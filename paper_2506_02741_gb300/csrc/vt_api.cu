@@ -91,7 +91,9 @@ struct vt_ctx {
     ViewXf *views = nullptr;
     TabRow *tab = nullptr;
     double *pose_partials = nullptr, *pose_copy = nullptr;
-    uint32_t *tile_ovf = nullptr;
+    uint32_t *blk_ovf = nullptr;      // list overflow flag per 8x4 pixel block
+    uint32_t *work_ctr = nullptr;     // work counters of the persistent kernels
+    int fwd_grid = 0;                 // resident blocks of k_composite_fwd (all SMs)
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
     float *accr = nullptr;        // and radius, per Gaussian
     // per-pixel lists of added Gaussians (separate allocation)
@@ -174,7 +176,8 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += align_up(sizeof(TabRow) * tab);
     b += align_up(sizeof(double) * 12 * t);              // pose partials
     b += align_up(sizeof(double) * 12);                  // pose copy
-    b += align_up(sizeof(uint32_t) * (t + 1));           // tile overflow flags
+    b += align_up(sizeof(uint32_t) * 8 * t);             // block overflow flags
+    b += align_up(sizeof(uint32_t) * 4);                 // work counters
     b += align_up(sizeof(float4) * g) + align_up(sizeof(float) * g);   // gradient accumulators
     return b;
 }
@@ -226,7 +229,8 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->tab = reinterpret_cast<TabRow *>(take(sizeof(TabRow) * tab));
     c->pose_partials = reinterpret_cast<double *>(take(sizeof(double) * 12 * t));
     c->pose_copy = reinterpret_cast<double *>(take(sizeof(double) * 12));
-    c->tile_ovf = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
+    c->blk_ovf = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 8 * t));
+    c->work_ctr = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 4));
     c->acc4 = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
     c->accr = reinterpret_cast<float *>(take(sizeof(float) * g));
     c->cap_g = g;
@@ -272,6 +276,15 @@ vt_status vt_ctx_create(vt_ctx **ctx) {
     vt_ctx *c = new (std::nothrow) vt_ctx();
     if (!c) return fail(VT_ERR_OOM, "vt_ctx_create: out of host memory");
     cudaGetDevice(&c->device);
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_fwd, kBlockPix, 0) !=
+            cudaSuccess ||
+        sms <= 0 || per_sm <= 0) {
+        delete c;
+        return fail(VT_ERR_CUDA, "vt_ctx_create: cannot query the device");
+    }
+    c->fwd_grid = sms * per_sm;
     *ctx = c;
     return VT_OK;
 }
@@ -499,7 +512,8 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     {
         LaunchScope ls(c, K_SCAN, stream);
         k_scan_tiles<<<1, 1024, 0, stream>>>(c->tile_count, n_tiles, c->tile_off, c->tile_cursor,
-                                             c->status, (unsigned long long)c->cap_i);
+                                             c->status, (unsigned long long)c->cap_i,
+                                             c->work_ctr);
     }
     if (total > 0) {
         LaunchScope ls(c, K_EMIT, stream);
@@ -520,10 +534,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     }
     {
         LaunchScope ls(c, K_FWD, stream);
-        k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(
+        k_composite_fwd<<<std::min(c->fwd_grid, n_tiles), kBlockPix, 0, stream>>>(
             cam, c->tile_off, c->sorted, c->geo, c->app, rgb, depth, silhouette, c->pix_last,
-            c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap, c->tile_ovf,
-            c->status);
+            c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap, c->blk_ovf,
+            c->work_ctr, c->status);
     }
     VT_CUDA(cudaGetLastError(), "vt_render launch");
     c->table = T;
@@ -561,14 +575,14 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
     if (c->used_lists) {
         LaunchScope ls(c, K_BWD_LIST, stream);
         k_composite_bwd_list<<<c->n_tiles, kBlockPix, 0, stream>>>(
-            T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->tile_ovf,
+            T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->blk_ovf,
             dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->acc4, c->accr, c->status);
     }
     {   // tiles without complete per-pixel lists (all of them when none were kept)
         LaunchScope ls(c, K_BWD, stream);
         k_composite_bwd<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, dL_drgb,
-            dL_ddepth, dL_dsil, mode, c->pose_partials, c->tile_ovf, c->acc4, c->accr,
+            dL_ddepth, dL_dsil, mode, c->pose_partials, c->blk_ovf, c->acc4, c->accr,
             c->status);
     }
     if (attr && T.n_total > 0) {

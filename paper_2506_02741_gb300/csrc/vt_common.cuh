@@ -1,8 +1,8 @@
 // Shared device definitions of the vtsplat CUDA library (sm_103a).
 //
 // Layout of the workspace a render keeps (all in HBM, library-owned):
-//   geo[g]   : float4 x 2 per Gaussian  {iu, fu, iv, fv} {kx, ky, z, o}
-//   app[g]   : float4 per Gaussian      {c0, c1, c2, r}
+//   geo[g]   : float4 x 2 per Gaussian  {iu, fu, iv, fv} {kx', ky', 1/r, o}
+//   app[g]   : float4 per Gaussian      {c0, c1, c2, z}
 //   info[g]  : uint4 per Gaussian       {tx0 | ty0<<16, tx1 | ty1<<16, zkey bits, n_tiles}
 //   bucket   : uint64 per instance      (zkey << 32 | gid), unsorted per tile
 //   sorted   : uint32 per instance      Gaussian ids, per tile in (zkey, gid) order
@@ -140,17 +140,49 @@ __device__ __forceinline__ ff ff_div(ff a, ff b) {
 __device__ __forceinline__ ff ff_from(float2 v) { return {v.x, v.y}; }
 
 // ---------------------------------------------------------------------------
-// Shared per-pair footprint: q = du^2 kx + dv^2 ky with explicit rounding so
-// that the forward and backward kernels take bit-identical decisions.
-__device__ __forceinline__ float pair_q(int px, int py, const float4 &g0, const float4 &g1,
-                                        float &du, float &dv) {
+// Shared per-pair footprint, in base-2 exponent form: with kx' = -kx log2(e)/2
+// and ky' likewise (kx = (z / (fx r))^2 etc., so q = du^2 kx + dv^2 ky),
+//   t = du^2 kx' + dv^2 ky' = -q log2(e) / 2,   exp(-q/2) = 2^t.
+// A pair is included iff t >= t_min = max(-4.5 log2(e), -log2(255 o)), i.e.
+// q <= 9 and o exp(-q/2) >= 1/255.  Explicit rounding makes the forward and
+// backward kernels take bit-identical decisions.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kTScale = -0.5f * kLog2e;          // t = q * kTScale
+constexpr float kQFromT = -2.0f * 0.69314718055994531f;   // q = t * kQFromT
+
+// The pixel offsets du = (px - iu) - fu, dv = (py - iv) - fv take one
+// rounding each (the integer differences are exact in FP32).
+__device__ __forceinline__ float pair_t(float du, float dv, float kxs, float kys) {
+    return __fmaf_rn(__fmul_rn(du, kxs), du, __fmul_rn(__fmul_rn(dv, kys), dv));
+}
+// Offsets and exponent of pixel (px, py) for a Gaussian record g0/g1.
+__device__ __forceinline__ float pair_t_at(int px, int py, const float4 &g0, const float4 &g1,
+                                           float &du, float &dv) {
     du = __fsub_rn((float)(px - __float_as_int(g0.x)), g0.y);
     dv = __fsub_rn((float)(py - __float_as_int(g0.z)), g0.w);
-    float a = __fmul_rn(__fmul_rn(du, du), g1.x);
-    return __fmaf_rn(__fmul_rn(dv, dv), g1.y, a);
+    return pair_t(du, dv, g1.x, g1.y);
 }
 
-__device__ __forceinline__ float pair_gauss(float q) { return __expf(__fmul_rn(-0.5f, q)); }
+// 2^t with the hardware approximation (t in [-6.5, 0]: no subnormals).
+__device__ __forceinline__ float exp2_approx(float t) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(t));
+    return y;
+}
+
+// log2(x) with the hardware approximation (x >= 1 here).
+__device__ __forceinline__ float log2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Inclusion threshold on t for opacity o (both cuts: q <= 9 and
+// o exp(-q/2) >= 1/255); every kernel derives it with this function, so the
+// decisions agree bit for bit.
+__device__ __forceinline__ float t_min_of(float o) {
+    return fmaxf(kQMax * kTScale, -log2_approx(__fmul_rn(255.f, o)));
+}
 
 // Attribute loads in either storage precision.
 __device__ __forceinline__ float ld_attr(const void *p, int prec, int64_t i) {
@@ -174,7 +206,8 @@ __global__ void k_setup(SecTable T, Camera cam, const double *pose12, ViewXf *vi
 __global__ void k_preprocess(SecTable T, Camera cam, const ViewXf *views, const TabRow *tab,
                              float4 *geo, float4 *app, uint4 *info, uint32_t *tile_count);
 __global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *tile_off,
-                             uint32_t *tile_cursor, Status *st, unsigned long long cap);
+                             uint32_t *tile_cursor, Status *st, unsigned long long cap,
+                             uint32_t *work_ctr);
 __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
                        unsigned long long *bucket, const Status *st);
 __global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,
@@ -183,8 +216,8 @@ __global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned lon
 __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
                                 const float4 *geo, const float4 *app, float *rgb, float *depth,
                                 float *sil, uint32_t *pix_last, uint32_t *pix_nadd,
-                                float *pix_T, uint2 *plist, int plist_cap, uint32_t *tile_ovf,
-                                const Status *st);
+                                float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
+                                uint32_t *work_ctr, const Status *st);
 __global__ void k_composite_bwd(SecTable T, Camera cam, const uint32_t *tile_off,
                                 const uint32_t *sorted, const float4 *geo, const float4 *app,
                                 const uint32_t *pix_last, const float *pix_T,
@@ -194,7 +227,7 @@ __global__ void k_composite_bwd(SecTable T, Camera cam, const uint32_t *tile_off
 __global__ void k_composite_bwd_list(SecTable T, Camera cam, const float4 *geo,
                                      const float4 *app, const uint32_t *pix_nadd,
                                      const float *pix_T, const uint2 *plist, int plist_cap,
-                                     const uint32_t *tile_ovf, const float *g_rgb,
+                                     const uint32_t *blk_ovf, const float *g_rgb,
                                      const float *g_depth, const float *g_sil, int mode,
                                      double *pose_partials, float4 *acc4, float *accr,
                                      const Status *st);

@@ -1,144 +1,174 @@
-// Per-tile front-to-back compositing (forward) and its back-to-front replay
-// (backward).  One block of 256 threads per 16x16 tile, one thread per pixel;
-// warp w owns the 8x4 pixel block ((w & 1) * 8, (w >> 1) * 4) of the tile.
-// Gaussians of the tile's depth-sorted list are staged in shared memory in
-// batches of 256; before evaluating a Gaussian for its 32 pixels a warp
-// checks, one Gaussian per lane, whether the Gaussian's 3-sigma disc touches
-// its 8x4 block, and only visits the ones that do.  sm_103a; no tensor cores.
+// Front-to-back compositing (forward) and its back-to-front replay
+// (backward).  The image is cut into 16x16 tiles and each tile into eight 8x4
+// pixel blocks, one warp and one pixel per lane each; block w of a tile has
+// its origin at ((w & 1) * 8, (w >> 1) * 4).  A warp walks the depth-sorted
+// list of its tile; before evaluating a Gaussian for its 32 pixels it checks,
+// one Gaussian per lane, whether any pixel of its block can pass the
+// inclusion test, and only visits the ones that can.  sm_103a; no tensor
+// cores (the per-pair work is a handful of scalar operations).
+//
+// Every pair's exponent t, inclusion decision and alpha come from the same
+// FP32 operations (pair_t_at) in the forward and both backward kernels.
 #include "vt_common.cuh"
 
 namespace vt {
 
 constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kWarps = kBlockPix / 32;
 
-// Conservative test: does the disc q <= 9 of a Gaussian (centre iu + fu,
-// iv + fv, coefficients kx, ky) touch the pixel rectangle [x0,x1] x [y0,y1]?
-// The distance is shrunk by 1e-3 px so that rounding of the float centre
-// never drops a pixel the exact per-pixel test would include.
-__device__ __forceinline__ bool disc_touches(const float4 &g0, const float4 &g1, float x0, float x1,
-                                             float y0, float y1) {
-    const float uc = (float)__float_as_int(g0.x) + g0.y;
-    const float vc = (float)__float_as_int(g0.z) + g0.w;
-    const float dx = fmaxf(fmaxf(x0 - uc, uc - x1) - 1e-3f, 0.f);
-    const float dy = fmaxf(fmaxf(y0 - vc, vc - y1) - 1e-3f, 0.f);
-    return dx * dx * g1.x + dy * dy * g1.y <= kQMax;
+// Conservative test: can a pixel of the block (columns 0..lxmax and rows
+// 0..lymax from the block origin) pass t >= t_min for a Gaussian at offsets
+// du0 ~ bx0 - uc, dv0 ~ by0 - vc from the origin?  The nearest pixel is taken
+// 1e-3 px nearer and the threshold loosened by 1e-4 relative so that rounding
+// never drops a pixel the per-pixel test includes.
+__device__ __forceinline__ bool block_touches(float du0, float dv0, float kxs, float kys,
+                                              float tmin, float lxmax, float lymax) {
+    const float dx = fmaxf(fmaxf(du0, -du0 - lxmax) - 1e-3f, 0.f);
+    const float dy = fmaxf(fmaxf(dv0, -dv0 - lymax) - 1e-3f, 0.f);
+    return dx * dx * kxs + dy * dy * kys >= tmin * 1.0001f - 1e-6f;
 }
 
-// Forward.  Each warp streams through its tile's depth-sorted list on its
-// own (no block barriers): the 32 lanes load the next 32 list entries and
-// their records into registers one round ahead, test them against the warp's
-// 8x4 pixel block, stage the round in warp-private shared memory and walk the
-// relevant ones in order.  A warp leaves as soon as all its pixels have
+// OR of the list-overflow flags of the eight blocks of a tile.
+__device__ __forceinline__ bool tile_flagged(const uint32_t *blk_ovf, int tile) {
+    const uint4 *f = reinterpret_cast<const uint4 *>(blk_ovf + (size_t)tile * kWarps);
+    const uint4 a = f[0], b = f[1];
+    return (a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w) != 0u;
+}
+
+// Forward.  Persistent: every warp takes 8x4 pixel blocks from a work counter
+// (zeroed by k_scan_tiles) until none are left, so that a warp whose pixels
+// saturate early moves on instead of waiting for the rest of its tile.  Per
+// block the warp streams through the tile's list in rounds of 32 entries: the
+// lanes load the next round's records into registers while the current round
+// is composited, test them against the block, stage the round in
+// warp-private shared memory ({bx0 - iu, by0 - iv, fu, fv}, {kx', ky', t_min,
+// o}, {c, z}, id) and walk the relevant ones in order.  Adding the lane's
+// column lx to bx0 - iu gives px - iu exactly, so du = (px - iu) - fu is
+// bit-identical to pair_t_at.  The warp leaves the block once all its pixels have
 // terminated.  With plist != NULL every pixel also records the id of every
 // Gaussian it added together with the transmittance in front of it (up to
-// plist_cap entries, pixel-major), which the backward
-// replays instead of the tile list; tiles where a pixel added more are
-// flagged in tile_ovf.
+// plist_cap entries, pixel-major), which the backward replays instead of the
+// tile list; blk_ovf[item] flags blocks where a pixel added more (always 1
+// without lists).
 __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, float *rgb, float *depth, float *sil, uint32_t *pix_last,
-    uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap, uint32_t *tile_ovf,
-    const Status *st) {
-    __shared__ float4 s_g0[kBlockPix / 32][32], s_g1[kBlockPix / 32][32], s_a[kBlockPix / 32][32];
-    __shared__ uint32_t s_gid[kBlockPix / 32][32];
+    uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
+    uint32_t *work_ctr, const Status *st) {
+    __shared__ float4 s_f[kWarps][32], s_k[kWarps][32], s_c[kWarps][32];
+    __shared__ uint32_t s_gid[kWarps][32];
     if (st->flags) return;
-    const int tile = blockIdx.x;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
-    const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
-    const bool inside = px < cam.W && py < cam.H;
-    const float rx0 = (float)bx0, rx1 = (float)min(bx0 + 7, cam.W - 1);
-    const float ry0 = (float)by0, ry1 = (float)min(by0 + 3, cam.H - 1);
-    const uint32_t start = tile_off[tile];
-    const int n = (int)(tile_off[tile + 1] - start);
-    const size_t p = inside ? (size_t)py * cam.W + px : 0;
-    uint2 *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
-
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
-    uint32_t last = 0, nadd = 0;
-    bool done = !inside;
-    float4 (&g0s)[32] = s_g0[warp];
-    float4 (&g1s)[32] = s_g1[warp];
-    float4 (&as)[32] = s_a[warp];
+    const int lx = lane & 7, ly = lane >> 3;
+    const float lxf = (float)lx, lyf = (float)ly;
+    const int n_items = cam.tiles_x * cam.tiles_y * kWarps;
+    float4 (&fs)[32] = s_f[warp];
+    float4 (&ks)[32] = s_k[warp];
+    float4 (&cs)[32] = s_c[warp];
     uint32_t (&ids)[32] = s_gid[warp];
+    const size_t HW = (size_t)cam.W * cam.H;
 
-    uint32_t gid_n = 0;
-    float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
-    if (!__all_sync(kFullMask, done) && lane < n) {
-        gid_n = sorted[start + lane];
-        g0n = geo[2 * (size_t)gid_n];
-        g1n = geo[2 * (size_t)gid_n + 1];
-        an = app[gid_n];
-    }
-    for (int base = 0; base < n; base += 32) {
-        if (__all_sync(kFullMask, done)) break;
-        const uint32_t gid = gid_n;
-        const float4 g0 = g0n, g1 = g1n, a = an;
-        const bool valid = base + lane < n;
-        const int inext = base + 32 + lane;
-        if (inext < n) {   // prefetch the next round while this one is composited
-            gid_n = sorted[start + inext];
-            g0n = geo[2 * (size_t)gid_n];
-            g1n = geo[2 * (size_t)gid_n + 1];
-            an = app[gid_n];
-        }
-        const bool rel = valid && disc_touches(g0, g1, rx0, rx1, ry0, ry1);
-        unsigned mask = __ballot_sync(kFullMask, rel);
-        if (!mask) continue;
-        __syncwarp();
-        g0s[lane] = g0;
-        g1s[lane] = g1;
-        as[lane] = a;
-        ids[lane] = gid;
-        __syncwarp();
-        while (mask) {
-            const int j = __ffs(mask) - 1;
-            mask &= mask - 1;
-            if (done) continue;
-            const float4 h0 = g0s[j], h1 = g1s[j];
-            float du, dv;
-            const float q = pair_q(px, py, h0, h1, du, dv);
-            if (!(q <= kQMax)) continue;
-            const float ah = __fmul_rn(h1.w, pair_gauss(q));
-            if (!(ah >= kAlphaMin)) continue;
-            const float al = fminf(ah, kAlphaClamp);
-            const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
-            if (Tn < kTMin) {
-                done = true;
-                continue;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(work_ctr, 1u);
+        item = __shfl_sync(kFullMask, item, 0);
+        if (item >= n_items) break;
+        const int tile = item / kWarps, sub = item % kWarps;
+        const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+        const int bx0 = tx * kTile + (sub & 1) * 8, by0 = ty * kTile + (sub >> 1) * 4;
+        const int px = bx0 + lx, py = by0 + ly;
+        const bool inside = px < cam.W && py < cam.H;
+        const float lxmax = (float)min(7, cam.W - 1 - bx0);
+        const float lymax = (float)min(3, cam.H - 1 - by0);
+        const uint32_t start = tile_off[tile];
+        const int n = (int)(tile_off[tile + 1] - start);
+        const size_t p = inside ? (size_t)py * cam.W + px : 0;
+        uint2 *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
+        const uint32_t cap = mylist ? (uint32_t)plist_cap : 0u;
+
+        float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
+        uint32_t last = 0, nadd = 0;
+        bool done = !inside;
+        // Two-stage prefetch: the ids of round r + 2 and the records of round
+        // r + 1 are in flight while round r is composited, so a gather never
+        // waits on the id load in front of it.
+        uint32_t gid_n = 0, gid_nn = 0;
+        float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
+        if (!__all_sync(kFullMask, done)) {
+            if (lane < n) {
+                gid_n = sorted[start + lane];
+                g0n = geo[2 * (size_t)gid_n];
+                g1n = geo[2 * (size_t)gid_n + 1];
+                an = app[gid_n];
             }
-            const float w = __fmul_rn(al, T);
-            const float T_prev = T;
-            const float4 c = as[j];
-            c0 = __fmaf_rn(w, c.x, c0);
-            c1 = __fmaf_rn(w, c.y, c1);
-            c2 = __fmaf_rn(w, c.z, c2);
-            dd = __fmaf_rn(w, h1.z, dd);
-            ss = __fadd_rn(ss, w);
-            T = Tn;
-            last = (uint32_t)(base + j) + 1u;
-            if (mylist && nadd < (uint32_t)plist_cap)
-                mylist[nadd] = make_uint2(ids[j], __float_as_uint(T_prev));
-            ++nadd;
+            if (32 + lane < n) gid_nn = sorted[start + 32 + lane];
         }
-    }
-    if (inside) {
-        const size_t HW = (size_t)cam.W * cam.H;
-        if (rgb) {
-            rgb[p] = c0;
-            rgb[HW + p] = c1;
-            rgb[2 * HW + p] = c2;
+        for (int base = 0; base < n; base += 32) {
+            if (__all_sync(kFullMask, done)) break;
+            const uint32_t gid = gid_n;
+            const float4 g0 = g0n, g1 = g1n, a = an;
+            const bool valid = base + lane < n;
+            if (base + 32 + lane < n) {   // records of the next round
+                gid_n = gid_nn;
+                g0n = geo[2 * (size_t)gid_n];
+                g1n = geo[2 * (size_t)gid_n + 1];
+                an = app[gid_n];
+            }
+            if (base + 64 + lane < n) gid_nn = sorted[start + base + 64 + lane];
+            const float ku = (float)(bx0 - __float_as_int(g0.x));
+            const float kv = (float)(by0 - __float_as_int(g0.z));
+            const float tmin = t_min_of(g1.w);
+            const bool rel = valid && block_touches(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmax,
+                                                    lymax);
+            unsigned mask = __ballot_sync(kFullMask, rel);
+            if (!mask) continue;
+            __syncwarp();
+            fs[lane] = make_float4(ku, kv, g0.y, g0.w);
+            ks[lane] = make_float4(g1.x, g1.y, tmin, g1.w);
+            cs[lane] = a;
+            ids[lane] = gid;
+            __syncwarp();
+            while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (done) continue;
+                const float4 f = fs[j], k = ks[j];
+                const float t = pair_t(__fsub_rn(__fadd_rn(f.x, lxf), f.z),
+                                       __fsub_rn(__fadd_rn(f.y, lyf), f.w), k.x, k.y);
+                if (!(t >= k.z)) continue;
+                const float al = fminf(__fmul_rn(k.w, exp2_approx(t)), kAlphaClamp);
+                const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
+                if (Tn < kTMin) {
+                    done = true;
+                    continue;
+                }
+                const float w = __fmul_rn(al, T);
+                const float4 c = cs[j];
+                c0 = __fmaf_rn(w, c.x, c0);
+                c1 = __fmaf_rn(w, c.y, c1);
+                c2 = __fmaf_rn(w, c.z, c2);
+                dd = __fmaf_rn(w, c.w, dd);
+                ss = __fadd_rn(ss, w);
+                if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
+                T = Tn;
+                last = (uint32_t)(base + j) + 1u;
+                ++nadd;
+            }
         }
-        if (depth) depth[p] = dd;
-        if (sil) sil[p] = ss;
-        pix_last[p] = last;
-        pix_nadd[p] = nadd;
-        pix_T[p] = T;
-    }
-    if (tile_ovf) {
-        const int ovf = __syncthreads_or(plist != nullptr && nadd > (uint32_t)plist_cap);
-        if (threadIdx.x == 0) tile_ovf[tile] = plist ? (uint32_t)ovf : 1u;
+        if (inside) {
+            if (rgb) {
+                rgb[p] = c0;
+                rgb[HW + p] = c1;
+                rgb[2 * HW + p] = c2;
+            }
+            if (depth) depth[p] = dd;
+            if (sil) sil[p] = ss;
+            pix_last[p] = last;
+            pix_nadd[p] = nadd;
+            pix_T[p] = T;
+        }
+        const bool ovf = __any_sync(kFullMask, nadd > cap);
+        if (lane == 0) blk_ovf[item] = plist ? (uint32_t)ovf : 1u;
     }
 }
 
@@ -207,22 +237,25 @@ __device__ __forceinline__ void bwd_pixel_init(BwdPixel &P, float Tfin, float gC
     P.have_ref = false;
 }
 
-// One added Gaussian of the pixel, visited back to front.  Returns its
-// colour / opacity / radius gradient terms and adds its pose terms to acc.
-// Ti_fwd >= 0 is the forward's transmittance in front of this Gaussian
-// (recorded in the per-pixel list); otherwise it is recovered by division,
-// which accumulates the rounding of every Gaussian behind.
+// One added Gaussian of the pixel, visited back to front (g0, g1: footprint
+// record with 1/r in g1.z, a: colour and depth z, t: exponent of pair_t,
+// G = 2^t, ah = o G).  Returns its colour / opacity / radius gradient terms
+// and adds its pose terms to acc.  Ti_fwd >= 0 is the forward's transmittance in front
+// of this Gaussian (recorded in the per-pixel list); otherwise it is
+// recovered by division, which accumulates the rounding of every Gaussian
+// behind.
 __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const float4 &g1,
-                                         const float4 &a, float q, float du, float dv, float G,
-                                         float ah, const Camera &cam, bool want_pose,
-                                         PoseAcc &acc, float &dc0, float &dc1, float &dc2,
-                                         float &dop, float &drd, float Ti_fwd = -1.f) {
+                                         const float4 &a, float t, float du, float dv, float G,
+                                         float ah, const Camera &cam, bool want_pose, PoseAcc &acc,
+                                         float &dc0, float &dc1, float &dc2, float &dop,
+                                         float &drd, float Ti_fwd = -1.f) {
     const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
     const float al = fminf(ah, kAlphaClamp);
     const float om = 1.f - al;
     const float Ti = Ti_fwd >= 0.f ? Ti_fwd : P.T / om;
     const float w = al * Ti;
-    const float z = g1.z, r = a.w;
+    const float z = a.w, q = t * kQFromT;
+    const float ir = g1.z, ir2 = ir * ir;
     if (!P.have_ref) {
         P.have_ref = true;
         P.cr0 = a.x;
@@ -245,9 +278,8 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
         dop = dal * G;
         dq = -0.5f * ah * dal;
     }
-    drd = dq * (-2.f * q / r);
+    drd = dq * (-2.f * q * ir);
     if (want_pose) {
-        const float ir2 = 1.f / (r * r);
         const float ex = z * du * ifx, ey = z * dv * ify;
         const float gx = dq * (-2.f * ex * ir2);
         const float gy = dq * (-2.f * ey * ir2);
@@ -328,23 +360,25 @@ __device__ __forceinline__ void write_pose_partial(const PoseAcc &acc, double (*
 // only tiles with tile_mask[t] != 0; NULL = all tiles).
 __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     SecTable Tab, Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
-    const float4 *app, const uint32_t *pix_last, const float *pix_T, const float *g_rgb,
-    const float *g_depth, const float *g_sil, int mode, double *pose_partials,
-    const uint32_t *tile_mask, float4 *acc4, float *accr, const Status *st) {
+    const float4 *app, const uint32_t *pix_last, const float *pix_T,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, const uint32_t *tile_mask, float4 *acc4, float *accr,
+    const Status *st) {
     __shared__ float4 s_g0[kBatch], s_g1[kBatch], s_a[kBatch];
+    __shared__ float s_tmin[kBatch];
     __shared__ uint32_t s_gid[kBatch];
     __shared__ double s_pose[kBlockPix / 32][12];
     __shared__ uint32_t s_last;
     if (st->flags) return;
     const int tile = blockIdx.x;
-    if (tile_mask && !tile_mask[tile]) return;
+    if (tile_mask && !tile_flagged(tile_mask, tile)) return;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
     const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
     const bool inside = px < cam.W && py < cam.H;
-    const float rx0 = (float)bx0, rx1 = (float)min(bx0 + 7, cam.W - 1);
-    const float ry0 = (float)by0, ry1 = (float)min(by0 + 3, cam.H - 1);
+    const float lxmax = (float)min(7, cam.W - 1 - bx0);
+    const float lymax = (float)min(3, cam.H - 1 - by0);
     const uint32_t start = tile_off[tile];
     const bool want_attr = (mode & VT_GRAD_ATTR) != 0, want_pose = (mode & VT_GRAD_POSE) != 0;
 
@@ -382,7 +416,9 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
             if ((int)threadIdx.x < nb) {
                 const uint32_t g = sorted[start + b0 + threadIdx.x];
                 s_g0[threadIdx.x] = geo[2 * (size_t)g];
-                s_g1[threadIdx.x] = geo[2 * (size_t)g + 1];
+                const float4 h1 = geo[2 * (size_t)g + 1];
+                s_g1[threadIdx.x] = h1;
+                s_tmin[threadIdx.x] = t_min_of(h1.w);
                 s_a[threadIdx.x] = app[g];
                 s_gid[threadIdx.x] = g;
             }
@@ -391,8 +427,12 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                 for (int j0 = ((nb - 1) >> 5) << 5; j0 >= 0; j0 -= 32) {
                     const int jj = j0 + lane;
                     bool rel = false;
-                    if (jj < nb && (uint32_t)(b0 + jj) < wl)
-                        rel = disc_touches(s_g0[jj], s_g1[jj], rx0, rx1, ry0, ry1);
+                    if (jj < nb && (uint32_t)(b0 + jj) < wl) {
+                        const float4 h0 = s_g0[jj], h1 = s_g1[jj];
+                        rel = block_touches((float)(bx0 - __float_as_int(h0.x)) - h0.y,
+                                            (float)(by0 - __float_as_int(h0.z)) - h0.w, h1.x,
+                                            h1.y, s_tmin[jj], lxmax, lymax);
+                    }
                     unsigned mask = __ballot_sync(kFullMask, rel);
                     while (mask) {
                         const int bit = 31 - __clz(mask);
@@ -403,15 +443,13 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                         if ((uint32_t)(b0 + j) < my_last) {
                             const float4 g0 = s_g0[j], g1 = s_g1[j];
                             float du, dv;
-                            const float q = pair_q(px, py, g0, g1, du, dv);
-                            if (q <= kQMax) {
-                                const float G = pair_gauss(q);
+                            const float t = pair_t_at(px, py, g0, g1, du, dv);
+                            if (t >= s_tmin[j]) {
+                                const float G = exp2_approx(t);
                                 const float ah = __fmul_rn(g1.w, G);
-                                if (ah >= kAlphaMin) {
-                                    contrib = true;
-                                    bwd_pair(P, g0, g1, s_a[j], q, du, dv, G, ah, cam, want_pose,
-                                             acc, dc0, dc1, dc2, dop, drd);
-                                }
+                                contrib = true;
+                                bwd_pair(P, g0, g1, s_a[j], t, du, dv, G, ah, cam, want_pose,
+                                         acc, dc0, dc1, dc2, dop, drd);
                             }
                         }
                         if (want_attr && __any_sync(kFullMask, contrib)) {
@@ -434,17 +472,18 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
 
 // Per-pixel list replay: every lane walks the ids its pixel added, recorded
 // by the forward, from the last to the first, loading each record one step
-// ahead.  No filtering and no block barriers in the walk; tiles flagged in
-// tile_ovf (a pixel exceeded the list capacity) are left to k_composite_bwd.
+// ahead.  No filtering and no block barriers in the walk; tiles with a block
+// flagged in blk_ovf (a pixel exceeded the list capacity) are left to
+// k_composite_bwd.
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
-    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
-    const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *tile_ovf,
+    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
+    const uint32_t *blk_ovf,
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
     double *pose_partials, float4 *acc4, float *accr, const Status *st) {
     __shared__ double s_pose[kBlockPix / 32][12];
     if (st->flags) return;
     const int tile = blockIdx.x;
-    if (tile_ovf[tile]) return;
+    if (tile_flagged(blk_ovf, tile)) return;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
@@ -471,7 +510,9 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc.a[i] = 0.f;
     const uint2 *mylist = plist + p * (size_t)plist_cap;
-    uint2 e_n = make_uint2(0u, 0u);
+    // Two-stage prefetch: the list entry two steps ahead and the records one
+    // step ahead are in flight while the current Gaussian is processed.
+    uint2 e_n = make_uint2(0u, 0u), e_nn = e_n;
     float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
     if (n > 0) {
         e_n = mylist[n - 1];
@@ -479,22 +520,24 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
         g1n = geo[2 * (size_t)e_n.x + 1];
         an = app[e_n.x];
     }
+    if (n > 1) e_nn = mylist[n - 2];
     for (int k = n - 1; k >= 0; --k) {
         const uint32_t g = e_n.x;
         const float Ti = __uint_as_float(e_n.y);
         const float4 g0 = g0n, g1 = g1n, a = an;
-        if (k > 0) {   // prefetch the next (nearer) Gaussian
-            e_n = mylist[k - 1];
+        if (k > 0) {   // records of the next (nearer) Gaussian
+            e_n = e_nn;
             g0n = geo[2 * (size_t)e_n.x];
             g1n = geo[2 * (size_t)e_n.x + 1];
             an = app[e_n.x];
         }
+        if (k > 1) e_nn = mylist[k - 2];
         float du, dv;
-        const float q = pair_q(px, py, g0, g1, du, dv);
-        const float G = pair_gauss(q);
+        const float t = pair_t_at(px, py, g0, g1, du, dv);
+        const float G = exp2_approx(t);
         const float ah = __fmul_rn(g1.w, G);
         float dc0, dc1, dc2, dop, drd;
-        bwd_pair(P, g0, g1, a, q, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd, Ti);
+        bwd_pair(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd, Ti);
         if (want_attr) add_attr_grads(Tab, g, dc0, dc1, dc2, dop, drd, acc4, accr);
     }
     if (want_pose) write_pose_partial(acc, s_pose, pose_partials, tile);

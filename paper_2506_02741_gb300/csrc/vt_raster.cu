@@ -119,6 +119,8 @@ __device__ __forceinline__ void for_each_tile(uint32_t r0, uint32_t r1, uint32_t
 // in float-float, derives the footprint coefficients kx = (z / (fx r))^2,
 // ky = (z / (fy r))^2 (q = du^2 kx + dv^2 ky in pixels) and the conservative
 // pixel box of the disc q <= min(9, 2 ln(255 o)), and counts its tiles.
+// The records keep kx, ky scaled to the base-2 exponent t = -q log2(e)/2
+// (see pair_t) and 1/r for the backward.
 __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, const ViewXf *views,
                                                     const TabRow *tab, float4 *geo, float4 *app,
                                                     uint4 *info, uint32_t *tile_count) {
@@ -191,11 +193,12 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
                     const float fu = __fadd_rn(__fsub_rn(uc.hi, (float)iu), uc.lo);
                     const float fv = __fadd_rn(__fsub_rn(vc.hi, (float)iv), vc.lo);
                     geo[2 * gid] = make_float4(__int_as_float(iu), fu, __int_as_float(iv), fv);
-                    geo[2 * gid + 1] = make_float4(kx, ky, z, o);
+                    geo[2 * gid + 1] = make_float4(__fmul_rn(kx, kTScale), __fmul_rn(ky, kTScale),
+                                                   __frcp_rn(r), o);
                     const float c0 = ld_attr(S.colour, S.prec, 3 * li + 0);
                     const float c1 = ld_attr(S.colour, S.prec, 3 * li + 1);
                     const float c2 = ld_attr(S.colour, S.prec, 3 * li + 2);
-                    app[gid] = make_float4(c0, c1, c2, r);
+                    app[gid] = make_float4(c0, c1, c2, z);
                 }
             }
         }
@@ -212,11 +215,15 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
 // Flags a capacity shortage instead of letting later kernels overrun.
 __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count, int n_tiles,
                                                      uint32_t *tile_off, uint32_t *tile_cursor,
-                                                     Status *st, unsigned long long cap) {
+                                                     Status *st, unsigned long long cap,
+                                                     uint32_t *work_ctr) {
     __shared__ unsigned long long warp_sums[32];
     __shared__ unsigned long long carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0;
+    if (tid == 0) {
+        carry = 0;
+        work_ctr[0] = 0u;   // work counter of the persistent compositor
+    }
     __syncthreads();
     for (int base = 0; base < n_tiles; base += 1024) {
         const int i = base + tid;

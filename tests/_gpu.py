@@ -61,9 +61,19 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def assert_grad_close(g, ref, tol=1e-4, name="", abs_ref=None):
+# Bound on the rounding noise of a pose-gradient component summed per pixel
+# in FP32 and across pixels in FP64, in units of the oracle's noise scale
+# sqrt(sum_p n_p m_p^2): per pixel, each of the n_p terms and each running
+# sum rounds with relative error <= 2^-24 (a few roundings per term), and the
+# pixels' errors are independent, so the total stays within a few units of
+# 2^-24 x the scale; 8 leaves room for the tail.
+POSE_NOISE = 8.0 * 2.0 ** -24
+
+
+def assert_grad_close(g, ref, tol=1e-4, name="", abs_ref=None, noise=None):
     """Per-tensor relative L2 <= tol, and per element
-    |g - ref| <= tol * max(|ref|, 1e-3 max|ref|) + tol * sum|terms|.
+    |g - ref| <= tol * max(|ref|, 1e-3 max|ref|) + tol * sum|terms|
+                 + POSE_NOISE * noise.
 
     The second term applies the same relative tolerance to the componentwise
     magnitude of each pixel's term (the oracle reports, per element, the sum
@@ -79,5 +89,7 @@ def assert_grad_close(g, ref, tol=1e-4, name="", abs_ref=None):
     bound = tol * np.maximum(np.abs(ref), floor)
     if abs_ref is not None:
         bound = bound + tol * np.asarray(abs_ref, np.float64).ravel()
+    if noise is not None:
+        bound = bound + POSE_NOISE * np.asarray(noise, np.float64).ravel()
     bad = np.abs(g - ref) > bound
     assert not bad.any(), (name, int(bad.sum()), float(np.max(np.abs(g - ref) / bound)))

@@ -171,8 +171,9 @@ def test_backward_parity(dev, case):
                         abs_ref=want["abs_opacity"][0])
     G.assert_grad_close(grads[0][2].cpu().numpy(), want["radius"][0], name="radius",
                         abs_ref=want["abs_radius"][0])
-    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist")
-    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat")
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist",
+                        noise=want["twist_noise"])
+    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", noise=want["mat_noise"])
 
 
 def test_pose_only_and_attr_only_modes_agree(dev):
@@ -358,8 +359,9 @@ def test_backward_paths_agree(dev, cap):
     for k, name in enumerate(("colour", "opacity", "radius")):
         G.assert_grad_close(grads[0][k].cpu().numpy(), want[name][0], name=name,
                             abs_ref=want["abs_" + name][0])
-    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist")
-    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat")
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist",
+                        noise=want["twist_noise"])
+    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", noise=want["mat_noise"])
 
 
 def test_budget_disables_lists(dev):

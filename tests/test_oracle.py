@@ -282,6 +282,25 @@ def test_pose_gradient_finite_differences():
         np.testing.assert_allclose(an, fd, rtol=2e-6, atol=2e-6 * scale, err_msg=kind)
 
 
+def test_pose_noise_scale():
+    """The pose noise scale sqrt(sum_p n_p m_p^2) bounds each component from
+    above by Cauchy-Schwarz (|g_i| <= sum_p m_p <= sqrt(P) x scale), is zero
+    without upstream gradients and scales linearly with them."""
+    sec, target, K = h.tiny_section()
+    args = (K.astuple(), K.W, K.H)
+    gR, gD, gS = _upstream((K.H, K.W), 23)
+    g = oracle.backward(sec, target, *args, g_rgb=gR, g_depth=gD, g_sil=gS)
+    P = K.W * K.H
+    for kind in ("twist", "mat"):
+        nz = g[kind + "_noise"]
+        assert np.all(nz > 0)
+        assert np.all(np.abs(g[kind]) <= np.sqrt(P) * nz * (1 + 1e-12))
+    g2 = oracle.backward(sec, target, *args, g_rgb=2 * gR, g_depth=2 * gD, g_sil=2 * gS)
+    np.testing.assert_allclose(g2["twist_noise"], 2 * g["twist_noise"], rtol=1e-12)
+    z = oracle.backward(sec, target, *args, g_rgb=0 * gR)
+    assert np.all(z["twist_noise"] == 0) and np.all(z["mat_noise"] == 0)
+
+
 def test_attribute_gradient_finite_differences():
     sec, target, K = h.tiny_section()
     args = (K.astuple(), K.W, K.H)
