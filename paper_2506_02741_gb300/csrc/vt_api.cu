@@ -92,8 +92,6 @@ struct vt_ctx {
     TabRow *tab = nullptr;
     double *pose_partials = nullptr, *pose_copy = nullptr;
     uint32_t *blk_ovf = nullptr;      // list overflow flag per 8x4 pixel block
-    uint32_t *work_ctr = nullptr;     // work counters of the persistent kernels
-    int fwd_grid = 0;                 // resident blocks of k_composite_fwd (all SMs)
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
     float *accr = nullptr;        // and radius, per Gaussian
     // per-pixel lists of added Gaussians (separate allocation)
@@ -177,7 +175,6 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += align_up(sizeof(double) * 12 * t);              // pose partials
     b += align_up(sizeof(double) * 12);                  // pose copy
     b += align_up(sizeof(uint32_t) * 8 * t);             // block overflow flags
-    b += align_up(sizeof(uint32_t) * 4);                 // work counters
     b += align_up(sizeof(float4) * g) + align_up(sizeof(float) * g);   // gradient accumulators
     return b;
 }
@@ -230,7 +227,6 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->pose_partials = reinterpret_cast<double *>(take(sizeof(double) * 12 * t));
     c->pose_copy = reinterpret_cast<double *>(take(sizeof(double) * 12));
     c->blk_ovf = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 8 * t));
-    c->work_ctr = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 4));
     c->acc4 = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
     c->accr = reinterpret_cast<float *>(take(sizeof(float) * g));
     c->cap_g = g;
@@ -276,15 +272,6 @@ vt_status vt_ctx_create(vt_ctx **ctx) {
     vt_ctx *c = new (std::nothrow) vt_ctx();
     if (!c) return fail(VT_ERR_OOM, "vt_ctx_create: out of host memory");
     cudaGetDevice(&c->device);
-    int sms = 0, per_sm = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_fwd, kBlockPix, 0) !=
-            cudaSuccess ||
-        sms <= 0 || per_sm <= 0) {
-        delete c;
-        return fail(VT_ERR_CUDA, "vt_ctx_create: cannot query the device");
-    }
-    c->fwd_grid = sms * per_sm;
     *ctx = c;
     return VT_OK;
 }
@@ -512,8 +499,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     {
         LaunchScope ls(c, K_SCAN, stream);
         k_scan_tiles<<<1, 1024, 0, stream>>>(c->tile_count, n_tiles, c->tile_off, c->tile_cursor,
-                                             c->status, (unsigned long long)c->cap_i,
-                                             c->work_ctr);
+                                             c->status, (unsigned long long)c->cap_i);
     }
     if (total > 0) {
         LaunchScope ls(c, K_EMIT, stream);
@@ -534,10 +520,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     }
     {
         LaunchScope ls(c, K_FWD, stream);
-        k_composite_fwd<<<std::min(c->fwd_grid, n_tiles), kBlockPix, 0, stream>>>(
+        k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(
             cam, c->tile_off, c->sorted, c->geo, c->app, rgb, depth, silhouette, c->pix_last,
             c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap, c->blk_ovf,
-            c->work_ctr, c->status);
+            c->status);
     }
     VT_CUDA(cudaGetLastError(), "vt_render launch");
     c->table = T;

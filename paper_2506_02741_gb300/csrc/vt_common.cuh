@@ -206,8 +206,7 @@ __global__ void k_setup(SecTable T, Camera cam, const double *pose12, ViewXf *vi
 __global__ void k_preprocess(SecTable T, Camera cam, const ViewXf *views, const TabRow *tab,
                              float4 *geo, float4 *app, uint4 *info, uint32_t *tile_count);
 __global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *tile_off,
-                             uint32_t *tile_cursor, Status *st, unsigned long long cap,
-                             uint32_t *work_ctr);
+                             uint32_t *tile_cursor, Status *st, unsigned long long cap);
 __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
                        unsigned long long *bucket, const Status *st);
 __global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,
@@ -217,7 +216,7 @@ __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint
                                 const float4 *geo, const float4 *app, float *rgb, float *depth,
                                 float *sil, uint32_t *pix_last, uint32_t *pix_nadd,
                                 float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
-                                uint32_t *work_ctr, const Status *st);
+                                const Status *st);
 __global__ void k_composite_bwd(SecTable T, Camera cam, const uint32_t *tile_off,
                                 const uint32_t *sorted, const float4 *geo, const float4 *app,
                                 const uint32_t *pix_last, const float *pix_T,

@@ -35,10 +35,12 @@ __device__ __forceinline__ bool tile_flagged(const uint32_t *blk_ovf, int tile) 
     return (a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w) != 0u;
 }
 
-// Forward.  Persistent: every warp takes 8x4 pixel blocks from a work counter
-// (zeroed by k_scan_tiles) until none are left, so that a warp whose pixels
-// saturate early moves on instead of waiting for the rest of its tile.  Per
-// block the warp streams through the tile's list in rounds of 32 entries: the
+// Forward.  One block of eight warps per tile; the warps never synchronise,
+// so a warp whose pixels saturate early retires instead of waiting for the
+// rest of its tile (the eight warps of a tile still share its records in L1:
+// handing pixel blocks to warps from a global work counter, which spreads a
+// tile's blocks over several SMs, measured slower).  Per pixel block the warp
+// streams through the tile's list in rounds of 32 entries: the
 // lanes load the next round's records into registers while the current round
 // is composited, test them against the block, stage the round in
 // warp-private shared memory ({bx0 - iu, by0 - iv, fu, fv}, {kx', ky', t_min,
@@ -54,122 +56,116 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, float *rgb, float *depth, float *sil, uint32_t *pix_last,
     uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
-    uint32_t *work_ctr, const Status *st) {
+    const Status *st) {
     __shared__ float4 s_f[kWarps][32], s_k[kWarps][32], s_c[kWarps][32];
     __shared__ uint32_t s_gid[kWarps][32];
     if (st->flags) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lx = lane & 7, ly = lane >> 3;
     const float lxf = (float)lx, lyf = (float)ly;
-    const int n_items = cam.tiles_x * cam.tiles_y * kWarps;
     float4 (&fs)[32] = s_f[warp];
     float4 (&ks)[32] = s_k[warp];
     float4 (&cs)[32] = s_c[warp];
     uint32_t (&ids)[32] = s_gid[warp];
     const size_t HW = (size_t)cam.W * cam.H;
 
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = (int)atomicAdd(work_ctr, 1u);
-        item = __shfl_sync(kFullMask, item, 0);
-        if (item >= n_items) break;
-        const int tile = item / kWarps, sub = item % kWarps;
-        const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-        const int bx0 = tx * kTile + (sub & 1) * 8, by0 = ty * kTile + (sub >> 1) * 4;
-        const int px = bx0 + lx, py = by0 + ly;
-        const bool inside = px < cam.W && py < cam.H;
-        const float lxmax = (float)min(7, cam.W - 1 - bx0);
-        const float lymax = (float)min(3, cam.H - 1 - by0);
-        const uint32_t start = tile_off[tile];
-        const int n = (int)(tile_off[tile + 1] - start);
-        const size_t p = inside ? (size_t)py * cam.W + px : 0;
-        uint2 *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
-        const uint32_t cap = mylist ? (uint32_t)plist_cap : 0u;
+    const int item = blockIdx.x * kWarps + warp;
+    const int tile = blockIdx.x, sub = warp;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int bx0 = tx * kTile + (sub & 1) * 8, by0 = ty * kTile + (sub >> 1) * 4;
+    const int px = bx0 + lx, py = by0 + ly;
+    const bool inside = px < cam.W && py < cam.H;
+    const float lxmax = (float)min(7, cam.W - 1 - bx0);
+    const float lymax = (float)min(3, cam.H - 1 - by0);
+    const uint32_t start = tile_off[tile];
+    const int n = (int)(tile_off[tile + 1] - start);
+    const size_t p = inside ? (size_t)py * cam.W + px : 0;
+    uint2 *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
+    const uint32_t cap = mylist ? (uint32_t)plist_cap : 0u;
 
-        float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
-        uint32_t last = 0, nadd = 0;
-        bool done = !inside;
-        // Two-stage prefetch: the ids of round r + 2 and the records of round
-        // r + 1 are in flight while round r is composited, so a gather never
-        // waits on the id load in front of it.
-        uint32_t gid_n = 0, gid_nn = 0;
-        float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
-        if (!__all_sync(kFullMask, done)) {
-            if (lane < n) {
-                gid_n = sorted[start + lane];
-                g0n = geo[2 * (size_t)gid_n];
-                g1n = geo[2 * (size_t)gid_n + 1];
-                an = app[gid_n];
-            }
-            if (32 + lane < n) gid_nn = sorted[start + 32 + lane];
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
+    uint32_t last = 0, nadd = 0;
+    bool done = !inside;
+    // Two-stage prefetch: the ids of round r + 2 and the records of round
+    // r + 1 are in flight while round r is composited, so a gather never
+    // waits on the id load in front of it.
+    uint32_t gid_n = 0, gid_nn = 0;
+    float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
+    if (!__all_sync(kFullMask, done)) {
+        if (lane < n) {
+            gid_n = sorted[start + lane];
+            g0n = geo[2 * (size_t)gid_n];
+            g1n = geo[2 * (size_t)gid_n + 1];
+            an = app[gid_n];
         }
-        for (int base = 0; base < n; base += 32) {
-            if (__all_sync(kFullMask, done)) break;
-            const uint32_t gid = gid_n;
-            const float4 g0 = g0n, g1 = g1n, a = an;
-            const bool valid = base + lane < n;
-            if (base + 32 + lane < n) {   // records of the next round
-                gid_n = gid_nn;
-                g0n = geo[2 * (size_t)gid_n];
-                g1n = geo[2 * (size_t)gid_n + 1];
-                an = app[gid_n];
-            }
-            if (base + 64 + lane < n) gid_nn = sorted[start + base + 64 + lane];
-            const float ku = (float)(bx0 - __float_as_int(g0.x));
-            const float kv = (float)(by0 - __float_as_int(g0.z));
-            const float tmin = t_min_of(g1.w);
-            const bool rel = valid && block_touches(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmax,
-                                                    lymax);
-            unsigned mask = __ballot_sync(kFullMask, rel);
-            if (!mask) continue;
-            __syncwarp();
-            fs[lane] = make_float4(ku, kv, g0.y, g0.w);
-            ks[lane] = make_float4(g1.x, g1.y, tmin, g1.w);
-            cs[lane] = a;
-            ids[lane] = gid;
-            __syncwarp();
-            while (mask) {
-                const int j = __ffs(mask) - 1;
-                mask &= mask - 1;
-                if (done) continue;
-                const float4 f = fs[j], k = ks[j];
-                const float t = pair_t(__fsub_rn(__fadd_rn(f.x, lxf), f.z),
-                                       __fsub_rn(__fadd_rn(f.y, lyf), f.w), k.x, k.y);
-                if (!(t >= k.z)) continue;
-                const float al = fminf(__fmul_rn(k.w, exp2_approx(t)), kAlphaClamp);
-                const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
-                if (Tn < kTMin) {
-                    done = true;
-                    continue;
-                }
-                const float w = __fmul_rn(al, T);
-                const float4 c = cs[j];
-                c0 = __fmaf_rn(w, c.x, c0);
-                c1 = __fmaf_rn(w, c.y, c1);
-                c2 = __fmaf_rn(w, c.z, c2);
-                dd = __fmaf_rn(w, c.w, dd);
-                ss = __fadd_rn(ss, w);
-                if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
-                T = Tn;
-                last = (uint32_t)(base + j) + 1u;
-                ++nadd;
-            }
-        }
-        if (inside) {
-            if (rgb) {
-                rgb[p] = c0;
-                rgb[HW + p] = c1;
-                rgb[2 * HW + p] = c2;
-            }
-            if (depth) depth[p] = dd;
-            if (sil) sil[p] = ss;
-            pix_last[p] = last;
-            pix_nadd[p] = nadd;
-            pix_T[p] = T;
-        }
-        const bool ovf = __any_sync(kFullMask, nadd > cap);
-        if (lane == 0) blk_ovf[item] = plist ? (uint32_t)ovf : 1u;
+        if (32 + lane < n) gid_nn = sorted[start + 32 + lane];
     }
+    for (int base = 0; base < n; base += 32) {
+        if (__all_sync(kFullMask, done)) break;
+        const uint32_t gid = gid_n;
+        const float4 g0 = g0n, g1 = g1n, a = an;
+        const bool valid = base + lane < n;
+        if (base + 32 + lane < n) {   // records of the next round
+            gid_n = gid_nn;
+            g0n = geo[2 * (size_t)gid_n];
+            g1n = geo[2 * (size_t)gid_n + 1];
+            an = app[gid_n];
+        }
+        if (base + 64 + lane < n) gid_nn = sorted[start + base + 64 + lane];
+        const float ku = (float)(bx0 - __float_as_int(g0.x));
+        const float kv = (float)(by0 - __float_as_int(g0.z));
+        const float tmin = t_min_of(g1.w);
+        const bool rel = valid && block_touches(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmax,
+                                                lymax);
+        unsigned mask = __ballot_sync(kFullMask, rel);
+        if (!mask) continue;
+        __syncwarp();
+        fs[lane] = make_float4(ku, kv, g0.y, g0.w);
+        ks[lane] = make_float4(g1.x, g1.y, tmin, g1.w);
+        cs[lane] = a;
+        ids[lane] = gid;
+        __syncwarp();
+        while (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1;
+            if (done) continue;
+            const float4 f = fs[j], k = ks[j];
+            const float t = pair_t(__fsub_rn(__fadd_rn(f.x, lxf), f.z),
+                                   __fsub_rn(__fadd_rn(f.y, lyf), f.w), k.x, k.y);
+            if (!(t >= k.z)) continue;
+            const float al = fminf(__fmul_rn(k.w, exp2_approx(t)), kAlphaClamp);
+            const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
+            if (Tn < kTMin) {
+                done = true;
+                continue;
+            }
+            const float w = __fmul_rn(al, T);
+            const float4 c = cs[j];
+            c0 = __fmaf_rn(w, c.x, c0);
+            c1 = __fmaf_rn(w, c.y, c1);
+            c2 = __fmaf_rn(w, c.z, c2);
+            dd = __fmaf_rn(w, c.w, dd);
+            ss = __fadd_rn(ss, w);
+            if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
+            T = Tn;
+            last = (uint32_t)(base + j) + 1u;
+            ++nadd;
+        }
+    }
+    if (inside) {
+        if (rgb) {
+            rgb[p] = c0;
+            rgb[HW + p] = c1;
+            rgb[2 * HW + p] = c2;
+        }
+        if (depth) depth[p] = dd;
+        if (sil) sil[p] = ss;
+        pix_last[p] = last;
+        pix_nadd[p] = nadd;
+        pix_T[p] = T;
+    }
+    const bool ovf = __any_sync(kFullMask, nadd > cap);
+    if (lane == 0) blk_ovf[item] = plist ? (uint32_t)ovf : 1u;
 }
 
 // ---------------------------------------------------------------------------

@@ -215,15 +215,11 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
 // Flags a capacity shortage instead of letting later kernels overrun.
 __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count, int n_tiles,
                                                      uint32_t *tile_off, uint32_t *tile_cursor,
-                                                     Status *st, unsigned long long cap,
-                                                     uint32_t *work_ctr) {
+                                                     Status *st, unsigned long long cap) {
     __shared__ unsigned long long warp_sums[32];
     __shared__ unsigned long long carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        carry = 0;
-        work_ctr[0] = 0u;   // work counter of the persistent compositor
-    }
+    if (tid == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < n_tiles; base += 1024) {
         const int i = base + tid;
