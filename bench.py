@@ -475,7 +475,7 @@ def main():
         tr.obs_depth.copy_(h_d[f], non_blocking=True)
         loss = tr.replay()
         res[:12].copy_(tr.pose)
-        res[12].copy_(loss)
+        res[12:].copy_(loss)
         out_host.copy_(res, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0

@@ -190,6 +190,76 @@ vt_status vt_render_backward(vt_ctx *ctx, const float *dL_drgb, const float *dL_
                              const float *dL_dsil, int32_t mode, const vt_grads *grads,
                              double *d_twist, double *d_mat, vt_stream stream);
 
+/* ---- Loss inputs: visibility check (Sec. 3.3) and the masked L1 terms of
+ * Eq. 1 (tracking) and Eq. 2 (mapping). ---------------------------------- */
+
+/* One view of a section for the visibility check. */
+typedef struct {
+    const float *depth;       /* device, H x W metres; <= 0 or non-finite = invalid */
+    int32_t W, H;
+    vt_intrinsics K;
+    const double *pose12;     /* device, 12 doubles, camera-to-world */
+} vt_view;
+
+#define VT_MAX_VIS_VIEWS 8
+
+/* Visibility check (Sec. 3.3): visible[p] (device uint8, H x W) = 1 iff the
+ * valid depth pixel p of `depth` (device, H x W), back-projected with
+ * intrinsics K and pose12 (device), lands in front of and inside one of
+ * views[0, n_views) (host array, 1 <= n_views <= VT_MAX_VIS_VIEWS) at a depth
+ * within rel_tol (the paper's 1%: 0.01) of that view's depth map bilinearly
+ * interpolated at the projection (all four neighbours valid); else 0.  The
+ * paper takes the union over a section's head, middle and last frames.
+ * Pixels sit at integer coordinates.  The arithmetic is FP64 in a fixed
+ * order without contraction, so the decisions equal those of a plain FP64
+ * evaluation of the same formula. */
+vt_status vt_visibility(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                        const double *pose12, const vt_view *views, int32_t n_views,
+                        double rel_tol, uint8_t *visible, vt_stream stream);
+
+/* Weights and masks of the masked L1 loss. */
+typedef struct {
+    double w_rgb;             /* alpha of Eq. 1, rho of Eq. 2 */
+    double w_depth;           /* beta of Eq. 1, sigma of Eq. 2 */
+    float sil_min;            /* covered iff silhouette > sil_min; < 0: no coverage mask */
+    int32_t rgb_needs_depth;  /* 1: the colour term is also masked by valid observed depth */
+} vt_l1_weights;
+
+/* Masked L1 loss and its image gradient, P = W H:
+ *   L = w_rgb / (3P) sum_{p,c} m_c(p) |rgb - obs_rgb| + w_depth / P sum_p m_d(p) |depth - obs_depth|
+ *   m_d = valid observed depth AND covered AND visible,
+ *   m_c = covered AND visible [AND valid observed depth if rgb_needs_depth],
+ *   covered = silhouette > sil_min (always when sil_min < 0; silhouette may
+ *   then be NULL), visible = visible[p] != 0 (always when visible is NULL).
+ * Eq. 1: (alpha, beta, 0.99, 1) with the visibility mask of vt_visibility;
+ * Eq. 2 L1 terms: (rho, sigma, -1, 0).  All images are device float32
+ * (rgb 3 x H x W, the others H x W).  d_rgb and d_depth (device float32, may
+ * be NULL) are overwritten with dL/drgb = w_rgb / (3P) m_c sign(rgb -
+ * obs_rgb) and dL/ddepth = w_depth / P m_d sign(depth - obs_depth), sign(0)
+ * = 0; loss (device, one double, may be NULL) receives L, summed in FP64 in a
+ * fixed order.  ctx provides scratch only (its last render is untouched);
+ * size it with vt_ctx_reserve before capturing a graph. */
+vt_status vt_masked_l1(vt_ctx *ctx, int32_t W, int32_t H, const float *rgb, const float *depth,
+                       const float *silhouette, const float *obs_rgb, const float *obs_depth,
+                       const uint8_t *visible, vt_l1_weights w, float *d_rgb, float *d_depth,
+                       double *loss, vt_stream stream);
+
+/* One Adam step on the camera pose (Sec. 3.3 tracking optimises the pose of
+ * the latest frame; the supplementary gives Adam learning rates lr_rot and
+ * lr_trans).  With the twist gradient g = d_twist (device, 6 doubles, as
+ * accumulated by vt_render_backward) and state (device, 13 doubles: m[6],
+ * v[6], step count t, zero-initialised):
+ *   t += 1, m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ *   s = lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ *   pose12 (device) <- pose12 Exp(-s)  (right perturbation, xi = (rho, phi)),
+ * and d_twist is zeroed for the next backward.  lr (host, 6 doubles) holds
+ * the rates for rho (translation) then phi (rotation).  FP64, one thread.
+ * ctx may be NULL; when given it only records the launch (vt_ctx_timing,
+ * vt_ctx_launch_count). */
+vt_status vt_pose_adam(vt_ctx *ctx, double *pose12, double *d_twist, double *state,
+                       const double *lr, double beta1, double beta2, double eps,
+                       vt_stream stream);
+
 /* Per-kernel timing of the context's launches with CUDA events on the
  * launching stream (enable != 0).  vt_ctx_timing synchronises the stream
  * and writes, for up to n_max kernels, their names (static strings), the

@@ -4,7 +4,9 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product path (the CUDA library and
 its binding) never does.
 
-The arithmetic lives in ``vt_oracle.c``; this module compiles it with gcc
+The arithmetic lives in ``vt_oracle.c`` (rendering and its gradient) and
+``vt_oracle_loss.c`` (visibility check and masked L1 loss); this module
+compiles them with gcc
 (``-O2 -fopenmp -ffp-contract=off``, no fast-math) into ``oracle/_build`` and
 marshals numpy arrays through ctypes.
 """
@@ -22,7 +24,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SRC = [os.path.join(_HERE, "vt_oracle.c"), os.path.join(_HERE, "vt_oracle.h")]
+_SRC = [os.path.join(_HERE, "vt_oracle.c"), os.path.join(_HERE, "vt_oracle_loss.c"),
+        os.path.join(_HERE, "vt_oracle.h")]
 _lock = threading.Lock()
 _lib = None
 
@@ -35,7 +38,7 @@ def build(force: bool = False) -> str:
     if stale:
         tmp = _SO + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC[0], "-lm"]
+               "-fPIC", "-shared", "-o", tmp, _SRC[0], _SRC[1], "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _SO)
     return _SO
@@ -72,6 +75,17 @@ class _Grads(C.Structure):
                 ("twist_noise", C.c_double * 6), ("mat_noise", C.c_double * 12)]
 
 
+class _View(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("W", C.c_int32), ("H", C.c_int32),
+                ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("pose", C.c_double * 12)]
+
+
+class _L1Weights(C.Structure):
+    _fields_ = [("w_rgb", C.c_double), ("w_depth", C.c_double), ("sil_min", C.c_double),
+                ("rgb_needs_depth", C.c_int32)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -92,6 +106,14 @@ def lib():
             L.orc_section_init.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                            C.c_int32, C.c_float, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p]
+            L.orc_visibility.restype = None
+            L.orc_visibility.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_float,
+                                         C.c_float, C.c_float, C.c_void_p, C.c_void_p,
+                                         C.c_int32, C.c_double, C.c_void_p]
+            L.orc_masked_l1.restype = C.c_double
+            L.orc_masked_l1.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, _L1Weights,
+                                        C.c_void_p, C.c_void_p]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -274,3 +296,41 @@ def section_init(depth, rgb, K, poses) -> Section:
     return Section(W, H, tuple(float(np.float32(k)) for k in K),
                    np.asarray(poses, np.float64).reshape(V, 3, 4).copy(), depth,
                    src[:n].copy(), col[:n].copy(), op[:n].copy(), rad[:n].copy())
+
+
+def visibility(depth, K, pose, views, rel_tol=0.01):
+    """Visibility mask (H, W) bool of the valid pixels of ``depth`` (seen
+    with intrinsics K and camera-to-world ``pose``) to the union of
+    ``views``: a list of (depth (h, w) f32, K, pose)."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    H, W = depth.shape
+    keep = [np.ascontiguousarray(d, np.float32) for d, _, _ in views]
+    arr = (_View * max(len(views), 1))()
+    for i, ((_, k, p), d) in enumerate(zip(views, keep)):
+        arr[i] = _View(_ptr(d), d.shape[1], d.shape[0], *(float(np.float32(x)) for x in k),
+                       (C.c_double * 12)(*pose12(p)[0]))
+    out = np.zeros((H, W), np.uint8)
+    fx, fy, cx, cy = (float(np.float32(k)) for k in K)
+    flat = pose12(pose)[0]
+    lib().orc_visibility(_ptr(depth), W, H, fx, fy, cx, cy, _ptr(flat), arr, len(views),
+                         float(rel_tol), _ptr(out))
+    return out.astype(bool)
+
+
+def masked_l1(rgb, depth, sil, obs_rgb, obs_depth, w_rgb, w_depth, sil_min=-1.0,
+              rgb_needs_depth=False, visible=None):
+    """Masked L1 loss of Eq. 1 / Eq. 2 (value, float64) and its gradient with
+    respect to rgb (3, H, W) and depth (H, W), float64."""
+    rgb, depth, sil, obs_rgb, obs_depth = (np.ascontiguousarray(a, np.float32) for a in
+                                           (rgb, depth, sil, obs_rgb, obs_depth))
+    H, W = depth.shape
+    vis = None if visible is None else np.ascontiguousarray(visible, np.uint8)
+    d_rgb = np.zeros((3, H, W))
+    d_depth = np.zeros((H, W))
+    # the coverage threshold is the FP32 value the kernel compares against
+    w = _L1Weights(float(w_rgb), float(w_depth), float(np.float32(sil_min)),
+                   int(bool(rgb_needs_depth)))
+    loss = lib().orc_masked_l1(W, H, _ptr(rgb), _ptr(depth), _ptr(sil), _ptr(obs_rgb),
+                               _ptr(obs_depth), None if vis is None else _ptr(vis), w,
+                               _ptr(d_rgb), _ptr(d_depth))
+    return float(loss), d_rgb, d_depth

@@ -1,0 +1,43 @@
+"""Plain float64 NumPy reference of the tracking optimiser step (test
+infrastructure; see the package docstring for who may import it).
+
+Adam on the camera-pose twist (Sec. 3.3 optimises the pose of the latest
+frame; the supplementary gives the Adam learning rates lr_rot, lr_trans),
+with the pose retracted by right-multiplication with the SE(3) exponential:
+
+    t += 1,  m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+    s = lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+    P <- P Exp(-s),  xi = (rho, phi).
+
+The exponential is evaluated here as the matrix exponential of the 4 x 4
+twist matrix [[phi]x, rho; 0, 0] (SciPy's expm), independently of the
+closed form the kernel uses.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import expm
+
+
+def se3_exp(xi) -> np.ndarray:
+    """(3, 4) [R | t] = Exp of the twist xi = (rho, phi)."""
+    rho, phi = np.asarray(xi[:3], np.float64), np.asarray(xi[3:], np.float64)
+    A = np.zeros((4, 4))
+    A[:3, :3] = [[0.0, -phi[2], phi[1]], [phi[2], 0.0, -phi[0]], [-phi[1], phi[0], 0.0]]
+    A[:3, 3] = rho
+    return expm(A)[:3, :]
+
+
+def adam_pose_step(pose, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-15):
+    """One step; returns (new pose (3, 4), m, v, t)."""
+    g = np.asarray(grad, np.float64)
+    t = t + 1.0
+    m = beta1 * np.asarray(m, np.float64) + (1 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1 - beta2) * g * g
+    s = np.asarray(lr, np.float64) * (m / (1 - beta1 ** t)) / (np.sqrt(v / (1 - beta2 ** t)) + eps)
+    E = se3_exp(-s)
+    P = np.asarray(pose, np.float64).reshape(3, 4)
+    R = P[:, :3] @ E[:, :3]
+    tr = P[:, :3] @ E[:, 3] + P[:, 3]
+    return np.hstack([R, tr[:, None]]), m, v, t

@@ -114,6 +114,37 @@ int64_t orc_section_init(const float *depth, const float *rgb, int32_t n_views, 
                          int32_t H, float fx, uint32_t *src, double *colour,
                          double *opacity, double *radius);
 
+/* ---- loss inputs (vt_oracle_loss.c) ---------------------------------- */
+
+typedef struct {
+    const float *depth;          /* H x W, metres; <=0 or non-finite = invalid */
+    int32_t W, H;
+    float fx, fy, cx, cy;
+    double pose[12];             /* camera-to-world: R row-major then t */
+} orc_view;
+
+/* Visibility check (Sec. 3.3): visible[p] = 1 iff the valid depth pixel p of
+ * the current frame, back-projected with `pose`, projects in front of and
+ * inside at least one of the views with a depth within rel_tol (0.01) of the
+ * view's bilinearly interpolated depth (all four neighbours valid). */
+void orc_visibility(const float *depth, int32_t W, int32_t H, float fx, float fy, float cx,
+                    float cy, const double *pose, const orc_view *views, int32_t n_views,
+                    double rel_tol, uint8_t *visible);
+
+typedef struct {
+    double w_rgb;                /* alpha (Eq. 1) or rho (Eq. 2) */
+    double w_depth;              /* beta (Eq. 1) or sigma (Eq. 2) */
+    double sil_min;              /* covered iff silhouette > sil_min (an FP32 value, widened);
+                                    < 0: no coverage mask */
+    int32_t rgb_needs_depth;     /* 1: the colour term is masked by valid observed depth too */
+} orc_l1_weights;
+
+/* L = w_rgb / (3P) sum m_c |V' - V| + w_depth / P sum m_d |D' - D| and its
+ * gradient (d_rgb 3 x H x W, d_depth H x W; either may be NULL). */
+double orc_masked_l1(int32_t W, int32_t H, const float *rgb, const float *depth, const float *sil,
+                     const float *obs_rgb, const float *obs_depth, const uint8_t *visible,
+                     orc_l1_weights w, double *d_rgb, double *d_depth);
+
 #ifdef __cplusplus
 }
 #endif

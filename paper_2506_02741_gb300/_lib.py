@@ -36,6 +36,19 @@ class GradsC(C.Structure):
     _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p)]
 
 
+class ViewC(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("W", C.c_int32), ("H", C.c_int32), ("K", Intrinsics),
+                ("pose12", C.c_void_p)]
+
+
+class L1WeightsC(C.Structure):
+    _fields_ = [("w_rgb", C.c_double), ("w_depth", C.c_double), ("sil_min", C.c_float),
+                ("rgb_needs_depth", C.c_int32)]
+
+
+MAX_VIS_VIEWS = 8
+
+
 class VTError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -64,6 +77,12 @@ def _declare(L):
                                 C.c_int32, _P, _P, _P, _P]),
         "vt_render_backward": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.POINTER(GradsC), _P, _P,
                                          _P]),
+        "vt_visibility": (C.c_int, [_P, C.c_int32, C.c_int32, Intrinsics, _P, C.POINTER(ViewC),
+                                    C.c_int32, C.c_double, _P, _P]),
+        "vt_masked_l1": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, L1WeightsC,
+                                   _P, _P, _P, _P]),
+        "vt_pose_adam": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_double,
+                                   C.c_double, C.c_double, _P]),
         "vt_ctx_set_timing": (C.c_int, [_P, C.c_int32]),
         "vt_ctx_timing": (C.c_int32, [_P, _P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_double), C.c_int32, C.c_int32]),
@@ -89,7 +108,7 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_render_backward", "vt_ctx_set_timing", "vt_ctx_timing", "vt_ctx_launch_count",
            "vt_ctx_debug_copy", "vt_last_error", "vt_version", "vt_ctx_set_list_capacity",
            "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists",
-           "vt_backproject_noalloc"]
+           "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam"]
 
 
 def lib_path() -> str:

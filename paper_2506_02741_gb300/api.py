@@ -153,6 +153,50 @@ def backproject(depth: torch.Tensor, K, pose, stream=None):
     return cen[:n], pix[:n]
 
 
+def visibility(depth: torch.Tensor, K, pose, views, rel_tol: float = 0.01, out=None,
+               stream=None) -> torch.Tensor:
+    """Visibility check of Sec. 3.3: (H, W) uint8 mask of the valid pixels of
+    ``depth`` (seen with intrinsics K from ``pose``, (12,) float64 device or a
+    (3, 4) matrix) whose depth in one of ``views`` lies within rel_tol of that
+    view's interpolated depth map.  views: list of (depth (h, w) float32
+    device, K, pose (12,) float64 device), at most 8 (the paper uses a
+    section's head, middle and last frames)."""
+    depth = _cuda(depth, torch.float32, "depth")
+    H, W = depth.shape
+    P = pose if isinstance(pose, torch.Tensor) else pose12(pose, depth.device)
+    P = _cuda(P, torch.float64, "pose", (12,))
+    if not 1 <= len(views) <= L.MAX_VIS_VIEWS:
+        raise ValueError(f"visibility takes 1..{L.MAX_VIS_VIEWS} views")
+    vs = []
+    for d, k, p in views:
+        d = _cuda(d, torch.float32, "view depth")
+        p = _cuda(p, torch.float64, "view pose", (12,))
+        vs.append(L.ViewC(_ptr(d), d.shape[1], d.shape[0], _intr(k), _ptr(p)))
+    arr = (L.ViewC * len(vs))(*vs)
+    if out is None:
+        out = torch.empty(H, W, dtype=torch.uint8, device=depth.device)
+    out = _cuda(out, torch.uint8, "out", (H, W))
+    L.check(L.lib().vt_visibility(_ptr(depth), W, H, _intr(K), _ptr(P), arr, len(vs),
+                                  float(rel_tol), _ptr(out), _stream(stream)), "vt_visibility")
+    return out
+
+
+def pose_adam(pose: torch.Tensor, d_twist: torch.Tensor, state: torch.Tensor, lr,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, renderer=None,
+              stream=None):
+    """One Adam step on the pose (12,) float64 from the twist gradient (6,)
+    float64 (zeroed afterwards), state (13,) float64 = (m, v, t); lr: six
+    rates (rho then phi).  renderer (optional) records the launch."""
+    _cuda(pose, torch.float64, "pose", (12,))
+    _cuda(d_twist, torch.float64, "d_twist", (6,))
+    _cuda(state, torch.float64, "state", (13,))
+    rates = (C.c_double * 6)(*[float(x) for x in lr])
+    ctx = renderer._ctx if renderer is not None else None
+    L.check(L.lib().vt_pose_adam(ctx, _ptr(pose), _ptr(d_twist), _ptr(state), rates,
+                                 float(beta1), float(beta2), float(eps), _stream(stream)),
+            "vt_pose_adam")
+
+
 class Renderer:
     """Owns one vt_ctx (the library's render workspace) on the current device."""
 
@@ -243,7 +287,8 @@ class Renderer:
         (d_colour (n,3), d_opacity (n,), d_radius (n,)) float32 device tensors
         or None (frozen section); gradients are accumulated (+=).  With
         pose_grad, d_twist (6,) and d_mat (12,) float64 device tensors are
-        accumulated (created as zeros if not given).  Returns (d_twist, d_mat)."""
+        accumulated (both created as zeros when neither is given; a missing
+        one is not computed when the other is).  Returns (d_twist, d_mat)."""
         mode = 0
         grads = None
         if attr_grads is not None:
@@ -259,21 +304,52 @@ class Renderer:
         if pose_grad:
             mode |= L.VT_GRAD_POSE
             dev = self.last[1].device if self.last else "cuda"
-            if d_twist is None:
+            if d_twist is None and d_mat is None:
                 d_twist = torch.zeros(6, dtype=torch.float64, device=dev)
-            if d_mat is None:
                 d_mat = torch.zeros(12, dtype=torch.float64, device=dev)
         L.check(self._lib.vt_render_backward(self._ctx, _ptr(d_rgb), _ptr(d_depth), _ptr(d_sil),
                                              mode, grads, _ptr(d_twist), _ptr(d_mat),
                                              _stream(stream)), "vt_render_backward")
         return d_twist, d_mat
 
+    def masked_l1(self, rgb, depth, sil, obs_rgb, obs_depth, w_rgb: float, w_depth: float,
+                  sil_min: float = -1.0, rgb_needs_depth: bool = False, visible=None,
+                  d_rgb=None, d_depth=None, loss=None, stream=None):
+        """Masked L1 terms of Eq. 1 / Eq. 2 and their image gradient in one
+        kernel (this context provides the scratch of the loss sum).  Eq. 1:
+        (alpha, beta, sil_min=0.99, rgb_needs_depth=True, visible=mask);
+        Eq. 2: (rho, sigma).  Returns (loss (1,) float64, d_rgb (3,H,W),
+        d_depth (H,W)); given output tensors are overwritten."""
+        depth = _cuda(depth, torch.float32, "depth")
+        H, W = depth.shape
+        dev = depth.device
+        _cuda(rgb, torch.float32, "rgb", (3, H, W))
+        _cuda(obs_rgb, torch.float32, "obs_rgb", (3, H, W))
+        _cuda(obs_depth, torch.float32, "obs_depth", (H, W))
+        if sil is not None:
+            _cuda(sil, torch.float32, "sil", (H, W))
+        if visible is not None:
+            _cuda(visible, torch.uint8, "visible", (H, W))
+        if d_rgb is None:
+            d_rgb = torch.empty(3, H, W, device=dev)
+        if d_depth is None:
+            d_depth = torch.empty(H, W, device=dev)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device=dev)
+        w = L.L1WeightsC(float(w_rgb), float(w_depth), float(sil_min), int(bool(rgb_needs_depth)))
+        L.check(self._lib.vt_masked_l1(self._ctx, W, H, _ptr(rgb), _ptr(depth), _ptr(sil),
+                                       _ptr(obs_rgb), _ptr(obs_depth), _ptr(visible), w,
+                                       _ptr(_cuda(d_rgb, torch.float32, "d_rgb", (3, H, W))),
+                                       _ptr(_cuda(d_depth, torch.float32, "d_depth", (H, W))),
+                                       _ptr(loss), _stream(stream)), "vt_masked_l1")
+        return loss, d_rgb, d_depth
+
     # -- instrumentation -----------------------------------------------------
     def set_timing(self, on: bool = True):
         L.check(self._lib.vt_ctx_set_timing(self._ctx, int(bool(on))), "vt_ctx_set_timing")
 
     def timing(self, reset: bool = True, stream=None) -> dict:
-        n = 16
+        n = 64
         names = (C.c_char_p * n)()
         launches = (C.c_int64 * n)()
         ms = (C.c_double * n)()

@@ -50,13 +50,15 @@ constexpr size_t kSortSmemBigBytes =
 
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
-    K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_NUM
+    K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
+    K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
                                    "k_composite_bwd", "k_pose_finalize", "k_backproject",
                                    "k_section_init",  "k_count_valid",   "k_composite_bwd_list",
-                                   "k_sort_tiles_long", "k_attr_scatter"};
+                                   "k_sort_tiles_long", "k_attr_scatter", "k_masked_l1",
+                                   "k_sum_partials",  "k_pose_adam"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -92,6 +94,8 @@ struct vt_ctx {
     TabRow *tab = nullptr;
     double *pose_partials = nullptr, *pose_copy = nullptr;
     uint32_t *blk_ovf = nullptr;      // list overflow flag per 8x4 pixel block
+    double *loss_part = nullptr;      // masked-L1 block partials (separate allocation)
+    int64_t loss_cap = 0;             // blocks they hold
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
     float *accr = nullptr;        // and radius, per Gaussian
     // per-pixel lists of added Gaussians (separate allocation)
@@ -240,6 +244,27 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     return VT_OK;
 }
 
+// Scratch of the masked-L1 loss: two doubles per block of 256 pixels.  Grows
+// on the stream; refuses to grow while the stream is being captured.
+vt_status ensure_loss(vt_ctx *c, int64_t blocks, cudaStream_t s) {
+    if (blocks <= c->loss_cap) return VT_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    VT_CUDA(cudaStreamIsCapturing(s, &cs), "capture query");
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(VT_ERR_STATE, "vt_masked_l1: scratch must be reserved before graph capture");
+    if (c->loss_part) cudaFreeAsync(c->loss_part, s);
+    c->loss_part = nullptr;
+    c->loss_cap = 0;
+    void *p = nullptr;
+    const cudaError_t e = cudaMallocAsync(&p, sizeof(double) * 2 * blocks, s);
+    if (e != cudaSuccess)
+        return fail(VT_ERR_OOM, "loss scratch of %lld blocks: %s", (long long)blocks,
+                    cudaGetErrorString(e));
+    c->loss_part = static_cast<double *>(p);
+    c->loss_cap = blocks;
+    return VT_OK;
+}
+
 int64_t default_instances(int64_t g) { return 4 * g + 65536; }
 
 vt_status check_intrinsics(const vt_intrinsics &K, const char *who) {
@@ -280,6 +305,7 @@ void vt_ctx_destroy(vt_ctx *c) {
     if (!c) return;
     free_arena(c, c->stream);
     if (c->plist) cudaFreeAsync(c->plist, c->stream);
+    if (c->loss_part) cudaFreeAsync(c->loss_part, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
@@ -306,6 +332,7 @@ vt_status vt_ctx_reserve(vt_ctx *c, int64_t n_gaussians, int32_t W, int32_t H,
     c->reserved_i = std::max(c->reserved_i, n_instances);  // later renders keep this capacity
     const int64_t tiles = (int64_t)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
     c->stream = stream;
+    if ((st = ensure_loss(c, ((int64_t)W * H + 255) / 256, stream))) return st;
     return ensure(c, std::max<int64_t>(n_gaussians, 1), n_instances, (int64_t)W * H, tiles,
                   std::max<int64_t>(c->cap_v, 1), std::max<int64_t>(c->cap_tab, 1), stream);
 }
@@ -582,6 +609,95 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
                                                d_mat);
     }
     VT_CUDA(cudaGetLastError(), "vt_render_backward launch");
+    return VT_OK;
+}
+
+vt_status vt_visibility(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                        const double *pose12, const vt_view *views, int32_t n_views,
+                        double rel_tol, uint8_t *visible, vt_stream stream) {
+    vt_status st = check_image(W, H, "vt_visibility");
+    if (st) return st;
+    if ((st = check_intrinsics(K, "vt_visibility"))) return st;
+    if (!depth || !pose12 || !visible || !views)
+        return fail(VT_ERR_INVALID_ARG, "vt_visibility: NULL depth, pose, views or output");
+    if (n_views < 1 || n_views > VT_MAX_VIS_VIEWS)
+        return fail(VT_ERR_INVALID_ARG, "vt_visibility: n_views = %d outside [1, %d]", n_views,
+                    VT_MAX_VIS_VIEWS);
+    if (!(std::isfinite(rel_tol) && rel_tol >= 0.0))
+        return fail(VT_ERR_INVALID_ARG, "vt_visibility: rel_tol must be finite and >= 0");
+    VisViews vv{};
+    vv.n = n_views;
+    for (int k = 0; k < n_views; ++k) {
+        const vt_view &V = views[k];
+        if ((st = check_image(V.W, V.H, "vt_visibility view"))) return st;
+        if ((st = check_intrinsics(V.K, "vt_visibility view"))) return st;
+        if (!V.depth || !V.pose12)
+            return fail(VT_ERR_INVALID_ARG, "vt_visibility: view %d has NULL depth or pose", k);
+        vv.v[k] = VisView{V.depth, V.W, V.H, V.K.fx, V.K.fy, V.K.cx, V.K.cy, V.pose12};
+    }
+    const int64_t P = (int64_t)W * H;
+    k_visibility<<<(unsigned)((P + 255) / 256), 256, 0, stream>>>(
+        depth, W, H, K.fx, K.fy, K.cx, K.cy, pose12, vv, rel_tol, visible);
+    VT_CUDA(cudaGetLastError(), "vt_visibility launch");
+    return VT_OK;
+}
+
+vt_status vt_masked_l1(vt_ctx *c, int32_t W, int32_t H, const float *rgb, const float *depth,
+                       const float *silhouette, const float *obs_rgb, const float *obs_depth,
+                       const uint8_t *visible, vt_l1_weights w, float *d_rgb, float *d_depth,
+                       double *loss, vt_stream stream) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_masked_l1: ctx is NULL");
+    vt_status st = check_image(W, H, "vt_masked_l1");
+    if (st) return st;
+    if (!rgb || !depth || !obs_rgb || !obs_depth)
+        return fail(VT_ERR_INVALID_ARG, "vt_masked_l1: NULL image");
+    if (w.sil_min >= 0.f && !silhouette)
+        return fail(VT_ERR_INVALID_ARG, "vt_masked_l1: coverage mask needs the silhouette");
+    if (!std::isfinite(w.w_rgb) || !std::isfinite(w.w_depth) || std::isnan(w.sil_min))
+        return fail(VT_ERR_INVALID_ARG, "vt_masked_l1: weights must be finite");
+    const int64_t P = (int64_t)W * H;
+    const int64_t nb = (P + 255) / 256;
+    if (loss && (st = ensure_loss(c, nb, stream))) return st;
+    const double wc = w.w_rgb / (3.0 * (double)P), wd = w.w_depth / (double)P;
+    {
+        LaunchScope ls(c, K_L1, stream);
+        k_masked_l1<<<(unsigned)nb, 256, 0, stream>>>(
+            P, rgb, depth, silhouette, obs_rgb, obs_depth, visible, w.sil_min,
+            w.rgb_needs_depth ? 1 : 0, (float)wc, (float)wd, d_rgb, d_depth,
+            loss ? c->loss_part : nullptr);
+    }
+    if (loss) {
+        LaunchScope ls(c, K_L1_SUM, stream);
+        k_sum_partials<<<1, 1024, 0, stream>>>(c->loss_part, (int)nb, wc, wd, loss);
+    }
+    VT_CUDA(cudaGetLastError(), "vt_masked_l1 launch");
+    return VT_OK;
+}
+
+vt_status vt_pose_adam(vt_ctx *c, double *pose12, double *d_twist, double *state,
+                       const double *lr, double beta1, double beta2, double eps,
+                       vt_stream stream) {
+    if (!pose12 || !d_twist || !state || !lr)
+        return fail(VT_ERR_INVALID_ARG, "vt_pose_adam: NULL pose, gradient, state or rates");
+    PoseAdamParams prm{};
+    for (int i = 0; i < 6; ++i) {
+        if (!std::isfinite(lr[i]) || lr[i] < 0.0)
+            return fail(VT_ERR_INVALID_ARG, "vt_pose_adam: learning rates must be finite, >= 0");
+        prm.lr[i] = lr[i];
+    }
+    if (!(beta1 >= 0.0 && beta1 < 1.0 && beta2 >= 0.0 && beta2 < 1.0 && eps >= 0.0 &&
+          std::isfinite(eps)))
+        return fail(VT_ERR_INVALID_ARG, "vt_pose_adam: need 0 <= beta < 1 and finite eps >= 0");
+    prm.beta1 = beta1;
+    prm.beta2 = beta2;
+    prm.eps = eps;
+    if (c) {
+        LaunchScope ls(c, K_POSE_ADAM, stream);
+        k_pose_adam<<<1, 32, 0, stream>>>(pose12, d_twist, state, prm);
+    } else {
+        k_pose_adam<<<1, 32, 0, stream>>>(pose12, d_twist, state, prm);
+    }
+    VT_CUDA(cudaGetLastError(), "vt_pose_adam launch");
     return VT_OK;
 }
 

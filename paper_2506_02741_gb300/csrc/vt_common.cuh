@@ -231,6 +231,34 @@ __global__ void k_composite_bwd_list(SecTable T, Camera cam, const float4 *geo,
                                      double *pose_partials, float4 *acc4, float *accr,
                                      const Status *st);
 __global__ void k_attr_scatter(SecTable T, const float4 *acc4, const float *accr);
+
+// Loss inputs (vt_loss.cu).
+struct VisView {
+    const float *depth;
+    int W, H;
+    float fx, fy, cx, cy;
+    const double *pose;
+};
+struct VisViews {
+    int n;
+    VisView v[VT_MAX_VIS_VIEWS];
+};
+__global__ void k_visibility(const float *depth, int W, int H, float fx, float fy, float cx,
+                             float cy, const double *pose, VisViews views, double rel_tol,
+                             uint8_t *visible);
+__global__ void k_masked_l1(int64_t P, const float *rgb, const float *depth, const float *sil,
+                            const float *obs_rgb, const float *obs_depth, const uint8_t *visible,
+                            float sil_min, int rgb_needs_depth, float gc, float gd, float *d_rgb,
+                            float *d_depth, double *partials);
+__global__ void k_sum_partials(const double *partials, int n_blocks, double wc, double wd,
+                               double *loss);
+
+// Tracking optimiser step (vt_pose.cu).
+struct PoseAdamParams {
+    double lr[6];
+    double beta1, beta2, eps;
+};
+__global__ void k_pose_adam(double *pose, double *d_twist, double *state, PoseAdamParams prm);
 __global__ void k_pose_finalize(const double *partials, int n_parts, const double *pose_copy,
                                 double *d_twist, double *d_mat);
 __global__ void k_count_valid(const float *depth, int64_t total, uint32_t *block_counts);

@@ -1,0 +1,149 @@
+// Loss inputs of tracking and mapping: the visibility check of Sec. 3.3 and
+// the masked L1 terms of Eq. 1 / Eq. 2 with their image gradient, fused into
+// one pass over the pixels.  Both kernels are HBM-bound: one thread per pixel,
+// coalesced planar loads and stores.
+#include "vt_common.cuh"
+
+namespace vt {
+
+__device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d > 0.f; }
+
+// FP64 with explicit rounding (no contraction), in the order of the plain
+// definition: ((a0 x0 + a1 x1) + a2 x2).
+__device__ __forceinline__ double dot3(double a0, double x0, double a1, double x1, double a2,
+                                       double x2) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a0, x0), __dmul_rn(a1, x1)), __dmul_rn(a2, x2));
+}
+
+// Bilinear depth of view V at (x, y); false outside the image or when one of
+// the four neighbours lacks valid depth.
+__device__ __forceinline__ bool interp_depth(const VisView &V, double x, double y, double &out) {
+    if (!(x >= 0.0 && x <= (double)(V.W - 1) && y >= 0.0 && y <= (double)(V.H - 1)))
+        return false;
+    const int i0 = (int)floor(x), j0 = (int)floor(y);
+    const int i1 = min(i0 + 1, V.W - 1), j1 = min(j0 + 1, V.H - 1);
+    const double fx = __dsub_rn(x, (double)i0), fy = __dsub_rn(y, (double)j0);
+    const float d00 = V.depth[(size_t)j0 * V.W + i0], d10 = V.depth[(size_t)j0 * V.W + i1];
+    const float d01 = V.depth[(size_t)j1 * V.W + i0], d11 = V.depth[(size_t)j1 * V.W + i1];
+    if (!valid_depth(d00) || !valid_depth(d10) || !valid_depth(d01) || !valid_depth(d11))
+        return false;
+    const double gx = __dsub_rn(1.0, fx), gy = __dsub_rn(1.0, fy);
+    const double top = __dadd_rn(__dmul_rn((double)d00, gx), __dmul_rn((double)d10, fx));
+    const double bot = __dadd_rn(__dmul_rn((double)d01, gx), __dmul_rn((double)d11, fx));
+    out = __dadd_rn(__dmul_rn(top, gy), __dmul_rn(bot, fy));
+    return true;
+}
+
+// One thread per pixel of the current frame: back-project with its pose,
+// then for each view transform into the view, project, interpolate the
+// view's depth and test |z - D~| <= rel_tol D~ (union over views).
+__global__ void __launch_bounds__(256) k_visibility(const float *depth, int W, int H, float fx,
+                                                    float fy, float cx, float cy,
+                                                    const double *pose, VisViews views,
+                                                    double rel_tol, uint8_t *visible) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)W * H) return;
+    const int v = (int)(p / W), u = (int)(p - (int64_t)v * W);
+    const float D = depth[p];
+    uint8_t vis = 0;
+    if (valid_depth(D)) {
+        const double a = __ddiv_rn(__dsub_rn((double)u, (double)cx), (double)fx);
+        const double b = __ddiv_rn(__dsub_rn((double)v, (double)cy), (double)fy);
+        const double xc0 = __dmul_rn((double)D, a), xc1 = __dmul_rn((double)D, b),
+                     xc2 = (double)D;
+        double X[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            X[i] = __dadd_rn(dot3(pose[3 * i], xc0, pose[3 * i + 1], xc1, pose[3 * i + 2], xc2),
+                             pose[9 + i]);
+        for (int k = 0; k < views.n && !vis; ++k) {
+            const VisView &V = views.v[k];
+            const double *Pk = V.pose;
+            const double d0 = __dsub_rn(X[0], Pk[9]), d1 = __dsub_rn(X[1], Pk[10]),
+                         d2 = __dsub_rn(X[2], Pk[11]);
+            const double x0 = dot3(Pk[0], d0, Pk[3], d1, Pk[6], d2);
+            const double x1 = dot3(Pk[1], d0, Pk[4], d1, Pk[7], d2);
+            const double x2 = dot3(Pk[2], d0, Pk[5], d1, Pk[8], d2);
+            if (!(x2 > 0.0)) continue;
+            const double px = __dadd_rn(__dmul_rn((double)V.fx, __ddiv_rn(x0, x2)), (double)V.cx);
+            const double py = __dadd_rn(__dmul_rn((double)V.fy, __ddiv_rn(x1, x2)), (double)V.cy);
+            double Dk;
+            if (!interp_depth(V, px, py, Dk)) continue;
+            if (fabs(__dsub_rn(x2, Dk)) <= __dmul_rn(rel_tol, Dk)) vis = 1;
+        }
+    }
+    visible[p] = vis;
+}
+
+__device__ __forceinline__ float sign_of(float e) { return e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f); }
+
+// One thread per pixel: masks, |residuals| and the gradient of the masked L1
+// loss; per block the two FP64 sums (colour, depth) go to partials[2 b + i].
+__global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, const float *depth,
+                                                   const float *sil, const float *obs_rgb,
+                                                   const float *obs_depth, const uint8_t *visible,
+                                                   float sil_min, int rgb_needs_depth, float gc,
+                                                   float gd, float *d_rgb, float *d_depth,
+                                                   double *partials) {
+    __shared__ double s_sum[2][8];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double sc = 0.0, sd = 0.0;
+    if (p < P) {
+        const bool valid = valid_depth(obs_depth[p]);
+        const bool covered = !(sil_min >= 0.f) || sil[p] > sil_min;
+        const bool vis = visible == nullptr || visible[p] != 0;
+        const bool m_d = valid && covered && vis;
+        const bool m_c = covered && vis && (!rgb_needs_depth || valid);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float r = rgb[c * P + p], o = obs_rgb[c * P + p];
+            if (m_c) sc += fabs((double)r - (double)o);
+            if (d_rgb) d_rgb[c * P + p] = m_c ? gc * sign_of(r - o) : 0.f;
+        }
+        const float r = depth[p], o = obs_depth[p];
+        if (m_d) sd = fabs((double)r - (double)o);
+        if (d_depth) d_depth[p] = m_d ? gd * sign_of(r - o) : 0.f;
+    }
+    if (!partials) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_sum[0][warp] = sc;
+        s_sum[1][warp] = sd;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += s_sum[threadIdx.x][w];
+        partials[2 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// One block: fixed-order sums of the per-block partials, then
+// L = wc * sum_c + wd * sum_d.
+__global__ void __launch_bounds__(1024) k_sum_partials(const double *partials, int n_blocks,
+                                                       double wc, double wd, double *loss) {
+    __shared__ double s[2][1024];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
+        a += partials[2 * i];
+        b += partials[2 * i + 1];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + h];
+            s[1][threadIdx.x] += s[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = __dadd_rn(__dmul_rn(wc, s[0][0]), __dmul_rn(wd, s[1][0]));
+}
+
+}  // namespace vt

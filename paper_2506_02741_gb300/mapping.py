@@ -6,9 +6,9 @@ section and minimising the L1 terms of Eq. 2,
 
 with U masking pixels without valid depth.  The SSIM term of Eq. 2 is not
 part of this driver.  The render and its attribute gradient run in the vtsplat
-kernels; the loss gradient and the Adam step (learning rates of the
-supplementary: colour 0.0025, radius 0.005, opacity 0.05) are torch ops on
-the device.
+kernels, the loss and its image gradient in one kernel (vt_masked_l1); the
+Adam step (learning rates of the supplementary: colour 0.0025, radius 0.005,
+opacity 0.05) is a torch fused optimiser on the device.
 
 The learning rates apply, as in the 3D Gaussian splatting family the paper
 builds on, to logit(opacity) and log(radius) (a reading: the paper gives the
@@ -51,26 +51,23 @@ class SectionMapper:
         self.rgb = torch.empty(3, self.H, self.W, device=dev)
         self.depth = torch.empty(self.H, self.W, device=dev)
         self.sil = torch.empty(self.H, self.W, device=dev)
-        self.loss = torch.zeros((), device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.g_rgb = torch.zeros(3, self.H, self.W, device=dev)
+        self.g_depth = torch.zeros(self.H, self.W, device=dev)
 
     def step(self, view: int):
         """One mapping iteration rendering from section view ``view``."""
         pose = self.sec.poses[view]
         K = self.sec.K
         self.R.render([self.sec], pose, K, self.W, self.H, self.rgb, self.depth, self.sil)
-        P = float(self.W * self.H)
-        V = self.rgb_obs[view]
-        D = self.depth_obs[view]
-        U = (D > 0).float()
-        dr = self.rgb - V
-        dd = self.depth - D
-        self.loss = self.rho * dr.abs().sum() / (3 * P) + self.sigma * (dd.abs() * U).sum() / P
-        g_rgb = (torch.sign(dr) * (self.rho / (3 * P))).contiguous()
-        g_d = (torch.sign(dd) * U * (self.sigma / P)).contiguous()
+        self.R.masked_l1(self.rgb, self.depth, None, self.rgb_obs[view], self.depth_obs[view],
+                         self.rho, self.sigma, d_rgb=self.g_rgb, d_depth=self.g_depth,
+                         loss=self.loss)
         self.master[0].grad.zero_()
         self.d_o.zero_()
         self.d_r.zero_()
-        self.R.backward(g_rgb, g_d, None, attr_grads=[(self.master[0].grad, self.d_o, self.d_r)])
+        self.R.backward(self.g_rgb, self.g_depth, None,
+                        attr_grads=[(self.master[0].grad, self.d_o, self.d_r)])
         with torch.no_grad():
             o = torch.sigmoid(self.master[1])
             r = torch.exp(self.master[2])

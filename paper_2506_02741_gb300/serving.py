@@ -59,7 +59,9 @@ class _Work:
         self.depth = torch.empty(H, W, device=dev)
         self.sil = torch.empty(H, W, device=dev)
         self.d_twist = torch.zeros(6, dtype=torch.float64, device=dev)
-        self.d_mat = torch.zeros(12, dtype=torch.float64, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.g_rgb = torch.zeros(3, H, W, device=dev)
+        self.g_depth = torch.zeros(H, W, device=dev)
         self.obs_rgb, self.obs_depth = server.observations[bucket]
         self.host = torch.empty((3, H, W) if kind == "render" else (6,),
                                 dtype=torch.float32 if kind == "render" else torch.float64
@@ -69,13 +71,12 @@ class _Work:
     def run(self):
         R = self.slot.renderer
         R.render([self.sec], self.pose, self.K, self.W, self.H, self.rgb, self.depth, self.sil)
-        if self.kind == "track":
-            P = float(self.W * self.H)
-            mask = ((self.obs_depth > 0) & (self.sil > 0.99)).float()
-            g_rgb = (torch.sign(self.rgb - self.obs_rgb) * mask * (0.5 / (3 * P))).contiguous()
-            g_d = (torch.sign(self.depth - self.obs_depth) * mask * (0.025 / P)).contiguous()
+        if self.kind == "track":   # Eq. 1 masked L1 (alpha 0.5, beta 0.025), pose gradient
+            R.masked_l1(self.rgb, self.depth, self.sil, self.obs_rgb, self.obs_depth, 0.5, 0.025,
+                        sil_min=0.99, rgb_needs_depth=True, d_rgb=self.g_rgb,
+                        d_depth=self.g_depth, loss=self.loss)
             self.d_twist.zero_()
-            R.backward(g_rgb, g_d, None, pose_grad=True, d_twist=self.d_twist, d_mat=self.d_mat)
+            R.backward(self.g_rgb, self.g_depth, None, pose_grad=True, d_twist=self.d_twist)
 
 
 class _Slot:

@@ -1,0 +1,140 @@
+"""Loss inputs through the C ABI against the oracle: the visibility check of
+Sec. 3.3 (bit-exact masks: both sides decide in FP64 with the same operation
+order) and the masked L1 terms of Eq. 1 / Eq. 2 (gradients exact, loss to FP64
+summation order)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_02741_gb300 import api
+from paper_2506_02741_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _room(K, Kv, idx=(0, 10, 20), cur=29):
+    """Current frame (intrinsics K) and three section views (intrinsics Kv)
+    of the seeded room along the seeded trajectory."""
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(cur + 1)
+    fc = syn.render_frames(room, K, [path[cur]])
+    fv = syn.render_frames(room, Kv, [path[i] for i in idx])
+    views = [(fv.depth[k], Kv.astuple(), path[i]) for k, i in enumerate(idx)]
+    return fc.depth[0], path[cur], views
+
+
+CASES = {
+    "tiny_64x48": (syn.TINY, syn.TINY),
+    "ragged_37x23_views_50x30": (syn.scaled_intrinsics(37, 23), syn.scaled_intrinsics(50, 30)),
+    "vga_640x480": (syn.VGA, syn.VGA),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_visibility_bit_exact(dev, case):
+    K, Kv = CASES[case]
+    depth, pose, views = _room(K, Kv)
+    depth = depth.copy()
+    depth[0, :3] = 0.0                      # invalid pixels of the current frame
+    depth[-1, -1] = np.nan
+    views[1][0][2, :] = 0.0                 # an invalid row in one view
+    want = oracle.visibility(depth, K.astuple(), pose, views)
+    assert 0.02 < want.mean() < 0.999
+    gv = [(torch.from_numpy(np.ascontiguousarray(d)).to(dev), k, api.pose12(p, dev))
+          for d, k, p in views]
+    got = api.visibility(torch.from_numpy(depth).to(dev), K.astuple(), api.pose12(pose, dev), gv)
+    assert np.array_equal(got.cpu().numpy().astype(bool), want)
+    # one view at a time reproduces each member of the union
+    for v, g in zip(views, gv):
+        w1 = oracle.visibility(depth, K.astuple(), pose, [v])
+        g1 = api.visibility(torch.from_numpy(depth).to(dev), K.astuple(), api.pose12(pose, dev), [g])
+        assert np.array_equal(g1.cpu().numpy().astype(bool), w1)
+
+
+def _images(rng, H, W):
+    rgb = rng.random((3, H, W)).astype(np.float32)
+    obs = rng.random((3, H, W)).astype(np.float32)
+    dep = (0.5 + 3 * rng.random((H, W))).astype(np.float32)
+    od = (0.5 + 3 * rng.random((H, W))).astype(np.float32)
+    sil = rng.random((H, W)).astype(np.float32)
+    sil[rng.random((H, W)) < 0.3] = np.float32(0.99)       # exactly at the threshold
+    od[rng.random((H, W)) < 0.05] = 0.0
+    od[rng.random((H, W)) < 0.02] = np.nan
+    obs[:, 1, 1] = rgb[:, 1, 1]                             # zero residuals
+    od[2, 2] = dep[2, 2]
+    vis = rng.random((H, W)) < 0.8
+    return rgb, dep, sil, obs, od, vis
+
+
+@pytest.mark.parametrize("H, W", [(23, 37), (480, 640), (1, 1)])
+@pytest.mark.parametrize("form", ["eq1_visible", "eq1", "eq2"])
+def test_masked_l1_matches_oracle(dev, H, W, form):
+    rng = np.random.default_rng(H * 1000 + W)
+    if H < 3:
+        rgb, dep, sil, obs, od, vis = (a[..., :H, :W] for a in _images(rng, 3, 3))
+        rgb, dep, sil, obs, od, vis = (np.ascontiguousarray(a) for a in (rgb, dep, sil, obs, od, vis))
+    else:
+        rgb, dep, sil, obs, od, vis = _images(rng, H, W)
+    kw = {"eq1_visible": dict(w_rgb=0.5, w_depth=0.025, sil_min=0.99, rgb_needs_depth=True),
+          "eq1": dict(w_rgb=0.5, w_depth=0.025, sil_min=0.99, rgb_needs_depth=True),
+          "eq2": dict(w_rgb=0.8, w_depth=1.0, sil_min=-1.0, rgb_needs_depth=False)}[form]
+    v = vis if form == "eq1_visible" else None
+    L, gr, gd = oracle.masked_l1(rgb, dep, sil, obs, od, visible=v, **kw)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    R = api.Renderer()
+    loss, d_rgb, d_depth = R.masked_l1(t(rgb), t(dep), t(sil) if kw["sil_min"] >= 0 else None,
+                                       t(obs), t(od), visible=None if v is None else t(v.astype(np.uint8)),
+                                       **kw)
+    torch.cuda.synchronize()
+    assert np.array_equal(d_rgb.cpu().numpy(), gr.astype(np.float32))
+    assert np.array_equal(d_depth.cpu().numpy(), gd.astype(np.float32))
+    assert float(loss.item()) == pytest.approx(L, rel=1e-12, abs=1e-300)
+
+
+def test_loss_inputs_reject_bad_arguments(dev):
+    R = api.Renderer()
+    z = torch.zeros(4, 5, device=dev)
+    z3 = torch.zeros(3, 4, 5, device=dev)
+    with pytest.raises(api.L.VTError):
+        R.masked_l1(z3, z, None, z3, z, 0.5, 0.025, sil_min=0.99)     # needs the silhouette
+    p = api.pose12(syn.identity_pose(), dev)
+    with pytest.raises(ValueError):
+        api.visibility(z, syn.TINY.astuple(), p, [])
+    with pytest.raises(api.L.VTError):
+        api.visibility(z, (0.0, 1.0, 2.0, 2.0), p, [(z, syn.TINY.astuple(), p)])
+
+
+@pytest.mark.parametrize("lr_rot", [4e-4, 0.0])
+def test_pose_adam_matches_reference(dev, lr_rot):
+    """Five Adam steps on the pose against the float64 reference (lr_rot = 0
+    takes the small-angle branch of the exponential); the gradient buffer is
+    zeroed after each step."""
+    from oracle import pose as op
+    rng = np.random.default_rng(11)
+    P = syn.perturb_pose(syn.identity_pose(), rng, 0.3, 20.0)
+    lr = [2e-3] * 3 + [lr_rot] * 3
+    pose = api.pose12(P, dev)
+    state = torch.zeros(13, dtype=torch.float64, device=dev)
+    d_tw = torch.zeros(6, dtype=torch.float64, device=dev)
+    m, v, t = np.zeros(6), np.zeros(6), 0.0
+    for _ in range(5):
+        g = rng.normal(0, 1, 6) * np.array([1, 10, 0.1, 1, 5, 0.5])
+        d_tw.copy_(torch.from_numpy(g))
+        api.pose_adam(pose, d_tw, state, lr)
+        P, m, v, t = op.adam_pose_step(P, g, m, v, t, lr)
+        torch.cuda.synchronize()
+        assert not d_tw.any()
+        np.testing.assert_allclose(api.matrix_of(pose), P, rtol=1e-12, atol=1e-14)
+        st = state.cpu().numpy()
+        np.testing.assert_allclose(st[:6], m, rtol=1e-13)
+        np.testing.assert_allclose(st[6:12], v, rtol=1e-13)
+        assert st[12] == t

@@ -1,0 +1,43 @@
+"""Pins of the tracking optimiser reference (oracle/pose.py): closed forms
+of the SE(3) exponential and of Adam's first step."""
+
+import numpy as np
+import pytest
+
+from oracle import pose as op
+
+
+def test_exp_of_translation_and_rotation():
+    E = op.se3_exp([0.1, -0.2, 0.3, 0.0, 0.0, 0.0])
+    np.testing.assert_allclose(E, np.hstack([np.eye(3), [[0.1], [-0.2], [0.3]]]), atol=1e-15)
+    th = 0.3
+    E = op.se3_exp([0.0, 0.0, 0.0, 0.0, 0.0, th])
+    c, s = np.cos(th), np.sin(th)
+    np.testing.assert_allclose(E[:, :3], [[c, -s, 0], [s, c, 0], [0, 0, 1]], atol=1e-15)
+    np.testing.assert_allclose(E[:, 3], 0.0, atol=1e-15)
+
+
+def test_exp_inverse_and_screw_translation():
+    """Exp(xi) Exp(-xi) = I; a screw about z moves a point on the axis by
+    rho_z only."""
+    xi = np.array([0.05, -0.02, 0.07, 0.1, -0.3, 0.2])
+    A, B = op.se3_exp(xi), op.se3_exp(-xi)
+    np.testing.assert_allclose(A[:, :3] @ B[:, :3], np.eye(3), atol=1e-14)
+    np.testing.assert_allclose(A[:, :3] @ B[:, 3] + A[:, 3], 0.0, atol=1e-14)
+    E = op.se3_exp([0.0, 0.0, 0.4, 0.0, 0.0, 1.1])
+    np.testing.assert_allclose(E[:, 3], [0.0, 0.0, 0.4], atol=1e-15)
+
+
+def test_adam_first_step_is_sign_step():
+    """At t = 1 the bias-corrected moments are g and g^2, so the step is
+    lr * g / (|g| + eps) = lr * sign(g) up to eps."""
+    P = np.hstack([np.eye(3), [[1.0], [2.0], [3.0]]])
+    g = np.array([0.3, -2.0, 1e-3, -0.5, 0.25, 4.0])
+    lr = np.array([2e-3] * 3 + [4e-4] * 3)
+    Pn, m, v, t = op.adam_pose_step(P, g, np.zeros(6), np.zeros(6), 0.0, lr, eps=0.0)
+    assert t == 1.0
+    np.testing.assert_allclose(m, 0.1 * g, rtol=1e-15)
+    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-14)   # 1 - 0.999 rounds
+    E = op.se3_exp(-lr * np.sign(g))
+    np.testing.assert_allclose(Pn[:, :3], E[:, :3], atol=1e-15)
+    np.testing.assert_allclose(Pn[:, 3], E[:, 3] + P[:, 3], atol=1e-15)
