@@ -260,6 +260,34 @@ vt_status vt_pose_adam(vt_ctx *ctx, double *pose12, double *d_twist, double *sta
                        const double *lr, double beta1, double beta2, double eps,
                        vt_stream stream);
 
+/* Adam hyper-parameters of the mapping step: learning rates of the five
+ * parameter planes (c0, c1, c2, logit o, log r; the supplementary gives
+ * colour 0.0025, opacity 0.05, radius 0.005) and the moment decays. */
+typedef struct {
+    float lr[5];
+    float beta1, beta2, eps;
+} vt_adam_params;
+
+/* One Adam step on the attributes of the n Gaussians of a section being
+ * mapped (Sec. 3.4 learns colour, opacity and radius), taken on FP32
+ * parameters theta = (c0, c1, c2, logit o, log r) (a reading: the paper
+ * gives the rates, not the parametrisation):
+ *   g = (dL/dc, dL/do o (1 - o), dL/dr r)     (chain rule at the current theta)
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   theta -= lr m / (1 - b1^t) / (sqrt(v) / sqrt(1 - b2^t) + eps),
+ * then the activated values (c, sigmoid, exp) are written to the section's
+ * storage colour (n x 3), opacity, radius in precision prec, and the
+ * gradients d_colour (n x 3), d_opacity, d_radius (device float32, as
+ * accumulated by vt_render_backward) are zeroed.  theta, m, v: device
+ * float32, 5 planes of n (plane k = parameter k of every Gaussian); m and v
+ * start at zero.  step: device, 3 doubles, zero-initialised: the step count
+ * t (incremented here) and the two bias corrections.  ctx may be NULL; when
+ * given it only records the launches. */
+vt_status vt_attr_adam(vt_ctx *ctx, int64_t n, float *theta, float *m, float *v, double *step,
+                       float *d_colour, float *d_opacity, float *d_radius, vt_precision prec,
+                       void *colour, void *opacity, void *radius, vt_adam_params p,
+                       vt_stream stream);
+
 /* Per-kernel timing of the context's launches with CUDA events on the
  * launching stream (enable != 0).  vt_ctx_timing synchronises the stream
  * and writes, for up to n_max kernels, their names (static strings), the

@@ -41,3 +41,30 @@ def adam_pose_step(pose, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-15):
     R = P[:, :3] @ E[:, :3]
     tr = P[:, :3] @ E[:, 3] + P[:, 3]
     return np.hstack([R, tr[:, None]]), m, v, t
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def attr_adam_step(theta, m, v, t, d_colour, d_opacity, d_radius, lr, beta1=0.9, beta2=0.999,
+                   eps=1e-8):
+    """One Adam step of the mapping optimiser on theta (5, n) =
+    (c0, c1, c2, logit o, log r): the gradients with respect to the activated
+    values (d_colour (n, 3), d_opacity (n,), d_radius (n,)) are taken to theta
+    by the chain rule at the current theta,
+        m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+        theta -= lr m / (1 - b1^t) / (sqrt(v) / sqrt(1 - b2^t) + eps).
+    Returns (theta, m, v, t, colour (n, 3), opacity (n,), radius (n,))."""
+    theta = np.asarray(theta, np.float64)
+    o = sigmoid(theta[3])
+    r = np.exp(theta[4])
+    g = np.stack([d_colour[:, 0], d_colour[:, 1], d_colour[:, 2],
+                  np.asarray(d_opacity, np.float64) * o * (1 - o),
+                  np.asarray(d_radius, np.float64) * r]).astype(np.float64)
+    t = t + 1.0
+    m = beta1 * np.asarray(m, np.float64) + (1 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1 - beta2) * g * g
+    lr = np.asarray(lr, np.float64)[:, None]
+    theta = theta - lr * (m / (1 - beta1 ** t)) / (np.sqrt(v) / np.sqrt(1 - beta2 ** t) + eps)
+    return theta, m, v, t, theta[:3].T.copy(), sigmoid(theta[3]), np.exp(theta[4])

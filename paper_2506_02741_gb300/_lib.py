@@ -46,6 +46,11 @@ class L1WeightsC(C.Structure):
                 ("rgb_needs_depth", C.c_int32)]
 
 
+class AdamParamsC(C.Structure):
+    _fields_ = [("lr", C.c_float * 5), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float)]
+
+
 MAX_VIS_VIEWS = 8
 
 
@@ -83,6 +88,8 @@ def _declare(L):
                                    _P, _P, _P, _P]),
         "vt_pose_adam": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double), C.c_double,
                                    C.c_double, C.c_double, _P]),
+        "vt_attr_adam": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P,
+                                   _P, AdamParamsC, _P]),
         "vt_ctx_set_timing": (C.c_int, [_P, C.c_int32]),
         "vt_ctx_timing": (C.c_int32, [_P, _P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_double), C.c_int32, C.c_int32]),
@@ -108,7 +115,8 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_render_backward", "vt_ctx_set_timing", "vt_ctx_timing", "vt_ctx_launch_count",
            "vt_ctx_debug_copy", "vt_last_error", "vt_version", "vt_ctx_set_list_capacity",
            "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists",
-           "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam"]
+           "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam",
+           "vt_attr_adam"]
 
 
 def lib_path() -> str:

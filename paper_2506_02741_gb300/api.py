@@ -197,6 +197,32 @@ def pose_adam(pose: torch.Tensor, d_twist: torch.Tensor, state: torch.Tensor, lr
             "vt_pose_adam")
 
 
+def attr_adam(section, theta: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+              step: torch.Tensor, d_colour: torch.Tensor, d_opacity: torch.Tensor,
+              d_radius: torch.Tensor, lr, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8, renderer=None, stream=None):
+    """One Adam step on the section's attributes in the parametrisation
+    theta = (c0, c1, c2, logit o, log r) ((5, n) float32; m, v alike; step
+    (3,) float64 zero-initialised); the section's colour / opacity / radius
+    storage is overwritten with the activated values and the gradients
+    (d_colour (n, 3), d_opacity, d_radius float32) are zeroed.  lr: five
+    rates (one per parameter plane)."""
+    n = section.n
+    for name, t in (("theta", theta), ("m", m), ("v", v)):
+        _cuda(t, torch.float32, name, (5, n))
+    _cuda(step, torch.float64, "step", (3,))
+    _cuda(d_colour, torch.float32, "d_colour", (n, 3))
+    _cuda(d_opacity, torch.float32, "d_opacity", (n,))
+    _cuda(d_radius, torch.float32, "d_radius", (n,))
+    p = L.AdamParamsC((C.c_float * 5)(*[float(x) for x in lr]), float(beta1), float(beta2),
+                      float(eps))
+    ctx = renderer._ctx if renderer is not None else None
+    L.check(L.lib().vt_attr_adam(ctx, n, _ptr(theta), _ptr(m), _ptr(v), _ptr(step),
+                                 _ptr(d_colour), _ptr(d_opacity), _ptr(d_radius), section.prec,
+                                 _ptr(section.colour), _ptr(section.opacity),
+                                 _ptr(section.radius), p, _stream(stream)), "vt_attr_adam")
+
+
 class Renderer:
     """Owns one vt_ctx (the library's render workspace) on the current device."""
 

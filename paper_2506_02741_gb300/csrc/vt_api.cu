@@ -51,14 +51,15 @@ constexpr size_t kSortSmemBigBytes =
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
-    K_NUM
+    K_ADAM_COUNT, K_ATTR_ADAM, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
                                    "k_composite_bwd", "k_pose_finalize", "k_backproject",
                                    "k_section_init",  "k_count_valid",   "k_composite_bwd_list",
                                    "k_sort_tiles_long", "k_attr_scatter", "k_masked_l1",
-                                   "k_sum_partials",  "k_pose_adam"};
+                                   "k_sum_partials",  "k_pose_adam",     "k_adam_step_count",
+                                   "k_attr_adam"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -698,6 +699,56 @@ vt_status vt_pose_adam(vt_ctx *c, double *pose12, double *d_twist, double *state
         k_pose_adam<<<1, 32, 0, stream>>>(pose12, d_twist, state, prm);
     }
     VT_CUDA(cudaGetLastError(), "vt_pose_adam launch");
+    return VT_OK;
+}
+
+vt_status vt_attr_adam(vt_ctx *c, int64_t n, float *theta, float *m, float *v, double *step,
+                       float *d_colour, float *d_opacity, float *d_radius, vt_precision prec,
+                       void *colour, void *opacity, void *radius, vt_adam_params p,
+                       vt_stream stream) {
+    if (n < 0) return fail(VT_ERR_INVALID_ARG, "vt_attr_adam: n < 0");
+    if (prec != VT_F32 && prec != VT_F16)
+        return fail(VT_ERR_INVALID_ARG, "vt_attr_adam: unknown precision %d", (int)prec);
+    if (!step) return fail(VT_ERR_INVALID_ARG, "vt_attr_adam: NULL step");
+    if (n > 0 && (!theta || !m || !v || !d_colour || !d_opacity || !d_radius || !colour ||
+                  !opacity || !radius))
+        return fail(VT_ERR_INVALID_ARG, "vt_attr_adam: NULL array");
+    AttrAdamParams prm{};
+    for (int k = 0; k < 5; ++k) {
+        if (!std::isfinite(p.lr[k]) || p.lr[k] < 0.f)
+            return fail(VT_ERR_INVALID_ARG, "vt_attr_adam: learning rates must be finite, >= 0");
+        prm.lr[k] = p.lr[k];
+    }
+    if (!(p.beta1 >= 0.f && p.beta1 < 1.f && p.beta2 >= 0.f && p.beta2 < 1.f && p.eps >= 0.f &&
+          std::isfinite(p.eps)))
+        return fail(VT_ERR_INVALID_ARG, "vt_attr_adam: need 0 <= beta < 1 and finite eps >= 0");
+    prm.beta1 = p.beta1;
+    prm.beta2 = p.beta2;
+    prm.eps = p.eps;
+    auto launch = [&]() {
+        k_adam_step_count<<<1, 32, 0, stream>>>(step, (double)p.beta1, (double)p.beta2);
+    };
+    if (c) {
+        LaunchScope ls(c, K_ADAM_COUNT, stream);
+        launch();
+    } else {
+        launch();
+    }
+    if (n > 0) {
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        auto upd = [&]() {
+            k_attr_adam<<<nb, 256, 0, stream>>>(n, theta, m, v, step, d_colour, d_opacity,
+                                                d_radius, (int)prec, colour, opacity, radius,
+                                                prm);
+        };
+        if (c) {
+            LaunchScope ls(c, K_ATTR_ADAM, stream);
+            upd();
+        } else {
+            upd();
+        }
+    }
+    VT_CUDA(cudaGetLastError(), "vt_attr_adam launch");
     return VT_OK;
 }
 

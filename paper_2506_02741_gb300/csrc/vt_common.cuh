@@ -259,6 +259,16 @@ struct PoseAdamParams {
     double beta1, beta2, eps;
 };
 __global__ void k_pose_adam(double *pose, double *d_twist, double *state, PoseAdamParams prm);
+
+// Mapping optimiser step (vt_pose.cu).
+struct AttrAdamParams {
+    float lr[5];
+    float beta1, beta2, eps;
+};
+__global__ void k_adam_step_count(double *step, double beta1, double beta2);
+__global__ void k_attr_adam(int64_t n, float *theta, float *m, float *v, const double *step,
+                            float *d_colour, float *d_opacity, float *d_radius, int prec,
+                            void *colour, void *opacity, void *radius, AttrAdamParams prm);
 __global__ void k_pose_finalize(const double *partials, int n_parts, const double *pose_copy,
                                 double *d_twist, double *d_mat);
 __global__ void k_count_valid(const float *depth, int64_t total, uint32_t *block_counts);

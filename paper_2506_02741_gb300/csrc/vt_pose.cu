@@ -1,9 +1,12 @@
-// Tracking optimiser step (Sec. 3.3: the pose of the latest frame is
-// optimised with Adam, learning rates lr_rot / lr_trans of the
-// supplementary): one thread updates the Adam moments from the twist
-// gradient, forms the step and retracts the pose by right-multiplication
-// with the SE(3) exponential.  FP64 throughout; a single launch replaces the
-// few dozen element-wise ops this takes in a tensor library.
+// Optimiser steps of tracking and mapping.
+//  - Tracking (Sec. 3.3: the pose of the latest frame is optimised with Adam,
+//    learning rates lr_rot / lr_trans of the supplementary): one thread
+//    updates the Adam moments from the twist gradient, forms the step and
+//    retracts the pose by right-multiplication with the SE(3) exponential.
+//    FP64 throughout; one launch replaces a few dozen tensor ops.
+//  - Mapping (Sec. 3.4 learns colour, opacity and radius; supplementary
+//    learning rates): one thread per Gaussian, Adam on (c, logit o, log r)
+//    in FP32, storage written back in the section's precision.
 #include "vt_common.cuh"
 
 namespace vt {
@@ -60,6 +63,78 @@ __global__ void k_pose_adam(double *pose, double *d_twist, double *state, PoseAd
     }
     for (int k = 0; k < 9; ++k) pose[k] = Rn[k];
     for (int i = 0; i < 3; ++i) pose[9 + i] = tn[i];
+}
+
+// Step counter of the attribute optimiser: step[0] = t (incremented),
+// step[1] = 1 / (1 - b1^t), step[2] = 1 / sqrt(1 - b2^t).
+__global__ void k_adam_step_count(double *step, double beta1, double beta2) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double t = step[0] + 1.0;
+    step[0] = t;
+    step[1] = 1.0 / (1.0 - pow(beta1, t));
+    step[2] = 1.0 / sqrt(1.0 - pow(beta2, t));
+}
+
+__device__ __forceinline__ void st_any(void *p, int prec, int64_t i, float x) {
+    if (prec == VT_F16)
+        static_cast<__half *>(p)[i] = __float2half_rn(x);
+    else
+        static_cast<float *>(p)[i] = x;
+}
+
+// One thread per Gaussian: chain rule to (c, logit o, log r), Adam on the
+// five FP32 parameters (planes of theta / m / v), activated values written to
+// the section's storage, gradients zeroed.  HBM-bound (~180 B per Gaussian):
+// every input is loaded before the first store so that the loads overlap.
+__global__ void __launch_bounds__(256) k_attr_adam(int64_t n, float *__restrict__ theta,
+                                                   float *__restrict__ m, float *__restrict__ v,
+                                                   const double *__restrict__ step,
+                                                   float *__restrict__ d_colour,
+                                                   float *__restrict__ d_opacity,
+                                                   float *__restrict__ d_radius, int prec,
+                                                   void *__restrict__ colour,
+                                                   void *__restrict__ opacity,
+                                                   void *__restrict__ radius, AttrAdamParams prm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float th[5], g[5], mk[5], vk[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        th[k] = theta[k * n + i];
+        mk[k] = m[k * n + i];
+        vk[k] = v[k * n + i];
+    }
+    g[0] = d_colour[3 * i];
+    g[1] = d_colour[3 * i + 1];
+    g[2] = d_colour[3 * i + 2];
+    g[3] = d_opacity[i];
+    g[4] = d_radius[i];
+    const float s1 = (float)step[1], s2 = (float)step[2];
+    const float o = 1.f / (1.f + expf(-th[3]));
+    g[3] *= o * (1.f - o);
+    g[4] *= expf(th[4]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        mk[k] = prm.beta1 * mk[k] + (1.f - prm.beta1) * g[k];
+        vk[k] = prm.beta2 * vk[k] + (1.f - prm.beta2) * g[k] * g[k];
+        th[k] -= prm.lr[k] * s1 * mk[k] / (sqrtf(vk[k]) * s2 + prm.eps);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        theta[k * n + i] = th[k];
+        m[k * n + i] = mk[k];
+        v[k * n + i] = vk[k];
+    }
+    d_colour[3 * i] = 0.f;
+    d_colour[3 * i + 1] = 0.f;
+    d_colour[3 * i + 2] = 0.f;
+    d_opacity[i] = 0.f;
+    d_radius[i] = 0.f;
+    st_any(colour, prec, 3 * i, th[0]);
+    st_any(colour, prec, 3 * i + 1, th[1]);
+    st_any(colour, prec, 3 * i + 2, th[2]);
+    st_any(opacity, prec, i, 1.f / (1.f + expf(-th[3])));
+    st_any(radius, prec, i, expf(th[4]));
 }
 
 }  // namespace vt

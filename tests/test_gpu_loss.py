@@ -118,7 +118,7 @@ def test_pose_adam_matches_reference(dev, lr_rot):
     """Five Adam steps on the pose against the float64 reference (lr_rot = 0
     takes the small-angle branch of the exponential); the gradient buffer is
     zeroed after each step."""
-    from oracle import pose as op
+    from oracle import optim as op
     rng = np.random.default_rng(11)
     P = syn.perturb_pose(syn.identity_pose(), rng, 0.3, 20.0)
     lr = [2e-3] * 3 + [lr_rot] * 3
@@ -138,3 +138,66 @@ def test_pose_adam_matches_reference(dev, lr_rot):
         np.testing.assert_allclose(st[:6], m, rtol=1e-13)
         np.testing.assert_allclose(st[6:12], v, rtol=1e-13)
         assert st[12] == t
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_attr_adam_matches_reference(dev, prec):
+    """Three fused Adam steps on a section's attributes against the float64
+    reference (FP32 arithmetic: 1e-5 relative on the parameters); storage
+    written in the section's precision; gradients zeroed."""
+    from oracle import optim as op
+    rng = np.random.default_rng(5)
+    n = 1000                                    # not a multiple of the block size
+    dt = torch.float16 if prec == "f16" else torch.float32
+    col = rng.random((n, 3)).astype(np.float32)
+    opa = (0.05 + 0.9 * rng.random(n)).astype(np.float32)
+    rad = (0.002 + 0.01 * rng.random(n)).astype(np.float32)
+    sec = api.Section(poses=torch.zeros(1, 12, dtype=torch.float64, device=dev),
+                      depth=torch.ones(1, 1, n, device=dev), K=(1.0, 1.0, 0.0, 0.0),
+                      src=torch.arange(n, dtype=torch.int32, device=dev),
+                      colour=torch.from_numpy(col).to(dev, dt),
+                      opacity=torch.from_numpy(opa).to(dev, dt),
+                      radius=torch.from_numpy(rad).to(dev, dt))
+    theta = np.stack([col[:, 0], col[:, 1], col[:, 2], np.log(opa / (1 - opa)), np.log(rad)])
+    th_d = torch.from_numpy(theta.astype(np.float32)).to(dev)
+    m_d, v_d = torch.zeros(5, n, device=dev), torch.zeros(5, n, device=dev)
+    st = torch.zeros(3, dtype=torch.float64, device=dev)
+    th, m, v, t = theta.astype(np.float32).astype(np.float64), np.zeros((5, n)), np.zeros((5, n)), 0.0
+    lr = [0.0025] * 3 + [0.05, 0.005]
+    for _ in range(3):
+        dc = rng.normal(0, 1e-3, (n, 3)).astype(np.float32)
+        do = rng.normal(0, 1e-3, n).astype(np.float32)
+        dr = rng.normal(0, 1e-1, n).astype(np.float32)
+        gdc, gdo, gdr = (torch.from_numpy(a).to(dev) for a in (dc, do, dr))
+        api.attr_adam(sec, th_d, m_d, v_d, st, gdc, gdo, gdr, lr)
+        th, m, v, t, c_ref, o_ref, r_ref = op.attr_adam_step(th, m, v, t, dc, do, dr, lr)
+        torch.cuda.synchronize()
+        assert not gdc.any() and not gdo.any() and not gdr.any()
+        np.testing.assert_allclose(th_d.cpu().numpy(), th, rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(m_d.cpu().numpy(), m, rtol=1e-4, atol=1e-12)
+        np.testing.assert_allclose(v_d.cpu().numpy(), v, rtol=1e-4, atol=1e-16)
+        tol = 1e-3 if prec == "f16" else 1e-5
+        np.testing.assert_allclose(sec.colour.float().cpu().numpy(), c_ref, rtol=tol, atol=1e-6)
+        np.testing.assert_allclose(sec.opacity.float().cpu().numpy(), o_ref, rtol=tol)
+        np.testing.assert_allclose(sec.radius.float().cpu().numpy(), r_ref, rtol=tol)
+        assert st[0].item() == t
+
+
+def test_mapper_reduces_loss(dev):
+    """A few mapping iterations (render, fused loss, attribute backward, fused
+    Adam) on a perturbed section lower the Eq. 2 L1 loss."""
+    from paper_2506_02741_gb300.mapping import SectionMapper
+    K = syn.scaled_intrinsics(160, 120)
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(15)
+    keys = [path[i] for i in (0, 5, 10)]
+    fr = syn.render_frames(room, K, keys)
+    depth = torch.from_numpy(fr.depth).to(dev)
+    rgb = torch.from_numpy(fr.rgb).to(dev)
+    sec = api.Section.from_rgbd(depth, rgb, K.astuple(), np.stack(keys))
+    g = torch.Generator(device=dev).manual_seed(0)
+    sec.colour.copy_((sec.colour + 0.2 * torch.rand(sec.colour.shape, generator=g, device=dev)).clamp(0, 1))
+    R = api.Renderer()
+    mp = SectionMapper(R, sec, rgb)
+    losses = [float(mp.step(i % 3).item()) for i in range(30)]
+    assert losses[-1] < 0.8 * losses[0]

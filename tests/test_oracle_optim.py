@@ -1,10 +1,10 @@
-"""Pins of the tracking optimiser reference (oracle/pose.py): closed forms
+"""Pins of the optimiser references (oracle/optim.py): closed forms
 of the SE(3) exponential and of Adam's first step."""
 
 import numpy as np
 import pytest
 
-from oracle import pose as op
+from oracle import optim as op
 
 
 def test_exp_of_translation_and_rotation():
@@ -41,3 +41,28 @@ def test_adam_first_step_is_sign_step():
     E = op.se3_exp(-lr * np.sign(g))
     np.testing.assert_allclose(Pn[:, :3], E[:, :3], atol=1e-15)
     np.testing.assert_allclose(Pn[:, 3], E[:, 3] + P[:, 3], atol=1e-15)
+
+
+def test_attr_adam_first_step_and_chain_rule():
+    """First step: theta moves by lr * sign(g) (eps = 0) with g the chain-rule
+    gradient; a zero gradient leaves theta unchanged; the activated outputs
+    are sigmoid / exp of the new theta."""
+    rng = np.random.default_rng(0)
+    n = 7
+    theta = np.stack([rng.random(n), rng.random(n), rng.random(n),
+                      rng.normal(0, 1, n), np.log(0.01 + rng.random(n))])
+    dc = rng.normal(0, 1, (n, 3))
+    do = rng.normal(0, 1, n)
+    dr = rng.normal(0, 1, n)
+    dr[2] = 0.0
+    lr = [0.0025] * 3 + [0.05, 0.005]
+    th, m, v, t, col, op_, rad = op.attr_adam_step(theta, np.zeros((5, n)), np.zeros((5, n)),
+                                                   0.0, dc, do, dr, lr, eps=1e-300)
+    o = 1 / (1 + np.exp(-theta[3]))
+    g = np.stack([dc[:, 0], dc[:, 1], dc[:, 2], do * o * (1 - o), dr * np.exp(theta[4])])
+    np.testing.assert_allclose(th, theta - np.array(lr)[:, None] * np.sign(g), rtol=0,
+                               atol=1e-15)
+    assert th[4, 2] == theta[4, 2]     # zero gradient: 0 / (0 + eps)
+    np.testing.assert_allclose(op_, 1 / (1 + np.exp(-th[3])), rtol=1e-15)
+    np.testing.assert_allclose(rad, np.exp(th[4]), rtol=1e-15)
+    np.testing.assert_array_equal(col, th[:3].T)
