@@ -247,8 +247,8 @@ vt_status vt_masked_l1(vt_ctx *ctx, int32_t W, int32_t H, const float *rgb, cons
 /* One Adam step on the camera pose (Sec. 3.3 tracking optimises the pose of
  * the latest frame; the supplementary gives Adam learning rates lr_rot and
  * lr_trans).  With the twist gradient g = d_twist (device, 6 doubles, as
- * accumulated by vt_render_backward) and state (device, 13 doubles: m[6],
- * v[6], step count t, zero-initialised):
+ * accumulated by vt_render_backward) and state (device, 15 doubles: m[6],
+ * v[6], step count t, b1^t, b2^t; zero-initialised, zero again to restart):
  *   t += 1, m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
  *   s = lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
  *   pose12 (device) <- pose12 Exp(-s)  (right perturbation, xi = (rho, phi)),

@@ -185,11 +185,12 @@ def pose_adam(pose: torch.Tensor, d_twist: torch.Tensor, state: torch.Tensor, lr
               beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, renderer=None,
               stream=None):
     """One Adam step on the pose (12,) float64 from the twist gradient (6,)
-    float64 (zeroed afterwards), state (13,) float64 = (m, v, t); lr: six
+    float64 (zeroed afterwards), state (15,) float64 = (m, v, t, b1^t, b2^t),
+    zero-initialised; lr: six
     rates (rho then phi).  renderer (optional) records the launch."""
     _cuda(pose, torch.float64, "pose", (12,))
     _cuda(d_twist, torch.float64, "d_twist", (6,))
-    _cuda(state, torch.float64, "state", (13,))
+    _cuda(state, torch.float64, "state", (15,))
     rates = (C.c_double * 6)(*[float(x) for x in lr])
     ctx = renderer._ctx if renderer is not None else None
     L.check(L.lib().vt_pose_adam(ctx, _ptr(pose), _ptr(d_twist), _ptr(state), rates,

@@ -39,8 +39,15 @@ vt_status cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-// Tile lists up to kSortSmemN entries are sorted in shared memory by blocks
-// small enough for two per SM; longer ones (up to kSortSmemBig) by a second
+// Tile lists are sorted in shared memory by size class, each class by a
+// launch whose blocks hold just enough shared memory for its longest list, so
+// that short lists run several blocks per SM: (0, 2048], (2048, 4096],
+// (4096, kSortSmemN] on the caller's stream; the few longer ones (up to
+// kSortSmemBig in shared memory, beyond that in global memory) by a launch on
+// an auxiliary stream that overlaps the others.
+constexpr int kSortClassS = 2048, kSortClassM = 4096;
+constexpr size_t sort_smem_bytes(int n) { return 2 * (size_t)n * 8 + 16 * 256 * 4; }
+// (kept for the long-list launch and the attribute of the largest one)
 // launch with one large block per SM; longer still in global memory.
 constexpr int kSortSmemN = 6144;
 constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 16 * 256 * 4;
@@ -51,7 +58,7 @@ constexpr size_t kSortSmemBigBytes =
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
-    K_ADAM_COUNT, K_ATTR_ADAM, K_NUM
+    K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -59,7 +66,7 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "k_section_init",  "k_count_valid",   "k_composite_bwd_list",
                                    "k_sort_tiles_long", "k_attr_scatter", "k_masked_l1",
                                    "k_sum_partials",  "k_pose_adam",     "k_adam_step_count",
-                                   "k_attr_adam"};
+                                   "k_attr_adam",     "k_sort_tiles_mid", "k_sort_tiles_large"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -95,6 +102,9 @@ struct vt_ctx {
     TabRow *tab = nullptr;
     double *pose_partials = nullptr, *pose_copy = nullptr;
     uint32_t *blk_ovf = nullptr;      // list overflow flag per 8x4 pixel block
+    cudaStream_t aux = nullptr;       // auxiliary stream of the long-list sort
+    int n_sm = 1;                     // SMs of the device
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *loss_part = nullptr;      // masked-L1 block partials (separate allocation)
     int64_t loss_cap = 0;             // blocks they hold
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
@@ -298,6 +308,14 @@ vt_status vt_ctx_create(vt_ctx **ctx) {
     vt_ctx *c = new (std::nothrow) vt_ctx();
     if (!c) return fail(VT_ERR_OOM, "vt_ctx_create: out of host memory");
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        vt_ctx_destroy(c);
+        return fail(VT_ERR_CUDA, "vt_ctx_create: cannot create the auxiliary stream");
+    }
     *ctx = c;
     return VT_OK;
 }
@@ -313,6 +331,12 @@ void vt_ctx_destroy(vt_ctx *c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaStreamDestroy(c->aux);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -534,18 +558,38 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         k_emit<<<gblocks, 256, 0, stream>>>(total, c->info, cam, c->tile_cursor, c->bucket,
                                             c->status);
     }
+    // fork: the long lists sort on the auxiliary stream (works under graph
+    // capture too: the fork and join events make it a parallel branch)
+    VT_CUDA(cudaEventRecord(c->ev_fork, stream), "sort fork");
+    VT_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "sort fork");
     {
-        LaunchScope ls(c, K_SORT, stream);
-        k_sort_tiles<<<n_tiles, 512, kSortSmemBytes, stream>>>(c->tile_off, n_tiles, c->bucket,
-                                                               c->alt, c->sorted, c->status,
-                                                               kSortSmemN, 0, kSortSmemN);
-    }
-    {
-        LaunchScope ls(c, K_SORT_BIG, stream);
-        k_sort_tiles<<<n_tiles, 512, kSortSmemBigBytes, stream>>>(
+        LaunchScope ls(c, K_SORT_BIG, c->aux);
+        // one block per SM at most: these lists are few, and the launch must
+        // not hold every SM's shared memory while the others run
+        k_sort_tiles<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortSmemBig,
             kSortSmemN, 0x7fffffff);
     }
+    VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
+    {
+        LaunchScope ls(c, K_SORT, stream);
+        k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassS), stream>>>(
+            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortClassS, 0,
+            kSortClassS);
+    }
+    {
+        LaunchScope ls(c, K_SORT_M, stream);
+        k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
+            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortClassM,
+            kSortClassS, kSortClassM);
+    }
+    {
+        LaunchScope ls(c, K_SORT_L, stream);
+        k_sort_tiles<<<n_tiles, 512, kSortSmemBytes, stream>>>(
+            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortSmemN,
+            kSortClassM, kSortSmemN);
+    }
+    VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
     {
         LaunchScope ls(c, K_FWD, stream);
         k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(
@@ -696,7 +740,7 @@ vt_status vt_pose_adam(vt_ctx *c, double *pose12, double *d_twist, double *state
         LaunchScope ls(c, K_POSE_ADAM, stream);
         k_pose_adam<<<1, 32, 0, stream>>>(pose12, d_twist, state, prm);
     } else {
-        k_pose_adam<<<1, 32, 0, stream>>>(pose12, d_twist, state, prm);
+        k_pose_adam<<<1, 32, 0, stream>>>(pose12, d_twist, state, prm);   // one warp
     }
     VT_CUDA(cudaGetLastError(), "vt_pose_adam launch");
     return VT_OK;

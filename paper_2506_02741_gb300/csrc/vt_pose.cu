@@ -11,22 +11,32 @@
 
 namespace vt {
 
-// state: m[6], v[6], t.  lr: rho then phi.
+// One warp: lanes 0..5 update the moments of one twist component each, lane
+// 0 then forms the exponential and the retraction.  state: m[6], v[6], t,
+// b1^t, b2^t (running products instead of pow, which is slow in FP64).
+// lr: rho then phi.
 __global__ void k_pose_adam(double *pose, double *d_twist, double *state, PoseAdamParams prm) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double t = state[12] + 1.0;
-    state[12] = t;
-    const double c1 = 1.0 - pow(prm.beta1, t), c2 = 1.0 - pow(prm.beta2, t);
-    double xi[6];
-    for (int i = 0; i < 6; ++i) {
-        const double g = d_twist[i];
-        const double m = prm.beta1 * state[i] + (1.0 - prm.beta1) * g;
-        const double v = prm.beta2 * state[6 + i] + (1.0 - prm.beta2) * g * g;
-        state[i] = m;
-        state[6 + i] = v;
-        xi[i] = -prm.lr[i] * (m / c1) / (sqrt(v / c2) + prm.eps);
-        d_twist[i] = 0.0;   // ready for the next backward's accumulation
+    const int lane = threadIdx.x;
+    const double t_old = state[12];
+    const double p1 = (t_old == 0.0 ? 1.0 : state[13]) * prm.beta1;   // b1^t
+    const double p2 = (t_old == 0.0 ? 1.0 : state[14]) * prm.beta2;   // b2^t
+    double x = 0.0;
+    if (lane < 6) {
+        const double g = d_twist[lane];
+        const double m = prm.beta1 * state[lane] + (1.0 - prm.beta1) * g;
+        const double v = prm.beta2 * state[6 + lane] + (1.0 - prm.beta2) * g * g;
+        state[lane] = m;
+        state[6 + lane] = v;
+        x = -prm.lr[lane] * (m / (1.0 - p1)) / (sqrt(v / (1.0 - p2)) + prm.eps);
+        d_twist[lane] = 0.0;   // ready for the next backward's accumulation
     }
+    double xi[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xi[k] = __shfl_sync(0xffffffffu, x, k);
+    if (lane != 0) return;
+    state[12] = t_old + 1.0;
+    state[13] = p1;
+    state[14] = p2;
     // Exp of the twist (rho, phi): R = I + a K + b K^2, t = (I + b K + c K^2) rho
     const double *rho = xi, *phi = xi + 3;
     const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
@@ -36,7 +46,9 @@ __global__ void k_pose_adam(double *pose, double *d_twist, double *state, PoseAd
         b = 0.5 - th2 / 24.0;
         c = 1.0 / 6.0 - th2 / 120.0;
     } else {
-        const double th = sqrt(th2), s = sin(th), co = cos(th);
+        const double th = sqrt(th2);
+        double s, co;
+        sincos(th, &s, &co);
         a = s / th;
         b = (1.0 - co) / th2;
         c = (th - s) / (th2 * th);

@@ -381,24 +381,12 @@ __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigne
 
 __device__ __forceinline__ unsigned bits_of(uint32_t span) { return span ? 32 - __clz(span) : 0; }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *tile_off,
-                                                             int n_tiles,
-                                                             unsigned long long *bucket,
-                                                             unsigned long long *alt,
-                                                             uint32_t *sorted, Status *st,
-                                                             int smem_n, int lo, int hi) {
-    extern __shared__ unsigned long long sm[];
-    __shared__ uint32_t red[4][kSortWarps];
-    if (st->flags) return;
-    const int t = blockIdx.x;
-    const uint32_t start = tile_off[t];
-    const int n = (int)(tile_off[t + 1] - start);
-    if (n <= lo || n > hi) return;   // another launch sorts this size class
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (n == 1) {
-        if (tid == 0) sorted[start] = (uint32_t)bucket[start];
-        return;
-    }
+// Sorts one tile's list [start, start + n) (2 <= n) with the whole block.
+__device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned long long *alt,
+                                          uint32_t *sorted, Status *st, uint32_t start, int n,
+                                          int smem_n, unsigned long long *sm,
+                                          uint32_t (*red)[kSortWarps], int tid, int lane,
+                                          int warp) {
     const bool big = n > smem_n;
     uint32_t *hist = reinterpret_cast<uint32_t *>(sm + 2 * smem_n);
     unsigned long long *A = big ? bucket + start : sm;
@@ -498,6 +486,30 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *til
     }
     const unsigned long long gm = bg >= 64 ? ~0ull : ((1ull << bg) - 1ull);
     for (int i = tid; i < n; i += kSortThreads) sorted[start + i] = gmin + (uint32_t)(cur[i] & gm);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *tile_off,
+                                                             int n_tiles,
+                                                             unsigned long long *bucket,
+                                                             unsigned long long *alt,
+                                                             uint32_t *sorted, Status *st,
+                                                             int smem_n, int lo, int hi) {
+    extern __shared__ unsigned long long sm[];
+    __shared__ uint32_t red[4][kSortWarps];
+    if (st->flags) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // grid-stride over tiles: a launch may have fewer blocks than tiles
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const uint32_t start = tile_off[t];
+        const int n = (int)(tile_off[t + 1] - start);
+        if (n <= lo || n > hi) continue;   // another launch sorts this size class
+        if (n == 1) {
+            if (tid == 0) sorted[start] = (uint32_t)bucket[start];
+            continue;
+        }
+        sort_tile(bucket, alt, sorted, st, start, n, smem_n, sm, red, tid, lane, warp);
+        __syncthreads();   // shared memory is reused by the next tile
+    }
 }
 
 }  // namespace vt

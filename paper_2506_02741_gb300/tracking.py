@@ -37,7 +37,7 @@ class PoseTracker:
         self.pose = api.pose12(pose0, device)
         self.alpha, self.beta = float(alpha), float(beta)
         self.lr = [float(lr_trans)] * 3 + [float(lr_rot)] * 3
-        self.state = torch.zeros(13, dtype=torch.float64, device=device)   # Adam m, v, t
+        self.state = torch.zeros(15, dtype=torch.float64, device=device)   # Adam m, v, t, b^t
         self.d_twist = torch.zeros(6, dtype=torch.float64, device=device)
         self.rgb = torch.empty(3, H, W, device=device)
         self.depth = torch.empty(H, W, device=device)

@@ -80,3 +80,54 @@ def test_fullsize_crop_parity(cfg):
     G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist",
                         noise=want["twist_noise"])
     G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", noise=want["mat_noise"])
+
+
+def _tile_lists_sorted(R, n, W, H):
+    z = R.debug(0, n, np.float32)
+    tiles_x = (W + 15) // 16
+    n_tiles = tiles_x * ((H + 15) // 16)
+    off = R.debug(1, n_tiles + 1).astype(np.int64)
+    lists = R.debug(2, int(off[-1])).astype(np.int64)
+    zk = z.view(np.uint32).astype(np.uint64)
+    key = (zk[lists] << np.uint64(32)) | lists.astype(np.uint64)
+    tile_of = np.searchsorted(off, np.arange(lists.size), side="right") - 1
+    same_tile = tile_of[1:] == tile_of[:-1]
+    assert np.all((key[1:] > key[:-1])[same_tile])
+    return np.diff(off)
+
+
+def test_tile_sort_every_size_class():
+    """Every tile list is ordered by (depth key, id) at the tracking size
+    (tiles of every shared-memory size class, including the few longest sorted
+    on the auxiliary stream) and in a crafted case whose lists exceed the
+    shared-memory sort (global-memory path); the latter also matches the
+    oracle's render."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    K = syn.VGA
+    osec, target = _section(K, 8, "f32")
+    sec = G.to_device(osec, "f32")
+    R = api.Renderer()
+    R.render([sec], api.pose12(target, dev), K.astuple(), K.W, K.H, checked=True)
+    lens = _tile_lists_sorted(R, osec.n, K.W, K.H)
+    for lo, hi in ((1, 2048), (2048, 4096), (4096, 6144), (6144, 13312)):
+        assert np.any((lens > lo) & (lens <= hi)), (lo, hi)
+    # 30 views of a 64x48 camera with 3x radii: lists beyond 13312 entries
+    Kt = syn.TINY
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(31)
+    fr = syn.render_frames(room, Kt, path[:30])
+    big = oracle.section_init(fr.depth, fr.rgb, Kt.astuple(), np.stack(path[:30]))
+    big.radius = big.radius * 3.0
+    big = G.quantise(big, "f32")
+    bsec = G.to_device(big, "f32")
+    R2 = api.Renderer()
+    R2.reserve(big.n, Kt.W, Kt.H, 40 * big.n)
+    out = R2.render([bsec], api.pose12(path[30], dev), Kt.astuple(), Kt.W, Kt.H, checked=True)
+    lens = _tile_lists_sorted(R2, big.n, Kt.W, Kt.H)
+    assert lens.max() > 13312
+    ref = oracle.render([big], path[30], Kt.astuple(), Kt.W, Kt.H)
+    clean = G.clean_mask(ref)
+    assert clean.mean() > 0.8          # ~30 overlapping layers: more marginal decisions
+    G.assert_forward_close(out, ref, clean)

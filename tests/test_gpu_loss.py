@@ -123,7 +123,7 @@ def test_pose_adam_matches_reference(dev, lr_rot):
     P = syn.perturb_pose(syn.identity_pose(), rng, 0.3, 20.0)
     lr = [2e-3] * 3 + [lr_rot] * 3
     pose = api.pose12(P, dev)
-    state = torch.zeros(13, dtype=torch.float64, device=dev)
+    state = torch.zeros(15, dtype=torch.float64, device=dev)
     d_tw = torch.zeros(6, dtype=torch.float64, device=dev)
     m, v, t = np.zeros(6), np.zeros(6), 0.0
     for _ in range(5):
