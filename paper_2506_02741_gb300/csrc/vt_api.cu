@@ -41,15 +41,16 @@ vt_status cuda_fail(cudaError_t e, const char *what) {
 
 // Tile lists are sorted in shared memory by size class, each class by a
 // launch whose blocks hold just enough shared memory for its longest list, so
-// that short lists run several blocks per SM: (0, 2048], (2048, 4096],
-// (4096, kSortSmemN] on the caller's stream; the few longer ones (up to
+// that short lists run several blocks per SM (4, 3 and 2 of 228 KB):
+// (0, 1536], (1536, 3584], (3584, kSortSmemN] on the caller's stream; the few
+// longer ones (up to
 // kSortSmemBig in shared memory, beyond that in global memory) by a launch on
 // an auxiliary stream that overlaps the others.
-constexpr int kSortClassS = 2048, kSortClassM = 4096;
+constexpr int kSortClassS = 1536, kSortClassM = 3584;
 constexpr size_t sort_smem_bytes(int n) { return 2 * (size_t)n * 8 + 16 * 256 * 4; }
 // (kept for the long-list launch and the attribute of the largest one)
 // launch with one large block per SM; longer still in global memory.
-constexpr int kSortSmemN = 6144;
+constexpr int kSortSmemN = 6000;
 constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 16 * 256 * 4;
 constexpr int kSortSmemBig = 13312;
 constexpr size_t kSortSmemBigBytes =

@@ -28,6 +28,54 @@ __device__ __forceinline__ bool block_touches(float du0, float dv0, float kxs, f
     return dx * dx * kxs + dy * dy * kys >= tmin * 1.0001f - 1e-6f;
 }
 
+// Conservative set of the pixels of an 8x4 block (bit lx + 8 ly, columns
+// 0..lxmax, rows 0..lymax) that can pass t >= t_min for a Gaussian at offsets
+// du0 ~ bx0 - uc, dv0 ~ by0 - vc: row by row, kx' (du0 + lx)^2 >= t_min -
+// ky' (dv0 + ly)^2 bounds |du0 + lx|.  The threshold is loosened by 1e-4
+// relative and the half-width widened by 1e-3 px, which covers the rounding of
+// the exact per-pixel test and of the approximate reciprocal and square root.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ uint32_t pixel_mask(float du0, float dv0, float kxs, float kys,
+                                               float tmin, int lxmax, int lymax) {
+    const float tl = tmin * 1.0001f - 1e-6f;
+    const float ikx = rcp_approx(kxs);   // kx' < 0
+    uint32_t m = 0u;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float dv = dv0 + (float)r;
+        const float s = (tl - kys * dv * dv) * ikx;   // bound on (du0 + lx)^2
+        if (r <= lymax && s >= 0.f) {
+            const float w = sqrt_approx(s) * 1.0001f + 1e-3f;
+            const int lo = max(0, (int)ceilf(-du0 - w));
+            const int hi = min(lxmax, (int)floorf(w - du0));
+            if (lo <= hi) m |= ((0xFFu >> (7 - hi)) & (0xFFu << lo)) << (8 * r);
+        }
+    }
+    return m;
+}
+
+// 32 x 32 bit transpose across a warp: on return bit j of lane i's word is
+// bit i of lane j's input word (five butterfly stages).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+    const uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int w = 16 >> s;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, w);
+        x = (lane & w) ? ((x & ~M[s]) | ((y & ~M[s]) >> w)) : ((x & M[s]) | ((y & M[s]) << w));
+    }
+    return x;
+}
+
 // OR of the list-overflow flags of the eight blocks of a tile.
 __device__ __forceinline__ bool tile_flagged(const uint32_t *blk_ovf, int tile) {
     const uint4 *f = reinterpret_cast<const uint4 *>(blk_ovf + (size_t)tile * kWarps);
@@ -75,8 +123,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     const int bx0 = tx * kTile + (sub & 1) * 8, by0 = ty * kTile + (sub >> 1) * 4;
     const int px = bx0 + lx, py = by0 + ly;
     const bool inside = px < cam.W && py < cam.H;
-    const float lxmax = (float)min(7, cam.W - 1 - bx0);
-    const float lymax = (float)min(3, cam.H - 1 - by0);
+    const int lxmaxi = min(7, cam.W - 1 - bx0), lymaxi = min(3, cam.H - 1 - by0);
     const uint32_t start = tile_off[tile];
     const int n = (int)(tile_off[tile + 1] - start);
     const size_t p = inside ? (size_t)py * cam.W + px : 0;
@@ -115,20 +162,25 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
         const float ku = (float)(bx0 - __float_as_int(g0.x));
         const float kv = (float)(by0 - __float_as_int(g0.z));
         const float tmin = t_min_of(g1.w);
-        const bool rel = valid && block_touches(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmax,
-                                                lymax);
-        unsigned mask = __ballot_sync(kFullMask, rel);
-        if (!mask) continue;
+        const uint32_t pm =
+            valid ? pixel_mask(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmaxi, lymaxi) : 0u;
+        if (!__any_sync(kFullMask, pm != 0u)) continue;
         __syncwarp();
         fs[lane] = make_float4(ku, kv, g0.y, g0.w);
         ks[lane] = make_float4(g1.x, g1.y, tmin, g1.w);
         cs[lane] = a;
         ids[lane] = gid;
+        // this pixel's candidates of the round, in list order (bit j = entry j)
+        uint32_t cand = transpose32(pm, lane);
         __syncwarp();
-        while (mask) {
-            const int j = __ffs(mask) - 1;
-            mask &= mask - 1;
-            if (done) continue;
+        if (done) cand = 0u;
+        // each lane walks its own candidates: lanes work on different
+        // Gaussians at once, and the warp takes as many steps as the busiest
+        // pixel has candidates
+        while (__any_sync(kFullMask, cand != 0u)) {
+            if (!cand) continue;
+            const int j = __ffs(cand) - 1;
+            cand &= cand - 1u;
             const float4 f = fs[j], k = ks[j];
             const float t = pair_t(__fsub_rn(__fadd_rn(f.x, lxf), f.z),
                                    __fsub_rn(__fadd_rn(f.y, lyf), f.w), k.x, k.y);
@@ -137,6 +189,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
             const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
             if (Tn < kTMin) {
                 done = true;
+                cand = 0u;
                 continue;
             }
             const float w = __fmul_rn(al, T);

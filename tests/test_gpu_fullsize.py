@@ -111,7 +111,7 @@ def test_tile_sort_every_size_class():
     R = api.Renderer()
     R.render([sec], api.pose12(target, dev), K.astuple(), K.W, K.H, checked=True)
     lens = _tile_lists_sorted(R, osec.n, K.W, K.H)
-    for lo, hi in ((1, 2048), (2048, 4096), (4096, 6144), (6144, 13312)):
+    for lo, hi in ((1, 1536), (1536, 3584), (3584, 6000), (6000, 13312)):
         assert np.any((lens > lo) & (lens <= hi)), (lo, hi)
     # 30 views of a 64x48 camera with 3x radii: lists beyond 13312 entries
     Kt = syn.TINY
