@@ -166,6 +166,23 @@ vt_status vt_section_init(const float *depth, const float *rgb, int32_t n_views,
                           void *colour, void *opacity, void *radius, int64_t cap,
                           int64_t *n_out, vt_stream stream);
 
+/* Complement initialisation of a regular frame (Sec. 3.4: the section is
+ * splatted into a silhouette at the frame's pose and Gaussians are
+ * initialised where it leaves the frame uncovered): one Gaussian per pixel
+ * with valid depth and silhouette < sil_max (0.5 in the paper's setting),
+ * colour = V(u, v), opacity 0.9, radius = D / fx, in raster order.  depth,
+ * silhouette (H x W) and rgb (3 x H x W): device float32 of the new frame.
+ * The frame becomes view number `view` of the section, so src = view * W * H +
+ * v * W + u; the caller appends the outputs (device, capacity cap; count to
+ * n_out, a device int64) to the section's arrays and the frame's depth and
+ * pose to its views.  Allocates stream-ordered scratch of 8 bytes per 256
+ * pixels. */
+vt_status vt_section_complement(const float *depth, const float *rgb, const float *silhouette,
+                                int32_t W, int32_t H, vt_intrinsics K, float sil_max,
+                                int32_t view, vt_precision prec, uint32_t *src, void *colour,
+                                void *opacity, void *radius, int64_t cap, int64_t *n_out,
+                                vt_stream stream);
+
 /* Render sections [secs, secs + n_secs) (their concatenation, as in the
  * multi-section render of Sec. 3.4) from the camera pose12 (device, 12
  * doubles) with intrinsics K into W x H images.  rgb (3 x H x W), depth and

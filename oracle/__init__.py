@@ -114,6 +114,11 @@ def lib():
             L.orc_masked_l1.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, _L1Weights,
                                         C.c_void_p, C.c_void_p]
+            L.orc_section_complement.restype = C.c_int64
+            L.orc_section_complement.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                                 C.c_int32, C.c_float, C.c_float, C.c_int32,
+                                                 C.c_void_p, C.c_void_p, C.c_void_p,
+                                                 C.c_void_p]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -334,3 +339,22 @@ def masked_l1(rgb, depth, sil, obs_rgb, obs_depth, w_rgb, w_depth, sil_min=-1.0,
                                _ptr(obs_depth), None if vis is None else _ptr(vis), w,
                                _ptr(d_rgb), _ptr(d_depth))
     return float(loss), d_rgb, d_depth
+
+
+def section_complement(depth, rgb, sil, K, view, sil_max=0.5):
+    """Complement initialisation of one frame: (src, colour (n, 3), opacity,
+    radius) of the Gaussians at its valid, uncovered pixels (silhouette <
+    sil_max); the frame is view ``view`` of the section."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    rgb = np.ascontiguousarray(rgb, np.float32)
+    sil = np.ascontiguousarray(sil, np.float32)
+    H, W = depth.shape
+    cap = H * W
+    src = np.zeros(cap, np.uint32)
+    col = np.zeros((cap, 3))
+    op = np.zeros(cap)
+    rad = np.zeros(cap)
+    n = lib().orc_section_complement(_ptr(depth), _ptr(rgb), _ptr(sil), W, H,
+                                     float(np.float32(K[0])), float(np.float32(sil_max)),
+                                     int(view), _ptr(src), _ptr(col), _ptr(op), _ptr(rad))
+    return src[:n].copy(), col[:n].copy(), op[:n].copy(), rad[:n].copy()

@@ -576,3 +576,19 @@ int64_t orc_section_init(const float *depth, const float *rgb, int32_t n_views, 
         }
     return n;
 }
+
+int64_t orc_section_complement(const float *depth, const float *rgb, const float *sil,
+                               int32_t W, int32_t H, float fx, float sil_max, int32_t view,
+                               uint32_t *src, double *colour, double *opacity, double *radius) {
+    int64_t plane = (int64_t)W * H, n = 0;
+    for (int64_t p = 0; p < plane; ++p) {
+        float D = depth[p];
+        if (!valid_depth(D) || !(sil[p] < sil_max)) continue;   /* covered: no new Gaussian */
+        src[n] = (uint32_t)((int64_t)view * plane + p);
+        for (int c = 0; c < 3; ++c) colour[3 * n + c] = rgb[c * plane + p];
+        opacity[n] = 0.9;
+        radius[n] = (double)D / (double)fx;
+        ++n;
+    }
+    return n;
+}

@@ -114,6 +114,14 @@ int64_t orc_section_init(const float *depth, const float *rgb, int32_t n_views, 
                          int32_t H, float fx, uint32_t *src, double *colour,
                          double *opacity, double *radius);
 
+/* Complement initialisation of a regular frame (Sec. 3.4): one Gaussian per
+ * pixel of the frame with valid depth whose silhouette (the section rendered
+ * from the frame's pose) is below sil_max; the frame is view `view`, so
+ * src = view * W * H + pixel.  Returns n. */
+int64_t orc_section_complement(const float *depth, const float *rgb, const float *sil,
+                               int32_t W, int32_t H, float fx, float sil_max, int32_t view,
+                               uint32_t *src, double *colour, double *opacity, double *radius);
+
 /* ---- loss inputs (vt_oracle_loss.c) ---------------------------------- */
 
 typedef struct {

@@ -136,6 +136,40 @@ class Section:
         return Section(P, depth, tuple(float(np.float32(k)) for k in K), src[:n].contiguous(),
                        col[:n].contiguous(), op[:n].contiguous(), rad[:n].contiguous())
 
+    def append_view(self, depth: torch.Tensor, rgb: torch.Tensor, pose, silhouette: torch.Tensor,
+                    sil_max: float = 0.5, stream=None) -> "Section":
+        """Complement initialisation of a regular frame (Sec. 3.4): a new
+        section with the frame as its last view and one Gaussian per pixel
+        with valid depth that ``silhouette`` (this section rendered from the
+        frame's pose) leaves uncovered (< sil_max).  depth (H, W), rgb
+        (3, H, W) float32 device; the frame's intrinsics are the section's.
+        Synchronises once to learn the count."""
+        V, H, W = self.depth.shape
+        depth = _cuda(depth, torch.float32, "depth", (H, W))
+        rgb = _cuda(rgb, torch.float32, "rgb", (3, H, W))
+        silhouette = _cuda(silhouette, torch.float32, "silhouette", (H, W))
+        dev = depth.device
+        p = pose if isinstance(pose, torch.Tensor) else pose12(pose, dev)
+        p = _cuda(p, torch.float64, "pose", (12,))
+        dt = self.colour.dtype
+        cap = H * W
+        src = torch.empty(cap, dtype=torch.int32, device=dev)
+        col = torch.empty(cap, 3, dtype=dt, device=dev)
+        op = torch.empty(cap, dtype=dt, device=dev)
+        rad = torch.empty(cap, dtype=dt, device=dev)
+        n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+        L.check(L.lib().vt_section_complement(_ptr(depth), _ptr(rgb), _ptr(silhouette), W, H,
+                                              _intr(self.K), float(sil_max), V, self.prec,
+                                              _ptr(src), _ptr(col), _ptr(op), _ptr(rad), cap,
+                                              _ptr(n_out), _stream(stream)),
+                "vt_section_complement")
+        n = int(n_out.item())
+        cat = lambda a, b: torch.cat([a, b[:n]]).contiguous()
+        return Section(torch.cat([self.poses, p[None]]).contiguous(),
+                       torch.cat([self.depth, depth[None]]).contiguous(), self.K,
+                       cat(self.src, src), cat(self.colour, col), cat(self.opacity, op),
+                       cat(self.radius, rad))
+
 
 def backproject(depth: torch.Tensor, K, pose, stream=None):
     """World centres (n, 3) float32 and raster pixel indices (n,) of the valid

@@ -856,11 +856,44 @@ vt_status vt_section_init(const float *depth, const float *rgb, int32_t n_views,
     if ((st = compaction_scratch(total, &counts, &offs, &nb, stream))) return st;
     k_count_valid<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, total, counts);
     k_scan_counts<<<1, 1024, 0, stream>>>(counts, nb, offs, reinterpret_cast<long long *>(n_out));
-    k_section_init<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, rgb, plane, total, K.fx,
-                                                            (int)prec, offs, src, colour,
-                                                            opacity, radius, cap);
+    k_section_init<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, rgb, nullptr, 0.f, plane,
+                                                            total, K.fx, (int)prec, offs, 0u, src,
+                                                            colour, opacity, radius, cap);
     cudaFreeAsync(counts, stream);
     VT_CUDA(cudaGetLastError(), "vt_section_init launch");
+    return VT_OK;
+}
+
+vt_status vt_section_complement(const float *depth, const float *rgb, const float *silhouette,
+                                int32_t W, int32_t H, vt_intrinsics K, float sil_max,
+                                int32_t view, vt_precision prec, uint32_t *src, void *colour,
+                                void *opacity, void *radius, int64_t cap, int64_t *n_out,
+                                vt_stream stream) {
+    vt_status st = check_image(W, H, "vt_section_complement");
+    if (st) return st;
+    if ((st = check_intrinsics(K, "vt_section_complement"))) return st;
+    if (view < 0 || (int64_t)(view + 1) * W * H > (int64_t)0xffffffffll)
+        return fail(VT_ERR_INVALID_ARG, "vt_section_complement: view %d out of range", view);
+    if (prec != VT_F32 && prec != VT_F16)
+        return fail(VT_ERR_INVALID_ARG, "vt_section_complement: unknown precision");
+    if (!std::isfinite(sil_max))
+        return fail(VT_ERR_INVALID_ARG, "vt_section_complement: sil_max must be finite");
+    if (!depth || !rgb || !silhouette || !n_out || cap < 0 ||
+        (cap > 0 && (!src || !colour || !opacity || !radius)))
+        return fail(VT_ERR_INVALID_ARG,
+                    "vt_section_complement: NULL pointer or negative capacity");
+    const int64_t plane = (int64_t)W * H;
+    uint32_t *counts, *offs;
+    int64_t nb;
+    if ((st = compaction_scratch(plane, &counts, &offs, &nb, stream))) return st;
+    k_count_yield<<<(unsigned)nb, kInitBlock, 0, stream>>>(depth, plane, silhouette, sil_max,
+                                                           counts);
+    k_scan_counts<<<1, 1024, 0, stream>>>(counts, nb, offs, reinterpret_cast<long long *>(n_out));
+    k_section_init<<<(unsigned)nb, kInitBlock, 0, stream>>>(
+        depth, rgb, silhouette, sil_max, plane, plane, K.fx, (int)prec, offs,
+        (uint32_t)((int64_t)view * plane), src, colour, opacity, radius, cap);
+    cudaFreeAsync(counts, stream);
+    VT_CUDA(cudaGetLastError(), "vt_section_complement launch");
     return VT_OK;
 }
 

@@ -272,15 +272,17 @@ __global__ void k_attr_adam(int64_t n, float *theta, float *m, float *v, const d
 __global__ void k_pose_finalize(const double *partials, int n_parts, const double *pose_copy,
                                 double *d_twist, double *d_mat);
 __global__ void k_count_valid(const float *depth, int64_t total, uint32_t *block_counts);
+__global__ void k_count_yield(const float *depth, int64_t total, const float *sil,
+                              float sil_max, uint32_t *block_counts);
 __global__ void k_scan_counts(const uint32_t *counts, int64_t n, uint32_t *offs,
                               long long *n_out);
 __global__ void k_backproject(const float *depth, int W, int H, vt_intrinsics K,
                               const double *pose12, const uint32_t *offs, float *centres,
                               uint32_t *pix, int64_t cap);
-__global__ void k_section_init(const float *depth, const float *rgb, int64_t plane,
-                               int64_t total, float fx, int prec, const uint32_t *offs,
-                               uint32_t *src, void *colour, void *opacity, void *radius,
-                               int64_t cap);
+__global__ void k_section_init(const float *depth, const float *rgb, const float *sil,
+                               float sil_max, int64_t plane, int64_t total, float fx, int prec,
+                               const uint32_t *offs, uint32_t src_base, uint32_t *src,
+                               void *colour, void *opacity, void *radius, int64_t cap);
 
 constexpr int kInitBlock = 256;
 

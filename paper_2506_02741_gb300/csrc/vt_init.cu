@@ -22,10 +22,31 @@ __device__ __forceinline__ uint32_t block_rank(bool valid) {
     return base + __popc(b & ((1u << lane) - 1u));
 }
 
+// A pixel yields a Gaussian when its depth is valid and, when a silhouette is
+// given (complement initialisation, Sec. 3.4), the current render leaves it
+// uncovered (silhouette < sil_max).
+__device__ __forceinline__ bool yields(const float *depth, const float *sil, float sil_max,
+                                       int64_t i, float &D) {
+    D = depth[i];
+    return depth_ok(D) && (sil == nullptr || sil[i] < sil_max);
+}
+
 __global__ void __launch_bounds__(kInitBlock) k_count_valid(const float *depth, int64_t total,
                                                             uint32_t *block_counts) {
     const int64_t i = (int64_t)blockIdx.x * kInitBlock + threadIdx.x;
     const bool v = i < total && depth_ok(depth[i]);
+    const int n = __syncthreads_count(v);
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = (uint32_t)n;
+}
+
+// Per-block counts of the pixels that yield a Gaussian (valid depth and, with
+// a silhouette, uncovered).
+__global__ void __launch_bounds__(kInitBlock) k_count_yield(const float *depth, int64_t total,
+                                                            const float *sil, float sil_max,
+                                                            uint32_t *block_counts) {
+    const int64_t i = (int64_t)blockIdx.x * kInitBlock + threadIdx.x;
+    float D;
+    const bool v = i < total && yields(depth, sil, sil_max, i, D);
     const int n = __syncthreads_count(v);
     if (threadIdx.x == 0) block_counts[blockIdx.x] = (uint32_t)n;
 }
@@ -88,19 +109,20 @@ __global__ void __launch_bounds__(kInitBlock) k_backproject(const float *depth, 
     pix[pos] = (uint32_t)i;
 }
 
-// One Gaussian per valid depth pixel of all views, in (view, pixel) order:
-// colour = V(u, v), opacity = 0.9, radius = D / fx.
+// One Gaussian per yielding pixel of all views, in (view, pixel) order:
+// colour = V(u, v), opacity = 0.9, radius = D / fx; src = src_base + index.
 __global__ void __launch_bounds__(kInitBlock) k_section_init(
-    const float *depth, const float *rgb, int64_t plane, int64_t total, float fx, int prec,
-    const uint32_t *offs, uint32_t *src, void *colour, void *opacity, void *radius, int64_t cap) {
+    const float *depth, const float *rgb, const float *sil, float sil_max, int64_t plane,
+    int64_t total, float fx, int prec, const uint32_t *offs, uint32_t src_base, uint32_t *src,
+    void *colour, void *opacity, void *radius, int64_t cap) {
     const int64_t i = (int64_t)blockIdx.x * kInitBlock + threadIdx.x;
-    const float D = i < total ? depth[i] : 0.f;
-    const bool v = i < total && depth_ok(D);
+    float D = 0.f;
+    const bool v = i < total && yields(depth, sil, sil_max, i, D);
     const int64_t pos = (int64_t)offs[blockIdx.x] + block_rank(v);
     if (!v || pos >= cap) return;
     const int64_t view = i / plane, p = i - view * plane;
     const float r = __fdiv_rn(D, fx);
-    src[pos] = (uint32_t)i;
+    src[pos] = src_base + (uint32_t)i;
     for (int ch = 0; ch < 3; ++ch) {
         const float c = rgb[(view * 3 + ch) * plane + p];
         if (prec == VT_F16)

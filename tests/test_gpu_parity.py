@@ -84,6 +84,52 @@ def test_section_init_bitexact(dev):
         np.testing.assert_array_equal(s.radius.cpu().numpy(), r32.astype(dt))
 
 
+def test_section_complement(dev):
+    """Complement initialisation against the oracle (bit-exact outputs), and
+    the completed section's render against the oracle's render of the same
+    Gaussians."""
+    K = syn.TINY
+    path = syn.trajectory(12)
+    room = syn.make_room(syn.SCENE_SEED)
+    f0 = syn.render_frames(room, K, [path[0]])
+    f1 = syn.render_frames(room, K, [path[11]])
+    d1 = f1.depth[0].copy()
+    d1[1, 1] = np.nan
+    for prec in ("f32", "f16"):
+        sec = api.Section.from_rgbd(torch.from_numpy(f0.depth).to(dev),
+                                    torch.from_numpy(f0.rgb).to(dev), K.astuple(),
+                                    np.stack([path[0]]), precision=prec)
+        R = api.Renderer()
+        _, _, sil = R.render([sec], api.pose12(path[11], dev), K.astuple(), K.W, K.H, checked=True)
+        sil_h = sil.cpu().numpy()
+        src, col, op, rad = oracle.section_complement(d1, f1.rgb[0], sil_h, K.astuple(), view=1)
+        assert 5 < src.size < K.W * K.H // 2
+        both = sec.append_view(torch.from_numpy(d1).to(dev), torch.from_numpy(f1.rgb[0]).to(dev),
+                               path[11], sil)
+        n0 = sec.n
+        dt = np.float16 if prec == "f16" else np.float32
+        assert both.n == n0 + src.size and both.n_views == 2
+        np.testing.assert_array_equal(both.src[n0:].cpu().numpy().view(np.uint32), src)
+        np.testing.assert_array_equal(both.colour[n0:].cpu().numpy(), col.astype(np.float32).astype(dt))
+        np.testing.assert_array_equal(both.opacity[n0:].cpu().numpy(), op.astype(np.float32).astype(dt))
+        r32 = d1.reshape(-1)[src - K.W * K.H] / np.float32(K.fx)
+        np.testing.assert_array_equal(both.radius[n0:].cpu().numpy(), r32.astype(dt))
+        if prec == "f32":
+            osec = G.quantise(oracle.Section(K.W, K.H, K.astuple(), np.stack([path[0], path[11]]),
+                                             np.stack([f0.depth[0], d1]),
+                                             both.src.cpu().numpy().view(np.uint32),
+                                             both.colour.cpu().numpy().astype(np.float64),
+                                             both.opacity.cpu().numpy().astype(np.float64),
+                                             both.radius.cpu().numpy().astype(np.float64)))
+            # seen from a pose between the views (from the frame's own pose the
+            # new Gaussians' neighbours sit exactly at q = 9)
+            ref = oracle.render([osec], path[10], K.astuple(), K.W, K.H)
+            out = R.render([both], api.pose12(path[10], dev), K.astuple(), K.W, K.H, checked=True)
+            clean = G.clean_mask(ref)
+            assert clean.mean() > 0.8
+            G.assert_forward_close(out, ref, clean)
+
+
 def test_backproject(dev):
     room = syn.make_room()
     K = syn.scaled_intrinsics(96, 72)
