@@ -157,8 +157,8 @@ def make_workload(rank: int, n_frames: int, K=None):
 def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
     """Mapping workload: 1200x680 section of 10 views (8,160,000 Gaussians),
     colour/opacity/radius in ``prec``, FP32 compositing; one step = render
-    from a random section view + Eq. 2 L1 terms + attribute backward + Adam
-    (+ FP16 write-back).  Returns a summary dict."""
+    from a random section view + Eq. 2 (L1 terms and the SSIM term) +
+    attribute backward + Adam (+ FP16 write-back).  Returns a summary dict."""
     import torch
 
     from paper_2506_02741_gb300 import api
@@ -184,7 +184,7 @@ def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
     e1 = torch.cuda.Event(enable_timing=True)
     R.set_timing(True)
     R.timing(reset=True)
-    l0 = float(m.loss)
+    l0 = float(m.losses.sum())
     e0.record()
     for v in views[warmup:]:
         m.step(v)
@@ -197,7 +197,7 @@ def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
     return {"workload": f"mapping_1200x680_10views_{prec}", "gaussians": sec.n,
             "iters": iters, "ms_per_step": ms / iters,
             "mpix_s": K.W * K.H * iters / (ms / 1e3) / 1e6,
-            "loss_first": l0, "loss_last": float(m.loss),
+            "loss_first": l0, "loss_last": float(m.losses.sum()),
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
 
 

@@ -261,6 +261,20 @@ vt_status vt_masked_l1(vt_ctx *ctx, int32_t W, int32_t H, const float *rgb, cons
                        const uint8_t *visible, vt_l1_weights w, float *d_rgb, float *d_depth,
                        double *loss, vt_stream stream);
 
+/* SSIM term of Eq. 2 (Sec. 3.4 mapping loss: tau L_S(V, V'), L_S the SSIM
+ * loss; tau = 0.2 in Sec. 4).  L_S = 1 - mean SSIM over the pixels and the
+ * three channels of rgb (rendered) against obs_rgb (observed), both device
+ * float32 3 x H x W; SSIM per channel with an 11 x 11 Gaussian window
+ * (sigma 1.5, weights normalised to 1, zero padding) and C1 = 0.01^2,
+ * C2 = 0.03^2.  loss (device, one double, may be NULL) is overwritten with
+ * weight * L_S (FP64 sum in a fixed order); d_rgb (device float32
+ * 3 x H x W, may be NULL) is ACCUMULATED (+=) with weight * dL_S/drgb, so it
+ * adds to the gradient vt_masked_l1 wrote.  ctx holds the scratch (60 bytes
+ * per pixel), allocated on the first call of a size: call once before
+ * capturing a graph. */
+vt_status vt_ssim(vt_ctx *ctx, int32_t W, int32_t H, const float *rgb, const float *obs_rgb,
+                  double weight, float *d_rgb, double *loss, vt_stream stream);
+
 /* One Adam step on the camera pose (Sec. 3.3 tracking optimises the pose of
  * the latest frame; the supplementary gives Adam learning rates lr_rot and
  * lr_trans).  With the twist gradient g = d_twist (device, 6 doubles, as

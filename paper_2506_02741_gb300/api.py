@@ -258,11 +258,31 @@ def attr_adam(section, theta: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
                                  _ptr(section.radius), p, _stream(stream)), "vt_attr_adam")
 
 
+# Contexts released while a CUDA graph was being captured on the current
+# stream: destroying one then would synchronise and free device memory in the
+# middle of the capture, so they wait for the next context operation outside
+# a capture.
+_deferred = []
+
+
+def _capturing() -> bool:
+    try:
+        return torch.cuda.is_available() and torch.cuda.is_current_stream_capturing()
+    except Exception:
+        return False
+
+
+def _flush_deferred(lib):
+    while _deferred and not _capturing():
+        lib.vt_ctx_destroy(_deferred.pop())
+
+
 class Renderer:
     """Owns one vt_ctx (the library's render workspace) on the current device."""
 
     def __init__(self):
         self._lib = L.lib()
+        _flush_deferred(self._lib)
         h = C.c_void_p()
         L.check(self._lib.vt_ctx_create(C.byref(h)), "vt_ctx_create")
         self._ctx = h
@@ -270,7 +290,11 @@ class Renderer:
 
     def close(self):
         if getattr(self, "_ctx", None):
-            self._lib.vt_ctx_destroy(self._ctx)
+            if _capturing():
+                _deferred.append(self._ctx)
+            else:
+                self._lib.vt_ctx_destroy(self._ctx)
+                _flush_deferred(self._lib)
             self._ctx = None
 
     def __del__(self):
@@ -404,6 +428,21 @@ class Renderer:
                                        _ptr(_cuda(d_depth, torch.float32, "d_depth", (H, W))),
                                        _ptr(loss), _stream(stream)), "vt_masked_l1")
         return loss, d_rgb, d_depth
+
+    def ssim(self, rgb, obs_rgb, weight: float, d_rgb=None, loss=None, stream=None):
+        """SSIM term of Eq. 2: loss (1,) float64 = weight * (1 - mean SSIM);
+        d_rgb (3, H, W) float32, when given, is accumulated (+=) with its
+        gradient.  Returns (loss, d_rgb)."""
+        rgb = _cuda(rgb, torch.float32, "rgb")
+        _, H, W = rgb.shape
+        _cuda(obs_rgb, torch.float32, "obs_rgb", (3, H, W))
+        if d_rgb is not None:
+            _cuda(d_rgb, torch.float32, "d_rgb", (3, H, W))
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device=rgb.device)
+        L.check(self._lib.vt_ssim(self._ctx, W, H, _ptr(rgb), _ptr(obs_rgb), float(weight),
+                                  _ptr(d_rgb), _ptr(loss), _stream(stream)), "vt_ssim")
+        return loss, d_rgb
 
     # -- instrumentation -----------------------------------------------------
     def set_timing(self, on: bool = True):

@@ -59,7 +59,7 @@ constexpr size_t kSortSmemBigBytes =
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
-    K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_NUM
+    K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_SSIM_FWD, K_SSIM_BWD, K_SSIM_SUM, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -67,7 +67,8 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "k_section_init",  "k_count_valid",   "k_composite_bwd_list",
                                    "k_sort_tiles_long", "k_attr_scatter", "k_masked_l1",
                                    "k_sum_partials",  "k_pose_adam",     "k_adam_step_count",
-                                   "k_attr_adam",     "k_sort_tiles_mid", "k_sort_tiles_large"};
+                                   "k_attr_adam",     "k_sort_tiles_mid", "k_sort_tiles_large",
+                                   "k_ssim_fwd",      "k_ssim_bwd",       "k_ssim_sum"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -108,6 +109,8 @@ struct vt_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *loss_part = nullptr;      // masked-L1 block partials (separate allocation)
     int64_t loss_cap = 0;             // blocks they hold
+    void *ssim_buf = nullptr;         // SSIM maps (15 floats per pixel) + block partials
+    int64_t ssim_cap = 0;             // pixels it holds
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
     float *accr = nullptr;        // and radius, per Gaussian
     // per-pixel lists of added Gaussians (separate allocation)
@@ -323,9 +326,14 @@ vt_status vt_ctx_create(vt_ctx **ctx) {
 
 void vt_ctx_destroy(vt_ctx *c) {
     if (!c) return;
+    // the teardown touches only this context's streams and memory: let it run
+    // while another thread captures a graph in global mode
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    cudaThreadExchangeStreamCaptureMode(&mode);
     free_arena(c, c->stream);
     if (c->plist) cudaFreeAsync(c->plist, c->stream);
     if (c->loss_part) cudaFreeAsync(c->loss_part, c->stream);
+    if (c->ssim_buf) cudaFreeAsync(c->ssim_buf, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
@@ -339,6 +347,7 @@ void vt_ctx_destroy(vt_ctx *c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
+    cudaThreadExchangeStreamCaptureMode(&mode);
 }
 
 size_t vt_workspace_bytes(int64_t n_gaussians, int32_t W, int32_t H, int64_t n_instances) {
@@ -717,6 +726,61 @@ vt_status vt_masked_l1(vt_ctx *c, int32_t W, int32_t H, const float *rgb, const 
         k_sum_partials<<<1, 1024, 0, stream>>>(c->loss_part, (int)nb, wc, wd, loss);
     }
     VT_CUDA(cudaGetLastError(), "vt_masked_l1 launch");
+    return VT_OK;
+}
+
+vt_status vt_ssim(vt_ctx *c, int32_t W, int32_t H, const float *rgb, const float *obs_rgb,
+                  double weight, float *d_rgb, double *loss, vt_stream stream) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_ssim: ctx is NULL");
+    vt_status st = check_image(W, H, "vt_ssim");
+    if (st) return st;
+    if (!rgb || !obs_rgb) return fail(VT_ERR_INVALID_ARG, "vt_ssim: NULL image");
+    if (!std::isfinite(weight)) return fail(VT_ERR_INVALID_ARG, "vt_ssim: weight must be finite");
+    const int64_t P = (int64_t)W * H;
+    const dim3 grid((W + 31) / 32, (H + 7) / 8);
+    const int64_t nb = (int64_t)grid.x * grid.y;
+    // 15 map floats per pixel (5 maps x 3 channels), then 2 doubles per block
+    const int64_t need = std::max<int64_t>(P, 256 * nb);
+    if (need > c->ssim_cap) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        VT_CUDA(cudaStreamIsCapturing(stream, &cs), "capture query");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(VT_ERR_STATE, "vt_ssim: scratch must be sized before graph capture");
+        if (c->ssim_buf) cudaFreeAsync(c->ssim_buf, stream);
+        c->ssim_buf = nullptr;
+        c->ssim_cap = 0;
+        const int64_t cap = need;
+        void *p = nullptr;
+        const size_t bytes =
+            align_up(sizeof(float) * 15 * (size_t)cap) + sizeof(double) * 2 * (cap / 256 + 1);
+        const cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+        if (e != cudaSuccess)
+            return fail(VT_ERR_OOM, "SSIM scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
+        c->ssim_buf = p;
+        c->ssim_cap = cap;
+    }
+    float *maps = static_cast<float *>(c->ssim_buf);
+    double *part = reinterpret_cast<double *>(static_cast<char *>(c->ssim_buf) +
+                                              align_up(sizeof(float) * 15 * (size_t)c->ssim_cap));
+    SsimWindow win{};
+    double g[11], sum = 0.0;
+    for (int k = -5; k <= 5; ++k) sum += (g[k + 5] = std::exp(-(double)(k * k) / 4.5));
+    for (int k = 0; k < 11; ++k) win.g[k] = (float)(g[k] / sum);
+    const double n = 3.0 * (double)P;
+    {
+        LaunchScope ls(c, K_SSIM_FWD, stream);
+        k_ssim_fwd<<<grid, 256, 0, stream>>>(W, H, rgb, obs_rgb, win, maps, loss ? part : nullptr);
+    }
+    if (loss) {   // weight (1 - sum SSIM / n) = (weight / n) (count - sum SSIM)
+        LaunchScope ls(c, K_SSIM_SUM, stream);
+        k_sum_partials<<<1, 1024, 0, stream>>>(part, (int)nb, -weight / n, weight / n, loss);
+    }
+    if (d_rgb) {
+        LaunchScope ls(c, K_SSIM_BWD, stream);
+        k_ssim_bwd<<<grid, 256, 0, stream>>>(W, H, rgb, obs_rgb, win, maps, (float)(-weight / n),
+                                             d_rgb);
+    }
+    VT_CUDA(cudaGetLastError(), "vt_ssim launch");
     return VT_OK;
 }
 

@@ -260,6 +260,15 @@ struct PoseAdamParams {
 };
 __global__ void k_pose_adam(double *pose, double *d_twist, double *state, PoseAdamParams prm);
 
+// SSIM term (vt_ssim.cu): the 11 normalised 1-D window weights.
+struct SsimWindow {
+    float g[11];
+};
+__global__ void k_ssim_fwd(int W, int H, const float *x, const float *y, SsimWindow win,
+                           float *maps, double *partials);
+__global__ void k_ssim_bwd(int W, int H, const float *x, const float *y, SsimWindow win,
+                           const float *maps, float scale, float *d_x);
+
 // Mapping optimiser step (vt_pose.cu).
 struct AttrAdamParams {
     float lr[5];

@@ -4,11 +4,12 @@ section and minimising the L1 terms of Eq. 2,
 
     rho |V - V'|_1 + sigma U |D - D'|_1        (rho = 0.8, sigma = 1.0),
 
-with U masking pixels without valid depth.  The SSIM term of Eq. 2 is not
-part of this driver.  Every step of an iteration runs in the vtsplat kernels:
-render, the masked L1 loss and its image gradient (vt_masked_l1), the
-attribute backward and one fused Adam step (vt_attr_adam; learning rates of
-the supplementary: colour 0.0025, radius 0.005, opacity 0.05).
+with U masking pixels without valid depth, plus tau L_S (tau = 0.2, Sec. 4;
+ssim=False leaves it out).  Every step of an iteration runs in the vtsplat
+kernels: render, the masked L1 loss and its image gradient (vt_masked_l1),
+the SSIM term accumulated into the same gradient (vt_ssim), the attribute
+backward and one fused Adam step (vt_attr_adam; learning rates of the
+supplementary: colour 0.0025, radius 0.005, opacity 0.05).
 
 The learning rates apply, as in the 3D Gaussian splatting family the paper
 builds on, to logit(opacity) and log(radius) (a reading: the paper gives the
@@ -29,13 +30,14 @@ from . import api
 class SectionMapper:
     def __init__(self, renderer: api.Renderer, section: api.Section, frames_rgb: torch.Tensor,
                  lr_colour: float = 0.0025, lr_opacity: float = 0.05, lr_radius: float = 0.005,
-                 rho: float = 0.8, sigma: float = 1.0):
+                 rho: float = 0.8, sigma: float = 1.0, tau: float = 0.2, ssim: bool = True):
         self.R = renderer
         self.sec = section
         self.rgb_obs = frames_rgb                      # (V, 3, H, W) float32, device
         self.depth_obs = section.depth                 # (V, H, W)
         self.V, self.H, self.W = section.depth.shape
-        self.rho, self.sigma = float(rho), float(sigma)
+        self.rho, self.sigma, self.tau = float(rho), float(sigma), float(tau)
+        self.use_ssim = bool(ssim)
         self.lr = [lr_colour] * 3 + [lr_opacity, lr_radius]
         dev = section.colour.device
         n = section.n
@@ -51,7 +53,8 @@ class SectionMapper:
         self.rgb = torch.empty(3, self.H, self.W, device=dev)
         self.depth = torch.empty(self.H, self.W, device=dev)
         self.sil = torch.empty(self.H, self.W, device=dev)
-        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.losses = torch.zeros(2, dtype=torch.float64, device=dev)   # L1 terms, SSIM term
+        self.loss = self.losses[:1]
         self.g_rgb = torch.zeros(3, self.H, self.W, device=dev)
         self.g_depth = torch.zeros(self.H, self.W, device=dev)
 
@@ -61,13 +64,16 @@ class SectionMapper:
                       self.depth, self.sil)
         self.R.masked_l1(self.rgb, self.depth, None, self.rgb_obs[view], self.depth_obs[view],
                          self.rho, self.sigma, d_rgb=self.g_rgb, d_depth=self.g_depth,
-                         loss=self.loss)
+                         loss=self.losses[0:1])
+        if self.use_ssim:
+            self.R.ssim(self.rgb, self.rgb_obs[view], self.tau, d_rgb=self.g_rgb,
+                        loss=self.losses[1:2])
         # the gradients were zeroed by the previous Adam step (and at construction)
         self.R.backward(self.g_rgb, self.g_depth, None,
                         attr_grads=[(self.d_colour, self.d_opacity, self.d_radius)])
         api.attr_adam(self.sec, self.theta, self.m, self.v, self.step_state, self.d_colour,
                       self.d_opacity, self.d_radius, self.lr, renderer=self.R)
-        return self.loss
+        return self.losses.sum() if self.use_ssim else self.losses[0]
 
 
 def random_views(n_views: int, iters: int, seed: int = 0):

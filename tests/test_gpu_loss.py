@@ -201,3 +201,32 @@ def test_mapper_reduces_loss(dev):
     mp = SectionMapper(R, sec, rgb)
     losses = [float(mp.step(i % 3).item()) for i in range(30)]
     assert losses[-1] < 0.8 * losses[0]
+
+
+@pytest.mark.parametrize("K", [syn.scaled_intrinsics(37, 23), syn.VGA, syn.scaled_intrinsics(4, 3)])
+def test_ssim_matches_reference(dev, K):
+    """SSIM term of Eq. 2 against the float64 reference on a rendered frame
+    and its neighbour (smooth texture, edges, borders): loss to 1e-6
+    relative; gradient to 1e-4 relative per tensor, and per element within
+    1e-4 max(|ref|, 1e-3 max|ref|) + 1e-4 m (m: componentwise magnitude of
+    the window sum, the same model as the attribute gradients); the gradient
+    accumulates into d_rgb."""
+    from oracle import ssim as os_
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(3)
+    fr = syn.render_frames(room, K, [path[0], path[2]])
+    x, y = fr.rgb[1], fr.rgb[0]
+    L, g, mag = os_.ssim_loss(x, y, 0.2, magnitude=True)
+    R = api.Renderer()
+    xd, yd = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+    d = torch.zeros(3, K.H, K.W, device=dev)
+    loss, d = R.ssim(xd, yd, 0.2, d_rgb=d)
+    torch.cuda.synchronize()
+    assert float(loss.item()) == pytest.approx(L, rel=1e-6, abs=1e-9)
+    got = d.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - g) <= 1e-4 * np.linalg.norm(g)
+    bound = 1e-4 * np.maximum(np.abs(g), 1e-3 * np.abs(g).max()) + 1e-4 * mag
+    assert np.all(np.abs(got - g) <= bound)
+    R.ssim(xd, yd, 0.2, d_rgb=d)                 # accumulates: twice the gradient
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy(), (2 * got).astype(np.float32))
