@@ -86,18 +86,23 @@ typedef struct {
     const void *radius;     /* n, activated value > 0 (metres, a standard deviation) */
 } vt_section;
 
-/* Per-section gradient buffers (device float32, accumulated with +=).  A
- * NULL pointer skips that gradient; a section whose three pointers are NULL
+/* Per-section gradient buffers (device, accumulated with +=).  A NULL
+ * pointer skips that gradient; a section whose attribute pointers are NULL
  * is frozen (only the learnable section gets gradients, Sec. 3.2 / Eq. 2). */
 typedef struct {
-    float *d_colour;  /* n x 3 */
-    float *d_opacity; /* n */
-    float *d_radius;  /* n */
+    float *d_colour;       /* n x 3, float32 */
+    float *d_opacity;      /* n, float32 */
+    float *d_radius;       /* n, float32 */
+    double *d_view_twist;  /* n_views x 6 (VT_GRAD_VIEWS): dL/d(rho, phi) of each source
+                              view's pose P_k for the right perturbation P_k Exp(xi) */
+    double *d_view_mat;    /* n_views x 12 (VT_GRAD_VIEWS): dL/dR_k (row-major), dL/dt_k */
 } vt_grads;
 
 typedef enum {
-    VT_GRAD_ATTR = 1, /* colour, opacity, radius (mapping, Eq. 2) */
-    VT_GRAD_POSE = 2  /* target camera pose (tracking, Eq. 1) */
+    VT_GRAD_ATTR = 1,  /* colour, opacity, radius (mapping, Eq. 2) */
+    VT_GRAD_POSE = 2,  /* target camera pose (tracking, Eq. 1) */
+    VT_GRAD_VIEWS = 4  /* source-view poses through the centres mu = R_k X_c + t_k
+                          (head-frame bundle adjustment, Sec. 3.4) */
 } vt_grad_mode;
 
 /* Opaque render context: the library-owned workspace (projected Gaussians,
@@ -197,6 +202,12 @@ vt_status vt_render(vt_ctx *ctx, const vt_section *secs, int32_t n_secs, const d
  * mode is a combination of vt_grad_mode bits.
  *   VT_GRAD_ATTR: grads[s] (host array of n_secs entries) receive
  *     dL/dcolour, dL/dopacity, dL/dradius of section s (+=, float32).
+ *   VT_GRAD_VIEWS: grads[s].d_view_twist / d_view_mat (device doubles, +=)
+ *     receive the gradients with respect to the poses of section s's source
+ *     views (sections with both NULL are skipped): per Gaussian dL/dx of its
+ *     centre (float32 accumulation), then per view FP64 sums
+ *     dL/dR_k = R sum g X_c^T, dL/dt_k = R sum g, dL/drho_k = R_k^T R sum g,
+ *     dL/dphi_k = sum X_c x (R_k^T R g), X_c = D ((u-cx)/fx, (v-cy)/fy, 1).
  *   VT_GRAD_POSE: d_twist (device, 6 doubles) += dL/d(rho, phi) for the
  *     right perturbation P exp(xi), xi = (rho, phi); d_mat (device, 12
  *     doubles) += dL/dR (row-major) and dL/dt.  The pose sums are reduced in

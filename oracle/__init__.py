@@ -71,7 +71,7 @@ class _Upstream(C.Structure):
 class _Grads(C.Structure):
     _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
                 ("a_colour", C.c_void_p), ("a_opacity", C.c_void_p), ("a_radius", C.c_void_p),
-                ("twist", C.c_double * 6), ("mat", C.c_double * 12),
+                ("d_x", C.c_void_p), ("twist", C.c_double * 6), ("mat", C.c_double * 12),
                 ("twist_noise", C.c_double * 6), ("mat_noise", C.c_double * 12)]
 
 
@@ -239,7 +239,8 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     term, i.e. of the absolute values of the products its formula adds;
     twist_noise (6,) and mat_noise (12,): per component
     sqrt(sum over pixels of n_p m_p^2), n_p the pixel's added Gaussians and
-    m_p the componentwise magnitude of the pixel's contribution)."""
+    m_p the componentwise magnitude of the pixel's contribution; x: per
+    section (n, 3) dL/dx of every centre in the target camera frame)."""
     secs, arr, keep = _sections(secs)
     ups = [None if g is None else np.ascontiguousarray(g, np.float64) for g in (g_rgb, g_depth, g_sil)]
     up = _Upstream(*[_ptr(u) for u in ups])
@@ -249,8 +250,9 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     acol = [np.zeros((s.n, 3)) for s in secs]
     aop = [np.zeros(s.n) for s in secs]
     arad = [np.zeros(s.n) for s in secs]
+    dx = [np.zeros((s.n, 3)) for s in secs]
     arrs = [(C.c_void_p * len(secs))(*[_ptr(a) for a in lst])
-            for lst in (dcol, dop, drad, acol, aop, arad)]
+            for lst in (dcol, dop, drad, acol, aop, arad, dx)]
     g = _Grads(*[C.cast(a, C.c_void_p) for a in arrs])
     cam = _camera(pose, K, W, H)
     rc = lib().orc_backward(C.byref(arr), len(secs), C.byref(cam), int(bool(binned)), C.byref(up),
@@ -259,7 +261,43 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
         raise RuntimeError("oracle backward failed")
     return dict(colour=dcol, opacity=dop, radius=drad, twist=np.array(g.twist[:]),
                 mat=np.array(g.mat[:]), abs_colour=acol, abs_opacity=aop, abs_radius=arad,
-                twist_noise=np.array(g.twist_noise[:]), mat_noise=np.array(g.mat_noise[:]))
+                twist_noise=np.array(g.twist_noise[:]), mat_noise=np.array(g.mat_noise[:]),
+                x=dx)
+
+
+def view_pose_grads(sec: Section, pose, d_x):
+    """Gradients with respect to the source-view poses P_k = [R_k | t_k] of a
+    section (head-frame bundle adjustment, Sec. 3.4) from d_x = dL/dx of its
+    centres in the target camera frame: the centre of Gaussian i of view k is
+    mu = R_k X_c + t_k, X_c = D ((u - cx)/fx, (v - cy)/fy, 1), and
+    x = R^T (mu - t), so dL/dmu = R dL/dx and
+        dL/dR_k = sum dL/dmu X_c^T,  dL/dt_k = sum dL/dmu,
+        dL/drho_k = R_k^T sum dL/dmu,  dL/dphi_k = sum X_c x (R_k^T dL/dmu)
+    for the right perturbation P_k Exp(xi).  Returns (twist (V, 6), mat
+    (V, 12)) float64."""
+    R = np.asarray(pose, np.float64).reshape(3, 4)[:, :3]
+    V = sec.poses.shape[0]
+    plane = sec.W * sec.H
+    src = sec.src.astype(np.int64)
+    view = src // plane
+    pix = src - view * plane
+    u = (pix % sec.W).astype(np.float64)
+    v = (pix // sec.W).astype(np.float64)
+    fx, fy, cx, cy = (float(np.float32(k)) for k in sec.K)
+    D = sec.depth.reshape(-1)[src].astype(np.float64)
+    Xc = np.stack([D * (u - cx) / fx, D * (v - cy) / fy, D], axis=1)
+    dmu = np.asarray(d_x, np.float64) @ R.T              # rows: R g
+    twist = np.zeros((V, 6))
+    mat = np.zeros((V, 12))
+    for k in range(V):
+        sel = view == k
+        Rk = sec.poses[k][:, :3]
+        mat[k, :9] = (dmu[sel].T @ Xc[sel]).reshape(-1)
+        mat[k, 9:] = dmu[sel].sum(0)
+        w = dmu[sel] @ Rk                                   # rows: R_k^T dL/dmu
+        twist[k, :3] = w.sum(0)
+        twist[k, 3:] = np.cross(Xc[sel], w).sum(0)
+    return twist, mat
 
 
 def zkeys(sec: Section, pose, K, W, H):

@@ -489,6 +489,9 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
                     }
                     double gv[3] = {gx, gy, gz};
                     const double *x = G->x;
+                    if (gr->d_x && gr->d_x[G->sec])
+                        for (int a = 0; a < 3; ++a)
+                            atomic_add(&gr->d_x[G->sec][3 * G->local + a], gv[a]);
                     ltw[0] -= gx;
                     ltw[1] -= gy;
                     ltw[2] -= gz;

@@ -73,6 +73,9 @@ typedef struct {
     double **a_opacity;          /* optional: the same for opacity (sum of |products| of the
                                     dL/dalpha formula times dalpha/do) */
     double **a_radius;           /* optional: the same for radius */
+    double **d_x;                /* optional, per section n x 3: dL/dx of each Gaussian's
+                                    centre in the target camera frame (summed over pixels);
+                                    the source-view pose gradients follow from it */
     double twist[6];             /* dL/d(rho, phi) for P(xi) = P * Exp(xi) */
     double mat[12];              /* dL/dR (row-major 3x3) then dL/dt */
     double twist_noise[6];       /* sqrt(sum over pixels of n_p m_p^2), n_p the pixel's added

@@ -15,7 +15,7 @@ from . import build as _build
 VT_OK, VT_ERR_INVALID_ARG, VT_ERR_OOM, VT_ERR_CUDA, VT_ERR_CAPACITY, VT_ERR_TIMEOUT, \
     VT_ERR_STATE = range(7)
 VT_F32, VT_F16 = 0, 1
-VT_GRAD_ATTR, VT_GRAD_POSE = 1, 2
+VT_GRAD_ATTR, VT_GRAD_POSE, VT_GRAD_VIEWS = 1, 2, 4
 
 STATUS_NAMES = {0: "VT_OK", 1: "VT_ERR_INVALID_ARG", 2: "VT_ERR_OOM", 3: "VT_ERR_CUDA",
                 4: "VT_ERR_CAPACITY", 5: "VT_ERR_TIMEOUT", 6: "VT_ERR_STATE"}
@@ -33,7 +33,8 @@ class SectionC(C.Structure):
 
 
 class GradsC(C.Structure):
-    _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p)]
+    _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
+                ("d_view_twist", C.c_void_p), ("d_view_mat", C.c_void_p)]
 
 
 class ViewC(C.Structure):

@@ -367,25 +367,33 @@ class Renderer:
         return rgb, depth, sil
 
     def backward(self, d_rgb=None, d_depth=None, d_sil=None, attr_grads=None, pose_grad=False,
-                 d_twist=None, d_mat=None, stream=None):
+                 d_twist=None, d_mat=None, view_grads=None, stream=None):
         """Backward of the last render.  attr_grads: per section a tuple
         (d_colour (n,3), d_opacity (n,), d_radius (n,)) float32 device tensors
         or None (frozen section); gradients are accumulated (+=).  With
         pose_grad, d_twist (6,) and d_mat (12,) float64 device tensors are
         accumulated (both created as zeros when neither is given; a missing
-        one is not computed when the other is).  Returns (d_twist, d_mat)."""
+        one is not computed when the other is).  view_grads: per section a
+        tuple (d_view_twist (V,6), d_view_mat (V,12)) float64 device tensors
+        (either may be None) or None: gradients with respect to the section's
+        source-view poses (head-frame bundle adjustment), accumulated.
+        Returns (d_twist, d_mat)."""
         mode = 0
         grads = None
-        if attr_grads is not None:
-            mode |= L.VT_GRAD_ATTR
+        if attr_grads is not None or view_grads is not None:
+            n = len(attr_grads) if attr_grads is not None else len(view_grads)
             gl = []
-            for g in attr_grads:
-                if g is None:
-                    gl.append(L.GradsC(None, None, None))
-                else:
-                    dc, do, dr = g
-                    gl.append(L.GradsC(_ptr(dc), _ptr(do), _ptr(dr)))
+            for s in range(n):
+                ag = attr_grads[s] if attr_grads is not None else None
+                vg = view_grads[s] if view_grads is not None else None
+                dc, do, dr = ag if ag is not None else (None, None, None)
+                vt, vm = vg if vg is not None else (None, None)
+                gl.append(L.GradsC(_ptr(dc), _ptr(do), _ptr(dr), _ptr(vt), _ptr(vm)))
             grads = (L.GradsC * len(gl))(*gl)
+            if attr_grads is not None:
+                mode |= L.VT_GRAD_ATTR
+            if view_grads is not None:
+                mode |= L.VT_GRAD_VIEWS
         if pose_grad:
             mode |= L.VT_GRAD_POSE
             dev = self.last[1].device if self.last else "cuda"

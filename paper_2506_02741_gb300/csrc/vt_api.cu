@@ -59,7 +59,8 @@ constexpr size_t kSortSmemBigBytes =
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
-    K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_SSIM_FWD, K_SSIM_BWD, K_SSIM_SUM, K_NUM
+    K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_SSIM_FWD, K_SSIM_BWD, K_SSIM_SUM,
+    K_VIEW_GRADS, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -68,7 +69,8 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "k_sort_tiles_long", "k_attr_scatter", "k_masked_l1",
                                    "k_sum_partials",  "k_pose_adam",     "k_adam_step_count",
                                    "k_attr_adam",     "k_sort_tiles_mid", "k_sort_tiles_large",
-                                   "k_ssim_fwd",      "k_ssim_bwd",       "k_ssim_sum"};
+                                   "k_ssim_fwd",      "k_ssim_bwd",       "k_ssim_sum",
+                                   "k_view_grads"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -113,6 +115,7 @@ struct vt_ctx {
     int64_t ssim_cap = 0;             // pixels it holds
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
     float *accr = nullptr;        // and radius, per Gaussian
+    float4 *accg = nullptr;       // dL/dx of each centre (source-view gradients)
     // per-pixel lists of added Gaussians (separate allocation)
     int list_cap = kDefaultListCap;
     uint2 *plist = nullptr;       // (id, transmittance in front) per added Gaussian
@@ -195,6 +198,7 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += align_up(sizeof(double) * 12);                  // pose copy
     b += align_up(sizeof(uint32_t) * 8 * t);             // block overflow flags
     b += align_up(sizeof(float4) * g) + align_up(sizeof(float) * g);   // gradient accumulators
+    b += align_up(sizeof(float4) * g);                   // centre gradients
     return b;
 }
 
@@ -248,6 +252,7 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->blk_ovf = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * 8 * t));
     c->acc4 = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
     c->accr = reinterpret_cast<float *>(take(sizeof(float) * g));
+    c->accg = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
     c->cap_g = g;
     c->cap_i = i;
     c->cap_p = p;
@@ -620,10 +625,10 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
                              double *d_twist, double *d_mat, vt_stream stream) {
     if (!c) return fail(VT_ERR_INVALID_ARG, "vt_render_backward: ctx is NULL");
     if (!c->has_render) return fail(VT_ERR_STATE, "vt_render_backward: no render on this context");
-    if (mode & ~(VT_GRAD_ATTR | VT_GRAD_POSE))
+    if (mode & ~(VT_GRAD_ATTR | VT_GRAD_POSE | VT_GRAD_VIEWS))
         return fail(VT_ERR_INVALID_ARG, "vt_render_backward: unknown mode bits 0x%x", mode);
-    if ((mode & VT_GRAD_ATTR) && !grads && c->table.n > 0)
-        return fail(VT_ERR_INVALID_ARG, "vt_render_backward: ATTR mode needs grads");
+    if ((mode & (VT_GRAD_ATTR | VT_GRAD_VIEWS)) && !grads && c->table.n > 0)
+        return fail(VT_ERR_INVALID_ARG, "vt_render_backward: ATTR / VIEWS mode needs grads");
     if ((mode & VT_GRAD_POSE) && !d_twist && !d_mat)
         return fail(VT_ERR_INVALID_ARG, "vt_render_backward: POSE mode needs d_twist or d_mat");
     if (!mode) return VT_OK;
@@ -634,7 +639,14 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
             T.s[s].d_opacity = grads[s].d_opacity;
             T.s[s].d_radius = grads[s].d_radius;
         }
+        if (mode & VT_GRAD_VIEWS) {
+            T.s[s].d_view_twist = grads[s].d_view_twist;
+            T.s[s].d_view_mat = grads[s].d_view_mat;
+        }
     }
+    const bool views = (mode & VT_GRAD_VIEWS) != 0;
+    if (views && T.n_total > 0)
+        VT_CUDA(cudaMemsetAsync(c->accg, 0, sizeof(float4) * T.n_total, stream), "grad acc reset");
     const bool attr = (mode & VT_GRAD_ATTR) != 0;
     if (attr && T.n_total > 0) {
         VT_CUDA(cudaMemsetAsync(c->acc4, 0, sizeof(float4) * T.n_total, stream), "grad acc reset");
@@ -642,21 +654,29 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
     }
     if (c->used_lists) {
         LaunchScope ls(c, K_BWD_LIST, stream);
-        k_composite_bwd_list<<<c->n_tiles, kBlockPix, 0, stream>>>(
+        auto kern = views ? k_composite_bwd_list_views : k_composite_bwd_list;
+        kern<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->blk_ovf,
-            dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->acc4, c->accr, c->status);
+            dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->acc4, c->accr, c->accg,
+            c->status);
     }
     {   // tiles without complete per-pixel lists (all of them when none were kept)
         LaunchScope ls(c, K_BWD, stream);
         k_composite_bwd<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, dL_drgb,
-            dL_ddepth, dL_dsil, mode, c->pose_partials, c->blk_ovf, c->acc4, c->accr,
+            dL_ddepth, dL_dsil, mode, c->pose_partials, c->blk_ovf, c->acc4, c->accr, c->accg,
             c->status);
     }
     if (attr && T.n_total > 0) {
         LaunchScope ls(c, K_SCATTER, stream);
         k_attr_scatter<<<(unsigned)((T.n_total + 255) / 256), 256, 0, stream>>>(T, c->acc4,
                                                                                c->accr);
+    }
+    if (views && T.n_total > 0) {
+        int n_views = 0;
+        for (int s = 0; s < T.n; ++s) n_views += T.s[s].n_views;
+        LaunchScope ls(c, K_VIEW_GRADS, stream);
+        k_view_grads<<<n_views, kBlockPix, 0, stream>>>(T, c->accg, c->pose_copy);
     }
     if (mode & VT_GRAD_POSE) {
         LaunchScope ls(c, K_POSE, stream);

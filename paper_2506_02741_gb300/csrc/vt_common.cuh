@@ -41,6 +41,7 @@ struct SecDesc {
     const uint32_t *src;
     const void *colour, *opacity, *radius;
     float *d_colour, *d_opacity, *d_radius;  // backward only
+    double *d_view_twist, *d_view_mat;        // backward only (source-view poses)
     int64_t gbase, n;       // global id range [gbase, gbase + n)
     int64_t tab_base;       // first table row of view 0
     int32_t view_base;      // first ViewXf of this section
@@ -222,14 +223,22 @@ __global__ void k_composite_bwd(SecTable T, Camera cam, const uint32_t *tile_off
                                 const uint32_t *pix_last, const float *pix_T,
                                 const float *g_rgb, const float *g_depth, const float *g_sil,
                                 int mode, double *pose_partials, const uint32_t *tile_mask,
-                                float4 *acc4, float *accr, const Status *st);
+                                float4 *acc4, float *accr, float4 *accg, const Status *st);
 __global__ void k_composite_bwd_list(SecTable T, Camera cam, const float4 *geo,
                                      const float4 *app, const uint32_t *pix_nadd,
                                      const float *pix_T, const uint2 *plist, int plist_cap,
                                      const uint32_t *blk_ovf, const float *g_rgb,
                                      const float *g_depth, const float *g_sil, int mode,
                                      double *pose_partials, float4 *acc4, float *accr,
-                                     const Status *st);
+                                     float4 *accg, const Status *st);
+__global__ void k_composite_bwd_list_views(SecTable T, Camera cam, const float4 *geo,
+                                           const float4 *app, const uint32_t *pix_nadd,
+                                           const float *pix_T, const uint2 *plist, int plist_cap,
+                                           const uint32_t *blk_ovf, const float *g_rgb,
+                                           const float *g_depth, const float *g_sil, int mode,
+                                           double *pose_partials, float4 *acc4, float *accr,
+                                           float4 *accg, const Status *st);
+__global__ void k_view_grads(SecTable T, const float4 *accg, const double *pose_copy);
 __global__ void k_attr_scatter(SecTable T, const float4 *acc4, const float *accr);
 
 // Loss inputs (vt_loss.cu).

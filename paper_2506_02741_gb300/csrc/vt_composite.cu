@@ -297,7 +297,8 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
                                          const float4 &a, float t, float du, float dv, float G,
                                          float ah, const Camera &cam, bool want_pose, PoseAcc &acc,
                                          float &dc0, float &dc1, float &dc2, float &dop,
-                                         float &drd, float Ti_fwd = -1.f) {
+                                         float &drd, bool want_geo, float &gxo, float &gyo,
+                                         float &gzo, float Ti_fwd = -1.f) {
     const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
     const float al = fminf(ah, kAlphaClamp);
     const float om = 1.f - al;
@@ -328,11 +329,18 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
         dq = -0.5f * ah * dal;
     }
     drd = dq * (-2.f * q * ir);
-    if (want_pose) {
+    gxo = gyo = gzo = 0.f;
+    if (want_pose || want_geo) {
         const float ex = z * du * ifx, ey = z * dv * ify;
         const float gx = dq * (-2.f * ex * ir2);
         const float gy = dq * (-2.f * ey * ir2);
         const float gz = dq * (2.f * (P.pxn * ex + P.pyn * ey) * ir2) + P.gD * w;
+        gxo = gx;
+        gyo = gy;
+        gzo = gz;
+    }
+    if (want_pose) {
+        const float gx = gxo, gy = gyo, gz = gzo;
         const float uc = (float)__float_as_int(g0.x) + g0.y;
         const float vc = (float)__float_as_int(g0.z) + g0.w;
         const float X[3] = {z * (uc - cam.cx) * ifx, z * (vc - cam.cy) * ify, z};
@@ -354,17 +362,24 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
     P.T = Ti;
 }
 
-// Attribute gradient terms go to a workspace accumulator indexed by Gaussian
-// id: one 16-byte vector atomic for (colour, opacity) and one for the radius
-// instead of five scalar ones; k_attr_scatter then adds them to the caller's
-// per-section buffers.  Gaussians of frozen sections are skipped.
-__device__ __forceinline__ void add_attr_grads(const SecTable &Tab, int64_t g, float dc0,
-                                               float dc1, float dc2, float dop, float drd,
-                                               float4 *acc4, float *accr) {
+// Per-Gaussian gradient terms go to workspace accumulators indexed by
+// Gaussian id: one 16-byte vector atomic for (colour, opacity), one for the
+// radius instead of five scalar ones (k_attr_scatter then adds them to the
+// caller's per-section buffers), and with source-view gradients one for dL/dx
+// of the centre (k_view_grads reduces them per view).  Gaussians of sections
+// that want neither are skipped.
+__device__ __forceinline__ void add_pair_grads(const SecTable &Tab, int64_t g, bool want_attr,
+                                               bool want_views, float dc0, float dc1, float dc2,
+                                               float dop, float drd, float gx, float gy,
+                                               float gz, float4 *acc4, float *accr,
+                                               float4 *accg) {
     const SecDesc &S = Tab.s[find_section(Tab, g)];
-    if (!S.d_colour && !S.d_opacity && !S.d_radius) return;
-    atomicAdd(acc4 + g, make_float4(dc0, dc1, dc2, dop));
-    atomicAdd(accr + g, drd);
+    if (want_attr && (S.d_colour || S.d_opacity || S.d_radius)) {
+        atomicAdd(acc4 + g, make_float4(dc0, dc1, dc2, dop));
+        atomicAdd(accr + g, drd);
+    }
+    if (want_views && (S.d_view_twist || S.d_view_mat))
+        atomicAdd(accg + g, make_float4(gx, gy, gz, 0.f));
 }
 
 __global__ void __launch_bounds__(256) k_attr_scatter(SecTable Tab, const float4 *acc4,
@@ -411,7 +426,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     SecTable Tab, Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
     const float4 *app, const uint32_t *pix_last, const float *pix_T,
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
-    double *pose_partials, const uint32_t *tile_mask, float4 *acc4, float *accr,
+    double *pose_partials, const uint32_t *tile_mask, float4 *acc4, float *accr, float4 *accg,
     const Status *st) {
     __shared__ float4 s_g0[kBatch], s_g1[kBatch], s_a[kBatch];
     __shared__ float s_tmin[kBatch];
@@ -430,6 +445,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     const float lymax = (float)min(3, cam.H - 1 - by0);
     const uint32_t start = tile_off[tile];
     const bool want_attr = (mode & VT_GRAD_ATTR) != 0, want_pose = (mode & VT_GRAD_POSE) != 0;
+    const bool want_views = (mode & VT_GRAD_VIEWS) != 0;
 
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t p = inside ? (size_t)py * cam.W + px : 0;
@@ -488,6 +504,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                         mask &= ~(1u << bit);
                         const int j = j0 + bit;
                         float dc0 = 0.f, dc1 = 0.f, dc2 = 0.f, dop = 0.f, drd = 0.f;
+                        float gx = 0.f, gy = 0.f, gz = 0.f;
                         bool contrib = false;
                         if ((uint32_t)(b0 + j) < my_last) {
                             const float4 g0 = s_g0[j], g1 = s_g1[j];
@@ -498,17 +515,21 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                                 const float ah = __fmul_rn(g1.w, G);
                                 contrib = true;
                                 bwd_pair(P, g0, g1, s_a[j], t, du, dv, G, ah, cam, want_pose,
-                                         acc, dc0, dc1, dc2, dop, drd);
+                                         acc, dc0, dc1, dc2, dop, drd, want_views, gx, gy, gz);
                             }
                         }
-                        if (want_attr && __any_sync(kFullMask, contrib)) {
+                        if ((want_attr || want_views) && __any_sync(kFullMask, contrib)) {
                             dc0 = warp_sum(dc0);
                             dc1 = warp_sum(dc1);
                             dc2 = warp_sum(dc2);
                             dop = warp_sum(dop);
                             drd = warp_sum(drd);
+                            gx = warp_sum(gx);
+                            gy = warp_sum(gy);
+                            gz = warp_sum(gz);
                             if (lane == 0)
-                                add_attr_grads(Tab, s_gid[j], dc0, dc1, dc2, dop, drd, acc4, accr);
+                                add_pair_grads(Tab, s_gid[j], want_attr, want_views, dc0, dc1,
+                                               dc2, dop, drd, gx, gy, gz, acc4, accr, accg);
                         }
                     }
                 }
@@ -524,12 +545,16 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
 // ahead.  No filtering and no block barriers in the walk; tiles with a block
 // flagged in blk_ovf (a pixel exceeded the list capacity) are left to
 // k_composite_bwd.
-__global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
-    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
-    const uint32_t *blk_ovf,
-    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
-    double *pose_partials, float4 *acc4, float *accr, const Status *st) {
-    __shared__ double s_pose[kBlockPix / 32][12];
+// Views = true compiles the source-view gradient path (mode VT_GRAD_VIEWS)
+// into k_composite_bwd_list_views; the tracking and mapping paths launch
+// k_composite_bwd_list, which does not carry it.
+template <bool Views>
+__device__ __forceinline__ void bwd_list_body(
+    const SecTable &Tab, const Camera &cam, const float4 *geo, const float4 *app,
+    const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
+    const uint32_t *blk_ovf, const float *g_rgb, const float *g_depth, const float *g_sil,
+    int mode, double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st,
+    double (*s_pose)[12]) {
     if (st->flags) return;
     const int tile = blockIdx.x;
     if (tile_flagged(blk_ovf, tile)) return;
@@ -539,6 +564,7 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
     const int py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
     const bool inside = px < cam.W && py < cam.H;
     const bool want_attr = (mode & VT_GRAD_ATTR) != 0, want_pose = (mode & VT_GRAD_POSE) != 0;
+    const bool want_views = Views && (mode & VT_GRAD_VIEWS) != 0;
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t p = inside ? (size_t)py * cam.W + px : 0;
     int n = inside ? (int)pix_nadd[p] : 0;
@@ -585,11 +611,128 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
         const float t = pair_t_at(px, py, g0, g1, du, dv);
         const float G = exp2_approx(t);
         const float ah = __fmul_rn(g1.w, G);
-        float dc0, dc1, dc2, dop, drd;
-        bwd_pair(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd, Ti);
-        if (want_attr) add_attr_grads(Tab, g, dc0, dc1, dc2, dop, drd, acc4, accr);
+        float dc0, dc1, dc2, dop, drd, gx, gy, gz;
+        bwd_pair(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd,
+                 want_views, gx, gy, gz, Ti);
+        if (want_attr || want_views)
+            add_pair_grads(Tab, g, want_attr, want_views, dc0, dc1, dc2, dop, drd, gx, gy, gz,
+                           acc4, accr, accg);
     }
     if (want_pose) write_pose_partial(acc, s_pose, pose_partials, tile);
+}
+
+__global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
+    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
+    const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *blk_ovf,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st) {
+    __shared__ double s_pose[kBlockPix / 32][12];
+    bwd_list_body<false>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf, g_rgb,
+                         g_depth, g_sil, mode, pose_partials, acc4, accr, accg, st, s_pose);
+}
+
+__global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_views(
+    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
+    const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *blk_ovf,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st) {
+    __shared__ double s_pose[kBlockPix / 32][12];
+    bwd_list_body<true>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf, g_rgb,
+                        g_depth, g_sil, mode, pose_partials, acc4, accr, accg, st, s_pose);
+}
+
+// Source-view pose gradients (head-frame bundle adjustment, Sec. 3.4): one
+// block per (section, view); the view's Gaussians are a contiguous range of
+// the section (ids are in (view, pixel) order).  FP64 fixed-order sums over
+// them of g X_c^T and g, with g = dL/dx of the centre in the target frame and
+// X_c = D ((u - cx)/fx, (v - cy)/fy, 1); then
+//   dL/dR_k = R A,  dL/dt_k = R s,  dL/drho_k = R_k^T R s,
+//   dL/dphi_k = sum X_c x (R_k^T R g)   (from B = R_k^T R A),
+// accumulated (+=) into the section's outputs.
+__global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *accg,
+                                                    const double *pose_copy) {
+    __shared__ double red[12][kBlockPix / 32];
+    __shared__ int64_t range[2];
+    int b = blockIdx.x, s = 0;
+    for (; s < Tab.n; ++s) {
+        if (b < Tab.s[s].n_views) break;
+        b -= Tab.s[s].n_views;
+    }
+    if (s >= Tab.n) return;
+    const SecDesc &S = Tab.s[s];
+    if (!S.d_view_twist && !S.d_view_mat) return;
+    const int k = b;
+    const uint32_t plane = (uint32_t)S.W * (uint32_t)S.H;
+    if (threadIdx.x < 2) {   // first index with src >= (k + threadIdx.x) * plane
+        const uint64_t key = (uint64_t)(k + threadIdx.x) * plane;
+        int64_t lo = 0, hi = S.n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((uint64_t)S.src[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        range[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    double acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+    for (int64_t i = range[0] + threadIdx.x; i < range[1]; i += blockDim.x) {
+        const float4 g = accg[S.gbase + i];
+        if (g.x == 0.f && g.y == 0.f && g.z == 0.f) continue;
+        const uint32_t src = S.src[i], pix = src - (uint32_t)k * plane;
+        const uint32_t v = pix / (uint32_t)S.W, u = pix - v * (uint32_t)S.W;
+        const double D = (double)S.depth[src];
+        const double X[3] = {D * (((double)u - (double)S.cx) / (double)S.fx),
+                             D * (((double)v - (double)S.cy) / (double)S.fy), D};
+        const double gv[3] = {(double)g.x, (double)g.y, (double)g.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[3 * a + c] += gv[a] * X[c];
+            acc[9 + a] += gv[a];
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        const double v = warp_sum_d(acc[i]);
+        if (lane == 0) red[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double A[9], sv[3];
+    for (int i = 0; i < 12; ++i) {
+        double t = 0.0;
+        for (int w = 0; w < kBlockPix / 32; ++w) t += red[i][w];
+        if (i < 9) A[i] = t;
+        else sv[i - 9] = t;
+    }
+    const double *R = pose_copy, *Rk = S.poses + 12 * k;
+    double Am[9], sm[3];
+    for (int a = 0; a < 3; ++a) {
+        for (int c = 0; c < 3; ++c)
+            Am[3 * a + c] = R[3 * a] * A[c] + R[3 * a + 1] * A[3 + c] + R[3 * a + 2] * A[6 + c];
+        sm[a] = R[3 * a] * sv[0] + R[3 * a + 1] * sv[1] + R[3 * a + 2] * sv[2];
+    }
+    if (S.d_view_mat) {
+        double *o = S.d_view_mat + 12 * k;
+        for (int i = 0; i < 9; ++i) o[i] += Am[i];
+        for (int a = 0; a < 3; ++a) o[9 + a] += sm[a];
+    }
+    if (S.d_view_twist) {
+        double B[9], rho[3];
+        for (int c = 0; c < 3; ++c) {
+            for (int e = 0; e < 3; ++e)
+                B[3 * c + e] = Rk[c] * Am[e] + Rk[3 + c] * Am[3 + e] + Rk[6 + c] * Am[6 + e];
+            rho[c] = Rk[c] * sm[0] + Rk[3 + c] * sm[1] + Rk[6 + c] * sm[2];
+        }
+        double *o = S.d_view_twist + 6 * k;
+        for (int c = 0; c < 3; ++c) o[c] += rho[c];
+        o[3] += B[2 * 3 + 1] - B[1 * 3 + 2];
+        o[4] += B[0 * 3 + 2] - B[2 * 3 + 0];
+        o[5] += B[1 * 3 + 0] - B[0 * 3 + 1];
+    }
 }
 
 // Fixed-order FP64 sum of the per-tile partials, then

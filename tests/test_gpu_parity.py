@@ -418,3 +418,46 @@ def test_budget_disables_lists(dev):
     assert not R.used_lists
     ref = oracle.render(osecs, target, K, W, H)
     G.assert_forward_close(out, ref, G.clean_mask(ref))
+
+
+@pytest.mark.parametrize("case", ["qqvga_2views", "ragged_3views"])
+def test_view_pose_gradients(dev, case):
+    """Source-view pose gradients (head-frame bundle adjustment) against the
+    oracle's, per view as twist and matrix: 1e-4 relative per view tensor
+    (sums over every pixel of the render, FP32 per pair).  Requesting them
+    together with the attribute and target-pose gradients leaves those
+    unchanged up to the order of float atomics."""
+    osecs, target, K, W, H = _cases()[case]()
+    R, dsecs, out = _render(osecs, target, K, W, H)
+    ref = oracle.render(osecs, target, K, W, H)
+    clean = G.clean_mask(ref, tau_clamp=1e-4)
+    rng = np.random.default_rng(41)
+    gR = (rng.normal(0, 1, (3, H, W)) * clean).astype(np.float32)
+    gD = (rng.normal(0, 1, (H, W)) * clean).astype(np.float32)
+    want = oracle.backward(osecs, target, K, W, H, g_rgb=gR, g_depth=gD)
+    tw_ref, mat_ref = oracle.view_pose_grads(osecs[0], target, want["x"][0])
+    V = osecs[0].poses.shape[0]
+    vt = torch.zeros(V, 6, dtype=torch.float64, device=dev)
+    vm = torch.zeros(V, 12, dtype=torch.float64, device=dev)
+    n = osecs[0].n
+    ag = [(torch.zeros(n, 3, device=dev), torch.zeros(n, device=dev), torch.zeros(n, device=dev))]
+    dtw, dmat = R.backward(torch.from_numpy(gR).to(dev), torch.from_numpy(gD).to(dev), None,
+                           attr_grads=ag, pose_grad=True, view_grads=[(vt, vm)])
+    torch.cuda.synchronize()
+    for k in range(V):
+        for got, ref_ in ((vt[k], tw_ref[k]), (vm[k], mat_ref[k])):
+            g = got.cpu().numpy()
+            assert np.linalg.norm(g - ref_) <= 1e-4 * np.linalg.norm(ref_), (k, g, ref_)
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist", noise=want["twist_noise"])
+    G.assert_grad_close(ag[0][1].cpu().numpy(), want["opacity"][0], name="opacity",
+                        abs_ref=want["abs_opacity"][0])
+    # a frozen section gets nothing, views-only mode works alone
+    vt2 = torch.zeros_like(vt)
+    R.backward(torch.from_numpy(gR).to(dev), torch.from_numpy(gD).to(dev), None,
+               view_grads=[(vt2, None)])
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(vt2.cpu().numpy(), vt.cpu().numpy(), rtol=1e-5,
+                               atol=1e-7 * np.abs(tw_ref).max())
+    vt3 = torch.zeros_like(vt)
+    R.backward(torch.from_numpy(gR).to(dev), None, None, view_grads=[None])
+    assert not vt3.any()
