@@ -245,6 +245,18 @@ vt_status vt_visibility(const float *depth, int32_t W, int32_t H, vt_intrinsics 
                         const double *pose12, const vt_view *views, int32_t n_views,
                         double rel_tol, uint8_t *visible, vt_stream stream);
 
+/* Overlap-section selection (Sec. 3.3): the head frame's depth (device,
+ * H x W), back-projected with its initial pose12 (device), checked against
+ * each view of views[0, n_views) separately with the test of vt_visibility;
+ * counts[k] (device uint32, overwritten) = number of valid pixels visible to
+ * view k; *n_valid (device uint32, overwritten, may be NULL) = number of valid
+ * pixels.  The paper keeps the candidate views (every N1 = 5th frame) whose
+ * visible fraction exceeds gamma (0.24-0.26). */
+vt_status vt_visibility_counts(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                               const double *pose12, const vt_view *views, int32_t n_views,
+                               double rel_tol, uint32_t *counts, uint32_t *n_valid,
+                               vt_stream stream);
+
 /* Weights and masks of the masked L1 loss. */
 typedef struct {
     double w_rgb;             /* alpha of Eq. 1, rho of Eq. 2 */

@@ -94,6 +94,9 @@ def _declare(L):
         "vt_section_complement": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, Intrinsics,
                                             C.c_float, C.c_int32, C.c_int, _P, _P, _P, _P,
                                             C.c_int64, _P, _P]),
+        "vt_visibility_counts": (C.c_int, [_P, C.c_int32, C.c_int32, Intrinsics, _P,
+                                           C.POINTER(ViewC), C.c_int32, C.c_double, _P, _P,
+                                           _P]),
         "vt_ssim": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P, _P]),
         "vt_ctx_set_timing": (C.c_int, [_P, C.c_int32]),
         "vt_ctx_timing": (C.c_int32, [_P, _P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
@@ -121,7 +124,8 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_ctx_debug_copy", "vt_last_error", "vt_version", "vt_ctx_set_list_capacity",
            "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists",
            "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam",
-           "vt_attr_adam", "vt_section_complement", "vt_ssim"]
+           "vt_attr_adam", "vt_section_complement", "vt_ssim",
+           "vt_visibility_counts"]
 
 
 def lib_path() -> str:

@@ -215,6 +215,34 @@ def visibility(depth: torch.Tensor, K, pose, views, rel_tol: float = 0.01, out=N
     return out
 
 
+def visibility_counts(depth: torch.Tensor, K, pose, views, rel_tol: float = 0.01, stream=None):
+    """Per view, the number of valid pixels of ``depth`` (seen from ``pose``)
+    visible to it (views as in visibility(); any number, 8 per launch), and
+    the number of valid pixels.  Returns (counts (len(views),) int64 numpy,
+    n_valid); synchronises once."""
+    depth = _cuda(depth, torch.float32, "depth")
+    H, W = depth.shape
+    dev = depth.device
+    P = pose if isinstance(pose, torch.Tensor) else pose12(pose, dev)
+    P = _cuda(P, torch.float64, "pose", (12,))
+    counts = torch.zeros(max(len(views), 1), dtype=torch.int32, device=dev)
+    n_valid = torch.zeros(1, dtype=torch.int32, device=dev)
+    keep = []
+    for b in range(0, len(views), L.MAX_VIS_VIEWS):
+        vs = []
+        for d, k, p in views[b:b + L.MAX_VIS_VIEWS]:
+            d = _cuda(d, torch.float32, "view depth")
+            p = _cuda(p, torch.float64, "view pose", (12,))
+            keep += [d, p]
+            vs.append(L.ViewC(_ptr(d), d.shape[1], d.shape[0], _intr(k), _ptr(p)))
+        arr = (L.ViewC * len(vs))(*vs)
+        L.check(L.lib().vt_visibility_counts(_ptr(depth), W, H, _intr(K), _ptr(P), arr, len(vs),
+                                             float(rel_tol), C.c_void_p(counts.data_ptr() + 4 * b),
+                                             _ptr(n_valid), _stream(stream)),
+                "vt_visibility_counts")
+    return counts[:len(views)].cpu().numpy().astype(np.int64), int(n_valid.item())
+
+
 def pose_adam(pose: torch.Tensor, d_twist: torch.Tensor, state: torch.Tensor, lr,
               beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, renderer=None,
               stream=None):

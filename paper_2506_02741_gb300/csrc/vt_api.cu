@@ -687,29 +687,57 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
     return VT_OK;
 }
 
-vt_status vt_visibility(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
-                        const double *pose12, const vt_view *views, int32_t n_views,
-                        double rel_tol, uint8_t *visible, vt_stream stream) {
-    vt_status st = check_image(W, H, "vt_visibility");
+// Shared checks of the visibility entry points; fills vv.
+static vt_status vis_args(const char *who, const float *depth, int32_t W, int32_t H,
+                          vt_intrinsics K, const double *pose12, const vt_view *views,
+                          int32_t n_views, double rel_tol, const void *out, VisViews &vv) {
+    vt_status st = check_image(W, H, who);
     if (st) return st;
-    if ((st = check_intrinsics(K, "vt_visibility"))) return st;
-    if (!depth || !pose12 || !visible || !views)
-        return fail(VT_ERR_INVALID_ARG, "vt_visibility: NULL depth, pose, views or output");
+    if ((st = check_intrinsics(K, who))) return st;
+    if (!depth || !pose12 || !out || !views)
+        return fail(VT_ERR_INVALID_ARG, "%s: NULL depth, pose, views or output", who);
     if (n_views < 1 || n_views > VT_MAX_VIS_VIEWS)
-        return fail(VT_ERR_INVALID_ARG, "vt_visibility: n_views = %d outside [1, %d]", n_views,
+        return fail(VT_ERR_INVALID_ARG, "%s: n_views = %d outside [1, %d]", who, n_views,
                     VT_MAX_VIS_VIEWS);
     if (!(std::isfinite(rel_tol) && rel_tol >= 0.0))
-        return fail(VT_ERR_INVALID_ARG, "vt_visibility: rel_tol must be finite and >= 0");
-    VisViews vv{};
+        return fail(VT_ERR_INVALID_ARG, "%s: rel_tol must be finite and >= 0", who);
+    vv = VisViews{};
     vv.n = n_views;
     for (int k = 0; k < n_views; ++k) {
         const vt_view &V = views[k];
-        if ((st = check_image(V.W, V.H, "vt_visibility view"))) return st;
-        if ((st = check_intrinsics(V.K, "vt_visibility view"))) return st;
+        if ((st = check_image(V.W, V.H, who))) return st;
+        if ((st = check_intrinsics(V.K, who))) return st;
         if (!V.depth || !V.pose12)
-            return fail(VT_ERR_INVALID_ARG, "vt_visibility: view %d has NULL depth or pose", k);
+            return fail(VT_ERR_INVALID_ARG, "%s: view %d has NULL depth or pose", who, k);
         vv.v[k] = VisView{V.depth, V.W, V.H, V.K.fx, V.K.fy, V.K.cx, V.K.cy, V.pose12};
     }
+    return VT_OK;
+}
+
+vt_status vt_visibility_counts(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                               const double *pose12, const vt_view *views, int32_t n_views,
+                               double rel_tol, uint32_t *counts, uint32_t *n_valid,
+                               vt_stream stream) {
+    VisViews vv;
+    vt_status st = vis_args("vt_visibility_counts", depth, W, H, K, pose12, views, n_views,
+                            rel_tol, counts, vv);
+    if (st) return st;
+    VT_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_views, stream), "counts reset");
+    if (n_valid) VT_CUDA(cudaMemsetAsync(n_valid, 0, sizeof(uint32_t), stream), "counts reset");
+    const int64_t P = (int64_t)W * H;
+    k_visibility_counts<<<(unsigned)((P + 255) / 256), 256, 0, stream>>>(
+        depth, W, H, K.fx, K.fy, K.cx, K.cy, pose12, vv, rel_tol, counts, n_valid);
+    VT_CUDA(cudaGetLastError(), "vt_visibility_counts launch");
+    return VT_OK;
+}
+
+vt_status vt_visibility(const float *depth, int32_t W, int32_t H, vt_intrinsics K,
+                        const double *pose12, const vt_view *views, int32_t n_views,
+                        double rel_tol, uint8_t *visible, vt_stream stream) {
+    VisViews vv;
+    vt_status st = vis_args("vt_visibility", depth, W, H, K, pose12, views, n_views, rel_tol,
+                            visible, vv);
+    if (st) return st;
     const int64_t P = (int64_t)W * H;
     k_visibility<<<(unsigned)((P + 255) / 256), 256, 0, stream>>>(
         depth, W, H, K.fx, K.fy, K.cx, K.cy, pose12, vv, rel_tol, visible);

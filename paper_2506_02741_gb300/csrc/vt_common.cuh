@@ -255,6 +255,9 @@ struct VisViews {
 __global__ void k_visibility(const float *depth, int W, int H, float fx, float fy, float cx,
                              float cy, const double *pose, VisViews views, double rel_tol,
                              uint8_t *visible);
+__global__ void k_visibility_counts(const float *depth, int W, int H, float fx, float fy,
+                                    float cx, float cy, const double *pose, VisViews views,
+                                    double rel_tol, uint32_t *counts, uint32_t *n_valid);
 __global__ void k_masked_l1(int64_t P, const float *rgb, const float *depth, const float *sil,
                             const float *obs_rgb, const float *obs_depth, const uint8_t *visible,
                             float sil_min, int rgb_needs_depth, float gc, float gd, float *d_rgb,

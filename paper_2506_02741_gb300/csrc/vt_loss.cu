@@ -34,6 +34,40 @@ __device__ __forceinline__ bool interp_depth(const VisView &V, double x, double 
     return true;
 }
 
+// World point of pixel p of the current frame (false for invalid depth).
+__device__ __forceinline__ bool world_point(const float *depth, int W, int64_t p, float fx,
+                                            float fy, float cx, float cy, const double *pose,
+                                            double X[3]) {
+    const int v = (int)(p / W), u = (int)(p - (int64_t)v * W);
+    const float D = depth[p];
+    if (!valid_depth(D)) return false;
+    const double a = __ddiv_rn(__dsub_rn((double)u, (double)cx), (double)fx);
+    const double b = __ddiv_rn(__dsub_rn((double)v, (double)cy), (double)fy);
+    const double xc0 = __dmul_rn((double)D, a), xc1 = __dmul_rn((double)D, b), xc2 = (double)D;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        X[i] = __dadd_rn(dot3(pose[3 * i], xc0, pose[3 * i + 1], xc1, pose[3 * i + 2], xc2),
+                         pose[9 + i]);
+    return true;
+}
+
+// Is world point X visible to view V: in front, projecting inside, and within
+// rel_tol of the view's interpolated depth.
+__device__ __forceinline__ bool visible_to(const VisView &V, const double X[3], double rel_tol) {
+    const double *Pk = V.pose;
+    const double d0 = __dsub_rn(X[0], Pk[9]), d1 = __dsub_rn(X[1], Pk[10]),
+                 d2 = __dsub_rn(X[2], Pk[11]);
+    const double x0 = dot3(Pk[0], d0, Pk[3], d1, Pk[6], d2);
+    const double x1 = dot3(Pk[1], d0, Pk[4], d1, Pk[7], d2);
+    const double x2 = dot3(Pk[2], d0, Pk[5], d1, Pk[8], d2);
+    if (!(x2 > 0.0)) return false;
+    const double px = __dadd_rn(__dmul_rn((double)V.fx, __ddiv_rn(x0, x2)), (double)V.cx);
+    const double py = __dadd_rn(__dmul_rn((double)V.fy, __ddiv_rn(x1, x2)), (double)V.cy);
+    double Dk;
+    if (!interp_depth(V, px, py, Dk)) return false;
+    return fabs(__dsub_rn(x2, Dk)) <= __dmul_rn(rel_tol, Dk);
+}
+
 // One thread per pixel of the current frame: back-project with its pose,
 // then for each view transform into the view, project, interpolate the
 // view's depth and test |z - D~| <= rel_tol D~ (union over views).
@@ -43,36 +77,31 @@ __global__ void __launch_bounds__(256) k_visibility(const float *depth, int W, i
                                                     double rel_tol, uint8_t *visible) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (int64_t)W * H) return;
-    const int v = (int)(p / W), u = (int)(p - (int64_t)v * W);
-    const float D = depth[p];
+    double X[3];
     uint8_t vis = 0;
-    if (valid_depth(D)) {
-        const double a = __ddiv_rn(__dsub_rn((double)u, (double)cx), (double)fx);
-        const double b = __ddiv_rn(__dsub_rn((double)v, (double)cy), (double)fy);
-        const double xc0 = __dmul_rn((double)D, a), xc1 = __dmul_rn((double)D, b),
-                     xc2 = (double)D;
-        double X[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            X[i] = __dadd_rn(dot3(pose[3 * i], xc0, pose[3 * i + 1], xc1, pose[3 * i + 2], xc2),
-                             pose[9 + i]);
-        for (int k = 0; k < views.n && !vis; ++k) {
-            const VisView &V = views.v[k];
-            const double *Pk = V.pose;
-            const double d0 = __dsub_rn(X[0], Pk[9]), d1 = __dsub_rn(X[1], Pk[10]),
-                         d2 = __dsub_rn(X[2], Pk[11]);
-            const double x0 = dot3(Pk[0], d0, Pk[3], d1, Pk[6], d2);
-            const double x1 = dot3(Pk[1], d0, Pk[4], d1, Pk[7], d2);
-            const double x2 = dot3(Pk[2], d0, Pk[5], d1, Pk[8], d2);
-            if (!(x2 > 0.0)) continue;
-            const double px = __dadd_rn(__dmul_rn((double)V.fx, __ddiv_rn(x0, x2)), (double)V.cx);
-            const double py = __dadd_rn(__dmul_rn((double)V.fy, __ddiv_rn(x1, x2)), (double)V.cy);
-            double Dk;
-            if (!interp_depth(V, px, py, Dk)) continue;
-            if (fabs(__dsub_rn(x2, Dk)) <= __dmul_rn(rel_tol, Dk)) vis = 1;
-        }
-    }
+    if (world_point(depth, W, p, fx, fy, cx, cy, pose, X))
+        for (int k = 0; k < views.n && !vis; ++k) vis = visible_to(views.v[k], X, rel_tol);
     visible[p] = vis;
+}
+
+// Overlap selection (Sec. 3.3): for every view separately, the number of
+// valid pixels of the current frame visible to it (counts[k]), and the
+// number of valid pixels (*n_valid).  Warp-aggregated integer atomics.
+__global__ void __launch_bounds__(256) k_visibility_counts(const float *depth, int W, int H,
+                                                           float fx, float fy, float cx,
+                                                           float cy, const double *pose,
+                                                           VisViews views, double rel_tol,
+                                                           uint32_t *counts, uint32_t *n_valid) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    double X[3];
+    const bool ok = p < (int64_t)W * H && world_point(depth, W, p, fx, fy, cx, cy, pose, X);
+    const unsigned vb = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0 && vb && n_valid) atomicAdd(n_valid, (uint32_t)__popc(vb));
+    for (int k = 0; k < views.n; ++k) {
+        const unsigned b = __ballot_sync(0xffffffffu, ok && visible_to(views.v[k], X, rel_tol));
+        if (lane == 0 && b) atomicAdd(&counts[k], (uint32_t)__popc(b));
+    }
 }
 
 __device__ __forceinline__ float sign_of(float e) { return e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f); }
