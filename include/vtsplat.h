@@ -96,13 +96,18 @@ typedef struct {
     double *d_view_twist;  /* n_views x 6 (VT_GRAD_VIEWS): dL/d(rho, phi) of each source
                               view's pose P_k for the right perturbation P_k Exp(xi) */
     double *d_view_mat;    /* n_views x 12 (VT_GRAD_VIEWS): dL/dR_k (row-major), dL/dt_k */
+    float *d_depth;        /* n, float32 (VT_GRAD_VIEWS): dL/dD of each Gaussian's depth,
+                              i.e. of its position along its pixel's ray (the movable
+                              Gaussians of the supplementary); apply by editing the
+                              section's depth map at src */
 } vt_grads;
 
 typedef enum {
     VT_GRAD_ATTR = 1,  /* colour, opacity, radius (mapping, Eq. 2) */
     VT_GRAD_POSE = 2,  /* target camera pose (tracking, Eq. 1) */
     VT_GRAD_VIEWS = 4  /* source-view poses through the centres mu = R_k X_c + t_k
-                          (head-frame bundle adjustment, Sec. 3.4) */
+                          (head-frame bundle adjustment, Sec. 3.4), and each
+                          Gaussian's depth along its ray */
 } vt_grad_mode;
 
 /* Opaque render context: the library-owned workspace (projected Gaussians,
@@ -207,7 +212,9 @@ vt_status vt_render(vt_ctx *ctx, const vt_section *secs, int32_t n_secs, const d
  *     views (sections with both NULL are skipped): per Gaussian dL/dx of its
  *     centre (float32 accumulation), then per view FP64 sums
  *     dL/dR_k = R sum g X_c^T, dL/dt_k = R sum g, dL/drho_k = R_k^T R sum g,
- *     dL/dphi_k = sum X_c x (R_k^T R g), X_c = D ((u-cx)/fx, (v-cy)/fy, 1).
+ *     dL/dphi_k = sum X_c x (R_k^T R g), X_c = D ((u-cx)/fx, (v-cy)/fy, 1);
+ *     grads[s].d_depth (device float32, +=, may be NULL) receives
+ *     dL/dD = (R g) . (R_k X_c / D) per Gaussian.
  *   VT_GRAD_POSE: d_twist (device, 6 doubles) += dL/d(rho, phi) for the
  *     right perturbation P exp(xi), xi = (rho, phi); d_mat (device, 12
  *     doubles) += dL/dR (row-major) and dL/dt.  The pose sums are reduced in

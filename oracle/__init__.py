@@ -71,7 +71,7 @@ class _Upstream(C.Structure):
 class _Grads(C.Structure):
     _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
                 ("a_colour", C.c_void_p), ("a_opacity", C.c_void_p), ("a_radius", C.c_void_p),
-                ("d_x", C.c_void_p), ("twist", C.c_double * 6), ("mat", C.c_double * 12),
+                ("d_x", C.c_void_p), ("a_x", C.c_void_p), ("twist", C.c_double * 6), ("mat", C.c_double * 12),
                 ("twist_noise", C.c_double * 6), ("mat_noise", C.c_double * 12)]
 
 
@@ -240,7 +240,8 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     twist_noise (6,) and mat_noise (12,): per component
     sqrt(sum over pixels of n_p m_p^2), n_p the pixel's added Gaussians and
     m_p the componentwise magnitude of the pixel's contribution; x: per
-    section (n, 3) dL/dx of every centre in the target camera frame)."""
+    section (n, 3) dL/dx of every centre in the target camera frame, abs_x
+    its componentwise term magnitudes)."""
     secs, arr, keep = _sections(secs)
     ups = [None if g is None else np.ascontiguousarray(g, np.float64) for g in (g_rgb, g_depth, g_sil)]
     up = _Upstream(*[_ptr(u) for u in ups])
@@ -251,8 +252,9 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     aop = [np.zeros(s.n) for s in secs]
     arad = [np.zeros(s.n) for s in secs]
     dx = [np.zeros((s.n, 3)) for s in secs]
+    ax = [np.zeros((s.n, 3)) for s in secs]
     arrs = [(C.c_void_p * len(secs))(*[_ptr(a) for a in lst])
-            for lst in (dcol, dop, drad, acol, aop, arad, dx)]
+            for lst in (dcol, dop, drad, acol, aop, arad, dx, ax)]
     g = _Grads(*[C.cast(a, C.c_void_p) for a in arrs])
     cam = _camera(pose, K, W, H)
     rc = lib().orc_backward(C.byref(arr), len(secs), C.byref(cam), int(bool(binned)), C.byref(up),
@@ -262,7 +264,7 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     return dict(colour=dcol, opacity=dop, radius=drad, twist=np.array(g.twist[:]),
                 mat=np.array(g.mat[:]), abs_colour=acol, abs_opacity=aop, abs_radius=arad,
                 twist_noise=np.array(g.twist_noise[:]), mat_noise=np.array(g.mat_noise[:]),
-                x=dx)
+                x=dx, abs_x=ax)
 
 
 def view_pose_grads(sec: Section, pose, d_x):
@@ -396,3 +398,27 @@ def section_complement(depth, rgb, sil, K, view, sil_max=0.5):
                                      float(np.float32(K[0])), float(np.float32(sil_max)),
                                      int(view), _ptr(src), _ptr(col), _ptr(op), _ptr(rad))
     return src[:n].copy(), col[:n].copy(), op[:n].copy(), rad[:n].copy()
+
+
+def depth_grads(sec: Section, pose, d_x, abs_x=None):
+    """dL/dD of every Gaussian's depth along its pixel's ray (the movable
+    Gaussians of the supplementary): mu = R_k D K^-1 [u v 1] + t_k, so
+    dL/dD = (R dL/dx) . (R_k X_c / D).  Returns (n,) float64, and with abs_x
+    (the componentwise magnitudes of d_x) also the magnitude bound
+    sum_ab |R_k^T R|_ab abs_x_b |X_c / D|_a."""
+    R = np.asarray(pose, np.float64).reshape(3, 4)[:, :3]
+    plane = sec.W * sec.H
+    src = sec.src.astype(np.int64)
+    view = src // plane
+    pix = src - view * plane
+    u = (pix % sec.W).astype(np.float64)
+    v = (pix // sec.W).astype(np.float64)
+    fx, fy, cx, cy = (float(np.float32(k)) for k in sec.K)
+    ray = np.stack([(u - cx) / fx, (v - cy) / fy, np.ones_like(u)], axis=1)   # X_c / D
+    dmu = np.asarray(d_x, np.float64) @ R.T
+    Rk = sec.poses[view][:, :, :3]                                            # (n, 3, 3)
+    val = np.einsum("na,nab,nb->n", dmu, Rk, ray)
+    if abs_x is None:
+        return val
+    M = np.abs(np.einsum("nca,cb->nab", Rk, R))                               # |R_k^T R|
+    return val, np.einsum("nab,nb,na->n", M, np.asarray(abs_x, np.float64), np.abs(ray))

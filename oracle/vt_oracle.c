@@ -492,6 +492,16 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
                     if (gr->d_x && gr->d_x[G->sec])
                         for (int a = 0; a < 3; ++a)
                             atomic_add(&gr->d_x[G->sec][3 * G->local + a], gv[a]);
+                    if (gr->a_x && gr->a_x[G->sec]) {
+                        /* |dq| <= ahat / 2 mal below the clamp, 0 above */
+                        const double mq = e->ahat < ORC_A_CLAMP ? 0.5 * e->ahat * mal : 0.0;
+                        const double ax[3] = {
+                            mq * 2.0 * fabs(e->ex) / (r * r), mq * 2.0 * fabs(e->ey) / (r * r),
+                            mq * 2.0 * (fabs(px * e->ex) + fabs(py * e->ey)) / (r * r) +
+                                fabs(gD * w)};
+                        for (int a = 0; a < 3; ++a)
+                            atomic_add(&gr->a_x[G->sec][3 * G->local + a], ax[a]);
+                    }
                     ltw[0] -= gx;
                     ltw[1] -= gy;
                     ltw[2] -= gz;

@@ -76,6 +76,8 @@ typedef struct {
     double **d_x;                /* optional, per section n x 3: dL/dx of each Gaussian's
                                     centre in the target camera frame (summed over pixels);
                                     the source-view pose gradients follow from it */
+    double **a_x;                /* optional, per section n x 3: componentwise magnitude of
+                                    the terms of d_x (as a_colour for colour) */
     double twist[6];             /* dL/d(rho, phi) for P(xi) = P * Exp(xi) */
     double mat[12];              /* dL/dR (row-major 3x3) then dL/dt */
     double twist_noise[6];       /* sqrt(sum over pixels of n_p m_p^2), n_p the pixel's added

@@ -34,7 +34,8 @@ class SectionC(C.Structure):
 
 class GradsC(C.Structure):
     _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
-                ("d_view_twist", C.c_void_p), ("d_view_mat", C.c_void_p)]
+                ("d_view_twist", C.c_void_p), ("d_view_mat", C.c_void_p),
+                ("d_depth", C.c_void_p)]
 
 
 class ViewC(C.Structure):

@@ -403,8 +403,9 @@ class Renderer:
         accumulated (both created as zeros when neither is given; a missing
         one is not computed when the other is).  view_grads: per section a
         tuple (d_view_twist (V,6), d_view_mat (V,12)) float64 device tensors
-        (either may be None) or None: gradients with respect to the section's
-        source-view poses (head-frame bundle adjustment), accumulated.
+        [, d_depth (n,) float32] (any may be None) or None: gradients with
+        respect to the section's source-view poses (head-frame bundle
+        adjustment) and to each Gaussian's depth along its ray, accumulated.
         Returns (d_twist, d_mat)."""
         mode = 0
         grads = None
@@ -415,8 +416,9 @@ class Renderer:
                 ag = attr_grads[s] if attr_grads is not None else None
                 vg = view_grads[s] if view_grads is not None else None
                 dc, do, dr = ag if ag is not None else (None, None, None)
-                vt, vm = vg if vg is not None else (None, None)
-                gl.append(L.GradsC(_ptr(dc), _ptr(do), _ptr(dr), _ptr(vt), _ptr(vm)))
+                vg = tuple(vg) + (None,) * (3 - len(vg)) if vg is not None else (None,) * 3
+                vt, vm, vd = vg
+                gl.append(L.GradsC(_ptr(dc), _ptr(do), _ptr(dr), _ptr(vt), _ptr(vm), _ptr(vd)))
             grads = (L.GradsC * len(gl))(*gl)
             if attr_grads is not None:
                 mode |= L.VT_GRAD_ATTR

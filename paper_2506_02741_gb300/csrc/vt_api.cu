@@ -642,6 +642,7 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
         if (mode & VT_GRAD_VIEWS) {
             T.s[s].d_view_twist = grads[s].d_view_twist;
             T.s[s].d_view_mat = grads[s].d_view_mat;
+            T.s[s].d_depth = grads[s].d_depth;
         }
     }
     const bool views = (mode & VT_GRAD_VIEWS) != 0;

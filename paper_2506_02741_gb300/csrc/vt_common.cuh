@@ -42,6 +42,7 @@ struct SecDesc {
     const void *colour, *opacity, *radius;
     float *d_colour, *d_opacity, *d_radius;  // backward only
     double *d_view_twist, *d_view_mat;        // backward only (source-view poses)
+    float *d_depth;                           // backward only (depth along the ray)
     int64_t gbase, n;       // global id range [gbase, gbase + n)
     int64_t tab_base;       // first table row of view 0
     int32_t view_base;      // first ViewXf of this section

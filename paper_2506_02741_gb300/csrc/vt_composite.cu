@@ -378,7 +378,7 @@ __device__ __forceinline__ void add_pair_grads(const SecTable &Tab, int64_t g, b
         atomicAdd(acc4 + g, make_float4(dc0, dc1, dc2, dop));
         atomicAdd(accr + g, drd);
     }
-    if (want_views && (S.d_view_twist || S.d_view_mat))
+    if (want_views && (S.d_view_twist || S.d_view_mat || S.d_depth))
         atomicAdd(accg + g, make_float4(gx, gy, gz, 0.f));
 }
 
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *
     }
     if (s >= Tab.n) return;
     const SecDesc &S = Tab.s[s];
-    if (!S.d_view_twist && !S.d_view_mat) return;
+    if (!S.d_view_twist && !S.d_view_mat && !S.d_depth) return;
     const int k = b;
     const uint32_t plane = (uint32_t)S.W * (uint32_t)S.H;
     if (threadIdx.x < 2) {   // first index with src >= (k + threadIdx.x) * plane
@@ -677,6 +677,7 @@ __global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *
     double acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+    const double *R = pose_copy, *Rk = S.poses + 12 * k;
     for (int64_t i = range[0] + threadIdx.x; i < range[1]; i += blockDim.x) {
         const float4 g = accg[S.gbase + i];
         if (g.x == 0.f && g.y == 0.f && g.z == 0.f) continue;
@@ -686,6 +687,15 @@ __global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *
         const double X[3] = {D * (((double)u - (double)S.cx) / (double)S.fx),
                              D * (((double)v - (double)S.cy) / (double)S.fy), D};
         const double gv[3] = {(double)g.x, (double)g.y, (double)g.z};
+        if (S.d_depth) {   // dL/dD = (R g) . (R_k X_c / D)
+            double dd = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double rg = R[3 * a] * gv[0] + R[3 * a + 1] * gv[1] + R[3 * a + 2] * gv[2];
+                const double rx = (Rk[3 * a] * X[0] + Rk[3 * a + 1] * X[1] + Rk[3 * a + 2] * X[2]) / D;
+                dd += rg * rx;
+            }
+            S.d_depth[i] += (float)dd;
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -708,7 +718,6 @@ __global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *
         if (i < 9) A[i] = t;
         else sv[i - 9] = t;
     }
-    const double *R = pose_copy, *Rk = S.poses + 12 * k;
     double Am[9], sm[3];
     for (int a = 0; a < 3; ++a) {
         for (int c = 0; c < 3; ++c)

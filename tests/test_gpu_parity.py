@@ -424,7 +424,8 @@ def test_budget_disables_lists(dev):
 def test_view_pose_gradients(dev, case):
     """Source-view pose gradients (head-frame bundle adjustment) against the
     oracle's, per view as twist and matrix: 1e-4 relative per view tensor
-    (sums over every pixel of the render, FP32 per pair).  Requesting them
+    (sums over every pixel of the render, FP32 per pair); each Gaussian's
+    depth gradient (movable along its ray) within the gradient tolerance.  Requesting them
     together with the attribute and target-pose gradients leaves those
     unchanged up to the order of float atomics."""
     osecs, target, K, W, H = _cases()[case]()
@@ -440,10 +441,13 @@ def test_view_pose_gradients(dev, case):
     vt = torch.zeros(V, 6, dtype=torch.float64, device=dev)
     vm = torch.zeros(V, 12, dtype=torch.float64, device=dev)
     n = osecs[0].n
+    vd = torch.zeros(n, device=dev)
     ag = [(torch.zeros(n, 3, device=dev), torch.zeros(n, device=dev), torch.zeros(n, device=dev))]
     dtw, dmat = R.backward(torch.from_numpy(gR).to(dev), torch.from_numpy(gD).to(dev), None,
-                           attr_grads=ag, pose_grad=True, view_grads=[(vt, vm)])
+                           attr_grads=ag, pose_grad=True, view_grads=[(vt, vm, vd)])
     torch.cuda.synchronize()
+    dref, dmag = oracle.depth_grads(osecs[0], target, want["x"][0], want["abs_x"][0])
+    G.assert_grad_close(vd.cpu().numpy(), dref, name="depth", abs_ref=dmag)
     for k in range(V):
         for got, ref_ in ((vt[k], tw_ref[k]), (vm[k], mat_ref[k])):
             g = got.cpu().numpy()

@@ -70,3 +70,39 @@ def test_rigid_motion_of_everything_has_no_view_gradient_sum():
     tw, mat = oracle.view_pose_grads(sec, target, g["x"][0])
     tot = mat[:, 9:].sum(0) + g["mat"][9:]
     assert np.abs(tot).max() <= 1e-9 * np.abs(g["mat"][9:]).max()
+
+
+def test_depth_gradient_finite_differences():
+    """Moving single Gaussians along their rays (their depth-map values)
+    changes the loss as dL/dD predicts."""
+    K = syn.scaled_intrinsics(48, 36)
+    sec, target = h.multiview_section(K, n_views=2, seed=12)
+    args = (K.astuple(), K.W, K.H)
+    cap = 192
+    base = oracle.render(sec, target, *args, list_cap=cap)
+    rng = np.random.default_rng(33)
+    gR = rng.normal(0, 1, (3, K.H, K.W))
+    gD = rng.normal(0, 1, (K.H, K.W))
+    g = oracle.backward(sec, target, *args, g_rgb=gR, g_depth=gD)
+    dd = oracle.depth_grads(sec, target, g["x"][0])
+    order = np.argsort(-np.abs(dd))
+    checked = 0
+    for i in order[:40]:
+        src = int(sec.src[i])
+        D = sec.depth.reshape(-1)[src]
+        renders = []
+        for s in (+1, -1):
+            t = copy.copy(sec)
+            t.depth = sec.depth.copy()
+            t.depth.reshape(-1)[src] = np.float32(D * (1 + s * 2e-6))
+            renders.append((oracle.render(t, target, *args, list_cap=cap),
+                            float(t.depth.reshape(-1)[src])))
+        (rp, dp), (rm, dm) = renders
+        if not _stable(base, [rp, rm]).all():
+            continue                     # a decision moved: the loss is not smooth here
+        fd = h.l_diff(rp, rm, gR, gD, np.zeros_like(gD)) / (dp - dm)
+        np.testing.assert_allclose(dd[i], fd, rtol=2e-3, atol=1e-6 * np.abs(dd).max())
+        checked += 1
+        if checked == 8:
+            break
+    assert checked >= 5
