@@ -201,6 +201,64 @@ def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
 
 
+def run_head_frame(dev, iters: int = 50):
+    """Head-frame workload (Sec. 3.3 / 3.4) on the 640x480 8-keyframe section
+    of the tracking workload: overlap counts of the head frame against the 8
+    keyframes (candidate views), its visibility mask against the first,
+    middle and last keyframe, tracking iterations whose Eq. 1 mask includes
+    that visibility (one CUDA graph per iteration), and the backward that
+    also returns the source-view pose gradients (bundle adjustment).
+    CUDA-event times per call; returns a summary dict."""
+    import torch
+
+    from paper_2506_02741_gb300 import api
+    from paper_2506_02741_gb300.tracking import PoseTracker
+    K, keys, section, targets, starts = make_workload(0, 1)
+    Kt = K.astuple()
+    sec = api.Section.from_rgbd(torch.from_numpy(section.depth).to(dev),
+                                torch.from_numpy(section.rgb).to(dev), Kt, np.stack(keys))
+    d = torch.from_numpy(targets.depth[0]).to(dev)
+    rgb = torch.from_numpy(targets.rgb[0]).to(dev)
+    p0 = api.pose12(starts[0], dev)
+    views = [(sec.depth[k], Kt, sec.poses[k]) for k in range(sec.n_views)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(n):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / n
+
+    counts_ms = timed(lambda: api.visibility_counts(d, Kt, p0, views), 20)
+    vis = api.visibility(d, Kt, p0, [views[0], views[len(views) // 2], views[-1]])
+    vis_ms = timed(lambda: api.visibility(d, Kt, p0, [views[0], views[len(views) // 2],
+                                                        views[-1]], out=vis), 50)
+    R = api.Renderer()
+    tr = PoseTracker(R, [sec], Kt, K.W, K.H, starts[0], device=dev)
+    tr.set_target(rgb, d, visible=vis)
+    R.render([sec], tr.pose, Kt, K.W, K.H, checked=True)
+    tr.capture()
+    track_ms = timed(tr.replay, iters)
+    vt = torch.zeros(sec.n_views, 6, dtype=torch.float64, device=dev)
+    vm = torch.zeros(sec.n_views, 12, dtype=torch.float64, device=dev)
+    R.render([sec], p0, Kt, K.W, K.H)
+    g_rgb = torch.full((3, K.H, K.W), 1e-6, device=dev)
+    ba_ms = timed(lambda: R.backward(g_rgb, None, None, pose_grad=True,
+                                     view_grads=[(vt, vm)]), 20)
+    pose_ms = timed(lambda: R.backward(g_rgb, None, None, pose_grad=True), 20)
+    return {"workload": "head_frame_640x480_8kf_fp32", "candidate_views": sec.n_views,
+            "overlap_counts_ms": counts_ms, "visibility_mask_ms": vis_ms,
+            "visible_fraction": float(vis.float().mean()),
+            "tracking_with_visibility_ms_per_iter": track_ms,
+            "tracking_with_visibility_mpix_s": K.W * K.H / track_ms / 1e3,
+            "backward_pose_and_views_ms": ba_ms, "backward_pose_only_ms": pose_ms}
+
+
 def run_serving(dev, n_req: int = 300):
     """Serving workload: 4 resident sections (0.3 M - 8.3 M Gaussians),
     Poisson render/track requests (70% track) over 320x240 ... 1920x1080.
@@ -516,6 +574,7 @@ def main():
     mapping = None
     if rank == 0 and not args.no_mapping:
         mapping = {prec: run_mapping(dev, prec, args.mapping_iters) for prec in ("f16", "f32")}
+    head_frame = run_head_frame(dev) if rank == 0 and not args.no_mapping else None
 
     serving_line = None
     if rank == 0 and not args.no_serving:
@@ -548,6 +607,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "mapping": mapping,
+            "head_frame": head_frame,
             "serving": serving_line,
             "clocks": clocks,
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items()},

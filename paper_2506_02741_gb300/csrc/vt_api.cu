@@ -111,6 +111,8 @@ struct vt_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *loss_part = nullptr;      // masked-L1 block partials (separate allocation)
     int64_t loss_cap = 0;             // blocks they hold
+    double *view_part = nullptr;      // per-view chunk partials of the view gradients
+    size_t view_part_bytes = 0;
     void *ssim_buf = nullptr;         // SSIM maps (15 floats per pixel) + block partials
     int64_t ssim_cap = 0;             // pixels it holds
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
@@ -339,6 +341,7 @@ void vt_ctx_destroy(vt_ctx *c) {
     if (c->plist) cudaFreeAsync(c->plist, c->stream);
     if (c->loss_part) cudaFreeAsync(c->loss_part, c->stream);
     if (c->ssim_buf) cudaFreeAsync(c->ssim_buf, c->stream);
+    if (c->view_part) cudaFreeAsync(c->view_part, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
@@ -676,8 +679,26 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
     if (views && T.n_total > 0) {
         int n_views = 0;
         for (int s = 0; s < T.n; ++s) n_views += T.s[s].n_views;
+        const size_t need = sizeof(double) * 12 * (size_t)n_views * kViewChunks;
+        if (need > c->view_part_bytes) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            VT_CUDA(cudaStreamIsCapturing(stream, &cs), "capture query");
+            if (cs != cudaStreamCaptureStatusNone)
+                return fail(VT_ERR_STATE, "vt_render_backward: view-gradient scratch must be "
+                                          "sized by a call before graph capture");
+            if (c->view_part) cudaFreeAsync(c->view_part, stream);
+            c->view_part = nullptr;
+            c->view_part_bytes = 0;
+            void *p = nullptr;
+            VT_CUDA(cudaMallocAsync(&p, need, stream), "view-gradient scratch");
+            c->view_part = static_cast<double *>(p);
+            c->view_part_bytes = need;
+        }
         LaunchScope ls(c, K_VIEW_GRADS, stream);
-        k_view_grads<<<n_views, kBlockPix, 0, stream>>>(T, c->accg, c->pose_copy);
+        k_view_grads<<<n_views * kViewChunks, kBlockPix, 0, stream>>>(T, c->accg, c->pose_copy,
+                                                                      c->view_part);
+        k_view_finalize<<<(n_views + 63) / 64, 64, 0, stream>>>(T, c->pose_copy, c->view_part,
+                                                              n_views);
     }
     if (mode & VT_GRAD_POSE) {
         LaunchScope ls(c, K_POSE, stream);

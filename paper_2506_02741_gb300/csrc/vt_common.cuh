@@ -239,7 +239,11 @@ __global__ void k_composite_bwd_list_views(SecTable T, Camera cam, const float4 
                                            const float *g_depth, const float *g_sil, int mode,
                                            double *pose_partials, float4 *acc4, float *accr,
                                            float4 *accg, const Status *st);
-__global__ void k_view_grads(SecTable T, const float4 *accg, const double *pose_copy);
+constexpr int kViewChunks = 64;   // blocks per source view in k_view_grads
+__global__ void k_view_grads(SecTable T, const float4 *accg, const double *pose_copy,
+                             double *partials);
+__global__ void k_view_finalize(SecTable T, const double *pose_copy, const double *partials,
+                                int n_views);
 __global__ void k_attr_scatter(SecTable T, const float4 *acc4, const float *accr);
 
 // Loss inputs (vt_loss.cu).

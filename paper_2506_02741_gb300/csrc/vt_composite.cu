@@ -641,27 +641,39 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_views(
                         g_depth, g_sil, mode, pose_partials, acc4, accr, accg, st, s_pose);
 }
 
-// Source-view pose gradients (head-frame bundle adjustment, Sec. 3.4): one
-// block per (section, view); the view's Gaussians are a contiguous range of
-// the section (ids are in (view, pixel) order).  FP64 fixed-order sums over
-// them of g X_c^T and g, with g = dL/dx of the centre in the target frame and
-// X_c = D ((u - cx)/fx, (v - cy)/fy, 1); then
+// Source-view pose gradients (head-frame bundle adjustment, Sec. 3.4).  The
+// Gaussians of one view are a contiguous range of their section (ids are in
+// (view, pixel) order).  k_view_grads: kViewChunks blocks per (section, view)
+// each sum g X_c^T and g over an equal share of the range (per thread in
+// FP32, across the block in FP64, fixed order), with g = dL/dx of the centre
+// in the target frame and X_c = D ((u - cx)/fx, (v - cy)/fy, 1), and write
+// per-Gaussian depth gradients dL/dD = (R g) . (R_k X_c / D) on the way;
+// k_view_finalize: one thread per view sums the chunk partials in order and
+// forms
 //   dL/dR_k = R A,  dL/dt_k = R s,  dL/drho_k = R_k^T R s,
 //   dL/dphi_k = sum X_c x (R_k^T R g)   (from B = R_k^T R A),
 // accumulated (+=) into the section's outputs.
-__global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *accg,
-                                                    const double *pose_copy) {
-    __shared__ double red[12][kBlockPix / 32];
-    __shared__ int64_t range[2];
-    int b = blockIdx.x, s = 0;
-    for (; s < Tab.n; ++s) {
-        if (b < Tab.s[s].n_views) break;
+__device__ __forceinline__ bool view_of_block(const SecTable &Tab, int b, int &s, int &k) {
+    for (s = 0; s < Tab.n; ++s) {
+        if (b < Tab.s[s].n_views) {
+            k = b;
+            return true;
+        }
         b -= Tab.s[s].n_views;
     }
-    if (s >= Tab.n) return;
+    return false;
+}
+
+__global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *accg,
+                                                    const double *pose_copy, double *partials) {
+    __shared__ double red[12][kBlockPix / 32];
+    __shared__ int64_t range[2];
+    const int vb = blockIdx.x / kViewChunks, chunk = blockIdx.x % kViewChunks;
+    int s, k;
+    if (!view_of_block(Tab, vb, s, k)) return;
     const SecDesc &S = Tab.s[s];
+    double *out = partials + (size_t)blockIdx.x * 12;
     if (!S.d_view_twist && !S.d_view_mat && !S.d_depth) return;
-    const int k = b;
     const uint32_t plane = (uint32_t)S.W * (uint32_t)S.H;
     if (threadIdx.x < 2) {   // first index with src >= (k + threadIdx.x) * plane
         const uint64_t key = (uint64_t)(k + threadIdx.x) * plane;
@@ -674,50 +686,70 @@ __global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *
         range[threadIdx.x] = lo;
     }
     __syncthreads();
-    double acc[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+    const int64_t len = range[1] - range[0];
+    const int64_t c0 = range[0] + len * chunk / kViewChunks;
+    const int64_t c1 = range[0] + len * (chunk + 1) / kViewChunks;
     const double *R = pose_copy, *Rk = S.poses + 12 * k;
-    for (int64_t i = range[0] + threadIdx.x; i < range[1]; i += blockDim.x) {
+    float Mf[9];   // R_k^T R (for the depth gradient), FP32
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c)
+            Mf[3 * a + c] = (float)(Rk[a] * R[c] + Rk[3 + a] * R[3 + c] + Rk[6 + a] * R[6 + c]);
+    const float ifx = 1.f / S.fx, ify = 1.f / S.fy;
+    float acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = 0.f;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
         const float4 g = accg[S.gbase + i];
         if (g.x == 0.f && g.y == 0.f && g.z == 0.f) continue;
         const uint32_t src = S.src[i], pix = src - (uint32_t)k * plane;
         const uint32_t v = pix / (uint32_t)S.W, u = pix - v * (uint32_t)S.W;
-        const double D = (double)S.depth[src];
-        const double X[3] = {D * (((double)u - (double)S.cx) / (double)S.fx),
-                             D * (((double)v - (double)S.cy) / (double)S.fy), D};
-        const double gv[3] = {(double)g.x, (double)g.y, (double)g.z};
-        if (S.d_depth) {   // dL/dD = (R g) . (R_k X_c / D)
-            double dd = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                const double rg = R[3 * a] * gv[0] + R[3 * a + 1] * gv[1] + R[3 * a + 2] * gv[2];
-                const double rx = (Rk[3 * a] * X[0] + Rk[3 * a + 1] * X[1] + Rk[3 * a + 2] * X[2]) / D;
-                dd += rg * rx;
-            }
-            S.d_depth[i] += (float)dd;
+        const float D = S.depth[src];
+        const float ray[3] = {((float)u - S.cx) * ifx, ((float)v - S.cy) * ify, 1.f};
+        const float X[3] = {D * ray[0], D * ray[1], D};
+        const float gv[3] = {g.x, g.y, g.z};
+        if (S.d_depth) {   // dL/dD = (R g) . (R_k ray) = ray . (R_k^T R g)
+            float dd = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                dd += ray[a] * (Mf[3 * a] * gv[0] + Mf[3 * a + 1] * gv[1] + Mf[3 * a + 2] * gv[2]);
+            S.d_depth[i] += dd;
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) acc[3 * a + c] += gv[a] * X[c];
+            for (int c = 0; c < 3; ++c) acc[3 * a + c] = fmaf(gv[a], X[c], acc[3 * a + c]);
             acc[9 + a] += gv[a];
         }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-        const double v = warp_sum_d(acc[i]);
+        const double v = warp_sum_d((double)acc[i]);
         if (lane == 0) red[i][warp] = v;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double A[9], sv[3];
-    for (int i = 0; i < 12; ++i) {
+    if (threadIdx.x < 12) {
         double t = 0.0;
-        for (int w = 0; w < kBlockPix / 32; ++w) t += red[i][w];
-        if (i < 9) A[i] = t;
-        else sv[i - 9] = t;
+        for (int w = 0; w < kBlockPix / 32; ++w) t += red[threadIdx.x][w];
+        out[threadIdx.x] = t;
     }
+}
+
+__global__ void k_view_finalize(SecTable Tab, const double *pose_copy, const double *partials,
+                                int n_views) {
+    const int vb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (vb >= n_views) return;
+    int s, k;
+    if (!view_of_block(Tab, vb, s, k)) return;
+    const SecDesc &S = Tab.s[s];
+    if (!S.d_view_twist && !S.d_view_mat) return;
+    double A[9] = {0}, sv[3] = {0};
+    for (int c = 0; c < kViewChunks; ++c) {
+        const double *p = partials + ((size_t)vb * kViewChunks + c) * 12;
+        for (int i = 0; i < 9; ++i) A[i] += p[i];
+        for (int i = 0; i < 3; ++i) sv[i] += p[9 + i];
+    }
+    const double *R = pose_copy, *Rk = S.poses + 12 * k;
     double Am[9], sm[3];
     for (int a = 0; a < 3; ++a) {
         for (int c = 0; c < 3; ++c)
