@@ -197,7 +197,8 @@ vt_status vt_section_complement(const float *depth, const float *rgb, const floa
  * multi-section render of Sec. 3.4) from the camera pose12 (device, 12
  * doubles) with intrinsics K into W x H images.  rgb (3 x H x W), depth and
  * silhouette (H x W) are device float32; any of them may be NULL.  The
- * context keeps what vt_render_backward needs. */
+ * context keeps what vt_render_backward needs.  W and H are at most 65535
+ * (VT_ERR_INVALID_ARG beyond). */
 vt_status vt_render(vt_ctx *ctx, const vt_section *secs, int32_t n_secs, const double *pose12,
                     vt_intrinsics K, int32_t W, int32_t H, float *rgb, float *depth,
                     float *silhouette, vt_stream stream);

@@ -53,6 +53,7 @@ constexpr size_t sort_smem_bytes(int n) { return 2 * (size_t)n * 8 + 16 * 256 * 
 constexpr int kSortSmemN = 6000;
 constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 16 * 256 * 4;
 constexpr int kSortSmemBig = 13312;
+static_assert(kSortSmemBig < (1 << 24), "shared-memory sorts carry 24-bit bucket positions");
 constexpr size_t kSortSmemBigBytes =
     2 * kSortSmemBig * sizeof(unsigned long long) + 16 * 256 * 4;
 
@@ -99,6 +100,8 @@ struct vt_ctx {
     uint32_t *tile_count = nullptr, *tile_off = nullptr, *tile_cursor = nullptr;
     unsigned long long *bucket = nullptr, *alt = nullptr;
     uint32_t *sorted = nullptr;
+    uint8_t *bmask = nullptr;         // per sorted entry: 8x4 blocks of the tile it reaches
+    uint8_t *bmask_u = nullptr;       // the same per bucket entry, before the sort
     uint32_t *pix_last = nullptr, *pix_nadd = nullptr;
     float *pix_T = nullptr;
     Status *status = nullptr;
@@ -192,6 +195,7 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += 3 * align_up(sizeof(uint32_t) * (t + 1));       // tile count/off/cursor
     b += 2 * align_up(sizeof(unsigned long long) * i);   // bucket, alt
     b += align_up(sizeof(uint32_t) * i);                 // sorted
+    b += 2 * align_up(i);                                // block masks (bucket, sorted)
     b += 3 * align_up(sizeof(uint32_t) * p);             // last, nadd, T
     b += align_up(sizeof(Status));
     b += align_up(sizeof(ViewXf) * v);
@@ -243,6 +247,8 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->bucket = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * i));
     c->alt = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * i));
     c->sorted = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * i));
+    c->bmask = reinterpret_cast<uint8_t *>(take(i));
+    c->bmask_u = reinterpret_cast<uint8_t *>(take(i));
     c->pix_last = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * p));
     c->pix_nadd = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * p));
     c->pix_T = reinterpret_cast<float *>(take(sizeof(float) * p));
@@ -296,8 +302,8 @@ vt_status check_intrinsics(const vt_intrinsics &K, const char *who) {
 }
 
 vt_status check_image(int32_t W, int32_t H, const char *who) {
-    if (W <= 0 || H <= 0 || (int64_t)W * H > (int64_t)1 << 31 || W > 16 * 65535 ||
-        H > 16 * 65535)
+    // pixel boxes pack u and v into 16 bits each
+    if (W <= 0 || H <= 0 || (int64_t)W * H > (int64_t)1 << 31 || W > 65535 || H > 65535)
         return fail(VT_ERR_INVALID_ARG, "%s: image size %d x %d out of range", who, W, H);
     return VT_OK;
 }
@@ -574,7 +580,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     if (total > 0) {
         LaunchScope ls(c, K_EMIT, stream);
         k_emit<<<gblocks, 256, 0, stream>>>(total, c->info, cam, c->tile_cursor, c->bucket,
-                                            c->status);
+                                            c->bmask_u, c->status);
     }
     // fork: the long lists sort on the auxiliary stream (works under graph
     // capture too: the fork and join events make it a parallel branch)
@@ -585,34 +591,34 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         // one block per SM at most: these lists are few, and the launch must
         // not hold every SM's shared memory while the others run
         k_sort_tiles<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortSmemBig,
-            kSortSmemN, 0x7fffffff);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
+            cam, c->status, kSortSmemBig, kSortSmemN, 0x7fffffff);
     }
     VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
     {
         LaunchScope ls(c, K_SORT, stream);
         k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassS), stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortClassS, 0,
-            kSortClassS);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
+            cam, c->status, kSortClassS, 0, kSortClassS);
     }
     {
         LaunchScope ls(c, K_SORT_M, stream);
         k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortClassM,
-            kSortClassS, kSortClassM);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
+            cam, c->status, kSortClassM, kSortClassS, kSortClassM);
     }
     {
         LaunchScope ls(c, K_SORT_L, stream);
         k_sort_tiles<<<n_tiles, 512, kSortSmemBytes, stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->sorted, c->status, kSortSmemN,
-            kSortClassM, kSortSmemN);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
+            cam, c->status, kSortSmemN, kSortClassM, kSortSmemN);
     }
     VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
     {
         LaunchScope ls(c, K_FWD, stream);
         k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(
-            cam, c->tile_off, c->sorted, c->geo, c->app, rgb, depth, silhouette, c->pix_last,
-            c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap, c->blk_ovf,
+            cam, c->tile_off, c->sorted, c->bmask, c->geo, c->app, rgb, depth, silhouette,
+            c->pix_last, c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap, c->blk_ovf,
             c->status);
     }
     VT_CUDA(cudaGetLastError(), "vt_render launch");

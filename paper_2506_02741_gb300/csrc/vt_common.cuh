@@ -186,6 +186,50 @@ __device__ __forceinline__ float t_min_of(float o) {
     return fmaxf(kQMax * kTScale, -log2_approx(__fmul_rn(255.f, o)));
 }
 
+// Conservative test: can a pixel of the block (columns 0..lxmax and rows
+// 0..lymax from the block origin) pass t >= t_min for a Gaussian at offsets
+// du0 ~ bx0 - uc, dv0 ~ by0 - vc from the origin?  The nearest pixel is taken
+// 1e-3 px nearer and the threshold loosened by 1e-4 relative so that rounding
+// never drops a pixel the per-pixel test includes.
+__device__ __forceinline__ bool block_touches(float du0, float dv0, float kxs, float kys,
+                                              float tmin, float lxmax, float lymax) {
+    const float dx = fmaxf(fmaxf(du0, -du0 - lxmax) - 1e-3f, 0.f);
+    const float dy = fmaxf(fmaxf(dv0, -dv0 - lymax) - 1e-3f, 0.f);
+    return dx * dx * kxs + dy * dy * kys >= tmin * 1.0001f - 1e-6f;
+}
+
+// Which of the eight 8x4 pixel blocks of tile (tx, ty) (block w at
+// ((w & 1) * 8, (w >> 1) * 4)) can a pixel of pass t >= t_min for the
+// Gaussian with records (g0, g1): bit w set (block_touches per block; blocks
+// outside the image get 0).  Written next to each sorted tile entry so that a
+// warp of the compositor only visits the entries of its own block.
+__device__ __forceinline__ uint32_t tile_block_mask(float4 g0, float4 g1, int tx, int ty,
+                                                    const Camera &cam) {
+    // the block_touches test with the column and row terms formed once: two
+    // block columns (x offsets 0, 8) and four block rows (y offsets 0, 4, 8, 12)
+    const float tl = t_min_of(g1.w) * 1.0001f - 1e-6f;
+    float ex[2], ey[4];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int bx0 = tx * kTile + 8 * c;
+        const float du0 = (float)(bx0 - __float_as_int(g0.x)) - g0.y;
+        const float dx = fmaxf(fmaxf(du0, -du0 - (float)min(7, cam.W - 1 - bx0)) - 1e-3f, 0.f);
+        ex[c] = bx0 < cam.W ? dx * dx * g1.x : -INFINITY;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int by0 = ty * kTile + 4 * r;
+        const float dv0 = (float)(by0 - __float_as_int(g0.z)) - g0.w;
+        const float dy = fmaxf(fmaxf(dv0, -dv0 - (float)min(3, cam.H - 1 - by0)) - 1e-3f, 0.f);
+        ey[r] = by0 < cam.H ? dy * dy * g1.y : -INFINITY;
+    }
+    uint32_t m = 0u;
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+        if (ex[w & 1] + ey[w >> 1] >= tl) m |= 1u << w;
+    return m;
+}
+
 // Attribute loads in either storage precision.
 __device__ __forceinline__ float ld_attr(const void *p, int prec, int64_t i) {
     if (prec == VT_F16) return __half2float(reinterpret_cast<const __half *>(p)[i]);
@@ -210,12 +254,15 @@ __global__ void k_preprocess(SecTable T, Camera cam, const ViewXf *views, const 
 __global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *tile_off,
                              uint32_t *tile_cursor, Status *st, unsigned long long cap);
 __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
-                       unsigned long long *bucket, const Status *st);
+                       unsigned long long *bucket, uint8_t *bmask_u, const Status *st);
 __global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,
-                             unsigned long long *alt, uint32_t *sorted, Status *st, int smem_n,
-                             int lo, int hi);
+                             unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted,
+                             uint8_t *bmask,
+                             const float4 *geo, Camera cam, Status *st, int smem_n, int lo,
+                             int hi);
 __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
-                                const float4 *geo, const float4 *app, float *rgb, float *depth,
+                                const uint8_t *bmask, const float4 *geo, const float4 *app,
+                                float *rgb, float *depth,
                                 float *sil, uint32_t *pix_last, uint32_t *pix_nadd,
                                 float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
                                 const Status *st);

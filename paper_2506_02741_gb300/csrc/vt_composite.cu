@@ -16,18 +16,6 @@ namespace vt {
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kWarps = kBlockPix / 32;
 
-// Conservative test: can a pixel of the block (columns 0..lxmax and rows
-// 0..lymax from the block origin) pass t >= t_min for a Gaussian at offsets
-// du0 ~ bx0 - uc, dv0 ~ by0 - vc from the origin?  The nearest pixel is taken
-// 1e-3 px nearer and the threshold loosened by 1e-4 relative so that rounding
-// never drops a pixel the per-pixel test includes.
-__device__ __forceinline__ bool block_touches(float du0, float dv0, float kxs, float kys,
-                                              float tmin, float lxmax, float lymax) {
-    const float dx = fmaxf(fmaxf(du0, -du0 - lxmax) - 1e-3f, 0.f);
-    const float dy = fmaxf(fmaxf(dv0, -dv0 - lymax) - 1e-3f, 0.f);
-    return dx * dx * kxs + dy * dy * kys >= tmin * 1.0001f - 1e-6f;
-}
-
 // Conservative set of the pixels of an 8x4 block (bit lx + 8 ly, columns
 // 0..lxmax, rows 0..lymax) that can pass t >= t_min for a Gaussian at offsets
 // du0 ~ bx0 - uc, dv0 ~ by0 - vc: row by row, kx' (du0 + lx)^2 >= t_min -
@@ -87,26 +75,31 @@ __device__ __forceinline__ bool tile_flagged(const uint32_t *blk_ovf, int tile) 
 // so a warp whose pixels saturate early retires instead of waiting for the
 // rest of its tile (the eight warps of a tile still share its records in L1:
 // handing pixel blocks to warps from a global work counter, which spreads a
-// tile's blocks over several SMs, measured slower).  Per pixel block the warp
-// streams through the tile's list in rounds of 32 entries: the
-// lanes load the next round's records into registers while the current round
-// is composited, test them against the block, stage the round in
+// tile's blocks over several SMs, measured slower).  A warp only visits the
+// list entries whose block mask (written by the sort) has its block's bit:
+// it classifies the masks 128 entries at a time into a warp-private ring of
+// list indices and takes them out in batches of 32, in list order.  For a
+// batch the lanes load the records (one batch ahead; the ids two batches
+// ahead), build each Gaussian's pixel set in the block, stage the batch in
 // warp-private shared memory ({bx0 - iu, by0 - iv, fu, fv}, {kx', ky', t_min,
-// o}, {c, z}, id) and walk the relevant ones in order.  Adding the lane's
-// column lx to bx0 - iu gives px - iu exactly, so du = (px - iu) - fu is
-// bit-identical to pair_t_at.  The warp leaves the block once all its pixels have
-// terminated.  With plist != NULL every pixel also records the id of every
-// Gaussian it added together with the transmittance in front of it (up to
-// plist_cap entries, pixel-major), which the backward replays instead of the
-// tile list; blk_ovf[item] flags blocks where a pixel added more (always 1
-// without lists).
+// o}, {c, z}, id, list index) and walk the relevant ones in order.  Adding
+// the lane's column lx to bx0 - iu gives px - iu exactly, so du = (px - iu) -
+// fu is bit-identical to pair_t_at.  The warp leaves the block once all its
+// pixels have terminated.  With plist != NULL every pixel also records the id
+// of every Gaussian it added together with the transmittance in front of it
+// (up to plist_cap entries, pixel-major), which the backward replays instead
+// of the tile list; blk_ovf[item] flags blocks where a pixel added more
+// (always 1 without lists).
+constexpr int kQueue = 256;   // ring of list indices per warp (>= 31 + 128)
+
 __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
-    Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
-    const float4 *app, float *rgb, float *depth, float *sil, uint32_t *pix_last,
-    uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
-    const Status *st) {
+    Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const uint8_t *bmask,
+    const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
+    uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
+    uint32_t *blk_ovf, const Status *st) {
     __shared__ float4 s_f[kWarps][32], s_k[kWarps][32], s_c[kWarps][32];
-    __shared__ uint32_t s_gid[kWarps][32];
+    __shared__ uint32_t s_gid[kWarps][32], s_idx[kWarps][32];
+    __shared__ uint32_t s_q[kWarps][kQueue];
     if (st->flags) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lx = lane & 7, ly = lane >> 3;
@@ -115,6 +108,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     float4 (&ks)[32] = s_k[warp];
     float4 (&cs)[32] = s_c[warp];
     uint32_t (&ids)[32] = s_gid[warp];
+    uint32_t (&lidx)[32] = s_idx[warp];
+    uint32_t (&q)[kQueue] = s_q[warp];
     const size_t HW = (size_t)cam.W * cam.H;
 
     const int item = blockIdx.x * kWarps + warp;
@@ -129,48 +124,88 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     const size_t p = inside ? (size_t)py * cam.W + px : 0;
     uint2 *mylist = (plist && inside) ? plist + p * (size_t)plist_cap : nullptr;
     const uint32_t cap = mylist ? (uint32_t)plist_cap : 0u;
+    const uint32_t my_bit = 1u << sub, lt_mask = (1u << lane) - 1u;
+
+    // Ring of this block's list indices: head qh, length qn; scan = next list
+    // index to classify, mw = the block masks of entries scan + lane + 32 j
+    // (byte j), loaded one window ahead.
+    uint32_t qh = 0, qn = 0, mw = 0;
+    int scan = 0;
+    auto load_window = [&]() {
+        mw = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = scan + 32 * j + lane;
+            if (e < n) mw |= (uint32_t)bmask[start + e] << (8 * j);
+        }
+    };
+    auto take = [&](uint32_t &idx, int &cnt) {
+        while (qn < 32u && scan < n) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool mine = (mw >> (8 * j)) & my_bit;
+                const unsigned rel = __ballot_sync(kFullMask, mine);
+                if (mine) q[(qh + qn + __popc(rel & lt_mask)) & (kQueue - 1)] = scan + 32 * j + lane;
+                qn += __popc(rel);
+            }
+            scan += 128;
+            load_window();
+        }
+        __syncwarp();
+        cnt = (int)min(qn, 32u);
+        idx = lane < cnt ? q[(qh + lane) & (kQueue - 1)] : 0u;
+        qh += cnt;
+        qn -= cnt;
+    };
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
     uint32_t last = 0, nadd = 0;
     bool done = !inside;
-    // Two-stage prefetch: the ids of round r + 2 and the records of round
-    // r + 1 are in flight while round r is composited, so a gather never
-    // waits on the id load in front of it.
-    uint32_t gid_n = 0, gid_nn = 0;
+    // Two-stage prefetch: the ids of batch r + 2 and the records of batch
+    // r + 1 are in flight while batch r is composited.
+    uint32_t idx_n = 0, idx_nn = 0, gid_n = 0, gid_nn = 0;
+    int cnt_n = 0, cnt_nn = 0;
     float4 g0n = make_float4(0.f, 0.f, 0.f, 0.f), g1n = g0n, an = g0n;
     if (!__all_sync(kFullMask, done)) {
-        if (lane < n) {
-            gid_n = sorted[start + lane];
+        load_window();
+        take(idx_n, cnt_n);
+        if (lane < cnt_n) {
+            gid_n = sorted[start + idx_n];
             g0n = geo[2 * (size_t)gid_n];
             g1n = geo[2 * (size_t)gid_n + 1];
             an = app[gid_n];
         }
-        if (32 + lane < n) gid_nn = sorted[start + 32 + lane];
+        take(idx_nn, cnt_nn);
+        if (lane < cnt_nn) gid_nn = sorted[start + idx_nn];
     }
-    for (int base = 0; base < n; base += 32) {
-        if (__all_sync(kFullMask, done)) break;
-        const uint32_t gid = gid_n;
+    for (;;) {
+        const int cnt = cnt_n;
+        if (cnt == 0 || __all_sync(kFullMask, done)) break;
+        const uint32_t gid = gid_n, idx = idx_n;
         const float4 g0 = g0n, g1 = g1n, a = an;
-        const bool valid = base + lane < n;
-        if (base + 32 + lane < n) {   // records of the next round
-            gid_n = gid_nn;
+        idx_n = idx_nn;
+        cnt_n = cnt_nn;
+        gid_n = gid_nn;
+        if (lane < cnt_n) {   // records of the next batch
             g0n = geo[2 * (size_t)gid_n];
             g1n = geo[2 * (size_t)gid_n + 1];
             an = app[gid_n];
         }
-        if (base + 64 + lane < n) gid_nn = sorted[start + base + 64 + lane];
+        take(idx_nn, cnt_nn);
+        if (lane < cnt_nn) gid_nn = sorted[start + idx_nn];
         const float ku = (float)(bx0 - __float_as_int(g0.x));
         const float kv = (float)(by0 - __float_as_int(g0.z));
         const float tmin = t_min_of(g1.w);
         const uint32_t pm =
-            valid ? pixel_mask(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmaxi, lymaxi) : 0u;
+            lane < cnt ? pixel_mask(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmaxi, lymaxi) : 0u;
         if (!__any_sync(kFullMask, pm != 0u)) continue;
         __syncwarp();
         fs[lane] = make_float4(ku, kv, g0.y, g0.w);
         ks[lane] = make_float4(g1.x, g1.y, tmin, g1.w);
         cs[lane] = a;
         ids[lane] = gid;
-        // this pixel's candidates of the round, in list order (bit j = entry j)
+        lidx[lane] = idx;
+        // this pixel's candidates of the batch, in list order (bit j = entry j)
         uint32_t cand = transpose32(pm, lane);
         __syncwarp();
         if (done) cand = 0u;
@@ -201,7 +236,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
             ss = __fadd_rn(ss, w);
             if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
             T = Tn;
-            last = (uint32_t)(base + j) + 1u;
+            last = lidx[j] + 1u;
             ++nadd;
         }
     }

@@ -88,17 +88,18 @@ __global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const dou
 }
 
 // ---------------------------------------------------------------------------
-// Warp-aggregated visit of the tiles of each lane's tile rectangle: lanes
-// that hit the same tile in the same step share one atomic.  fn(tile, peers,
-// rank) is called by every active lane; the lowest lane of each peer group
-// is the leader.
+// Warp-aggregated visit of the tiles that each lane's pixel box (b0 = u0 |
+// v0 << 16, b1 = u1 | v1 << 16, inclusive) overlaps: lanes that hit the same
+// tile in the same step share one atomic.  fn(tile, peers, rank, tx, ty) is
+// called by every active lane; the lowest lane of each peer group is the
+// leader.
 template <class Fn>
-__device__ __forceinline__ void for_each_tile(uint32_t r0, uint32_t r1, uint32_t nt, int tiles_x,
+__device__ __forceinline__ void for_each_tile(uint32_t b0, uint32_t b1, uint32_t nt, int tiles_x,
                                               Fn &&fn) {
     const int lane = threadIdx.x & 31;
     const unsigned maxnt = __reduce_max_sync(kFull, nt);
-    const uint32_t tx0 = r0 & 0xffffu, ty0 = r0 >> 16, tx1 = r1 & 0xffffu;
-    const uint32_t w = tx1 - tx0 + 1;
+    const uint32_t tx0 = (b0 & 0xffffu) / kTile, ty0 = (b0 >> 16) / kTile;
+    const uint32_t w = (b1 & 0xffffu) / kTile - tx0 + 1;
     for (unsigned j = 0; j < maxnt; ++j) {
         const bool act = j < nt;
         const unsigned am = __ballot_sync(kFull, act);
@@ -107,9 +108,24 @@ __device__ __forceinline__ void for_each_tile(uint32_t r0, uint32_t r1, uint32_t
             const uint32_t t = (ty0 + jy) * (uint32_t)tiles_x + tx0 + jx;
             const unsigned peers = __match_any_sync(am, t);
             const int rank = __popc(peers & ((1u << lane) - 1u));
-            fn(t, peers, rank);
+            fn(t, peers, rank, tx0 + jx, ty0 + jy);
         }
     }
+}
+
+// The 8x4 blocks of tile (tx, ty) (block w at ((w & 1) * 8, (w >> 1) * 4))
+// that the pixel box overlaps, bit w.  The box holds every pixel that can
+// pass t >= t_min (k_preprocess), so the mask is conservative.
+__device__ __forceinline__ uint32_t box_block_mask(uint32_t b0, uint32_t b1, uint32_t tx,
+                                                   uint32_t ty) {
+    const int u0 = (int)(b0 & 0xffffu) - (int)(tx * kTile), u1 = (int)(b1 & 0xffffu) - (int)(tx * kTile);
+    const int v0 = (int)(b0 >> 16) - (int)(ty * kTile), v1 = (int)(b1 >> 16) - (int)(ty * kTile);
+    const uint32_t cols = (u0 <= 7 && u1 >= 0 ? 1u : 0u) | (u0 <= 15 && u1 >= 8 ? 2u : 0u);
+    uint32_t m = 0u;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (v0 <= 4 * r + 3 && v1 >= 4 * r) m |= cols << (2 * r);
+    return m;
 }
 
 // ---------------------------------------------------------------------------
@@ -120,7 +136,8 @@ __device__ __forceinline__ void for_each_tile(uint32_t r0, uint32_t r1, uint32_t
 // ky = (z / (fy r))^2 (q = du^2 kx + dv^2 ky in pixels) and the conservative
 // pixel box of the disc q <= min(9, 2 ln(255 o)), and counts its tiles.
 // The records keep kx, ky scaled to the base-2 exponent t = -q log2(e)/2
-// (see pair_t) and 1/r for the backward.
+// (see pair_t) and 1/r for the backward; info keeps the pixel box, the depth
+// key and the tile count.
 __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, const ViewXf *views,
                                                     const TabRow *tab, float4 *geo, float4 *app,
                                                     uint4 *info, uint32_t *tile_count) {
@@ -185,8 +202,8 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
                 if (ok) {
                     const uint32_t tx0 = (uint32_t)u0 / kTile, tx1 = (uint32_t)u1 / kTile;
                     const uint32_t ty0 = (uint32_t)v0 / kTile, ty1 = (uint32_t)v1 / kTile;
-                    r0 = tx0 | (ty0 << 16);
-                    r1 = tx1 | (ty1 << 16);
+                    r0 = (uint32_t)u0 | ((uint32_t)v0 << 16);
+                    r1 = (uint32_t)u1 | ((uint32_t)v1 << 16);
                     nt = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
                     zbits = __float_as_uint(zkey);
                     const int iu = __float2int_rn(uc.hi), iv = __float2int_rn(vc.hi);
@@ -204,9 +221,10 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
         }
         info[gid] = make_uint4(r0, r1, zbits, nt);
     }
-    for_each_tile(r0, r1, nt, cam.tiles_x, [&](uint32_t t, unsigned peers, int rank) {
-        if (rank == 0) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
-    });
+    for_each_tile(r0, r1, nt, cam.tiles_x,
+                  [&](uint32_t t, unsigned peers, int rank, uint32_t, uint32_t) {
+                      if (rank == 0) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
+                  });
 }
 
 // ---------------------------------------------------------------------------
@@ -259,23 +277,26 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count,
 
 // ---------------------------------------------------------------------------
 // k_emit: one thread per Gaussian; appends (zkey << 32 | gid) to the bucket of
-// every tile of its rectangle (the same tiles counted in k_preprocess).
+// every tile of its pixel box (the same tiles counted in k_preprocess), and
+// the entry's block mask (box_block_mask) at the same position of bmask_u.
 __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Camera cam,
-                                              uint32_t *tile_cursor,
-                                              unsigned long long *bucket, const Status *st) {
+                                              uint32_t *tile_cursor, unsigned long long *bucket,
+                                              uint8_t *bmask_u, const Status *st) {
     if (st->flags) return;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint4 in = make_uint4(0, 0, 0, 0);
     if (gid < n) in = info[gid];
     const unsigned long long key = ((unsigned long long)in.z << 32) | (unsigned long long)gid;
     const int lane = threadIdx.x & 31;
-    for_each_tile(in.x, in.y, in.w, cam.tiles_x, [&](uint32_t t, unsigned peers, int rank) {
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&tile_cursor[t], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        bucket[base + rank] = key;
-    });
+    for_each_tile(in.x, in.y, in.w, cam.tiles_x,
+                  [&](uint32_t t, unsigned peers, int rank, uint32_t tx, uint32_t ty) {
+                      const int leader = __ffs(peers) - 1;
+                      uint32_t base = 0;
+                      if (lane == leader) base = atomicAdd(&tile_cursor[t], (uint32_t)__popc(peers));
+                      base = __shfl_sync(peers, base, leader);
+                      bucket[base + rank] = key;
+                      bmask_u[base + rank] = (uint8_t)box_block_mask(in.x, in.y, tx, ty);
+                  });
 }
 
 // ---------------------------------------------------------------------------
@@ -287,7 +308,8 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Came
 // which orders ties by Gaussian id.  A launch handles the tiles whose list
 // length lies in (lo, hi]; lists of up to smem_n entries are sorted in shared
 // memory, longer ones in place in the tile's own range of the bucket and its
-// twin buffer.
+// twin buffer.  Next to each sorted id goes the entry's 8-bit block mask
+// (tile_block_mask): which 8x4 pixel blocks of the tile it can reach.
 
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -381,21 +403,49 @@ __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigne
 
 __device__ __forceinline__ unsigned bits_of(uint32_t span) { return span ? 32 - __clz(span) : 0; }
 
+// Writes the sorted ids of a tile and their block masks, the masks computed
+// from the records (used where the sort could not carry them): id_of(i)
+// gives entry i.
+struct SortOut {
+    uint32_t *__restrict__ sorted;
+    uint8_t *__restrict__ bmask;
+    const float4 *__restrict__ geo;
+    Camera cam;
+    uint32_t start;
+    int tx, ty;
+    template <class F>
+    __device__ __forceinline__ void put_all(int n, int tid, F id_of) const {
+        for (int i = tid; i < n; i += kSortThreads) {
+            const uint32_t g = id_of(i);
+            sorted[start + i] = g;
+            bmask[start + i] = (uint8_t)tile_block_mask(__ldg(geo + 2 * (size_t)g),
+                                                        __ldg(geo + 2 * (size_t)g + 1), tx, ty,
+                                                        cam);
+        }
+    }
+};
+
 // Sorts one tile's list [start, start + n) (2 <= n) with the whole block.
+// Lists sorted in shared memory carry (block mask << 24 | position in the
+// bucket) in the low word, so the masks written by k_emit travel with the
+// entries and the ids are read back from the bucket (which stays intact);
+// lists sorted in place carry the id and their masks are recomputed.
 __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned long long *alt,
-                                          uint32_t *sorted, Status *st, uint32_t start, int n,
-                                          int smem_n, unsigned long long *sm,
-                                          uint32_t (*red)[kSortWarps], int tid, int lane,
-                                          int warp) {
+                                          const uint8_t *bmask_u, const SortOut &out,
+                                          Status *st, uint32_t start, int n, int smem_n,
+                                          unsigned long long *sm, uint32_t (*red)[kSortWarps],
+                                          int tid, int lane, int warp) {
     const bool big = n > smem_n;
     uint32_t *hist = reinterpret_cast<uint32_t *>(sm + 2 * smem_n);
     unsigned long long *A = big ? bucket + start : sm;
     unsigned long long *B = big ? alt + start : sm + smem_n;
     if (big && tid == 0) atomicAdd(&st->n_overflow_tiles, 1ull);
+    const unsigned long long *orig = bucket + start;
+    // id of an entry from its low word
+    auto id_of = [&](uint32_t lw) { return big ? lw : (uint32_t)orig[lw & 0xffffffu]; };
     uint32_t zmin = 0xffffffffu, zmax = 0, gmin = 0xffffffffu, gmax = 0;
     for (int i = tid; i < n; i += kSortThreads) {
         const unsigned long long k = bucket[start + i];
-        if (!big) A[i] = k;
         const uint32_t z = (uint32_t)(k >> 32), g = (uint32_t)k;
         zmin = min(zmin, z);
         zmax = max(zmax, z);
@@ -426,8 +476,9 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
     const unsigned bz = bits_of(zmax - zmin), bg = bits_of(gmax - gmin);
     // pass A: depth key relative to the tile minimum in the high word
     for (int i = tid; i < n; i += kSortThreads) {
-        const unsigned long long k = A[i];
-        A[i] = ((unsigned long long)((uint32_t)(k >> 32) - zmin) << 32) | (k & 0xffffffffull);
+        const unsigned long long k = orig[i];
+        const uint32_t lw = big ? (uint32_t)k : ((uint32_t)bmask_u[start + i] << 24) | (uint32_t)i;
+        A[i] = ((unsigned long long)((uint32_t)(k >> 32) - zmin) << 32) | lw;
     }
     __syncthreads();
     unsigned long long *cur = A, *oth = B;
@@ -457,8 +508,9 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
         }
         for (int a = i + 1; a < e; ++a) {   // insertion sort by id
             const unsigned long long k = cur[a];
+            const uint32_t gk = id_of((uint32_t)k);
             int b = a - 1;
-            while (b >= i && (uint32_t)cur[b] > (uint32_t)k) {
+            while (b >= i && id_of((uint32_t)cur[b]) > gk) {
                 cur[b + 1] = cur[b];
                 --b;
             }
@@ -467,13 +519,21 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
     }
     long_run = __syncthreads_or(long_run);
     if (!long_run) {
-        for (int i = tid; i < n; i += kSortThreads) sorted[start + i] = (uint32_t)cur[i];
+        if (big) {
+            out.put_all(n, tid, [&](int i) { return (uint32_t)cur[i]; });
+        } else {
+            for (int i = tid; i < n; i += kSortThreads) {
+                const uint32_t lw = (uint32_t)cur[i];
+                out.sorted[start + i] = id_of(lw);
+                out.bmask[start + i] = (uint8_t)(lw >> 24);
+            }
+        }
         return;
     }
     // pass B: (zrel, gid - gmin) packed into bz + bg <= 64 bits
     for (int i = tid; i < n; i += kSortThreads) {
         const unsigned long long k = cur[i];
-        const unsigned long long zr = k >> 32, gr = (uint32_t)k - gmin;
+        const unsigned long long zr = k >> 32, gr = id_of((uint32_t)k) - gmin;
         cur[i] = (bg == 64 ? 0ull : (zr << bg)) | gr;
     }
     __syncthreads();
@@ -485,15 +545,18 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
         oth = tmp;
     }
     const unsigned long long gm = bg >= 64 ? ~0ull : ((1ull << bg) - 1ull);
-    for (int i = tid; i < n; i += kSortThreads) sorted[start + i] = gmin + (uint32_t)(cur[i] & gm);
+    out.put_all(n, tid, [&](int i) { return gmin + (uint32_t)(cur[i] & gm); });
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *tile_off,
                                                              int n_tiles,
                                                              unsigned long long *bucket,
                                                              unsigned long long *alt,
-                                                             uint32_t *sorted, Status *st,
-                                                             int smem_n, int lo, int hi) {
+                                                             const uint8_t *bmask_u,
+                                                             uint32_t *sorted, uint8_t *bmask,
+                                                             const float4 *geo, Camera cam,
+                                                             Status *st, int smem_n, int lo,
+                                                             int hi) {
     extern __shared__ unsigned long long sm[];
     __shared__ uint32_t red[4][kSortWarps];
     if (st->flags) return;
@@ -503,11 +566,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *til
         const uint32_t start = tile_off[t];
         const int n = (int)(tile_off[t + 1] - start);
         if (n <= lo || n > hi) continue;   // another launch sorts this size class
+        const SortOut out{sorted, bmask, geo, cam, start, t % cam.tiles_x, t / cam.tiles_x};
         if (n == 1) {
-            if (tid == 0) sorted[start] = (uint32_t)bucket[start];
+            if (tid == 0) {
+                sorted[start] = (uint32_t)bucket[start];
+                bmask[start] = bmask_u[start];
+            }
             continue;
         }
-        sort_tile(bucket, alt, sorted, st, start, n, smem_n, sm, red, tid, lane, warp);
+        sort_tile(bucket, alt, bmask_u, out, st, start, n, smem_n, sm, red, tid, lane, warp);
         __syncthreads();   // shared memory is reused by the next tile
     }
 }
