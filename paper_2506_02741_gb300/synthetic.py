@@ -283,3 +283,16 @@ def random_attributes(n: int, seed: int, opacity_range=(0.05, 0.98), colour_jitt
     opacity = rng.uniform(opacity_range[0], opacity_range[1], n)
     rscale = rng.uniform(0.6, 1.8, n)
     return colour, opacity, rscale
+
+
+def random_ellipsoids(radius, seed: int, spread: float = 0.35):
+    """Seeded ellipsoid attributes for the anisotropic variant: per Gaussian
+    three axis scales radius * exp(N(0, spread)) and a rotation quaternion
+    (w, x, y, z) drawn uniformly (a normalised 4-D normal sample, w >= 0)."""
+    rng = np.random.default_rng(seed)
+    r = np.asarray(radius, np.float64).reshape(-1)
+    scale = r[:, None] * np.exp(rng.normal(0.0, spread, (r.size, 3)))
+    q = rng.normal(0.0, 1.0, (r.size, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q[q[:, 0] < 0] *= -1.0
+    return scale, q
