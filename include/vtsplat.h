@@ -83,7 +83,20 @@ typedef struct {
     vt_precision prec;
     const void *colour;     /* n x 3 */
     const void *opacity;    /* n, activated value in (0, 1] */
-    const void *radius;     /* n, activated value > 0 (metres, a standard deviation) */
+        const void *radius;     /* n, activated value > 0 (metres, a standard deviation);
+                               unused (may be NULL) for ellipsoids */
+    /* Ellipsoids (the anisotropic variant of the ablation on the Gaussians'
+     * attributes, Sec. 4): with scale != NULL every Gaussian of the section
+     * is the ellipsoid R(q) diag(s^2) R(q)^T, expressed in the camera frame
+     * of its source view (it moves with that view), and is splatted with
+     * the local affine (EWA) projection at its centre:
+     *   Sigma_2D = J M R(q) diag(s^2) R(q)^T M^T J^T + 0.3 I (pixels^2),
+     *   M = R^T R_k, J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]],
+     *   q = d^T Sigma_2D^-1 d for the pixel offset d from the projected
+     *   centre; inclusion, clamp, order and termination as for the spheres. */
+    const void *scale;      /* n x 3 standard deviations (metres, > 0) or NULL */
+    const void *rot;        /* n x 4 quaternions (w, x, y, z), normalised on use;
+                               required with scale */
 } vt_section;
 
 /* Per-section gradient buffers (device, accumulated with +=).  A NULL
@@ -99,7 +112,10 @@ typedef struct {
     float *d_depth;        /* n, float32 (VT_GRAD_VIEWS): dL/dD of each Gaussian's depth,
                               i.e. of its position along its pixel's ray (the movable
                               Gaussians of the supplementary); apply by editing the
-                              section's depth map at src */
+                                                            section's depth map at src */
+    float *d_scale;        /* n x 3, float32 (ellipsoid sections, VT_GRAD_ATTR) */
+    float *d_rot;          /* n x 4, float32 (ellipsoid sections, VT_GRAD_ATTR): with
+                              respect to the stored (unnormalised) quaternion */
 } vt_grads;
 
 typedef enum {
@@ -197,8 +213,9 @@ vt_status vt_section_complement(const float *depth, const float *rgb, const floa
  * multi-section render of Sec. 3.4) from the camera pose12 (device, 12
  * doubles) with intrinsics K into W x H images.  rgb (3 x H x W), depth and
  * silhouette (H x W) are device float32; any of them may be NULL.  The
- * context keeps what vt_render_backward needs.  W and H are at most 65535
- * (VT_ERR_INVALID_ARG beyond). */
+  * context keeps what vt_render_backward needs.  W and H are at most 65535
+ * (VT_ERR_INVALID_ARG beyond).  The sections of one render are either all
+ * spheres or all ellipsoids (VT_ERR_INVALID_ARG otherwise). */
 vt_status vt_render(vt_ctx *ctx, const vt_section *secs, int32_t n_secs, const double *pose12,
                     vt_intrinsics K, int32_t W, int32_t H, float *rgb, float *depth,
                     float *silhouette, vt_stream stream);
@@ -206,8 +223,9 @@ vt_status vt_render(vt_ctx *ctx, const vt_section *secs, int32_t n_secs, const d
 /* Backward of the last vt_render on ctx for L with upstream gradients
  * dL_drgb (3 x H x W), dL_ddepth, dL_dsil (H x W; each device, NULL = 0).
  * mode is a combination of vt_grad_mode bits.
- *   VT_GRAD_ATTR: grads[s] (host array of n_secs entries) receive
- *     dL/dcolour, dL/dopacity, dL/dradius of section s (+=, float32).
+  *   VT_GRAD_ATTR: grads[s] (host array of n_secs entries) receive
+ *     dL/dcolour, dL/dopacity, dL/dradius of section s (+=, float32); for
+ *     ellipsoids d_scale and d_rot instead of d_radius.
  *   VT_GRAD_VIEWS: grads[s].d_view_twist / d_view_mat (device doubles, +=)
  *     receive the gradients with respect to the poses of section s's source
  *     views (sections with both NULL are skipped): per Gaussian dL/dx of its
@@ -219,7 +237,12 @@ vt_status vt_render(vt_ctx *ctx, const vt_section *secs, int32_t n_secs, const d
  *   VT_GRAD_POSE: d_twist (device, 6 doubles) += dL/d(rho, phi) for the
  *     right perturbation P exp(xi), xi = (rho, phi); d_mat (device, 12
  *     doubles) += dL/dR (row-major) and dL/dt.  The pose sums are reduced in
- *     FP64 in a fixed order (bit-reproducible).
+  *     FP64 in a fixed order (bit-reproducible).  For ellipsoids the pose
+ *     gradient also runs through the covariance: dL/dR adds
+ *     R Sigma_c (G + G^T) per Gaussian, G = dL/dSigma_c.
+ * For ellipsoids the per-pair terms are accumulated per Gaussian (float32
+ * atomics) and a per-Gaussian pass chains them to the scale, the quaternion
+ * and the pose; VT_GRAD_VIEWS is not available for them (VT_ERR_INVALID_ARG).
  * The included sets and their order are those of the render (piecewise
  * constant).  Returns VT_ERR_STATE when ctx holds no render. */
 vt_status vt_render_backward(vt_ctx *ctx, const float *dL_drgb, const float *dL_ddepth,

@@ -29,13 +29,14 @@ class SectionC(C.Structure):
     _fields_ = [("n_views", C.c_int32), ("W", C.c_int32), ("H", C.c_int32), ("K", Intrinsics),
                 ("poses", C.c_void_p), ("depth", C.c_void_p), ("n", C.c_int64),
                 ("src", C.c_void_p), ("prec", C.c_int), ("colour", C.c_void_p),
-                ("opacity", C.c_void_p), ("radius", C.c_void_p)]
+                ("opacity", C.c_void_p), ("radius", C.c_void_p), ("scale", C.c_void_p),
+                ("rot", C.c_void_p)]
 
 
 class GradsC(C.Structure):
     _fields_ = [("d_colour", C.c_void_p), ("d_opacity", C.c_void_p), ("d_radius", C.c_void_p),
                 ("d_view_twist", C.c_void_p), ("d_view_mat", C.c_void_p),
-                ("d_depth", C.c_void_p)]
+                ("d_depth", C.c_void_p), ("d_scale", C.c_void_p), ("d_rot", C.c_void_p)]
 
 
 class ViewC(C.Structure):

@@ -68,7 +68,11 @@ class Section:
 
     poses (V, 12) float64, depth (V, H, W) float32, src (n,) int32 holding
     the uint32 source index (view*H + v)*W + u in increasing order,
-    colour (n, 3), opacity (n,), radius (n,) in float32 or float16."""
+    colour (n, 3), opacity (n,), radius (n,) in float32 or float16.  With
+    scale (n, 3) and rot (n, 4) (same dtype) the Gaussians are ellipsoids
+    (the anisotropic variant of the attribute ablation, Sec. 4): axis
+    standard deviations and quaternions (w, x, y, z) in the source view's
+    camera frame; the radius is then not used."""
     poses: torch.Tensor
     depth: torch.Tensor
     K: tuple
@@ -76,6 +80,8 @@ class Section:
     colour: torch.Tensor
     opacity: torch.Tensor
     radius: torch.Tensor
+    scale: torch.Tensor | None = None
+    rot: torch.Tensor | None = None
 
     @property
     def n(self) -> int:
@@ -100,13 +106,31 @@ class Section:
         _cuda(self.colour, dt, "colour", (self.n, 3))
         _cuda(self.opacity, dt, "opacity", (self.n,))
         _cuda(self.radius, dt, "radius", (self.n,))
+        if (self.scale is None) != (self.rot is None):
+            raise ValueError("scale and rot come together")
+        if self.scale is not None:
+            _cuda(self.scale, dt, "scale", (self.n, 3))
+            _cuda(self.rot, dt, "rot", (self.n, 4))
+
+    @property
+    def ellipsoids(self) -> bool:
+        return self.scale is not None
+
+    def with_ellipsoids(self, scale, rot) -> "Section":
+        """The same Gaussians as ellipsoids with the given axis scales (n, 3)
+        and quaternions (n, 4), converted to the section's dtype and device
+        (the other arrays are shared)."""
+        dt, dev = self.colour.dtype, self.colour.device
+        as_t = lambda a: (a if isinstance(a, torch.Tensor) else torch.as_tensor(np.asarray(a)))
+        return dataclasses.replace(self, scale=as_t(scale).to(dev, dt).contiguous(),
+                                   rot=as_t(rot).to(dev, dt).contiguous())
 
     def c_struct(self) -> L.SectionC:
         self.validate()
         V, H, W = self.depth.shape
         return L.SectionC(V, W, H, _intr(self.K), _ptr(self.poses), _ptr(self.depth), self.n,
                           _ptr(self.src), self.prec, _ptr(self.colour), _ptr(self.opacity),
-                          _ptr(self.radius))
+                          _ptr(self.radius), _ptr(self.scale), _ptr(self.rot))
 
     @staticmethod
     def from_rgbd(depth: torch.Tensor, rgb: torch.Tensor, K, poses, precision: str = "f32",
@@ -398,7 +422,8 @@ class Renderer:
                  d_twist=None, d_mat=None, view_grads=None, stream=None):
         """Backward of the last render.  attr_grads: per section a tuple
         (d_colour (n,3), d_opacity (n,), d_radius (n,)) float32 device tensors
-        or None (frozen section); gradients are accumulated (+=).  With
+        or None (frozen section); for ellipsoid sections (d_colour, d_opacity,
+        None, d_scale (n,3), d_rot (n,4)); gradients are accumulated (+=).  With
         pose_grad, d_twist (6,) and d_mat (12,) float64 device tensors are
         accumulated (both created as zeros when neither is given; a missing
         one is not computed when the other is).  view_grads: per section a
@@ -415,10 +440,12 @@ class Renderer:
             for s in range(n):
                 ag = attr_grads[s] if attr_grads is not None else None
                 vg = view_grads[s] if view_grads is not None else None
-                dc, do, dr = ag if ag is not None else (None, None, None)
+                ag = tuple(ag) + (None,) * (5 - len(ag)) if ag is not None else (None,) * 5
+                dc, do, dr, ds, dq = ag
                 vg = tuple(vg) + (None,) * (3 - len(vg)) if vg is not None else (None,) * 3
                 vt, vm, vd = vg
-                gl.append(L.GradsC(_ptr(dc), _ptr(do), _ptr(dr), _ptr(vt), _ptr(vm), _ptr(vd)))
+                gl.append(L.GradsC(_ptr(dc), _ptr(do), _ptr(dr), _ptr(vt), _ptr(vm), _ptr(vd),
+                                   _ptr(ds), _ptr(dq)))
             grads = (L.GradsC * len(gl))(*gl)
             if attr_grads is not None:
                 mode |= L.VT_GRAD_ATTR

@@ -61,7 +61,7 @@ enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
     K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_SSIM_FWD, K_SSIM_BWD, K_SSIM_SUM,
-    K_VIEW_GRADS, K_NUM
+    K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -71,7 +71,9 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "k_sum_partials",  "k_pose_adam",     "k_adam_step_count",
                                    "k_attr_adam",     "k_sort_tiles_mid", "k_sort_tiles_large",
                                    "k_ssim_fwd",      "k_ssim_bwd",       "k_ssim_sum",
-                                   "k_view_grads"};
+                                   "k_view_grads",    "k_preprocess_aniso",
+                                   "k_composite_fwd_aniso", "k_composite_bwd_list_aniso",
+                                   "k_composite_bwd_aniso", "k_aniso_chain"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -120,7 +122,9 @@ struct vt_ctx {
     int64_t ssim_cap = 0;             // pixels it holds
     float4 *acc4 = nullptr;       // attribute-gradient accumulators (colour, opacity)
     float *accr = nullptr;        // and radius, per Gaussian
-    float4 *accg = nullptr;       // dL/dx of each centre (source-view gradients)
+    float4 *accg = nullptr;       // dL/dx of each centre (source-view gradients); for
+                                  // ellipsoids dL/d(a', b', c') and the direct depth term
+    float2 *accm = nullptr;       // ellipsoids: dL/d(u_c, v_c) per Gaussian
     // per-pixel lists of added Gaussians (separate allocation)
     int list_cap = kDefaultListCap;
     uint2 *plist = nullptr;       // (id, transmittance in front) per added Gaussian
@@ -129,6 +133,7 @@ struct vt_ctx {
     bool used_lists = false;
     // last render
     bool has_render = false;
+    bool aniso = false;           // the last render's sections are ellipsoids
     SecTable table{};
     Camera cam{};
     int n_tiles = 0;
@@ -205,6 +210,7 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += align_up(sizeof(uint32_t) * 8 * t);             // block overflow flags
     b += align_up(sizeof(float4) * g) + align_up(sizeof(float) * g);   // gradient accumulators
     b += align_up(sizeof(float4) * g);                   // centre gradients
+    b += align_up(sizeof(float2) * g);                   // ellipse centre terms
     return b;
 }
 
@@ -261,6 +267,7 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->acc4 = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
     c->accr = reinterpret_cast<float *>(take(sizeof(float) * g));
     c->accg = reinterpret_cast<float4 *>(take(sizeof(float4) * g));
+    c->accm = reinterpret_cast<float2 *>(take(sizeof(float2) * g));
     c->cap_g = g;
     c->cap_i = i;
     c->cap_p = p;
@@ -472,6 +479,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     SecTable T{};
     T.n = n_secs;
     int64_t total = 0, views = 0, tabrows = 0;
+    bool aniso = false;
     for (int s = 0; s < n_secs; ++s) {
         const vt_section &S = secs[s];
         if (S.n < 0) return fail(VT_ERR_INVALID_ARG, "vt_render: section %d has n < 0", s);
@@ -482,7 +490,13 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
             return fail(VT_ERR_INVALID_ARG, "vt_render: section %d precision %d unknown", s,
                         (int)S.prec);
         if ((st = check_intrinsics(S.K, "vt_render section"))) return st;
-        if (S.n > 0 && (!S.poses || !S.depth || !S.src || !S.colour || !S.opacity || !S.radius))
+        const bool ell = S.scale != nullptr;
+        if (s == 0) aniso = ell;
+        if (ell != aniso)
+            return fail(VT_ERR_INVALID_ARG, "vt_render: sections %d and 0 differ in footprint "
+                                            "(ellipsoids and spheres in one render)", s);
+        if (S.n > 0 && (!S.poses || !S.depth || !S.src || !S.colour || !S.opacity ||
+                        (ell ? !S.rot : !S.radius)))
             return fail(VT_ERR_INVALID_ARG, "vt_render: section %d has a NULL array", s);
         SecDesc &D = T.s[s];
         D.poses = S.poses;
@@ -491,7 +505,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         D.colour = S.colour;
         D.opacity = S.opacity;
         D.radius = S.radius;
+        D.scale = S.scale;
+        D.rot = S.rot;
         D.d_colour = D.d_opacity = D.d_radius = nullptr;
+        D.d_scale = D.d_rot = nullptr;
         D.gbase = total;
         D.n = S.n;
         D.tab_base = tabrows;
@@ -568,9 +585,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     }
     const unsigned gblocks = (unsigned)((total + 255) / 256);
     if (total > 0) {
-        LaunchScope ls(c, K_PREPROCESS, stream);
-        k_preprocess<<<gblocks, 256, 0, stream>>>(T, cam, c->views, c->tab, c->geo, c->app,
-                                                  c->info, c->tile_count);
+        LaunchScope ls(c, aniso ? K_PRE_AN : K_PREPROCESS, stream);
+        auto kern = aniso ? k_preprocess_aniso : k_preprocess;
+        kern<<<gblocks, 256, 0, stream>>>(T, cam, c->views, c->tab, c->geo, c->app, c->info,
+                                          c->tile_count);
     }
     {
         LaunchScope ls(c, K_SCAN, stream);
@@ -591,41 +609,104 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         // one block per SM at most: these lists are few, and the launch must
         // not hold every SM's shared memory while the others run
         k_sort_tiles<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
-            cam, c->status, kSortSmemBig, kSortSmemN, 0x7fffffff);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, 0x7fffffff);
     }
     VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
     {
         LaunchScope ls(c, K_SORT, stream);
         k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassS), stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
-            cam, c->status, kSortClassS, 0, kSortClassS);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
+            aniso ? nullptr : c->geo, cam, c->status, kSortClassS, 0, kSortClassS);
     }
     {
         LaunchScope ls(c, K_SORT_M, stream);
         k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
-            cam, c->status, kSortClassM, kSortClassS, kSortClassM);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
+            aniso ? nullptr : c->geo, cam, c->status, kSortClassM, kSortClassS, kSortClassM);
     }
     {
         LaunchScope ls(c, K_SORT_L, stream);
         k_sort_tiles<<<n_tiles, 512, kSortSmemBytes, stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo,
-            cam, c->status, kSortSmemN, kSortClassM, kSortSmemN);
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN);
     }
     VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
     {
-        LaunchScope ls(c, K_FWD, stream);
-        k_composite_fwd<<<n_tiles, kBlockPix, 0, stream>>>(
+        LaunchScope ls(c, aniso ? K_FWD_AN : K_FWD, stream);
+        auto kern = aniso ? k_composite_fwd_aniso : k_composite_fwd;
+        kern<<<n_tiles, kBlockPix, 0, stream>>>(
             cam, c->tile_off, c->sorted, c->bmask, c->geo, c->app, rgb, depth, silhouette,
-            c->pix_last, c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap, c->blk_ovf,
-            c->status);
+            c->pix_last, c->pix_nadd, c->pix_T, c->used_lists ? c->plist : nullptr, c->list_cap,
+            c->blk_ovf, c->status);
     }
     VT_CUDA(cudaGetLastError(), "vt_render launch");
+    c->aniso = aniso;
     c->table = T;
     c->cam = cam;
     c->n_tiles = n_tiles;
     c->has_render = true;
+    return VT_OK;
+}
+
+// Backward of an ellipsoid render: per-pair terms accumulated per Gaussian
+// by the list (and replay) kernels, colour / opacity scattered as for the
+// spheres, then the per-Gaussian chain to scale, quaternion and pose.
+static vt_status backward_aniso(vt_ctx *c, SecTable &T, const float *dL_drgb,
+                                const float *dL_ddepth, const float *dL_dsil, int32_t mode,
+                                const vt_grads *grads, double *d_twist, double *d_mat,
+                                cudaStream_t stream) {
+    if (mode & VT_GRAD_VIEWS)
+        return fail(VT_ERR_INVALID_ARG,
+                    "vt_render_backward: source-view gradients are not available for ellipsoids");
+    const bool attr = (mode & VT_GRAD_ATTR) != 0, pose = (mode & VT_GRAD_POSE) != 0;
+    for (int s = 0; s < T.n; ++s) {
+        if (!attr) continue;
+        T.s[s].d_colour = grads[s].d_colour;
+        T.s[s].d_opacity = grads[s].d_opacity;
+        T.s[s].d_radius = nullptr;
+        T.s[s].d_scale = grads[s].d_scale;
+        T.s[s].d_rot = grads[s].d_rot;
+    }
+    if (T.n_total > 0) {
+        if (attr)
+            VT_CUDA(cudaMemsetAsync(c->acc4, 0, sizeof(float4) * T.n_total, stream),
+                    "grad acc reset");
+        VT_CUDA(cudaMemsetAsync(c->accg, 0, sizeof(float4) * T.n_total, stream), "grad acc reset");
+        VT_CUDA(cudaMemsetAsync(c->accm, 0, sizeof(float2) * T.n_total, stream), "grad acc reset");
+    }
+    if (c->used_lists) {
+        LaunchScope ls(c, K_BWD_LIST_AN, stream);
+        k_composite_bwd_list_aniso<<<c->n_tiles, kBlockPix, 0, stream>>>(
+            T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->blk_ovf,
+            dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->acc4, c->accr, c->accg,
+            c->accm, c->status);
+    }
+    {   // tiles without complete per-pixel lists (all of them when none were kept)
+        LaunchScope ls(c, K_BWD_AN, stream);
+        k_composite_bwd_aniso<<<c->n_tiles, kBlockPix, 0, stream>>>(
+            T, c->cam, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, dL_drgb,
+            dL_ddepth, dL_dsil, mode, c->blk_ovf, c->acc4, c->accg, c->accm, c->status);
+    }
+    if (attr && T.n_total > 0) {
+        LaunchScope ls(c, K_SCATTER, stream);
+        k_attr_scatter<<<(unsigned)((T.n_total + 255) / 256), 256, 0, stream>>>(T, c->acc4,
+                                                                               c->accr);
+    }
+    const int chain_blocks =
+        (int)std::max<int64_t>(1, std::min<int64_t>((T.n_total + 255) / 256, c->n_tiles));
+    {
+        LaunchScope ls(c, K_CHAIN, stream);
+        k_aniso_chain<<<chain_blocks, 256, 0, stream>>>(T, c->cam, c->views, c->geo, c->app,
+                                                       c->accg, c->accm, (int)pose, (int)attr,
+                                                       c->pose_partials);
+    }
+    if (pose) {
+        LaunchScope ls(c, K_POSE, stream);
+        k_pose_finalize<<<1, 384, 0, stream>>>(c->pose_partials, chain_blocks, c->pose_copy,
+                                               d_twist, d_mat);
+    }
+    VT_CUDA(cudaGetLastError(), "vt_render_backward launch");
     return VT_OK;
 }
 
@@ -642,6 +723,9 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
         return fail(VT_ERR_INVALID_ARG, "vt_render_backward: POSE mode needs d_twist or d_mat");
     if (!mode) return VT_OK;
     SecTable T = c->table;
+    if (c->aniso)
+        return backward_aniso(c, T, dL_drgb, dL_ddepth, dL_dsil, mode, grads, d_twist, d_mat,
+                              stream);
     for (int s = 0; s < T.n; ++s) {
         if (mode & VT_GRAD_ATTR) {
             T.s[s].d_colour = grads[s].d_colour;

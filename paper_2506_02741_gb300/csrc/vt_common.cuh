@@ -40,7 +40,9 @@ struct SecDesc {
     const float *depth;
     const uint32_t *src;
     const void *colour, *opacity, *radius;
+    const void *scale, *rot;                  // ellipsoids (NULL: spheres)
     float *d_colour, *d_opacity, *d_radius;  // backward only
+    float *d_scale, *d_rot;                   // backward only (ellipsoids)
     double *d_view_twist, *d_view_mat;        // backward only (source-view poses)
     float *d_depth;                           // backward only (depth along the ray)
     int64_t gbase, n;       // global id range [gbase, gbase + n)
@@ -151,6 +153,8 @@ __device__ __forceinline__ ff ff_from(float2 v) { return {v.x, v.y}; }
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTScale = -0.5f * kLog2e;          // t = q * kTScale
 constexpr float kQFromT = -2.0f * 0.69314718055994531f;   // q = t * kQFromT
+constexpr float kLn2 = 0.69314718055994531f;
+constexpr float kLowPass = 0.3f;                   // EWA low-pass added to Sigma_2D (px^2)
 
 // The pixel offsets du = (px - iu) - fu, dv = (py - iv) - fv take one
 // rounding each (the integer differences are exact in FP32).
@@ -163,6 +167,19 @@ __device__ __forceinline__ float pair_t_at(int px, int py, const float4 &g0, con
     du = __fsub_rn((float)(px - __float_as_int(g0.x)), g0.y);
     dv = __fsub_rn((float)(py - __float_as_int(g0.z)), g0.w);
     return pair_t(du, dv, g1.x, g1.y);
+}
+// Ellipsoids: the record holds (a', b', c') = kTScale (Q00, 2 Q01, Q11) of
+// the conic Q = Sigma_2D^-1, and t = a' du^2 + b' du dv + c' dv^2; the
+// sphere form is the special case b' = 0 term by term.
+__device__ __forceinline__ float pair_t_aniso(float du, float dv, float a, float b, float c) {
+    return __fmaf_rn(__fmul_rn(du, a), du,
+                     __fmaf_rn(__fmul_rn(du, b), dv, __fmul_rn(__fmul_rn(dv, c), dv)));
+}
+__device__ __forceinline__ float pair_t_at_aniso(int px, int py, const float4 &g0,
+                                                 const float4 &g1, float &du, float &dv) {
+    du = __fsub_rn((float)(px - __float_as_int(g0.x)), g0.y);
+    dv = __fsub_rn((float)(py - __float_as_int(g0.z)), g0.w);
+    return pair_t_aniso(du, dv, g1.x, g1.y, g1.z);
 }
 
 // 2^t with the hardware approximation (t in [-6.5, 0]: no subnormals).
@@ -251,21 +268,28 @@ __global__ void k_setup(SecTable T, Camera cam, const double *pose12, ViewXf *vi
                         double *pose_copy);
 __global__ void k_preprocess(SecTable T, Camera cam, const ViewXf *views, const TabRow *tab,
                              float4 *geo, float4 *app, uint4 *info, uint32_t *tile_count);
+__global__ void k_preprocess_aniso(SecTable T, Camera cam, const ViewXf *views,
+                                   const TabRow *tab, float4 *geo, float4 *app, uint4 *info,
+                                   uint32_t *tile_count);
 __global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *tile_off,
                              uint32_t *tile_cursor, Status *st, unsigned long long cap);
 __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
                        unsigned long long *bucket, uint8_t *bmask_u, const Status *st);
 __global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,
                              unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted,
-                             uint8_t *bmask,
-                             const float4 *geo, Camera cam, Status *st, int smem_n, int lo,
-                             int hi);
+                             uint8_t *bmask, const float4 *geo, Camera cam, Status *st,
+                             int smem_n, int lo, int hi);
 __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
                                 const uint8_t *bmask, const float4 *geo, const float4 *app,
-                                float *rgb, float *depth,
-                                float *sil, uint32_t *pix_last, uint32_t *pix_nadd,
-                                float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
-                                const Status *st);
+                                float *rgb, float *depth, float *sil, uint32_t *pix_last,
+                                uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
+                                uint32_t *blk_ovf, const Status *st);
+__global__ void k_composite_fwd_aniso(Camera cam, const uint32_t *tile_off,
+                                      const uint32_t *sorted, const uint8_t *bmask,
+                                      const float4 *geo, const float4 *app, float *rgb,
+                                      float *depth, float *sil, uint32_t *pix_last,
+                                      uint32_t *pix_nadd, float *pix_T, uint2 *plist,
+                                      int plist_cap, uint32_t *blk_ovf, const Status *st);
 __global__ void k_composite_bwd(SecTable T, Camera cam, const uint32_t *tile_off,
                                 const uint32_t *sorted, const float4 *geo, const float4 *app,
                                 const uint32_t *pix_last, const float *pix_T,
@@ -279,6 +303,25 @@ __global__ void k_composite_bwd_list(SecTable T, Camera cam, const float4 *geo,
                                      const float *g_depth, const float *g_sil, int mode,
                                      double *pose_partials, float4 *acc4, float *accr,
                                      float4 *accg, const Status *st);
+__global__ void k_composite_bwd_list_aniso(SecTable T, Camera cam, const float4 *geo,
+                                           const float4 *app, const uint32_t *pix_nadd,
+                                           const float *pix_T, const uint2 *plist, int plist_cap,
+                                           const uint32_t *blk_ovf, const float *g_rgb,
+                                           const float *g_depth, const float *g_sil, int mode,
+                                           double *pose_partials, float4 *acc4, float *accr,
+                                           float4 *accg, float2 *accm, const Status *st);
+__global__ void k_composite_bwd_aniso(SecTable T, Camera cam, const uint32_t *tile_off,
+                                      const uint32_t *sorted, const float4 *geo,
+                                      const float4 *app, const uint32_t *pix_last,
+                                      const float *pix_T, const float *g_rgb,
+                                      const float *g_depth, const float *g_sil, int mode,
+                                      const uint32_t *tile_mask, float4 *acc4, float4 *accg,
+                                      float2 *accm, const Status *st);
+// Ellipsoids, per Gaussian: accumulated conic / centre terms -> scale,
+// quaternion and FP64 pose partials (one per block).
+__global__ void k_aniso_chain(SecTable T, Camera cam, const ViewXf *views, const float4 *geo,
+                              const float4 *app, const float4 *accg, const float2 *accm,
+                              int want_pose, int want_attr, double *pose_partials);
 __global__ void k_composite_bwd_list_views(SecTable T, Camera cam, const float4 *geo,
                                            const float4 *app, const uint32_t *pix_nadd,
                                            const float *pix_T, const uint2 *plist, int plist_cap,

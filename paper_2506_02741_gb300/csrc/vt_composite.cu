@@ -51,6 +51,34 @@ __device__ __forceinline__ uint32_t pixel_mask(float du0, float dv0, float kxs, 
     return m;
 }
 
+// The same for an ellipse record (a', b', c'): row by row the pixels with
+// a' du^2 + b' dv du + c' dv^2 >= t_min lie in the interval of du around
+// b' dv / (2 |a'|) of half-width sqrt((b' dv)^2 + 4 |a'| (c' dv^2 - t_min))
+// / (2 |a'|).  The threshold is loosened by 1e-3 relative and the interval
+// widened by 1e-3 px plus 1e-4 of its centre and half-width.
+__device__ __forceinline__ uint32_t pixel_mask_aniso(float du0, float dv0, float a, float b,
+                                                     float c, float tmin, int lxmax, int lymax) {
+    const float tl = tmin * 1.001f - 1e-5f;
+    const float na = -a;                          // > 0
+    const float h2 = 0.5f * rcp_approx(na);       // 1 / (2 |a'|)
+    uint32_t m = 0u;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float dv = dv0 + (float)r;
+        const float bd = b * dv;
+        const float disc = bd * bd + 4.f * na * (c * dv * dv - tl);
+        if (r <= lymax && disc >= 0.f) {
+            const float ctr = bd * h2;
+            const float hw0 = sqrt_approx(disc) * h2;
+            const float hw = hw0 * 1.0001f + 1e-3f + 1e-4f * (fabsf(ctr) + hw0);
+            const int lo = max(0, (int)ceilf(ctr - hw - du0));
+            const int hi = min(lxmax, (int)floorf(ctr + hw - du0));
+            if (lo <= hi) m |= ((0xFFu >> (7 - hi)) & (0xFFu << lo)) << (8 * r);
+        }
+    }
+    return m;
+}
+
 // 32 x 32 bit transpose across a warp: on return bit j of lane i's word is
 // bit i of lane j's input word (five butterfly stages).
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
@@ -90,16 +118,20 @@ __device__ __forceinline__ bool tile_flagged(const uint32_t *blk_ovf, int tile) 
 // (up to plist_cap entries, pixel-major), which the backward replays instead
 // of the tile list; blk_ovf[item] flags blocks where a pixel added more
 // (always 1 without lists).
+// Aniso = true composites ellipsoid records (a', b', c', o): their pixel
+// sets come from pixel_mask_aniso and the pair exponent from pair_t_aniso.
 constexpr int kQueue = 256;   // ring of list indices per warp (>= 31 + 128)
 
-__global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
-    Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const uint8_t *bmask,
+template <bool Aniso>
+__device__ __forceinline__ void fwd_body(
+    const Camera &cam, const uint32_t *tile_off, const uint32_t *sorted, const uint8_t *bmask,
     const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
     uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
     uint32_t *blk_ovf, const Status *st) {
     __shared__ float4 s_f[kWarps][32], s_k[kWarps][32], s_c[kWarps][32];
     __shared__ uint32_t s_gid[kWarps][32], s_idx[kWarps][32];
     __shared__ uint32_t s_q[kWarps][kQueue];
+    __shared__ float s_b[Aniso ? kWarps : 1][32];   // b' of the ellipse records
     if (st->flags) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lx = lane & 7, ly = lane >> 3;
@@ -196,12 +228,16 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
         const float ku = (float)(bx0 - __float_as_int(g0.x));
         const float kv = (float)(by0 - __float_as_int(g0.z));
         const float tmin = t_min_of(g1.w);
-        const uint32_t pm =
-            lane < cnt ? pixel_mask(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmaxi, lymaxi) : 0u;
+        uint32_t pm = 0u;
+        if (lane < cnt)
+            pm = Aniso ? pixel_mask_aniso(ku - g0.y, kv - g0.w, g1.x, g1.y, g1.z, tmin, lxmaxi,
+                                          lymaxi)
+                       : pixel_mask(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmaxi, lymaxi);
         if (!__any_sync(kFullMask, pm != 0u)) continue;
         __syncwarp();
         fs[lane] = make_float4(ku, kv, g0.y, g0.w);
-        ks[lane] = make_float4(g1.x, g1.y, tmin, g1.w);
+        ks[lane] = make_float4(g1.x, Aniso ? g1.z : g1.y, tmin, g1.w);
+        if (Aniso) s_b[Aniso ? warp : 0][lane] = g1.y;
         cs[lane] = a;
         ids[lane] = gid;
         lidx[lane] = idx;
@@ -217,8 +253,10 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
             const int j = __ffs(cand) - 1;
             cand &= cand - 1u;
             const float4 f = fs[j], k = ks[j];
-            const float t = pair_t(__fsub_rn(__fadd_rn(f.x, lxf), f.z),
-                                   __fsub_rn(__fadd_rn(f.y, lyf), f.w), k.x, k.y);
+            const float du = __fsub_rn(__fadd_rn(f.x, lxf), f.z);
+            const float dv = __fsub_rn(__fadd_rn(f.y, lyf), f.w);
+            const float t = Aniso ? pair_t_aniso(du, dv, k.x, s_b[Aniso ? warp : 0][j], k.y)
+                                  : pair_t(du, dv, k.x, k.y);
             if (!(t >= k.z)) continue;
             const float al = fminf(__fmul_rn(k.w, exp2_approx(t)), kAlphaClamp);
             const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
@@ -254,6 +292,24 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     }
     const bool ovf = __any_sync(kFullMask, nadd > cap);
     if (lane == 0) blk_ovf[item] = plist ? (uint32_t)ovf : 1u;
+}
+
+__global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
+    Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const uint8_t *bmask,
+    const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
+    uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
+    uint32_t *blk_ovf, const Status *st) {
+    fwd_body<false>(cam, tile_off, sorted, bmask, geo, app, rgb, depth, sil, pix_last, pix_nadd,
+                    pix_T, plist, plist_cap, blk_ovf, st);
+}
+
+__global__ void __launch_bounds__(kBlockPix) k_composite_fwd_aniso(
+    Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const uint8_t *bmask,
+    const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
+    uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
+    uint32_t *blk_ovf, const Status *st) {
+    fwd_body<true>(cam, tile_off, sorted, bmask, geo, app, rgb, depth, sil, pix_last, pix_nadd,
+                   pix_T, plist, plist_cap, blk_ovf, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -321,6 +377,48 @@ __device__ __forceinline__ void bwd_pixel_init(BwdPixel &P, float Tfin, float gC
     P.have_ref = false;
 }
 
+// The footprint-independent part of a back-to-front step: the Gaussian's
+// alpha, the transmittance in front of it (the forward's, or recovered by
+// division), its weight w and dL/dalpha from the pixel's running sums;
+// bwd_advance then moves the sums past it.
+struct BwdStep {
+    float om, Ti, w, dal;
+};
+
+__device__ __forceinline__ BwdStep bwd_step(BwdPixel &P, const float4 &a, float ah,
+                                            float Ti_fwd) {
+    BwdStep S;
+    const float al = fminf(ah, kAlphaClamp);
+    S.om = 1.f - al;
+    S.Ti = Ti_fwd >= 0.f ? Ti_fwd : P.T / S.om;
+    S.w = al * S.Ti;
+    const float z = a.w;
+    if (!P.have_ref) {
+        P.have_ref = true;
+        P.cr0 = a.x;
+        P.cr1 = a.y;
+        P.cr2 = a.z;
+        P.zr = z;
+    }
+    const float e0 = a.x - P.cr0, e1 = a.y - P.cr1, e2 = a.z - P.cr2, ez = z - P.zr;
+    const float num = P.gC0 * (a.x * P.Tfin + e0 * P.Sb - P.A0) +
+                      P.gC1 * (a.y * P.Tfin + e1 * P.Sb - P.A1) +
+                      P.gC2 * (a.z * P.Tfin + e2 * P.Sb - P.A2) +
+                      P.gD * (z * P.Tfin + ez * P.Sb - P.Bd) + P.gS * P.Tfin;
+    S.dal = num / S.om;
+    return S;
+}
+
+__device__ __forceinline__ void bwd_advance(BwdPixel &P, const float4 &a, const BwdStep &S) {
+    const float e0 = a.x - P.cr0, e1 = a.y - P.cr1, e2 = a.z - P.cr2, ez = a.w - P.zr;
+    P.A0 = __fmaf_rn(S.w, e0, P.A0);
+    P.A1 = __fmaf_rn(S.w, e1, P.A1);
+    P.A2 = __fmaf_rn(S.w, e2, P.A2);
+    P.Bd = __fmaf_rn(S.w, ez, P.Bd);
+    P.Sb += S.w;
+    P.T = S.Ti;
+}
+
 // One added Gaussian of the pixel, visited back to front (g0, g1: footprint
 // record with 1/r in g1.z, a: colour and depth z, t: exponent of pair_t,
 // G = 2^t, ah = o G).  Returns its colour / opacity / radius gradient terms
@@ -335,25 +433,10 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
                                          float &drd, bool want_geo, float &gxo, float &gyo,
                                          float &gzo, float Ti_fwd = -1.f) {
     const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
-    const float al = fminf(ah, kAlphaClamp);
-    const float om = 1.f - al;
-    const float Ti = Ti_fwd >= 0.f ? Ti_fwd : P.T / om;
-    const float w = al * Ti;
+    const BwdStep S = bwd_step(P, a, ah, Ti_fwd);
+    const float w = S.w, dal = S.dal;
     const float z = a.w, q = t * kQFromT;
     const float ir = g1.z, ir2 = ir * ir;
-    if (!P.have_ref) {
-        P.have_ref = true;
-        P.cr0 = a.x;
-        P.cr1 = a.y;
-        P.cr2 = a.z;
-        P.zr = z;
-    }
-    const float e0 = a.x - P.cr0, e1 = a.y - P.cr1, e2 = a.z - P.cr2, ez = z - P.zr;
-    const float num = P.gC0 * (a.x * P.Tfin + e0 * P.Sb - P.A0) +
-                      P.gC1 * (a.y * P.Tfin + e1 * P.Sb - P.A1) +
-                      P.gC2 * (a.z * P.Tfin + e2 * P.Sb - P.A2) +
-                      P.gD * (z * P.Tfin + ez * P.Sb - P.Bd) + P.gS * P.Tfin;
-    const float dal = num / om;
     dc0 = P.gC0 * w;
     dc1 = P.gC1 * w;
     dc2 = P.gC2 * w;
@@ -389,12 +472,33 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
         acc.a[10] += gy;
         acc.a[11] += gz;
     }
-    P.A0 = __fmaf_rn(w, e0, P.A0);
-    P.A1 = __fmaf_rn(w, e1, P.A1);
-    P.A2 = __fmaf_rn(w, e2, P.A2);
-    P.Bd = __fmaf_rn(w, ez, P.Bd);
-    P.Sb += w;
-    P.T = Ti;
+    bwd_advance(P, a, S);
+}
+
+// The same step for an ellipse record g1 = (a', b', c', o): with
+// dL/dt = dL/dalpha ahat ln 2 below the clamp, the pair adds
+//   dL/d(a', b', c') = dL/dt (du^2, du dv, dv^2),
+//   dL/du_c = -dL/dt (2 a' du + b' dv),  dL/dv_c = -dL/dt (b' du + 2 c' dv),
+// and the direct depth term gD w; the per-Gaussian pass (k_aniso_chain)
+// turns their sums into scale, quaternion and pose gradients.
+__device__ __forceinline__ void bwd_pair_aniso(BwdPixel &P, const float4 &g1, const float4 &a,
+                                               float du, float dv, float G, float ah,
+                                               float &dc0, float &dc1, float &dc2, float &dop,
+                                               float4 &dgq, float2 &dm, float Ti_fwd) {
+    const BwdStep S = bwd_step(P, a, ah, Ti_fwd);
+    dc0 = P.gC0 * S.w;
+    dc1 = P.gC1 * S.w;
+    dc2 = P.gC2 * S.w;
+    float dt = 0.f;
+    dop = 0.f;
+    if (ah < kAlphaClamp) {
+        dop = S.dal * G;
+        dt = S.dal * ah * kLn2;
+    }
+    const float tu = dt * du, tv = dt * dv;
+    dgq = make_float4(tu * du, tu * dv, tv * dv, P.gD * S.w);
+    dm = make_float2(-(2.f * g1.x * tu + g1.y * tv), -(g1.y * tu + 2.f * g1.z * tv));
+    bwd_advance(P, a, S);
 }
 
 // Per-Gaussian gradient terms go to workspace accumulators indexed by
@@ -415,6 +519,23 @@ __device__ __forceinline__ void add_pair_grads(const SecTable &Tab, int64_t g, b
     }
     if (want_views && (S.d_view_twist || S.d_view_mat || S.d_depth))
         atomicAdd(accg + g, make_float4(gx, gy, gz, 0.f));
+}
+
+// Ellipsoids: (colour, opacity) as above when the section wants them; the
+// conic / depth terms and the centre terms when the pose gradient or the
+// section's scale / quaternion gradients are wanted.
+__device__ __forceinline__ void add_pair_grads_aniso(const SecTable &Tab, int64_t g, bool want_attr,
+                                                     bool want_pose, float dc0, float dc1,
+                                                     float dc2, float dop, const float4 &dgq,
+                                                     const float2 &dm, float4 *acc4,
+                                                     float4 *accg, float2 *accm) {
+    const SecDesc &S = Tab.s[find_section(Tab, g)];
+    if (want_attr && (S.d_colour || S.d_opacity))
+        atomicAdd(acc4 + g, make_float4(dc0, dc1, dc2, dop));
+    if (want_pose || (want_attr && (S.d_scale || S.d_rot))) {
+        atomicAdd(accg + g, dgq);
+        atomicAdd(accm + g, dm);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_attr_scatter(SecTable Tab, const float4 *acc4,
@@ -452,17 +573,56 @@ __device__ __forceinline__ void write_pose_partial(const PoseAcc &acc, double (*
     }
 }
 
+// One ellipse entry of a replay batch for the whole warp (every lane one
+// pixel): the lanes whose pixel added it take their step, and the warp's
+// sums go to the per-Gaussian accumulators from lane 0.
+__device__ __forceinline__ void replay_pair_aniso(const SecTable &Tab, BwdPixel &P,
+                                                  const float4 &g0, const float4 &g1,
+                                                  const float4 &a, float tmin, uint32_t gid,
+                                                  bool before_last, int px, int py, int lane,
+                                                  bool want_attr, bool want_pose, float4 *acc4,
+                                                  float4 *accg, float2 *accm) {
+    float dc0 = 0.f, dc1 = 0.f, dc2 = 0.f, dop = 0.f;
+    float4 dgq = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 dm = make_float2(0.f, 0.f);
+    bool contrib = false;
+    if (before_last) {
+        float du, dv;
+        const float t = pair_t_at_aniso(px, py, g0, g1, du, dv);
+        if (t >= tmin) {
+            const float G = exp2_approx(t);
+            contrib = true;
+            bwd_pair_aniso(P, g1, a, du, dv, G, __fmul_rn(g1.w, G), dc0, dc1, dc2, dop, dgq, dm,
+                           -1.f);
+        }
+    }
+    if (!__any_sync(kFullMask, contrib)) return;
+    dc0 = warp_sum(dc0);
+    dc1 = warp_sum(dc1);
+    dc2 = warp_sum(dc2);
+    dop = warp_sum(dop);
+    dgq = make_float4(warp_sum(dgq.x), warp_sum(dgq.y), warp_sum(dgq.z), warp_sum(dgq.w));
+    dm = make_float2(warp_sum(dm.x), warp_sum(dm.y));
+    if (lane == 0)
+        add_pair_grads_aniso(Tab, gid, want_attr, want_pose, dc0, dc1, dc2, dop, dgq, dm, acc4,
+                             accg, accm);
+}
+
 // Tile replay: the block walks its tile's list from the largest list end of
 // its pixels back to the front in shared-memory batches; each warp visits the
 // Gaussians whose disc touches its 8x4 block.  Used when no per-pixel lists
 // were kept (memory budget) and for tiles whose lists overflowed (tile_mask:
 // only tiles with tile_mask[t] != 0; NULL = all tiles).
-__global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
-    SecTable Tab, Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
-    const float4 *app, const uint32_t *pix_last, const float *pix_T,
+// Aniso = true replays ellipsoid records (k_composite_bwd_aniso): every
+// entry of the batch is visited (no block filter for the rotated conic), the
+// warp sums each Gaussian's terms and adds them per Gaussian.
+template <bool Aniso>
+__device__ __forceinline__ void replay_body(
+    const SecTable &Tab, const Camera &cam, const uint32_t *tile_off, const uint32_t *sorted,
+    const float4 *geo, const float4 *app, const uint32_t *pix_last, const float *pix_T,
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
     double *pose_partials, const uint32_t *tile_mask, float4 *acc4, float *accr, float4 *accg,
-    const Status *st) {
+    float2 *accm, const Status *st) {
     __shared__ float4 s_g0[kBatch], s_g1[kBatch], s_a[kBatch];
     __shared__ float s_tmin[kBatch];
     __shared__ uint32_t s_gid[kBatch];
@@ -529,15 +689,21 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
                     bool rel = false;
                     if (jj < nb && (uint32_t)(b0 + jj) < wl) {
                         const float4 h0 = s_g0[jj], h1 = s_g1[jj];
-                        rel = block_touches((float)(bx0 - __float_as_int(h0.x)) - h0.y,
-                                            (float)(by0 - __float_as_int(h0.z)) - h0.w, h1.x,
-                                            h1.y, s_tmin[jj], lxmax, lymax);
+                        rel = Aniso || block_touches((float)(bx0 - __float_as_int(h0.x)) - h0.y,
+                                                     (float)(by0 - __float_as_int(h0.z)) - h0.w,
+                                                     h1.x, h1.y, s_tmin[jj], lxmax, lymax);
                     }
                     unsigned mask = __ballot_sync(kFullMask, rel);
                     while (mask) {
                         const int bit = 31 - __clz(mask);
                         mask &= ~(1u << bit);
                         const int j = j0 + bit;
+                        if constexpr (Aniso) {
+                            replay_pair_aniso(Tab, P, s_g0[j], s_g1[j], s_a[j], s_tmin[j],
+                                              s_gid[j], (uint32_t)(b0 + j) < my_last, px, py,
+                                              lane, want_attr, want_pose, acc4, accg, accm);
+                            continue;
+                        }
                         float dc0 = 0.f, dc1 = 0.f, dc2 = 0.f, dop = 0.f, drd = 0.f;
                         float gx = 0.f, gy = 0.f, gz = 0.f;
                         bool contrib = false;
@@ -572,7 +738,26 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
             __syncthreads();
         }
     }
-    if (want_pose) write_pose_partial(acc, s_pose, pose_partials, tile);
+    if (want_pose && !Aniso) write_pose_partial(acc, s_pose, pose_partials, tile);
+}
+
+__global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
+    SecTable Tab, Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
+    const float4 *app, const uint32_t *pix_last, const float *pix_T,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, const uint32_t *tile_mask, float4 *acc4, float *accr, float4 *accg,
+    const Status *st) {
+    replay_body<false>(Tab, cam, tile_off, sorted, geo, app, pix_last, pix_T, g_rgb, g_depth,
+                       g_sil, mode, pose_partials, tile_mask, acc4, accr, accg, nullptr, st);
+}
+
+__global__ void __launch_bounds__(kBlockPix) k_composite_bwd_aniso(
+    SecTable Tab, Camera cam, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
+    const float4 *app, const uint32_t *pix_last, const float *pix_T, const float *g_rgb,
+    const float *g_depth, const float *g_sil, int mode, const uint32_t *tile_mask, float4 *acc4,
+    float4 *accg, float2 *accm, const Status *st) {
+    replay_body<true>(Tab, cam, tile_off, sorted, geo, app, pix_last, pix_T, g_rgb, g_depth,
+                      g_sil, mode, nullptr, tile_mask, acc4, nullptr, accg, accm, st);
 }
 
 // Per-pixel list replay: every lane walks the ids its pixel added, recorded
@@ -582,14 +767,16 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
 // k_composite_bwd.
 // Views = true compiles the source-view gradient path (mode VT_GRAD_VIEWS)
 // into k_composite_bwd_list_views; the tracking and mapping paths launch
-// k_composite_bwd_list, which does not carry it.
-template <bool Views>
+// k_composite_bwd_list, which does not carry it.  Aniso = true walks
+// ellipsoid records (k_composite_bwd_list_aniso): per-Gaussian accumulation
+// instead of per-lane pose sums.
+template <bool Views, bool Aniso>
 __device__ __forceinline__ void bwd_list_body(
     const SecTable &Tab, const Camera &cam, const float4 *geo, const float4 *app,
     const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
     const uint32_t *blk_ovf, const float *g_rgb, const float *g_depth, const float *g_sil,
-    int mode, double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st,
-    double (*s_pose)[12]) {
+    int mode, double *pose_partials, float4 *acc4, float *accr, float4 *accg, float2 *accm,
+    const Status *st, double (*s_pose)[12]) {
     if (st->flags) return;
     const int tile = blockIdx.x;
     if (tile_flagged(blk_ovf, tile)) return;
@@ -643,17 +830,27 @@ __device__ __forceinline__ void bwd_list_body(
         }
         if (k > 1) e_nn = mylist[k - 2];
         float du, dv;
-        const float t = pair_t_at(px, py, g0, g1, du, dv);
+        const float t = Aniso ? pair_t_at_aniso(px, py, g0, g1, du, dv)
+                              : pair_t_at(px, py, g0, g1, du, dv);
         const float G = exp2_approx(t);
         const float ah = __fmul_rn(g1.w, G);
-        float dc0, dc1, dc2, dop, drd, gx, gy, gz;
-        bwd_pair(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop, drd,
-                 want_views, gx, gy, gz, Ti);
-        if (want_attr || want_views)
-            add_pair_grads(Tab, g, want_attr, want_views, dc0, dc1, dc2, dop, drd, gx, gy, gz,
-                           acc4, accr, accg);
+        if constexpr (Aniso) {
+            float dc0, dc1, dc2, dop;
+            float4 dgq;
+            float2 dm;
+            bwd_pair_aniso(P, g1, a, du, dv, G, ah, dc0, dc1, dc2, dop, dgq, dm, Ti);
+            add_pair_grads_aniso(Tab, g, want_attr, want_pose, dc0, dc1, dc2, dop, dgq, dm, acc4,
+                                 accg, accm);
+        } else {
+            float dc0, dc1, dc2, dop, drd, gx, gy, gz;
+            bwd_pair(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop,
+                     drd, want_views, gx, gy, gz, Ti);
+            if (want_attr || want_views)
+                add_pair_grads(Tab, g, want_attr, want_views, dc0, dc1, dc2, dop, drd, gx, gy, gz,
+                               acc4, accr, accg);
+        }
     }
-    if (want_pose) write_pose_partial(acc, s_pose, pose_partials, tile);
+    if (want_pose && !Aniso) write_pose_partial(acc, s_pose, pose_partials, tile);
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
@@ -662,8 +859,20 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
     double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st) {
     __shared__ double s_pose[kBlockPix / 32][12];
-    bwd_list_body<false>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf, g_rgb,
-                         g_depth, g_sil, mode, pose_partials, acc4, accr, accg, st, s_pose);
+    bwd_list_body<false, false>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf,
+                                g_rgb, g_depth, g_sil, mode, pose_partials, acc4, accr, accg,
+                                nullptr, st, s_pose);
+}
+
+__global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_aniso(
+    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
+    const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *blk_ovf,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, float4 *acc4, float *accr, float4 *accg, float2 *accm,
+    const Status *st) {
+    bwd_list_body<false, true>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf,
+                               g_rgb, g_depth, g_sil, mode, pose_partials, acc4, accr, accg, accm,
+                               st, nullptr);
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_views(
@@ -672,8 +881,184 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_views(
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
     double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st) {
     __shared__ double s_pose[kBlockPix / 32][12];
-    bwd_list_body<true>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf, g_rgb,
-                        g_depth, g_sil, mode, pose_partials, acc4, accr, accg, st, s_pose);
+    bwd_list_body<true, false>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf,
+                               g_rgb, g_depth, g_sil, mode, pose_partials, acc4, accr, accg,
+                               nullptr, st, s_pose);
+}
+
+// Ellipsoids, one thread per Gaussian (grid-stride; one FP64 pose partial
+// per block).  From the accumulated dL/d(a', b', c'), the direct depth term
+// and dL/d(u_c, v_c):
+//   M_Q = kTScale [[da', db'], [db', dc']]       (t = kTScale d^T Q d),
+//   G2 = dL/dSigma_2D = -Q M_Q Q,  Gc = dL/dSigma_c = J^T G2 J,
+//   dL/dJ = 2 G2 J Sigma_c,
+//   g = dL/dx through (u_c, v_c), J(x) and the depth output;
+// the pose terms A = x g^T + 2 Sigma_c Gc and s = g (k_pose_finalize forms
+// the twist and the matrix from them: R^T Sigma_w R = Sigma_c gives dL/dR =
+// R Sigma_c (Gc + Gc^T) for the covariance), and with the section's
+// scale / quaternion gradients Gk = M^T Gc M, dL/ds_i = 2 s_i (R^T Gk R)_ii,
+// dL/dR(q) = 2 Gk R(q) diag(s^2), chained through the normalisation of q.
+// FP32 per Gaussian; the pose sums in FP64 across the block.
+__global__ void __launch_bounds__(256) k_aniso_chain(SecTable Tab, Camera cam,
+                                                     const ViewXf *views, const float4 *geo,
+                                                     const float4 *app, const float4 *accg,
+                                                     const float2 *accm, int want_pose,
+                                                     int want_attr, double *pose_partials) {
+    __shared__ double red[12][8];
+    float acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Tab.n_total;
+         i += stride) {
+        const float4 dg = accg[i];
+        const float2 dm = accm[i];
+        if (dg.x == 0.f && dg.y == 0.f && dg.z == 0.f && dg.w == 0.f && dm.x == 0.f &&
+            dm.y == 0.f)
+            continue;
+        const SecDesc &S = Tab.s[find_section(Tab, i)];
+        const int64_t li = i - S.gbase;
+        const float4 g0 = geo[2 * i], g1 = geo[2 * i + 1];
+        const float z = app[i].w, iz = 1.f / z;
+        const float ucr = ((float)__float_as_int(g0.x) - cam.cx) + g0.y;
+        const float vcr = ((float)__float_as_int(g0.z) - cam.cy) + g0.w;
+        const float J0[3] = {cam.fx * iz, 0.f, -ucr * iz}, J1[3] = {0.f, cam.fy * iz, -vcr * iz};
+        // G2 = -Q M_Q Q
+        const float ik = 1.f / kTScale;
+        const float Q00 = g1.x * ik, Q01 = 0.5f * g1.y * ik, Q11 = g1.z * ik;
+        const float m00 = kTScale * dg.x, m01 = kTScale * dg.y, m11 = kTScale * dg.z;
+        const float a00 = Q00 * m00 + Q01 * m01, a01 = Q00 * m01 + Q01 * m11;
+        const float a10 = Q01 * m00 + Q11 * m01, a11 = Q01 * m01 + Q11 * m11;
+        const float G00 = -(a00 * Q00 + a01 * Q01), G01 = -(a00 * Q01 + a01 * Q11);
+        const float G11 = -(a10 * Q01 + a11 * Q11);
+        // P = G2 J (2 x 3), Gc = J^T P
+        float P0[3], P1[3], Gc[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            P0[c] = G00 * J0[c] + G01 * J1[c];
+            P1[c] = G01 * J0[c] + G11 * J1[c];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) Gc[3 * a + b] = J0[a] * P0[b] + J1[a] * P1[b];
+        // Sigma_c = U U^T, U = M R(q) diag(s)
+        const uint32_t plane = (uint32_t)S.W * (uint32_t)S.H;
+        const float *Mf = views[S.view_base + S.src[li] / plane].Mf;
+        const float sc[3] = {ld_attr(S.scale, S.prec, 3 * li), ld_attr(S.scale, S.prec, 3 * li + 1),
+                             ld_attr(S.scale, S.prec, 3 * li + 2)};
+        float qv[4] = {ld_attr(S.rot, S.prec, 4 * li), ld_attr(S.rot, S.prec, 4 * li + 1),
+                       ld_attr(S.rot, S.prec, 4 * li + 2), ld_attr(S.rot, S.prec, 4 * li + 3)};
+        const float qn = sqrtf(qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]);
+        const float iq = 1.f / qn;
+        const float w = qv[0] * iq, x = qv[1] * iq, y = qv[2] * iq, zq = qv[3] * iq;
+        const float Rq[9] = {1.f - 2.f * (y * y + zq * zq), 2.f * (x * y - w * zq),
+                             2.f * (x * zq + w * y),        2.f * (x * y + w * zq),
+                             1.f - 2.f * (x * x + zq * zq), 2.f * (y * zq - w * x),
+                             2.f * (x * zq - w * y),        2.f * (y * zq + w * x),
+                             1.f - 2.f * (x * x + y * y)};
+        float U[9], Sc[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                U[3 * a + k] = (Mf[3 * a] * Rq[k] + Mf[3 * a + 1] * Rq[3 + k] +
+                                Mf[3 * a + 2] * Rq[6 + k]) * sc[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                Sc[3 * a + b] = U[3 * a] * U[3 * b] + U[3 * a + 1] * U[3 * b + 1] +
+                                U[3 * a + 2] * U[3 * b + 2];
+        // dL/dJ = 2 P Sigma_c, only the entries of J that vary
+        float GJ0[3], GJ1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            GJ0[c] = 2.f * (P0[0] * Sc[c] + P0[1] * Sc[3 + c] + P0[2] * Sc[6 + c]);
+            GJ1[c] = 2.f * (P1[0] * Sc[c] + P1[1] * Sc[3 + c] + P1[2] * Sc[6 + c]);
+        }
+        float g[3];
+        g[0] = dm.x * J0[0] - GJ0[2] * J0[0] * iz;
+        g[1] = dm.y * J1[1] - GJ1[2] * J1[1] * iz;
+        g[2] = -(dm.x * ucr + dm.y * vcr) * iz -
+               iz * (GJ0[0] * J0[0] + GJ1[1] * J1[1] + 2.f * (GJ0[2] * J0[2] + GJ1[2] * J1[2])) +
+               dg.w;
+        if (want_pose) {
+            const float X[3] = {ucr * z / cam.fx, vcr * z / cam.fy, z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    acc[3 * a + b] += X[a] * g[b] + 2.f * (Sc[3 * a] * Gc[b] +
+                                                           Sc[3 * a + 1] * Gc[3 + b] +
+                                                           Sc[3 * a + 2] * Gc[6 + b]);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) acc[9 + b] += g[b];
+        }
+        if (want_attr && (S.d_scale || S.d_rot)) {
+            float Gk[9], RG[9], V[3];   // M^T Gc M, Gk R(q), diag(R^T Gk R)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float T_[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    T_[d] = Gc[3 * a] * Mf[d] + Gc[3 * a + 1] * Mf[3 + d] + Gc[3 * a + 2] * Mf[6 + d];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) RG[3 * a + d] = T_[d];   // (Gc M)[a][d]
+            }
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    Gk[3 * b + d] = Mf[b] * RG[d] + Mf[3 + b] * RG[3 + d] + Mf[6 + b] * RG[6 + d];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    RG[3 * a + k] = Gk[3 * a] * Rq[k] + Gk[3 * a + 1] * Rq[3 + k] +
+                                    Gk[3 * a + 2] * Rq[6 + k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                V[k] = Rq[k] * RG[k] + Rq[3 + k] * RG[3 + k] + Rq[6 + k] * RG[6 + k];
+            if (S.d_scale) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) S.d_scale[3 * li + k] += 2.f * sc[k] * V[k];
+            }
+            if (S.d_rot) {
+                float gR[9];   // 2 Gk R(q) diag(s^2)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) gR[3 * a + k] = 2.f * RG[3 * a + k] * sc[k] * sc[k];
+                const float dw = 2.f * (-zq * gR[1] + y * gR[2] + zq * gR[3] - x * gR[5] -
+                                        y * gR[6] + x * gR[7]);
+                const float dx = 2.f * (y * gR[1] + zq * gR[2] + y * gR[3] - 2.f * x * gR[4] -
+                                        w * gR[5] + zq * gR[6] + w * gR[7] - 2.f * x * gR[8]);
+                const float dy = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] +
+                                        zq * gR[5] - w * gR[6] + zq * gR[7] - 2.f * y * gR[8]);
+                const float dz = 2.f * (-2.f * zq * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] -
+                                        2.f * zq * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+                const float proj = dw * w + dx * x + dy * y + dz * zq;
+                S.d_rot[4 * li + 0] += (dw - w * proj) * iq;
+                S.d_rot[4 * li + 1] += (dx - x * proj) * iq;
+                S.d_rot[4 * li + 2] += (dy - y * proj) * iq;
+                S.d_rot[4 * li + 3] += (dz - zq * proj) * iq;
+            }
+        }
+    }
+    if (!want_pose) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double v = warp_sum_d((double)acc[k]);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+        pose_partials[(size_t)blockIdx.x * 12 + threadIdx.x] = t;
+    }
 }
 
 // Source-view pose gradients (head-frame bundle adjustment, Sec. 3.4).  The

@@ -129,6 +129,68 @@ __device__ __forceinline__ uint32_t box_block_mask(uint32_t b0, uint32_t b1, uin
 }
 
 // ---------------------------------------------------------------------------
+// Footprint of an ellipsoid (the anisotropic variant): with its scale s and
+// normalised quaternion q, the view -> target rotation M (FP32 composite of
+// the render) and the Jacobian of the projection at the centre,
+//   J = [[fx/z, 0, -(u_c - cx)/z], [0, fy/z, -(v_c - cy)/z]],
+// T = J M R(q) diag(s) (2 x 3) and Sigma_2D = T T^T + 0.3 I (sums of squares
+// on the diagonal, no cancellation there).  The determinant takes the
+// product Sigma_01^2 with its rounding error (two FMAs), so the conic
+// Q = Sigma_2D^-1 keeps a few ulp where the ellipse is thin.  Returns the
+// record (a', b', c', o) = (kTScale Q00, 2 kTScale Q01, kTScale Q11, o) and
+// the half extents sqrt(qlim Sigma_ii) of the ellipse q <= qlim, widened.
+__device__ __forceinline__ bool ellipse_footprint(const SecDesc &S, int64_t li, const float *Mf,
+                                                  float ucr, float vcr, float z,
+                                                  const Camera &cam, float o, float qlim,
+                                                  float4 &g1, float &ex, float &ey) {
+    const float s0 = ld_attr(S.scale, S.prec, 3 * li), s1 = ld_attr(S.scale, S.prec, 3 * li + 1),
+                s2 = ld_attr(S.scale, S.prec, 3 * li + 2);
+    float qw = ld_attr(S.rot, S.prec, 4 * li), qx = ld_attr(S.rot, S.prec, 4 * li + 1),
+          qy = ld_attr(S.rot, S.prec, 4 * li + 2), qz = ld_attr(S.rot, S.prec, 4 * li + 3);
+    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    if (!(s0 > 0.f && s1 > 0.f && s2 > 0.f && isfinite(s0 + s1 + s2) && qn2 > 0.f &&
+          isfinite(qn2)))
+        return false;
+    const float iq = rsqrtf(qn2);
+    qw *= iq;
+    qx *= iq;
+    qy *= iq;
+    qz *= iq;
+    const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz),
+                         2.f * (qx * qz + qw * qy),       2.f * (qx * qy + qw * qz),
+                         1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                         2.f * (qx * qz - qw * qy),       2.f * (qy * qz + qw * qx),
+                         1.f - 2.f * (qx * qx + qy * qy)};
+    const float iz = 1.f / z;
+    const float j00 = cam.fx * iz, j02 = -ucr * iz, j11 = cam.fy * iz, j12 = -vcr * iz;
+    float B0[3], B1[3];   // J M
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        B0[c] = j00 * Mf[c] + j02 * Mf[6 + c];
+        B1[c] = j11 * Mf[3 + c] + j12 * Mf[6 + c];
+    }
+    const float sc[3] = {s0, s1, s2};
+    float T0[3], T1[3];   // J M R(q) diag(s)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T0[k] = (B0[0] * Rq[k] + B0[1] * Rq[3 + k] + B0[2] * Rq[6 + k]) * sc[k];
+        T1[k] = (B1[0] * Rq[k] + B1[1] * Rq[3 + k] + B1[2] * Rq[6 + k]) * sc[k];
+    }
+    const float S00 = T0[0] * T0[0] + T0[1] * T0[1] + T0[2] * T0[2] + kLowPass;
+    const float S11 = T1[0] * T1[0] + T1[1] * T1[1] + T1[2] * T1[2] + kLowPass;
+    const float S01 = T0[0] * T1[0] + T0[1] * T1[1] + T0[2] * T1[2];
+    const float w = S01 * S01;
+    const float det = __fmaf_rn(S00, S11, -w) - __fmaf_rn(S01, S01, -w);
+    if (!(det > 0.f) || !isfinite(det)) return false;
+    const float idet = 1.f / det;
+    const float Q00 = S11 * idet, Q01 = -S01 * idet, Q11 = S00 * idet;
+    g1 = make_float4(Q00 * kTScale, 2.f * Q01 * kTScale, Q11 * kTScale, o);
+    ex = sqrtf(qlim * S00) * 1.001f + 1e-2f;
+    ey = sqrtf(qlim * S11) * 1.001f + 1e-2f;
+    return isfinite(g1.x) && isfinite(g1.y) && isfinite(g1.z);
+}
+
+// ---------------------------------------------------------------------------
 // k_preprocess: one thread per Gaussian.  Gathers its depth pixel, computes
 // the FP32 depth key (fixed operation order, identical to the definition),
 // culls invalid depth, z_key < 0.1 and opacity < 1/255, projects the centre
@@ -137,10 +199,13 @@ __device__ __forceinline__ uint32_t box_block_mask(uint32_t b0, uint32_t b1, uin
 // pixel box of the disc q <= min(9, 2 ln(255 o)), and counts its tiles.
 // The records keep kx, ky scaled to the base-2 exponent t = -q log2(e)/2
 // (see pair_t) and 1/r for the backward; info keeps the pixel box, the depth
-// key and the tile count.
-__global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, const ViewXf *views,
-                                                    const TabRow *tab, float4 *geo, float4 *app,
-                                                    uint4 *info, uint32_t *tile_count) {
+// key and the tile count.  Ellipsoids (Aniso) keep the conic instead (see
+// ellipse_footprint).
+template <bool Aniso>
+__device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera &cam,
+                                                const ViewXf *views, const TabRow *tab,
+                                                float4 *geo, float4 *app, uint4 *info,
+                                                uint32_t *tile_count) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t r0 = 0, r1 = 0, nt = 0, zbits = 0;
     if (gid < T.n_total) {
@@ -156,7 +221,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
         const bool in_range = k < (uint32_t)S.n_views;   // src beyond the views: no Gaussian
         const float D = in_range ? S.depth[src] : 0.f;
         const float o = ld_attr(S.opacity, S.prec, li);
-        const float r = ld_attr(S.radius, S.prec, li);
+        const float r = Aniso ? 1.f : ld_attr(S.radius, S.prec, li);
         bool ok = in_range && isfinite(D) && D > 0.f && o >= kAlphaMin && r > 0.f && isfinite(r);
         const ViewXf &X = views[S.view_base + (ok ? k : 0)];
         float zkey = 0.f;
@@ -183,16 +248,26 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
             const ff nz = ff_add(ff_mul_f(hz, D), ff_from(X.mz));
             const ff uc = ff_div(nu, nz), vc = ff_div(nv, nz);
             const float z = nz.hi;
-            const float tx = __fdiv_rn(z, __fmul_rn(cam.fx, r));
-            const float ty = __fdiv_rn(z, __fmul_rn(cam.fy, r));
-            const float kx = __fmul_rn(tx, tx), ky = __fmul_rn(ty, ty);
             float qlim = kQMax;
             const float qo = 2.f * logf(255.f * o);
             if (qo < qlim) qlim = qo;
             qlim = qlim * 1.0001f + 1e-4f;
-            const float ex = sqrtf(qlim / kx) + 1e-3f, ey = sqrtf(qlim / ky) + 1e-3f;
-            ok = z > 0.f && kx > 0.f && ky > 0.f && isfinite(kx) && isfinite(ky) &&
-                 fabsf(uc.hi) < 16777216.f && fabsf(vc.hi) < 16777216.f;
+            float ex, ey;
+            float4 g1;
+            if constexpr (!Aniso) {
+                const float tx = __fdiv_rn(z, __fmul_rn(cam.fx, r));
+                const float ty = __fdiv_rn(z, __fmul_rn(cam.fy, r));
+                const float kx = __fmul_rn(tx, tx), ky = __fmul_rn(ty, ty);
+                ex = sqrtf(qlim / kx) + 1e-3f;
+                ey = sqrtf(qlim / ky) + 1e-3f;
+                ok = kx > 0.f && ky > 0.f && isfinite(kx) && isfinite(ky);
+                g1 = make_float4(__fmul_rn(kx, kTScale), __fmul_rn(ky, kTScale), __frcp_rn(r), o);
+            } else {
+                ok = ellipse_footprint(S, li, X.Mf, __fadd_rn(__fsub_rn(uc.hi, cam.cx), uc.lo),
+                                       __fadd_rn(__fsub_rn(vc.hi, cam.cy), vc.lo), z, cam, o,
+                                       qlim, g1, ex, ey);
+            }
+            ok = ok && z > 0.f && fabsf(uc.hi) < 16777216.f && fabsf(vc.hi) < 16777216.f;
             if (ok) {
                 const float u0 = fmaxf(ceilf(uc.hi - ex), 0.f);
                 const float u1 = fminf(floorf(uc.hi + ex), (float)(cam.W - 1));
@@ -210,8 +285,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
                     const float fu = __fadd_rn(__fsub_rn(uc.hi, (float)iu), uc.lo);
                     const float fv = __fadd_rn(__fsub_rn(vc.hi, (float)iv), vc.lo);
                     geo[2 * gid] = make_float4(__int_as_float(iu), fu, __int_as_float(iv), fv);
-                    geo[2 * gid + 1] = make_float4(__fmul_rn(kx, kTScale), __fmul_rn(ky, kTScale),
-                                                   __frcp_rn(r), o);
+                    geo[2 * gid + 1] = g1;
                     const float c0 = ld_attr(S.colour, S.prec, 3 * li + 0);
                     const float c1 = ld_attr(S.colour, S.prec, 3 * li + 1);
                     const float c2 = ld_attr(S.colour, S.prec, 3 * li + 2);
@@ -225,6 +299,19 @@ __global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, cons
                   [&](uint32_t t, unsigned peers, int rank, uint32_t, uint32_t) {
                       if (rank == 0) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
                   });
+}
+
+__global__ void __launch_bounds__(256) k_preprocess(SecTable T, Camera cam, const ViewXf *views,
+                                                    const TabRow *tab, float4 *geo, float4 *app,
+                                                    uint4 *info, uint32_t *tile_count) {
+    preprocess_body<false>(T, cam, views, tab, geo, app, info, tile_count);
+}
+
+__global__ void __launch_bounds__(256) k_preprocess_aniso(SecTable T, Camera cam,
+                                                          const ViewXf *views, const TabRow *tab,
+                                                          float4 *geo, float4 *app, uint4 *info,
+                                                          uint32_t *tile_count) {
+    preprocess_body<true>(T, cam, views, tab, geo, app, info, tile_count);
 }
 
 // ---------------------------------------------------------------------------
@@ -405,7 +492,8 @@ __device__ __forceinline__ unsigned bits_of(uint32_t span) { return span ? 32 - 
 
 // Writes the sorted ids of a tile and their block masks, the masks computed
 // from the records (used where the sort could not carry them): id_of(i)
-// gives entry i.
+// gives entry i.  Without records (geo NULL: ellipse records, which the
+// sphere test does not read) every block is marked.
 struct SortOut {
     uint32_t *__restrict__ sorted;
     uint8_t *__restrict__ bmask;
@@ -418,9 +506,10 @@ struct SortOut {
         for (int i = tid; i < n; i += kSortThreads) {
             const uint32_t g = id_of(i);
             sorted[start + i] = g;
-            bmask[start + i] = (uint8_t)tile_block_mask(__ldg(geo + 2 * (size_t)g),
-                                                        __ldg(geo + 2 * (size_t)g + 1), tx, ty,
-                                                        cam);
+            bmask[start + i] = geo ? (uint8_t)tile_block_mask(__ldg(geo + 2 * (size_t)g),
+                                                              __ldg(geo + 2 * (size_t)g + 1), tx,
+                                                              ty, cam)
+                                   : (uint8_t)0xFFu;
         }
     }
 };

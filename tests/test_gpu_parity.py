@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (the benchmark spec): FP32 forward within 1e-5 relative (floor 1 for
+Tolerances: FP32 forward within 1e-5 relative (floor 1 for
 colour/silhouette, 4 m for depth); gradients within 1e-4 relative (per-tensor
 L2 and per element with a floor of 1e-3 of the largest magnitude).  Integer
 and index results (section ids, depth keys, per-pixel counts, list order) are
