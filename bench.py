@@ -259,6 +259,68 @@ def run_head_frame(dev, iters: int = 50):
             "backward_pose_and_views_ms": ba_ms, "backward_pose_only_ms": pose_ms}
 
 
+def run_ellipsoids(dev, iters: int = 50):
+    """Anisotropic variant (ellipsoid Gaussians, EWA footprint) on the
+    640x480 8-keyframe section of the tracking workload: per Gaussian three
+    axis scales radius * exp(N(0, 0.35)) and a random rotation.  Times the
+    tracking iteration (render, Eq. 1 loss, pose backward through the
+    per-Gaussian chain, Adam; one CUDA graph) and the attribute backward
+    (colour, opacity, scale, quaternion), with CUDA events; per-kernel means
+    from eager iterations.  Returns a summary dict."""
+    import torch
+
+    from paper_2506_02741_gb300 import api
+    from paper_2506_02741_gb300 import synthetic as syn
+    from paper_2506_02741_gb300.tracking import PoseTracker
+    K, keys, section, targets, starts = make_workload(0, 1)
+    Kt = K.astuple()
+    sec = api.Section.from_rgbd(torch.from_numpy(section.depth).to(dev),
+                                torch.from_numpy(section.rgb).to(dev), Kt, np.stack(keys))
+    scale, quat = syn.random_ellipsoids(sec.radius.cpu().numpy(), 17)
+    esec = sec.with_ellipsoids(scale, quat)
+    d = torch.from_numpy(targets.depth[0]).to(dev)
+    rgb = torch.from_numpy(targets.rgb[0]).to(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(n):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / n
+
+    R = api.Renderer()
+    tr = PoseTracker(R, [esec], Kt, K.W, K.H, starts[0], device=dev)
+    tr.set_target(rgb, d)
+    R.render([esec], tr.pose, Kt, K.W, K.H, checked=True)
+    tr.capture()
+    track_ms = timed(tr.replay, iters)
+    n = esec.n
+    z = lambda *sh: torch.zeros(*sh, device=dev)
+    grads = [(z(n, 3), z(n), None, z(n, 3), z(n, 4))]
+    p0 = api.pose12(starts[0], dev)
+    R.render([esec], p0, Kt, K.W, K.H)
+    g_rgb = torch.full((3, K.H, K.W), 1e-6, device=dev)
+    g_d = torch.full((K.H, K.W), 1e-6, device=dev)
+    attr_ms = timed(lambda: R.backward(g_rgb, g_d, None, attr_grads=grads), 20)
+    fwd_ms = timed(lambda: R.render([esec], p0, Kt, K.W, K.H), 20)
+    R.set_timing(True)
+    R.timing(reset=True)
+    for _ in range(20):
+        tr.step()
+    torch.cuda.synchronize()
+    pk = R.timing(reset=True)
+    R.set_timing(False)
+    return {"workload": "ellipsoids_640x480_8kf_fp32", "gaussians": n,
+            "tracking_ms_per_iter": track_ms, "tracking_mpix_s": K.W * K.H / track_ms / 1e3,
+            "render_ms": fwd_ms, "attr_backward_ms": attr_ms,
+            "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
+
+
 def run_serving(dev, n_req: int = 300):
     """Serving workload: 4 resident sections (0.3 M - 8.3 M Gaussians),
     Poisson render/track requests (70% track) over 320x240 ... 1920x1080.
@@ -575,6 +637,7 @@ def main():
     if rank == 0 and not args.no_mapping:
         mapping = {prec: run_mapping(dev, prec, args.mapping_iters) for prec in ("f16", "f32")}
     head_frame = run_head_frame(dev) if rank == 0 and not args.no_mapping else None
+    ellipsoids = run_ellipsoids(dev) if rank == 0 and not args.no_mapping else None
 
     serving_line = None
     if rank == 0 and not args.no_serving:
@@ -608,6 +671,7 @@ def main():
             "cpu_baseline": cpu,
             "mapping": mapping,
             "head_frame": head_frame,
+            "ellipsoids": ellipsoids,
             "serving": serving_line,
             "clocks": clocks,
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items()},

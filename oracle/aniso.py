@@ -154,7 +154,14 @@ def render(sec: Section, scale, quat, pose, K, W, H, eps: float = EPS_LOWPASS,
     geo = _geometry(sec, scale, quat, pose, K, W, H, eps)
     n = sec.n
     ids = np.arange(n)
-    order = [i for i in np.lexsort((ids, geo["key"])) if geo["valid"][i]]
+    # Gaussians whose box (the one _box takes below) meets the image
+    with np.errstate(invalid="ignore"):
+        ex = np.sqrt(Q_MAX * 1.001 * geo["S2"][:, 0, 0])
+        ey = np.sqrt(Q_MAX * 1.001 * geo["S2"][:, 1, 1])
+        meets = ((np.ceil(geo["uc"] - ex) <= W - 1) & (np.floor(geo["uc"] + ex) >= 0) &
+                 (np.ceil(geo["vc"] - ey) <= H - 1) & (np.floor(geo["vc"] + ey) >= 0))
+    cand = geo["valid"] & meets
+    order = [i for i in np.lexsort((ids, geo["key"])) if cand[i]]
     P = W * H
     T = np.ones(P)
     done = np.zeros(P, bool)
@@ -216,15 +223,16 @@ def render(sec: Section, scale, quat, pose, K, W, H, eps: float = EPS_LOWPASS,
 
 
 def backward(sec: Section, scale, quat, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None,
-             eps: float = EPS_LOWPASS):
+             eps: float = EPS_LOWPASS, fwd=None):
     """Gradients of <g_rgb, rgb> + <g_depth, depth> + <g_sil, sil> with the
     included sets and their order held fixed.  Returns colour (n, 3),
     opacity, scale (n, 3), quat (n, 4), x (n, 3) = dL/dx of the centres in
     the target camera, twist (6,) = dL/d(rho, phi) for P Exp(xi), mat (12,) =
     dL/dR row-major then dL/dt, and abs_* the componentwise magnitude of
     each (the sum of the absolute values of the terms its formula adds,
-    propagated through the per-Gaussian chain with absolute Jacobians)."""
-    f = render(sec, scale, quat, pose, K, W, H, eps, keep=True)
+    propagated through the per-Gaussian chain with absolute Jacobians).
+    fwd: the result of render(..., keep=True) for the same inputs, reused."""
+    f = fwd if fwd is not None else render(sec, scale, quat, pose, K, W, H, eps, keep=True)
     geo = f["geo"]
     n = sec.n
     P = W * H
@@ -276,9 +284,32 @@ def backward(sec: Section, scale, quat, pose, K, W, H, g_rgb=None, g_depth=None,
 
 def _chain(geo, sec, scale, quat, d_col, a_col, d_op, a_op, d_Q, a_Q, d_uv, a_uv, d_z, a_z):
     """Per Gaussian: from dL/dQ, dL/d(u_c, v_c), dL/dz (direct) to the scale,
-    the quaternion, the centre and the target pose."""
-    ok = geo["valid"] & np.isfinite(geo["Q"]).all(axis=(1, 2)) & (geo["z"] > 0)
+    the quaternion, the centre and the target pose.  Only the Gaussians that
+    received a term are evaluated (the others contribute nothing)."""
     n = sec.n
+    live = np.flatnonzero((a_Q.reshape(n, -1).sum(1) + a_uv.sum(1) + a_z) > 0)
+    sub = lambda a: a[live]
+    d_Q, a_Q, d_uv, a_uv, d_z, a_z = map(sub, (d_Q, a_Q, d_uv, a_uv, d_z, a_z))
+    geo = {k: (v[live] if isinstance(v, np.ndarray) and v.shape[:1] == (n,) else v)
+           for k, v in geo.items()}
+    quat = np.asarray(quat, np.float64)[live]
+    out = _chain_rows(geo, quat, d_Q, a_Q, d_uv, a_uv, d_z, a_z)
+    full = {}
+    for k in ("scale", "quat", "x"):
+        for pre in ("", "abs_"):
+            v = out[pre + k]
+            f = np.zeros((n,) + v.shape[1:])
+            f[live] = v
+            full[pre + k] = f
+    full.update(colour=d_col, opacity=d_op, abs_colour=a_col, abs_opacity=a_op,
+                twist=out["twist"], mat=out["mat"], abs_twist=out["abs_twist"],
+                abs_mat=out["abs_mat"])
+    return full
+
+
+def _chain_rows(geo, quat, d_Q, a_Q, d_uv, a_uv, d_z, a_z):
+    ok = geo["valid"] & np.isfinite(geo["Q"]).all(axis=(1, 2)) & (geo["z"] > 0)
+    n = len(ok)
     Q, J, Sc, M, Rq, s = geo["Q"], geo["J"], geo["Sc"], geo["M"], geo["Rq"], geo["s"]
     x, z, fx, fy = geo["x"], geo["z"], geo["fx"], geo["fy"]
     A = np.abs
@@ -337,8 +368,7 @@ def _chain(geo, sec, scale, quat, d_col, a_col, d_op, a_op, d_Q, a_Q, d_uv, a_uv
     abs_twist = np.array([asg[0], asg[1], asg[2], aAm[2, 1] + aAm[1, 2], aAm[0, 2] + aAm[2, 0],
                           aAm[1, 0] + aAm[0, 1]])
     abs_mat = np.concatenate([(A(R) @ aAm).reshape(-1), A(R) @ asg])
-    return dict(colour=d_col, opacity=d_op, scale=d_scale, quat=d_quat, x=gx, twist=twist,
-                mat=mat, abs_colour=a_col, abs_opacity=a_op, abs_scale=a_scale,
+    return dict(scale=d_scale, quat=d_quat, x=gx, twist=twist, mat=mat, abs_scale=a_scale,
                 abs_quat=a_quat, abs_x=ax, abs_twist=abs_twist, abs_mat=abs_mat)
 
 

@@ -131,3 +131,50 @@ def test_tile_sort_every_size_class():
     clean = G.clean_mask(ref)
     assert clean.mean() > 0.8          # ~30 overlapping layers: more marginal decisions
     G.assert_forward_close(out, ref, clean)
+
+
+def test_fullsize_ellipsoid_crop_parity():
+    """The ellipsoid path at the full tracking size (640x480, 8 keyframes,
+    2,457,600 Gaussians, scales radius * exp(N(0, 0.35)), random rotations):
+    forward and gradients of a 96x80 crop against the anisotropic oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import aniso
+    dev = torch.device("cuda:0")
+    K = syn.VGA
+    osec, target = _section(K, 8, "f32")
+    q32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    scale, quat = (q32(a) for a in syn.random_ellipsoids(osec.radius, 17))
+    sec = G.to_device(osec).with_ellipsoids(torch.from_numpy(scale), torch.from_numpy(quat))
+    R = api.Renderer()
+    rgb, depth, sil = R.render([sec], api.pose12(target, dev), K.astuple(), K.W, K.H, checked=True)
+    cw, ch = 96, 80
+    x0, y0 = (K.W - cw) // 2 + 16, (K.H - ch) // 2 - 8
+    Kc = _crop(K, x0, y0)
+    ref = aniso.render(osec, scale, quat, target, Kc, cw, ch, keep=True)
+    clean = G.clean_mask(ref, tau_incl=1e-4)
+    assert clean.mean() > 0.9
+    sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
+    G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref, clean, tol=2e-5)
+    gm = G.clean_mask(ref, tau_incl=1e-4, tau_clamp=1e-4)
+    rng = np.random.default_rng(8)
+    gR = (rng.normal(0, 1, (3, ch, cw)) * gm).astype(np.float32)
+    gD = (rng.normal(0, 1, (ch, cw)) * gm).astype(np.float32)
+    want = aniso.backward(osec, scale, quat, target, Kc, cw, ch, gR, gD, fwd=ref)
+    full_gR = torch.zeros(3, K.H, K.W, device=dev)
+    full_gD = torch.zeros(K.H, K.W, device=dev)
+    full_gR[:, sl[0], sl[1]] = torch.from_numpy(gR).to(dev)
+    full_gD[sl] = torch.from_numpy(gD).to(dev)
+    n = osec.n
+    z = lambda *s: torch.zeros(*s, device=dev)
+    grads = [(z(n, 3), z(n), None, z(n, 3), z(n, 4))]
+    dtw, dmat = R.backward(full_gR, full_gD, None, attr_grads=grads, pose_grad=True)
+    torch.cuda.synchronize()
+    touched = np.flatnonzero(want["abs_opacity"] > 0)
+    assert touched.size > 1000
+    for k, name in ((0, "colour"), (1, "opacity"), (3, "scale"), (4, "quat")):
+        got = grads[0][k].cpu().numpy()
+        G.assert_grad_close(got[touched], want[name][touched], name=name,
+                            abs_ref=want["abs_" + name][touched])
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist", abs_ref=want["abs_twist"])
+    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", abs_ref=want["abs_mat"])
