@@ -68,3 +68,32 @@ def attr_adam_step(theta, m, v, t, d_colour, d_opacity, d_radius, lr, beta1=0.9,
     lr = np.asarray(lr, np.float64)[:, None]
     theta = theta - lr * (m / (1 - beta1 ** t)) / (np.sqrt(v) / np.sqrt(1 - beta2 ** t) + eps)
     return theta, m, v, t, theta[:3].T.copy(), sigmoid(theta[3]), np.exp(theta[4])
+
+
+def shape_grads(theta_s, d_scale, d_rot):
+    """Gradient with respect to theta_s (7, n) = (log s0, log s1, log s2,
+    q0, q1, q2, q3) of the ellipsoid shape from the gradients with respect
+    to the activated scale s = exp(log s) (n, 3) and the stored quaternion
+    (n, 4): the chain rule dL/dlog s = dL/ds s, the quaternion as stored."""
+    theta_s = np.asarray(theta_s, np.float64)
+    s = np.exp(theta_s[:3])
+    return np.concatenate([np.asarray(d_scale, np.float64).T * s,
+                           np.asarray(d_rot, np.float64).T]).astype(np.float64)
+
+
+def shape_adam_step(theta_s, m, v, t, d_scale, d_rot, lr_scale, lr_rot, beta1=0.9,
+                    beta2=0.999, eps=1e-8):
+    """One Adam step of the ellipsoid shape (the anisotropic variant of the
+    attribute ablation, Sec. 4) in the parametrisation of shape_grads, with
+    one rate for the three log scales and one for the four quaternion
+    components (the 3D Gaussian splatting convention; the quaternion is
+    normalised where it is used, not here).  Returns (theta_s, m, v, t,
+    scale (n, 3), rot (n, 4))."""
+    g = shape_grads(theta_s, d_scale, d_rot)
+    t = t + 1.0
+    m = beta1 * np.asarray(m, np.float64) + (1 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1 - beta2) * g * g
+    lr = np.array([lr_scale] * 3 + [lr_rot] * 4, np.float64)[:, None]
+    theta_s = np.asarray(theta_s, np.float64) - lr * (m / (1 - beta1 ** t)) / (
+        np.sqrt(v) / np.sqrt(1 - beta2 ** t) + eps)
+    return theta_s, m, v, t, np.exp(theta_s[:3]).T.copy(), theta_s[3:].T.copy()

@@ -66,3 +66,39 @@ def test_attr_adam_first_step_and_chain_rule():
     np.testing.assert_allclose(op_, 1 / (1 + np.exp(-th[3])), rtol=1e-15)
     np.testing.assert_allclose(rad, np.exp(th[4]), rtol=1e-15)
     np.testing.assert_array_equal(col, th[:3].T)
+
+
+def test_shape_gradient_matches_finite_differences():
+    """shape_grads is the gradient of L(theta_s) = <a, exp(log s)> + <b, q>
+    in theta_s (central differences of that L, whose gradient with respect
+    to the activated values is (a, b))."""
+    rng = np.random.default_rng(3)
+    n = 5
+    th = np.concatenate([np.log(rng.uniform(0.01, 0.1, (3, n))), rng.normal(size=(4, n))])
+    a, b = rng.normal(size=(n, 3)), rng.normal(size=(n, 4))
+    L = lambda t: (a * np.exp(t[:3]).T).sum() + (b * t[3:].T).sum()
+    g = op.shape_grads(th, a, b)
+    for i in range(7):
+        for j in range(n):
+            e = np.zeros_like(th)
+            e[i, j] = 1e-6
+            fd = (L(th + e) - L(th - e)) / 2e-6
+            assert abs(fd - g[i, j]) <= 1e-8 * (1 + abs(fd))
+
+
+def test_shape_adam_first_step_is_sign_step():
+    """At t = 1 every parameter moves by its rate against the sign of its
+    gradient (log scales by lr_scale, quaternion components by lr_rot); the
+    outputs are exp of the log scales and the quaternion as stored."""
+    rng = np.random.default_rng(4)
+    n = 6
+    th = np.concatenate([np.log(rng.uniform(0.01, 0.1, (3, n))), rng.normal(size=(4, n))])
+    ds, dq = rng.normal(size=(n, 3)), rng.normal(size=(n, 4))
+    out, m, v, t, s, q = op.shape_adam_step(th, np.zeros((7, n)), np.zeros((7, n)), 0.0, ds, dq,
+                                            5e-3, 1e-3, eps=0.0)
+    assert t == 1.0
+    step = np.concatenate([np.full((3, n), 5e-3), np.full((4, n), 1e-3)])
+    g = np.concatenate([ds.T, dq.T])          # signs of dL/dlog s = dL/ds s (s > 0)
+    np.testing.assert_allclose(out, th - step * np.sign(g), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(s, np.exp(out[:3]).T, rtol=1e-15)
+    np.testing.assert_array_equal(q, out[3:].T)
