@@ -373,6 +373,26 @@ vt_status vt_attr_adam(vt_ctx *ctx, int64_t n, float *theta, float *m, float *v,
                        void *colour, void *opacity, void *radius, vt_adam_params p,
                        vt_stream stream);
 
+/* Ellipsoid shape step of the mapping optimiser (the anisotropic variant of
+ * the attribute ablation, Sec. 4): Adam on theta = (log s0, log s1, log s2,
+ * q0, q1, q2, q3) with rate lr_scale for the log scales and lr_rot for the
+ * quaternion components (the 3D Gaussian splatting convention; the
+ * quaternion is stored unnormalised and normalised where it is used):
+ *   g = (dL/ds s, dL/dq),  m, v and the bias corrections as vt_attr_adam,
+ * then scale = exp(log s) (n x 3) and rot = q (n x 4) are written in
+ * precision prec and d_scale (n x 3), d_rot (n x 4) (device float32, as
+ * accumulated by vt_render_backward) are zeroed.  theta, m, v: device
+ * float32, 7 planes of n; step: device, 3 doubles (its own counter,
+ * incremented here).  ctx may be NULL; when given it only records the
+ * launches. */
+typedef struct {
+    float lr_scale, lr_rot, beta1, beta2, eps;
+} vt_shape_adam_params;
+
+vt_status vt_shape_adam(vt_ctx *ctx, int64_t n, float *theta, float *m, float *v, double *step,
+                        float *d_scale, float *d_rot, vt_precision prec, void *scale, void *rot,
+                        vt_shape_adam_params p, vt_stream stream);
+
 /* Per-kernel timing of the context's launches with CUDA events on the
  * launching stream (enable != 0).  vt_ctx_timing synchronises the stream
  * and writes, for up to n_max kernels, their names (static strings), the

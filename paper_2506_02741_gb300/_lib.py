@@ -54,6 +54,11 @@ class AdamParamsC(C.Structure):
                 ("eps", C.c_float)]
 
 
+class ShapeAdamParamsC(C.Structure):
+    _fields_ = [("lr_scale", C.c_float), ("lr_rot", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 MAX_VIS_VIEWS = 8
 
 
@@ -93,6 +98,8 @@ def _declare(L):
                                    C.c_double, C.c_double, _P]),
         "vt_attr_adam": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P,
                                    _P, AdamParamsC, _P]),
+        "vt_shape_adam": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P,
+                                    ShapeAdamParamsC, _P]),
         "vt_section_complement": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, Intrinsics,
                                             C.c_float, C.c_int32, C.c_int, _P, _P, _P, _P,
                                             C.c_int64, _P, _P]),
@@ -127,7 +134,7 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists",
            "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam",
            "vt_attr_adam", "vt_section_complement", "vt_ssim",
-           "vt_visibility_counts"]
+           "vt_visibility_counts", "vt_shape_adam"]
 
 
 def lib_path() -> str:

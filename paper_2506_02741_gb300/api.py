@@ -310,6 +310,31 @@ def attr_adam(section, theta: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
                                  _ptr(section.radius), p, _stream(stream)), "vt_attr_adam")
 
 
+def shape_adam(section, theta: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+               step: torch.Tensor, d_scale: torch.Tensor, d_rot: torch.Tensor,
+               lr_scale: float = 0.005, lr_rot: float = 0.001, beta1: float = 0.9,
+               beta2: float = 0.999, eps: float = 1e-8, renderer=None, stream=None):
+    """One Adam step on an ellipsoid section's shape in the parametrisation
+    theta = (log s0, log s1, log s2, q0, q1, q2, q3) ((7, n) float32; m, v
+    alike; step (3,) float64 zero-initialised, its own counter); the
+    section's scale / rot storage is overwritten (exp of the log scales, the
+    quaternion as stored) and d_scale (n, 3), d_rot (n, 4) are zeroed."""
+    n = section.n
+    if section.scale is None:
+        raise ValueError("shape_adam needs an ellipsoid section")
+    for name, t in (("theta", theta), ("m", m), ("v", v)):
+        _cuda(t, torch.float32, name, (7, n))
+    _cuda(step, torch.float64, "step", (3,))
+    _cuda(d_scale, torch.float32, "d_scale", (n, 3))
+    _cuda(d_rot, torch.float32, "d_rot", (n, 4))
+    p = L.ShapeAdamParamsC(float(lr_scale), float(lr_rot), float(beta1), float(beta2),
+                           float(eps))
+    ctx = renderer._ctx if renderer is not None else None
+    L.check(L.lib().vt_shape_adam(ctx, n, _ptr(theta), _ptr(m), _ptr(v), _ptr(step),
+                                  _ptr(d_scale), _ptr(d_rot), section.prec, _ptr(section.scale),
+                                  _ptr(section.rot), p, _stream(stream)), "vt_shape_adam")
+
+
 # Contexts released while a CUDA graph was being captured on the current
 # stream: destroying one then would synchronise and free device memory in the
 # middle of the capture, so they wait for the next context operation outside

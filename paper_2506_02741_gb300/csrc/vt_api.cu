@@ -61,7 +61,7 @@ enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
     K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_SSIM_FWD, K_SSIM_BWD, K_SSIM_SUM,
-    K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_NUM
+    K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_SHAPE_ADAM, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -73,7 +73,7 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "k_ssim_fwd",      "k_ssim_bwd",       "k_ssim_sum",
                                    "k_view_grads",    "k_preprocess_aniso",
                                    "k_composite_fwd_aniso", "k_composite_bwd_list_aniso",
-                                   "k_composite_bwd_aniso", "k_aniso_chain"};
+                                   "k_composite_bwd_aniso", "k_aniso_chain", "k_shape_adam"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -1018,6 +1018,48 @@ vt_status vt_attr_adam(vt_ctx *c, int64_t n, float *theta, float *m, float *v, d
         }
     }
     VT_CUDA(cudaGetLastError(), "vt_attr_adam launch");
+    return VT_OK;
+}
+
+vt_status vt_shape_adam(vt_ctx *c, int64_t n, float *theta, float *m, float *v, double *step,
+                        float *d_scale, float *d_rot, vt_precision prec, void *scale, void *rot,
+                        vt_shape_adam_params p, vt_stream stream) {
+    if (n < 0) return fail(VT_ERR_INVALID_ARG, "vt_shape_adam: n < 0");
+    if (prec != VT_F32 && prec != VT_F16)
+        return fail(VT_ERR_INVALID_ARG, "vt_shape_adam: unknown precision %d", (int)prec);
+    if (!step) return fail(VT_ERR_INVALID_ARG, "vt_shape_adam: NULL step");
+    if (n > 0 && (!theta || !m || !v || !d_scale || !d_rot || !scale || !rot))
+        return fail(VT_ERR_INVALID_ARG, "vt_shape_adam: NULL array");
+    if (!(std::isfinite(p.lr_scale) && p.lr_scale >= 0.f && std::isfinite(p.lr_rot) &&
+          p.lr_rot >= 0.f))
+        return fail(VT_ERR_INVALID_ARG, "vt_shape_adam: learning rates must be finite, >= 0");
+    if (!(p.beta1 >= 0.f && p.beta1 < 1.f && p.beta2 >= 0.f && p.beta2 < 1.f && p.eps >= 0.f &&
+          std::isfinite(p.eps)))
+        return fail(VT_ERR_INVALID_ARG, "vt_shape_adam: need 0 <= beta < 1 and finite eps >= 0");
+    const ShapeAdamParams prm{p.lr_scale, p.lr_rot, p.beta1, p.beta2, p.eps};
+    auto count = [&]() {
+        k_adam_step_count<<<1, 32, 0, stream>>>(step, (double)p.beta1, (double)p.beta2);
+    };
+    if (c) {
+        LaunchScope ls(c, K_ADAM_COUNT, stream);
+        count();
+    } else {
+        count();
+    }
+    if (n > 0) {
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        auto upd = [&]() {
+            k_shape_adam<<<nb, 256, 0, stream>>>(n, theta, m, v, step, d_scale, d_rot, (int)prec,
+                                                 scale, rot, prm);
+        };
+        if (c) {
+            LaunchScope ls(c, K_SHAPE_ADAM, stream);
+            upd();
+        } else {
+            upd();
+        }
+    }
+    VT_CUDA(cudaGetLastError(), "vt_shape_adam launch");
     return VT_OK;
 }
 

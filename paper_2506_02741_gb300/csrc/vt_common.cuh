@@ -381,6 +381,12 @@ struct AttrAdamParams {
     float lr[5];
     float beta1, beta2, eps;
 };
+struct ShapeAdamParams {
+    float lr_scale, lr_rot, beta1, beta2, eps;
+};
+__global__ void k_shape_adam(int64_t n, float *theta, float *m, float *v, const double *step,
+                             float *d_scale, float *d_rot, int prec, void *scale, void *rot,
+                             ShapeAdamParams prm);
 __global__ void k_adam_step_count(double *step, double beta1, double beta2);
 __global__ void k_attr_adam(int64_t n, float *theta, float *m, float *v, const double *step,
                             float *d_colour, float *d_opacity, float *d_radius, int prec,

@@ -149,4 +149,56 @@ __global__ void __launch_bounds__(256) k_attr_adam(int64_t n, float *__restrict_
     st_any(radius, prec, i, expf(th[4]));
 }
 
+// Ellipsoid shape (anisotropic variant), one thread per Gaussian: Adam on
+// (log s0..2, q0..3) with the chain rule dL/dlog s = dL/ds s; the scale
+// exp(log s) and the quaternion as stored are written back in the
+// section's precision and the gradients zeroed.  Loads first, as above.
+__global__ void __launch_bounds__(256) k_shape_adam(int64_t n, float *__restrict__ theta,
+                                                    float *__restrict__ m, float *__restrict__ v,
+                                                    const double *__restrict__ step,
+                                                    float *__restrict__ d_scale,
+                                                    float *__restrict__ d_rot, int prec,
+                                                    void *__restrict__ scale,
+                                                    void *__restrict__ rot, ShapeAdamParams prm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float th[7], g[7], mk[7], vk[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        th[k] = theta[k * n + i];
+        mk[k] = m[k * n + i];
+        vk[k] = v[k * n + i];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = d_scale[3 * i + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g[3 + k] = d_rot[4 * i + k];
+    const float s1 = (float)step[1], s2 = (float)step[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] *= expf(th[k]);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const float lr = k < 3 ? prm.lr_scale : prm.lr_rot;
+        mk[k] = prm.beta1 * mk[k] + (1.f - prm.beta1) * g[k];
+        vk[k] = prm.beta2 * vk[k] + (1.f - prm.beta2) * g[k] * g[k];
+        th[k] -= lr * s1 * mk[k] / (sqrtf(vk[k]) * s2 + prm.eps);
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        theta[k * n + i] = th[k];
+        m[k * n + i] = mk[k];
+        v[k * n + i] = vk[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d_scale[3 * i + k] = 0.f;
+        st_any(scale, prec, 3 * i + k, expf(th[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        d_rot[4 * i + k] = 0.f;
+        st_any(rot, prec, 4 * i + k, th[3 + k]);
+    }
+}
+
 }  // namespace vt

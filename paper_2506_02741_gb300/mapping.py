@@ -9,7 +9,10 @@ ssim=False leaves it out).  Every step of an iteration runs in the vtsplat
 kernels: render, the masked L1 loss and its image gradient (vt_masked_l1),
 the SSIM term accumulated into the same gradient (vt_ssim), the attribute
 backward and one fused Adam step (vt_attr_adam; learning rates of the
-supplementary: colour 0.0025, radius 0.005, opacity 0.05).
+supplementary: colour 0.0025, radius 0.005, opacity 0.05).  Ellipsoid
+sections (the anisotropic variant of the attribute ablation) also learn
+their scales and rotations (vt_shape_adam; rates 0.005 for the log scales
+and 0.001 for the quaternion, the 3D Gaussian splatting defaults).
 
 The learning rates apply, as in the 3D Gaussian splatting family the paper
 builds on, to logit(opacity) and log(radius) (a reading: the paper gives the
@@ -30,7 +33,8 @@ from . import api
 class SectionMapper:
     def __init__(self, renderer: api.Renderer, section: api.Section, frames_rgb: torch.Tensor,
                  lr_colour: float = 0.0025, lr_opacity: float = 0.05, lr_radius: float = 0.005,
-                 rho: float = 0.8, sigma: float = 1.0, tau: float = 0.2, ssim: bool = True):
+                 rho: float = 0.8, sigma: float = 1.0, tau: float = 0.2, ssim: bool = True,
+                 lr_scale: float = 0.005, lr_rot: float = 0.001):
         self.R = renderer
         self.sec = section
         self.rgb_obs = frames_rgb                      # (V, 3, H, W) float32, device
@@ -57,6 +61,16 @@ class SectionMapper:
         self.loss = self.losses[:1]
         self.g_rgb = torch.zeros(3, self.H, self.W, device=dev)
         self.g_depth = torch.zeros(self.H, self.W, device=dev)
+        self.shape = None
+        if section.ellipsoids:
+            self.lr_shape = (float(lr_scale), float(lr_rot))
+            self.shape = torch.cat([torch.log(section.scale.detach().float()).t(),
+                                    section.rot.detach().float().t()]).contiguous()
+            self.shape_m = torch.zeros(7, n, device=dev)
+            self.shape_v = torch.zeros(7, n, device=dev)
+            self.shape_step = torch.zeros(3, dtype=torch.float64, device=dev)
+            self.d_scale = torch.zeros(n, 3, device=dev)
+            self.d_rot = torch.zeros(n, 4, device=dev)
 
     def step(self, view: int):
         """One mapping iteration rendering from section view ``view``."""
@@ -69,10 +83,16 @@ class SectionMapper:
             self.R.ssim(self.rgb, self.rgb_obs[view], self.tau, d_rgb=self.g_rgb,
                         loss=self.losses[1:2])
         # the gradients were zeroed by the previous Adam step (and at construction)
-        self.R.backward(self.g_rgb, self.g_depth, None,
-                        attr_grads=[(self.d_colour, self.d_opacity, self.d_radius)])
+        if self.shape is None:
+            grads = (self.d_colour, self.d_opacity, self.d_radius)
+        else:
+            grads = (self.d_colour, self.d_opacity, None, self.d_scale, self.d_rot)
+        self.R.backward(self.g_rgb, self.g_depth, None, attr_grads=[grads])
         api.attr_adam(self.sec, self.theta, self.m, self.v, self.step_state, self.d_colour,
                       self.d_opacity, self.d_radius, self.lr, renderer=self.R)
+        if self.shape is not None:
+            api.shape_adam(self.sec, self.shape, self.shape_m, self.shape_v, self.shape_step,
+                           self.d_scale, self.d_rot, *self.lr_shape, renderer=self.R)
         return self.losses.sum() if self.use_ssim else self.losses[0]
 
 

@@ -152,3 +152,66 @@ def test_ellipsoid_argument_errors(dev):
     with pytest.raises(ValueError):
         api.Section(ell.poses, ell.depth, ell.K, ell.src, ell.colour, ell.opacity, ell.radius,
                     scale=ell.scale).validate()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_shape_adam_matches_reference(dev, prec):
+    """Three Adam steps on the ellipsoid shape against the float64 reference
+    (FP32 arithmetic: 1e-5 relative on the parameters); storage written in
+    the section's precision; gradients zeroed; its own step counter."""
+    from oracle import optim as op
+    rng = np.random.default_rng(6)
+    n = 777
+    dt = torch.float16 if prec == "f16" else torch.float32
+    sc = rng.uniform(0.002, 0.02, (n, 3)).astype(np.float32)
+    qt = rng.normal(size=(n, 4)).astype(np.float32)
+    ones = torch.ones(n, device=dev, dtype=dt)
+    sec = api.Section(poses=torch.zeros(1, 12, dtype=torch.float64, device=dev),
+                      depth=torch.ones(1, 1, n, device=dev), K=(1.0, 1.0, 0.0, 0.0),
+                      src=torch.arange(n, dtype=torch.int32, device=dev),
+                      colour=torch.zeros(n, 3, device=dev, dtype=dt), opacity=ones * 0.5,
+                      radius=ones * 0.01, scale=torch.from_numpy(sc).to(dev, dt),
+                      rot=torch.from_numpy(qt).to(dev, dt))
+    th = np.ascontiguousarray(np.concatenate([np.log(sc).T, qt.T]), np.float32)
+    th_d = torch.from_numpy(th).to(dev)
+    m_d, v_d = torch.zeros(7, n, device=dev), torch.zeros(7, n, device=dev)
+    st = torch.zeros(3, dtype=torch.float64, device=dev)
+    th64, m, v, t = th.astype(np.float64), np.zeros((7, n)), np.zeros((7, n)), 0.0
+    for _ in range(3):
+        ds = rng.normal(0, 1e-2, (n, 3)).astype(np.float32)
+        dq = rng.normal(0, 1e-3, (n, 4)).astype(np.float32)
+        gds, gdq = torch.from_numpy(ds).to(dev), torch.from_numpy(dq).to(dev)
+        api.shape_adam(sec, th_d, m_d, v_d, st, gds, gdq, 0.005, 0.001)
+        th64, m, v, t, s_ref, q_ref = op.shape_adam_step(th64, m, v, t, ds, dq, 0.005, 0.001)
+        torch.cuda.synchronize()
+        assert not gds.any() and not gdq.any()
+        np.testing.assert_allclose(th_d.cpu().numpy(), th64, rtol=1e-5, atol=1e-6)
+        # m sums terms of both signs: its FP32 rounding is relative to the terms
+        np.testing.assert_allclose(m_d.cpu().numpy(), m, rtol=1e-4, atol=1e-6 * np.abs(m).max())
+        tol = 1e-3 if prec == "f16" else 1e-5
+        np.testing.assert_allclose(sec.scale.float().cpu().numpy(), s_ref, rtol=tol)
+        np.testing.assert_allclose(sec.rot.float().cpu().numpy(), q_ref, rtol=tol, atol=1e-6)
+        assert st[0].item() == t
+
+
+def test_ellipsoid_mapper_reduces_loss(dev):
+    """Mapping iterations on an ellipsoid section (render, Eq. 2 L1 + SSIM,
+    attribute backward, colour / opacity and shape Adam steps) lower the loss
+    and move the scales and rotations."""
+    from paper_2506_02741_gb300.mapping import SectionMapper
+    K = syn.scaled_intrinsics(160, 120)
+    room = syn.make_room(syn.SCENE_SEED)
+    path = syn.trajectory(15)
+    keys = [path[i] for i in (0, 5, 10)]
+    fr = syn.render_frames(room, K, keys)
+    depth = torch.from_numpy(fr.depth).to(dev)
+    rgb = torch.from_numpy(fr.rgb).to(dev)
+    sec = api.Section.from_rgbd(depth, rgb, K.astuple(), np.stack(keys))
+    scale, quat = syn.random_ellipsoids(sec.radius.cpu().numpy(), 2, spread=0.6)
+    sec = sec.with_ellipsoids(scale, quat)
+    s0, q0 = sec.scale.clone(), sec.rot.clone()
+    R = api.Renderer()
+    mp = SectionMapper(R, sec, rgb)
+    losses = [float(mp.step(i % 3).item()) for i in range(30)]
+    assert losses[-1] < 0.8 * losses[0], losses
+    assert not torch.equal(s0, sec.scale) and not torch.equal(q0, sec.rot)
