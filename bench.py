@@ -315,9 +315,20 @@ def run_ellipsoids(dev, iters: int = 50):
     torch.cuda.synchronize()
     pk = R.timing(reset=True)
     R.set_timing(False)
+    # mapping iterations (Eq. 2 L1 + SSIM, attribute backward, colour /
+    # opacity and shape Adam) on a copy of the section
+    from paper_2506_02741_gb300.mapping import SectionMapper, random_views
+    frames = torch.from_numpy(section.rgb).to(dev)
+    msec = api.Section.from_rgbd(torch.from_numpy(section.depth).to(dev), frames, Kt,
+                                 np.stack(keys)).with_ellipsoids(scale, quat)
+    mp = SectionMapper(api.Renderer(), msec, frames)
+    views = random_views(msec.n_views, 23, seed=1)
+    it = iter(views)
+    map_ms = timed(lambda: mp.step(next(it)), 20)
     return {"workload": "ellipsoids_640x480_8kf_fp32", "gaussians": n,
             "tracking_ms_per_iter": track_ms, "tracking_mpix_s": K.W * K.H / track_ms / 1e3,
             "render_ms": fwd_ms, "attr_backward_ms": attr_ms,
+            "mapping_ms_per_step": map_ms, "mapping_mpix_s": K.W * K.H / map_ms / 1e3,
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
 
 

@@ -128,19 +128,21 @@ __device__ __forceinline__ void fwd_body(
     const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
     uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
     uint32_t *blk_ovf, const Status *st) {
-    __shared__ float4 s_f[kWarps][32], s_k[kWarps][32], s_c[kWarps][32];
-    __shared__ uint32_t s_gid[kWarps][32], s_idx[kWarps][32];
+    // two staging halves of 32 entries per warp (see the walk below)
+    __shared__ float4 s_f[kWarps][64], s_k[kWarps][64], s_c[kWarps][64];
+    __shared__ uint32_t s_gid[kWarps][64], s_idx[kWarps][64];
     __shared__ uint32_t s_q[kWarps][kQueue];
-    __shared__ float s_b[Aniso ? kWarps : 1][32];   // b' of the ellipse records
+    __shared__ float s_b[Aniso ? kWarps : 1][64];   // b' of the ellipse records
     if (st->flags) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lx = lane & 7, ly = lane >> 3;
     const float lxf = (float)lx, lyf = (float)ly;
-    float4 (&fs)[32] = s_f[warp];
-    float4 (&ks)[32] = s_k[warp];
-    float4 (&cs)[32] = s_c[warp];
-    uint32_t (&ids)[32] = s_gid[warp];
-    uint32_t (&lidx)[32] = s_idx[warp];
+    float4 (&fs)[64] = s_f[warp];
+    float4 (&ks)[64] = s_k[warp];
+    float4 (&cs)[64] = s_c[warp];
+    uint32_t (&ids)[64] = s_gid[warp];
+    uint32_t (&lidx)[64] = s_idx[warp];
+    float (&bs)[64] = s_b[Aniso ? warp : 0];
     uint32_t (&q)[kQueue] = s_q[warp];
     const size_t HW = (size_t)cam.W * cam.H;
 
@@ -210,6 +212,52 @@ __device__ __forceinline__ void fwd_body(
         take(idx_nn, cnt_nn);
         if (lane < cnt_nn) gid_nn = sorted[start + idx_nn];
     }
+    // Each lane walks its own candidates: lanes work on different Gaussians
+    // at once.  The walk of a batch is lagged by one: while any lane still
+    // has candidates of the previous batch (cand_old, half ho), every lane
+    // takes its next candidate from there, or, once its own are done, from
+    // the current batch (cand_new, half hn), so lanes with few candidates
+    // run ahead instead of idling until the busiest pixel of the batch is
+    // through.  Per lane the order stays the list order.
+    uint32_t cand_old = 0u;
+    int ho = 1;
+    auto walk = [&](uint32_t &cand_new, int hn) {
+        while (__any_sync(kFullMask, cand_old != 0u)) {
+            const bool fo = cand_old != 0u;
+            const uint32_t src = fo ? cand_old : cand_new;
+            if (!src) continue;
+            const int j = (fo ? ho : hn) * 32 + __ffs(src) - 1;
+            if (fo)
+                cand_old &= cand_old - 1u;
+            else
+                cand_new &= cand_new - 1u;
+            const float4 f = fs[j], k = ks[j];
+            const float du = __fsub_rn(__fadd_rn(f.x, lxf), f.z);
+            const float dv = __fsub_rn(__fadd_rn(f.y, lyf), f.w);
+            const float t = Aniso ? pair_t_aniso(du, dv, k.x, bs[j], k.y)
+                                  : pair_t(du, dv, k.x, k.y);
+            if (!(t >= k.z)) continue;
+            const float al = fminf(__fmul_rn(k.w, exp2_approx(t)), kAlphaClamp);
+            const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
+            if (Tn < kTMin) {
+                done = true;
+                cand_old = 0u;
+                cand_new = 0u;
+                continue;
+            }
+            const float w = __fmul_rn(al, T);
+            const float4 c = cs[j];
+            c0 = __fmaf_rn(w, c.x, c0);
+            c1 = __fmaf_rn(w, c.y, c1);
+            c2 = __fmaf_rn(w, c.z, c2);
+            dd = __fmaf_rn(w, c.w, dd);
+            ss = __fadd_rn(ss, w);
+            if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
+            T = Tn;
+            last = lidx[j] + 1u;
+            ++nadd;
+        }
+    };
     for (;;) {
         const int cnt = cnt_n;
         if (cnt == 0 || __all_sync(kFullMask, done)) break;
@@ -234,50 +282,25 @@ __device__ __forceinline__ void fwd_body(
                                           lymaxi)
                        : pixel_mask(ku - g0.y, kv - g0.w, g1.x, g1.y, tmin, lxmaxi, lymaxi);
         if (!__any_sync(kFullMask, pm != 0u)) continue;
+        // stage the batch in the half that the previous batch does not hold
+        const int hn = ho ^ 1, sl = hn * 32 + lane;
         __syncwarp();
-        fs[lane] = make_float4(ku, kv, g0.y, g0.w);
-        ks[lane] = make_float4(g1.x, Aniso ? g1.z : g1.y, tmin, g1.w);
-        if (Aniso) s_b[Aniso ? warp : 0][lane] = g1.y;
-        cs[lane] = a;
-        ids[lane] = gid;
-        lidx[lane] = idx;
+        fs[sl] = make_float4(ku, kv, g0.y, g0.w);
+        ks[sl] = make_float4(g1.x, Aniso ? g1.z : g1.y, tmin, g1.w);
+        if (Aniso) bs[sl] = g1.y;
+        cs[sl] = a;
+        ids[sl] = gid;
+        lidx[sl] = idx;
         // this pixel's candidates of the batch, in list order (bit j = entry j)
-        uint32_t cand = transpose32(pm, lane);
+        uint32_t cand_new = transpose32(pm, lane);
         __syncwarp();
-        if (done) cand = 0u;
-        // each lane walks its own candidates: lanes work on different
-        // Gaussians at once, and the warp takes as many steps as the busiest
-        // pixel has candidates
-        while (__any_sync(kFullMask, cand != 0u)) {
-            if (!cand) continue;
-            const int j = __ffs(cand) - 1;
-            cand &= cand - 1u;
-            const float4 f = fs[j], k = ks[j];
-            const float du = __fsub_rn(__fadd_rn(f.x, lxf), f.z);
-            const float dv = __fsub_rn(__fadd_rn(f.y, lyf), f.w);
-            const float t = Aniso ? pair_t_aniso(du, dv, k.x, s_b[Aniso ? warp : 0][j], k.y)
-                                  : pair_t(du, dv, k.x, k.y);
-            if (!(t >= k.z)) continue;
-            const float al = fminf(__fmul_rn(k.w, exp2_approx(t)), kAlphaClamp);
-            const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
-            if (Tn < kTMin) {
-                done = true;
-                cand = 0u;
-                continue;
-            }
-            const float w = __fmul_rn(al, T);
-            const float4 c = cs[j];
-            c0 = __fmaf_rn(w, c.x, c0);
-            c1 = __fmaf_rn(w, c.y, c1);
-            c2 = __fmaf_rn(w, c.z, c2);
-            dd = __fmaf_rn(w, c.w, dd);
-            ss = __fadd_rn(ss, w);
-            if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
-            T = Tn;
-            last = lidx[j] + 1u;
-            ++nadd;
-        }
+        if (done) cand_new = 0u;
+        walk(cand_new, hn);
+        cand_old = cand_new;
+        ho = hn;
     }
+    uint32_t none = 0u;
+    walk(none, ho ^ 1);   // the last batch's remaining candidates
     if (inside) {
         if (rgb) {
             rgb[p] = c0;
