@@ -413,7 +413,11 @@ __device__ __forceinline__ BwdStep bwd_step(BwdPixel &P, const float4 &a, float 
     BwdStep S;
     const float al = fminf(ah, kAlphaClamp);
     S.om = 1.f - al;
-    S.Ti = Ti_fwd >= 0.f ? Ti_fwd : P.T / S.om;
+    // (the division only where no forward transmittance was recorded)
+    if (Ti_fwd >= 0.f)
+        S.Ti = Ti_fwd;
+    else
+        S.Ti = P.T / S.om;
     S.w = al * S.Ti;
     const float z = a.w;
     if (!P.have_ref) {
@@ -428,7 +432,7 @@ __device__ __forceinline__ BwdStep bwd_step(BwdPixel &P, const float4 &a, float 
                       P.gC1 * (a.y * P.Tfin + e1 * P.Sb - P.A1) +
                       P.gC2 * (a.z * P.Tfin + e2 * P.Sb - P.A2) +
                       P.gD * (z * P.Tfin + ez * P.Sb - P.Bd) + P.gS * P.Tfin;
-    S.dal = num / S.om;
+    S.dal = __fdividef(num, S.om);   // om in [0.01, 1]: within 2 ulp
     return S;
 }
 
