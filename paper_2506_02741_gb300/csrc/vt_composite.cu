@@ -221,41 +221,63 @@ __device__ __forceinline__ void fwd_body(
     // through.  Per lane the order stays the list order.
     uint32_t cand_old = 0u;
     int ho = 1;
+    // next candidate of this lane in walk order (previous batch first)
+    auto pick = [&](uint32_t &cand_new, int hn, int &j) {
+        const bool fo = cand_old != 0u;
+        const uint32_t src = fo ? cand_old : cand_new;
+        if (!src) return false;
+        j = (fo ? ho : hn) * 32 + __ffs(src) - 1;
+        if (fo)
+            cand_old &= cand_old - 1u;
+        else
+            cand_new &= cand_new - 1u;
+        return true;
+    };
+    auto exponent = [&](int j, float4 &k) {
+        const float4 f = fs[j];
+        k = ks[j];
+        const float du = __fsub_rn(__fadd_rn(f.x, lxf), f.z);
+        const float dv = __fsub_rn(__fadd_rn(f.y, lyf), f.w);
+        return Aniso ? pair_t_aniso(du, dv, k.x, bs[j], k.y) : pair_t(du, dv, k.x, k.y);
+    };
+    // composite candidate j (exponent t >= t_min, G = 2^t); false once the
+    // pixel terminates
+    auto add = [&](int j, float G, const float4 &k, uint32_t &cand_new) {
+        const float al = fminf(__fmul_rn(k.w, G), kAlphaClamp);
+        const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
+        if (Tn < kTMin) {
+            done = true;
+            cand_old = 0u;
+            cand_new = 0u;
+            return false;
+        }
+        const float w = __fmul_rn(al, T);
+        const float4 c = cs[j];
+        c0 = __fmaf_rn(w, c.x, c0);
+        c1 = __fmaf_rn(w, c.y, c1);
+        c2 = __fmaf_rn(w, c.z, c2);
+        dd = __fmaf_rn(w, c.w, dd);
+        ss = __fadd_rn(ss, w);
+        if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
+        T = Tn;
+        last = lidx[j] + 1u;
+        ++nadd;
+        return true;
+    };
+    // two candidates per step: their exponents and 2^t are independent and
+    // overlap; the second is composited after the first, unless the first
+    // terminated the pixel
     auto walk = [&](uint32_t &cand_new, int hn) {
         while (__any_sync(kFullMask, cand_old != 0u)) {
-            const bool fo = cand_old != 0u;
-            const uint32_t src = fo ? cand_old : cand_new;
-            if (!src) continue;
-            const int j = (fo ? ho : hn) * 32 + __ffs(src) - 1;
-            if (fo)
-                cand_old &= cand_old - 1u;
-            else
-                cand_new &= cand_new - 1u;
-            const float4 f = fs[j], k = ks[j];
-            const float du = __fsub_rn(__fadd_rn(f.x, lxf), f.z);
-            const float dv = __fsub_rn(__fadd_rn(f.y, lyf), f.w);
-            const float t = Aniso ? pair_t_aniso(du, dv, k.x, bs[j], k.y)
-                                  : pair_t(du, dv, k.x, k.y);
-            if (!(t >= k.z)) continue;
-            const float al = fminf(__fmul_rn(k.w, exp2_approx(t)), kAlphaClamp);
-            const float Tn = __fmaf_rn(-al, T, T);   // T (1 - alpha), one rounding
-            if (Tn < kTMin) {
-                done = true;
-                cand_old = 0u;
-                cand_new = 0u;
-                continue;
-            }
-            const float w = __fmul_rn(al, T);
-            const float4 c = cs[j];
-            c0 = __fmaf_rn(w, c.x, c0);
-            c1 = __fmaf_rn(w, c.y, c1);
-            c2 = __fmaf_rn(w, c.z, c2);
-            dd = __fmaf_rn(w, c.w, dd);
-            ss = __fadd_rn(ss, w);
-            if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
-            T = Tn;
-            last = lidx[j] + 1u;
-            ++nadd;
+            int ja = 0, jb = 0;
+            if (!pick(cand_new, hn, ja)) continue;
+            const bool two = pick(cand_new, hn, jb);
+            float4 ka, kb;
+            const float ta = exponent(ja, ka);
+            const float tb = two ? exponent(jb, kb) : 0.f;
+            const float Ga = exp2_approx(ta), Gb = exp2_approx(tb);
+            if (ta >= ka.z && !add(ja, Ga, ka, cand_new)) continue;
+            if (two && tb >= kb.z) add(jb, Gb, kb, cand_new);
         }
     };
     for (;;) {
