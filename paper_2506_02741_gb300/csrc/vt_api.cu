@@ -545,9 +545,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
                      n_tiles, std::max<int64_t>(views, 1), std::max<int64_t>(tabrows, 1), stream)))
         return st;
     if (!sort_attr_set) {
-        VT_CUDA(cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSortSmemBigBytes),
-                "sort smem attribute");
+        for (auto kern : {k_sort_tiles, k_sort_tiles_mid, k_sort_tiles_large, k_sort_tiles_long})
+            VT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSortSmemBigBytes),
+                    "sort smem attribute");
         sort_attr_set = true;
     }
     c->has_render = false;
@@ -608,7 +609,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         LaunchScope ls(c, K_SORT_BIG, c->aux);
         // one block per SM at most: these lists are few, and the launch must
         // not hold every SM's shared memory while the others run
-        k_sort_tiles<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
+        k_sort_tiles_long<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, 0x7fffffff);
     }
@@ -621,13 +622,13 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     }
     {
         LaunchScope ls(c, K_SORT_M, stream);
-        k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
+        k_sort_tiles_mid<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortClassM, kSortClassS, kSortClassM);
     }
     {
         LaunchScope ls(c, K_SORT_L, stream);
-        k_sort_tiles<<<n_tiles, 512, kSortSmemBytes, stream>>>(
+        k_sort_tiles_large<<<n_tiles, 512, kSortSmemBytes, stream>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN);
     }

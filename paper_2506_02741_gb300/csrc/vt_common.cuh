@@ -275,10 +275,17 @@ __global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *
                              uint32_t *tile_cursor, Status *st, unsigned long long cap);
 __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
                        unsigned long long *bucket, uint8_t *bmask_u, const Status *st);
-__global__ void k_sort_tiles(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,
-                             unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted,
-                             uint8_t *bmask, const float4 *geo, Camera cam, Status *st,
-                             int smem_n, int lo, int hi);
+// Per-tile depth sort, one kernel per list-length class (vt_raster.cu).
+#define VT_DECLARE_SORT(name)                                                                    \
+    __global__ void name(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,     \
+                         unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted,     \
+                         uint8_t *bmask, const float4 *geo, Camera cam, Status *st, int smem_n, \
+                         int lo, int hi);
+VT_DECLARE_SORT(k_sort_tiles)
+VT_DECLARE_SORT(k_sort_tiles_mid)
+VT_DECLARE_SORT(k_sort_tiles_large)
+VT_DECLARE_SORT(k_sort_tiles_long)
+#undef VT_DECLARE_SORT
 __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
                                 const uint8_t *bmask, const float4 *geo, const float4 *app,
                                 float *rgb, float *depth, float *sil, uint32_t *pix_last,

@@ -416,22 +416,48 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, bool vali
     return m;
 }
 
+// One stable LSD pass on bits [shift, shift + nbits) of the keys in[0, n)
+// into out.  Each warp histograms its contiguous chunk in groups of 32 (peer
+// lanes holding the same digit found with one ballot per digit bit), the
+// block scans the per-warp histograms in (digit, warp) order, and each warp
+// scatters its chunk.  With G > 0 and chunks of at most G groups, every
+// lane keeps its digit, its rank among its peers and their count in
+// registers between the two phases instead of ranking twice.
+template <int G>
 __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigned long long *out,
                                            int n, int shift, int nbits, uint32_t *hist) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned dmask = (1u << nbits) - 1u;
     const int per = (n + kSortWarps - 1) / kSortWarps;
     const int lo = min(n, warp * per), hi = min(n, lo + per);
+    const unsigned lt = (1u << lane) - 1u;
+    const bool cache = G > 0 && per <= G * 32;
+    uint32_t pk[G > 0 ? G : 1];
     for (int i = tid; i < kSortWarps * 256; i += kSortThreads) hist[i] = 0;
     __syncthreads();
     uint32_t *h = hist + warp * 256;
-    for (int i0 = lo; i0 < hi; i0 += 32) {
-        const int i = i0 + lane;
-        const bool valid = i < hi;
-        const unsigned d = valid ? (unsigned)(in[i] >> shift) & dmask : 0u;
-        const unsigned peers = digit_peers(d, nbits, valid);
-        if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
-        __syncwarp();
+    if (cache) {
+#pragma unroll
+        for (int gi = 0; gi < (G > 0 ? G : 1); ++gi) {
+            if (lo + gi * 32 >= hi) break;
+            const int i = lo + gi * 32 + lane;
+            const bool valid = i < hi;
+            const unsigned d = valid ? (unsigned)(in[i] >> shift) & dmask : 0u;
+            const unsigned peers = digit_peers(d, nbits, valid);
+            const unsigned rank = __popc(peers & lt), cnt = __popc(peers);
+            pk[gi] = d | (rank << 8) | (cnt << 13);
+            if (valid && rank == 0) h[d] += cnt;
+            __syncwarp();
+        }
+    } else {
+        for (int i0 = lo; i0 < hi; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < hi;
+            const unsigned d = valid ? (unsigned)(in[i] >> shift) & dmask : 0u;
+            const unsigned peers = digit_peers(d, nbits, valid);
+            if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
+            __syncwarp();
+        }
     }
     __syncthreads();
     // exclusive scan in (digit, warp) order
@@ -467,23 +493,37 @@ __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigne
     if (tid < 256)
         for (int w = 0; w < kSortWarps; ++w) hist[w * 256 + tid] += dsum[tid];
     __syncthreads();
-    for (int i0 = lo; i0 < hi; i0 += 32) {
-        const int i = i0 + lane;
-        const bool valid = i < hi;
-        unsigned long long key = 0;
-        unsigned d = 0;
-        if (valid) {
-            key = in[i];
-            d = (unsigned)(key >> shift) & dmask;
+    if (cache) {
+#pragma unroll
+        for (int gi = 0; gi < (G > 0 ? G : 1); ++gi) {
+            if (lo + gi * 32 >= hi) break;
+            const int i = lo + gi * 32 + lane;
+            const bool valid = i < hi;
+            const unsigned d = pk[gi] & 0xFFu, rank = (pk[gi] >> 8) & 31u, cnt = pk[gi] >> 13;
+            if (valid) out[h[d] + rank] = in[i];
+            __syncwarp();
+            if (valid && rank == 0) h[d] += cnt;
+            __syncwarp();
         }
-        const unsigned peers = digit_peers(d, nbits, valid);
-        if (valid) {
-            const uint32_t pos = h[d] + __popc(peers & ((1u << lane) - 1u));
-            out[pos] = key;
+    } else {
+        for (int i0 = lo; i0 < hi; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < hi;
+            unsigned long long key = 0;
+            unsigned d = 0;
+            if (valid) {
+                key = in[i];
+                d = (unsigned)(key >> shift) & dmask;
+            }
+            const unsigned peers = digit_peers(d, nbits, valid);
+            if (valid) {
+                const uint32_t pos = h[d] + __popc(peers & lt);
+                out[pos] = key;
+            }
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
+            __syncwarp();
         }
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
-        __syncwarp();
     }
     __syncthreads();
 }
@@ -514,11 +554,13 @@ struct SortOut {
     }
 };
 
-// Sorts one tile's list [start, start + n) (2 <= n) with the whole block.
+// Sorts one tile's list [start, start + n) (2 <= n) with the whole block
+// (G: register-cached radix ranks for chunks of up to G groups per warp).
 // Lists sorted in shared memory carry (block mask << 24 | position in the
 // bucket) in the low word, so the masks written by k_emit travel with the
 // entries and the ids are read back from the bucket (which stays intact);
 // lists sorted in place carry the id and their masks are recomputed.
+template <int G>
 __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned long long *alt,
                                           const uint8_t *bmask_u, const SortOut &out,
                                           Status *st, uint32_t start, int n, int smem_n,
@@ -572,7 +614,7 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
     __syncthreads();
     unsigned long long *cur = A, *oth = B;
     for (unsigned b = 0; b < bz; b += 8) {
-        radix_pass(cur, oth, n, 32 + b, min(8u, bz - b), hist);
+        radix_pass<G>(cur, oth, n, 32 + b, min(8u, bz - b), hist);
         unsigned long long *tmp = cur;
         cur = oth;
         oth = tmp;
@@ -628,7 +670,7 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
     __syncthreads();
     const unsigned tot = bz + bg;
     for (unsigned b = 0; b < tot; b += 8) {
-        radix_pass(cur, oth, n, b, min(8u, tot - b), hist);
+        radix_pass<G>(cur, oth, n, b, min(8u, tot - b), hist);
         unsigned long long *tmp = cur;
         cur = oth;
         oth = tmp;
@@ -637,15 +679,13 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
     out.put_all(n, tid, [&](int i) { return gmin + (uint32_t)(cur[i] & gm); });
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *tile_off,
-                                                             int n_tiles,
-                                                             unsigned long long *bucket,
-                                                             unsigned long long *alt,
-                                                             const uint8_t *bmask_u,
-                                                             uint32_t *sorted, uint8_t *bmask,
-                                                             const float4 *geo, Camera cam,
-                                                             Status *st, int smem_n, int lo,
-                                                             int hi) {
+template <int G>
+__device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_tiles,
+                                                unsigned long long *bucket,
+                                                unsigned long long *alt, const uint8_t *bmask_u,
+                                                uint32_t *sorted, uint8_t *bmask,
+                                                const float4 *geo, const Camera &cam, Status *st,
+                                                int smem_n, int lo, int hi) {
     extern __shared__ unsigned long long sm[];
     __shared__ uint32_t red[4][kSortWarps];
     if (st->flags) return;
@@ -663,9 +703,27 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *til
             }
             continue;
         }
-        sort_tile(bucket, alt, bmask_u, out, st, start, n, smem_n, sm, red, tid, lane, warp);
+        sort_tile<G>(bucket, alt, bmask_u, out, st, start, n, smem_n, sm, red, tid, lane, warp);
         __syncthreads();   // shared memory is reused by the next tile
     }
 }
+
+// One kernel per list-length class, each caching the radix ranks of up to
+// (class limit / 16 warps) entries per warp, with registers capped for two
+// blocks of 512 threads per SM; the long lists (one block per SM) rank
+// twice.
+#define VT_SORT_KERNEL(name, G, MIN_BLOCKS)                                                      \
+    __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) name(                            \
+        const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,                       \
+        unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,       \
+        const float4 *geo, Camera cam, Status *st, int smem_n, int lo, int hi) {                 \
+        sort_tiles_body<G>(tile_off, n_tiles, bucket, alt, bmask_u, sorted, bmask, geo, cam, st, \
+                           smem_n, lo, hi);                                                      \
+    }
+VT_SORT_KERNEL(k_sort_tiles, 3, 2)
+VT_SORT_KERNEL(k_sort_tiles_mid, 7, 2)
+VT_SORT_KERNEL(k_sort_tiles_large, 12, 2)
+VT_SORT_KERNEL(k_sort_tiles_long, 0, 1)
+#undef VT_SORT_KERNEL
 
 }  // namespace vt
