@@ -898,7 +898,7 @@ vt_status vt_ssim(vt_ctx *c, int32_t W, int32_t H, const float *rgb, const float
     if (!rgb || !obs_rgb) return fail(VT_ERR_INVALID_ARG, "vt_ssim: NULL image");
     if (!std::isfinite(weight)) return fail(VT_ERR_INVALID_ARG, "vt_ssim: weight must be finite");
     const int64_t P = (int64_t)W * H;
-    const dim3 grid((W + 31) / 32, (H + 7) / 8);
+    const dim3 grid((W + kSsimTileW - 1) / kSsimTileW, (H + kSsimTileH - 1) / kSsimTileH);
     const int64_t nb = (int64_t)grid.x * grid.y;
     // 15 map floats per pixel (5 maps x 3 channels), then 2 doubles per block
     const int64_t need = std::max<int64_t>(P, 256 * nb);

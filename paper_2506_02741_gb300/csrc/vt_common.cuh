@@ -375,6 +375,7 @@ struct PoseAdamParams {
 __global__ void k_pose_adam(double *pose, double *d_twist, double *state, PoseAdamParams prm);
 
 // SSIM term (vt_ssim.cu): the 11 normalised 1-D window weights.
+constexpr int kSsimTileW = 32, kSsimTileH = 32;   // SSIM output tile (256 threads)
 struct SsimWindow {
     float g[11];
 };
