@@ -20,6 +20,8 @@ for this variant):
     and pixel (u, v) of the target image sees
         q = d^T Sigma_2D^-1 d,   d = (u - u_c, v - v_c),
         u_c = fx x/z + cx,  v_c = fy y/z + cy;
+  * a Gaussian whose scales are not all positive and finite, or whose
+    quaternion is zero, is not rendered;
   * everything else is the isotropic render's: ahat = o exp(-q/2), included
     iff q <= 9 and ahat >= 1/255, alpha = min(0.99, ahat), order by the FP32
     depth key and then the id, stop before the Gaussian that would take the
@@ -126,7 +128,10 @@ def _geometry(sec: Section, scale, quat, pose, K, W, H, eps):
                       np.stack([-S2[:, 1, 0], S2[:, 0, 0]], 1)], 1) / det[:, None, None]
         uc = fx * (x[:, 0] / z) + cx
         vc = fy * (x[:, 1] / z) + cy
-    valid = np.asarray(valid, bool)
+    # an ellipsoid needs three positive finite scales and a non-zero quaternion
+    qn = np.linalg.norm(np.asarray(quat, np.float64), axis=1)
+    shape_ok = np.all((s > 0) & np.isfinite(s), axis=1) & (qn > 0) & np.isfinite(qn)
+    valid = np.asarray(valid, bool) & shape_ok
     return dict(key=key, valid=valid, x=x, M=M, Rq=Rq, s=s, Sk=Sk, Sc=Sc, J=J, S2=S2, Q=Q,
                 uc=uc, vc=vc, z=z, R=R, fx=fx, fy=fy)
 

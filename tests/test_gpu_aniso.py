@@ -215,3 +215,53 @@ def test_ellipsoid_mapper_reduces_loss(dev):
     losses = [float(mp.step(i % 3).item()) for i in range(30)]
     assert losses[-1] < 0.8 * losses[0], losses
     assert not torch.equal(s0, sec.scale) and not torch.equal(q0, sec.rot)
+
+
+def test_ellipsoid_fp16_storage_and_invalid_shapes(dev):
+    """FP16 storage (both sides read the same rounded attributes, FP32
+    arithmetic), with some Gaussians whose scales are zero, negative or NaN
+    or whose quaternion is zero: those are not rendered on either side."""
+    sec, scale, quat, target, K, W, H = _case("qqvga_2views")
+    f16 = lambda a: np.asarray(a, np.float16).astype(np.float64)
+    sec = G.quantise(sec, "f16")
+    scale, quat = f16(scale), f16(quat)
+    rng = np.random.default_rng(12)
+    bad = rng.choice(sec.n, 60, replace=False)
+    scale[bad[:15], 0] = 0.0
+    scale[bad[15:30], 1] = -1e-3
+    scale[bad[30:45], 2] = np.nan
+    quat[bad[45:]] = 0.0
+    dsec = G.to_device(sec, "f16").with_ellipsoids(torch.from_numpy(scale),
+                                                   torch.from_numpy(quat))
+    R = api.Renderer()
+    out = R.render([dsec], api.pose12(target, dev), K, W, H, checked=True)
+    torch.cuda.synchronize()
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ref = aniso.render(sec, scale, quat, target, K, W, H)
+    mask = G.clean_mask(ref, tau_incl=TAU_INCL)
+    assert mask.mean() > 0.9
+    G.assert_forward_close(out, ref, mask, tol=FWD_TOL)
+
+
+def test_thin_ellipsoids(dev):
+    """Needle- and disc-shaped ellipsoids (axis ratios up to ~30): forward
+    and pose gradient against the oracle."""
+    sec, _, _, target, K, W, H = _case("tiny")
+    rng = np.random.default_rng(13)
+    r = sec.radius
+    scale = np.stack([r * 3.0, r * 0.1, r * rng.choice([0.1, 3.0], sec.n)], 1)
+    quat = _q32(rng.normal(size=(sec.n, 4)))
+    scale = _q32(scale)
+    R = api.Renderer()
+    R.render([_device(sec, scale, quat)], api.pose12(target, dev), K, W, H, checked=True)
+    out = R.render([_device(sec, scale, quat)], api.pose12(target, dev), K, W, H)
+    ref = aniso.render(sec, scale, quat, target, K, W, H, keep=True)
+    mask = G.clean_mask(ref, tau_incl=TAU_INCL)
+    assert mask.mean() > 0.85
+    G.assert_forward_close(out, ref, mask, tol=FWD_TOL)
+    clean = G.clean_mask(ref, tau_incl=TAU_INCL, tau_clamp=1e-4)
+    gR = (rng.normal(0, 1, (3, H, W)) * clean).astype(np.float32)
+    want = aniso.backward(sec, scale, quat, target, K, W, H, gR, fwd=ref)
+    dtw, _ = R.backward(torch.from_numpy(gR).to(dev), None, None, pose_grad=True)
+    torch.cuda.synchronize()
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist", abs_ref=want["abs_twist"])

@@ -214,3 +214,25 @@ def test_magnitudes_bound_the_gradients():
     for k in ("colour", "opacity", "scale", "quat", "x", "twist", "mat"):
         assert np.all(np.abs(g[k]) <= g["abs_" + k] * (1 + 1e-9) + 1e-300), k
     assert np.abs(g["scale"]).max() > 0 and np.abs(g["quat"]).max() > 0
+
+
+def test_invalid_shapes_are_not_rendered():
+    """Gaussians with a non-positive or non-finite scale or a zero
+    quaternion are left out: the render equals that of the section without
+    them (their opacity set below the 1/255 skip)."""
+    sec, scale, quat, target, K, W, H = _small_case()
+    rng = np.random.default_rng(9)
+    bad = rng.choice(sec.n, 40, replace=False)
+    s2, q2 = scale.copy(), quat.copy()
+    s2[bad[:10], 0] = 0.0
+    s2[bad[10:20], 1] = -1e-3
+    s2[bad[20:30], 2] = np.nan
+    q2[bad[30:]] = 0.0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        got = aniso.render(sec, s2, q2, target, K, W, H)
+    op = sec.opacity.copy()
+    op[bad] = 0.0
+    import dataclasses
+    ref = aniso.render(dataclasses.replace(sec, opacity=op), scale, quat, target, K, W, H)
+    np.testing.assert_array_equal(got["rgb"], ref["rgb"])
+    np.testing.assert_array_equal(got["n_added"], ref["n_added"])
