@@ -72,8 +72,10 @@ struct ViewXf {
 };
 
 // One table row: three float-float values (u numerator, v numerator, z).
-struct TabRow {
+struct __align__(16) TabRow {
     float2 a, b, c;
+    float kf;    // FP32 (u - cx)/fx (column rows) or (v - cy)/fy (row rows) of the depth key
+    float pad;
 };
 
 struct Status {

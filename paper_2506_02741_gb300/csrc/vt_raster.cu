@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const dou
             out.a = make_float2(pu.hi, pu.lo);
             out.b = make_float2(pv.hi, pv.lo);
             out.c = make_float2(pz.hi, pz.lo);
+            out.kf = __fdiv_rn(__fsub_rn((float)i, S.cx), S.fx);
         } else {
             ff b = ff_div(ff_two_sum((float)(i - W), -S.cy), ff{S.fy, 0.f});
             ff pu = ff_add(ff_mul(rows[1], b), rows[2]);
@@ -82,7 +83,9 @@ __global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const dou
             out.a = make_float2(pu.hi, pu.lo);
             out.b = make_float2(pv.hi, pv.lo);
             out.c = make_float2(pz.hi, pz.lo);
+            out.kf = __fdiv_rn(__fsub_rn((float)(i - W), S.cy), S.fy);
         }
+        out.pad = 0.f;
         tb[i] = out;
     }
 }
@@ -224,13 +227,16 @@ __device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera 
         const float r = Aniso ? 1.f : ld_attr(S.radius, S.prec, li);
         bool ok = in_range && isfinite(D) && D > 0.f && o >= kAlphaMin && r > 0.f && isfinite(r);
         const ViewXf &X = views[S.view_base + (ok ? k : 0)];
+        const TabRow *tb = tab + S.tab_base + (int64_t)(ok ? k : 0) * (S.W + S.H);
+        TabRow A, B;
         float zkey = 0.f;
         if (ok) {
-            // depth key: a = (u - cx)/fx, b = (v - cy)/fy, X = D a, Y = D b,
-            // z = ((M20 X + M21 Y) + M22 D) + m2, every step rounded to FP32.
-            const float a = __fdiv_rn(__fsub_rn((float)u, S.cx), S.fx);
-            const float b = __fdiv_rn(__fsub_rn((float)v, S.cy), S.fy);
-            const float Xc = __fmul_rn(D, a), Yc = __fmul_rn(D, b);
+            A = tb[u];
+            B = tb[S.W + v];
+            // depth key: a = (u - cx)/fx, b = (v - cy)/fy (FP32 divisions of the
+            // view tables), X = D a, Y = D b, z = ((M20 X + M21 Y) + M22 D) + m2,
+            // every step rounded to FP32.
+            const float Xc = __fmul_rn(D, A.kf), Yc = __fmul_rn(D, B.kf);
             float z = __fmul_rn(X.Mf[6], Xc);
             z = __fadd_rn(z, __fmul_rn(X.Mf[7], Yc));
             z = __fadd_rn(z, __fmul_rn(X.Mf[8], D));
@@ -238,8 +244,6 @@ __device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera 
             ok = zkey >= kZNear;
         }
         if (ok) {
-            const TabRow *tb = tab + S.tab_base + (int64_t)k * (S.W + S.H);
-            const TabRow A = tb[u], B = tb[S.W + v];
             const ff hu = ff_add(ff_from(A.a), ff_from(B.a));
             const ff hv = ff_add(ff_from(A.b), ff_from(B.b));
             const ff hz = ff_add(ff_from(A.c), ff_from(B.c));
@@ -249,7 +253,7 @@ __device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera 
             const ff uc = ff_div(nu, nz), vc = ff_div(nv, nz);
             const float z = nz.hi;
             float qlim = kQMax;
-            const float qo = 2.f * logf(255.f * o);
+            const float qo = 2.f * __logf(255.f * o);   // box bound only (slack below)
             if (qo < qlim) qlim = qo;
             qlim = qlim * 1.0001f + 1e-4f;
             float ex, ey;
@@ -258,8 +262,8 @@ __device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera 
                 const float tx = __fdiv_rn(z, __fmul_rn(cam.fx, r));
                 const float ty = __fdiv_rn(z, __fmul_rn(cam.fy, r));
                 const float kx = __fmul_rn(tx, tx), ky = __fmul_rn(ty, ty);
-                ex = sqrtf(qlim / kx) + 1e-3f;
-                ey = sqrtf(qlim / ky) + 1e-3f;
+                ex = sqrtf(__fdividef(qlim, kx)) + 1e-3f;   // box bound only (slack)
+                ey = sqrtf(__fdividef(qlim, ky)) + 1e-3f;
                 ok = kx > 0.f && ky > 0.f && isfinite(kx) && isfinite(ky);
                 g1 = make_float4(__fmul_rn(kx, kTScale), __fmul_rn(ky, kTScale), __frcp_rn(r), o);
             } else {
