@@ -332,6 +332,56 @@ def run_ellipsoids(dev, iters: int = 50):
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
 
 
+def run_large(dev, reps: int = 5):
+    """The multi-section render at its large end: seven adjacent sections of
+    14 keyframes (every other frame of the path) at 640x480, 30,105,600
+    Gaussians rendered together from a pose between keyframes (about 1,500
+    Gaussians over each pixel), with the pose backward.  CUDA-event times
+    per call, with the default per-pixel list capacity (256: pixels that add
+    more send their tiles to the replay backward) and with 1024."""
+    import torch
+
+    from paper_2506_02741_gb300 import api
+    from paper_2506_02741_gb300 import synthetic as syn
+    K = syn.VGA
+    n_sec, per = 7, 14
+    path = syn.trajectory(n_sec * per * 2 + 5)
+    room = syn.make_room(syn.SCENE_SEED)
+    secs = []
+    for s in range(n_sec):
+        keys = [path[2 * (s * per + j)] for j in range(per)]
+        fr = syn.render_frames(room, K, keys)
+        secs.append(api.Section.from_rgbd(torch.from_numpy(fr.depth).to(dev),
+                                          torch.from_numpy(fr.rgb).to(dev), K.astuple(),
+                                          np.stack(keys)))
+    pose = api.pose12(path[n_sec * per + 1], dev)
+    g = torch.full((3, K.H, K.W), 1e-6, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    out = {"workload": "large_multisection_640x480_7x14kf_fp32",
+           "gaussians": int(sum(s.n for s in secs)), "sections": n_sec}
+    for cap in (256, 1024):
+        R = api.Renderer()
+        R.set_list_capacity(cap)
+        rgb, depth, sil = R.render(secs, pose, K.astuple(), K.W, K.H, checked=True)
+        out["instances"] = int(R.status())
+        R.backward(g, None, None, pose_grad=True)
+        torch.cuda.synchronize()
+        fwd = bwd = 0.0
+        for _ in range(reps):
+            ev[0].record()
+            R.render(secs, pose, K.astuple(), K.W, K.H, rgb, depth, sil)
+            ev[1].record()
+            R.backward(g, None, None, pose_grad=True)
+            ev[2].record()
+            torch.cuda.synchronize()
+            fwd += ev[0].elapsed_time(ev[1])
+            bwd += ev[1].elapsed_time(ev[2])
+        out[f"list_cap_{cap}"] = {"render_ms": fwd / reps, "pose_backward_ms": bwd / reps,
+                                  "mpix_s": K.W * K.H / ((fwd + bwd) / reps) / 1e3}
+        del R
+    return out
+
+
 def run_serving(dev, n_req: int = 300):
     """Serving workload: 4 resident sections (0.3 M - 8.3 M Gaussians),
     Poisson render/track requests (70% track) over 320x240 ... 1920x1080.
@@ -649,6 +699,7 @@ def main():
         mapping = {prec: run_mapping(dev, prec, args.mapping_iters) for prec in ("f16", "f32")}
     head_frame = run_head_frame(dev) if rank == 0 and not args.no_mapping else None
     ellipsoids = run_ellipsoids(dev) if rank == 0 and not args.no_mapping else None
+    large = run_large(dev) if rank == 0 and not args.no_mapping else None
 
     serving_line = None
     if rank == 0 and not args.no_serving:
@@ -683,6 +734,7 @@ def main():
             "mapping": mapping,
             "head_frame": head_frame,
             "ellipsoids": ellipsoids,
+            "large_render": large,
             "serving": serving_line,
             "clocks": clocks,
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items()},

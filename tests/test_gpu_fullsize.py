@@ -178,3 +178,98 @@ def test_fullsize_ellipsoid_crop_parity():
                             abs_ref=want["abs_" + name][touched])
     G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist", abs_ref=want["abs_twist"])
     G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", abs_ref=want["abs_mat"])
+
+
+def _large_sections(n_sec=7, per=14):
+    """Seven adjacent sections of 14 keyframes each (every other frame of the
+    path) at 640x480: 30,105,600 Gaussians, rendered together (the
+    multi-section render)."""
+    K = syn.VGA
+    path = syn.trajectory(n_sec * per * 2 + 5)
+    room = syn.make_room(syn.SCENE_SEED)
+    out = []
+    for s in range(n_sec):
+        keys = [path[2 * (s * per + j)] for j in range(per)]
+        fr = syn.render_frames(room, K, keys)
+        out.append((fr, np.stack(keys)))
+    return K, out, path[n_sec * per + 1]   # between keyframes (odd path index)
+
+
+def _crop_subset(osec, target, K, box, slack=3.0):
+    """The Gaussians of an oracle section whose 3-sigma disc can reach the
+    crop box (x0, y0, w, h), as a section of their own: ids keep their
+    relative order, so (z_key, id) orders them as in the whole render."""
+    import dataclasses
+    x0, y0, w, h = box
+    P = np.asarray(target, np.float64).reshape(3, 4)
+    R, t = P[:, :3], P[:, 3]
+    plane = osec.W * osec.H
+    src = osec.src.astype(np.int64)
+    view = src // plane
+    pix = src - view * plane
+    u, v = (pix % osec.W).astype(np.float64), (pix // osec.W).astype(np.float64)
+    fx, fy, cx, cy = (float(np.float32(k)) for k in osec.K)
+    D = osec.depth.reshape(-1)[src].astype(np.float64)
+    Xc = np.stack([D * (u - cx) / fx, D * (v - cy) / fy, D], 1)
+    mu = np.einsum("nab,nb->na", osec.poses[view][:, :, :3], Xc) + osec.poses[view][:, :, 3]
+    x = (mu - t) @ R
+    z = x[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        uc = K.fx * x[:, 0] / z + K.cx
+        vc = K.fy * x[:, 1] / z + K.cy
+        e = 3.0 * max(K.fx, K.fy) * osec.radius / z + slack
+        keep = (z > 0.05) & (uc + e >= x0) & (uc - e <= x0 + w - 1) & (vc + e >= y0) & \
+               (vc - e <= y0 + h - 1)
+    return dataclasses.replace(osec, src=osec.src[keep], colour=osec.colour[keep],
+                               opacity=osec.opacity[keep], radius=osec.radius[keep])
+
+
+def test_large_multisection_render():
+    """30.1 M Gaussians of seven sections rendered together at 640x480 (about
+    1,500 Gaussians over each pixel, so many per-pixel lists overflow and
+    their tiles take the replay backward), and again under a workspace
+    budget that keeps no lists at all: a 96x80 crop and the pose gradient of
+    an upstream gradient on that crop against the oracle, which renders the
+    Gaussians that can reach the crop; both backward forms agree."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    K, frames, target = _large_sections()
+    dsecs, osecs = [], []
+    for fr, keys in frames:
+        dsecs.append(api.Section.from_rgbd(torch.from_numpy(fr.depth).to(dev),
+                                           torch.from_numpy(fr.rgb).to(dev), K.astuple(), keys))
+        osecs.append(G.quantise(oracle.section_init(fr.depth, fr.rgb, K.astuple(), keys)))
+    assert sum(s.n for s in dsecs) == 30_105_600
+    cw, ch = 96, 80
+    x0, y0 = (K.W - cw) // 2 + 40, (K.H - ch) // 2 + 24
+    Kc = _crop(K, x0, y0)
+    subs = [_crop_subset(s, target, K, (x0, y0, cw, ch)) for s in osecs]
+    ref = oracle.render(subs, target, Kc, cw, ch)
+    clean = G.clean_mask(ref)
+    assert clean.mean() > 0.9
+    gm = G.clean_mask(ref, tau_clamp=1e-4)
+    rng = np.random.default_rng(5)
+    gR = (rng.normal(0, 1, (3, ch, cw)) * gm).astype(np.float32)
+    want = oracle.backward(subs, target, Kc, cw, ch, g_rgb=gR)
+    sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
+    full_gR = torch.zeros(3, K.H, K.W, device=dev)
+    full_gR[:, sl[0], sl[1]] = torch.from_numpy(gR).to(dev)
+    results = []
+    for budget in (None, 1):
+        R = api.Renderer()
+        if budget is not None:
+            R.set_budget(budget)
+        rgb, depth, sil = R.render(dsecs, api.pose12(target, dev), K.astuple(), K.W, K.H,
+                                   checked=True)
+        assert R.used_lists == (budget is None)
+        G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref, clean)
+        dtw, dmat = R.backward(full_gR, None, None, pose_grad=True)
+        torch.cuda.synchronize()
+        G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist",
+                            noise=want["twist_noise"])
+        results.append((rgb, dtw))
+        del R
+    assert torch.equal(results[0][0], results[1][0])
+    torch.testing.assert_close(results[0][1], results[1][1], rtol=1e-6,
+                               atol=1e-9 * float(results[1][1].abs().max()))
