@@ -43,9 +43,10 @@ vt_status cuda_fail(cudaError_t e, const char *what) {
 // launch whose blocks hold just enough shared memory for its longest list, so
 // that short lists run several blocks per SM (4, 3 and 2 of 228 KB):
 // (0, 1536], (1536, 3584], (3584, kSortSmemN] on the caller's stream; the few
-// longer ones (up to
-// kSortSmemBig in shared memory, beyond that in global memory) by a launch on
-// an auxiliary stream that overlaps the others.
+// longer ones (up to kSortSmemBig in shared memory, one block per SM; beyond
+// that in global memory, two blocks per SM with shared memory for the
+// histograms only) by launches on an auxiliary stream that overlap the
+// others.
 constexpr int kSortClassS = 1536, kSortClassM = 3584;
 constexpr size_t sort_smem_bytes(int n) { return 2 * (size_t)n * 8 + 16 * 256 * 4; }
 // (kept for the long-list launch and the attribute of the largest one)
@@ -56,6 +57,7 @@ constexpr int kSortSmemBig = 13312;
 static_assert(kSortSmemBig < (1 << 24), "shared-memory sorts carry 24-bit bucket positions");
 constexpr size_t kSortSmemBigBytes =
     2 * kSortSmemBig * sizeof(unsigned long long) + 16 * 256 * 4;
+constexpr size_t kSortHistBytes = 16 * 256 * 4;
 
 enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
@@ -611,7 +613,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         // not hold every SM's shared memory while the others run
         k_sort_tiles_long<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, 0x7fffffff);
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, kSortSmemBig);
+        k_sort_tiles_xl<<<std::min(n_tiles, 2 * c->n_sm), 512, kSortHistBytes, c->aux>>>(
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemBig, 0x7fffffff);
     }
     VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
     {

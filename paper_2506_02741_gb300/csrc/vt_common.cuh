@@ -287,6 +287,7 @@ VT_DECLARE_SORT(k_sort_tiles)
 VT_DECLARE_SORT(k_sort_tiles_mid)
 VT_DECLARE_SORT(k_sort_tiles_large)
 VT_DECLARE_SORT(k_sort_tiles_long)
+VT_DECLARE_SORT(k_sort_tiles_xl)
 #undef VT_DECLARE_SORT
 __global__ void k_composite_fwd(Camera cam, const uint32_t *tile_off, const uint32_t *sorted,
                                 const uint8_t *bmask, const float4 *geo, const float4 *app,

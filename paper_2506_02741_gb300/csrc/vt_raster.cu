@@ -571,7 +571,8 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
                                           unsigned long long *sm, uint32_t (*red)[kSortWarps],
                                           int tid, int lane, int warp) {
     const bool big = n > smem_n;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(sm + 2 * smem_n);
+    // lists sorted in global memory need only the histograms in shared memory
+    uint32_t *hist = reinterpret_cast<uint32_t *>(big ? sm : sm + 2 * smem_n);
     unsigned long long *A = big ? bucket + start : sm;
     unsigned long long *B = big ? alt + start : sm + smem_n;
     if (big && tid == 0) atomicAdd(&st->n_overflow_tiles, 1ull);
@@ -714,8 +715,9 @@ __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_
 
 // One kernel per list-length class, each caching the radix ranks of up to
 // (class limit / 16 warps) entries per warp, with registers capped for two
-// blocks of 512 threads per SM; the long lists (one block per SM) rank
-// twice.
+// blocks of 512 threads per SM; the long lists (one block per SM) and the
+// lists sorted in global memory (two blocks per SM, shared memory for the
+// histograms only) rank twice.
 #define VT_SORT_KERNEL(name, G, MIN_BLOCKS)                                                      \
     __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) name(                            \
         const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,                       \
@@ -728,6 +730,7 @@ VT_SORT_KERNEL(k_sort_tiles, 3, 2)
 VT_SORT_KERNEL(k_sort_tiles_mid, 7, 2)
 VT_SORT_KERNEL(k_sort_tiles_large, 12, 2)
 VT_SORT_KERNEL(k_sort_tiles_long, 0, 1)
+VT_SORT_KERNEL(k_sort_tiles_xl, 0, 2)
 #undef VT_SORT_KERNEL
 
 }  // namespace vt
