@@ -754,7 +754,8 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
     }
     if (c->used_lists) {
         LaunchScope ls(c, K_BWD_LIST, stream);
-        auto kern = views ? k_composite_bwd_list_views : k_composite_bwd_list;
+        auto kern = views ? k_composite_bwd_list_views
+                          : (attr ? k_composite_bwd_list : k_composite_bwd_list_pose);
         kern<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->blk_ovf,
             dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->acc4, c->accr, c->accg,

@@ -818,8 +818,9 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd_aniso(
 // into k_composite_bwd_list_views; the tracking and mapping paths launch
 // k_composite_bwd_list, which does not carry it.  Aniso = true walks
 // ellipsoid records (k_composite_bwd_list_aniso): per-Gaussian accumulation
-// instead of per-lane pose sums.
-template <bool Views, bool Aniso>
+// instead of per-lane pose sums.  PoseOnly = true (k_composite_bwd_list_pose)
+// leaves out the per-Gaussian terms, which tracking does not use.
+template <bool Views, bool Aniso, bool PoseOnly = false>
 __device__ __forceinline__ void bwd_list_body(
     const SecTable &Tab, const Camera &cam, const float4 *geo, const float4 *app,
     const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
@@ -894,7 +895,7 @@ __device__ __forceinline__ void bwd_list_body(
             float dc0, dc1, dc2, dop, drd, gx, gy, gz;
             bwd_pair(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop,
                      drd, want_views, gx, gy, gz, Ti);
-            if (want_attr || want_views)
+            if (!PoseOnly && (want_attr || want_views))
                 add_pair_grads(Tab, g, want_attr, want_views, dc0, dc1, dc2, dop, drd, gx, gy, gz,
                                acc4, accr, accg);
         }
@@ -911,6 +912,17 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
     bwd_list_body<false, false>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf,
                                 g_rgb, g_depth, g_sil, mode, pose_partials, acc4, accr, accg,
                                 nullptr, st, s_pose);
+}
+
+__global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_pose(
+    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
+    const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *blk_ovf,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st) {
+    __shared__ double s_pose[kBlockPix / 32][12];
+    bwd_list_body<false, false, true>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap,
+                                      blk_ovf, g_rgb, g_depth, g_sil, VT_GRAD_POSE, pose_partials,
+                                      acc4, accr, accg, nullptr, st, s_pose);
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_aniso(
