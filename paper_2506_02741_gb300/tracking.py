@@ -99,6 +99,84 @@ class PoseTracker:
         return self.loss
 
 
+class HostPipeline:
+    """Tracking iterations fed from pinned host memory, with each iteration's
+    pose and loss read back on the host, and the copies overlapped with the
+    compute of the neighbouring iterations.
+
+    step(rgb, depth) uploads the observed frame on a copy stream into one of
+    two device staging buffers (while the previous iteration still runs) and
+    replays the CUDA graph of that buffer: the copy of the staged frame into
+    the tracker's observation buffers, the tracking iteration and the copy of
+    (pose, loss) to a result buffer; the read-back of that buffer to pinned
+    memory follows.  It then waits for the previous iteration's read-back and
+    returns that iteration's 13 values (12 pose entries, loss) as a float64
+    NumPy array: results arrive one step late, so the host issues iteration
+    i + 1 while the device computes iteration i.  flush() returns the last
+    one.  The tracker must have been captured once (PoseTracker.capture: it
+    warms the step up and shows that it is capture-safe)."""
+
+    def __init__(self, tracker: PoseTracker):
+        if tracker.graph is None:
+            raise RuntimeError("HostPipeline needs a captured tracker (call capture() first)")
+        self.tr = tracker
+        dev = tracker.obs_rgb.device
+        self.copy_stream = torch.cuda.Stream(dev)
+        self.stage = [(torch.empty_like(tracker.obs_rgb), torch.empty_like(tracker.obs_depth))
+                      for _ in range(2)]
+        self.res = [torch.empty(13, dtype=torch.float64, device=dev) for _ in range(2)]
+        self.host = [torch.empty(13, dtype=torch.float64).pin_memory() for _ in range(2)]
+        self.staged = [torch.cuda.Event() for _ in range(2)]     # upload into stage k done
+        self.consumed = [torch.cuda.Event() for _ in range(2)]   # graph k done with stage k
+        self.ready = [torch.cuda.Event() for _ in range(2)]      # read-back k done
+        self.used = [False, False]
+        self.graphs = []
+        for k in range(2):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                tracker.obs_rgb.copy_(self.stage[k][0])
+                tracker.obs_depth.copy_(self.stage[k][1])
+                loss = tracker.step()
+                self.res[k][:12].copy_(tracker.pose)
+                self.res[k][12:].copy_(loss)
+            self.graphs.append(g)
+        self.pending = None
+        self.i = 0
+
+    def step(self, rgb: torch.Tensor, depth: torch.Tensor):
+        k = self.i & 1
+        main = torch.cuda.current_stream()
+        cs = self.copy_stream
+        if self.used[k]:
+            cs.wait_event(self.consumed[k])
+        with torch.cuda.stream(cs):
+            self.stage[k][0].copy_(rgb, non_blocking=True)
+            self.stage[k][1].copy_(depth, non_blocking=True)
+            self.staged[k].record(cs)
+        main.wait_event(self.staged[k])
+        self.graphs[k].replay()
+        self.consumed[k].record(main)
+        self.used[k] = True
+        self.host[k].copy_(self.res[k], non_blocking=True)
+        self.ready[k].record(main)
+        out = self._collect()
+        self.pending = k
+        self.i += 1
+        return out
+
+    def _collect(self):
+        if self.pending is None:
+            return None
+        j = self.pending
+        self.ready[j].synchronize()
+        self.pending = None
+        return self.host[j].numpy().copy()
+
+    def flush(self):
+        """Result of the last step() (None if there is none pending)."""
+        return self._collect()
+
+
 def pose_error(P, Q):
     """(translation error m, rotation error deg) between two (3,4) poses."""
     P = api.matrix_of(P) if not isinstance(P, np.ndarray) or P.shape == (12,) else P

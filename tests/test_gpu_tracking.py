@@ -64,3 +64,43 @@ def test_graph_replay_matches_eager():
         tr.replay()
     torch.cuda.synchronize()
     assert torch.equal(eager, tr.pose)
+
+
+def test_host_pipeline_matches_synchronous_steps():
+    """HostPipeline (frame uploads on a copy stream, results read one step
+    late) returns, step by step, exactly the pose and loss of synchronous
+    replays, across a change of the observed frame."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_02741_gb300.tracking import HostPipeline
+    dev = torch.device("cuda:0")
+    K, sec, R, tr, gt, start = _setup(dev, n_key=2)
+    p0 = api.pose12(start, dev)
+    tr.capture(warmup=2)
+    obs_rgb0, obs_d0 = tr.obs_rgb.cpu(), tr.obs_depth.cpu()
+    frames = [(obs_rgb0, obs_d0), (obs_rgb0.flip(-1).contiguous(), obs_d0.flip(-1).contiguous())]
+    order = [0, 0, 0, 1, 1, 0, 1]
+    # synchronous reference
+    tr.pose.copy_(p0)
+    tr.reset_optimiser()
+    want = []
+    for f in order:
+        tr.set_target(frames[f][0].to(dev), frames[f][1].to(dev))
+        loss = tr.replay()
+        torch.cuda.synchronize()
+        want.append(np.concatenate([tr.pose.cpu().numpy(), loss.cpu().numpy()]))
+    # pipelined from pinned host memory
+    pinned = [(a.pin_memory(), b.pin_memory()) for a, b in frames]
+    tr.pose.copy_(p0)
+    tr.reset_optimiser()
+    pipe = HostPipeline(tr)
+    got = []
+    for f in order:
+        r = pipe.step(*pinned[f])
+        if r is not None:
+            got.append(r)
+    got.append(pipe.flush())
+    assert pipe.flush() is None
+    assert len(got) == len(want)
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
