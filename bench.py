@@ -185,10 +185,12 @@ def run_mapping(dev, prec: str, iters: int, warmup: int = 3):
     R.set_timing(True)
     R.timing(reset=True)
     l0 = float(m.losses.sum())
+    torch.cuda.nvtx.range_push(f"mapping_{prec}")   # ncu --nvtx-include selects these steps
     e0.record()
     for v in views[warmup:]:
         m.step(v)
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     pk = R.timing(reset=True)

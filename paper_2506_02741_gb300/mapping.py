@@ -73,7 +73,11 @@ class SectionMapper:
             self.d_rot = torch.zeros(n, 4, device=dev)
 
     def step(self, view: int):
-        """One mapping iteration rendering from section view ``view``."""
+        """One mapping iteration rendering from section view ``view``.  Returns
+        the device tensor (L1 terms, SSIM term) of the iteration (the SSIM
+        entry stays 0 without the SSIM term); the Eq. 2 loss is their sum,
+        left to the caller so that the iteration launches no reduction of
+        its own."""
         self.R.render([self.sec], self.sec.poses[view], self.sec.K, self.W, self.H, self.rgb,
                       self.depth, self.sil)
         self.R.masked_l1(self.rgb, self.depth, None, self.rgb_obs[view], self.depth_obs[view],
@@ -93,7 +97,7 @@ class SectionMapper:
         if self.shape is not None:
             api.shape_adam(self.sec, self.shape, self.shape_m, self.shape_v, self.shape_step,
                            self.d_scale, self.d_rot, *self.lr_shape, renderer=self.R)
-        return self.losses.sum() if self.use_ssim else self.losses[0]
+        return self.losses
 
 
 def random_views(n_views: int, iters: int, seed: int = 0):

@@ -212,7 +212,7 @@ def test_ellipsoid_mapper_reduces_loss(dev):
     s0, q0 = sec.scale.clone(), sec.rot.clone()
     R = api.Renderer()
     mp = SectionMapper(R, sec, rgb)
-    losses = [float(mp.step(i % 3).item()) for i in range(30)]
+    losses = [float(mp.step(i % 3).cpu().sum()) for i in range(30)]
     assert losses[-1] < 0.8 * losses[0], losses
     assert not torch.equal(s0, sec.scale) and not torch.equal(q0, sec.rot)
 

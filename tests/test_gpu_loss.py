@@ -199,7 +199,7 @@ def test_mapper_reduces_loss(dev):
     sec.colour.copy_((sec.colour + 0.2 * torch.rand(sec.colour.shape, generator=g, device=dev)).clamp(0, 1))
     R = api.Renderer()
     mp = SectionMapper(R, sec, rgb)
-    losses = [float(mp.step(i % 3).item()) for i in range(30)]
+    losses = [float(mp.step(i % 3).cpu().sum()) for i in range(30)]
     assert losses[-1] < 0.8 * losses[0]
 
 
