@@ -49,8 +49,8 @@ vt_status cuda_fail(cudaError_t e, const char *what) {
 // others.
 constexpr int kSortClassS = 1536, kSortClassM = 3584;
 constexpr size_t sort_smem_bytes(int n) { return 2 * (size_t)n * 8 + 16 * 256 * 4; }
-// (kept for the long-list launch and the attribute of the largest one)
-// launch with one large block per SM; longer still in global memory.
+// Upper bound of the third class; lists up to kSortSmemBig sort in shared
+// memory with one block per SM, longer ones in global memory.
 constexpr int kSortSmemN = 6000;
 constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 16 * 256 * 4;
 constexpr int kSortSmemBig = 13312;
@@ -63,7 +63,8 @@ enum KernelId {
     K_SETUP, K_PREPROCESS, K_SCAN, K_EMIT, K_SORT, K_FWD, K_BWD, K_POSE, K_BACKPROJECT,
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
     K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_SSIM_FWD, K_SSIM_BWD, K_SSIM_SUM,
-    K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_SHAPE_ADAM, K_NUM
+    K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_SHAPE_ADAM,
+    K_SORT_XL, K_VIEW_FIN, K_BWD_LIST_POSE, K_BWD_LIST_VIEWS, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -75,7 +76,9 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "k_ssim_fwd",      "k_ssim_bwd",       "k_ssim_sum",
                                    "k_view_grads",    "k_preprocess_aniso",
                                    "k_composite_fwd_aniso", "k_composite_bwd_list_aniso",
-                                   "k_composite_bwd_aniso", "k_aniso_chain", "k_shape_adam"};
+                                   "k_composite_bwd_aniso", "k_aniso_chain", "k_shape_adam",
+                                   "k_sort_tiles_xl", "k_view_finalize",
+                                   "k_composite_bwd_list_pose", "k_composite_bwd_list_views"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -614,6 +617,9 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         k_sort_tiles_long<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, kSortSmemBig);
+    }
+    {
+        LaunchScope ls(c, K_SORT_XL, c->aux);
         k_sort_tiles_xl<<<std::min(n_tiles, 2 * c->n_sm), 512, kSortHistBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemBig, 0x7fffffff);
@@ -753,7 +759,8 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
         VT_CUDA(cudaMemsetAsync(c->accr, 0, sizeof(float) * T.n_total, stream), "grad acc reset");
     }
     if (c->used_lists) {
-        LaunchScope ls(c, K_BWD_LIST, stream);
+        LaunchScope ls(c, views ? K_BWD_LIST_VIEWS : (attr ? K_BWD_LIST : K_BWD_LIST_POSE),
+                       stream);
         auto kern = views ? k_composite_bwd_list_views
                           : (attr ? k_composite_bwd_list : k_composite_bwd_list_pose);
         kern<<<c->n_tiles, kBlockPix, 0, stream>>>(
@@ -791,9 +798,12 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
             c->view_part = static_cast<double *>(p);
             c->view_part_bytes = need;
         }
-        LaunchScope ls(c, K_VIEW_GRADS, stream);
-        k_view_grads<<<n_views * kViewChunks, kBlockPix, 0, stream>>>(T, c->accg, c->pose_copy,
-                                                                      c->view_part);
+        {
+            LaunchScope ls(c, K_VIEW_GRADS, stream);
+            k_view_grads<<<n_views * kViewChunks, kBlockPix, 0, stream>>>(T, c->accg, c->pose_copy,
+                                                                          c->view_part);
+        }
+        LaunchScope ls(c, K_VIEW_FIN, stream);
         k_view_finalize<<<(n_views + 63) / 64, 64, 0, stream>>>(T, c->pose_copy, c->view_part,
                                                               n_views);
     }
