@@ -453,14 +453,22 @@ def run_serving(dev, n_req: int = 300):
 
 
 def source_hash(files):
+    """Hash of the kernel's sources: whole files, or (file, marker) for the
+    part of a file before the first occurrence of marker."""
     h = hashlib.sha256()
     for f in files:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        f, marker = (f, None) if isinstance(f, str) else f
+        data = open(os.path.join(ROOT, f), "rb").read()
+        if marker is not None:
+            data = data[:data.index(marker.encode())]
+        h.update(data)
     return h.hexdigest()[:16]
 
 
+# the forward compositor is the part of vt_composite.cu before its backward section
+FWD_END = "\n// ---------------------------------------------------------------------------\n// Backward."
 KERNEL_SRC = {
-    "k_composite_fwd": ["paper_2506_02741_gb300/csrc/vt_composite.cu",
+    "k_composite_fwd": [("paper_2506_02741_gb300/csrc/vt_composite.cu", FWD_END),
                         "paper_2506_02741_gb300/csrc/vt_common.cuh"],
     "k_composite_bwd": ["paper_2506_02741_gb300/csrc/vt_composite.cu",
                         "paper_2506_02741_gb300/csrc/vt_common.cuh"],

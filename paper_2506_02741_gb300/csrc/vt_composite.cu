@@ -379,7 +379,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd_aniso(
 // Colour/opacity/radius gradients are summed over the warp with shuffles and
 // added to the section's buffers with one float atomic per value; the pose
 // needs only A = sum x g^T and s = sum g, kept per lane in FP32, summed over
-// the warp and the block in FP64 and written as one partial per tile.
+// the warp in float-float and over the block in FP64, and written as one
+// partial per tile.
 
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -393,6 +394,19 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
     return v;
 }
+
+// Warp sum of FP32 values in float-float (TwoSum-based additions, error
+// ~2^-47 of the sum of magnitudes): FP64 arithmetic is a narrow pipe on this
+// part, FP32 is not.  Every lane gets the same sum; to_double() widens it.
+__device__ __forceinline__ ff warp_sum_ff(float v) {
+    ff a{v, 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        a = ff_add(a, ff{__shfl_xor_sync(kFullMask, a.hi, o), __shfl_xor_sync(kFullMask, a.lo, o)});
+    return a;
+}
+
+__device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
 struct PoseAcc {
     float a[12];  // a[3*i + j] = sum x_i g_j ; a[9 + j] = sum g_j
@@ -604,15 +618,15 @@ __global__ void __launch_bounds__(256) k_attr_scatter(SecTable Tab, const float4
     if (S.d_radius) S.d_radius[li] += accr[g];
 }
 
-// Block sum of the per-lane pose terms in FP64, in a fixed order, written as
-// the tile's partial.
+// Block sum of the per-lane pose terms (warps in float-float, the block's
+// eight warp sums in FP64, fixed order), written as the tile's partial.
 __device__ __forceinline__ void write_pose_partial(const PoseAcc &acc, double (*s_pose)[12],
                                                    double *pose_partials, int tile) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-        const double v = warp_sum_d((double)acc.a[i]);
-        if (lane == 0) s_pose[warp][i] = v;
+        const ff v = warp_sum_ff(acc.a[i]);
+        if (lane == 0) s_pose[warp][i] = to_double(v);
     }
     __syncthreads();
     if (threadIdx.x < 12) {
@@ -959,7 +973,8 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_views(
 // R Sigma_c (Gc + Gc^T) for the covariance), and with the section's
 // scale / quaternion gradients Gk = M^T Gc M, dL/ds_i = 2 s_i (R^T Gk R)_ii,
 // dL/dR(q) = 2 Gk R(q) diag(s^2), chained through the normalisation of q.
-// FP32 per Gaussian; the pose sums in FP64 across the block.
+// FP32 per Gaussian; the pose sums in float-float across the warp and FP64
+// across the block.
 __global__ void __launch_bounds__(256) k_aniso_chain(SecTable Tab, Camera cam,
                                                      const ViewXf *views, const float4 *geo,
                                                      const float4 *app, const float4 *accg,
@@ -1111,8 +1126,8 @@ __global__ void __launch_bounds__(256) k_aniso_chain(SecTable Tab, Camera cam,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        const double v = warp_sum_d((double)acc[k]);
-        if (lane == 0) red[k][warp] = v;
+        const ff v = warp_sum_ff(acc[k]);
+        if (lane == 0) red[k][warp] = to_double(v);
     }
     __syncthreads();
     if (threadIdx.x < 12) {
@@ -1126,7 +1141,7 @@ __global__ void __launch_bounds__(256) k_aniso_chain(SecTable Tab, Camera cam,
 // Gaussians of one view are a contiguous range of their section (ids are in
 // (view, pixel) order).  k_view_grads: kViewChunks blocks per (section, view)
 // each sum g X_c^T and g over an equal share of the range (per thread in
-// FP32, across the block in FP64, fixed order), with g = dL/dx of the centre
+// FP32, across the warp in float-float and the block in FP64, fixed order), with g = dL/dx of the centre
 // in the target frame and X_c = D ((u - cx)/fx, (v - cy)/fy, 1), and write
 // per-Gaussian depth gradients dL/dD = (R g) . (R_k X_c / D) on the way;
 // k_view_finalize: one thread per view sums the chunk partials in order and
@@ -1205,8 +1220,8 @@ __global__ void __launch_bounds__(256) k_view_grads(SecTable Tab, const float4 *
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-        const double v = warp_sum_d((double)acc[i]);
-        if (lane == 0) red[i][warp] = v;
+        const ff v = warp_sum_ff(acc[i]);
+        if (lane == 0) red[i][warp] = to_double(v);
     }
     __syncthreads();
     if (threadIdx.x < 12) {

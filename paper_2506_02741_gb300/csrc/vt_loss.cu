@@ -106,8 +106,24 @@ __global__ void __launch_bounds__(256) k_visibility_counts(const float *depth, i
 
 __device__ __forceinline__ float sign_of(float e) { return e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f); }
 
+// |a - b| exactly, as a float-float: TwoSum gives a - b = s + e exactly, and
+// the rounded difference s carries the sign of the exact one (s = 0 only
+// when a = b).  A non-finite input makes the sum non-finite.
+__device__ __forceinline__ ff abs_diff(float a, float b) {
+    const ff d = ff_two_sum(a, -b);
+    return d.hi < 0.f ? ff{-d.hi, -d.lo} : d;
+}
+
+__device__ __forceinline__ ff shfl_xor_ff(ff a, int o) {
+    return ff{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
 // One thread per pixel: masks, |residuals| and the gradient of the masked L1
-// loss; per block the two FP64 sums (colour, depth) go to partials[2 b + i].
+// loss.  The residuals are exact float-floats, summed over the pixel's
+// channels and the warp in float-float (non-negative terms: ~2^-47 relative
+// per addition) and over the block's eight warps in FP64; per block the two
+// sums (colour, depth) go to partials[2 b + i].  FP64 arithmetic is a narrow
+// pipe on this part, so no per-pixel step uses it.
 __global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, const float *depth,
                                                    const float *sil, const float *obs_rgb,
                                                    const float *obs_depth, const uint8_t *visible,
@@ -116,7 +132,7 @@ __global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, 
                                                    double *partials) {
     __shared__ double s_sum[2][8];
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double sc = 0.0, sd = 0.0;
+    ff sc{0.f, 0.f}, sd{0.f, 0.f};
     if (p < P) {
         const bool valid = valid_depth(obs_depth[p]);
         const bool covered = !(sil_min >= 0.f) || sil[p] > sil_min;
@@ -126,23 +142,23 @@ __global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, 
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float r = rgb[c * P + p], o = obs_rgb[c * P + p];
-            if (m_c) sc += fabs((double)r - (double)o);
+            if (m_c) sc = ff_add(sc, abs_diff(r, o));
             if (d_rgb) d_rgb[c * P + p] = m_c ? gc * sign_of(r - o) : 0.f;
         }
         const float r = depth[p], o = obs_depth[p];
-        if (m_d) sd = fabs((double)r - (double)o);
+        if (m_d) sd = abs_diff(r, o);
         if (d_depth) d_depth[p] = m_d ? gd * sign_of(r - o) : 0.f;
     }
     if (!partials) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        sc = ff_add(sc, shfl_xor_ff(sc, o));
+        sd = ff_add(sd, shfl_xor_ff(sd, o));
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
-        s_sum[0][warp] = sc;
-        s_sum[1][warp] = sd;
+        s_sum[0][warp] = (double)sc.hi + (double)sc.lo;
+        s_sum[1][warp] = (double)sd.hi + (double)sd.lo;
     }
     __syncthreads();
     if (threadIdx.x < 2) {
