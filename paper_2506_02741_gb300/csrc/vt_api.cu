@@ -900,7 +900,7 @@ vt_status vt_masked_l1(vt_ctx *c, int32_t W, int32_t H, const float *rgb, const 
     }
     if (loss) {
         LaunchScope ls(c, K_L1_SUM, stream);
-        k_sum_partials<<<1, 1024, 0, stream>>>(c->loss_part, (int)nb, wc, wd, loss);
+        k_sum_partials<<<1, 256, 0, stream>>>(c->loss_part, (int)nb, wc, wd, loss);
     }
     VT_CUDA(cudaGetLastError(), "vt_masked_l1 launch");
     return VT_OK;
@@ -950,7 +950,7 @@ vt_status vt_ssim(vt_ctx *c, int32_t W, int32_t H, const float *rgb, const float
     }
     if (loss) {   // weight (1 - sum SSIM / n) = (weight / n) (count - sum SSIM)
         LaunchScope ls(c, K_SSIM_SUM, stream);
-        k_sum_partials<<<1, 1024, 0, stream>>>(part, (int)nb, -weight / n, weight / n, loss);
+        k_sum_partials<<<1, 256, 0, stream>>>(part, (int)nb, -weight / n, weight / n, loss);
     }
     if (d_rgb) {
         LaunchScope ls(c, K_SSIM_BWD, stream);

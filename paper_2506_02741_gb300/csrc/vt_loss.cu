@@ -168,27 +168,36 @@ __global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, 
     }
 }
 
-// One block: fixed-order sums of the per-block partials, then
+// One block: fixed-order sums of the per-block partials (strided per thread,
+// then the warp by shuffles, then the warps in order), then
 // L = wc * sum_c + wd * sum_d.
-__global__ void __launch_bounds__(1024) k_sum_partials(const double *partials, int n_blocks,
-                                                       double wc, double wd, double *loss) {
-    __shared__ double s[2][1024];
+__global__ void __launch_bounds__(256) k_sum_partials(const double *partials, int n_blocks,
+                                                      double wc, double wd, double *loss) {
+    __shared__ double s[2][8];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
         a += partials[2 * i];
         b += partials[2 * i + 1];
     }
-    s[0][threadIdx.x] = a;
-    s[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) {
-            s[0][threadIdx.x] += s[0][threadIdx.x + h];
-            s[1][threadIdx.x] += s[1][threadIdx.x + h];
-        }
-        __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    if (threadIdx.x == 0) *loss = __dadd_rn(__dmul_rn(wc, s[0][0]), __dmul_rn(wd, s[1][0]));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s[0][warp] = a;
+        s[1][warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            A += s[0][w];
+            B += s[1][w];
+        }
+        *loss = __dadd_rn(__dmul_rn(wc, A), __dmul_rn(wd, B));
+    }
 }
 
 }  // namespace vt

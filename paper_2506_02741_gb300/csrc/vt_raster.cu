@@ -7,11 +7,12 @@ namespace vt {
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
-// k_setup: one block per source view.  Thread 0 forms in FP64 the composite
-// transform of the view into the target camera, M = R^T R_k and
-// m = R^T (t_k - t), in the fixed operation order that defines the depth key
-// (each product and sum rounded on its own), plus the projection rows
-// U = fx M0 + cx M2, V = fy M1 + cy M2, Z = M2 and offsets as float-float.
+// k_setup: one block per source view.  Twelve threads form in FP64 the
+// composite transform of the view into the target camera, M = R^T R_k and
+// m = R^T (t_k - t), one entry each, in the fixed operation order that
+// defines the depth key (each product and sum rounded on its own), then the
+// projection rows U = fx M0 + cx M2, V = fy M1 + cy M2, Z = M2 and offsets as
+// float-float (FP64 is a narrow pipe: the twelve chains run side by side).
 // The block then fills the view's float-float tables, column u:
 // (U0, V0, Z0) * a_u and row v: (U1, V1, Z1) * b_v + (U2, V2, Z2), with
 // a_u = (u - cx_k)/fx_k, b_v = (v - cy_k)/fy_k, so that the projected centre's
@@ -19,49 +20,50 @@ constexpr unsigned kFull = 0xffffffffu;
 __global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const double *pose12,
                                                ViewXf *views, TabRow *tab, double *pose_copy) {
     __shared__ ff rows[9];  // U0 U1 U2 V0 V1 V2 Z0 Z1 Z2
+    __shared__ double sM[12];
     const int gv = blockIdx.x;
     int s = 0;
     for (int j = 1; j < T.n; ++j)
         if (gv >= T.s[j].view_base) s = j;
     const SecDesc &S = T.s[s];
     const int k = gv - S.view_base;
-    if (threadIdx.x == 0) {
+    const int i = threadIdx.x;
+    ViewXf &X = views[gv];
+    if (i < 12) {
         const double *R = pose12, *t = pose12 + 9;
         const double *Rk = S.poses + 12 * k, *tk = Rk + 9;
-        double M[9], m[3];
-        const double d0 = __dsub_rn(tk[0], t[0]), d1 = __dsub_rn(tk[1], t[1]),
-                     d2 = __dsub_rn(tk[2], t[2]);
-        for (int a = 0; a < 3; ++a) {
-            for (int b = 0; b < 3; ++b) {
-                double acc = __dmul_rn(R[0 * 3 + a], Rk[0 * 3 + b]);
-                acc = __dadd_rn(acc, __dmul_rn(R[1 * 3 + a], Rk[1 * 3 + b]));
-                acc = __dadd_rn(acc, __dmul_rn(R[2 * 3 + a], Rk[2 * 3 + b]));
-                M[a * 3 + b] = acc;
-            }
-            double acc = __dmul_rn(R[0 * 3 + a], d0);
-            acc = __dadd_rn(acc, __dmul_rn(R[1 * 3 + a], d1));
-            acc = __dadd_rn(acc, __dmul_rn(R[2 * 3 + a], d2));
-            m[a] = acc;
+        double acc;
+        if (i < 9) {   // M[a][b] = sum_c R[c][a] Rk[c][b]
+            const int a = i / 3, b = i % 3;
+            acc = __dmul_rn(R[0 * 3 + a], Rk[0 * 3 + b]);
+            acc = __dadd_rn(acc, __dmul_rn(R[1 * 3 + a], Rk[1 * 3 + b]));
+            acc = __dadd_rn(acc, __dmul_rn(R[2 * 3 + a], Rk[2 * 3 + b]));
+        } else {       // m[a] = sum_c R[c][a] (tk[c] - t[c])
+            const int a = i - 9;
+            acc = __dmul_rn(R[0 * 3 + a], __dsub_rn(tk[0], t[0]));
+            acc = __dadd_rn(acc, __dmul_rn(R[1 * 3 + a], __dsub_rn(tk[1], t[1])));
+            acc = __dadd_rn(acc, __dmul_rn(R[2 * 3 + a], __dsub_rn(tk[2], t[2])));
         }
-        ViewXf X;
-        for (int i = 0; i < 9; ++i) X.Mf[i] = __double2float_rn(M[i]);
-        for (int i = 0; i < 3; ++i) X.Mf[9 + i] = __double2float_rn(m[i]);
+        sM[i] = acc;
+        X.Mf[i] = __double2float_rn(acc);
+        if (gv == 0) pose_copy[i] = pose12[i];
+    }
+    __syncthreads();
+    if (i < 12) {
+        const double *M = sM, *m = sM + 9;
         const double fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
-        for (int b = 0; b < 3; ++b) {
-            rows[0 + b] = ff_from_double(fx * M[0 * 3 + b] + cx * M[2 * 3 + b]);
-            rows[3 + b] = ff_from_double(fy * M[1 * 3 + b] + cy * M[2 * 3 + b]);
-            rows[6 + b] = ff_from_double(M[2 * 3 + b]);
+        if (i < 9) {   // rows[r * 3 + b]: r = 0 U, 1 V, 2 Z
+            const int r = i / 3, b = i % 3;
+            const double v = r == 0 ? fx * M[0 * 3 + b] + cx * M[2 * 3 + b]
+                                    : (r == 1 ? fy * M[1 * 3 + b] + cy * M[2 * 3 + b] : M[2 * 3 + b]);
+            rows[i] = ff_from_double(v);
+        } else {
+            const int r = i - 9;
+            const double v = r == 0 ? fx * m[0] + cx * m[2] : (r == 1 ? fy * m[1] + cy * m[2] : m[2]);
+            const ff o = ff_from_double(v);
+            (r == 0 ? X.mu : (r == 1 ? X.mv : X.mz)) = make_float2(o.hi, o.lo);
+            if (r == 0) X.pad[0] = X.pad[1] = 0.f;
         }
-        ff mu = ff_from_double(fx * m[0] + cx * m[2]);
-        ff mv = ff_from_double(fy * m[1] + cy * m[2]);
-        ff mz = ff_from_double(m[2]);
-        X.mu = make_float2(mu.hi, mu.lo);
-        X.mv = make_float2(mv.hi, mv.lo);
-        X.mz = make_float2(mz.hi, mz.lo);
-        X.pad[0] = X.pad[1] = 0.f;
-        views[gv] = X;
-        if (gv == 0)
-            for (int i = 0; i < 12; ++i) pose_copy[i] = pose12[i];
     }
     __syncthreads();
     const int W = S.W, H = S.H;
