@@ -1,4 +1,4 @@
-"""Scene mapping driver (Sec. 3.4): learn the colour, opacity and radius of
+"""Scene mapping loop (Sec. 3.4): learn the colour, opacity and radius of
 the Gaussians of the current section by rendering it from the views of the
 section and minimising the L1 terms of Eq. 2,
 

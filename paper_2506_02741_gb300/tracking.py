@@ -1,4 +1,4 @@
-"""Camera tracking driver (Sec. 3.3): optimise the pose of the latest frame
+"""Camera tracking loop (Sec. 3.3): optimise the pose of the latest frame
 against fixed Gaussians by minimising Eq. 1,
 
     alpha * W |V - V'|_1 + beta * W |D - D'|_1,
