@@ -16,8 +16,6 @@ pre-tracking iterations.
 
 from __future__ import annotations
 
-import numpy as np
-
 from . import api
 from .tracking import PoseTracker
 

@@ -2,7 +2,6 @@
 of the SE(3) exponential and of Adam's first step."""
 
 import numpy as np
-import pytest
 
 from oracle import optim as op
 
