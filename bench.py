@@ -481,17 +481,21 @@ KERNEL_SRC = {
 }
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's
-    sources are unchanged since it was taken."""
+def capture_for(kernel, key="dram_bytes_per_launch"):
+    """A per-launch figure (DRAM bytes, warp instructions) from a committed
+    ncu summary, if the kernel's sources are unchanged since it was taken."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         e = t[WORKLOAD][kernel]
         if e.get("source_sha") == source_hash(KERNEL_SRC[kernel]):
-            return float(e["dram_bytes_per_launch"])
+            return float(e[key])
     except Exception:
         pass
     return None
+
+
+def traffic_for(kernel):
+    return capture_for(kernel, "dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------
@@ -705,6 +709,14 @@ def main():
     roof["kernel"] = dom
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["traffic"] = traffic_for(dom)
+    # the compositor's limit is instruction issue: the captured launch's warp
+    # instructions against 152 SMs x 4 schedulers x one instruction per clock
+    n_wi = capture_for(dom, "warp_instructions_per_launch")
+    if n_wi is not None:
+        issue_peak = 152 * 4 * 2.07e9
+        roof["issue"] = {"warp_instructions": n_wi, "achieved": n_wi / avg_s / 1e12,
+                         "peak": issue_peak / 1e12, "unit": "T warp-instructions/s",
+                         "frac": n_wi / avg_s / issue_peak}
     roof["timing"] = f"CUDA events around each launch, {n_prof} eager steps of the same workload"
 
     mapping = None

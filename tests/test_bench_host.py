@@ -50,6 +50,8 @@ def test_traffic_follows_the_forward_source(tmp_path):
     t = {b.WORKLOAD: {"k_composite_fwd": dict(entry, source_sha=entry_sha)}}
     json.dump(t, open(root / "profiles" / "traffic.json", "w"))
     assert b.traffic_for("k_composite_fwd") == float(entry["dram_bytes_per_launch"])
+    assert b.capture_for("k_composite_fwd", "warp_instructions_per_launch") == float(
+        entry["warp_instructions_per_launch"])
     comp = root / "paper_2506_02741_gb300" / "csrc" / "vt_composite.cu"
     text = comp.read_text()
     # an edit after the forward part (the backward) keeps it
@@ -58,6 +60,7 @@ def test_traffic_follows_the_forward_source(tmp_path):
     # an edit inside the forward part drops it
     comp.write_text("// leading comment\n" + text)
     assert b.traffic_for("k_composite_fwd") is None
+    assert b.capture_for("k_composite_fwd", "warp_instructions_per_launch") is None
     # so does an edit of the common header
     comp.write_text(text)
     hdr = root / "paper_2506_02741_gb300" / "csrc" / "vt_common.cuh"
