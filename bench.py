@@ -655,7 +655,7 @@ def main():
     # uploads its observed frame from pinned host memory (copy stream, double
     # buffered) and reads its pose + loss back into pinned memory; the host
     # takes each step's result while the next step computes
-    n_e2e = min(args.steps, 200)
+    n_e2e = min(args.steps, 1000)
     h_rgb = [torch.from_numpy(targets.rgb[i]).pin_memory() for i in range(args.frames)]
     h_d = [torch.from_numpy(targets.depth[i]).pin_memory() for i in range(args.frames)]
     h_start = [api.pose12(starts[i], "cpu").pin_memory() for i in range(args.frames)]
