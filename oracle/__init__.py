@@ -75,6 +75,14 @@ class _Grads(C.Structure):
                 ("twist_noise", C.c_double * 6), ("mat_noise", C.c_double * 12)]
 
 
+class _Lists(C.Structure):
+    _fields_ = [("ids", C.c_void_p), ("count", C.c_void_p), ("cap", C.c_int32)]
+
+
+class _Verdict(C.Structure):
+    _fields_ = [("status", C.c_void_p), ("flips", C.c_void_p), ("flip_margin", C.c_void_p)]
+
+
 class _View(C.Structure):
     _fields_ = [("depth", C.c_void_p), ("W", C.c_int32), ("H", C.c_int32),
                 ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
@@ -96,6 +104,12 @@ def lib():
             L.orc_backward.restype = C.c_int
             L.orc_backward.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                        C.c_void_p]
+            L.orc_render_lists.restype = C.c_int
+            L.orc_render_lists.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                           C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+            L.orc_backward_lists.restype = C.c_int
+            L.orc_backward_lists.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]
             L.orc_zkeys.restype = None
             L.orc_zkeys.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_backproject.restype = C.c_int64
@@ -243,6 +257,13 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
     section (n, 3) dL/dx of every centre in the target camera frame, abs_x
     its componentwise term magnitudes)."""
     secs, arr, keep = _sections(secs)
+    return _run_backward(secs, arr, pose, K, W, H, g_rgb, g_depth, g_sil,
+                         lambda a, cam, up, g: lib().orc_backward(
+                             C.byref(a), len(secs), C.byref(cam), int(bool(binned)),
+                             C.byref(up), C.byref(g)))
+
+
+def _run_backward(secs, arr, pose, K, W, H, g_rgb, g_depth, g_sil, call):
     ups = [None if g is None else np.ascontiguousarray(g, np.float64) for g in (g_rgb, g_depth, g_sil)]
     up = _Upstream(*[_ptr(u) for u in ups])
     dcol = [np.zeros((s.n, 3)) for s in secs]
@@ -257,14 +278,58 @@ def backward(secs, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None, binned=T
             for lst in (dcol, dop, drad, acol, aop, arad, dx, ax)]
     g = _Grads(*[C.cast(a, C.c_void_p) for a in arrs])
     cam = _camera(pose, K, W, H)
-    rc = lib().orc_backward(C.byref(arr), len(secs), C.byref(cam), int(bool(binned)), C.byref(up),
-                            C.byref(g))
+    rc = call(arr, cam, up, g)
     if rc != 0:
         raise RuntimeError("oracle backward failed")
     return dict(colour=dcol, opacity=dop, radius=drad, twist=np.array(g.twist[:]),
                 mat=np.array(g.mat[:]), abs_colour=acol, abs_opacity=aop, abs_radius=arad,
                 twist_noise=np.array(g.twist_noise[:]), mat_noise=np.array(g.mat_noise[:]),
                 x=dx, abs_x=ax)
+
+
+def _lists(ids, count, H, W):
+    ids = np.ascontiguousarray(ids, np.int64).reshape(H, W, -1)
+    count = np.ascontiguousarray(count, np.int32).reshape(H, W)
+    return ids, count, _Lists(_ptr(ids), _ptr(count), int(ids.shape[2]))
+
+
+def render_lists(secs, pose, K, W, H, ids, count, tau_incl=1e-5, tau_T=2e-4):
+    """Composite along given per-pixel lists of added Gaussians (ids (H, W,
+    cap) int64, front to back, count (H, W) entries each; ids are positions
+    in the concatenation of the sections) and check them against the
+    definition.  Returns the images of render() (rgb, depth, sil, T_final,
+    n_added) evaluated in FP64 along the lists, and per pixel ``status``
+    (0: the definition's list up to decisions within tau_incl / tau_T
+    (relative) of their thresholds; 1: not a list of the definition at all;
+    2: a decision differs by more than the margins), ``flips`` (decisions
+    taken otherwise than in FP64) and ``flip_margin`` (the largest relative
+    margin among them)."""
+    secs, arr, keep = _sections(secs)
+    ids, count, lst = _lists(ids, count, H, W)
+    out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), sil=np.zeros((H, W)),
+               T_final=np.zeros((H, W)), n_added=np.zeros((H, W), np.int32),
+               status=np.zeros((H, W), np.int32), flips=np.zeros((H, W), np.int32),
+               flip_margin=np.zeros((H, W)))
+    img = _Image(_ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["sil"]), _ptr(out["T_final"]),
+                 _ptr(out["n_added"]), None, None, None, None, 0)
+    vd = _Verdict(_ptr(out["status"]), _ptr(out["flips"]), _ptr(out["flip_margin"]))
+    cam = _camera(pose, K, W, H)
+    rc = lib().orc_render_lists(C.byref(arr), len(secs), C.byref(cam), C.byref(lst),
+                                float(tau_incl), float(tau_T), C.byref(img), C.byref(vd))
+    if rc != 0:
+        raise RuntimeError("oracle render_lists failed")
+    return out
+
+
+def backward_lists(secs, pose, K, W, H, ids, count, g_rgb=None, g_depth=None, g_sil=None):
+    """backward() with each pixel's added Gaussians taken from the given
+    lists (as render_lists) instead of from the FP64 decisions."""
+    secs, arr, keep = _sections(secs)
+    ids, count, lst = _lists(ids, count, H, W)
+    return _run_backward(secs, arr, pose, K, W, H, g_rgb, g_depth, g_sil,
+                         lambda a, cam, up, g: lib().orc_backward_lists(
+                             C.byref(a), len(secs), C.byref(cam), C.byref(lst), C.byref(up),
+                             C.byref(g)))
 
 
 def view_pose_grads(sec: Section, pose, d_x):

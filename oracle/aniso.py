@@ -227,6 +227,124 @@ def render(sec: Section, scale, quat, pose, K, W, H, eps: float = EPS_LOWPASS,
     return out
 
 
+def render_lists(sec: Section, scale, quat, pose, K, W, H, ids, count, tau_incl=1e-4,
+                 tau_T=2e-4, eps: float = EPS_LOWPASS, keep: bool = False):
+    """Composite along given per-pixel lists of added Gaussians and check
+    them against the definition, as the isotropic oracle's render_lists
+    does: ids (H, W, cap) int (front to back, positions in the section),
+    count (H, W).  Where an inclusion test or the termination test lies
+    within the rounding of a lower precision of its threshold both outcomes
+    are correct; a pixel's list is accepted (status 0) if it differs from
+    the FP64 decisions only at decisions within tau_incl / tau_T (relative)
+    of their thresholds: before its last entry every candidate is added or
+    excluded, after it the walk stops at a candidate whose inclusion ends
+    it, or excludes it.  status 1: no list of the definition (key order, a
+    repeated id, an id that is no candidate of the pixel); 2: a decision
+    differs by more than the margins.  Returns rgb, depth, sil, T_final,
+    n_added along the lists, status, flips, flip_margin and, with keep, the
+    records backward() replays."""
+    geo = _geometry(sec, scale, quat, pose, K, W, H, eps)
+    n = sec.n
+    P = W * H
+    ids = np.asarray(ids, np.int64).reshape(P, -1)
+    count = np.asarray(count, np.int64).reshape(P)
+    if ids.shape[1] == 0:
+        ids = np.full((P, 1), -1, np.int64)
+    cap = ids.shape[1]
+    with np.errstate(invalid="ignore"):
+        ex = np.sqrt(Q_MAX * 1.001 * geo["S2"][:, 0, 0])
+        ey = np.sqrt(Q_MAX * 1.001 * geo["S2"][:, 1, 1])
+        meets = ((np.ceil(geo["uc"] - ex) <= W - 1) & (np.floor(geo["uc"] + ex) >= 0) &
+                 (np.ceil(geo["vc"] - ey) <= H - 1) & (np.floor(geo["vc"] + ey) >= 0))
+    order = [i for i in np.lexsort((np.arange(n), geo["key"])) if (geo["valid"] & meets)[i]]
+    status = np.where((count < 0) | (count > cap), 1, 0).astype(np.int32)
+    # the lists themselves: valid ids in strictly increasing (key, id) order
+    j = np.arange(cap)[None, :]
+    used = j < count[:, None]
+    good = (ids >= 0) & (ids < n)
+    safe = np.where(good, ids, 0)
+    status[np.any(used & ~(good & geo["valid"][safe]), axis=1)] = 1
+    k = geo["key"][safe]
+    incr = (k[:, :-1] < k[:, 1:]) | ((k[:, :-1] == k[:, 1:]) & (safe[:, :-1] < safe[:, 1:]))
+    status[np.any(used[:, 1:] & ~incr, axis=1)] = 1
+    flips = np.zeros(P, np.int32)
+    fmax = np.zeros(P)
+    ptr = np.zeros(P, np.int64)
+    resolved = np.zeros(P, bool)
+    T = np.ones(P)
+    rgb = np.zeros((3, P))
+    dep = np.zeros(P)
+    sil = np.zeros(P)
+    colour = np.asarray(sec.colour, np.float64).reshape(-1, 3)
+    opac = np.asarray(sec.opacity, np.float64)
+    recs = []
+
+    def flip(mask, m, tau, p):
+        ok = mask & (m < tau)
+        flips[p[ok]] += 1
+        fmax[p[ok]] = np.maximum(fmax[p[ok]], m[ok])
+        status[p[mask & ~(m < tau)]] = 2
+
+    for i in order:
+        if not np.isfinite(geo["Q"][i]).all() or geo["z"][i] <= 0:
+            continue
+        b = _box(geo, i, W, H)
+        if b is None:
+            continue
+        u0, u1, v0, v1 = b
+        uu, vv = np.meshgrid(np.arange(u0, u1 + 1), np.arange(v0, v1 + 1))
+        p = (vv * W + uu).reshape(-1)
+        du = uu.reshape(-1) - geo["uc"][i]
+        dv = vv.reshape(-1) - geo["vc"][i]
+        Q = geo["Q"][i]
+        q = Q[0, 0] * du * du + (Q[0, 1] + Q[1, 0]) * du * dv + Q[1, 1] * dv * dv
+        G = np.exp(-0.5 * q)
+        ah = opac[i] * G
+        pq, pa = q <= Q_MAX, ah >= A_MIN
+        mq, ma = np.abs(q - Q_MAX) / Q_MAX, np.abs(ah - A_MIN) / A_MIN
+        inc = pq & pa
+        m_in = np.where(inc, np.minimum(mq, ma),
+                        np.maximum(np.where(pq, 0.0, mq), np.where(pa, 0.0, ma)))
+        band = q <= Q_MAX * 1.001
+        al = np.minimum(A_CLAMP, ah)
+        Tn = T[p] * (1.0 - al)
+        mT = np.abs(Tn - T_MIN) / T_MIN
+        phase_a = ptr[p] < count[p]
+        nxt = ids[p, np.minimum(ptr[p], cap - 1)]
+        listed = phase_a & (nxt == i)
+        active = (status[p] == 0) & ~resolved[p]
+        status[p[active & listed & ~band]] = 1
+        add = active & listed & band
+        flip(add & ~inc, m_in, tau_incl, p)
+        flip(add & (Tn < T_MIN), mT, tau_T, p)
+        flip(active & phase_a & ~listed & inc, m_in, tau_incl, p)
+        after = active & ~phase_a & band
+        stop = after & (inc | (m_in < tau_incl)) & ((Tn < T_MIN) | (mT < tau_T))
+        flip(stop & ~inc, m_in, np.inf, p)
+        flip(stop & ~(Tn < T_MIN), mT, np.inf, p)
+        resolved[p[stop]] = True
+        flip(after & ~stop & inc, m_in, tau_incl, p)
+        pi = p[add]
+        Ti = T[pi]
+        w = al[add] * Ti
+        rgb[:, pi] += colour[i][:, None] * w
+        dep[pi] += geo["z"][i] * w
+        sil[pi] += w
+        T[pi] = Tn[add]
+        ptr[pi] += 1
+        if keep and len(pi):
+            recs.append((i, pi, Ti, al[add], ah[add], q[add], du[add], dv[add]))
+    status[(status == 0) & (ptr < count)] = 1
+    out = dict(rgb=rgb.reshape(3, H, W), depth=dep.reshape(H, W), sil=sil.reshape(H, W),
+               T_final=T.reshape(H, W), n_added=count.reshape(H, W).astype(np.int32),
+               status=status.reshape(H, W), flips=flips.reshape(H, W),
+               flip_margin=fmax.reshape(H, W))
+    if keep:
+        out["recs"] = recs
+        out["geo"] = geo
+    return out
+
+
 def backward(sec: Section, scale, quat, pose, K, W, H, g_rgb=None, g_depth=None, g_sil=None,
              eps: float = EPS_LOWPASS, fwd=None):
     """Gradients of <g_rgb, rgb> + <g_depth, depth> + <g_sil, sil> with the

@@ -388,6 +388,147 @@ static void atomic_add(double *p, double v) {
     *p += v;
 }
 
+/* Pose sums of a thread (or of the whole image). */
+typedef struct {
+    double tw[6], mt[12], nz[18];
+} pose_sums;
+
+/* Gradient terms of one pixel whose added Gaussians are e[0..k) front to
+ * back (alpha, q, ahat, exp(-q/2) and the offsets e_x, e_y filled in) with
+ * final transmittance Tfin; Tb and wb are scratch of k doubles. */
+static void pixel_grads(const gpre *g, const double *R, double px, double py, const double gC[3],
+                        double gD, double gS, const inc_t *e_all, int64_t k, double Tfin,
+                        double *Tb, double *wb, orc_grads *gr, pose_sums *ps) {
+    double T = 1.0;
+    for (int64_t j = 0; j < k; ++j) {   /* transmittance before each, weights */
+        Tb[j] = T;
+        wb[j] = e_all[j].alpha * T;
+        T = T * (1.0 - e_all[j].alpha);
+    }
+    double A[3] = {0, 0, 0}, Bd = 0;    /* sums over the Gaussians behind */
+    double pm[18] = {0};                 /* componentwise pose magnitudes */
+    for (int64_t j = k - 1; j >= 0; --j) {
+        const inc_t *e = &e_all[j];
+        const gpre *G = &g[e->gi];
+        double w = wb[j], al = e->alpha, z = G->x[2];
+        double dal = Tb[j] * (gC[0] * G->c[0] + gC[1] * G->c[1] + gC[2] * G->c[2] + gD * z) -
+                     (gC[0] * A[0] + gC[1] * A[1] + gC[2] * A[2] + gD * Bd) / (1.0 - al) +
+                     gS * Tfin / (1.0 - al);
+        double dq = 0.0, dop = 0.0;
+        if (e->ahat < ORC_A_CLAMP) {
+            dop = dal * e->G;
+            dq = dal * (-0.5 * e->ahat);
+        }
+        double r = G->r;
+        double dr = dq * (-2.0 * e->q / r);
+        double gx = dq * (-2.0 * e->ex / (r * r));
+        double gy = dq * (-2.0 * e->ey / (r * r));
+        double gz = dq * (2.0 * (px * e->ex + py * e->ey) / (r * r)) + gD * w;
+        double **dcol = gr->d_colour, **dop_ = gr->d_opacity, **drad = gr->d_radius;
+        if (dcol && dcol[G->sec]) {
+            atomic_add(&dcol[G->sec][3 * G->local + 0], gC[0] * w);
+            atomic_add(&dcol[G->sec][3 * G->local + 1], gC[1] * w);
+            atomic_add(&dcol[G->sec][3 * G->local + 2], gC[2] * w);
+        }
+        if (dop_ && dop_[G->sec]) atomic_add(&dop_[G->sec][G->local], dop);
+        if (drad && drad[G->sec]) atomic_add(&drad[G->sec][G->local], dr);
+        /* Componentwise magnitude of every per-pixel term: the sum of the
+         * absolute values of the products the derivative formula adds,
+         * which bounds the floating-point error of evaluating the term
+         * (the term itself can cancel to far less). */
+        double mal = Tb[j] * (fabs(gC[0] * G->c[0]) + fabs(gC[1] * G->c[1]) +
+                              fabs(gC[2] * G->c[2]) + fabs(gD * z)) +
+                     (fabs(gC[0] * A[0]) + fabs(gC[1] * A[1]) + fabs(gC[2] * A[2]) +
+                      fabs(gD * Bd) + fabs(gS * Tfin)) / (1.0 - al);
+        if (gr->a_colour && gr->a_colour[G->sec])
+            for (int c = 0; c < 3; ++c)
+                atomic_add(&gr->a_colour[G->sec][3 * G->local + c], fabs(gC[c] * w));
+        if (e->ahat < ORC_A_CLAMP) {
+            if (gr->a_opacity && gr->a_opacity[G->sec])
+                atomic_add(&gr->a_opacity[G->sec][G->local], mal * e->G);
+            if (gr->a_radius && gr->a_radius[G->sec])
+                atomic_add(&gr->a_radius[G->sec][G->local], mal * 0.5 * e->ahat * 2.0 * e->q / r);
+        }
+        double gv[3] = {gx, gy, gz};
+        const double *x = G->x;
+        if (gr->d_x && gr->d_x[G->sec])
+            for (int a = 0; a < 3; ++a) atomic_add(&gr->d_x[G->sec][3 * G->local + a], gv[a]);
+        if (gr->a_x && gr->a_x[G->sec]) {
+            /* |dq| <= ahat / 2 mal below the clamp, 0 above */
+            const double mq = e->ahat < ORC_A_CLAMP ? 0.5 * e->ahat * mal : 0.0;
+            const double ax[3] = {mq * 2.0 * fabs(e->ex) / (r * r), mq * 2.0 * fabs(e->ey) / (r * r),
+                                  mq * 2.0 * (fabs(px * e->ex) + fabs(py * e->ey)) / (r * r) +
+                                      fabs(gD * w)};
+            for (int a = 0; a < 3; ++a) atomic_add(&gr->a_x[G->sec][3 * G->local + a], ax[a]);
+        }
+        ps->tw[0] -= gx;
+        ps->tw[1] -= gy;
+        ps->tw[2] -= gz;
+        ps->tw[3] += gv[1] * x[2] - gv[2] * x[1];
+        ps->tw[4] += gv[2] * x[0] - gv[0] * x[2];
+        ps->tw[5] += gv[0] * x[1] - gv[1] * x[0];
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) ps->mt[3 * b + a] += G->d[b] * gv[a];
+        for (int b = 0; b < 3; ++b)
+            ps->mt[9 + b] -= R[3 * b + 0] * gx + R[3 * b + 1] * gy + R[3 * b + 2] * gz;
+        /* magnitudes: |g| per axis from its products, then the same
+         * sums as above with every product taken absolute */
+        double ag[3] = {fabs(gx), fabs(gy),
+                        fabs(dq * 2.0 * px * e->ex / (r * r)) +
+                            fabs(dq * 2.0 * py * e->ey / (r * r)) + fabs(gD * w)};
+        pm[0] += ag[0];
+        pm[1] += ag[1];
+        pm[2] += ag[2];
+        pm[3] += ag[1] * fabs(x[2]) + ag[2] * fabs(x[1]);
+        pm[4] += ag[2] * fabs(x[0]) + ag[0] * fabs(x[2]);
+        pm[5] += ag[0] * fabs(x[1]) + ag[1] * fabs(x[0]);
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) pm[6 + 3 * b + a] += fabs(G->d[b]) * ag[a];
+        for (int b = 0; b < 3; ++b)
+            pm[15 + b] += fabs(R[3 * b + 0]) * ag[0] + fabs(R[3 * b + 1]) * ag[1] +
+                          fabs(R[3 * b + 2]) * ag[2];
+        A[0] += w * G->c[0];
+        A[1] += w * G->c[1];
+        A[2] += w * G->c[2];
+        Bd += w * z;
+    }
+    for (int i = 0; i < 18; ++i) ps->nz[i] += (double)k * pm[i] * pm[i];
+}
+
+static int upstream_at(const orc_upstream *up, int64_t HW, int64_t p, double gC[3], double *gD,
+                       double *gS) {
+    gC[0] = gC[1] = gC[2] = 0.0;
+    *gD = *gS = 0.0;
+    if (up->g_rgb) {
+        gC[0] = up->g_rgb[p];
+        gC[1] = up->g_rgb[HW + p];
+        gC[2] = up->g_rgb[2 * HW + p];
+    }
+    if (up->g_depth) *gD = up->g_depth[p];
+    if (up->g_sil) *gS = up->g_sil[p];
+    return !(gC[0] == 0 && gC[1] == 0 && gC[2] == 0 && *gD == 0 && *gS == 0);
+}
+
+static void finish_grads(const pose_sums *tot, orc_grads *gr) {
+    memcpy(gr->twist, tot->tw, sizeof tot->tw);
+    memcpy(gr->mat, tot->mt, sizeof tot->mt);
+    for (int i = 0; i < 6; ++i) gr->twist_noise[i] = sqrt(tot->nz[i]);
+    for (int i = 0; i < 12; ++i) gr->mat_noise[i] = sqrt(tot->nz[6 + i]);
+}
+
+static void add_sums(pose_sums *tot, const pose_sums *ps) {
+    for (int i = 0; i < 6; ++i) tot->tw[i] += ps->tw[i];
+    for (int i = 0; i < 12; ++i) tot->mt[i] += ps->mt[i];
+    for (int i = 0; i < 18; ++i) tot->nz[i] += ps->nz[i];
+}
+
+static void grow(double **Tb, double **wb, int64_t *cap, int64_t k) {
+    if (k <= *cap) return;
+    *cap = k;
+    *Tb = (double *)realloc(*Tb, sizeof(double) * (size_t)k);
+    *wb = (double *)realloc(*wb, sizeof(double) * (size_t)k);
+}
+
 int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int binned,
                  const orc_upstream *up, orc_grads *gr) {
     int64_t n = total_n(secs, n_secs);
@@ -397,27 +538,19 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
     bins_t B = {0};
     if (binned) build_bins(g, n, cam, &B);
     int64_t HW = (int64_t)cam->W * cam->H;
-    const double *R = cam->pose;
-    double tw[6] = {0}, mt[12] = {0}, nz[18] = {0};
+    pose_sums tot = {{0}};
 #pragma omp parallel num_threads(orc_get_threads())
     {
         scratch_t sc = {0};
-        double ltw[6] = {0}, lmt[12] = {0}, lnz[18] = {0};
+        pose_sums ps = {{0}};
         double *Tb = NULL, *wb = NULL;
         int64_t wcap = 0;
 #pragma omp for schedule(dynamic, 1)
         for (int v = 0; v < cam->H; ++v) {
             for (int u = 0; u < cam->W; ++u) {
                 int64_t p = (int64_t)v * cam->W + u;
-                double gC[3] = {0, 0, 0}, gD = 0, gS = 0;
-                if (up->g_rgb) {
-                    gC[0] = up->g_rgb[p];
-                    gC[1] = up->g_rgb[HW + p];
-                    gC[2] = up->g_rgb[2 * HW + p];
-                }
-                if (up->g_depth) gD = up->g_depth[p];
-                if (up->g_sil) gS = up->g_sil[p];
-                if (gC[0] == 0 && gC[1] == 0 && gC[2] == 0 && gD == 0 && gS == 0) continue;
+                double gC[3], gD, gS;
+                if (!upstream_at(up, HW, p, gC, &gD, &gS)) continue;
                 double px, py, margin = INFINITY, mc = INFINITY, Tfin;
                 pixel_coords(cam, u, v, &px, &py);
                 const int64_t *cand = NULL;
@@ -429,128 +562,263 @@ int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int
                 }
                 int64_t m = collect(g, cand, ncand, px, py, &sc, &margin, &mc);
                 int64_t k = walk(sc.buf, m, &Tfin, &margin);
-                if (k > wcap) {
-                    wcap = k;
-                    Tb = (double *)realloc(Tb, sizeof(double) * (size_t)wcap);
-                    wb = (double *)realloc(wb, sizeof(double) * (size_t)wcap);
-                }
-                double T = 1.0;
-                for (int64_t j = 0; j < k; ++j) {   /* transmittance before each, weights */
-                    Tb[j] = T;
-                    wb[j] = sc.buf[j].alpha * T;
-                    T = T * (1.0 - sc.buf[j].alpha);
-                }
-                double A[3] = {0, 0, 0}, Bd = 0;    /* sums over the Gaussians behind */
-                double pm[18] = {0};                 /* componentwise pose magnitudes */
-                for (int64_t j = k - 1; j >= 0; --j) {
-                    const inc_t *e = &sc.buf[j];
-                    const gpre *G = &g[e->gi];
-                    const orc_section *S = &secs[G->sec];
-                    double w = wb[j], al = e->alpha, z = G->x[2];
-                    double dal = Tb[j] * (gC[0] * G->c[0] + gC[1] * G->c[1] + gC[2] * G->c[2] + gD * z) -
-                                 (gC[0] * A[0] + gC[1] * A[1] + gC[2] * A[2] + gD * Bd) / (1.0 - al) +
-                                 gS * Tfin / (1.0 - al);
-                    double dq = 0.0, dop = 0.0;
-                    if (e->ahat < ORC_A_CLAMP) {
-                        dop = dal * e->G;
-                        dq = dal * (-0.5 * e->ahat);
-                    }
-                    double r = G->r;
-                    double dr = dq * (-2.0 * e->q / r);
-                    double gx = dq * (-2.0 * e->ex / (r * r));
-                    double gy = dq * (-2.0 * e->ey / (r * r));
-                    double gz = dq * (2.0 * (px * e->ex + py * e->ey) / (r * r)) + gD * w;
-                    (void)S;
-                    double **dcol = gr->d_colour, **dop_ = gr->d_opacity, **drad = gr->d_radius;
-                    if (dcol && dcol[G->sec]) {
-                        atomic_add(&dcol[G->sec][3 * G->local + 0], gC[0] * w);
-                        atomic_add(&dcol[G->sec][3 * G->local + 1], gC[1] * w);
-                        atomic_add(&dcol[G->sec][3 * G->local + 2], gC[2] * w);
-                    }
-                    if (dop_ && dop_[G->sec]) atomic_add(&dop_[G->sec][G->local], dop);
-                    if (drad && drad[G->sec]) atomic_add(&drad[G->sec][G->local], dr);
-                    /* Componentwise magnitude of every per-pixel term: the sum of the
-                     * absolute values of the products the derivative formula adds,
-                     * which bounds the floating-point error of evaluating the term
-                     * (the term itself can cancel to far less). */
-                    double mal = Tb[j] * (fabs(gC[0] * G->c[0]) + fabs(gC[1] * G->c[1]) +
-                                          fabs(gC[2] * G->c[2]) + fabs(gD * z)) +
-                                 (fabs(gC[0] * A[0]) + fabs(gC[1] * A[1]) + fabs(gC[2] * A[2]) +
-                                  fabs(gD * Bd) + fabs(gS * Tfin)) / (1.0 - al);
-                    if (gr->a_colour && gr->a_colour[G->sec])
-                        for (int c = 0; c < 3; ++c)
-                            atomic_add(&gr->a_colour[G->sec][3 * G->local + c], fabs(gC[c] * w));
-                    if (e->ahat < ORC_A_CLAMP) {
-                        if (gr->a_opacity && gr->a_opacity[G->sec])
-                            atomic_add(&gr->a_opacity[G->sec][G->local], mal * e->G);
-                        if (gr->a_radius && gr->a_radius[G->sec])
-                            atomic_add(&gr->a_radius[G->sec][G->local],
-                                       mal * 0.5 * e->ahat * 2.0 * e->q / r);
-                    }
-                    double gv[3] = {gx, gy, gz};
-                    const double *x = G->x;
-                    if (gr->d_x && gr->d_x[G->sec])
-                        for (int a = 0; a < 3; ++a)
-                            atomic_add(&gr->d_x[G->sec][3 * G->local + a], gv[a]);
-                    if (gr->a_x && gr->a_x[G->sec]) {
-                        /* |dq| <= ahat / 2 mal below the clamp, 0 above */
-                        const double mq = e->ahat < ORC_A_CLAMP ? 0.5 * e->ahat * mal : 0.0;
-                        const double ax[3] = {
-                            mq * 2.0 * fabs(e->ex) / (r * r), mq * 2.0 * fabs(e->ey) / (r * r),
-                            mq * 2.0 * (fabs(px * e->ex) + fabs(py * e->ey)) / (r * r) +
-                                fabs(gD * w)};
-                        for (int a = 0; a < 3; ++a)
-                            atomic_add(&gr->a_x[G->sec][3 * G->local + a], ax[a]);
-                    }
-                    ltw[0] -= gx;
-                    ltw[1] -= gy;
-                    ltw[2] -= gz;
-                    ltw[3] += gv[1] * x[2] - gv[2] * x[1];
-                    ltw[4] += gv[2] * x[0] - gv[0] * x[2];
-                    ltw[5] += gv[0] * x[1] - gv[1] * x[0];
-                    for (int b = 0; b < 3; ++b)
-                        for (int a = 0; a < 3; ++a) lmt[3 * b + a] += G->d[b] * gv[a];
-                    for (int b = 0; b < 3; ++b)
-                        lmt[9 + b] -= R[3 * b + 0] * gx + R[3 * b + 1] * gy + R[3 * b + 2] * gz;
-                    /* magnitudes: |g| per axis from its products, then the same
-                     * sums as above with every product taken absolute */
-                    double ag[3] = {fabs(gx), fabs(gy),
-                                    fabs(dq * 2.0 * px * e->ex / (r * r)) +
-                                        fabs(dq * 2.0 * py * e->ey / (r * r)) + fabs(gD * w)};
-                    pm[0] += ag[0];
-                    pm[1] += ag[1];
-                    pm[2] += ag[2];
-                    pm[3] += ag[1] * fabs(x[2]) + ag[2] * fabs(x[1]);
-                    pm[4] += ag[2] * fabs(x[0]) + ag[0] * fabs(x[2]);
-                    pm[5] += ag[0] * fabs(x[1]) + ag[1] * fabs(x[0]);
-                    for (int b = 0; b < 3; ++b)
-                        for (int a = 0; a < 3; ++a) pm[6 + 3 * b + a] += fabs(G->d[b]) * ag[a];
-                    for (int b = 0; b < 3; ++b)
-                        pm[15 + b] += fabs(R[3 * b + 0]) * ag[0] + fabs(R[3 * b + 1]) * ag[1] +
-                                      fabs(R[3 * b + 2]) * ag[2];
-                    A[0] += w * G->c[0];
-                    A[1] += w * G->c[1];
-                    A[2] += w * G->c[2];
-                    Bd += w * z;
-                }
-                for (int i = 0; i < 18; ++i) lnz[i] += (double)k * pm[i] * pm[i];
+                grow(&Tb, &wb, &wcap, k);
+                pixel_grads(g, cam->pose, px, py, gC, gD, gS, sc.buf, k, Tfin, Tb, wb, gr, &ps);
             }
         }
 #pragma omp critical
-        {
-            for (int i = 0; i < 6; ++i) tw[i] += ltw[i];
-            for (int i = 0; i < 12; ++i) mt[i] += lmt[i];
-            for (int i = 0; i < 18; ++i) nz[i] += lnz[i];
-        }
+        add_sums(&tot, &ps);
         free(sc.buf);
         free(Tb);
         free(wb);
     }
-    memcpy(gr->twist, tw, sizeof tw);
-    memcpy(gr->mat, mt, sizeof mt);
-    for (int i = 0; i < 6; ++i) gr->twist_noise[i] = sqrt(nz[i]);
-    for (int i = 0; i < 12; ++i) gr->mat_noise[i] = sqrt(nz[6 + i]);
+    finish_grads(&tot, gr);
     if (binned) free_bins(&B);
+    free(g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compositing along given decisions.  Where a decision of the definition
+ * (an inclusion test, the termination test) lies within the rounding of
+ * another precision of its threshold, both outcomes are correct results of
+ * the method.  orc_render_lists takes the per-pixel lists of added Gaussians
+ * another implementation reports, checks that they differ from the FP64
+ * decisions only at such decisions, and composites along them in FP64, so
+ * that the values can be compared at every pixel. */
+
+/* One candidate of a pixel: every valid Gaussian of its bin whose q lies in
+ * the band q <= 9 * 1.001, with its FP64 decision and the relative margin a
+ * flip of that decision needs. */
+typedef struct {
+    float zkey;
+    int64_t id;
+    double alpha, m_in;
+    int inc;
+} cand_t;
+
+static int cmp_cand(const void *a, const void *b) {
+    const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+    if (x->zkey < y->zkey) return -1;
+    if (x->zkey > y->zkey) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* key order of two Gaussians: (z_key, id) */
+static int key_less(const gpre *a, const gpre *b) {
+    return a->zkey < b->zkey || (a->zkey == b->zkey && a->id < b->id);
+}
+
+/* FP64 quantities of Gaussian G at the pixel (px, py). */
+static void pair_eval(const gpre *G, double px, double py, inc_t *e) {
+    e->zkey = G->zkey;
+    e->id = G->id;
+    e->ex = px * G->x[2] - G->x[0];
+    e->ey = py * G->x[2] - G->x[1];
+    e->q = (e->ex * e->ex + e->ey * e->ey) / (G->r * G->r);
+    e->G = exp(-0.5 * e->q);
+    e->ahat = G->o * e->G;
+    e->alpha = e->ahat < ORC_A_CLAMP ? e->ahat : ORC_A_CLAMP;
+}
+
+/* Inclusion decision of a pair and the relative margin a flip needs: an
+ * included pair flips when either test does (the smaller margin), an
+ * excluded one only when every failing test does (the larger). */
+static int inclusion(const inc_t *e, double *m_in) {
+    const double mq = fabs(e->q - ORC_Q_MAX) / ORC_Q_MAX;
+    const double ma = fabs(e->ahat - ORC_A_MIN) / ORC_A_MIN;
+    const int pq = e->q <= ORC_Q_MAX, pa = e->ahat >= ORC_A_MIN;
+    if (pq && pa) {
+        *m_in = mind(mq, ma);
+        return 1;
+    }
+    *m_in = (pq ? 0.0 : mq) > (pa ? 0.0 : ma) ? (pq ? 0.0 : mq) : (pa ? 0.0 : ma);
+    return 0;
+}
+
+static void note_flip(int32_t *flips, double *fmax, double m) {
+    ++*flips;
+    if (m > *fmax) *fmax = m;
+}
+
+int orc_render_lists(const orc_section *secs, int n_secs, const orc_camera *cam,
+                     const orc_lists *L, double tau_incl, double tau_T, orc_image *out,
+                     orc_verdict *vd) {
+    int64_t n = total_n(secs, n_secs);
+    gpre *g = (gpre *)malloc(sizeof(gpre) * (size_t)(n > 0 ? n : 1));
+    if (!g) return 1;
+    prepare(secs, n_secs, cam, g);
+    bins_t B = {0};
+    build_bins(g, n, cam, &B);
+    int64_t HW = (int64_t)cam->W * cam->H;
+#pragma omp parallel num_threads(orc_get_threads())
+    {
+        cand_t *cb = NULL;
+        int64_t ccap = 0;
+#pragma omp for schedule(dynamic, 1)
+        for (int v = 0; v < cam->H; ++v) {
+            for (int u = 0; u < cam->W; ++u) {
+                const int64_t p = (int64_t)v * cam->W + u;
+                const int64_t *ids = L->ids + p * (int64_t)L->cap;
+                const int32_t cnt = L->count[p];
+                double px, py;
+                pixel_coords(cam, u, v, &px, &py);
+                int32_t status = 0, flips = 0;
+                double fmax = 0.0;
+                /* the list itself: ids in range, valid, strictly increasing keys */
+                if (cnt < 0 || cnt > L->cap) status = 1;
+                for (int32_t j = 0; j < cnt && !status; ++j) {
+                    if (ids[j] < 0 || ids[j] >= n || !g[ids[j]].valid) status = 1;
+                    else if (j > 0 && !key_less(&g[ids[j - 1]], &g[ids[j]])) status = 1;
+                }
+                /* composite along the list in FP64 */
+                double C[3] = {0, 0, 0}, Dp = 0, S = 0, T = 1.0;
+                for (int32_t j = 0; j < cnt && !status; ++j) {
+                    const gpre *G = &g[ids[j]];
+                    inc_t e;
+                    pair_eval(G, px, py, &e);
+                    const double w = e.alpha * T;
+                    C[0] += w * G->c[0];
+                    C[1] += w * G->c[1];
+                    C[2] += w * G->c[2];
+                    Dp += w * G->x[2];
+                    S += w;
+                    T = T * (1.0 - e.alpha);
+                }
+                /* candidates of the pixel in key order */
+                const int64_t b = (int64_t)(v / ORC_BIN) * B.nbx + u / ORC_BIN;
+                const int64_t nb = B.start[b + 1] - B.start[b];
+                int64_t m = 0;
+                if (nb > ccap) {
+                    ccap = nb;
+                    cb = (cand_t *)realloc(cb, sizeof(cand_t) * (size_t)ccap);
+                }
+                for (int64_t j = 0; j < nb && !status; ++j) {
+                    const gpre *G = &g[B.items[B.start[b] + j]];
+                    if (!G->valid) continue;
+                    inc_t e;
+                    pair_eval(G, px, py, &e);
+                    if (!(e.q <= ORC_Q_MAX * ORC_BAND)) continue;
+                    cand_t *c = &cb[m++];
+                    c->zkey = G->zkey;
+                    c->id = G->id;
+                    c->alpha = e.alpha;
+                    c->inc = inclusion(&e, &c->m_in);
+                }
+                if (!status) qsort(cb, (size_t)m, sizeof(cand_t), cmp_cand);
+                /* walk the candidates: before the list's last entry every
+                 * candidate is either added (listed) or excluded; after it the
+                 * walk has either terminated at a candidate or excluded it */
+                double Tw = 1.0;
+                int32_t next = 0;
+                for (int64_t j = 0; j < m && !status; ++j) {
+                    const cand_t *c = &cb[j];
+                    const double Tn = Tw * (1.0 - c->alpha);
+                    const double mT = fabs(Tn - ORC_T_MIN) / ORC_T_MIN;
+                    if (next < cnt) {
+                        if (c->id == ids[next]) {          /* added */
+                            if (!c->inc) {
+                                if (c->m_in < tau_incl) note_flip(&flips, &fmax, c->m_in);
+                                else status = 2;
+                            }
+                            if (Tn < ORC_T_MIN) {
+                                if (mT < tau_T) note_flip(&flips, &fmax, mT);
+                                else status = 2;
+                            }
+                            Tw = Tn;
+                            ++next;
+                        } else if (c->inc) {               /* excluded, though included in FP64 */
+                            if (c->m_in < tau_incl) note_flip(&flips, &fmax, c->m_in);
+                            else status = 2;
+                        }
+                        continue;
+                    }
+                    /* after the list: terminate here, or exclude and go on */
+                    const int incl_ok = c->inc || c->m_in < tau_incl;
+                    const int term_ok = Tn < ORC_T_MIN || mT < tau_T;
+                    if (incl_ok && term_ok) {
+                        if (!c->inc) note_flip(&flips, &fmax, c->m_in);
+                        if (!(Tn < ORC_T_MIN)) note_flip(&flips, &fmax, mT);
+                        break;
+                    }
+                    if (!c->inc) continue;
+                    if (c->m_in < tau_incl) note_flip(&flips, &fmax, c->m_in);
+                    else status = 2;
+                }
+                if (!status && next < cnt) status = 1;   /* a listed id is not a candidate */
+                if (out->rgb) {
+                    out->rgb[p] = C[0];
+                    out->rgb[HW + p] = C[1];
+                    out->rgb[2 * HW + p] = C[2];
+                }
+                if (out->depth) out->depth[p] = Dp;
+                if (out->sil) out->sil[p] = S;
+                if (out->T_final) out->T_final[p] = T;
+                if (out->n_added) out->n_added[p] = cnt;
+                if (vd->status) vd->status[p] = status;
+                if (vd->flips) vd->flips[p] = flips;
+                if (vd->flip_margin) vd->flip_margin[p] = fmax;
+            }
+        }
+        free(cb);
+    }
+    free_bins(&B);
+    free(g);
+    return 0;
+}
+
+int orc_backward_lists(const orc_section *secs, int n_secs, const orc_camera *cam,
+                       const orc_lists *L, const orc_upstream *up, orc_grads *gr) {
+    int64_t n = total_n(secs, n_secs);
+    gpre *g = (gpre *)malloc(sizeof(gpre) * (size_t)(n > 0 ? n : 1));
+    if (!g) return 1;
+    prepare(secs, n_secs, cam, g);
+    for (int64_t p = 0; p < (int64_t)cam->W * cam->H; ++p) {
+        if (L->count[p] < 0 || L->count[p] > L->cap) { free(g); return 2; }
+        for (int32_t j = 0; j < L->count[p]; ++j) {
+            const int64_t id = L->ids[p * (int64_t)L->cap + j];
+            if (id < 0 || id >= n || !g[id].valid) { free(g); return 2; }
+        }
+    }
+    int64_t HW = (int64_t)cam->W * cam->H;
+    pose_sums tot = {{0}};
+#pragma omp parallel num_threads(orc_get_threads())
+    {
+        pose_sums ps = {{0}};
+        inc_t *eb = NULL;
+        double *Tb = NULL, *wb = NULL;
+        int64_t ecap = 0, wcap = 0;
+#pragma omp for schedule(dynamic, 1)
+        for (int v = 0; v < cam->H; ++v) {
+            for (int u = 0; u < cam->W; ++u) {
+                int64_t p = (int64_t)v * cam->W + u;
+                double gC[3], gD, gS;
+                if (!upstream_at(up, HW, p, gC, &gD, &gS)) continue;
+                double px, py;
+                pixel_coords(cam, u, v, &px, &py);
+                const int64_t k = L->count[p];
+                if (k > ecap) {
+                    ecap = k;
+                    eb = (inc_t *)realloc(eb, sizeof(inc_t) * (size_t)ecap);
+                }
+                double Tfin = 1.0;
+                for (int64_t j = 0; j < k; ++j) {
+                    const int64_t id = L->ids[p * (int64_t)L->cap + j];
+                    pair_eval(&g[id], px, py, &eb[j]);
+                    eb[j].gi = id;
+                    Tfin = Tfin * (1.0 - eb[j].alpha);
+                }
+                grow(&Tb, &wb, &wcap, k);
+                pixel_grads(g, cam->pose, px, py, gC, gD, gS, eb, k, Tfin, Tb, wb, gr, &ps);
+            }
+        }
+#pragma omp critical
+        add_sums(&tot, &ps);
+        free(eb);
+        free(Tb);
+        free(wb);
+    }
+    finish_grads(&tot, gr);
     free(g);
     return 0;
 }

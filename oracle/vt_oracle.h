@@ -107,6 +107,49 @@ int orc_render(const orc_section *secs, int n_secs, const orc_camera *cam, int b
 int orc_backward(const orc_section *secs, int n_secs, const orc_camera *cam, int binned,
                  const orc_upstream *up, orc_grads *g);
 
+/* ---- compositing along given decisions -------------------------------- */
+
+/* Per-pixel lists of added Gaussians, front to back, as another
+ * implementation of the method reports them: ids[(v*W + u)*cap + j] for
+ * j < count[v*W + u]; ids are positions in the concatenation of the
+ * sections (the ids of orc_image.lists). */
+typedef struct {
+    const int64_t *ids;
+    const int32_t *count;
+    int32_t cap;
+} orc_lists;
+
+/* Verdict on each pixel's list. */
+typedef struct {
+    int32_t *status;      /* H x W: 0 = the definition's list, up to decisions that lie within
+                             the given relative margins of their thresholds; 1 = no list of
+                             the definition at all (keys not strictly increasing, an id out of
+                             range, culled or outside the pixel's band q <= 9.009); 2 = a
+                             decision differs from its FP64 outcome by more than the margins */
+    int32_t *flips;       /* H x W: decisions taken otherwise than in FP64 */
+    double *flip_margin;  /* H x W: largest relative margin among them (0 if none) */
+} orc_verdict;
+
+/* Where an inclusion test (q <= 9, ahat >= 1/255) or the termination test
+ * (T' < 1e-4) lies within the rounding of a lower precision of its
+ * threshold, both outcomes are correct results.  For every pixel this
+ * checks that the given list differs from the FP64 decisions only at
+ * decisions within tau_incl (inclusion, relative) or tau_T (termination,
+ * relative) of their thresholds -- before the list's last entry every
+ * candidate is added or excluded, after it the walk stops at a candidate
+ * whose inclusion ends it, or excludes it -- and composites along the given
+ * list in FP64: rgb, depth, sil, T_final and n_added (= count) of out;
+ * the margin fields of out are not written.  Always binned.  Returns 0. */
+int orc_render_lists(const orc_section *secs, int n_secs, const orc_camera *cam,
+                     const orc_lists *L, double tau_incl, double tau_T, orc_image *out,
+                     orc_verdict *vd);
+
+/* orc_backward with each pixel's added Gaussians taken from L instead of
+ * from the FP64 decisions (alpha, q and the pose terms still in FP64).
+ * Returns 2 if an id is out of range or culled, else 0. */
+int orc_backward_lists(const orc_section *secs, int n_secs, const orc_camera *cam,
+                       const orc_lists *L, const orc_upstream *up, orc_grads *g);
+
 /* Centres of the Gaussians of one depth map: mu = R (D * K^-1 [u v 1]) + t
  * for every valid pixel in raster order.  Returns the count. */
 int64_t orc_backproject(const float *depth, int32_t W, int32_t H, float fx, float fy,
