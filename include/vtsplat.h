@@ -30,7 +30,8 @@
  *     memory, read during the call only.
  *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy
  *     default stream) and is asynchronous; no call synchronises the stream
- *     except vt_ctx_sync_status and vt_ctx_debug_copy, which say so.
+ *     except vt_ctx_sync_status and the inspection hooks vt_ctx_debug_copy
+ *     and vt_ctx_debug_pixel_lists, which say so.
  *   - Poses are camera-to-world 3x4 [R | t] as 12 doubles: R row-major, then t.
  *   - Images are float32, planar: rgb is 3 x H x W (channel-major), depth and
  *     silhouette H x W.
@@ -169,10 +170,14 @@ vt_status vt_backproject(const float *depth, int32_t W, int32_t H, vt_intrinsics
  * in a fixed 512 KiB array inside the library, present on every GPU that
  * loads it until the process exits; the call allocates nothing.
  *   - Depth maps are limited to W * H <= 2^24 pixels; larger ones return
- *     VT_ERR_INVALID_ARG (use vt_backproject).
- *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *     VT_ERR_INVALID_ARG (use vt_backproject), and both sides to 65535, as
+ *     for every entry point.
+ *   - A call made while `stream` is not being captured looks up the array's
+ *     device address on the current device (with that device current) and
+ *     caches it; calls during a stream capture use the cached address, so
+ *     make the first call on a device before any stream capture (a call
+ *     during capture with nothing cached returns VT_ERR_STATE).  After a
+ *     device reset, make one call outside capture again before capturing.
  *   - All calls share the one array: calls that may overlap on the GPU (on
  *     different streams, or from different threads) race and must be
  *     serialised by the caller.  No state carries over from one call to the
@@ -435,6 +440,24 @@ int32_t vt_ctx_used_lists(const vt_ctx *ctx);
  * negative vt_status. */
 int64_t vt_ctx_debug_copy(vt_ctx *ctx, int32_t what, void *dst, int64_t capacity,
                           vt_stream stream);
+
+/* Test and inspection hook: synchronises `stream` and copies the per-pixel
+ * lists the last render on ctx kept (vt_ctx_set_list_capacity) for the
+ * pixels of the rectangle [x0, x0 + w) x [y0, y0 + h) to host memory, pixels
+ * row-major: counts[y * w + x] (host uint32, w * h) = the number of Gaussians
+ * the pixel added; ids[(y * w + x) * cap + j] (host uint32, w * h * cap) =
+ * the id (section index and position, as the concatenation of the render's
+ * sections) of its j-th added Gaussian front to back and T_front (host
+ * float32, same layout, may be NULL) the transmittance in front of it, for
+ * j < min(count, cap, kept); other entries are left untouched.  *kept (may
+ * be NULL) receives the context's list capacity: a pixel whose count
+ * exceeds it has only its first `kept` entries recorded.  Returns
+ * VT_ERR_STATE when the last render kept no lists, VT_ERR_INVALID_ARG for a
+ * rectangle outside the image.  (Used by the tests to compare each pixel's
+ * decisions with the oracle's.) */
+vt_status vt_ctx_debug_pixel_lists(vt_ctx *ctx, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                                   int32_t cap, uint32_t *ids, float *T_front, uint32_t *counts,
+                                   int32_t *kept, vt_stream stream);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *vt_last_error(void);

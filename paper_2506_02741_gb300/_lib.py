@@ -116,6 +116,9 @@ def _declare(L):
         "vt_ctx_workspace_bytes": (C.c_size_t, [_P]),
         "vt_ctx_used_lists": (C.c_int32, [_P]),
         "vt_ctx_debug_copy": (C.c_int64, [_P, C.c_int32, _P, C.c_int64, _P]),
+        "vt_ctx_debug_pixel_lists": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                               C.c_int32, _P, _P, _P, C.POINTER(C.c_int32),
+                                               _P]),
         "vt_last_error": (C.c_char_p, []),
         "vt_version": (C.c_char_p, []),
     }
@@ -134,7 +137,7 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists",
            "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam",
            "vt_attr_adam", "vt_section_complement", "vt_ssim",
-           "vt_visibility_counts", "vt_shape_adam"]
+           "vt_visibility_counts", "vt_shape_adam", "vt_ctx_debug_pixel_lists"]
 
 
 def lib_path() -> str:

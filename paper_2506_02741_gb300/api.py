@@ -551,6 +551,32 @@ class Renderer:
     def launches(self) -> int:
         return int(self._lib.vt_ctx_launch_count(self._ctx))
 
+    def pixel_lists(self, x0: int, y0: int, w: int, h: int, cap: int | None = None,
+                    stream=None):
+        """Per-pixel lists of the last render for the rectangle (x0, y0, w, h)
+        (vt_ctx_debug_pixel_lists): ids (h, w, cap) int64 (-1 beyond each
+        pixel's entries), T_front (h, w, cap) float32, counts (h, w) int64 of
+        added Gaussians and the context's list capacity."""
+        kept = C.c_int32(0)
+        counts = np.zeros((h, w), np.uint32)
+        probe = np.zeros(1, np.uint32)
+        L.check(self._lib.vt_ctx_debug_pixel_lists(
+            self._ctx, int(x0), int(y0), int(w), int(h), 0, probe.ctypes.data_as(C.c_void_p),
+            None, counts.ctypes.data_as(C.c_void_p), C.byref(kept), _stream(stream)),
+            "vt_ctx_debug_pixel_lists")
+        if cap is None:
+            cap = max(1, min(int(kept.value), int(counts.max()) if counts.size else 1))
+        ids = np.full((h, w, cap), 0xFFFFFFFF, np.uint32)
+        T = np.zeros((h, w, cap), np.float32)
+        L.check(self._lib.vt_ctx_debug_pixel_lists(
+            self._ctx, int(x0), int(y0), int(w), int(h), int(cap),
+            ids.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
+            counts.ctypes.data_as(C.c_void_p), C.byref(kept), _stream(stream)),
+            "vt_ctx_debug_pixel_lists")
+        out = ids.astype(np.int64)
+        out[ids == 0xFFFFFFFF] = -1
+        return out, T, counts.astype(np.int64), int(kept.value)
+
     def debug(self, what: int, count: int, dtype=np.uint32, stream=None) -> np.ndarray:
         out = np.zeros(count, dtype)
         r = self._lib.vt_ctx_debug_copy(self._ctx, int(what), out.ctypes.data_as(C.c_void_p),

@@ -323,6 +323,12 @@ vt_status check_image(int32_t W, int32_t H, const char *who) {
 bool sort_attr_set = false;
 
 }  // namespace
+// The image-size rule of every entry point, for other translation units
+// (not exported).
+__attribute__((visibility("hidden"))) vt_status vt_internal_check_image(int32_t W, int32_t H,
+                                                                       const char *who) {
+    return check_image(W, H, who);
+}
 
 // ---------------------------------------------------------------------------
 
@@ -1216,6 +1222,42 @@ int64_t vt_ctx_debug_copy(vt_ctx *c, int32_t what, void *dst, int64_t capacity,
     if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
         return -VT_ERR_CUDA;
     return bytes;
+}
+
+vt_status vt_ctx_debug_pixel_lists(vt_ctx *c, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                                   int32_t cap, uint32_t *ids, float *T_front, uint32_t *counts,
+                                   int32_t *kept, vt_stream stream) {
+    if (!c || !counts || cap < 0 || (cap > 0 && !ids))
+        return fail(VT_ERR_INVALID_ARG, "vt_ctx_debug_pixel_lists: bad arguments");
+    if (!c->has_render) return fail(VT_ERR_STATE, "vt_ctx_debug_pixel_lists: no render");
+    if (x0 < 0 || y0 < 0 || w < 0 || h < 0 || x0 + w > c->cam.W || y0 + h > c->cam.H)
+        return fail(VT_ERR_INVALID_ARG, "vt_ctx_debug_pixel_lists: rectangle outside the image");
+    if (!c->used_lists)
+        return fail(VT_ERR_STATE, "vt_ctx_debug_pixel_lists: the last render kept no lists");
+    VT_CUDA(cudaStreamSynchronize(stream), "vt_ctx_debug_pixel_lists");
+    const int64_t lc = c->list_cap;
+    if (kept) *kept = (int32_t)lc;
+    std::vector<uint2> row((size_t)w * (size_t)lc);
+    for (int32_t y = 0; y < h; ++y) {
+        const int64_t p0 = (int64_t)(y0 + y) * c->cam.W + x0;
+        VT_CUDA(cudaMemcpy(counts + (size_t)y * w, c->pix_nadd + p0, sizeof(uint32_t) * w,
+                           cudaMemcpyDeviceToHost),
+                "pixel list counts");
+        if (w == 0 || lc == 0) continue;
+        VT_CUDA(cudaMemcpy(row.data(), c->plist + p0 * lc, sizeof(uint2) * row.size(),
+                           cudaMemcpyDeviceToHost),
+                "pixel lists");
+        for (int32_t x = 0; x < w; ++x) {
+            const int64_t n = std::min<int64_t>({(int64_t)counts[(size_t)y * w + x], lc, cap});
+            for (int64_t j = 0; j < n; ++j) {
+                const size_t o = ((size_t)y * w + x) * (size_t)cap + (size_t)j;
+                const uint2 e = row[(size_t)x * lc + j];
+                ids[o] = e.x;
+                if (T_front) std::memcpy(&T_front[o], &e.y, sizeof(float));
+            }
+        }
+    }
+    return VT_OK;
 }
 
 }  // extern "C"

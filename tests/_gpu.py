@@ -30,20 +30,73 @@ def to_device(sec: "oracle.Section", prec: str = "f32", device="cuda") -> api.Se
                        t(sec.radius).contiguous())
 
 
-def clean_mask(ref: dict, tau_incl=1e-5, tau_T=2e-4, tau_clamp=None) -> np.ndarray:
-    """Pixels whose every inclusion / termination decision is farther than the
-    given relative margins from its threshold: there FP32 and FP64 must take
-    the same decisions.  The FP32 kernels compute q to ~6e-7 and ahat to
-    ~3e-6 relative (exp of an argument up to 4.5), and the transmittance to
-    ~1e-4 after many steps near the 0.99 clamp, hence the default margins."""
-    m = (ref["margin"] > tau_incl) & (ref["margin_T"] > tau_T)
-    if tau_clamp is not None:
-        m &= ref["margin_clamp"] > tau_clamp
-    return m
+# Relative margins within which a decision of the definition may go either
+# way between the FP32 kernels and the FP64 oracle: the kernels compute q to
+# ~6e-7 and ahat to ~3e-6 relative (exp of an argument up to 4.5), and the
+# transmittance to ~1e-4 after many steps near the 0.99 clamp.
+TAU_INCL = 1e-5
+TAU_T = 2e-4
+
+# Per-case decision statistics of the parity tests (printed with -s).
+STATS = []
 
 
-def assert_forward_close(out, ref, mask, tol=1e-5, depth_scale=4.0):
+def gpu_lists(R, W, H, box=None, id_map=None):
+    """The GPU's decisions: per-pixel lists of added Gaussians (ids (h, w,
+    cap) int64 and counts (h, w)) of the last render of renderer R for the
+    rectangle box = (x0, y0, w, h) (default: the whole W x H image).  Every
+    pixel's list must be complete (no pixel added more than the context
+    keeps).  id_map translates the GPU's ids (positions in the concatenation
+    of the render's sections) to the oracle's."""
+    x0, y0, w, h = box or (0, 0, W, H)
+    ids, _T, counts, kept = R.pixel_lists(x0, y0, w, h)
+    assert counts.max(initial=0) <= kept, ("a pixel list overflowed", int(counts.max()), kept)
+    if id_map is not None:
+        ids = id_map(ids)
+        assert np.all(ids[np.arange(ids.shape[2])[None, None, :] < counts[:, :, None]] >= 0), \
+            "a Gaussian the GPU added is missing from the oracle's input"
+    return ids, counts
+
+
+def subset_map(keep_masks):
+    """id_map for an oracle input made of the Gaussians keep_masks[s] of each
+    section s of the GPU render, in their order (-1 for a Gaussian left
+    out)."""
+    bases = np.cumsum([0] + [len(k) for k in keep_masks[:-1]])
+    kept = np.concatenate([np.flatnonzero(k) + b for k, b in zip(keep_masks, bases)])
+    kept = kept.astype(np.int64)
+
+    def f(ids):
+        if kept.size == 0:
+            return np.full_like(ids, -1)
+        pos = np.minimum(np.searchsorted(kept, np.maximum(ids, 0)), kept.size - 1)
+        return np.where((ids >= 0) & (kept[pos] == ids), pos, -1)
+    return f
+
+
+def check_decisions(ref, name=""):
+    """Every pixel's GPU list is one of the definition's up to decisions
+    within the margins render_lists was given (status 0); records and
+    returns the count of pixels with a decision taken otherwise than in
+    FP64."""
+    st = ref["status"]
+    bad = np.argwhere(st != 0)
+    assert bad.size == 0, (name, int((st != 0).sum()), [tuple(b) for b in bad[:5]],
+                           [int(st[tuple(b)]) for b in bad[:5]])
+    rec = dict(case=name, pixels=int(st.size), flip_pixels=int((ref["flips"] > 0).sum()),
+               flips=int(ref["flips"].sum()),
+               max_flip_margin=float(ref["flip_margin"].max(initial=0.0)))
+    STATS.append(rec)
+    print("PARITY_DECISIONS", rec)
+    return rec
+
+
+def assert_forward_close(out, ref, mask=None, tol=1e-5, depth_scale=4.0):
+    """|gpu - ref| <= tol max(|ref|, s) at every pixel (of mask, if given),
+    s = 1 for colour and silhouette, depth_scale for depth."""
     rgb, depth, sil = (x.detach().cpu().numpy().astype(np.float64) for x in out)
+    if mask is None:
+        mask = np.ones(depth.shape, bool)
     err = {}
     for name, g, r, s in (("rgb", rgb, ref["rgb"], 1.0), ("depth", depth, ref["depth"], depth_scale),
                           ("sil", sil, ref["sil"], 1.0)):
@@ -93,3 +146,19 @@ def assert_grad_close(g, ref, tol=1e-4, name="", abs_ref=None, noise=None):
         bound = bound + POSE_NOISE * np.asarray(noise, np.float64).ravel()
     bad = np.abs(g - ref) > bound
     assert not bad.any(), (name, int(bad.sum()), float(np.max(np.abs(g - ref) / bound)))
+
+
+def decisions(dsecs, pose12, K, W, H, out=None, box=None, id_map=None, cap=None):
+    """The GPU's decisions of a render of dsecs taken on a fresh context that
+    keeps per-pixel lists (capacity cap, default the library's); with out
+    (the images of another render of the same inputs) the images must be
+    bit-identical: the decisions do not depend on whether lists are kept."""
+    R = api.Renderer()
+    if cap:
+        R.set_list_capacity(cap)
+    o = R.render(dsecs, pose12, K, W, H, checked=True)
+    torch.cuda.synchronize()
+    if out is not None:
+        for a, b in zip(o, out):
+            assert torch.equal(a, b)
+    return gpu_lists(R, W, H, box, id_map)

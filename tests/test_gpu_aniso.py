@@ -2,8 +2,10 @@
 with the FP64 oracle of oracle/aniso.py.
 
 Forward: FP32 within 2e-5 relative (floor 1 for colour / silhouette, 4 m
-for depth) on pixels whose decisions sit farther than 1e-4 (relative) from
-their thresholds.  The conic is formed in FP32 from J, M, R(q) and s (about
+for depth) at every pixel, against the oracle composited along the GPU's own
+per-pixel lists, which must be the definition's up to decisions within 1e-4
+(relative) of their inclusion thresholds or 2e-4 of the termination
+threshold.  The conic is formed in FP32 from J, M, R(q) and s (about
 ten rounded products and sums per entry before the 2 x 2 inverse), so q
 carries a few 1e-7 relative error where the sphere form has one or two
 roundings; alpha = o exp(-q/2) turns a relative error d of q into q d / 2
@@ -64,34 +66,41 @@ def _device(sec, scale, quat):
 CASES = ["tiny", "qqvga_2views", "ragged_3views"]
 
 
+def _lists_ref(R, sec, scale, quat, target, K, W, H, name, keep=False):
+    """The oracle composited along the last render's per-pixel lists, after
+    checking them against the definition."""
+    ids, cnt = G.gpu_lists(R, W, H)
+    ref = aniso.render_lists(sec, scale, quat, target, K, W, H, ids, cnt, tau_incl=TAU_INCL,
+                             keep=keep)
+    G.check_decisions(ref, name)
+    return ref
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_ellipsoid_forward_parity(dev, case):
     sec, scale, quat, target, K, W, H = _case(case)
     R = api.Renderer()
     out = R.render([_device(sec, scale, quat)], api.pose12(target, dev), K, W, H, checked=True)
     torch.cuda.synchronize()
-    ref = aniso.render(sec, scale, quat, target, K, W, H)
-    mask = G.clean_mask(ref, tau_incl=TAU_INCL)
-    assert mask.mean() > 0.9, mask.mean()
+    ref = _lists_ref(R, sec, scale, quat, target, K, W, H, "ellipsoids_" + case)
     assert ref["n_added"].mean() > 5
-    G.assert_forward_close(out, ref, mask, tol=FWD_TOL)
+    G.assert_forward_close(out, ref, tol=FWD_TOL)
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_ellipsoid_gradients(dev, case):
     """Colour, opacity, scale, quaternion and target-pose gradients against
-    the oracle's chain rule (upstream gradients on the clean pixels only)."""
+    the oracle's chain rule along the GPU's own per-pixel lists."""
     sec, scale, quat, target, K, W, H = _case(case)
     R = api.Renderer()
     dsec = _device(sec, scale, quat)
     R.render([dsec], api.pose12(target, dev), K, W, H, checked=True)
-    ref = aniso.render(sec, scale, quat, target, K, W, H)
-    clean = G.clean_mask(ref, tau_incl=TAU_INCL, tau_clamp=1e-4)
+    ref = _lists_ref(R, sec, scale, quat, target, K, W, H, "ellipsoid_grads_" + case, keep=True)
     rng = np.random.default_rng(31)
-    gR = (rng.normal(0, 1, (3, H, W)) * clean).astype(np.float32)
-    gD = (rng.normal(0, 1, (H, W)) * clean).astype(np.float32)
-    gS = (rng.normal(0, 1, (H, W)) * clean).astype(np.float32)
-    want = aniso.backward(sec, scale, quat, target, K, W, H, gR, gD, gS)
+    gR = rng.normal(0, 1, (3, H, W)).astype(np.float32)
+    gD = rng.normal(0, 1, (H, W)).astype(np.float32)
+    gS = rng.normal(0, 1, (H, W)).astype(np.float32)
+    want = aniso.backward(sec, scale, quat, target, K, W, H, gR, gD, gS, fwd=ref)
     n = sec.n
     z = lambda *s: torch.zeros(*s, device=dev)
     grads = [(z(n, 3), z(n), None, z(n, 3), z(n, 4))]
@@ -237,10 +246,8 @@ def test_ellipsoid_fp16_storage_and_invalid_shapes(dev):
     out = R.render([dsec], api.pose12(target, dev), K, W, H, checked=True)
     torch.cuda.synchronize()
     with np.errstate(invalid="ignore", divide="ignore"):
-        ref = aniso.render(sec, scale, quat, target, K, W, H)
-    mask = G.clean_mask(ref, tau_incl=TAU_INCL)
-    assert mask.mean() > 0.9
-    G.assert_forward_close(out, ref, mask, tol=FWD_TOL)
+        ref = _lists_ref(R, sec, scale, quat, target, K, W, H, "ellipsoids_fp16_invalid")
+    G.assert_forward_close(out, ref, tol=FWD_TOL)
 
 
 def test_thin_ellipsoids(dev):
@@ -255,12 +262,9 @@ def test_thin_ellipsoids(dev):
     R = api.Renderer()
     R.render([_device(sec, scale, quat)], api.pose12(target, dev), K, W, H, checked=True)
     out = R.render([_device(sec, scale, quat)], api.pose12(target, dev), K, W, H)
-    ref = aniso.render(sec, scale, quat, target, K, W, H, keep=True)
-    mask = G.clean_mask(ref, tau_incl=TAU_INCL)
-    assert mask.mean() > 0.85
-    G.assert_forward_close(out, ref, mask, tol=FWD_TOL)
-    clean = G.clean_mask(ref, tau_incl=TAU_INCL, tau_clamp=1e-4)
-    gR = (rng.normal(0, 1, (3, H, W)) * clean).astype(np.float32)
+    ref = _lists_ref(R, sec, scale, quat, target, K, W, H, "thin_ellipsoids", keep=True)
+    G.assert_forward_close(out, ref, tol=FWD_TOL)
+    gR = rng.normal(0, 1, (3, H, W)).astype(np.float32)
     want = aniso.backward(sec, scale, quat, target, K, W, H, gR, fwd=ref)
     dtw, _ = R.backward(torch.from_numpy(gR).to(dev), None, None, pose_grad=True)
     torch.cuda.synchronize()

@@ -55,12 +55,15 @@ def _loss_and_grads(dev, parts, target, K, g, recompute, pool):
 def test_autograd_matches_oracle_and_recompute(dev):
     K, parts, target = _three_sections()
     Kt = K.astuple()
-    ref = oracle.render(parts, target, Kt, K.W, K.H)
-    clean = G.clean_mask(ref, tau_clamp=1e-4)
+    # the GPU's decisions for these inputs (a render that keeps per-pixel
+    # lists); the oracle differentiates along them
+    ids, cnt = G.decisions([G.to_device(p) for p in parts], api.pose12(target, dev), Kt, K.W, K.H)
+    G.check_decisions(oracle.render_lists(parts, target, Kt, K.W, K.H, ids, cnt), "autograd")
     rng = np.random.default_rng(3)
-    gn = [(rng.normal(0, 1, s) * clean).astype(np.float32) for s in ((3, K.H, K.W), (K.H, K.W), (K.H, K.W))]
+    gn = [rng.normal(0, 1, s).astype(np.float32) for s in ((3, K.H, K.W), (K.H, K.W), (K.H, K.W))]
     g = [torch.from_numpy(x).to(dev) for x in gn]
-    want = oracle.backward(parts, target, Kt, K.W, K.H, g_rgb=gn[0], g_depth=gn[1], g_sil=gn[2])
+    want = oracle.backward_lists(parts, target, Kt, K.W, K.H, ids, cnt, g_rgb=gn[0], g_depth=gn[1],
+                                 g_sil=gn[2])
     pool = RendererPool()
     attr, dpose = _loss_and_grads(dev, parts, target, K, g, False, pool)
     for k, name in enumerate(("colour", "opacity", "radius")):

@@ -48,18 +48,18 @@ def test_fullsize_crop_parity(cfg):
     cw, ch = 96, 80
     x0, y0 = (K.W - cw) // 2 + 16, (K.H - ch) // 2 - 8
     Kc = _crop(K, x0, y0)
-    ref = oracle.render([osec], target, Kc, cw, ch)
-    clean = G.clean_mask(ref)
-    assert clean.mean() > 0.95
+    ids, cnt = G.decisions([sec], api.pose12(target, dev), K.astuple(), K.W, K.H,
+                           out=(rgb, depth, sil), box=(x0, y0, cw, ch), cap=1024)
+    ref = oracle.render_lists([osec], target, Kc, cw, ch, ids, cnt)
+    G.check_decisions(ref, "fullsize_" + cfg)
     sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
     out = (rgb[:, sl[0], sl[1]], depth[sl], sil[sl])
-    G.assert_forward_close(out, ref, clean)
+    G.assert_forward_close(out, ref)
     # backward with the upstream gradient on the crop only
-    gm = G.clean_mask(ref, tau_clamp=1e-4)
     rng = np.random.default_rng(8)
-    gR = (rng.normal(0, 1, (3, ch, cw)) * gm).astype(np.float32)
-    gD = (rng.normal(0, 1, (ch, cw)) * gm).astype(np.float32)
-    want = oracle.backward([osec], target, Kc, cw, ch, g_rgb=gR, g_depth=gD)
+    gR = rng.normal(0, 1, (3, ch, cw)).astype(np.float32)
+    gD = rng.normal(0, 1, (ch, cw)).astype(np.float32)
+    want = oracle.backward_lists([osec], target, Kc, cw, ch, ids, cnt, g_rgb=gR, g_depth=gD)
     full_gR = torch.zeros(3, K.H, K.W, device=dev)
     full_gD = torch.zeros(K.H, K.W, device=dev)
     full_gR[:, sl[0], sl[1]] = torch.from_numpy(gR).to(dev)
@@ -127,10 +127,11 @@ def test_tile_sort_every_size_class():
     out = R2.render([bsec], api.pose12(path[30], dev), Kt.astuple(), Kt.W, Kt.H, checked=True)
     lens = _tile_lists_sorted(R2, big.n, Kt.W, Kt.H)
     assert lens.max() > 13312
-    ref = oracle.render([big], path[30], Kt.astuple(), Kt.W, Kt.H)
-    clean = G.clean_mask(ref)
-    assert clean.mean() > 0.8          # ~30 overlapping layers: more marginal decisions
-    G.assert_forward_close(out, ref, clean)
+    ids, cnt = G.decisions([bsec], api.pose12(path[30], dev), Kt.astuple(), Kt.W, Kt.H, out=out,
+                           cap=4096)
+    ref = oracle.render_lists([big], path[30], Kt.astuple(), Kt.W, Kt.H, ids, cnt)
+    G.check_decisions(ref, "sort_global_memory_30layers")
+    G.assert_forward_close(out, ref)
 
 
 def test_fullsize_ellipsoid_crop_parity():
@@ -151,15 +152,15 @@ def test_fullsize_ellipsoid_crop_parity():
     cw, ch = 96, 80
     x0, y0 = (K.W - cw) // 2 + 16, (K.H - ch) // 2 - 8
     Kc = _crop(K, x0, y0)
-    ref = aniso.render(osec, scale, quat, target, Kc, cw, ch, keep=True)
-    clean = G.clean_mask(ref, tau_incl=1e-4)
-    assert clean.mean() > 0.9
+    ids, cnt = G.decisions([sec], api.pose12(target, dev), K.astuple(), K.W, K.H,
+                           out=(rgb, depth, sil), box=(x0, y0, cw, ch), cap=1024)
+    ref = aniso.render_lists(osec, scale, quat, target, Kc, cw, ch, ids, cnt, keep=True)
+    G.check_decisions(ref, "fullsize_ellipsoids")
     sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
-    G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref, clean, tol=2e-5)
-    gm = G.clean_mask(ref, tau_incl=1e-4, tau_clamp=1e-4)
+    G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref, tol=2e-5)
     rng = np.random.default_rng(8)
-    gR = (rng.normal(0, 1, (3, ch, cw)) * gm).astype(np.float32)
-    gD = (rng.normal(0, 1, (ch, cw)) * gm).astype(np.float32)
+    gR = rng.normal(0, 1, (3, ch, cw)).astype(np.float32)
+    gD = rng.normal(0, 1, (ch, cw)).astype(np.float32)
     want = aniso.backward(osec, scale, quat, target, Kc, cw, ch, gR, gD, fwd=ref)
     full_gR = torch.zeros(3, K.H, K.W, device=dev)
     full_gD = torch.zeros(K.H, K.W, device=dev)
@@ -221,7 +222,7 @@ def _crop_subset(osec, target, K, box, slack=3.0):
         keep = (z > 0.05) & (uc + e >= x0) & (uc - e <= x0 + w - 1) & (vc + e >= y0) & \
                (vc - e <= y0 + h - 1)
     return dataclasses.replace(osec, src=osec.src[keep], colour=osec.colour[keep],
-                               opacity=osec.opacity[keep], radius=osec.radius[keep])
+                               opacity=osec.opacity[keep], radius=osec.radius[keep]), keep
 
 
 def test_large_multisection_render():
@@ -244,14 +245,16 @@ def test_large_multisection_render():
     cw, ch = 96, 80
     x0, y0 = (K.W - cw) // 2 + 40, (K.H - ch) // 2 + 24
     Kc = _crop(K, x0, y0)
-    subs = [_crop_subset(s, target, K, (x0, y0, cw, ch)) for s in osecs]
-    ref = oracle.render(subs, target, Kc, cw, ch)
-    clean = G.clean_mask(ref)
-    assert clean.mean() > 0.9
-    gm = G.clean_mask(ref, tau_clamp=1e-4)
+    subs, keeps = zip(*[_crop_subset(s, target, K, (x0, y0, cw, ch)) for s in osecs])
+    # the GPU's decisions on the crop, from a render that keeps lists long
+    # enough for every pixel (about 1,500 Gaussians lie over each)
+    ids, cnt = G.decisions(dsecs, api.pose12(target, dev), K.astuple(), K.W, K.H,
+                           box=(x0, y0, cw, ch), id_map=G.subset_map(list(keeps)), cap=4096)
+    ref = oracle.render_lists(list(subs), target, Kc, cw, ch, ids, cnt)
+    G.check_decisions(ref, "large_multisection_30M")
     rng = np.random.default_rng(5)
-    gR = (rng.normal(0, 1, (3, ch, cw)) * gm).astype(np.float32)
-    want = oracle.backward(subs, target, Kc, cw, ch, g_rgb=gR)
+    gR = rng.normal(0, 1, (3, ch, cw)).astype(np.float32)
+    want = oracle.backward_lists(list(subs), target, Kc, cw, ch, ids, cnt, g_rgb=gR)
     sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
     full_gR = torch.zeros(3, K.H, K.W, device=dev)
     full_gR[:, sl[0], sl[1]] = torch.from_numpy(gR).to(dev)
@@ -263,7 +266,7 @@ def test_large_multisection_render():
         rgb, depth, sil = R.render(dsecs, api.pose12(target, dev), K.astuple(), K.W, K.H,
                                    checked=True)
         assert R.used_lists == (budget is None)
-        G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref, clean)
+        G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref)
         dtw, dmat = R.backward(full_gR, None, None, pose_grad=True)
         torch.cuda.synchronize()
         G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist",
