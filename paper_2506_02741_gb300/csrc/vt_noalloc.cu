@@ -16,6 +16,7 @@
 #include "vt_common.cuh"
 
 vt_status vt_internal_fail(vt_status s, const char *msg);
+vt_status vt_internal_check_image(int32_t W, int32_t H, const char *who);
 
 namespace {
 
@@ -34,17 +35,27 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint32_t *g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
-vt_status scratch_on_current_device(uint32_t **out) {
+// Device address of the scratch array on the current device.  It is looked
+// up (cudaGetSymbolAddress, with the device current) on every call made while
+// `stream` is not being captured, so that a device reset, after which the
+// module and its array may be loaded at another address, is followed; calls
+// made during a stream capture use the address cached by the last such
+// lookup on this device and fail if there was none.
+vt_status scratch_on_current_device(cudaStream_t stream, uint32_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return vt_internal_fail(VT_ERR_CUDA, "vt_backproject_noalloc: cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices)
         return vt_internal_fail(VT_ERR_INVALID_ARG, "vt_backproject_noalloc: device index too large");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return vt_internal_fail(VT_ERR_CUDA, "vt_backproject_noalloc: cudaStreamIsCapturing failed");
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_backproject_scratch);
         if (e != cudaSuccess || !p) {
@@ -54,6 +65,10 @@ vt_status scratch_on_current_device(uint32_t **out) {
                                     "array failed");
         }
         g_scratch_ptr[dev] = static_cast<uint32_t *>(p);
+    } else if (!g_scratch_ptr[dev]) {
+        return vt_internal_fail(VT_ERR_STATE,
+                                "vt_backproject_noalloc: the first call on a device must come "
+                                "before any stream capture");
     }
     *out = g_scratch_ptr[dev];
     return VT_OK;
@@ -65,8 +80,8 @@ extern "C" vt_status vt_backproject_noalloc(const float *depth, int32_t W, int32
                                             vt_intrinsics K, const double *pose12,
                                             float *centres, uint32_t *pix, int64_t cap,
                                             int64_t *n_out, vt_stream stream) {
-    if (W <= 0 || H <= 0)
-        return vt_internal_fail(VT_ERR_INVALID_ARG, "vt_backproject_noalloc: W and H must be > 0");
+    vt_status st = vt_internal_check_image(W, H, "vt_backproject_noalloc");
+    if (st != VT_OK) return st;
     const int64_t total = (int64_t)W * H;
     if (total > kNoAllocMaxPixels)
         return vt_internal_fail(VT_ERR_INVALID_ARG,
@@ -80,7 +95,7 @@ extern "C" vt_status vt_backproject_noalloc(const float *depth, int32_t W, int32
         return vt_internal_fail(VT_ERR_INVALID_ARG,
                                 "vt_backproject_noalloc: NULL pointer or negative capacity");
     uint32_t *scratch = nullptr;
-    vt_status st = scratch_on_current_device(&scratch);
+    st = scratch_on_current_device(stream, &scratch);
     if (st != VT_OK) return st;
     const int64_t nb = (total + vt::kInitBlock - 1) / vt::kInitBlock;
     uint32_t *counts = scratch, *offs = scratch + kNoAllocMaxBlocks;

@@ -69,3 +69,9 @@ def test_noalloc_rejects_oversize_depth_map():
                                     None)
     assert st == L.VT_ERR_INVALID_ARG
     assert b"2^24" in lib.vt_last_error()
+    # the per-side limit of every entry point applies here too
+    for fn in (lib.vt_backproject_noalloc, lib.vt_backproject):
+        st = fn(C.c_void_p(dummy.data_ptr()), 70000, 200, L.Intrinsics(500.0, 500.0, 10.0, 10.0),
+                C.c_void_p(pose.data_ptr()), C.c_void_p(dummy.data_ptr()),
+                C.c_void_p(dummy.data_ptr()), 0, C.c_void_p(n.data_ptr()), None)
+        assert st == L.VT_ERR_INVALID_ARG
