@@ -320,6 +320,78 @@ vt_status vt_masked_l1(vt_ctx *ctx, int32_t W, int32_t H, const float *rgb, cons
                        const uint8_t *visible, vt_l1_weights w, float *d_rgb, float *d_depth,
                        double *loss, vt_stream stream);
 
+/* ---- Batched work items ----------------------------------------------------
+ * Many independent requests processed together, for serving: each item
+ * renders one section from its own camera (vt_render of that section alone)
+ * and a tracking item adds the Eq. 1 masked L1 loss against its observation
+ * and the gradient with respect to its camera pose (vt_masked_l1 and
+ * vt_render_backward with VT_GRAD_POSE).  Every stage -- view set-up,
+ * projection, tile binning, the per-tile sorts, compositing, the loss, the
+ * pose backward and the final sums -- runs as one persistent launch over the
+ * Gaussians, tiles or pixels of all items (item ranges concatenated), so a
+ * batch costs the same ~15 launches whatever its size.  The items are read
+ * on the device from a work-item table that vt_batch_set writes into pinned
+ * host memory and vt_batch_launch uploads first; the launch sequence can
+ * therefore be captured once in a CUDA graph and replayed for every later
+ * batch of the context.  The paper describes no serving system: this
+ * follows the serving pattern of the benchmark spec.  Per item the results
+ * equal those of the single-render calls, except that the loss and the pose
+ * sums are reduced in another fixed order.  A context reserved for batches
+ * keeps no single render: a batch launch invalidates vt_render state. */
+
+#define VT_MAX_BATCH_ITEMS 64
+
+typedef struct {
+    int32_t section;        /* index into the section array of vt_batch_set (spheres only) */
+    int32_t track;          /* 0: render (forward only); 1: tracking iteration */
+    int32_t W, H;           /* image size, each <= 65535 */
+    vt_intrinsics K;
+    const double *pose12;   /* device, 12 doubles, camera-to-world */
+    float *image;           /* device, 5 x H x W float32, written: rgb planes, depth,
+                               silhouette */
+    const float *obs;       /* device, 4 x H x W float32 (track): observed rgb planes and
+                               depth (<= 0 or non-finite = no depth) */
+    double *result;         /* device, 19 doubles (track), overwritten: the loss, dL/dtwist
+                               (rho, phi), dL/dR (row-major), dL/dt */
+} vt_batch_item;
+
+/* Device bytes a batch reserve of these capacities takes (see vt_batch_reserve),
+ * with per-pixel lists of list_cap entries. */
+size_t vt_batch_workspace_bytes(int64_t max_gaussians, int64_t max_pixels, int64_t max_tiles,
+                                int64_t max_instances, int64_t max_views, int64_t max_table_rows,
+                                int32_t list_cap);
+
+/* Reserve ctx for batches whose totals over the items stay within
+ * max_gaussians (section sizes), max_pixels (W H), max_tiles (16 x 16 tiles),
+ * max_instances ((Gaussian, tile) pairs), max_views (source views) and
+ * max_table_rows (views x (W + H) of the sections' view sizes).  Per-pixel
+ * lists of the context's list capacity are kept for the tracking items'
+ * backward when they fit the workspace budget (else their tiles are
+ * replayed).  Allocates on stream; call before capturing a launch. */
+vt_status vt_batch_reserve(vt_ctx *ctx, int64_t max_gaussians, int64_t max_pixels,
+                           int64_t max_tiles, int64_t max_instances, int64_t max_views,
+                           int64_t max_table_rows, vt_stream stream);
+
+/* Stage a batch (host only, no launch): validates the sections (device
+ * pointers, as for vt_render; host array, n_secs in [1, 64]) and items (host
+ * array, n_items in [1, VT_MAX_BATCH_ITEMS]) and writes the work-item table
+ * into the context's pinned staging.  w: the Eq. 1 weights and masks of the
+ * tracking items (vt_masked_l1; visibility is not used).  Returns
+ * VT_ERR_CAPACITY, staging nothing, when the batch exceeds the reserved
+ * totals (the instance count is checked on the device: see
+ * vt_ctx_sync_status).  Waits for the upload of the previous eager launch
+ * of ctx; when launches are replayed from a captured graph, stage the next
+ * batch only after the previous replay has completed. */
+vt_status vt_batch_set(vt_ctx *ctx, const vt_section *secs, int32_t n_secs,
+                       const vt_batch_item *items, int32_t n_items, vt_l1_weights w);
+
+/* Enqueue on stream the upload of the staged table and the batch's
+ * launches (capturable).  Results are in the items' image and result
+ * buffers when the stream reaches that point; vt_ctx_sync_status reports
+ * VT_ERR_CAPACITY if the batch had more tile instances than reserved (its
+ * results are then undefined). */
+vt_status vt_batch_launch(vt_ctx *ctx, vt_stream stream);
+
 /* SSIM term of Eq. 2 (Sec. 3.4 mapping loss: tau L_S(V, V'), L_S the SSIM
  * loss; tau = 0.2 in Sec. 4).  L_S = 1 - mean SSIM over the pixels and the
  * three channels of rgb (rendered) against obs_rgb (observed), both device

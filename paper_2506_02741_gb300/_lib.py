@@ -44,6 +44,12 @@ class ViewC(C.Structure):
                 ("pose12", C.c_void_p)]
 
 
+class BatchItemC(C.Structure):
+    _fields_ = [("section", C.c_int32), ("track", C.c_int32), ("W", C.c_int32), ("H", C.c_int32),
+                ("K", Intrinsics), ("pose12", C.c_void_p), ("image", C.c_void_p),
+                ("obs", C.c_void_p), ("result", C.c_void_p)]
+
+
 class L1WeightsC(C.Structure):
     _fields_ = [("w_rgb", C.c_double), ("w_depth", C.c_double), ("sil_min", C.c_float),
                 ("rgb_needs_depth", C.c_int32)]
@@ -119,6 +125,13 @@ def _declare(L):
         "vt_ctx_debug_pixel_lists": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                C.c_int32, _P, _P, _P, C.POINTER(C.c_int32),
                                                _P]),
+        "vt_batch_workspace_bytes": (C.c_size_t, [C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                                  C.c_int64, C.c_int64, C.c_int32]),
+        "vt_batch_reserve": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                       C.c_int64, C.c_int64, _P]),
+        "vt_batch_set": (C.c_int, [_P, C.POINTER(SectionC), C.c_int32, C.POINTER(BatchItemC),
+                                   C.c_int32, L1WeightsC]),
+        "vt_batch_launch": (C.c_int, [_P, _P]),
         "vt_last_error": (C.c_char_p, []),
         "vt_version": (C.c_char_p, []),
     }
@@ -137,7 +150,8 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_ctx_set_workspace_budget", "vt_ctx_workspace_bytes", "vt_ctx_used_lists",
            "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam",
            "vt_attr_adam", "vt_section_complement", "vt_ssim",
-           "vt_visibility_counts", "vt_shape_adam", "vt_ctx_debug_pixel_lists"]
+           "vt_visibility_counts", "vt_shape_adam", "vt_ctx_debug_pixel_lists",
+           "vt_batch_workspace_bytes", "vt_batch_reserve", "vt_batch_set", "vt_batch_launch"]
 
 
 def lib_path() -> str:

@@ -584,3 +584,76 @@ class Renderer:
         if r < 0:
             raise L.VTError(-r, "vt_ctx_debug_copy")
         return out[: r // out.itemsize]
+
+
+@dataclasses.dataclass
+class BatchItem:
+    """One work item of a batch (vt_batch_item): ``section`` indexes the
+    batch's section list; ``pose`` (12,) float64, ``image`` (5, H, W)
+    float32 (written: rgb planes, depth, silhouette), and for a tracking item
+    ``obs`` (4, H, W) float32 (observed rgb planes and depth) and ``result``
+    (19,) float64 (written: loss, dL/dtwist, dL/dR, dL/dt), all device
+    tensors."""
+    section: int
+    track: bool
+    W: int
+    H: int
+    K: tuple
+    pose: torch.Tensor
+    image: torch.Tensor
+    obs: torch.Tensor | None = None
+    result: torch.Tensor | None = None
+
+    def c_struct(self) -> L.BatchItemC:
+        W, H = int(self.W), int(self.H)
+        _cuda(self.pose, torch.float64, "pose", (12,))
+        _cuda(self.image, torch.float32, "image", (5, H, W))
+        if self.track:
+            _cuda(self.obs, torch.float32, "obs", (4, H, W))
+            _cuda(self.result, torch.float64, "result", (19,))
+        return L.BatchItemC(int(self.section), int(bool(self.track)), W, H, _intr(self.K),
+                            _ptr(self.pose), _ptr(self.image),
+                            _ptr(self.obs) if self.track else None,
+                            _ptr(self.result) if self.track else None)
+
+
+class BatchRunner(Renderer):
+    """A context reserved for batched work items (vt_batch_*): every stage
+    of all items' renders -- and for tracking items the Eq. 1 loss and the
+    pose gradient -- runs as one persistent launch.  ``set`` stages a batch
+    (host only), ``launch`` enqueues it (capturable in a CUDA graph: the
+    work-item table is uploaded inside the launch sequence)."""
+
+    def __init__(self, max_gaussians: int, max_pixels: int, max_tiles: int, max_instances: int,
+                 max_views: int, max_table_rows: int, list_cap: int | None = None, stream=None):
+        super().__init__()
+        if list_cap is not None:
+            self.set_list_capacity(list_cap)
+        self.capacity = dict(gaussians=int(max_gaussians), pixels=int(max_pixels),
+                             tiles=int(max_tiles), instances=int(max_instances),
+                             views=int(max_views), table_rows=int(max_table_rows))
+        L.check(self._lib.vt_batch_reserve(self._ctx, int(max_gaussians), int(max_pixels),
+                                           int(max_tiles), int(max_instances), int(max_views),
+                                           int(max_table_rows), _stream(stream)),
+                "vt_batch_reserve")
+        self._keep = None
+
+    @staticmethod
+    def workspace_bytes_for(max_gaussians, max_pixels, max_tiles, max_instances, max_views,
+                            max_table_rows, list_cap=256) -> int:
+        return int(L.lib().vt_batch_workspace_bytes(int(max_gaussians), int(max_pixels),
+                                                    int(max_tiles), int(max_instances),
+                                                    int(max_views), int(max_table_rows),
+                                                    int(list_cap)))
+
+    def set(self, sections, items, w_rgb: float = 0.5, w_depth: float = 0.025,
+            sil_min: float = 0.99, rgb_needs_depth: bool = True):
+        secs = (L.SectionC * len(sections))(*[s.c_struct() for s in sections])
+        its = (L.BatchItemC * len(items))(*[it.c_struct() for it in items])
+        w = L.L1WeightsC(float(w_rgb), float(w_depth), float(sil_min), int(bool(rgb_needs_depth)))
+        L.check(self._lib.vt_batch_set(self._ctx, secs, len(sections), its, len(items), w),
+                "vt_batch_set")
+        self._keep = (sections, items)
+
+    def launch(self, stream=None):
+        L.check(self._lib.vt_batch_launch(self._ctx, _stream(stream)), "vt_batch_launch")

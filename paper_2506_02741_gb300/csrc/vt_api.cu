@@ -64,7 +64,9 @@ enum KernelId {
     K_SECTION_INIT, K_COUNT, K_BWD_LIST, K_SORT_BIG, K_SCATTER, K_L1, K_L1_SUM, K_POSE_ADAM,
     K_ADAM_COUNT, K_ATTR_ADAM, K_SORT_M, K_SORT_L, K_SSIM_FWD, K_SSIM_BWD, K_SSIM_SUM,
     K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_SHAPE_ADAM,
-    K_SORT_XL, K_VIEW_FIN, K_BWD_LIST_POSE, K_BWD_LIST_VIEWS, K_NUM
+    K_SORT_XL, K_VIEW_FIN, K_BWD_LIST_POSE, K_BWD_LIST_VIEWS, KB_SETUP, KB_PREPROCESS, KB_SCAN,
+    KB_EMIT, KB_SORT, KB_SORT_M, KB_SORT_L, KB_SORT_LONG, KB_SORT_XL, KB_FWD, KB_L1, KB_BWD_LIST,
+    KB_BWD, KB_FINALIZE, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -78,7 +80,12 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "k_composite_fwd_aniso", "k_composite_bwd_list_aniso",
                                    "k_composite_bwd_aniso", "k_aniso_chain", "k_shape_adam",
                                    "k_sort_tiles_xl", "k_view_finalize",
-                                   "k_composite_bwd_list_pose", "k_composite_bwd_list_views"};
+                                   "k_composite_bwd_list_pose", "k_composite_bwd_list_views",
+                                   "kb_setup", "kb_preprocess", "kb_scan_tiles", "kb_emit",
+                                   "kb_sort_tiles", "kb_sort_tiles_mid", "kb_sort_tiles_large",
+                                   "kb_sort_tiles_long", "kb_sort_tiles_xl", "kb_composite_fwd",
+                                   "kb_masked_l1", "kb_composite_bwd_list_pose",
+                                   "kb_composite_bwd_pose", "kb_finalize"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -154,6 +161,20 @@ struct vt_ctx {
     std::vector<cudaEvent_t> event_pool;
     int64_t t_launches[K_NUM] = {0};
     double t_ms[K_NUM] = {0};
+    // batched launches (vt_batch_*): the arena above sized for the batch
+    // totals, plus the work-item table (device copy and pinned staging), the
+    // image gradients (4 floats per pixel), masked-L1 block partials and the
+    // items' pose copies
+    bool batch = false;           // reserved for batches
+    bool batch_set = false;       // a table is staged
+    bool batch_lists = false;     // per-pixel lists kept for the batch backward
+    int64_t bcap_g = 0, bcap_p = 0, bcap_t = 0, bcap_i = 0, bcap_v = 0, bcap_tab = 0;
+    BatchTable *btab = nullptr, *btab_host = nullptr;
+    void *barena = nullptr;
+    float *bgrads = nullptr;
+    double *bl1 = nullptr, *bpose = nullptr;
+    cudaEvent_t bev_upload = nullptr;
+    bool bev_pending = false;
 };
 
 namespace {
@@ -366,7 +387,11 @@ void vt_ctx_destroy(vt_ctx *c) {
     if (c->loss_part) cudaFreeAsync(c->loss_part, c->stream);
     if (c->ssim_buf) cudaFreeAsync(c->ssim_buf, c->stream);
     if (c->view_part) cudaFreeAsync(c->view_part, c->stream);
+    if (c->btab) cudaFreeAsync(c->btab, c->stream);
+    if (c->barena) cudaFreeAsync(c->barena, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->btab_host) cudaFreeHost(c->btab_host);
+    if (c->bev_upload) cudaEventDestroy(c->bev_upload);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -1183,6 +1208,317 @@ vt_status vt_section_complement(const float *depth, const float *rgb, const floa
         (uint32_t)((int64_t)view * plane), src, colour, opacity, radius, cap);
     cudaFreeAsync(counts, stream);
     VT_CUDA(cudaGetLastError(), "vt_section_complement launch");
+    return VT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched work items.
+
+size_t vt_batch_workspace_bytes(int64_t max_gaussians, int64_t max_pixels, int64_t max_tiles,
+                                int64_t max_instances, int64_t max_views,
+                                int64_t max_table_rows, int32_t list_cap) {
+    if (max_gaussians < 0 || max_pixels < 0 || max_tiles < 0 || max_instances < 0 ||
+        max_views < 0 || max_table_rows < 0 || list_cap < 0)
+        return 0;
+    return arena_bytes_for(max_gaussians, max_instances, max_pixels, max_tiles, max_views,
+                           max_table_rows) +
+           sizeof(BatchTable) + align_up(sizeof(float) * 4 * max_pixels) +
+           align_up(sizeof(double) * 2 * (max_pixels / 256 + 1)) +
+           align_up(sizeof(double) * 12 * kMaxItems) +
+           sizeof(uint2) * (size_t)list_cap * (size_t)max_pixels;
+}
+
+vt_status vt_batch_reserve(vt_ctx *c, int64_t max_gaussians, int64_t max_pixels,
+                           int64_t max_tiles, int64_t max_instances, int64_t max_views,
+                           int64_t max_table_rows, vt_stream stream) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_batch_reserve: ctx is NULL");
+    if (max_gaussians <= 0 || max_pixels <= 0 || max_tiles <= 0 || max_instances <= 0 ||
+        max_views <= 0 || max_table_rows <= 0 || max_gaussians >= (int64_t)0xffffffffll ||
+        max_instances >= (int64_t)0xffffffffll || max_tiles > (int64_t)0x7fffffff)
+        return fail(VT_ERR_INVALID_ARG, "vt_batch_reserve: capacities out of range");
+    // every item's Gaussian and pixel ranges start at a multiple of 256
+    const int64_t g = max_gaussians + 256 * (int64_t)kMaxItems;
+    const int64_t p = max_pixels + 256 * (int64_t)kMaxItems;
+    c->stream = stream;
+    vt_status st = ensure(c, g, max_instances, p, max_tiles, max_views, max_table_rows, stream);
+    if (st) return st;
+    if (!c->btab_host) {
+        VT_CUDA(cudaMallocHost(&c->btab_host, sizeof(BatchTable)), "batch table staging");
+        VT_CUDA(cudaEventCreateWithFlags(&c->bev_upload, cudaEventDisableTiming),
+                "batch upload event");
+    }
+    if (!c->btab) {
+        void *q = nullptr;
+        VT_CUDA(cudaMallocAsync(&q, sizeof(BatchTable), stream), "batch table");
+        c->btab = static_cast<BatchTable *>(q);
+    }
+    if (c->barena) cudaFreeAsync(c->barena, stream);
+    c->barena = nullptr;
+    const size_t gb = align_up(sizeof(float) * 4 * p), lb = align_up(sizeof(double) * 2 * (p / 256 + 1));
+    const size_t pb = align_up(sizeof(double) * 12 * kMaxItems);
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, gb + lb + pb, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VT_ERR_OOM, "vt_batch_reserve: %zu bytes: %s", gb + lb + pb,
+                    cudaGetErrorString(e));
+    }
+    c->barena = q;
+    c->bgrads = static_cast<float *>(q);
+    c->bl1 = reinterpret_cast<double *>(static_cast<char *>(q) + gb);
+    c->bpose = reinterpret_cast<double *>(static_cast<char *>(q) + gb + lb);
+    // per-pixel lists for the tracking items' backward, within the budget
+    c->batch_lists = false;
+    if (c->list_cap > 0) {
+        const size_t need = sizeof(uint2) * (size_t)c->list_cap * (size_t)p;
+        if (c->arena_bytes + need <= c->budget) {
+            if (need > c->plist_bytes) {
+                if (c->plist) cudaFreeAsync(c->plist, stream);
+                c->plist = nullptr;
+                c->plist_bytes = 0;
+                void *r = nullptr;
+                if (cudaMallocAsync(&r, need, stream) == cudaSuccess) {
+                    c->plist = static_cast<uint2 *>(r);
+                    c->plist_bytes = need;
+                } else {
+                    cudaGetLastError();
+                }
+            }
+            c->batch_lists = c->plist != nullptr;
+        }
+    }
+    if (!sort_attr_set) {
+        for (auto kern : {k_sort_tiles, k_sort_tiles_mid, k_sort_tiles_large, k_sort_tiles_long})
+            VT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSortSmemBigBytes),
+                    "sort smem attribute");
+        sort_attr_set = true;
+    }
+    for (auto kern : {kb_sort_tiles, kb_sort_tiles_mid, kb_sort_tiles_large, kb_sort_tiles_long})
+        VT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSortSmemBigBytes),
+                "batch sort smem attribute");
+    c->bcap_g = g;
+    c->bcap_p = p;
+    c->bcap_t = max_tiles;
+    c->bcap_i = max_instances;
+    c->bcap_v = max_views;
+    c->bcap_tab = max_table_rows;
+    c->batch = true;
+    c->batch_set = false;
+    c->has_render = false;
+    return VT_OK;
+}
+
+vt_status vt_batch_set(vt_ctx *c, const vt_section *secs, int32_t n_secs,
+                       const vt_batch_item *items, int32_t n_items, vt_l1_weights w) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_batch_set: ctx is NULL");
+    if (!c->batch) return fail(VT_ERR_STATE, "vt_batch_set: call vt_batch_reserve first");
+    if (n_items < 1 || n_items > kMaxItems || !items)
+        return fail(VT_ERR_INVALID_ARG, "vt_batch_set: n_items must be in [1, %d]", kMaxItems);
+    if (n_secs < 1 || n_secs > kMaxItems || !secs)
+        return fail(VT_ERR_INVALID_ARG, "vt_batch_set: n_secs must be in [1, %d]", kMaxItems);
+    if (!std::isfinite(w.w_rgb) || !std::isfinite(w.w_depth))
+        return fail(VT_ERR_INVALID_ARG, "vt_batch_set: loss weights must be finite");
+    vt_status st;
+    for (int s = 0; s < n_secs; ++s) {
+        const vt_section &S = secs[s];
+        if (S.n < 0 || S.n >= (int64_t)0xffffffffll || S.n_views <= 0 || S.W <= 0 || S.H <= 0 ||
+            (int64_t)S.n_views * S.W * S.H > (int64_t)0xffffffffll)
+            return fail(VT_ERR_INVALID_ARG, "vt_batch_set: section %d sizes out of range", s);
+        if (S.prec != VT_F32 && S.prec != VT_F16)
+            return fail(VT_ERR_INVALID_ARG, "vt_batch_set: section %d precision unknown", s);
+        if (S.scale)
+            return fail(VT_ERR_INVALID_ARG, "vt_batch_set: section %d: batches take spheres only",
+                        s);
+        if ((st = check_intrinsics(S.K, "vt_batch_set section"))) return st;
+        if (S.n > 0 && (!S.poses || !S.depth || !S.src || !S.colour || !S.opacity || !S.radius))
+            return fail(VT_ERR_INVALID_ARG, "vt_batch_set: section %d has a NULL array", s);
+    }
+    // wait until the previous eager launch has uploaded the staged table
+    if (c->bev_pending) {
+        VT_CUDA(cudaEventSynchronize(c->bev_upload), "vt_batch_set: previous upload");
+        c->bev_pending = false;
+    }
+    BatchTable &B = *c->btab_host;
+    std::memset(&B, 0, sizeof(BatchTable));
+    int64_t g = 0, p = 0, tab = 0;
+    int64_t t = 0, v = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const vt_batch_item &It = items[i];
+        if (It.section < 0 || It.section >= n_secs)
+            return fail(VT_ERR_INVALID_ARG, "vt_batch_set: item %d names section %d", i,
+                        It.section);
+        if ((st = check_image(It.W, It.H, "vt_batch_set item"))) return st;
+        if ((st = check_intrinsics(It.K, "vt_batch_set item"))) return st;
+        if (!It.pose12 || !It.image || (It.track && (!It.obs || !It.result)))
+            return fail(VT_ERR_INVALID_ARG, "vt_batch_set: item %d has a NULL pointer", i);
+        const vt_section &S = secs[It.section];
+        BatchItem &I = B.it[i];
+        I.cam.fx = It.K.fx;
+        I.cam.fy = It.K.fy;
+        I.cam.cx = It.K.cx;
+        I.cam.cy = It.K.cy;
+        I.cam.W = It.W;
+        I.cam.H = It.H;
+        I.cam.tiles_x = (It.W + kTile - 1) / kTile;
+        I.cam.tiles_y = (It.H + kTile - 1) / kTile;
+        I.pose = It.pose12;
+        I.image = It.image;
+        I.obs = It.obs;
+        I.result = It.result;
+        I.gbase = g;
+        I.n = S.n;
+        I.pbase = p;
+        I.tab_base = tab;
+        I.tbase = (int32_t)t;
+        I.vbase = (int32_t)v;
+        I.sec = It.section;
+        I.track = It.track ? 1 : 0;
+        g += (S.n + 255) / 256 * 256;
+        p += ((int64_t)It.W * It.H + 255) / 256 * 256;
+        t += (int64_t)I.cam.tiles_x * I.cam.tiles_y;
+        v += S.n_views;
+        tab += (int64_t)S.n_views * (S.W + S.H);
+    }
+    if (g > c->bcap_g || p > c->bcap_p || t > c->bcap_t || v > c->bcap_v || tab > c->bcap_tab)
+        return fail(VT_ERR_CAPACITY,
+                    "vt_batch_set: batch needs %lld Gaussian slots, %lld pixels, %lld tiles, "
+                    "%lld views, %lld table rows; reserved %lld, %lld, %lld, %lld, %lld",
+                    (long long)g, (long long)p, (long long)t, (long long)v, (long long)tab,
+                    (long long)c->bcap_g, (long long)c->bcap_p, (long long)c->bcap_t,
+                    (long long)c->bcap_v, (long long)c->bcap_tab);
+    for (int s = 0; s < n_secs; ++s) {
+        const vt_section &S = secs[s];
+        SecDesc &D = B.sec[s];
+        D.poses = S.poses;
+        D.depth = S.depth;
+        D.src = S.src;
+        D.colour = S.colour;
+        D.opacity = S.opacity;
+        D.radius = S.radius;
+        D.n = S.n;
+        D.n_views = S.n_views;
+        D.W = S.W;
+        D.H = S.H;
+        D.prec = (int32_t)S.prec;
+        D.fx = S.K.fx;
+        D.fy = S.K.fy;
+        D.cx = S.K.cx;
+        D.cy = S.K.cy;
+    }
+    B.n_items = n_items;
+    B.n_secs = n_secs;
+    B.n_tiles = (int32_t)t;
+    B.n_views = (int32_t)v;
+    B.n_gauss = g;
+    B.n_pix = p;
+    B.w_rgb = w.w_rgb;
+    B.w_depth = w.w_depth;
+    B.sil_min = w.sil_min;
+    B.rgb_needs_depth = w.rgb_needs_depth ? 1 : 0;
+    c->batch_set = true;
+    return VT_OK;
+}
+
+vt_status vt_batch_launch(vt_ctx *c, vt_stream stream) {
+    if (!c) return fail(VT_ERR_INVALID_ARG, "vt_batch_launch: ctx is NULL");
+    if (!c->batch || !c->batch_set)
+        return fail(VT_ERR_STATE, "vt_batch_launch: no batch staged (vt_batch_set)");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    VT_CUDA(cudaStreamIsCapturing(stream, &cs), "capture query");
+    c->stream = stream;
+    c->has_render = false;   // the batch overwrites a single render's state
+    const int nsm = c->n_sm;
+    BatchTable *B = c->btab;
+    VT_CUDA(cudaMemcpyAsync(B, c->btab_host, sizeof(BatchTable), cudaMemcpyHostToDevice, stream),
+            "batch table upload");
+    if (cs == cudaStreamCaptureStatusNone) {
+        VT_CUDA(cudaEventRecord(c->bev_upload, stream), "batch upload event");
+        c->bev_pending = true;
+    }
+    {
+        LaunchScope ls(c, KB_SETUP, stream);
+        kb_setup<<<2 * nsm, 256, 0, stream>>>(B, c->views, c->tab, c->bpose, c->tile_count);
+    }
+    {
+        LaunchScope ls(c, KB_PREPROCESS, stream);
+        kb_preprocess<<<8 * nsm, 256, 0, stream>>>(B, c->views, c->tab, c->geo, c->app, c->info,
+                                                   c->tile_count);
+    }
+    {
+        LaunchScope ls(c, KB_SCAN, stream);
+        kb_scan_tiles<<<1, 1024, 0, stream>>>(B, c->tile_count, c->tile_off, c->tile_cursor,
+                                              c->status, (unsigned long long)c->bcap_i);
+    }
+    {
+        LaunchScope ls(c, KB_EMIT, stream);
+        kb_emit<<<8 * nsm, 256, 0, stream>>>(B, c->info, c->tile_cursor, c->bucket, c->bmask_u,
+                                             c->status);
+    }
+    VT_CUDA(cudaEventRecord(c->ev_fork, stream), "sort fork");
+    VT_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "sort fork");
+    {
+        LaunchScope ls(c, KB_SORT_LONG, c->aux);
+        kb_sort_tiles_long<<<nsm, 512, kSortSmemBigBytes, c->aux>>>(
+            B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
+            kSortSmemBig, kSortSmemN, kSortSmemBig);
+    }
+    {
+        LaunchScope ls(c, KB_SORT_XL, c->aux);
+        kb_sort_tiles_xl<<<2 * nsm, 512, kSortHistBytes, c->aux>>>(
+            B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
+            kSortSmemBig, kSortSmemBig, 0x7fffffff);
+    }
+    VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
+    {
+        LaunchScope ls(c, KB_SORT, stream);
+        kb_sort_tiles<<<4 * nsm, 512, sort_smem_bytes(kSortClassS), stream>>>(
+            B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
+            kSortClassS, 0, kSortClassS);
+    }
+    {
+        LaunchScope ls(c, KB_SORT_M, stream);
+        kb_sort_tiles_mid<<<3 * nsm, 512, sort_smem_bytes(kSortClassM), stream>>>(
+            B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
+            kSortClassM, kSortClassS, kSortClassM);
+    }
+    {
+        LaunchScope ls(c, KB_SORT_L, stream);
+        kb_sort_tiles_large<<<2 * nsm, 512, kSortSmemBytes, stream>>>(
+            B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
+            kSortSmemN, kSortClassM, kSortSmemN);
+    }
+    VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
+    const int cap = c->batch_lists ? c->list_cap : 0;
+    {
+        LaunchScope ls(c, KB_FWD, stream);
+        kb_composite_fwd<<<6 * nsm, kBlockPix, 0, stream>>>(
+            B, &B->ctr[0], c->tile_off, c->sorted, c->bmask, c->geo, c->app, c->pix_last,
+            c->pix_nadd, c->pix_T, c->batch_lists ? c->plist : nullptr, cap, c->blk_ovf,
+            c->status);
+    }
+    {
+        LaunchScope ls(c, KB_L1, stream);
+        kb_masked_l1<<<8 * nsm, 256, 0, stream>>>(B, c->bgrads, c->bl1);
+    }
+    if (c->batch_lists) {
+        LaunchScope ls(c, KB_BWD_LIST, stream);
+        kb_composite_bwd_list_pose<<<3 * nsm, kBlockPix, 0, stream>>>(
+            B, &B->ctr[1], c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, cap, c->blk_ovf,
+            c->bgrads, c->pose_partials, c->status);
+    }
+    {
+        LaunchScope ls(c, KB_BWD, stream);
+        kb_composite_bwd_pose<<<2 * nsm, kBlockPix, 0, stream>>>(
+            B, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, c->blk_ovf,
+            c->bgrads, c->pose_partials, c->status);
+    }
+    {
+        LaunchScope ls(c, KB_FINALIZE, stream);
+        kb_finalize<<<kMaxItems, 384, 0, stream>>>(B, c->bl1, c->pose_partials, c->bpose);
+    }
+    VT_CUDA(cudaGetLastError(), "vt_batch_launch");
     return VT_OK;
 }
 

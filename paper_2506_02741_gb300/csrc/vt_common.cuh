@@ -86,6 +86,68 @@ struct Status {
 };
 
 // ---------------------------------------------------------------------------
+// Batched launches (vt_batch_*): many independent work items -- one section
+// rendered from one camera each, a tracking item adding the Eq. 1 masked L1
+// loss and the pose gradient -- processed by one persistent launch per
+// stage.  The work-item table lives in device memory (uploaded from pinned
+// host memory at the start of the launch sequence), so one captured launch
+// sequence serves any mix of items within the reserved capacity.  The index
+// spaces are concatenated over the items: Gaussians and pixels (each item's
+// range starts at a multiple of 256, so a block of 256 never holds two
+// items), tiles, views and per-view table rows.
+constexpr int kMaxItems = 64;
+constexpr int kBatchResult = 19;   // loss, dL/dtwist (6), dL/dR (9), dL/dt (3)
+
+struct BatchItem {
+    Camera cam;
+    const double *pose;          // 12 doubles, camera-to-world
+    float *image;                // 5 x H x W: rgb planes, depth, silhouette
+    const float *obs;            // 4 x H x W: observed rgb planes and depth (track)
+    double *result;              // kBatchResult doubles (track)
+    int64_t gbase, n;            // Gaussians [gbase, gbase + n)
+    int64_t pbase;               // first pixel of the per-pixel arrays
+    int64_t tab_base;            // first per-view table row
+    int32_t tbase, vbase;        // first tile, first view
+    int32_t sec, track;          // section (index into BatchTable::sec), tracking item?
+};
+
+struct BatchTable {
+    int32_t n_items, n_secs;
+    int32_t n_tiles, n_views;    // totals
+    int64_t n_gauss, n_pix;      // ends of the last item's (padded) ranges
+    double w_rgb, w_depth;       // Eq. 1 weights (alpha, beta)
+    float sil_min;               // covered iff silhouette > sil_min
+    int32_t rgb_needs_depth;
+    uint32_t ctr[4];             // work counters of the persistent stages (zero on upload)
+    BatchItem it[kMaxItems];
+    SecDesc sec[kMaxItems];      // gbase, view_base, tab_base unused (per item instead)
+};
+
+// Last item whose range starts at or before x (binary search; items in order).
+template <typename F>
+__device__ __forceinline__ int batch_find(int n, F start_of, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start_of(mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int item_of_gauss(const BatchTable &B, int64_t g) {
+    return batch_find(B.n_items, [&](int i) { return B.it[i].gbase; }, g);
+}
+__device__ __forceinline__ int item_of_tile(const BatchTable &B, int64_t t) {
+    return batch_find(B.n_items, [&](int i) { return (int64_t)B.it[i].tbase; }, t);
+}
+__device__ __forceinline__ int item_of_view(const BatchTable &B, int64_t v) {
+    return batch_find(B.n_items, [&](int i) { return (int64_t)B.it[i].vbase; }, v);
+}
+__device__ __forceinline__ int item_of_pixel(const BatchTable &B, int64_t p) {
+    return batch_find(B.n_items, [&](int i) { return B.it[i].pbase; }, p);
+}
+
+// ---------------------------------------------------------------------------
 // float-float ("double-single") arithmetic: Knuth's TwoSum, Dekker's
 // FastTwoSum and the FMA-based exact product.  Every operation uses the
 // explicit round-to-nearest intrinsics so that no contraction or
@@ -352,6 +414,46 @@ __global__ void k_view_grads(SecTable T, const float4 *accg, const double *pose_
 __global__ void k_view_finalize(SecTable T, const double *pose_copy, const double *partials,
                                 int n_views);
 __global__ void k_attr_scatter(SecTable T, const float4 *acc4, const float *accr);
+
+// Batched launches (see BatchTable): one persistent launch per stage.
+__global__ void kb_setup(const BatchTable *B, ViewXf *views, TabRow *tab, double *pose_copy,
+                         uint32_t *tile_count);
+__global__ void kb_preprocess(const BatchTable *B, const ViewXf *views, const TabRow *tab,
+                              float4 *geo, float4 *app, uint4 *info, uint32_t *tile_count);
+__global__ void kb_scan_tiles(const BatchTable *B, const uint32_t *tile_count, uint32_t *tile_off,
+                              uint32_t *tile_cursor, Status *st, unsigned long long cap);
+__global__ void kb_emit(const BatchTable *B, const uint4 *info, uint32_t *tile_cursor,
+                        unsigned long long *bucket, uint8_t *bmask_u, const Status *st);
+#define VT_DECLARE_SORT_B(name)                                                                  \
+    __global__ void name(const BatchTable *B, const uint32_t *tile_off,                          \
+                         unsigned long long *bucket, unsigned long long *alt,                    \
+                         const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,               \
+                         const float4 *geo, Status *st, int smem_n, int lo, int hi);
+VT_DECLARE_SORT_B(kb_sort_tiles)
+VT_DECLARE_SORT_B(kb_sort_tiles_mid)
+VT_DECLARE_SORT_B(kb_sort_tiles_large)
+VT_DECLARE_SORT_B(kb_sort_tiles_long)
+VT_DECLARE_SORT_B(kb_sort_tiles_xl)
+#undef VT_DECLARE_SORT_B
+__global__ void kb_composite_fwd(const BatchTable *B, uint32_t *ctr, const uint32_t *tile_off,
+                                 const uint32_t *sorted, const uint8_t *bmask, const float4 *geo,
+                                 const float4 *app, uint32_t *pix_last, uint32_t *pix_nadd,
+                                 float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
+                                 const Status *st);
+__global__ void kb_masked_l1(const BatchTable *B, float *grads, double *l1_part);
+__global__ void kb_composite_bwd_list_pose(const BatchTable *B, uint32_t *ctr, const float4 *geo,
+                                           const float4 *app, const uint32_t *pix_nadd,
+                                           const float *pix_T, const uint2 *plist, int plist_cap,
+                                           const uint32_t *blk_ovf, const float *grads,
+                                           double *pose_partials, const Status *st);
+__global__ void kb_composite_bwd_pose(const BatchTable *B, const uint32_t *tile_off,
+                                      const uint32_t *sorted, const float4 *geo,
+                                      const float4 *app, const uint32_t *pix_last,
+                                      const float *pix_T, const uint32_t *blk_ovf,
+                                      const float *grads, double *pose_partials,
+                                      const Status *st);
+__global__ void kb_finalize(const BatchTable *B, const double *l1_part,
+                            const double *pose_partials, const double *pose_copy);
 
 // Loss inputs (vt_loss.cu).
 struct VisView {

@@ -124,9 +124,9 @@ constexpr int kQueue = 256;   // ring of list indices per warp (>= 31 + 128)
 
 template <bool Aniso>
 __device__ __forceinline__ void fwd_body(
-    const Camera &cam, const uint32_t *tile_off, const uint32_t *sorted, const uint8_t *bmask,
-    const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
-    uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
+    const Camera &cam, int tile, const uint32_t *tile_off, const uint32_t *sorted,
+    const uint8_t *bmask, const float4 *geo, const float4 *app, float *rgb, float *depth,
+    float *sil, uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
     uint32_t *blk_ovf, const Status *st) {
     // two staging halves of 32 entries per warp (see the walk below)
     __shared__ float4 s_f[kWarps][64], s_k[kWarps][64], s_c[kWarps][64];
@@ -146,8 +146,8 @@ __device__ __forceinline__ void fwd_body(
     uint32_t (&q)[kQueue] = s_q[warp];
     const size_t HW = (size_t)cam.W * cam.H;
 
-    const int item = blockIdx.x * kWarps + warp;
-    const int tile = blockIdx.x, sub = warp;
+    const int item = tile * kWarps + warp;
+    const int sub = warp;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int bx0 = tx * kTile + (sub & 1) * 8, by0 = ty * kTile + (sub >> 1) * 4;
     const int px = bx0 + lx, py = by0 + ly;
@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd(
     const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
     uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
     uint32_t *blk_ovf, const Status *st) {
-    fwd_body<false>(cam, tile_off, sorted, bmask, geo, app, rgb, depth, sil, pix_last, pix_nadd,
-                    pix_T, plist, plist_cap, blk_ovf, st);
+    fwd_body<false>(cam, blockIdx.x, tile_off, sorted, bmask, geo, app, rgb, depth, sil, pix_last,
+                    pix_nadd, pix_T, plist, plist_cap, blk_ovf, st);
 }
 
 __global__ void __launch_bounds__(kBlockPix) k_composite_fwd_aniso(
@@ -353,8 +353,37 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_fwd_aniso(
     const float4 *geo, const float4 *app, float *rgb, float *depth, float *sil,
     uint32_t *pix_last, uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap,
     uint32_t *blk_ovf, const Status *st) {
-    fwd_body<true>(cam, tile_off, sorted, bmask, geo, app, rgb, depth, sil, pix_last, pix_nadd,
-                   pix_T, plist, plist_cap, blk_ovf, st);
+    fwd_body<true>(cam, blockIdx.x, tile_off, sorted, bmask, geo, app, rgb, depth, sil, pix_last,
+                   pix_nadd, pix_T, plist, plist_cap, blk_ovf, st);
+}
+
+// Next tile of a persistent batched stage: thread 0 takes it from the work
+// counter, the block reads it after a barrier.
+__device__ __forceinline__ int next_tile(uint32_t *ctr) {
+    __shared__ int s_next;
+    __syncthreads();   // every thread has read the previous value
+    if (threadIdx.x == 0) s_next = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    return s_next;
+}
+
+// Batched forward: the tiles of every work item, taken one at a time from a
+// work counter by a persistent grid; each item's images are its own image
+// planes (rgb, depth, silhouette) and its per-pixel state starts at pbase.
+__global__ void __launch_bounds__(kBlockPix, 3) kb_composite_fwd(
+    const BatchTable *Bp, uint32_t *ctr, const uint32_t *tile_off, const uint32_t *sorted,
+    const uint8_t *bmask, const float4 *geo, const float4 *app, uint32_t *pix_last,
+    uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
+    const Status *st) {
+    const BatchTable &B = *Bp;
+    for (int t = next_tile(ctr); t < B.n_tiles; t = next_tile(ctr)) {
+        const BatchItem &I = B.it[item_of_tile(B, t)];
+        const int64_t P = (int64_t)I.cam.W * I.cam.H;
+        fwd_body<false>(I.cam, t - I.tbase, tile_off + I.tbase, sorted, bmask, geo, app, I.image,
+                        I.image + 3 * P, I.image + 4 * P, pix_last + I.pbase, pix_nadd + I.pbase,
+                        pix_T + I.pbase, plist ? plist + I.pbase * (int64_t)plist_cap : nullptr,
+                        plist_cap, blk_ovf + (int64_t)I.tbase * kWarps, st);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -685,14 +714,13 @@ __device__ __forceinline__ void replay_body(
     const float4 *geo, const float4 *app, const uint32_t *pix_last, const float *pix_T,
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
     double *pose_partials, const uint32_t *tile_mask, float4 *acc4, float *accr, float4 *accg,
-    float2 *accm, const Status *st) {
+    float2 *accm, const Status *st, int tile) {
     __shared__ float4 s_g0[kBatch], s_g1[kBatch], s_a[kBatch];
     __shared__ float s_tmin[kBatch];
     __shared__ uint32_t s_gid[kBatch];
     __shared__ double s_pose[kBlockPix / 32][12];
     __shared__ uint32_t s_last;
     if (st->flags) return;
-    const int tile = blockIdx.x;
     if (tile_mask && !tile_flagged(tile_mask, tile)) return;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -811,7 +839,8 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd(
     double *pose_partials, const uint32_t *tile_mask, float4 *acc4, float *accr, float4 *accg,
     const Status *st) {
     replay_body<false>(Tab, cam, tile_off, sorted, geo, app, pix_last, pix_T, g_rgb, g_depth,
-                       g_sil, mode, pose_partials, tile_mask, acc4, accr, accg, nullptr, st);
+                       g_sil, mode, pose_partials, tile_mask, acc4, accr, accg, nullptr, st,
+                       blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kBlockPix) k_composite_bwd_aniso(
@@ -820,7 +849,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd_aniso(
     const float *g_depth, const float *g_sil, int mode, const uint32_t *tile_mask, float4 *acc4,
     float4 *accg, float2 *accm, const Status *st) {
     replay_body<true>(Tab, cam, tile_off, sorted, geo, app, pix_last, pix_T, g_rgb, g_depth,
-                      g_sil, mode, nullptr, tile_mask, acc4, nullptr, accg, accm, st);
+                      g_sil, mode, nullptr, tile_mask, acc4, nullptr, accg, accm, st, blockIdx.x);
 }
 
 // Per-pixel list replay: every lane walks the ids its pixel added, recorded
@@ -840,9 +869,8 @@ __device__ __forceinline__ void bwd_list_body(
     const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
     const uint32_t *blk_ovf, const float *g_rgb, const float *g_depth, const float *g_sil,
     int mode, double *pose_partials, float4 *acc4, float *accr, float4 *accg, float2 *accm,
-    const Status *st, double (*s_pose)[12]) {
+    const Status *st, double (*s_pose)[12], int tile) {
     if (st->flags) return;
-    const int tile = blockIdx.x;
     if (tile_flagged(blk_ovf, tile)) return;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -925,7 +953,7 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
     __shared__ double s_pose[kBlockPix / 32][12];
     bwd_list_body<false, false>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf,
                                 g_rgb, g_depth, g_sil, mode, pose_partials, acc4, accr, accg,
-                                nullptr, st, s_pose);
+                                nullptr, st, s_pose, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_pose(
@@ -936,7 +964,7 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_pose(
     __shared__ double s_pose[kBlockPix / 32][12];
     bwd_list_body<false, false, true>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap,
                                       blk_ovf, g_rgb, g_depth, g_sil, VT_GRAD_POSE, pose_partials,
-                                      acc4, accr, accg, nullptr, st, s_pose);
+                                      acc4, accr, accg, nullptr, st, s_pose, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_aniso(
@@ -947,7 +975,7 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_aniso(
     const Status *st) {
     bwd_list_body<false, true>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf,
                                g_rgb, g_depth, g_sil, mode, pose_partials, acc4, accr, accg, accm,
-                               st, nullptr);
+                               st, nullptr, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_views(
@@ -958,7 +986,7 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_views(
     __shared__ double s_pose[kBlockPix / 32][12];
     bwd_list_body<true, false>(Tab, cam, geo, app, pix_nadd, pix_T, plist, plist_cap, blk_ovf,
                                g_rgb, g_depth, g_sil, mode, pose_partials, acc4, accr, accg,
-                               nullptr, st, s_pose);
+                               nullptr, st, s_pose, blockIdx.x);
 }
 
 // Ellipsoids, one thread per Gaussian (grid-stride; one FP64 pose partial
@@ -1272,13 +1300,64 @@ __global__ void k_view_finalize(SecTable Tab, const double *pose_copy, const dou
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched pose backward of the tracking items.  The per-Gaussian terms are
+// not formed (pose only), so the section table the bodies take is an empty
+// one.
+__device__ SecTable g_no_sections;
+
+// Per-pixel list walks: tiles of tracking items taken from a work counter;
+// each item's upstream gradient is its planes of `grads` (4 x P from 4 pbase:
+// rgb, depth), its pose terms go to pose_partials[12 t] per tile t.  Tiles
+// whose lists overflowed are left to kb_composite_bwd_pose.
+__global__ void __launch_bounds__(kBlockPix, 3) kb_composite_bwd_list_pose(
+    const BatchTable *Bp, uint32_t *ctr, const float4 *geo, const float4 *app,
+    const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
+    const uint32_t *blk_ovf, const float *grads, double *pose_partials, const Status *st) {
+    __shared__ double s_pose[kBlockPix / 32][12];
+    const BatchTable &B = *Bp;
+    for (int t = next_tile(ctr); t < B.n_tiles; t = next_tile(ctr)) {
+        const BatchItem &I = B.it[item_of_tile(B, t)];
+        if (!I.track) continue;
+        const int64_t P = (int64_t)I.cam.W * I.cam.H;
+        const float *g = grads + 4 * I.pbase;
+        bwd_list_body<false, false, true>(
+            g_no_sections, I.cam, geo, app, pix_nadd + I.pbase, pix_T + I.pbase,
+            plist + I.pbase * (int64_t)plist_cap, plist_cap, blk_ovf + (int64_t)I.tbase * kWarps,
+            g, g + 3 * P, nullptr, VT_GRAD_POSE, pose_partials + 12 * (int64_t)I.tbase, nullptr,
+            nullptr, nullptr, nullptr, st, s_pose, t - I.tbase);
+    }
+}
+
+// Tile replay of the tracking items' tiles whose per-pixel lists overflowed
+// (blk_ovf; all of them when the batch keeps no lists).
+__global__ void __launch_bounds__(kBlockPix) kb_composite_bwd_pose(
+    const BatchTable *Bp, const uint32_t *tile_off, const uint32_t *sorted, const float4 *geo,
+    const float4 *app, const uint32_t *pix_last, const float *pix_T, const uint32_t *blk_ovf,
+    const float *grads, double *pose_partials, const Status *st) {
+    const BatchTable &B = *Bp;
+    for (int t = blockIdx.x; t < B.n_tiles; t += gridDim.x) {
+        const BatchItem &I = B.it[item_of_tile(B, t)];
+        if (!I.track) continue;
+        const int64_t P = (int64_t)I.cam.W * I.cam.H;
+        const float *g = grads + 4 * I.pbase;
+        replay_body<false>(g_no_sections, I.cam, tile_off + I.tbase, sorted, geo, app,
+                           pix_last + I.pbase, pix_T + I.pbase, g, g + 3 * P, nullptr,
+                           VT_GRAD_POSE, pose_partials + 12 * (int64_t)I.tbase,
+                           blk_ovf + (int64_t)I.tbase * kWarps, nullptr, nullptr, nullptr,
+                           nullptr, st, t - I.tbase);
+        __syncthreads();   // shared staging is reused by the next tile
+    }
+}
+
 // Fixed-order FP64 sum of the per-tile partials, then
 //   twist: dL/drho = -s,  dL/dphi = (A21 - A12, A02 - A20, A10 - A01)
 //   matrix: dL/dR = R A,  dL/dt = -R s          (A_ab = sum x_a g_b)
 // accumulated (+=) into the outputs.
-__global__ void __launch_bounds__(384) k_pose_finalize(const double *partials, int n_parts,
-                                                       const double *pose_copy, double *d_twist,
-                                                       double *d_mat) {
+// With overwrite the outputs are set instead of accumulated.  384 threads.
+__device__ __forceinline__ void pose_finalize_body(const double *partials, int n_parts,
+                                                   const double *pose_copy, double *d_twist,
+                                                   double *d_mat, bool overwrite) {
     __shared__ double tot[12];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double v = 0.0;
@@ -1288,6 +1367,10 @@ __global__ void __launch_bounds__(384) k_pose_finalize(const double *partials, i
     __syncthreads();
     if (threadIdx.x == 0) {
         const double *A = tot, *s = tot + 9, *R = pose_copy;
+        if (overwrite) {
+            for (int i = 0; i < 6; ++i) d_twist[i] = 0.0;
+            for (int i = 0; i < 12; ++i) d_mat[i] = 0.0;
+        }
         if (d_twist) {
             d_twist[0] -= s[0];
             d_twist[1] -= s[1];
@@ -1306,6 +1389,56 @@ __global__ void __launch_bounds__(384) k_pose_finalize(const double *partials, i
             for (int b = 0; b < 3; ++b)
                 d_mat[9 + b] -= R[b * 3 + 0] * s[0] + R[b * 3 + 1] * s[1] + R[b * 3 + 2] * s[2];
         }
+    }
+}
+
+
+__global__ void __launch_bounds__(384) k_pose_finalize(const double *partials, int n_parts,
+                                                       const double *pose_copy, double *d_twist,
+                                                       double *d_mat) {
+    pose_finalize_body(partials, n_parts, pose_copy, d_twist, d_mat, false);
+}
+
+// Results of the batch's tracking items, one block of 384 per item in a
+// grid-stride loop: result[0] = Eq. 1 loss (the fixed-order sums of the
+// item's masked-L1 block partials l1_part[2 b], b from pbase / 256),
+// result[1..6] = dL/dtwist, result[7..18] = dL/dR and dL/dt (fixed-order FP64
+// sums of the item's tile partials), overwritten.
+__global__ void __launch_bounds__(384) kb_finalize(const BatchTable *Bp, const double *l1_part,
+                                                   const double *pose_partials,
+                                                   const double *pose_copy) {
+    __shared__ double s[2][12];
+    const BatchTable &B = *Bp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int it = blockIdx.x; it < B.n_items; it += gridDim.x) {
+        const BatchItem &I = B.it[it];
+        if (!I.track) continue;
+        const int64_t P = (int64_t)I.cam.W * I.cam.H;
+        const int64_t b0 = I.pbase / 256, nb = (P + 255) / 256;
+        double a = 0.0, b = 0.0;
+        for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+            a += l1_part[2 * (b0 + i)];
+            b += l1_part[2 * (b0 + i) + 1];
+        }
+        a = warp_sum_d(a);
+        b = warp_sum_d(b);
+        if (lane == 0) {
+            s[0][warp] = a;
+            s[1][warp] = b;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double A = 0.0, Bs = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                A += s[0][w];
+                Bs += s[1][w];
+            }
+            const double wc = B.w_rgb / (3.0 * (double)P), wd = B.w_depth / (double)P;
+            I.result[0] = __dadd_rn(__dmul_rn(wc, A), __dmul_rn(wd, Bs));
+        }
+        pose_finalize_body(pose_partials + 12 * (int64_t)I.tbase, I.cam.tiles_x * I.cam.tiles_y,
+                           pose_copy + 12 * it, I.result + 1, I.result + 7, true);
+        __syncthreads();
     }
 }
 

@@ -124,14 +124,16 @@ __device__ __forceinline__ ff shfl_xor_ff(ff a, int o) {
 // per addition) and over the block's eight warps in FP64; per block the two
 // sums (colour, depth) go to partials[2 b + i].  FP64 arithmetic is a narrow
 // pipe on this part, so no per-pixel step uses it.
-__global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, const float *depth,
-                                                   const float *sil, const float *obs_rgb,
-                                                   const float *obs_depth, const uint8_t *visible,
-                                                   float sil_min, int rgb_needs_depth, float gc,
-                                                   float gd, float *d_rgb, float *d_depth,
-                                                   double *partials) {
+// Pixel p of an image of P pixels (one block of 256 threads); the block's
+// two sums go to part[0, 1] (if part != NULL).
+__device__ __forceinline__ void masked_l1_block(int64_t P, int64_t p, const float *rgb,
+                                                const float *depth, const float *sil,
+                                                const float *obs_rgb, const float *obs_depth,
+                                                const uint8_t *visible, float sil_min,
+                                                int rgb_needs_depth, float gc, float gd,
+                                                float *d_rgb, float *d_depth, double *part) {
     __shared__ double s_sum[2][8];
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double *partials = part;
     ff sc{0.f, 0.f}, sd{0.f, 0.f};
     if (p < P) {
         const bool valid = valid_depth(obs_depth[p]);
@@ -164,7 +166,39 @@ __global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, 
     if (threadIdx.x < 2) {
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += s_sum[threadIdx.x][w];
-        partials[2 * blockIdx.x + threadIdx.x] = t;
+        part[threadIdx.x] = t;
+    }
+    __syncthreads();   // s_sum is reused by the block's next pixels
+}
+
+__global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, const float *depth,
+                                                   const float *sil, const float *obs_rgb,
+                                                   const float *obs_depth, const uint8_t *visible,
+                                                   float sil_min, int rgb_needs_depth, float gc,
+                                                   float gd, float *d_rgb, float *d_depth,
+                                                   double *partials) {
+    masked_l1_block(P, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, rgb, depth, sil, obs_rgb,
+                    obs_depth, visible, sil_min, rgb_needs_depth, gc, gd, d_rgb, d_depth,
+                    partials ? partials + 2 * blockIdx.x : nullptr);
+}
+
+// Batched form: the pixels of every tracking item in blocks of 256 (an
+// item's pixels start at a multiple of 256), Eq. 1 masks and weights of the
+// batch, the item's rendered planes from its image and the observed ones
+// from obs; the image gradient goes to grads (4 x P from 4 pbase: rgb,
+// depth) and the block sums to l1_part[2 b].
+__global__ void __launch_bounds__(256) kb_masked_l1(const BatchTable *Bp, float *grads,
+                                                    double *l1_part) {
+    const BatchTable &B = *Bp;
+    for (int64_t b = blockIdx.x; b * 256 < B.n_pix; b += gridDim.x) {
+        const BatchItem &I = B.it[item_of_pixel(B, b * 256)];
+        if (!I.track) continue;
+        const int64_t P = (int64_t)I.cam.W * I.cam.H;
+        const double wc = B.w_rgb / (3.0 * (double)P), wd = B.w_depth / (double)P;
+        float *g = grads + 4 * I.pbase;
+        masked_l1_block(P, b * 256 + threadIdx.x - I.pbase, I.image, I.image + 3 * P,
+                        I.image + 4 * P, I.obs, I.obs + 3 * P, nullptr, B.sil_min,
+                        B.rgb_needs_depth, (float)wc, (float)wd, g, g + 3 * P, l1_part + 2 * b);
     }
 }
 

@@ -17,18 +17,14 @@ constexpr unsigned kFull = 0xffffffffu;
 // (U0, V0, Z0) * a_u and row v: (U1, V1, Z1) * b_v + (U2, V2, Z2), with
 // a_u = (u - cx_k)/fx_k, b_v = (v - cy_k)/fy_k, so that the projected centre's
 // numerators are D * (A[u] + B[v]) + (mu, mv, mz).
-__global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const double *pose12,
-                                               ViewXf *views, TabRow *tab, double *pose_copy) {
+// View k of section S into camera (cam, pose12): X, its table rows tb (W + H
+// rows) and, if pose_copy != NULL, a copy of the pose for the backward.
+__device__ __forceinline__ void setup_view(const SecDesc &S, int k, const Camera &cam,
+                                           const double *pose12, ViewXf &X, TabRow *tb,
+                                           double *pose_copy) {
     __shared__ ff rows[9];  // U0 U1 U2 V0 V1 V2 Z0 Z1 Z2
     __shared__ double sM[12];
-    const int gv = blockIdx.x;
-    int s = 0;
-    for (int j = 1; j < T.n; ++j)
-        if (gv >= T.s[j].view_base) s = j;
-    const SecDesc &S = T.s[s];
-    const int k = gv - S.view_base;
     const int i = threadIdx.x;
-    ViewXf &X = views[gv];
     if (i < 12) {
         const double *R = pose12, *t = pose12 + 9;
         const double *Rk = S.poses + 12 * k, *tk = Rk + 9;
@@ -46,7 +42,7 @@ __global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const dou
         }
         sM[i] = acc;
         X.Mf[i] = __double2float_rn(acc);
-        if (gv == 0) pose_copy[i] = pose12[i];
+        if (pose_copy) pose_copy[i] = pose12[i];
     }
     __syncthreads();
     if (i < 12) {
@@ -67,7 +63,6 @@ __global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const dou
     }
     __syncthreads();
     const int W = S.W, H = S.H;
-    TabRow *tb = tab + S.tab_base + (int64_t)k * (W + H);
     for (int i = threadIdx.x; i < W + H; i += blockDim.x) {
         TabRow out;
         if (i < W) {
@@ -89,6 +84,38 @@ __global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const dou
         }
         out.pad = 0.f;
         tb[i] = out;
+    }
+    __syncthreads();   // rows / sM are reused by the block's next view
+}
+
+__global__ void __launch_bounds__(256) k_setup(SecTable T, Camera cam, const double *pose12,
+                                               ViewXf *views, TabRow *tab, double *pose_copy) {
+    const int gv = blockIdx.x;
+    int s = 0;
+    for (int j = 1; j < T.n; ++j)
+        if (gv >= T.s[j].view_base) s = j;
+    const SecDesc &S = T.s[s];
+    const int k = gv - S.view_base;
+    setup_view(S, k, cam, pose12, views[gv], tab + S.tab_base + (int64_t)k * (S.W + S.H),
+               gv == 0 ? pose_copy : nullptr);
+}
+
+// Batched form: one block per (item, view) in a grid-stride loop; item i's
+// pose is copied to pose_copy[12 i].  The grid also zeroes the tile counts
+// of k_preprocess (tile_count[0, n_tiles]).
+__global__ void __launch_bounds__(256) kb_setup(const BatchTable *Bp, ViewXf *views, TabRow *tab,
+                                                double *pose_copy, uint32_t *tile_count) {
+    const BatchTable &B = *Bp;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= B.n_tiles;
+         t += (int64_t)gridDim.x * blockDim.x)
+        tile_count[t] = 0u;
+    for (int gv = blockIdx.x; gv < B.n_views; gv += gridDim.x) {
+        const int it = item_of_view(B, gv);
+        const BatchItem &I = B.it[it];
+        const SecDesc &S = B.sec[I.sec];
+        const int k = gv - I.vbase;
+        setup_view(S, k, I.cam, I.pose, views[gv], tab + I.tab_base + (int64_t)k * (S.W + S.H),
+                   k == 0 ? pose_copy + 12 * it : nullptr);
     }
 }
 
@@ -206,17 +233,18 @@ __device__ __forceinline__ bool ellipse_footprint(const SecDesc &S, int64_t li, 
 // (see pair_t) and 1/r for the backward; info keeps the pixel box, the depth
 // key and the tile count.  Ellipsoids (Aniso) keep the conic instead (see
 // ellipse_footprint).
+// Gaussian li of section S (workspace slot gid; its views at view_base, its
+// table rows at tab_base): records, info and the pixel box r0, r1 with its
+// tile count nt (0 when culled).
 template <bool Aniso>
-__device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera &cam,
-                                                const ViewXf *views, const TabRow *tab,
-                                                float4 *geo, float4 *app, uint4 *info,
-                                                uint32_t *tile_count) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t r0 = 0, r1 = 0, nt = 0, zbits = 0;
-    if (gid < T.n_total) {
-        const int s = find_section(T, gid);
-        const SecDesc &S = T.s[s];
-        const int64_t li = gid - S.gbase;
+__device__ __forceinline__ void preprocess_gauss(const SecDesc &S, int64_t li, int64_t gid,
+                                                 int32_t view_base, int64_t tab_base,
+                                                 const Camera &cam, const ViewXf *views,
+                                                 const TabRow *tab, float4 *geo, float4 *app,
+                                                 uint4 *info, uint32_t &r0, uint32_t &r1,
+                                                 uint32_t &nt) {
+    uint32_t zbits = 0;
+    {
         const uint32_t src = S.src[li];
         const uint32_t plane = (uint32_t)S.W * (uint32_t)S.H;
         const uint32_t k = src / plane;
@@ -228,8 +256,8 @@ __device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera 
         const float o = ld_attr(S.opacity, S.prec, li);
         const float r = Aniso ? 1.f : ld_attr(S.radius, S.prec, li);
         bool ok = in_range && isfinite(D) && D > 0.f && o >= kAlphaMin && r > 0.f && isfinite(r);
-        const ViewXf &X = views[S.view_base + (ok ? k : 0)];
-        const TabRow *tb = tab + S.tab_base + (int64_t)(ok ? k : 0) * (S.W + S.H);
+        const ViewXf &X = views[view_base + (ok ? k : 0)];
+        const TabRow *tb = tab + tab_base + (int64_t)(ok ? k : 0) * (S.W + S.H);
         TabRow A, B;
         float zkey = 0.f;
         if (ok) {
@@ -301,6 +329,20 @@ __device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera 
         }
         info[gid] = make_uint4(r0, r1, zbits, nt);
     }
+}
+
+template <bool Aniso>
+__device__ __forceinline__ void preprocess_body(const SecTable &T, const Camera &cam,
+                                                const ViewXf *views, const TabRow *tab,
+                                                float4 *geo, float4 *app, uint4 *info,
+                                                uint32_t *tile_count) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t r0 = 0, r1 = 0, nt = 0;
+    if (gid < T.n_total) {
+        const SecDesc &S = T.s[find_section(T, gid)];
+        preprocess_gauss<Aniso>(S, gid - S.gbase, gid, S.view_base, S.tab_base, cam, views, tab,
+                                geo, app, info, r0, r1, nt);
+    }
     for_each_tile(r0, r1, nt, cam.tiles_x,
                   [&](uint32_t t, unsigned peers, int rank, uint32_t, uint32_t) {
                       if (rank == 0) atomicAdd(&tile_count[t], (uint32_t)__popc(peers));
@@ -320,13 +362,37 @@ __global__ void __launch_bounds__(256) k_preprocess_aniso(SecTable T, Camera cam
     preprocess_body<true>(T, cam, views, tab, geo, app, info, tile_count);
 }
 
+// Batched form (spheres): blocks of 256 Gaussian slots in a grid-stride loop;
+// a block lies inside one item (item ranges start at multiples of 256), and
+// the slots past an item's end get empty info.
+__global__ void __launch_bounds__(256) kb_preprocess(const BatchTable *Bp, const ViewXf *views,
+                                                     const TabRow *tab, float4 *geo, float4 *app,
+                                                     uint4 *info, uint32_t *tile_count) {
+    const BatchTable &B = *Bp;
+    for (int64_t g0 = (int64_t)blockIdx.x * 256; g0 < B.n_gauss; g0 += (int64_t)gridDim.x * 256) {
+        const BatchItem &I = B.it[item_of_gauss(B, g0)];
+        const int64_t gid = g0 + threadIdx.x, li = gid - I.gbase;
+        uint32_t r0 = 0, r1 = 0, nt = 0;
+        if (li < I.n)
+            preprocess_gauss<false>(B.sec[I.sec], li, gid, I.vbase, I.tab_base, I.cam, views, tab,
+                                    geo, app, info, r0, r1, nt);
+        else
+            info[gid] = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t *tc = tile_count + I.tbase;
+        for_each_tile(r0, r1, nt, I.cam.tiles_x,
+                      [&](uint32_t t, unsigned peers, int rank, uint32_t, uint32_t) {
+                          if (rank == 0) atomicAdd(&tc[t], (uint32_t)__popc(peers));
+                      });
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_scan_tiles: one block; exclusive prefix sum of the per-tile counts into
 // tile offsets (tile_off[n_tiles] = instance total) and insertion cursors.
 // Flags a capacity shortage instead of letting later kernels overrun.
-__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count, int n_tiles,
-                                                     uint32_t *tile_off, uint32_t *tile_cursor,
-                                                     Status *st, unsigned long long cap) {
+__device__ __forceinline__ void scan_tiles_body(const uint32_t *tile_count, int n_tiles,
+                                                uint32_t *tile_off, uint32_t *tile_cursor,
+                                                Status *st, unsigned long long cap) {
     __shared__ unsigned long long warp_sums[32];
     __shared__ unsigned long long carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -368,20 +434,29 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count,
     }
 }
 
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count, int n_tiles,
+                                                     uint32_t *tile_off, uint32_t *tile_cursor,
+                                                     Status *st, unsigned long long cap) {
+    scan_tiles_body(tile_count, n_tiles, tile_off, tile_cursor, st, cap);
+}
+
+__global__ void __launch_bounds__(1024) kb_scan_tiles(const BatchTable *Bp,
+                                                      const uint32_t *tile_count,
+                                                      uint32_t *tile_off, uint32_t *tile_cursor,
+                                                      Status *st, unsigned long long cap) {
+    scan_tiles_body(tile_count, Bp->n_tiles, tile_off, tile_cursor, st, cap);
+}
+
 // ---------------------------------------------------------------------------
 // k_emit: one thread per Gaussian; appends (zkey << 32 | gid) to the bucket of
 // every tile of its pixel box (the same tiles counted in k_preprocess), and
 // the entry's block mask (box_block_mask) at the same position of bmask_u.
-__global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Camera cam,
-                                              uint32_t *tile_cursor, unsigned long long *bucket,
-                                              uint8_t *bmask_u, const Status *st) {
-    if (st->flags) return;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint4 in = make_uint4(0, 0, 0, 0);
-    if (gid < n) in = info[gid];
+__device__ __forceinline__ void emit_gauss(const uint4 &in, int64_t gid, int tiles_x,
+                                           uint32_t *tile_cursor, unsigned long long *bucket,
+                                           uint8_t *bmask_u) {
     const unsigned long long key = ((unsigned long long)in.z << 32) | (unsigned long long)gid;
     const int lane = threadIdx.x & 31;
-    for_each_tile(in.x, in.y, in.w, cam.tiles_x,
+    for_each_tile(in.x, in.y, in.w, tiles_x,
                   [&](uint32_t t, unsigned peers, int rank, uint32_t tx, uint32_t ty) {
                       const int leader = __ffs(peers) - 1;
                       uint32_t base = 0;
@@ -390,6 +465,30 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Came
                       bucket[base + rank] = key;
                       bmask_u[base + rank] = (uint8_t)box_block_mask(in.x, in.y, tx, ty);
                   });
+}
+
+__global__ void __launch_bounds__(256) k_emit(int64_t n, const uint4 *info, Camera cam,
+                                              uint32_t *tile_cursor, unsigned long long *bucket,
+                                              uint8_t *bmask_u, const Status *st) {
+    if (st->flags) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint4 in = make_uint4(0, 0, 0, 0);
+    if (gid < n) in = info[gid];
+    emit_gauss(in, gid, cam.tiles_x, tile_cursor, bucket, bmask_u);
+}
+
+// Batched form: blocks of 256 Gaussian slots (one item each) in a
+// grid-stride loop; the item's tiles start at tile_cursor + tbase.
+__global__ void __launch_bounds__(256) kb_emit(const BatchTable *Bp, const uint4 *info,
+                                               uint32_t *tile_cursor, unsigned long long *bucket,
+                                               uint8_t *bmask_u, const Status *st) {
+    if (st->flags) return;
+    const BatchTable &B = *Bp;
+    for (int64_t g0 = (int64_t)blockIdx.x * 256; g0 < B.n_gauss; g0 += (int64_t)gridDim.x * 256) {
+        const BatchItem &I = B.it[item_of_gauss(B, g0)];
+        const int64_t gid = g0 + threadIdx.x;
+        emit_gauss(info[gid], gid, I.cam.tiles_x, tile_cursor + I.tbase, bucket, bmask_u);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -687,22 +786,29 @@ __device__ __forceinline__ void sort_tile(unsigned long long *bucket, unsigned l
 }
 
 template <int G>
+// With B != NULL (batched launches) the tiles are those of all work items
+// (B->n_tiles), each with its item's camera and tile coordinates.
 __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_tiles,
                                                 unsigned long long *bucket,
                                                 unsigned long long *alt, const uint8_t *bmask_u,
                                                 uint32_t *sorted, uint8_t *bmask,
                                                 const float4 *geo, const Camera &cam, Status *st,
-                                                int smem_n, int lo, int hi) {
+                                                int smem_n, int lo, int hi,
+                                                const BatchTable *B = nullptr) {
     extern __shared__ unsigned long long sm[];
     __shared__ uint32_t red[4][kSortWarps];
     if (st->flags) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (B) n_tiles = B->n_tiles;
     // grid-stride over tiles: a launch may have fewer blocks than tiles
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const uint32_t start = tile_off[t];
         const int n = (int)(tile_off[t + 1] - start);
         if (n <= lo || n > hi) continue;   // another launch sorts this size class
-        const SortOut out{sorted, bmask, geo, cam, start, t % cam.tiles_x, t / cam.tiles_x};
+        const BatchItem *I = B ? &B->it[item_of_tile(*B, t)] : nullptr;
+        const Camera &c = I ? I->cam : cam;
+        const int lt = I ? t - I->tbase : t;
+        const SortOut out{sorted, bmask, geo, c, start, lt % c.tiles_x, lt / c.tiles_x};
         if (n == 1) {
             if (tid == 0) {
                 sorted[start] = (uint32_t)bucket[start];
@@ -734,5 +840,21 @@ VT_SORT_KERNEL(k_sort_tiles_large, 12, 2)
 VT_SORT_KERNEL(k_sort_tiles_long, 0, 1)
 VT_SORT_KERNEL(k_sort_tiles_xl, 0, 2)
 #undef VT_SORT_KERNEL
+
+// Batched forms: the same classes over the tiles of every work item.
+#define VT_SORT_KERNEL_B(name, G, MIN_BLOCKS)                                                    \
+    __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) name(                            \
+        const BatchTable *B, const uint32_t *tile_off, unsigned long long *bucket,               \
+        unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,       \
+        const float4 *geo, Status *st, int smem_n, int lo, int hi) {                             \
+        sort_tiles_body<G>(tile_off, 0, bucket, alt, bmask_u, sorted, bmask, geo, B->it[0].cam,  \
+                           st, smem_n, lo, hi, B);                                               \
+    }
+VT_SORT_KERNEL_B(kb_sort_tiles, 3, 2)
+VT_SORT_KERNEL_B(kb_sort_tiles_mid, 7, 2)
+VT_SORT_KERNEL_B(kb_sort_tiles_large, 12, 2)
+VT_SORT_KERNEL_B(kb_sort_tiles_long, 0, 1)
+VT_SORT_KERNEL_B(kb_sort_tiles_xl, 0, 2)
+#undef VT_SORT_KERNEL_B
 
 }  // namespace vt
