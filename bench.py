@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--no-mapping", action="store_true", help="skip the FP16/FP32 mapping lines")
     p.add_argument("--mapping-iters", type=int, default=60)
     p.add_argument("--no-serving", action="store_true", help="skip the serving load points")
-    p.add_argument("--serving-requests", type=int, default=300)
+    p.add_argument("--serving-requests", type=int, default=10000,
+                   help="requests per serving load point")
     return p.parse_args()
 
 
@@ -384,71 +385,122 @@ def run_large(dev, reps: int = 5):
     return out
 
 
-def run_serving(dev, n_req: int = 300):
-    """Serving workload: 4 resident sections (0.3 M - 8.3 M Gaussians),
-    Poisson render/track requests (70% track) over 320x240 ... 1920x1080.
-    Served form: FP16 attributes, 4 slots, CUDA graphs.  Baseline: FP32
-    attributes, one request at a time, eager.  Returns a summary dict."""
+def serving_workload(dev, seed: int = 3):
+    """The serving workload: 16 resident sections of k 640x480 views each, k
+    log-uniform in [1, 33] (0.3 M - 10.1 M Gaussians), held in FP16 (served)
+    and FP32 (baseline); four request poses per section near its last view;
+    two observed frames per resolution bucket (pinned host memory) for the
+    track requests."""
     import torch
 
-    from paper_2506_02741_gb300 import api, serving
+    from paper_2506_02741_gb300 import api
     from paper_2506_02741_gb300 import synthetic as syn
+    rng = np.random.default_rng(seed)
+    K = syn.VGA
     room = syn.make_room(syn.SCENE_SEED)
-    path = syn.trajectory(40)
-    specs = ((320, 240, 4), (640, 480, 4), (1280, 720, 3), (1920, 1080, 4))
+    path = syn.trajectory(200)
+    pool_idx = list(range(0, 132, 4))                       # 33 views along the path
+    fr = syn.render_frames(room, K, [path[i] for i in pool_idx])
+    depth = torch.from_numpy(fr.depth).to(dev)
+    rgb = torch.from_numpy(fr.rgb).to(dev)
+    ks = np.rint(np.exp(rng.uniform(0.0, np.log(33.0), 16))).astype(int)
     sec16, sec32, poses = [], [], []
-    for k, (W, H, nv) in enumerate(specs):
-        K = syn.scaled_intrinsics(W, H)
-        keys = [path[4 * k + 3 * j] for j in range(nv)]
-        fr = syn.render_frames(room, K, keys)
-        d = torch.from_numpy(fr.depth).to(dev)
-        c = torch.from_numpy(fr.rgb).to(dev)
-        sec16.append(api.Section.from_rgbd(d, c, K.astuple(), np.stack(keys), precision="f16"))
-        sec32.append(api.Section.from_rgbd(d, c, K.astuple(), np.stack(keys), precision="f32"))
-        poses.append([syn.perturb_pose(keys[-1], np.random.default_rng(50 + 7 * k + j))
+    for s, k in enumerate(ks):
+        o = int(rng.integers(0, 33 - k + 1))
+        sl = slice(o, o + k)
+        keys = np.stack([path[i] for i in pool_idx[sl]])
+        sec16.append(api.Section.from_rgbd(depth[sl], rgb[sl], K.astuple(), keys,
+                                           precision="f16"))
+        sec32.append(api.Section.from_rgbd(depth[sl], rgb[sl], K.astuple(), keys,
+                                           precision="f32"))
+        poses.append([syn.perturb_pose(keys[-1], np.random.default_rng(50 + 7 * s + j))
                       for j in range(4)])
-    res = [(W, H) for W, H, _ in specs]
-    obs = []
-    for W, H in res:
-        dd, cc = syn.raycast(room, syn.scaled_intrinsics(W, H), path[9])
-        obs.append((torch.from_numpy(cc).to(dev), torch.from_numpy(dd).to(dev)))
+    res = [(320, 240), (640, 480), (1280, 720), (1920, 1080)]
+    frames = []
+    for b, (W, H) in enumerate(res):
+        fb = []
+        for i in (3, 61):
+            d, c = syn.raycast(room, syn.scaled_intrinsics(W, H), path[i])
+            fb.append(torch.from_numpy(np.concatenate([c, d[None]]).astype(np.float32)).pin_memory())
+        frames.append(fb)
+    return sec16, sec32, poses, res, frames
+
+
+def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
+    """Serving workload (16 resident sections 0.3 M - 10 M Gaussians,
+    Poisson requests 70% track / 30% render over 320x240 ... 1920x1080, every
+    track request uploading its own observation).  Served form: FP16
+    attributes, continuous batching with one persistent launch per stage,
+    two batch contexts, CUDA graphs.  Baseline: FP32 attributes, one request
+    at a time, eager.  Saturated throughput of each pattern alone (FP16,
+    graphs, batching) and of both forms; p50/p99 at 50/80/95% of the served
+    form's saturated rate, n_req requests per load point."""
+    import torch
+
+    from paper_2506_02741_gb300 import serving
+    sec16, sec32, poses, res, frames = serving_workload(dev)
     out = {"sections_gaussians": [s.n for s in sec16], "resolutions": res,
-           "mix": "70% track (fwd + Eq. 1 L1 + pose bwd, pose gradient to host), 30% render "
-                  "(colour image to host)"}
-    served = serving.Server(sec16, res, obs, n_slots=4, graphs=True)
-    base = serving.Server(sec32, res, obs, n_slots=1, graphs=False)
-    burst = serving.poisson_requests(n_req, 1e9, len(sec16), len(res), poses, seed=3)
-    served.warm(burst)
-    base.warm(burst)
-    sat = serving.latency_summary(served.run(burst), res)
-    sat_b = serving.latency_summary(base.run(burst), res)
-    out["saturated"] = {"served_req_s": n_req / sat["span_s"], "served_mpix_s": sat["mpix_s"],
-                        "baseline_req_s": n_req / sat_b["span_s"],
-                        "baseline_mpix_s": sat_b["mpix_s"], "slots": len(served.slots)}
+           "mix": "70% track (observation uploaded, fwd + Eq. 1 L1 + pose bwd, loss and pose "
+                  "gradient to host), 30% render (colour image to host)",
+           "requests_per_load_point": n_req}
+    req = lambda n, rate, seed: serving.poisson_requests(n, rate, 16, len(res), poses, seed=seed,
+                                                         frames=frames)
+    forms = {
+        "baseline_fp32_one_at_a_time": lambda: serving.SlotServer(sec32, res, 1, graphs=False,
+                                                                  keep_results=False),
+        "fp16_only": lambda: serving.SlotServer(sec16, res, 1, graphs=False, keep_results=False),
+        "graphs_only": lambda: serving.SlotServer(sec32, res, 1, graphs=True, keep_results=False),
+        "batching_only": lambda: serving.BatchServer(sec32, res, graphs=False,
+                                                     keep_results=False),
+        "served_fp16_batched_graphs": lambda: serving.BatchServer(sec16, res, graphs=True,
+                                                                  keep_results=False),
+    }
+    warm = req(400, 1e9, 7)
+    servers, sat = {}, {}
+    burst = req(n_burst, 1e9, 3)
+    for name, make in forms.items():
+        srv = make()
+        srv.warm(warm)
+        sm = serving.latency_summary(srv.run(burst, timeout=900.0), res)
+        sat[name] = {"req_s": sm["req_s"], "mpix_s": sm["mpix_s"]}
+        servers[name] = srv
+    out["saturated"] = sat
+    rate_sat = sat["served_fp16_batched_graphs"]["req_s"]
     loads = {}
-    for frac in (0.5, 0.9):
-        rate = frac * n_req / sat["span_s"]
-        reqs = serving.poisson_requests(n_req, rate, len(sec16), len(res), poses, seed=4)
-        a = serving.latency_summary(served.run(reqs), res)
-        reqs = serving.poisson_requests(n_req, rate, len(sec16), len(res), poses, seed=4)
-        b = serving.latency_summary(base.run(reqs, timeout=300.0), res)
-        loads[f"{int(frac * 100)}pct_of_served_saturation"] = {
-            "rate_req_s": rate, "served": a, "baseline_fp32_one_at_a_time": b}
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * rate_sat
+        point = {"rate_req_s": rate}
+        for name in ("served_fp16_batched_graphs", "baseline_fp32_one_at_a_time"):
+            sm = serving.latency_summary(servers[name].run(req(n_req, rate, 4), timeout=1800.0),
+                                         res)
+            point[name] = {k: sm[k] for k in ("p50_ms", "p99_ms", "mean_ms", "mpix_s", "req_s")}
+        loads[f"{int(frac * 100)}pct_of_served_saturation"] = point
     out["load_points"] = loads
-    # matched accuracy: FP16 vs FP32 colour on one request of every section
-    # The 3-sigma cut and the 1/255 skip are discontinuous: FP16 rounding of o
-    # and r moves a few Gaussians across them (jumps of ~0.01 c), so the
-    # difference is reported as a distribution.
+    bs = servers["served_fp16_batched_graphs"]
+    out["batch_contexts"] = [c.cap for c in bs.ctxs]
+    out["batch_splits_on_instance_overflow"] = bs.splits
+    # matched accuracy: FP16 vs FP32 colour of one render per section at
+    # 640x480.  The 3-sigma cut and the 1/255 skip are discontinuous: FP16
+    # rounding of o and r moves a few Gaussians across them (jumps of about
+    # 0.01 c), so the difference is reported as a distribution with the
+    # count of pixels above the 2e-3 bar.
+    from paper_2506_02741_gb300 import api
     diffs = []
+    R = api.Renderer()
+    from paper_2506_02741_gb300 import synthetic as syn
+    Kb = syn.scaled_intrinsics(640, 480).astuple()
     for k in range(len(sec16)):
-        r = serving.Request(0, "render", k, poses[k][0], 1)
-        (x,) = served.run([r])
-        (y,) = base.run([serving.Request(0, "render", k, poses[k][0], 1)])
-        diffs.append((x.result - y.result).abs().flatten().numpy())
+        pose = api.pose12(poses[k][0], dev)
+        a = R.render([sec16[k]], pose, Kb, 640, 480, checked=True)[0].clone()
+        b = R.render([sec32[k]], pose, Kb, 640, 480, checked=True)[0]
+        diffs.append((a - b).abs().flatten().cpu().numpy())
     d = np.concatenate(diffs)
     out["fp16_vs_fp32_colour_abs"] = {"max": float(d.max()), "p99": float(np.percentile(d, 99)),
                                       "p99_9": float(np.percentile(d, 99.9)),
-                                      "frac_above_2e-3": float(np.mean(d > 2e-3))}
+                                      "values_above_2e-3": int(np.sum(d > 2e-3)),
+                                      "values": int(d.size),
+                                      "reading": "2e-3 bar on pixels away from the discontinuous "
+                                                 "cuts (design notes, reading 17)"}
     return out
 
 

@@ -410,6 +410,13 @@ class Renderer:
         return int(need.value)
 
     # -- render --------------------------------------------------------------
+    def needed_instances(self, stream=None) -> int:
+        """Synchronises and returns the tile instances the last render (or
+        batch) needed (vt_ctx_sync_status)."""
+        need = C.c_int64(0)
+        self._lib.vt_ctx_sync_status(self._ctx, _stream(stream), C.byref(need))
+        return int(need.value)
+
     def render(self, sections, pose, K, W: int, H: int, rgb=None, depth=None, sil=None,
                stream=None, checked: bool = False):
         """Render (the concatenation of) ``sections`` from ``pose`` ((12,)

@@ -1,23 +1,34 @@
-"""Serving loop: many resident sections, render and track requests of uneven
-resolution and size, continuously batched on one GPU.
+"""Serving loops: many resident sections, render and track requests of uneven
+resolution and size on one GPU.
 
 * Sections (colour / opacity / radius in FP16 or FP32) stay resident on the
-  device; requests name a section, a camera pose and a resolution bucket.
-* A request is either ``render`` (forward: colour, depth, silhouette; the
-  colour image is copied to the host) or ``track`` (one tracking iteration:
-  forward, Eq. 1 L1 loss against the request's observation, pose backward;
-  the 6-vector pose gradient is copied to the host).
-* The server has ``n_slots`` slots, each with its own CUDA stream and render
-  context whose workspace is sized once for the largest request; the device
-  memory budget decides how many slots are backed.  Requests wait in arrival
-  order and are admitted into a slot as soon as one frees up; admitted
-  requests run concurrently on their slots' streams, so their kernels overlap
-  on the GPU (continuous batching at request granularity).
-* With ``graphs=True`` the work of each (slot, section, resolution, kind) is
-  captured once as a CUDA graph and replayed for every later request of that
-  kind; the inputs (pose, observation) live in the graph's fixed buffers.
-* Latency is measured from arrival to the result being visible on the host
-  (a CUDA event after the device-to-host copy, polled without blocking).
+  device; a request names a section, a camera pose and a resolution bucket.
+* ``render``: forward (colour, depth, silhouette); the colour image is copied
+  to the host.  ``track``: one tracking iteration -- forward, the Eq. 1 masked
+  L1 loss against the request's own observation (uploaded from the request's
+  pinned host frame as part of the request) and the pose backward; the loss
+  and the pose gradient are copied to the host.
+* Latency runs from arrival to the result being visible on the host (a CUDA
+  event after the device-to-host copy, polled without blocking).
+
+BatchServer is the served form: continuous batching with one persistent
+launch per stage (vt_batch_*).  It keeps ``n_contexts`` batch contexts, each
+with its own stream, workspace and capacity; whenever a context is idle it
+takes the queued requests in arrival order that fit its remaining capacity
+(Gaussians, pixels, tiles, views, estimated tile instances, 64 items) into
+one batch, uploads their poses and observations, launches the batch
+(replaying a CUDA graph captured once per context) and copies the results
+back.  Requests that arrive while batches run wait in the queue and are
+admitted as soon as a context frees up; the contexts' batches overlap on the
+device.  The capacities come from the free device memory at start-up
+(admission by free HBM): a request is deferred until a context has room and
+refused only if it can never fit one.  A batch that still exceeds the
+reserved tile instances on the device is run again in halves.
+
+SlotServer runs requests on ``n_slots`` independent render contexts (one
+request per slot and stream), optionally replaying a CUDA graph per
+(slot, section, bucket, kind); with one slot and no graphs it is the plain
+one-request-at-a-time form.
 """
 
 from __future__ import annotations
@@ -29,7 +40,10 @@ import time
 import numpy as np
 import torch
 
+from . import _lib as L
 from . import api
+
+TRACK_WEIGHTS = dict(w_rgb=0.5, w_depth=0.025, sil_min=0.99, rgb_needs_depth=True)
 
 
 @dataclasses.dataclass
@@ -40,8 +54,271 @@ class Request:
     pose: np.ndarray          # (3, 4) camera-to-world
     bucket: int               # index into the server's resolutions
     arrival: float = 0.0      # seconds from the start of the run
+    obs: torch.Tensor | None = None   # track: pinned host (4, H, W) float32 (rgb, depth)
     done: float = -1.0
     result: torch.Tensor | None = None
+
+
+def _pad(x: int) -> int:
+    return (x + 255) // 256 * 256
+
+
+# ---------------------------------------------------------------------------
+# Batched serving
+
+
+class _BatchCtx:
+    """One batch context: a BatchRunner with fixed pools for the items'
+    images, observations, poses and results, and the pinned host buffers the
+    results are copied to."""
+
+    def __init__(self, server: "BatchServer", cap: dict):
+        dev = server.device
+        self.stream = torch.cuda.Stream(device=dev)
+        self.cap = cap
+        with torch.cuda.stream(self.stream):
+            self.runner = api.BatchRunner(cap["gaussians"], cap["pixels"], cap["tiles"],
+                                          cap["instances"], cap["views"], cap["table_rows"],
+                                          list_cap=server.list_cap, stream=self.stream)
+        P = cap["pixels"]
+        n = self.max_items = 64      # VT_MAX_BATCH_ITEMS
+        self.image = torch.empty(5 * P, device=dev)
+        self.obs = torch.zeros(4 * P, device=dev)
+        self.poses = torch.zeros(n, 12, dtype=torch.float64, device=dev)
+        self.results = torch.zeros(n, 19, dtype=torch.float64, device=dev)
+        self.poses_host = torch.zeros(n, 12, dtype=torch.float64).pin_memory()
+        self.results_host = torch.zeros(n, 19, dtype=torch.float64).pin_memory()
+        self.rgb_host = torch.empty(3 * P, dtype=torch.float32).pin_memory()
+        self.graph = None
+        self.reqs: list[Request] = []
+        self.slices: list[tuple] = []
+        self.event = None
+
+    def busy(self) -> bool:
+        return bool(self.reqs)
+
+
+class BatchServer:
+    def __init__(self, sections, resolutions, n_contexts: int = 2, graphs: bool = True,
+                 memory_budget: int | None = None, list_cap: int = 64, keep_results: bool = True,
+                 device="cuda"):
+        """sections: list of api.Section (resident, spheres); resolutions:
+        list of (W, H) buckets.  The contexts share memory_budget (default:
+        70% of the free device memory) in equal parts."""
+        from . import synthetic as syn
+        self.device = torch.device(device)
+        self.sections = sections
+        self.resolutions = [tuple(r) for r in resolutions]
+        self.intrinsics = [syn.scaled_intrinsics(W, H).astuple() for W, H in self.resolutions]
+        self.graphs = graphs
+        self.list_cap = int(list_cap)
+        self.keep_results = keep_results
+        free, _ = torch.cuda.mem_get_info(self.device)
+        self.memory_budget = int(memory_budget if memory_budget is not None else 0.7 * free)
+        self.n_contexts = int(n_contexts)
+        self.ctxs: list[_BatchCtx] = []
+        # tile instances per (section, bucket): measured at warm-up, raised
+        # when a batch overflows
+        self.inst_est: dict = {}
+        self.splits = 0
+
+    # -- capacity -------------------------------------------------------------
+    def _need(self, r: Request) -> dict:
+        s = self.sections[r.section]
+        W, H = self.resolutions[r.bucket]
+        return dict(gaussians=_pad(s.n), pixels=_pad(W * H),
+                    tiles=((W + 15) // 16) * ((H + 15) // 16), views=s.n_views,
+                    table_rows=s.n_views * (s.depth.shape[-1] + s.depth.shape[-2]),
+                    instances=int(self.inst_est.get((r.section, r.bucket), 6 * s.n + 65536)))
+
+    def _capacity(self, requests) -> dict:
+        """Per-context capacity: the largest request at least, the rest of the
+        context's share of the memory budget spread over the totals in the
+        proportions of the request mix."""
+        needs = [self._need(r) for r in requests]
+        big = {k: max(n[k] for n in needs) for k in needs[0]}
+        mean = {k: float(np.mean([n[k] for n in needs])) for k in needs[0]}
+        share = self.memory_budget // max(1, self.n_contexts)
+        per_item = api.BatchRunner.workspace_bytes_for(
+            mean["gaussians"], mean["pixels"], mean["tiles"], mean["instances"], mean["views"],
+            mean["table_rows"], self.list_cap) + 36 * mean["pixels"]
+        items = int(max(1, min(64, share // max(per_item, 1))))
+        cap = {k: int(max(big[k], items * mean[k])) for k in big}
+        while True:
+            need = api.BatchRunner.workspace_bytes_for(
+                cap["gaussians"], cap["pixels"], cap["tiles"], cap["instances"], cap["views"],
+                cap["table_rows"], self.list_cap) + 36 * cap["pixels"]
+            if need <= share or all(cap[k] <= big[k] for k in cap):
+                break
+            cap = {k: int(max(big[k], 0.85 * cap[k])) for k in cap}
+        cap["tiles"] = max(cap["tiles"], 1)
+        return cap
+
+    def _measure_instances(self, requests):
+        """Tile instances of one render of every (section, bucket) the
+        requests use, at one of their poses, with a 1.5x margin."""
+        R = api.Renderer()
+        seen = {}
+        for r in requests:
+            key = (r.section, r.bucket)
+            if key in seen:
+                continue
+            seen[key] = r
+        for (s, b), r in seen.items():
+            W, H = self.resolutions[b]
+            R.render([self.sections[s]], api.pose12(r.pose, self.device), self.intrinsics[b], W, H,
+                     checked=True)
+            self.inst_est[(s, b)] = int(1.5 * R.needed_instances()) + 4096
+        del R
+        torch.cuda.synchronize()
+
+    def warm(self, requests):
+        """Measure the instance counts, size and create the contexts, run one
+        batch on each and capture its launch graph."""
+        self._measure_instances(requests)
+        cap = self._capacity(requests)
+        self.ctxs = [_BatchCtx(self, cap) for _ in range(self.n_contexts)]
+        for ctx in self.ctxs:
+            r = requests[0]
+            self._launch(ctx, [dataclasses.replace(r, obs=self._dummy_obs(r))], warmup=True)
+            ctx.event.synchronize()
+            ctx.reqs = []
+        torch.cuda.synchronize()
+
+    def _dummy_obs(self, r):
+        if r.kind != "track":
+            return None
+        W, H = self.resolutions[r.bucket]
+        return r.obs if r.obs is not None else torch.zeros(4, H, W).pin_memory()
+
+    # -- batches -------------------------------------------------------------
+    def _fits(self, ctx, used, need) -> bool:
+        return len(used["n"]) < ctx.max_items and all(
+            used[k] + need[k] <= ctx.cap[k] for k in ctx.cap)
+
+    def _items(self, ctx, reqs):
+        items, slices = [], []
+        off = 0
+        for i, r in enumerate(reqs):
+            W, H = self.resolutions[r.bucket]
+            P = W * H
+            img = ctx.image[5 * off:5 * off + 5 * P].view(5, H, W)
+            it = api.BatchItem(r.section, r.kind == "track", W, H, self.intrinsics[r.bucket],
+                               ctx.poses[i], img)
+            if r.kind == "track":
+                it.obs = ctx.obs[4 * off:4 * off + 4 * P].view(4, H, W)
+                it.result = ctx.results[i]
+            items.append(it)
+            slices.append((off, P, W, H))
+            off += _pad(P)
+        return items, slices
+
+    def _launch(self, ctx, reqs, warmup=False):
+        items, slices = self._items(ctx, reqs)
+        with torch.cuda.stream(ctx.stream):
+            for i, r in enumerate(reqs):
+                ctx.poses_host[i] = torch.from_numpy(
+                    np.asarray(api.pose12(r.pose, "cpu").numpy(), np.float64))
+            ctx.poses.copy_(ctx.poses_host, non_blocking=True)
+            for it, r in zip(items, reqs):
+                if r.kind == "track":     # the request's own observation
+                    it.obs.copy_(r.obs, non_blocking=True)
+            ctx.runner.set(self.sections, items, **TRACK_WEIGHTS)
+            if self.graphs and ctx.graph is None and warmup:
+                ctx.runner.launch(stream=ctx.stream)      # eager once, then capture
+                ctx.stream.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=ctx.stream):
+                    ctx.runner.launch(stream=ctx.stream)
+                ctx.graph = g
+                ctx.runner.set(self.sections, items, **TRACK_WEIGHTS)
+            if ctx.graph is not None:
+                ctx.graph.replay()
+            else:
+                ctx.runner.launch(stream=ctx.stream)
+            n = len(reqs)
+            if any(r.kind == "track" for r in reqs):
+                ctx.results_host[:n].copy_(ctx.results[:n], non_blocking=True)
+            for (off, P, W, H), r in zip(slices, reqs):
+                if r.kind == "render":
+                    ctx.rgb_host[3 * off:3 * off + 3 * P].copy_(ctx.image[5 * off:5 * off + 3 * P],
+                                                                non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(ctx.stream)
+        ctx.reqs, ctx.slices, ctx.event = list(reqs), slices, ev
+
+    def _finish(self, ctx, now, finished, queue):
+        try:
+            ctx.runner.status(ctx.stream)
+        except L.VTError as e:
+            if e.status != L.VT_ERR_CAPACITY:
+                raise
+            # more tile instances than estimated: raise the estimates of the
+            # batch's (section, bucket) pairs and run it again in halves
+            for r in ctx.reqs:
+                k = (r.section, r.bucket)
+                self.inst_est[k] = 2 * self.inst_est.get(k, 0) + 65536
+            self.splits += 1
+            for r in reversed(ctx.reqs):
+                queue.appendleft(r)
+            ctx.reqs = []
+            return
+        for i, ((off, P, W, H), r) in enumerate(zip(ctx.slices, ctx.reqs)):
+            r.done = now
+            if self.keep_results:
+                if r.kind == "render":
+                    r.result = ctx.rgb_host[3 * off:3 * off + 3 * P].view(3, H, W).clone()
+                else:
+                    r.result = ctx.results_host[i].clone()
+            finished.append(r)
+        ctx.reqs = []
+
+    def run(self, requests, timeout: float = 600.0):
+        """Serve ``requests`` (arrival times in seconds from now).  Returns
+        them with ``done`` (and ``result``) set."""
+        for r in requests:
+            n = self._need(r)
+            if any(n[k] > self.ctxs[0].cap[k] for k in ("gaussians", "pixels", "tiles", "views",
+                                                         "table_rows")):
+                raise ValueError(f"request {r.rid} can never fit a batch context")
+        queue = collections.deque()
+        pending = list(sorted(requests, key=lambda r: r.arrival))
+        nxt, finished = 0, []
+        t0 = time.perf_counter()
+        while len(finished) < len(requests):
+            now = time.perf_counter() - t0
+            if now > timeout:
+                raise TimeoutError("serving run exceeded its time limit")
+            while nxt < len(pending) and pending[nxt].arrival <= now:
+                queue.append(pending[nxt])
+                nxt += 1
+            for ctx in self.ctxs:          # completions (non-blocking)
+                if ctx.busy() and ctx.event.query():
+                    self._finish(ctx, time.perf_counter() - t0, finished, queue)
+            for ctx in self.ctxs:          # admissions in arrival order
+                if ctx.busy() or not queue:
+                    continue
+                used = dict(gaussians=0, pixels=0, tiles=0, views=0, table_rows=0, instances=0,
+                            n=[])
+                take = []
+                while queue:
+                    need = self._need(queue[0])
+                    if not self._fits(ctx, used, need):
+                        break
+                    for k in need:
+                        used[k] += need[k]
+                    used["n"].append(1)
+                    take.append(queue.popleft())
+                if not take:               # the head does not fit: a lone item always does
+                    take.append(queue.popleft())
+                self._launch(ctx, take)
+            if all(c.busy() for c in self.ctxs) or (not queue and nxt < len(pending)):
+                time.sleep(20e-6)
+        return finished
+
+
+# ---------------------------------------------------------------------------
+# One request per slot
 
 
 class _Work:
@@ -62,8 +339,9 @@ class _Work:
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
         self.g_rgb = torch.zeros(3, H, W, device=dev)
         self.g_depth = torch.zeros(H, W, device=dev)
-        self.obs_rgb, self.obs_depth = server.observations[bucket]
-        self.host = torch.empty((3, H, W) if kind == "render" else (6,),
+        self.obs = torch.zeros(4, H, W, device=dev)
+        self.out = torch.zeros(7, dtype=torch.float64, device=dev)   # loss, twist
+        self.host = torch.empty((3, H, W) if kind == "render" else (7,),
                                 dtype=torch.float32 if kind == "render" else torch.float64
                                 ).pin_memory()
         self.graph = None
@@ -72,11 +350,13 @@ class _Work:
         R = self.slot.renderer
         R.render([self.sec], self.pose, self.K, self.W, self.H, self.rgb, self.depth, self.sil)
         if self.kind == "track":   # Eq. 1 masked L1 (alpha 0.5, beta 0.025), pose gradient
-            R.masked_l1(self.rgb, self.depth, self.sil, self.obs_rgb, self.obs_depth, 0.5, 0.025,
+            R.masked_l1(self.rgb, self.depth, self.sil, self.obs[:3], self.obs[3], 0.5, 0.025,
                         sil_min=0.99, rgb_needs_depth=True, d_rgb=self.g_rgb,
                         d_depth=self.g_depth, loss=self.loss)
             self.d_twist.zero_()
             R.backward(self.g_rgb, self.g_depth, None, pose_grad=True, d_twist=self.d_twist)
+            self.out[:1].copy_(self.loss)
+            self.out[1:].copy_(self.d_twist)
 
 
 class _Slot:
@@ -91,25 +371,23 @@ class _Slot:
         self.work = None
 
 
-class Server:
-    def __init__(self, sections, resolutions, observations, n_slots: int = 4,
-                 graphs: bool = True, memory_budget: int | None = None, device="cuda"):
+class SlotServer:
+    def __init__(self, sections, resolutions, n_slots: int = 4, graphs: bool = True,
+                 memory_budget: int | None = None, keep_results: bool = True, device="cuda"):
         """sections: list of api.Section (resident); resolutions: list of
-        (W, H); observations: per bucket (rgb (3,H,W), depth (H,W)) device
-        tensors used as the tracking target."""
+        (W, H) buckets."""
         from . import synthetic as syn
         self.device = torch.device(device)
         self.sections = sections
         self.resolutions = [tuple(r) for r in resolutions]
         self.intrinsics = [syn.scaled_intrinsics(W, H).astuple() for W, H in self.resolutions]
-        self.observations = observations
         self.graphs = graphs
+        self.keep_results = keep_results
         self.slots = [_Slot(self, i) for i in range(n_slots)]
         free, total = torch.cuda.mem_get_info(self.device)
         self.memory_budget = memory_budget if memory_budget is not None else int(free * 0.8)
-        self.max_instances_per_gaussian = 3.0
+        self.max_instances_per_gaussian = 6.0
 
-    # -- memory ---------------------------------------------------------------
     # Every slot's workspace is sized once, before any graph is captured, for
     # the largest request it may serve (captured graphs hold the workspace's
     # addresses, so it must never move afterwards).  The memory budget decides
@@ -136,22 +414,12 @@ class Server:
                 work.run()
             slot.reserved = (n_max, W * H, i_max)
         torch.cuda.synchronize()
-        self.per_slot_bytes = per_slot
 
-    def _fits(self, slot, req):
-        n, inst = self._need(req)
-        W, H = self.resolutions[req.bucket]
-        g, p, i = slot.reserved
-        return n <= g and W * H <= p and inst <= i
-
-    # -- execution --------------------------------------------------------------
     def _launch(self, slot, req):
         key = (req.section, req.bucket, req.kind)
         work = slot.works.get(key)
         with torch.cuda.stream(slot.stream):
             if work is None:
-                if not self._fits(slot, req):
-                    raise RuntimeError("request larger than the slot workspaces sized in warm()")
                 work = _Work(slot, self, req.section, req.bucket, req.kind)
                 slot.works[key] = work
                 if self.graphs:
@@ -162,12 +430,13 @@ class Server:
                         work.run()
                     work.graph = g
             work.pose.copy_(api.pose12(req.pose, self.device), non_blocking=True)
+            if req.kind == "track":           # the request's own observation
+                work.obs.copy_(req.obs, non_blocking=True)
             if work.graph is not None:
                 work.graph.replay()
             else:
                 work.run()
-            src = work.rgb if req.kind == "render" else work.d_twist
-            work.host.copy_(src, non_blocking=True)
+            work.host.copy_(work.rgb if req.kind == "render" else work.out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(slot.stream)
         slot.request, slot.event, slot.work = req, ev, work
@@ -176,16 +445,12 @@ class Server:
         """Size the slot workspaces and capture the graphs for every
         (slot, section, bucket, kind) the requests use."""
         self._size_slots(requests)
-        keys = sorted({(r.section, r.bucket, r.kind, tuple(r.pose.reshape(-1))) for r in requests},
-                      key=lambda k: k[:3])
-        seen = set()
-        for s, b, k, p in keys:
-            if (s, b, k) in seen:
-                continue
-            seen.add((s, b, k))
-            req = Request(-1, k, s, np.asarray(p).reshape(3, 4), b)
+        seen = {}
+        for r in requests:
+            seen.setdefault((r.section, r.bucket, r.kind), r)
+        for r in seen.values():
             for slot in self.slots:
-                self._launch(slot, req)
+                self._launch(slot, r)
                 slot.event.synchronize()
                 slot.request = None
         torch.cuda.synchronize()
@@ -210,7 +475,8 @@ class Server:
                 if slot.request is not None and slot.event.query():
                     r = slot.request
                     r.done = time.perf_counter() - t0
-                    r.result = slot.work.host.clone()
+                    if self.keep_results:
+                        r.result = slot.work.host.clone()
                     finished.append(r)
                     slot.request = None
                     busy -= 1
@@ -231,12 +497,15 @@ def latency_summary(done, resolutions):
     pix = sum(resolutions[r.bucket][0] * resolutions[r.bucket][1] for r in done)
     return {"requests": len(done), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "mpix_s": pix / span / 1e6, "span_s": span}
+            "mpix_s": pix / span / 1e6, "req_s": len(done) / span, "span_s": span}
 
 
-def poisson_requests(n, rate_per_s, n_sections, n_buckets, poses, seed=3, track_frac=0.7):
+def poisson_requests(n, rate_per_s, n_sections, n_buckets, poses, seed=3, track_frac=0.7,
+                     frames=None):
     """Seeded request stream: Poisson arrivals, 70% track / 30% render,
-    uniform section and resolution; poses drawn from ``poses``."""
+    uniform section and resolution; poses drawn from ``poses`` (per section);
+    frames[b] (a list of pinned host (4, H, W) observations of bucket b), if
+    given, supply the track requests' observations."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_per_s, n))
     out = []
@@ -244,6 +513,9 @@ def poisson_requests(n, rate_per_s, n_sections, n_buckets, poses, seed=3, track_
         kind = "track" if rng.random() < track_frac else "render"
         s = int(rng.integers(n_sections))
         b = int(rng.integers(n_buckets))
-        out.append(Request(i, kind, s, poses[s][int(rng.integers(len(poses[s])))], b,
-                           arrival=float(t[i])))
+        pose = poses[s][int(rng.integers(len(poses[s])))]
+        obs = None
+        if kind == "track" and frames is not None:
+            obs = frames[b][int(rng.integers(len(frames[b])))]
+        out.append(Request(i, kind, s, pose, b, arrival=float(t[i]), obs=obs))
     return out

@@ -60,12 +60,20 @@ def test_counts_and_selection(dev):
 
 
 def test_pretrack_picks_the_smallest_loss(dev):
+    """The candidates tracked together as one batched workload give the
+    poses and losses of tracking them one after the other (the same pose
+    gradients up to FP32 rounding, the same Adam steps); the section with
+    the smallest loss is picked."""
     K = syn.TINY
     secs, fr, path, head = _sections(dev, K)
     start = syn.perturb_pose(path[head], np.random.default_rng(4))
-    best, res = overlap.pretrack(secs, [1, 2, 3], torch.from_numpy(fr.rgb[head]).to(dev),
-                                 torch.from_numpy(fr.depth[head]).to(dev), start, K.astuple(),
-                                 K.W, K.H, iters=10)
-    assert set(res) == {1, 2, 3}
-    assert best == min(res, key=lambda s: res[s][0])
+    args = (secs, [1, 2, 3], torch.from_numpy(fr.rgb[head]).to(dev),
+            torch.from_numpy(fr.depth[head]).to(dev), start, K.astuple(), K.W, K.H)
+    best, res = overlap.pretrack(*args, iters=10, batched=True)
+    best1, res1 = overlap.pretrack(*args, iters=10, batched=False)
+    assert set(res) == set(res1) == {1, 2, 3}
+    assert best == min(res, key=lambda s: res[s][0]) == best1
+    for s in res:
+        np.testing.assert_allclose(res[s][1], res1[s][1], rtol=0, atol=1e-7)
+        assert res[s][0] == pytest.approx(res1[s][0], rel=1e-6)
     assert all(np.isfinite(v[0]) for v in res.values())
