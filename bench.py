@@ -254,7 +254,29 @@ def run_head_frame(dev, iters: int = 50):
     ba_ms = timed(lambda: R.backward(g_rgb, None, None, pose_grad=True,
                                      view_grads=[(vt, vm)]), 20)
     pose_ms = timed(lambda: R.backward(g_rgb, None, None, pose_grad=True), 20)
+    # pre-tracking against three candidate sections (keyframes 0-2, 3-5,
+    # 5-7 of the section), 20 iterations each: batched (one launch per
+    # stage for the three) and one after the other
+    from paper_2506_02741_gb300 import overlap
+    P = K.W * K.H
+    cands = [api.Section(sec.poses[a:b].contiguous(), sec.depth[a:b].contiguous(), sec.K,
+                         (sec.src[a * P:b * P] - a * P).contiguous(),
+                         sec.colour[a * P:b * P].contiguous(), sec.opacity[a * P:b * P].contiguous(),
+                         sec.radius[a * P:b * P].contiguous())
+             for a, b in ((0, 3), (3, 6), (5, 8))]
+    pre = {}
+    for batched in (True, False, True):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, res = overlap.pretrack(cands, [0, 1, 2], rgb, d, starts[0], Kt, K.W, K.H, iters=20,
+                                     batched=batched)
+        torch.cuda.synchronize()
+        pre["batched_ms" if batched else "one_after_another_ms"] = (time.perf_counter() - t0) * 1e3
+    pre.update(candidates=3, iterations=20, picked=int(best),
+               losses=[float(res[k][0]) for k in sorted(res)],
+               timing="wall clock of the call (host included), second batched call")
     return {"workload": "head_frame_640x480_8kf_fp32", "candidate_views": sec.n_views,
+            "pretrack": pre,
             "overlap_counts_ms": counts_ms, "visibility_mask_ms": vis_ms,
             "visible_fraction": float(vis.float().mean()),
             "tracking_with_visibility_ms_per_iter": track_ms,
@@ -335,53 +357,110 @@ def run_ellipsoids(dev, iters: int = 50):
             "per_kernel_ms": {k: round(v[1] / max(v[0], 1), 5) for k, v in pk.items() if v[0]}}
 
 
-def run_large(dev, reps: int = 5):
-    """The multi-section render at its large end: seven adjacent sections of
-    14 keyframes (every other frame of the path) at 640x480, 30,105,600
-    Gaussians rendered together from a pose between keyframes (about 1,500
-    Gaussians over each pixel), with the pose backward.  CUDA-event times
-    per call, with the default per-pixel list capacity (256: pixels that add
-    more send their tiles to the replay backward) and with 1024."""
+def large_scene_sections(dev, n_sec: int = 6, per: int = 16, every: int = 5):
+    """Sections of the 2000-frame multi-room path (five rooms side by side,
+    keyframes every 5th frame): n_sec adjacent sections of ``per`` keyframes
+    at 640x480 starting at frame 200, and a target pose inside the middle
+    section (between keyframes)."""
     import torch
 
     from paper_2506_02741_gb300 import api
     from paper_2506_02741_gb300 import synthetic as syn
     K = syn.VGA
-    n_sec, per = 7, 14
-    path = syn.trajectory(n_sec * per * 2 + 5)
-    room = syn.make_room(syn.SCENE_SEED)
+    rooms = syn.make_rooms(5)
+    path = syn.multi_room_trajectory(2000, 5)
+    first = 200
+    idx = [first + every * j for j in range(n_sec * per)]
+    fr = syn.render_multi(rooms, K, [path[i] for i in idx])
     secs = []
     for s in range(n_sec):
-        keys = [path[2 * (s * per + j)] for j in range(per)]
-        fr = syn.render_frames(room, K, keys)
-        secs.append(api.Section.from_rgbd(torch.from_numpy(fr.depth).to(dev),
-                                          torch.from_numpy(fr.rgb).to(dev), K.astuple(),
-                                          np.stack(keys)))
-    pose = api.pose12(path[n_sec * per + 1], dev)
-    g = torch.full((3, K.H, K.W), 1e-6, device=dev)
+        sl = slice(s * per, (s + 1) * per)
+        secs.append(api.Section.from_rgbd(torch.from_numpy(fr.depth[sl]).to(dev),
+                                          torch.from_numpy(fr.rgb[sl]).to(dev), K.astuple(),
+                                          np.stack([path[i] for i in idx[sl]])))
+    target = path[first + every * (n_sec * per // 2) + 2]
+    return K, secs, target, path, idx
+
+
+def run_large(dev, reps: int = 5):
+    """The large-scene workload on the 2000-frame multi-room path: (a) one
+    section of 4, 8 and 16 keyframes (1.2 M - 4.9 M Gaussians), render and
+    pose backward of a frame two after its last keyframe; (b) six adjacent
+    sections of 16 keyframes rendered together (29.5 M Gaussians, the
+    multi-section render) with the pose backward: under a 150 GB workspace
+    budget (per-pixel lists kept, capacity 1024), under a forced small budget
+    (no lists: the backward replays the tile lists), and through
+    torch.autograd with recompute (nothing kept between forward and
+    backward: the backward re-runs projection, binning and sort).  CUDA-event
+    times per call."""
+    import torch
+
+    from paper_2506_02741_gb300 import api
+    from paper_2506_02741_gb300.autograd import splat
+    K, secs, target, path, idx = large_scene_sections(dev)
+    Kt = K.astuple()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    out = {"workload": "large_multisection_640x480_7x14kf_fp32",
-           "gaussians": int(sum(s.n for s in secs)), "sections": n_sec}
-    for cap in (256, 1024):
-        R = api.Renderer()
-        R.set_list_capacity(cap)
-        rgb, depth, sil = R.render(secs, pose, K.astuple(), K.W, K.H, checked=True)
-        out["instances"] = int(R.status())
+    g = torch.full((3, K.H, K.W), 1e-6, device=dev)
+
+    def timed(R, sections, pose):
+        rgb, depth, sil = R.render(sections, pose, Kt, K.W, K.H, checked=True)
         R.backward(g, None, None, pose_grad=True)
         torch.cuda.synchronize()
         fwd = bwd = 0.0
         for _ in range(reps):
             ev[0].record()
-            R.render(secs, pose, K.astuple(), K.W, K.H, rgb, depth, sil)
+            R.render(sections, pose, Kt, K.W, K.H, rgb, depth, sil)
             ev[1].record()
             R.backward(g, None, None, pose_grad=True)
             ev[2].record()
             torch.cuda.synchronize()
             fwd += ev[0].elapsed_time(ev[1])
             bwd += ev[1].elapsed_time(ev[2])
-        out[f"list_cap_{cap}"] = {"render_ms": fwd / reps, "pose_backward_ms": bwd / reps,
-                                  "mpix_s": K.W * K.H / ((fwd + bwd) / reps) / 1e3}
+        return {"render_ms": fwd / reps, "pose_backward_ms": bwd / reps,
+                "mpix_s": K.W * K.H / ((fwd + bwd) / reps) / 1e3,
+                "instances": R.needed_instances(), "lists": R.used_lists,
+                "workspace_gb": R.workspace_bytes / 1e9}
+
+    out = {"workload": "multiroom_2000f_640x480", "rooms": 5, "frames": 2000,
+           "keyframe_every": 5, "sections": {}}
+    base = secs[0]
+    for kf in (4, 8, 16):
+        sub = api.Section(base.poses[:kf].contiguous(), base.depth[:kf].contiguous(), base.K,
+                          base.src[:kf * K.W * K.H].contiguous(),
+                          base.colour[:kf * K.W * K.H].contiguous(),
+                          base.opacity[:kf * K.W * K.H].contiguous(),
+                          base.radius[:kf * K.W * K.H].contiguous())
+        R = api.Renderer()
+        pose = api.pose12(path[idx[kf - 1] + 2], dev)
+        out["sections"][f"{kf}_keyframes"] = dict(timed(R, [sub], pose), gaussians=sub.n)
         del R
+    pose = api.pose12(target, dev)
+    big = {"gaussians": int(sum(s.n for s in secs)), "sections": len(secs)}
+    R = api.Renderer()
+    R.set_list_capacity(1024)
+    R.set_budget(150 << 30)
+    big["budget_150GB"] = timed(R, secs, pose)
+    del R
+    R = api.Renderer()
+    R.set_budget(1)
+    big["budget_forced_small"] = timed(R, secs, pose)
+    del R
+    pz = pose.clone().requires_grad_(True)
+    times = []
+    for r in range(reps + 1):
+        ev[0].record()
+        rgb, _, _ = splat(secs, pz, Kt, K.W, K.H, recompute=True)
+        ev[1].record()
+        (rgb * g).sum().backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+        if r:
+            times.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
+    f, b = np.mean(times, axis=0)
+    big["autograd_recompute"] = {"forward_ms": float(f), "backward_ms": float(b),
+                                 "note": "backward re-runs projection, binning, sort and "
+                                         "forward, then the tile replay"}
+    out["multi_section"] = big
     return out
 
 

@@ -450,6 +450,22 @@ vt_status vt_attr_adam(vt_ctx *ctx, int64_t n, float *theta, float *m, float *v,
                        void *colour, void *opacity, void *radius, vt_adam_params p,
                        vt_stream stream);
 
+/* Optimiser state of the mapping step (vt_attr_adam) from a section's
+ * storage: theta (device float32, 5 planes of n) = (c0, c1, c2, logit o,
+ * log r) with o clamped to [1e-4, 1 - 1e-4] first (o = 1 has no finite
+ * logit); m and v (5 planes) zeroed; step (device, 3 doubles) zeroed.  With
+ * scale != NULL (ellipsoid section) the state of vt_shape_adam instead:
+ * theta = (log s0, log s1, log s2, q0, q1, q2, q3), m and v 7 planes of n.
+ * colour, opacity, radius, scale, rot: device arrays of the section in
+ * precision prec (radius unused with scale; colour and opacity unused with
+ * scale).  This is the parametrisation of the design's optimiser reading
+ * (the paper gives the rates, not the parametrisation).  ctx may be NULL;
+ * when given it only records the launch. */
+vt_status vt_adam_init(vt_ctx *ctx, int64_t n, vt_precision prec, const void *colour,
+                       const void *opacity, const void *radius, const void *scale,
+                       const void *rot, float *theta, float *m, float *v, double *step,
+                       vt_stream stream);
+
 /* Ellipsoid shape step of the mapping optimiser (the anisotropic variant of
  * the attribute ablation, Sec. 4): Adam on theta = (log s0, log s1, log s2,
  * q0, q1, q2, q3) with rate lr_scale for the log scales and lr_rot for the

@@ -132,6 +132,8 @@ def _declare(L):
         "vt_batch_set": (C.c_int, [_P, C.POINTER(SectionC), C.c_int32, C.POINTER(BatchItemC),
                                    C.c_int32, L1WeightsC]),
         "vt_batch_launch": (C.c_int, [_P, _P]),
+        "vt_adam_init": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                   _P]),
         "vt_last_error": (C.c_char_p, []),
         "vt_version": (C.c_char_p, []),
     }
@@ -151,7 +153,8 @@ EXPORTS = ["vt_ctx_create", "vt_ctx_destroy", "vt_ctx_reserve", "vt_workspace_by
            "vt_backproject_noalloc", "vt_visibility", "vt_masked_l1", "vt_pose_adam",
            "vt_attr_adam", "vt_section_complement", "vt_ssim",
            "vt_visibility_counts", "vt_shape_adam", "vt_ctx_debug_pixel_lists",
-           "vt_batch_workspace_bytes", "vt_batch_reserve", "vt_batch_set", "vt_batch_launch"]
+           "vt_batch_workspace_bytes", "vt_batch_reserve", "vt_batch_set", "vt_batch_launch",
+           "vt_adam_init"]
 
 
 def lib_path() -> str:

@@ -310,6 +310,27 @@ def attr_adam(section, theta: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
                                  _ptr(section.radius), p, _stream(stream)), "vt_attr_adam")
 
 
+def adam_init(section, shape: bool = False, renderer=None, stream=None):
+    """Optimiser state of a section from its storage (vt_adam_init): returns
+    (theta, m, v, step) for vt_attr_adam (theta planes c0, c1, c2, logit o,
+    log r) or, with shape, for vt_shape_adam (log s0..2, q0..3)."""
+    n = section.n
+    dev = section.colour.device
+    planes = 7 if shape else 5
+    theta = torch.empty(planes, n, device=dev)
+    m = torch.empty(planes, n, device=dev)
+    v = torch.empty(planes, n, device=dev)
+    step = torch.empty(3, dtype=torch.float64, device=dev)
+    ctx = renderer._ctx if renderer is not None else None
+    sc = _ptr(section.scale) if shape else None
+    rt = _ptr(section.rot) if shape else None
+    L.check(L.lib().vt_adam_init(ctx, n, section.prec, None if shape else _ptr(section.colour),
+                                 None if shape else _ptr(section.opacity),
+                                 None if shape else _ptr(section.radius), sc, rt, _ptr(theta),
+                                 _ptr(m), _ptr(v), _ptr(step), _stream(stream)), "vt_adam_init")
+    return theta, m, v, step
+
+
 def shape_adam(section, theta: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
                step: torch.Tensor, d_scale: torch.Tensor, d_rot: torch.Tensor,
                lr_scale: float = 0.005, lr_rot: float = 0.001, beta1: float = 0.9,

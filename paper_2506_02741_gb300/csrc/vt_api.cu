@@ -66,7 +66,7 @@ enum KernelId {
     K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_SHAPE_ADAM,
     K_SORT_XL, K_VIEW_FIN, K_BWD_LIST_POSE, K_BWD_LIST_VIEWS, KB_SETUP, KB_PREPROCESS, KB_SCAN,
     KB_EMIT, KB_SORT, KB_SORT_M, KB_SORT_L, KB_SORT_LONG, KB_SORT_XL, KB_FWD, KB_L1, KB_BWD_LIST,
-    KB_BWD, KB_FINALIZE, K_NUM
+    KB_BWD, KB_FINALIZE, K_ADAM_INIT, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -85,7 +85,7 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "kb_sort_tiles", "kb_sort_tiles_mid", "kb_sort_tiles_large",
                                    "kb_sort_tiles_long", "kb_sort_tiles_xl", "kb_composite_fwd",
                                    "kb_masked_l1", "kb_composite_bwd_list_pose",
-                                   "kb_composite_bwd_pose", "kb_finalize"};
+                                   "kb_composite_bwd_pose", "kb_finalize", "k_adam_init"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -1016,6 +1016,35 @@ vt_status vt_pose_adam(vt_ctx *c, double *pose12, double *d_twist, double *state
         k_pose_adam<<<1, 32, 0, stream>>>(pose12, d_twist, state, prm);   // one warp
     }
     VT_CUDA(cudaGetLastError(), "vt_pose_adam launch");
+    return VT_OK;
+}
+
+vt_status vt_adam_init(vt_ctx *c, int64_t n, vt_precision prec, const void *colour,
+                       const void *opacity, const void *radius, const void *scale,
+                       const void *rot, float *theta, float *m, float *v, double *step,
+                       vt_stream stream) {
+    if (n < 0) return fail(VT_ERR_INVALID_ARG, "vt_adam_init: n < 0");
+    if (prec != VT_F32 && prec != VT_F16)
+        return fail(VT_ERR_INVALID_ARG, "vt_adam_init: unknown precision %d", (int)prec);
+    if (!step) return fail(VT_ERR_INVALID_ARG, "vt_adam_init: NULL step");
+    if (n > 0 && (!theta || !m || !v ||
+                  (scale ? !rot : (!colour || !opacity || !radius))))
+        return fail(VT_ERR_INVALID_ARG, "vt_adam_init: NULL array");
+    VT_CUDA(cudaMemsetAsync(step, 0, 3 * sizeof(double), stream), "vt_adam_init step");
+    if (n > 0) {
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        auto go = [&]() {
+            k_adam_init<<<nb, 256, 0, stream>>>(n, (int)prec, colour, opacity, radius, scale,
+                                                rot, theta, m, v);
+        };
+        if (c) {
+            LaunchScope ls(c, K_ADAM_INIT, stream);
+            go();
+        } else {
+            go();
+        }
+    }
+    VT_CUDA(cudaGetLastError(), "vt_adam_init launch");
     return VT_OK;
 }
 

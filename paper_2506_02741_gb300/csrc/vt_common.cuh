@@ -147,6 +147,23 @@ __device__ __forceinline__ int item_of_pixel(const BatchTable &B, int64_t p) {
     return batch_find(B.n_items, [&](int i) { return B.it[i].pbase; }, p);
 }
 
+// The item of a position in a grid-stride loop, remembered between
+// iterations: positions grow, so the search runs only when one leaves the
+// current item's range [lo, hi).
+struct ItemCursor {
+    int it = -1;
+    int64_t lo = 0, hi = 0;
+    template <typename F>
+    __device__ __forceinline__ int at(const BatchTable &B, F start_of, int64_t x) {
+        if (it < 0 || x < lo || x >= hi) {
+            it = batch_find(B.n_items, start_of, x);
+            lo = start_of(it);
+            hi = it + 1 < B.n_items ? start_of(it + 1) : INT64_MAX;
+        }
+        return it;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // float-float ("double-single") arithmetic: Knuth's TwoSum, Dekker's
 // FastTwoSum and the FMA-based exact product.  Every operation uses the
@@ -511,6 +528,9 @@ __global__ void k_adam_step_count(double *step, double beta1, double beta2);
 __global__ void k_attr_adam(int64_t n, float *theta, float *m, float *v, const double *step,
                             float *d_colour, float *d_opacity, float *d_radius, int prec,
                             void *colour, void *opacity, void *radius, AttrAdamParams prm);
+__global__ void k_adam_init(int64_t n, int prec, const void *colour, const void *opacity,
+                            const void *radius, const void *scale, const void *rot, float *theta,
+                            float *m, float *v);
 __global__ void k_pose_finalize(const double *partials, int n_parts, const double *pose_copy,
                                 double *d_twist, double *d_mat);
 __global__ void k_count_valid(const float *depth, int64_t total, uint32_t *block_counts);

@@ -376,8 +376,10 @@ __global__ void __launch_bounds__(kBlockPix, 3) kb_composite_fwd(
     uint32_t *pix_nadd, float *pix_T, uint2 *plist, int plist_cap, uint32_t *blk_ovf,
     const Status *st) {
     const BatchTable &B = *Bp;
+    ItemCursor cur;
+    const auto tstart = [&](int i) { return (int64_t)B.it[i].tbase; };
     for (int t = next_tile(ctr); t < B.n_tiles; t = next_tile(ctr)) {
-        const BatchItem &I = B.it[item_of_tile(B, t)];
+        const BatchItem &I = B.it[cur.at(B, tstart, t)];
         const int64_t P = (int64_t)I.cam.W * I.cam.H;
         fwd_body<false>(I.cam, t - I.tbase, tile_off + I.tbase, sorted, bmask, geo, app, I.image,
                         I.image + 3 * P, I.image + 4 * P, pix_last + I.pbase, pix_nadd + I.pbase,
@@ -1316,8 +1318,10 @@ __global__ void __launch_bounds__(kBlockPix, 3) kb_composite_bwd_list_pose(
     const uint32_t *blk_ovf, const float *grads, double *pose_partials, const Status *st) {
     __shared__ double s_pose[kBlockPix / 32][12];
     const BatchTable &B = *Bp;
+    ItemCursor cur;
+    const auto tstart = [&](int i) { return (int64_t)B.it[i].tbase; };
     for (int t = next_tile(ctr); t < B.n_tiles; t = next_tile(ctr)) {
-        const BatchItem &I = B.it[item_of_tile(B, t)];
+        const BatchItem &I = B.it[cur.at(B, tstart, t)];
         if (!I.track) continue;
         const int64_t P = (int64_t)I.cam.W * I.cam.H;
         const float *g = grads + 4 * I.pbase;
@@ -1336,9 +1340,12 @@ __global__ void __launch_bounds__(kBlockPix) kb_composite_bwd_pose(
     const float4 *app, const uint32_t *pix_last, const float *pix_T, const uint32_t *blk_ovf,
     const float *grads, double *pose_partials, const Status *st) {
     const BatchTable &B = *Bp;
+    ItemCursor cur;
+    const auto tstart = [&](int i) { return (int64_t)B.it[i].tbase; };
     for (int t = blockIdx.x; t < B.n_tiles; t += gridDim.x) {
-        const BatchItem &I = B.it[item_of_tile(B, t)];
+        const BatchItem &I = B.it[cur.at(B, tstart, t)];
         if (!I.track) continue;
+        if (!tile_flagged(blk_ovf + (int64_t)I.tbase * kWarps, t - I.tbase)) continue;
         const int64_t P = (int64_t)I.cam.W * I.cam.H;
         const float *g = grads + 4 * I.pbase;
         replay_body<false>(g_no_sections, I.cam, tile_off + I.tbase, sorted, geo, app,

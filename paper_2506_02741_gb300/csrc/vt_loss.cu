@@ -190,8 +190,10 @@ __global__ void __launch_bounds__(256) k_masked_l1(int64_t P, const float *rgb, 
 __global__ void __launch_bounds__(256) kb_masked_l1(const BatchTable *Bp, float *grads,
                                                     double *l1_part) {
     const BatchTable &B = *Bp;
+    ItemCursor cur;
+    const auto pstart = [&](int i) { return B.it[i].pbase; };
     for (int64_t b = blockIdx.x; b * 256 < B.n_pix; b += gridDim.x) {
-        const BatchItem &I = B.it[item_of_pixel(B, b * 256)];
+        const BatchItem &I = B.it[cur.at(B, pstart, b * 256)];
         if (!I.track) continue;
         const int64_t P = (int64_t)I.cam.W * I.cam.H;
         const double wc = B.w_rgb / (3.0 * (double)P), wd = B.w_depth / (double)P;

@@ -201,4 +201,33 @@ __global__ void __launch_bounds__(256) k_shape_adam(int64_t n, float *__restrict
     }
 }
 
+// Optimiser state of the mapping step from the section's storage, one
+// thread per Gaussian: theta = (c0, c1, c2, logit o, log r) with o clamped
+// to [1e-4, 1 - 1e-4] (so that the logit is finite), moments zero.  With
+// scale != NULL the ellipsoid shape state instead: theta = (log s0, log s1,
+// log s2, q0, q1, q2, q3).
+__global__ void __launch_bounds__(256) k_adam_init(int64_t n, int prec, const void *colour,
+                                                   const void *opacity, const void *radius,
+                                                   const void *scale, const void *rot,
+                                                   float *theta, float *m, float *v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int planes = scale ? 7 : 5;
+    float th[7];
+    if (scale) {
+        for (int k = 0; k < 3; ++k) th[k] = logf(ld_attr(scale, prec, 3 * i + k));
+        for (int k = 0; k < 4; ++k) th[3 + k] = ld_attr(rot, prec, 4 * i + k);
+    } else {
+        for (int k = 0; k < 3; ++k) th[k] = ld_attr(colour, prec, 3 * i + k);
+        const float o = fminf(fmaxf(ld_attr(opacity, prec, i), 1e-4f), 1.f - 1e-4f);
+        th[3] = logf(o / (1.f - o));
+        th[4] = logf(ld_attr(radius, prec, i));
+    }
+    for (int k = 0; k < planes; ++k) {
+        theta[k * n + i] = th[k];
+        m[k * n + i] = 0.f;
+        v[k * n + i] = 0.f;
+    }
+}
+
 }  // namespace vt

@@ -369,8 +369,10 @@ __global__ void __launch_bounds__(256) kb_preprocess(const BatchTable *Bp, const
                                                      const TabRow *tab, float4 *geo, float4 *app,
                                                      uint4 *info, uint32_t *tile_count) {
     const BatchTable &B = *Bp;
+    ItemCursor cur;
+    const auto gstart = [&](int i) { return B.it[i].gbase; };
     for (int64_t g0 = (int64_t)blockIdx.x * 256; g0 < B.n_gauss; g0 += (int64_t)gridDim.x * 256) {
-        const BatchItem &I = B.it[item_of_gauss(B, g0)];
+        const BatchItem &I = B.it[cur.at(B, gstart, g0)];
         const int64_t gid = g0 + threadIdx.x, li = gid - I.gbase;
         uint32_t r0 = 0, r1 = 0, nt = 0;
         if (li < I.n)
@@ -484,8 +486,10 @@ __global__ void __launch_bounds__(256) kb_emit(const BatchTable *Bp, const uint4
                                                uint8_t *bmask_u, const Status *st) {
     if (st->flags) return;
     const BatchTable &B = *Bp;
+    ItemCursor cur;
+    const auto gstart = [&](int i) { return B.it[i].gbase; };
     for (int64_t g0 = (int64_t)blockIdx.x * 256; g0 < B.n_gauss; g0 += (int64_t)gridDim.x * 256) {
-        const BatchItem &I = B.it[item_of_gauss(B, g0)];
+        const BatchItem &I = B.it[cur.at(B, gstart, g0)];
         const int64_t gid = g0 + threadIdx.x;
         emit_gauss(info[gid], gid, I.cam.tiles_x, tile_cursor + I.tbase, bucket, bmask_u);
     }
@@ -800,12 +804,14 @@ __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_
     if (st->flags) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (B) n_tiles = B->n_tiles;
+    ItemCursor cur;
     // grid-stride over tiles: a launch may have fewer blocks than tiles
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const uint32_t start = tile_off[t];
         const int n = (int)(tile_off[t + 1] - start);
         if (n <= lo || n > hi) continue;   // another launch sorts this size class
-        const BatchItem *I = B ? &B->it[item_of_tile(*B, t)] : nullptr;
+        const BatchItem *I =
+            B ? &B->it[cur.at(*B, [&](int i) { return (int64_t)B->it[i].tbase; }, t)] : nullptr;
         const Camera &c = I ? I->cam : cam;
         const int lt = I ? t - I->tbase : t;
         const SortOut out{sorted, bmask, geo, c, start, lt % c.tiles_x, lt / c.tiles_x};

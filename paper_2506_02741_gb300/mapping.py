@@ -45,12 +45,8 @@ class SectionMapper:
         self.lr = [lr_colour] * 3 + [lr_opacity, lr_radius]
         dev = section.colour.device
         n = section.n
-        o = section.opacity.detach().float().clamp(1e-4, 1 - 1e-4)
-        self.theta = torch.stack([*section.colour.detach().float().t(), torch.log(o / (1 - o)),
-                                  torch.log(section.radius.detach().float())]).contiguous()
-        self.m = torch.zeros(5, n, device=dev)
-        self.v = torch.zeros(5, n, device=dev)
-        self.step_state = torch.zeros(3, dtype=torch.float64, device=dev)
+        # (c, logit o, log r) and zero moments, formed by the library
+        self.theta, self.m, self.v, self.step_state = api.adam_init(section, renderer=renderer)
         self.d_colour = torch.zeros(n, 3, device=dev)
         self.d_opacity = torch.zeros(n, device=dev)
         self.d_radius = torch.zeros(n, device=dev)
@@ -64,11 +60,8 @@ class SectionMapper:
         self.shape = None
         if section.ellipsoids:
             self.lr_shape = (float(lr_scale), float(lr_rot))
-            self.shape = torch.cat([torch.log(section.scale.detach().float()).t(),
-                                    section.rot.detach().float().t()]).contiguous()
-            self.shape_m = torch.zeros(7, n, device=dev)
-            self.shape_v = torch.zeros(7, n, device=dev)
-            self.shape_step = torch.zeros(3, dtype=torch.float64, device=dev)
+            self.shape, self.shape_m, self.shape_v, self.shape_step = api.adam_init(
+                section, shape=True, renderer=renderer)
             self.d_scale = torch.zeros(n, 3, device=dev)
             self.d_rot = torch.zeros(n, 4, device=dev)
 

@@ -14,16 +14,18 @@ resolution and size on one GPU.
 BatchServer is the served form: continuous batching with one persistent
 launch per stage (vt_batch_*).  It keeps ``n_contexts`` batch contexts, each
 with its own stream, workspace and capacity; whenever a context is idle it
-takes the queued requests in arrival order that fit its remaining capacity
-(Gaussians, pixels, tiles, views, estimated tile instances, 64 items) into
-one batch, uploads their poses and observations, launches the batch
-(replaying a CUDA graph captured once per context) and copies the results
-back.  Requests that arrive while batches run wait in the queue and are
-admitted as soon as a context frees up; the contexts' batches overlap on the
-device.  The capacities come from the free device memory at start-up
-(admission by free HBM): a request is deferred until a context has room and
-refused only if it can never fit one.  A batch that still exceeds the
-reserved tile instances on the device is run again in halves.
+takes the queued requests in arrival order into one batch while they fit its
+capacity (Gaussians, pixels, tiles, views, estimated tile instances, 64
+items) and their estimated GPU time stays within ``batch_ms`` -- a lone
+request goes at once, batches grow as requests queue up -- uploads their
+poses and observations, launches the batch (replaying a CUDA graph captured
+once per context) and copies the results back.  Requests that arrive while
+batches run wait in the queue and are admitted as soon as a context frees
+up; the contexts' batches overlap on the device.  The capacities come from
+the free device memory at start-up (admission by free HBM): a request is
+deferred until a context has room and refused only if it can never fit one.
+A batch that exceeds the reserved tile instances on the device (found after
+it ran) raises the estimates and is queued again.
 
 SlotServer runs requests on ``n_slots`` independent render contexts (one
 request per slot and stream), optionally replaying a CUDA graph per
@@ -74,7 +76,13 @@ class _BatchCtx:
 
     def __init__(self, server: "BatchServer", cap: dict):
         dev = server.device
-        self.stream = torch.cuda.Stream(device=dev)
+        # one stream per priority level: a batch launched while k others run
+        # goes on streams[k], so the GPU's block scheduler favours the
+        # batches in the order they were admitted and a later batch fills
+        # the SMs the earlier ones leave idle
+        self.streams = [torch.cuda.Stream(device=dev, priority=-(server.n_contexts - 1 - k))
+                        for k in range(server.n_contexts)]
+        self.stream = self.streams[0]
         self.cap = cap
         with torch.cuda.stream(self.stream):
             self.runner = api.BatchRunner(cap["gaussians"], cap["pixels"], cap["tiles"],
@@ -99,12 +107,15 @@ class _BatchCtx:
 
 
 class BatchServer:
-    def __init__(self, sections, resolutions, n_contexts: int = 2, graphs: bool = True,
-                 memory_budget: int | None = None, list_cap: int = 64, keep_results: bool = True,
-                 device="cuda"):
+    def __init__(self, sections, resolutions, n_contexts: int = 3, graphs: bool = True,
+                 memory_budget: int | None = None, list_cap: int = 256, batch_ms: float = 4.0,
+                 keep_results: bool = True, device="cuda"):
         """sections: list of api.Section (resident, spheres); resolutions:
         list of (W, H) buckets.  The contexts share memory_budget (default:
-        70% of the free device memory) in equal parts."""
+        70% of the free device memory) in equal parts.  A batch takes the
+        queued requests in arrival order while their estimated GPU time stays
+        within batch_ms (the first request always goes), so that batches
+        grow only when requests queue up."""
         from . import synthetic as syn
         self.device = torch.device(device)
         self.sections = sections
@@ -112,14 +123,16 @@ class BatchServer:
         self.intrinsics = [syn.scaled_intrinsics(W, H).astuple() for W, H in self.resolutions]
         self.graphs = graphs
         self.list_cap = int(list_cap)
+        self.batch_ms = float(batch_ms)
         self.keep_results = keep_results
         free, _ = torch.cuda.mem_get_info(self.device)
         self.memory_budget = int(memory_budget if memory_budget is not None else 0.7 * free)
         self.n_contexts = int(n_contexts)
         self.ctxs: list[_BatchCtx] = []
         # tile instances per (section, bucket): measured at warm-up, raised
-        # when a batch overflows
+        # when a batch overflows; GPU milliseconds per (section, bucket, kind)
         self.inst_est: dict = {}
+        self.ms_est: dict = {}
         self.splits = 0
 
     # -- capacity -------------------------------------------------------------
@@ -131,27 +144,33 @@ class BatchServer:
                     table_rows=s.n_views * (s.depth.shape[-1] + s.depth.shape[-2]),
                     instances=int(self.inst_est.get((r.section, r.bucket), 6 * s.n + 65536)))
 
+    def _ms(self, r: Request) -> float:
+        k = (r.section, r.bucket, r.kind)
+        if k in self.ms_est:
+            return self.ms_est[k]
+        return float(np.mean(list(self.ms_est.values()))) if self.ms_est else self.batch_ms
+
+    def _bytes(self, cap) -> int:
+        return api.BatchRunner.workspace_bytes_for(
+            cap["gaussians"], cap["pixels"], cap["tiles"], cap["instances"], cap["views"],
+            cap["table_rows"], self.list_cap) + 36 * cap["pixels"]
+
     def _capacity(self, requests) -> dict:
-        """Per-context capacity: the largest request at least, the rest of the
-        context's share of the memory budget spread over the totals in the
-        proportions of the request mix."""
+        """Per-context capacity: room for the largest request and for
+        ``per_batch`` average requests (the batches batch_ms allows), within
+        the context's share of the memory budget."""
         needs = [self._need(r) for r in requests]
         big = {k: max(n[k] for n in needs) for k in needs[0]}
         mean = {k: float(np.mean([n[k] for n in needs])) for k in needs[0]}
+        ms = float(np.mean([self._ms(r) for r in requests]))
+        per_batch = int(min(64, max(2, 2.0 * self.batch_ms / max(ms, 1e-3))))
         share = self.memory_budget // max(1, self.n_contexts)
-        per_item = api.BatchRunner.workspace_bytes_for(
-            mean["gaussians"], mean["pixels"], mean["tiles"], mean["instances"], mean["views"],
-            mean["table_rows"], self.list_cap) + 36 * mean["pixels"]
-        items = int(max(1, min(64, share // max(per_item, 1))))
-        cap = {k: int(max(big[k], items * mean[k])) for k in big}
-        while True:
-            need = api.BatchRunner.workspace_bytes_for(
-                cap["gaussians"], cap["pixels"], cap["tiles"], cap["instances"], cap["views"],
-                cap["table_rows"], self.list_cap) + 36 * cap["pixels"]
-            if need <= share or all(cap[k] <= big[k] for k in cap):
-                break
+        cap = {k: int(max(big[k], per_batch * mean[k])) for k in big}
+        while self._bytes(cap) > share and any(cap[k] > big[k] for k in cap):
             cap = {k: int(max(big[k], 0.85 * cap[k])) for k in cap}
-        cap["tiles"] = max(cap["tiles"], 1)
+        if self._bytes(cap) > share:
+            raise MemoryError(f"the largest request needs {self._bytes(cap)} bytes, more than "
+                              f"a context's share {share} of the budget")
         return cap
 
     def _measure_instances(self, requests):
@@ -160,10 +179,7 @@ class BatchServer:
         R = api.Renderer()
         seen = {}
         for r in requests:
-            key = (r.section, r.bucket)
-            if key in seen:
-                continue
-            seen[key] = r
+            seen.setdefault((r.section, r.bucket), r)
         for (s, b), r in seen.items():
             W, H = self.resolutions[b]
             R.render([self.sections[s]], api.pose12(r.pose, self.device), self.intrinsics[b], W, H,
@@ -172,10 +188,36 @@ class BatchServer:
         del R
         torch.cuda.synchronize()
 
+    def _measure_times(self, ctx, requests):
+        """GPU time of a one-item batch of every (section, bucket, kind) the
+        requests use (CUDA events, second of two runs)."""
+        seen = {}
+        for r in requests:
+            seen.setdefault((r.section, r.bucket, r.kind), r)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for key, r in seen.items():
+            r = dataclasses.replace(r, obs=self._dummy_obs(r))
+            items, _ = self._items(ctx, [r])
+            with torch.cuda.stream(ctx.stream):
+                for _ in range(2):
+                    if r.kind == "track":
+                        items[0].obs.copy_(r.obs, non_blocking=True)
+                    ctx.runner.set(self.sections, items, **TRACK_WEIGHTS)
+                    e0.record(ctx.stream)
+                    ctx.runner.launch(stream=ctx.stream)
+                    e1.record(ctx.stream)
+                e1.synchronize()
+            self.ms_est[key] = e0.elapsed_time(e1)
+
     def warm(self, requests):
-        """Measure the instance counts, size and create the contexts, run one
-        batch on each and capture its launch graph."""
+        """Measure instance counts, create the contexts, time every kind of
+        request once, run one batch on each context and capture its launch
+        graph."""
         self._measure_instances(requests)
+        probe = _BatchCtx(self, {k: v for k, v in self._need_max(requests).items()})
+        self._measure_times(probe, requests)
+        del probe
+        torch.cuda.synchronize()
         cap = self._capacity(requests)
         self.ctxs = [_BatchCtx(self, cap) for _ in range(self.n_contexts)]
         for ctx in self.ctxs:
@@ -185,6 +227,10 @@ class BatchServer:
             ctx.reqs = []
         torch.cuda.synchronize()
 
+    def _need_max(self, requests) -> dict:
+        needs = [self._need(r) for r in requests]
+        return {k: max(n[k] for n in needs) for k in needs[0]}
+
     def _dummy_obs(self, r):
         if r.kind != "track":
             return None
@@ -192,9 +238,9 @@ class BatchServer:
         return r.obs if r.obs is not None else torch.zeros(4, H, W).pin_memory()
 
     # -- batches -------------------------------------------------------------
-    def _fits(self, ctx, used, need) -> bool:
-        return len(used["n"]) < ctx.max_items and all(
-            used[k] + need[k] <= ctx.cap[k] for k in ctx.cap)
+    def _fits(self, ctx, used, need, ms) -> bool:
+        return (used["items"] < ctx.max_items and used["ms"] + ms <= self.batch_ms and
+                all(used[k] + need[k] <= ctx.cap[k] for k in ctx.cap))
 
     def _items(self, ctx, reqs):
         items, slices = [], []
@@ -213,12 +259,12 @@ class BatchServer:
             off += _pad(P)
         return items, slices
 
-    def _launch(self, ctx, reqs, warmup=False):
+    def _launch(self, ctx, reqs, warmup=False, level=0):
         items, slices = self._items(ctx, reqs)
+        ctx.stream = ctx.streams[min(level, len(ctx.streams) - 1)]
         with torch.cuda.stream(ctx.stream):
             for i, r in enumerate(reqs):
-                ctx.poses_host[i] = torch.from_numpy(
-                    np.asarray(api.pose12(r.pose, "cpu").numpy(), np.float64))
+                ctx.poses_host[i] = api.pose12(r.pose, "cpu")
             ctx.poses.copy_(ctx.poses_host, non_blocking=True)
             for it, r in zip(items, reqs):
                 if r.kind == "track":     # the request's own observation
@@ -254,7 +300,7 @@ class BatchServer:
             if e.status != L.VT_ERR_CAPACITY:
                 raise
             # more tile instances than estimated: raise the estimates of the
-            # batch's (section, bucket) pairs and run it again in halves
+            # batch's (section, bucket) pairs and queue its requests again
             for r in ctx.reqs:
                 k = (r.section, r.bucket)
                 self.inst_est[k] = 2 * self.inst_est.get(k, 0) + 65536
@@ -299,19 +345,21 @@ class BatchServer:
                 if ctx.busy() or not queue:
                     continue
                 used = dict(gaussians=0, pixels=0, tiles=0, views=0, table_rows=0, instances=0,
-                            n=[])
-                take = []
+                            items=0, ms=0.0)
+                take = [queue.popleft()]   # the head always goes (it fits an empty context)
+                for k, v in self._need(take[0]).items():
+                    used[k] += v
+                used["items"], used["ms"] = 1, self._ms(take[0])
                 while queue:
-                    need = self._need(queue[0])
-                    if not self._fits(ctx, used, need):
+                    need, ms = self._need(queue[0]), self._ms(queue[0])
+                    if not self._fits(ctx, used, need, ms):
                         break
                     for k in need:
                         used[k] += need[k]
-                    used["n"].append(1)
+                    used["items"] += 1
+                    used["ms"] += ms
                     take.append(queue.popleft())
-                if not take:               # the head does not fit: a lone item always does
-                    take.append(queue.popleft())
-                self._launch(ctx, take)
+                self._launch(ctx, take, level=sum(c.busy() for c in self.ctxs))
             if all(c.busy() for c in self.ctxs) or (not queue and nxt < len(pending)):
                 time.sleep(20e-6)
         return finished

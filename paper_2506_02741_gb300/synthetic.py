@@ -245,6 +245,53 @@ def render_frames(room: Room, K: Intrinsics, poses: list) -> Frames:
     return Frames(K, list(poses), np.stack(ds), np.stack(cs))
 
 
+# ----------------------------------------------------------------------------
+# multi-room scene: closed rooms side by side along x (room k spans
+# x in [4k - 2, 4k + 2] and has its own seeded spheres, colours and light);
+# a frame shows the room its camera is in.
+
+ROOM_PITCH = 4.0
+
+
+def make_rooms(n_rooms: int, seed: int = SCENE_SEED) -> list:
+    return [make_room(seed + 101 * k, x_offset=ROOM_PITCH * k) for k in range(n_rooms)]
+
+
+def room_of(rooms: list, pose: np.ndarray) -> Room:
+    k = int(np.clip(np.floor((pose[0, 3] + ROOM_PITCH / 2) / ROOM_PITCH), 0, len(rooms) - 1))
+    return rooms[k]
+
+
+def multi_room_trajectory(n_frames: int, n_rooms: int, seed: int = TRAJECTORY_SEED,
+                          max_step_m: float = 0.02, max_step_deg: float = 1.0) -> list:
+    """A smooth seeded path through n_rooms rooms: the camera advances along
+    x at a constant speed from 0.6 m inside the first room's far wall to 0.6 m
+    before the last room's (at most half of max_step_m per frame) and wanders
+    by the seeded sinusoids of trajectory() within the other half of the
+    per-frame bounds."""
+    speed = (ROOM_PITCH * n_rooms - 1.2) / max(n_frames - 1, 1)
+    if speed > 0.5 * max_step_m:
+        raise ValueError("too few frames for the rooms at this step bound")
+    wander = trajectory(n_frames, seed, max_step_m=0.5 * max_step_m, max_step_deg=max_step_deg)
+    x0 = -ROOM_PITCH / 2 + 0.6
+    out = []
+    for f, p in enumerate(wander):
+        q = p.copy()
+        q[0, 3] += x0 + speed * f
+        q[2, 3] += 0.4
+        out.append(q)
+    return out
+
+
+def render_multi(rooms: list, K: Intrinsics, poses: list) -> Frames:
+    ds, cs = [], []
+    for p in poses:
+        d, c = raycast(room_of(rooms, p), K, p)
+        ds.append(d)
+        cs.append(c)
+    return Frames(K, list(poses), np.stack(ds), np.stack(cs))
+
+
 def tiny_workload(seed: int = SCENE_SEED):
     """64x48, one view at the identity pose, target pose perturbed by
     (1 cm, 0.5 deg) noise."""

@@ -276,3 +276,88 @@ def test_large_multisection_render():
     assert torch.equal(results[0][0], results[1][0])
     torch.testing.assert_close(results[0][1], results[1][1], rtol=1e-6,
                                atol=1e-9 * float(results[1][1].abs().max()))
+
+
+def _multiroom_sections(dev, n_sec=6, per=16, every=5):
+    """Six adjacent sections of 16 keyframes (every 5th frame from frame 200)
+    of the 2000-frame path through five rooms, 640x480: 29,491,200
+    Gaussians; the target pose lies inside the middle section."""
+    K = syn.VGA
+    rooms = syn.make_rooms(5)
+    path = syn.multi_room_trajectory(2000, 5)
+    idx = [200 + every * j for j in range(n_sec * per)]
+    fr = syn.render_multi(rooms, K, [path[i] for i in idx])
+    dsecs, osecs = [], []
+    for s in range(n_sec):
+        sl = slice(s * per, (s + 1) * per)
+        keys = np.stack([path[i] for i in idx[sl]])
+        dsecs.append(api.Section.from_rgbd(torch.from_numpy(fr.depth[sl]).to(dev),
+                                           torch.from_numpy(fr.rgb[sl]).to(dev), K.astuple(),
+                                           keys))
+        osecs.append(G.quantise(oracle.section_init(fr.depth[sl], fr.rgb[sl], K.astuple(), keys)))
+    return K, dsecs, osecs, path[200 + every * (n_sec * per // 2) + 2]
+
+
+def test_multiroom_large_scene_finite_differences():
+    """The large end of the multi-room workload (29.5 M Gaussians of six
+    sections rendered together): a 96x80 crop and its pose gradient against
+    the oracle along the GPU's decisions (given the Gaussians that can reach
+    the crop), and central differences of the GPU forward in the opacity of
+    64 sampled Gaussians against the oracle's opacity gradient: the GPU's
+    render at that scale changes as the oracle's gradient says."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    K, dsecs, osecs, target = _multiroom_sections(dev)
+    assert sum(s.n for s in dsecs) == 29_491_200
+    pose = api.pose12(target, dev)
+    R = api.Renderer()
+    rgb, depth, sil = R.render(dsecs, pose, K.astuple(), K.W, K.H, checked=True)
+    cw, ch = 96, 80
+    x0, y0 = (K.W - cw) // 2 + 24, (K.H - ch) // 2 - 16
+    Kc = _crop(K, x0, y0)
+    subs, keeps = zip(*[_crop_subset(s, target, K, (x0, y0, cw, ch)) for s in osecs])
+    ids, cnt = G.decisions(dsecs, pose, K.astuple(), K.W, K.H, out=(rgb, depth, sil),
+                           box=(x0, y0, cw, ch), id_map=G.subset_map(list(keeps)), cap=4096)
+    ref = oracle.render_lists(list(subs), target, Kc, cw, ch, ids, cnt)
+    G.check_decisions(ref, "multiroom_29.5M")
+    sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
+    G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref)
+    rng = np.random.default_rng(21)
+    gR = rng.normal(0, 1, (3, ch, cw)).astype(np.float32)
+    want = oracle.backward_lists(list(subs), target, Kc, cw, ch, ids, cnt, g_rgb=gR)
+    full_gR = torch.zeros(3, K.H, K.W, device=dev)
+    full_gR[:, sl[0], sl[1]] = torch.from_numpy(gR).to(dev)
+    dtw, _ = R.backward(full_gR, None, None, pose_grad=True)
+    torch.cuda.synchronize()
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist", noise=want["twist_noise"])
+    # 64 Gaussians with the largest opacity terms (o = 0.9 everywhere: the
+    # 1/255 cut lies outside the 3-sigma disc, so a small change of o moves
+    # no inclusion decision)
+    cand = []
+    for s, (k, a) in enumerate(zip(keeps, want["abs_opacity"])):
+        full = np.flatnonzero(k)
+        for j in np.argsort(-a)[:64]:
+            cand.append((a[j], s, int(full[j]), float(want["opacity"][s][j])))
+    cand.sort(reverse=True)
+    g_crop = torch.from_numpy(gR.astype(np.float64)).to(dev)
+
+    def loss():
+        out, _, _ = R.render(dsecs, pose, K.astuple(), K.W, K.H)
+        return float((out[:, sl[0], sl[1]].double() * g_crop).sum())
+
+    e = 1e-3
+    ok = 0
+    for _, s, li, g_want in cand[:64]:
+        o = dsecs[s].opacity
+        v = float(o[li])
+        o[li] = v + e
+        lp = loss()
+        o[li] = v - e
+        lm = loss()
+        o[li] = v
+        fd = (lp - lm) / (2 * e)
+        ok += abs(fd - g_want) <= 1e-2 * abs(g_want) + 1e-4
+    # a pixel whose walk stops within the step of its termination threshold
+    # jumps; allow a few of the 64
+    assert ok >= 60, ok

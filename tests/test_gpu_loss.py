@@ -183,6 +183,37 @@ def test_attr_adam_matches_reference(dev, prec):
         assert st[0].item() == t
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_adam_init_from_storage(dev, prec):
+    """vt_adam_init: theta = (c, logit o, log r) of the stored values (o
+    clamped to [1e-4, 1 - 1e-4], so o = 1 and o = 0 stay finite), moments
+    and step zeroed; for ellipsoids (log s, q)."""
+    rng = np.random.default_rng(8)
+    n = 777
+    dt = torch.float16 if prec == "f16" else torch.float32
+    col = rng.random((n, 3)).astype(np.float32)
+    opa = rng.random(n).astype(np.float32)
+    opa[:3] = [0.0, 1.0, 0.5]
+    rad = (0.002 + 0.01 * rng.random(n)).astype(np.float32)
+    sc = rng.uniform(0.002, 0.02, (n, 3)).astype(np.float32)
+    qt = rng.normal(size=(n, 4)).astype(np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    sec = api.Section(poses=torch.zeros(1, 12, dtype=torch.float64, device=dev),
+                      depth=torch.ones(1, 1, n, device=dev), K=(1.0, 1.0, 0.0, 0.0),
+                      src=torch.arange(n, dtype=torch.int32, device=dev), colour=t(col),
+                      opacity=t(opa), radius=t(rad), scale=t(sc), rot=t(qt))
+    stored = lambda x: x.float().cpu().numpy().astype(np.float64)
+    th, m, v, st = api.adam_init(sec)
+    o = np.clip(stored(sec.opacity), 1e-4, 1 - 1e-4)
+    want = np.stack([*stored(sec.colour).T, np.log(o / (1 - o)), np.log(stored(sec.radius))])
+    np.testing.assert_allclose(th.cpu().numpy(), want, rtol=2e-6, atol=2e-6)
+    assert not m.any() and not v.any() and not st.any()
+    th, m, v, st = api.adam_init(sec, shape=True)
+    want = np.concatenate([np.log(stored(sec.scale)).T, stored(sec.rot).T])
+    np.testing.assert_allclose(th.cpu().numpy(), want, rtol=2e-6, atol=2e-6)
+    assert th.shape == (7, n) and not m.any() and not v.any()
+
+
 def test_mapper_reduces_loss(dev):
     """A few mapping iterations (render, fused loss, attribute backward, fused
     Adam) on a perturbed section lower the Eq. 2 L1 loss."""

@@ -135,7 +135,7 @@ def test_admission_under_a_small_budget(dev, setup):
     sections = setup[0]
     reqs = _requests(setup, n=20, seed=11, rate=1e6)
     server = serving.BatchServer(sections, RES, n_contexts=2, graphs=False,
-                                 memory_budget=200 << 20)
+                                 memory_budget=600 << 20)
     server.warm(reqs)
     cap = server.ctxs[0].cap
     done = server.run(reqs)
