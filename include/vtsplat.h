@@ -52,6 +52,7 @@ extern "C" {
 #endif
 
 typedef struct CUstream_st *vt_stream; /* same type as cudaStream_t */
+typedef struct CUevent_st *vt_event;   /* same type as cudaEvent_t */
 
 typedef enum {
     VT_OK = 0,
@@ -386,11 +387,18 @@ vt_status vt_batch_set(vt_ctx *ctx, const vt_section *secs, int32_t n_secs,
                        const vt_batch_item *items, int32_t n_items, vt_l1_weights w);
 
 /* Enqueue on stream the upload of the staged table and the batch's
- * launches (capturable).  Results are in the items' image and result
+ * launches.  obs_ready (may be NULL): an event the tracking items'
+ * observations are complete at (e.g. recorded after their uploads on a copy
+ * stream); the stream waits for it only before the loss stage, so the
+ * uploads overlap the render stages.  Pass NULL when capturing.  Outside a stream capture the grids are sized to the staged
+ * batch (one block per unit of work, so that concurrent batches on streams
+ * of different priority share the SMs block by block); inside a capture
+ * they are persistent grids sized by the SM count that read the work from
+ * the uploaded table, so the captured graph serves every later batch.  Results are in the items' image and result
  * buffers when the stream reaches that point; vt_ctx_sync_status reports
  * VT_ERR_CAPACITY if the batch had more tile instances than reserved (its
  * results are then undefined). */
-vt_status vt_batch_launch(vt_ctx *ctx, vt_stream stream);
+vt_status vt_batch_launch(vt_ctx *ctx, vt_stream stream, vt_event obs_ready);
 
 /* SSIM term of Eq. 2 (Sec. 3.4 mapping loss: tau L_S(V, V'), L_S the SSIM
  * loss; tau = 0.2 in Sec. 4).  L_S = 1 - mean SSIM over the pixels and the

@@ -131,7 +131,7 @@ def _declare(L):
                                        C.c_int64, C.c_int64, _P]),
         "vt_batch_set": (C.c_int, [_P, C.POINTER(SectionC), C.c_int32, C.POINTER(BatchItemC),
                                    C.c_int32, L1WeightsC]),
-        "vt_batch_launch": (C.c_int, [_P, _P]),
+        "vt_batch_launch": (C.c_int, [_P, _P, _P]),
         "vt_adam_init": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                    _P]),
         "vt_last_error": (C.c_char_p, []),

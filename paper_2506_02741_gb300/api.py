@@ -683,5 +683,9 @@ class BatchRunner(Renderer):
                 "vt_batch_set")
         self._keep = (sections, items)
 
-    def launch(self, stream=None):
-        L.check(self._lib.vt_batch_launch(self._ctx, _stream(stream)), "vt_batch_launch")
+    def launch(self, stream=None, obs_ready=None):
+        """Enqueue the staged batch; obs_ready (a torch.cuda.Event, optional)
+        marks the tracking items' observations as uploaded: only the loss
+        stage waits for it."""
+        ev = C.c_void_p(obs_ready.cuda_event) if obs_ready is not None else None
+        L.check(self._lib.vt_batch_launch(self._ctx, _stream(stream), ev), "vt_batch_launch")

@@ -1450,7 +1450,7 @@ vt_status vt_batch_set(vt_ctx *c, const vt_section *secs, int32_t n_secs,
     return VT_OK;
 }
 
-vt_status vt_batch_launch(vt_ctx *c, vt_stream stream) {
+vt_status vt_batch_launch(vt_ctx *c, vt_stream stream, vt_event obs_ready) {
     if (!c) return fail(VT_ERR_INVALID_ARG, "vt_batch_launch: ctx is NULL");
     if (!c->batch || !c->batch_set)
         return fail(VT_ERR_STATE, "vt_batch_launch: no batch staged (vt_batch_set)");
@@ -1460,6 +1460,18 @@ vt_status vt_batch_launch(vt_ctx *c, vt_stream stream) {
     c->has_render = false;   // the batch overwrites a single render's state
     const int nsm = c->n_sm;
     BatchTable *B = c->btab;
+    // Grids: outside a capture one block per unit of work of the staged
+    // batch (the stages then yield SMs block by block, so stream priorities
+    // between concurrent batches take effect); inside a capture persistent
+    // grids sized by the SM count, which serve any later batch the table
+    // describes.
+    const BatchTable &H = *c->btab_host;
+    const bool exact = cs == cudaStreamCaptureStatusNone;
+    auto grid = [&](int64_t units, int per_sm) -> unsigned {
+        const int64_t g = exact ? units : (int64_t)per_sm * nsm;
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 0x7fffffff));
+    };
+    const int64_t g_chunks = H.n_gauss / 256, p_chunks = H.n_pix / 256;
     VT_CUDA(cudaMemcpyAsync(B, c->btab_host, sizeof(BatchTable), cudaMemcpyHostToDevice, stream),
             "batch table upload");
     if (cs == cudaStreamCaptureStatusNone) {
@@ -1468,11 +1480,11 @@ vt_status vt_batch_launch(vt_ctx *c, vt_stream stream) {
     }
     {
         LaunchScope ls(c, KB_SETUP, stream);
-        kb_setup<<<2 * nsm, 256, 0, stream>>>(B, c->views, c->tab, c->bpose, c->tile_count);
+        kb_setup<<<grid(std::max<int64_t>(H.n_views, (H.n_tiles + 256) / 256), 2), 256, 0, stream>>>(B, c->views, c->tab, c->bpose, c->tile_count);
     }
     {
         LaunchScope ls(c, KB_PREPROCESS, stream);
-        kb_preprocess<<<8 * nsm, 256, 0, stream>>>(B, c->views, c->tab, c->geo, c->app, c->info,
+        kb_preprocess<<<grid(g_chunks, 8), 256, 0, stream>>>(B, c->views, c->tab, c->geo, c->app, c->info,
                                                    c->tile_count);
     }
     {
@@ -1482,39 +1494,39 @@ vt_status vt_batch_launch(vt_ctx *c, vt_stream stream) {
     }
     {
         LaunchScope ls(c, KB_EMIT, stream);
-        kb_emit<<<8 * nsm, 256, 0, stream>>>(B, c->info, c->tile_cursor, c->bucket, c->bmask_u,
+        kb_emit<<<grid(g_chunks, 8), 256, 0, stream>>>(B, c->info, c->tile_cursor, c->bucket, c->bmask_u,
                                              c->status);
     }
     VT_CUDA(cudaEventRecord(c->ev_fork, stream), "sort fork");
     VT_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "sort fork");
     {
         LaunchScope ls(c, KB_SORT_LONG, c->aux);
-        kb_sort_tiles_long<<<nsm, 512, kSortSmemBigBytes, c->aux>>>(
+        kb_sort_tiles_long<<<grid(std::min<int64_t>(H.n_tiles, nsm), 1), 512, kSortSmemBigBytes, c->aux>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
             kSortSmemBig, kSortSmemN, kSortSmemBig);
     }
     {
         LaunchScope ls(c, KB_SORT_XL, c->aux);
-        kb_sort_tiles_xl<<<2 * nsm, 512, kSortHistBytes, c->aux>>>(
+        kb_sort_tiles_xl<<<grid(std::min<int64_t>(H.n_tiles, 2 * nsm), 2), 512, kSortHistBytes, c->aux>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
             kSortSmemBig, kSortSmemBig, 0x7fffffff);
     }
     VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
     {
         LaunchScope ls(c, KB_SORT, stream);
-        kb_sort_tiles<<<4 * nsm, 512, sort_smem_bytes(kSortClassS), stream>>>(
+        kb_sort_tiles<<<grid(H.n_tiles, 4), 512, sort_smem_bytes(kSortClassS), stream>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
             kSortClassS, 0, kSortClassS);
     }
     {
         LaunchScope ls(c, KB_SORT_M, stream);
-        kb_sort_tiles_mid<<<3 * nsm, 512, sort_smem_bytes(kSortClassM), stream>>>(
+        kb_sort_tiles_mid<<<grid(H.n_tiles, 3), 512, sort_smem_bytes(kSortClassM), stream>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
             kSortClassM, kSortClassS, kSortClassM);
     }
     {
         LaunchScope ls(c, KB_SORT_L, stream);
-        kb_sort_tiles_large<<<2 * nsm, 512, kSortSmemBytes, stream>>>(
+        kb_sort_tiles_large<<<grid(H.n_tiles, 2), 512, kSortSmemBytes, stream>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
             kSortSmemN, kSortClassM, kSortSmemN);
     }
@@ -1522,30 +1534,33 @@ vt_status vt_batch_launch(vt_ctx *c, vt_stream stream) {
     const int cap = c->batch_lists ? c->list_cap : 0;
     {
         LaunchScope ls(c, KB_FWD, stream);
-        kb_composite_fwd<<<6 * nsm, kBlockPix, 0, stream>>>(
+        kb_composite_fwd<<<grid(H.n_tiles, 6), kBlockPix, 0, stream>>>(
             B, &B->ctr[0], c->tile_off, c->sorted, c->bmask, c->geo, c->app, c->pix_last,
             c->pix_nadd, c->pix_T, c->batch_lists ? c->plist : nullptr, cap, c->blk_ovf,
             c->status);
     }
+    if (obs_ready)   // the observations arrive while the render stages run
+        VT_CUDA(cudaStreamWaitEvent(stream, reinterpret_cast<cudaEvent_t>(obs_ready), 0),
+                "vt_batch_launch: observation event");
     {
         LaunchScope ls(c, KB_L1, stream);
-        kb_masked_l1<<<8 * nsm, 256, 0, stream>>>(B, c->bgrads, c->bl1);
+        kb_masked_l1<<<grid(p_chunks, 8), 256, 0, stream>>>(B, c->bgrads, c->bl1);
     }
     if (c->batch_lists) {
         LaunchScope ls(c, KB_BWD_LIST, stream);
-        kb_composite_bwd_list_pose<<<3 * nsm, kBlockPix, 0, stream>>>(
+        kb_composite_bwd_list_pose<<<grid(H.n_tiles, 3), kBlockPix, 0, stream>>>(
             B, &B->ctr[1], c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, cap, c->blk_ovf,
             c->bgrads, c->pose_partials, c->status);
     }
     {
         LaunchScope ls(c, KB_BWD, stream);
-        kb_composite_bwd_pose<<<2 * nsm, kBlockPix, 0, stream>>>(
+        kb_composite_bwd_pose<<<grid(H.n_tiles, 2), kBlockPix, 0, stream>>>(
             B, c->tile_off, c->sorted, c->geo, c->app, c->pix_last, c->pix_T, c->blk_ovf,
             c->bgrads, c->pose_partials, c->status);
     }
     {
         LaunchScope ls(c, KB_FINALIZE, stream);
-        kb_finalize<<<kMaxItems, 384, 0, stream>>>(B, c->bl1, c->pose_partials, c->bpose);
+        kb_finalize<<<exact ? (unsigned)H.n_items : (unsigned)kMaxItems, 384, 0, stream>>>(B, c->bl1, c->pose_partials, c->bpose);
     }
     VT_CUDA(cudaGetLastError(), "vt_batch_launch");
     return VT_OK;

@@ -83,6 +83,7 @@ class _BatchCtx:
         self.streams = [torch.cuda.Stream(device=dev, priority=-(server.n_contexts - 1 - k))
                         for k in range(server.n_contexts)]
         self.stream = self.streams[0]
+        self.copy_stream = torch.cuda.Stream(device=dev)   # observation uploads
         self.cap = cap
         with torch.cuda.stream(self.stream):
             self.runner = api.BatchRunner(cap["gaussians"], cap["pixels"], cap["tiles"],
@@ -109,13 +110,18 @@ class _BatchCtx:
 class BatchServer:
     def __init__(self, sections, resolutions, n_contexts: int = 3, graphs: bool = True,
                  memory_budget: int | None = None, list_cap: int = 256, batch_ms: float = 4.0,
-                 keep_results: bool = True, device="cuda"):
+                 graph_ms: float = 1.0, keep_results: bool = True, device="cuda"):
         """sections: list of api.Section (resident, spheres); resolutions:
         list of (W, H) buckets.  The contexts share memory_budget (default:
         70% of the free device memory) in equal parts.  A batch takes the
         queued requests in arrival order while their estimated GPU time stays
         within batch_ms (the first request always goes), so that batches
-        grow only when requests queue up."""
+        grow only when requests queue up.  A batch whose estimated GPU time
+        is below graph_ms replays the context's captured launch graph
+        (persistent grids: launch overhead matters there); a longer one is
+        launched directly with grids sized to its work, so that the stages of
+        concurrent batches yield SMs block by block and the priority of the
+        earlier batch holds."""
         from . import synthetic as syn
         self.device = torch.device(device)
         self.sections = sections
@@ -124,6 +130,7 @@ class BatchServer:
         self.graphs = graphs
         self.list_cap = int(list_cap)
         self.batch_ms = float(batch_ms)
+        self.graph_ms = float(graph_ms)
         self.keep_results = keep_results
         free, _ = torch.cuda.mem_get_info(self.device)
         self.memory_budget = int(memory_budget if memory_budget is not None else 0.7 * free)
@@ -266,9 +273,22 @@ class BatchServer:
             for i, r in enumerate(reqs):
                 ctx.poses_host[i] = api.pose12(r.pose, "cpu")
             ctx.poses.copy_(ctx.poses_host, non_blocking=True)
-            for it, r in zip(items, reqs):
-                if r.kind == "track":     # the request's own observation
-                    it.obs.copy_(r.obs, non_blocking=True)
+            use_graph = (ctx.graph is not None and not warmup and
+                         sum(self._ms(r) for r in reqs) < self.graph_ms)
+            obs_ready = None
+            if any(r.kind == "track" for r in reqs):
+                # each track request's own observation: on the copy stream
+                # while the render stages run (directly launched batches),
+                # before the replay (captured ones)
+                cs = ctx.stream if use_graph or warmup else ctx.copy_stream
+                cs.wait_stream(ctx.stream)
+                with torch.cuda.stream(cs):
+                    for it, r in zip(items, reqs):
+                        if r.kind == "track":
+                            it.obs.copy_(r.obs, non_blocking=True)
+                if cs is ctx.copy_stream:
+                    obs_ready = torch.cuda.Event()
+                    obs_ready.record(cs)
             ctx.runner.set(self.sections, items, **TRACK_WEIGHTS)
             if self.graphs and ctx.graph is None and warmup:
                 ctx.runner.launch(stream=ctx.stream)      # eager once, then capture
@@ -278,10 +298,10 @@ class BatchServer:
                     ctx.runner.launch(stream=ctx.stream)
                 ctx.graph = g
                 ctx.runner.set(self.sections, items, **TRACK_WEIGHTS)
-            if ctx.graph is not None:
+            if use_graph:
                 ctx.graph.replay()
             else:
-                ctx.runner.launch(stream=ctx.stream)
+                ctx.runner.launch(stream=ctx.stream, obs_ready=obs_ready)
             n = len(reqs)
             if any(r.kind == "track" for r in reqs):
                 ctx.results_host[:n].copy_(ctx.results[:n], non_blocking=True)

@@ -304,7 +304,12 @@ def test_multiroom_large_scene_finite_differences():
     the oracle along the GPU's decisions (given the Gaussians that can reach
     the crop), and central differences of the GPU forward in the opacity of
     64 sampled Gaussians against the oracle's opacity gradient: the GPU's
-    render at that scale changes as the oracle's gradient says."""
+    render at that scale changes as the oracle's gradient says.  The
+    difference quotients take the upstream gradient on the pixels whose
+    termination decision is more than 5% from its threshold (there a step of
+    2e-3 in o moves the transmittance by under 2% and no walk stops
+    elsewhere; o = 0.9 puts the 1/255 cut outside the 3-sigma disc, so no
+    inclusion decision moves either)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
@@ -331,24 +336,34 @@ def test_multiroom_large_scene_finite_differences():
     dtw, _ = R.backward(full_gR, None, None, pose_grad=True)
     torch.cuda.synchronize()
     G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist", noise=want["twist_noise"])
-    # 64 Gaussians with the largest opacity terms (o = 0.9 everywhere: the
-    # 1/255 cut lies outside the 3-sigma disc, so a small change of o moves
-    # no inclusion decision)
+    # 64 Gaussians with the largest opacity terms under the upstream gradient
+    # of the pixels far from their termination threshold
+    far = oracle.render(list(subs), target, Kc, cw, ch)["margin_T"] > 0.05
+    assert far.sum() > 500
+    gF = (gR * far).astype(np.float32)
+    wantF = oracle.backward_lists(list(subs), target, Kc, cw, ch, ids, cnt, g_rgb=gF)
+    # (a Gaussian's opacity gradient sums terms of both signs over its
+    # pixels and the pixels behind it; the FP32 difference quotient resolves
+    # the sum where it does not cancel to far below its terms' magnitude,
+    # so the sample is the Gaussians with the largest gradients among those
+    # whose gradient keeps a tenth of that magnitude)
     cand = []
-    for s, (k, a) in enumerate(zip(keeps, want["abs_opacity"])):
+    for s, (k, a, v) in enumerate(zip(keeps, wantF["abs_opacity"], wantF["opacity"])):
         full = np.flatnonzero(k)
-        for j in np.argsort(-a)[:64]:
-            cand.append((a[j], s, int(full[j]), float(want["opacity"][s][j])))
+        ok_ = np.abs(v) > 0.1 * a
+        for j in np.flatnonzero(ok_)[np.argsort(-np.abs(v[ok_]))][:64]:
+            cand.append((abs(v[j]), s, int(full[j]), float(v[j]), float(a[j])))
     cand.sort(reverse=True)
-    g_crop = torch.from_numpy(gR.astype(np.float64)).to(dev)
+    assert len(cand) >= 64
+    g_crop = torch.from_numpy(gF.astype(np.float64)).to(dev)
 
     def loss():
         out, _, _ = R.render(dsecs, pose, K.astuple(), K.W, K.H)
         return float((out[:, sl[0], sl[1]].double() * g_crop).sum())
 
-    e = 1e-3
+    e = 2e-3
     ok = 0
-    for _, s, li, g_want in cand[:64]:
+    for _, s, li, g_want, mag in cand[:64]:
         o = dsecs[s].opacity
         v = float(o[li])
         o[li] = v + e
@@ -357,7 +372,6 @@ def test_multiroom_large_scene_finite_differences():
         lm = loss()
         o[li] = v
         fd = (lp - lm) / (2 * e)
-        ok += abs(fd - g_want) <= 1e-2 * abs(g_want) + 1e-4
-    # a pixel whose walk stops within the step of its termination threshold
-    # jumps; allow a few of the 64
+        ok += abs(fd - g_want) <= 1e-2 * abs(g_want) + 1e-3 * mag
+    # allow a few of the 64 for a decision the oracle's margins misjudge
     assert ok >= 60, ok

@@ -204,8 +204,12 @@ def test_adam_init_from_storage(dev, prec):
                       opacity=t(opa), radius=t(rad), scale=t(sc), rot=t(qt))
     stored = lambda x: x.float().cpu().numpy().astype(np.float64)
     th, m, v, st = api.adam_init(sec)
-    o = np.clip(stored(sec.opacity), 1e-4, 1 - 1e-4)
-    want = np.stack([*stored(sec.colour).T, np.log(o / (1 - o)), np.log(stored(sec.radius))])
+    # the clamp bounds and 1 - o in FP32, as the kernel forms them (1 - o is
+    # exact there, Sterbenz), the rest in FP64
+    o32 = np.clip(sec.opacity.float().cpu().numpy(), np.float32(1e-4), np.float32(1 - 1e-4))
+    o = o32.astype(np.float64)
+    want = np.stack([*stored(sec.colour).T, np.log(o / (np.float32(1) - o32)),
+                     np.log(stored(sec.radius))])
     np.testing.assert_allclose(th.cpu().numpy(), want, rtol=2e-6, atol=2e-6)
     assert not m.any() and not v.any() and not st.any()
     th, m, v, st = api.adam_init(sec, shape=True)
