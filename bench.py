@@ -820,12 +820,21 @@ def main():
     avg_s = tot_ms / n_l / 1e3
     mp = peaks()
     clocks = clk.summary()
+    # unit counts from the device, the clock the ALU and issue peaks assume:
+    # the maximum SM clock (MEASURED_PEAKS.json, else nvidia-smi's sample),
+    # reported next to the median sampled during the timed region
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = float(mp.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    peak_clock = {"sm_count": n_sm, "sm_mhz_assumed": f_max / 1e6,
+                  "sm_mhz_sampled_median": clocks.get("sm_mhz")}
     if dom in ("k_composite_fwd", "k_composite_bwd"):
         flops = pairs_fwd * (FP32_FLOPS_PER_PAIR_FWD if dom == "k_composite_fwd"
                              else FP32_FLOPS_PER_PAIR_BWD)
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        peak = n_sm * 128 * 2 * f_max / 1e12
         roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "unit": "TFLOP/s",
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {f_max / 1e9:.2f} GHz "
+                               "(nominal unit counts, measured maximum clock)",
                 "algorithmic": f"{pairs_fwd} included pairs x "
                                f"{flops // max(pairs_fwd, 1)} FP32 flops"}
     else:
@@ -837,6 +846,7 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if mp else "fallback 6.8 TB/s",
                 "algorithmic": f"{byts} bytes per launch"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["clock"] = peak_clock
     roof["kernel"] = dom
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["traffic"] = traffic_for(dom)
@@ -844,7 +854,7 @@ def main():
     # instructions against 152 SMs x 4 schedulers x one instruction per clock
     n_wi = capture_for(dom, "warp_instructions_per_launch")
     if n_wi is not None:
-        issue_peak = 152 * 4 * 2.07e9
+        issue_peak = n_sm * 4 * f_max
         roof["issue"] = {"warp_instructions": n_wi, "achieved": n_wi / avg_s / 1e12,
                          "peak": issue_peak / 1e12, "unit": "T warp-instructions/s",
                          "frac": n_wi / avg_s / issue_peak}

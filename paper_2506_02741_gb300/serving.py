@@ -197,7 +197,8 @@ class BatchServer:
 
     def _measure_times(self, ctx, requests):
         """GPU time of a one-item batch of every (section, bucket, kind) the
-        requests use (CUDA events, second of two runs)."""
+        requests use, at the pose of the first such request (CUDA events,
+        second of two runs)."""
         seen = {}
         for r in requests:
             seen.setdefault((r.section, r.bucket, r.kind), r)
@@ -206,6 +207,7 @@ class BatchServer:
             r = dataclasses.replace(r, obs=self._dummy_obs(r))
             items, _ = self._items(ctx, [r])
             with torch.cuda.stream(ctx.stream):
+                ctx.poses[0].copy_(api.pose12(r.pose, self.device))
                 for _ in range(2):
                     if r.kind == "track":
                         items[0].obs.copy_(r.obs, non_blocking=True)
@@ -214,6 +216,7 @@ class BatchServer:
                     ctx.runner.launch(stream=ctx.stream)
                     e1.record(ctx.stream)
                 e1.synchronize()
+            ctx.runner.status(ctx.stream)
             self.ms_est[key] = e0.elapsed_time(e1)
 
     def warm(self, requests):
