@@ -36,7 +36,9 @@ one-request-at-a-time form.
 from __future__ import annotations
 
 import collections
+import contextlib
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -63,6 +65,21 @@ class Request:
 
 def _pad(x: int) -> int:
     return (x + 255) // 256 * 256
+
+
+@contextlib.contextmanager
+def _no_gc():
+    """The serving loops hold Python's cyclic garbage collector off while they
+    run (a collection pauses the loop for milliseconds, which shows up as
+    latency of whatever request is due then); it runs once afterwards."""
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+        gc.collect()
 
 
 # ---------------------------------------------------------------------------
@@ -96,6 +113,7 @@ class _BatchCtx:
         self.poses = torch.zeros(n, 12, dtype=torch.float64, device=dev)
         self.results = torch.zeros(n, 19, dtype=torch.float64, device=dev)
         self.poses_host = torch.zeros(n, 12, dtype=torch.float64).pin_memory()
+        self.poses_np = self.poses_host.numpy()     # the same pinned memory
         self.results_host = torch.zeros(n, 19, dtype=torch.float64).pin_memory()
         self.rgb_host = torch.empty(3 * P, dtype=torch.float32).pin_memory()
         self.graph = None
@@ -273,8 +291,10 @@ class BatchServer:
         items, slices = self._items(ctx, reqs)
         ctx.stream = ctx.streams[min(level, len(ctx.streams) - 1)]
         with torch.cuda.stream(ctx.stream):
-            for i, r in enumerate(reqs):
-                ctx.poses_host[i] = api.pose12(r.pose, "cpu")
+            n = len(reqs)
+            p = np.stack([np.asarray(r.pose, np.float64).reshape(3, 4) for r in reqs])
+            ctx.poses_np[:n, :9] = p[:, :, :3].reshape(n, 9)
+            ctx.poses_np[:n, 9:] = p[:, :, 3]
             ctx.poses.copy_(ctx.poses_host, non_blocking=True)
             use_graph = (ctx.graph is not None and not warmup and
                          sum(self._ms(r) for r in reqs) < self.graph_ms)
@@ -345,6 +365,10 @@ class BatchServer:
     def run(self, requests, timeout: float = 600.0):
         """Serve ``requests`` (arrival times in seconds from now).  Returns
         them with ``done`` (and ``result``) set."""
+        with _no_gc():
+            return self._run(requests, timeout)
+
+    def _run(self, requests, timeout):
         for r in requests:
             n = self._need(r)
             if any(n[k] > self.ctxs[0].cap[k] for k in ("gaussians", "pixels", "tiles", "views",
@@ -529,6 +553,10 @@ class SlotServer:
     def run(self, requests, timeout: float = 600.0):
         """Serve ``requests`` (sorted by arrival time, in seconds from now).
         Returns the requests with ``done`` set and their results."""
+        with _no_gc():
+            return self._run(requests, timeout)
+
+    def _run(self, requests, timeout):
         queue = collections.deque()
         pending = list(sorted(requests, key=lambda r: r.arrival))
         nxt = 0

@@ -6,6 +6,8 @@ so that both sides read identical values.
 
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import torch
 
@@ -39,6 +41,22 @@ TAU_T = 2e-4
 
 # Per-case decision statistics of the parity tests (printed with -s).
 STATS = []
+
+
+def _case() -> str:
+    return os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+
+
+def _report(kind, name, ratio, strict=None, rel=None):
+    """Prints the achieved error of one compared tensor as a fraction of its
+    bound (ratio <= 1 passes); strict: the same against the plain per-element
+    bound tol * max(|ref|, floor) without the magnitude and noise terms."""
+    rec = dict(case=_case(), tensor=name, ratio=round(float(ratio), 4))
+    if strict is not None:
+        rec["strict_ratio"] = round(float(strict), 4)
+    if rel is not None:
+        rec["rel_l2"] = float(f"{rel:.3g}")
+    print(kind, rec)
 
 
 def gpu_lists(R, W, H, box=None, id_map=None):
@@ -104,7 +122,9 @@ def assert_forward_close(out, ref, mask=None, tol=1e-5, depth_scale=4.0):
         bound = tol * np.maximum(np.abs(r), s)
         bad = (np.abs(g - r) > bound) & m
         err[name] = float(np.max(np.abs(g - r)[m])) if m.any() else 0.0
-        assert not bad.any(), (name, int(bad.sum()), float(np.max((np.abs(g - r) / bound)[m])))
+        ratio = float(np.max((np.abs(g - r) / bound)[m])) if m.any() else 0.0
+        _report("PARITY_ERROR", name, ratio)
+        assert not bad.any(), (name, int(bad.sum()), ratio)
     return err
 
 
@@ -137,15 +157,19 @@ def assert_grad_close(g, ref, tol=1e-4, name="", abs_ref=None, noise=None):
     Gaussians of alpha ~0.9)."""
     g = np.asarray(g, np.float64).ravel()
     ref = np.asarray(ref, np.float64).ravel()
-    assert rel_l2(g, ref) <= tol, (name, rel_l2(g, ref))
     floor = 1e-3 * np.max(np.abs(ref)) if ref.size else 0.0
     bound = tol * np.maximum(np.abs(ref), floor)
+    diff = np.abs(g - ref)
+    strict = float(np.max(diff / np.maximum(bound, 1e-300))) if ref.size else 0.0
+    assert rel_l2(g, ref) <= tol, (name, rel_l2(g, ref))
     if abs_ref is not None:
         bound = bound + tol * np.asarray(abs_ref, np.float64).ravel()
     if noise is not None:
         bound = bound + POSE_NOISE * np.asarray(noise, np.float64).ravel()
-    bad = np.abs(g - ref) > bound
-    assert not bad.any(), (name, int(bad.sum()), float(np.max(np.abs(g - ref) / bound)))
+    bad = diff > bound
+    ratio = float(np.max(diff / np.maximum(bound, 1e-300))) if ref.size else 0.0
+    _report("PARITY_ERROR", name, ratio, strict, rel_l2(g, ref))
+    assert not bad.any(), (name, int(bad.sum()), ratio)
 
 
 def decisions(dsecs, pose12, K, W, H, out=None, box=None, id_map=None, cap=None):
