@@ -505,15 +505,24 @@ def serving_workload(dev, seed: int = 3):
     return sec16, sec32, poses, res, frames
 
 
+# the served form's smallest batch time budget (the budget follows the queue
+# between this and the server's batch_ms)
+SERVE_BATCH_MS_MIN = 1.0
+
+
 def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
     """Serving workload (16 resident sections 0.3 M - 10 M Gaussians,
     Poisson requests 70% track / 30% render over 320x240 ... 1920x1080, every
     track request uploading its own observation).  Served form: FP16
-    attributes, continuous batching with one persistent launch per stage,
-    two batch contexts, CUDA graphs.  Baseline: FP32 attributes, one request
-    at a time, eager.  Saturated throughput of each pattern alone (FP16,
-    graphs, batching) and of both forms; p50/p99 at 50/80/95% of the served
-    form's saturated rate, n_req requests per load point."""
+    attributes, continuous batching with one launch per stage over the
+    batch, three batch contexts, a lone request on the context's
+    single-request renderer, CUDA graphs.  Baseline: FP32 attributes, one
+    request at a time, eager.  Saturated throughput of each pattern alone
+    (FP16, graphs, batching) and of both forms; p50/p99 at 50/80/95% of the
+    served form's saturated rate, n_req requests per load point and form,
+    measured in two halves in the order baseline, served, served, baseline
+    (so that a drift of the GPU over the run weighs on both forms alike),
+    SM clocks sampled meanwhile."""
     import torch
 
     from paper_2506_02741_gb300 import serving
@@ -529,10 +538,10 @@ def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
                                                                   keep_results=False),
         "fp16_only": lambda: serving.SlotServer(sec16, res, 1, graphs=False, keep_results=False),
         "graphs_only": lambda: serving.SlotServer(sec32, res, 1, graphs=True, keep_results=False),
-        "batching_only": lambda: serving.BatchServer(sec32, res, graphs=False,
+        "batching_only": lambda: serving.BatchServer(sec32, res, graphs=False, solo=False,
                                                      keep_results=False),
-        "served_fp16_batched_graphs": lambda: serving.BatchServer(sec16, res, graphs=True,
-                                                                  keep_results=False),
+        "served_fp16_batched_graphs": lambda: serving.BatchServer(
+            sec16, res, graphs=True, keep_results=False, batch_ms_min=SERVE_BATCH_MS_MIN),
     }
     warm = req(400, 1e9, 7)
     servers, sat = {}, {}
@@ -546,16 +555,31 @@ def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
     out["saturated"] = sat
     rate_sat = sat["served_fp16_batched_graphs"]["req_s"]
     loads = {}
+    bs = servers["served_fp16_batched_graphs"]
+    half = n_req // 2
+    order = (("baseline_fp32_one_at_a_time", 4), ("served_fp16_batched_graphs", 4),
+             ("served_fp16_batched_graphs", 5), ("baseline_fp32_one_at_a_time", 5))
     for frac in (0.5, 0.8, 0.95):
         rate = frac * rate_sat
-        point = {"rate_req_s": rate}
-        for name in ("served_fp16_batched_graphs", "baseline_fp32_one_at_a_time"):
-            sm = serving.latency_summary(servers[name].run(req(n_req, rate, 4), timeout=1800.0),
-                                         res)
-            point[name] = {k: sm[k] for k in ("p50_ms", "p99_ms", "mean_ms", "mpix_s", "req_s")}
+        point = {"rate_req_s": rate, "requests_per_form": 2 * half}
+        runs = {name: [] for name, _ in order}
+        solo0, batched0 = bs.n_solo, bs.n_batched
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for name, seed in order:
+                done = servers[name].run(req(half, rate, seed), timeout=1800.0)
+                runs[name].append(done)
+        for name, parts in runs.items():
+            lat = np.concatenate([[(r.done - r.arrival) * 1e3 for r in d] for d in parts])
+            sums = [serving.latency_summary(d, res) for d in parts]
+            point[name] = {"p50_ms": float(np.percentile(lat, 50)),
+                           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                           "mpix_s": float(np.mean([x["mpix_s"] for x in sums])),
+                           "req_s": float(np.mean([x["req_s"] for x in sums]))}
+        point["served_fp16_batched_graphs"]["alone_fraction"] = (
+            (bs.n_solo - solo0) / max(1, bs.n_solo - solo0 + bs.n_batched - batched0))
+        point["clocks"] = clk.summary()
         loads[f"{int(frac * 100)}pct_of_served_saturation"] = point
     out["load_points"] = loads
-    bs = servers["served_fp16_batched_graphs"]
     out["batch_contexts"] = [c.cap for c in bs.ctxs]
     out["batch_splits_on_instance_overflow"] = bs.splits
     # matched accuracy: FP16 vs FP32 colour of one render per section at

@@ -194,6 +194,7 @@ __device__ __forceinline__ void fwd_body(
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dd = 0.f, ss = 0.f;
     uint32_t last = 0, nadd = 0;
+    int lastj = -1;   // staging slot of the last Gaussian added in this walk
     bool done = !inside;
     // Two-stage prefetch: the ids of batch r + 2 and the records of batch
     // r + 1 are in flight while batch r is composited.
@@ -260,7 +261,7 @@ __device__ __forceinline__ void fwd_body(
         ss = __fadd_rn(ss, w);
         if (nadd < cap) mylist[nadd] = make_uint2(ids[j], __float_as_uint(T));
         T = Tn;
-        last = lidx[j] + 1u;
+        lastj = j;   // its list index is read once the walk is through
         ++nadd;
         return true;
     };
@@ -278,6 +279,10 @@ __device__ __forceinline__ void fwd_body(
             const float Ga = exp2_approx(ta), Gb = exp2_approx(tb);
             if (ta >= ka.z && !add(ja, Ga, ka, cand_new)) continue;
             if (two && tb >= kb.z) add(jb, Gb, kb, cand_new);
+        }
+        if (lastj >= 0) {   // both staging halves are intact until the next batch
+            last = lidx[lastj] + 1u;
+            lastj = -1;
         }
     };
     for (;;) {

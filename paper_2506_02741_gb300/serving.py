@@ -25,7 +25,10 @@ up; the contexts' batches overlap on the device.  The capacities come from
 the free device memory at start-up (admission by free HBM): a request is
 deferred until a context has room and refused only if it can never fit one.
 A batch that exceeds the reserved tile instances on the device (found after
-it ran) raises the estimates and is queued again.
+it ran) raises the estimates and is queued again.  A request admitted alone
+(the queue held nothing else) runs on the context's single-request renderer
+instead, replaying a graph captured per (section, bucket, kind): at low load
+most requests go that way and skip the batched launches' work-item table.
 
 SlotServer runs requests on ``n_slots`` independent render contexts (one
 request per slot and stream), optionally replaying a CUDA graph per
@@ -118,8 +121,11 @@ class _BatchCtx:
         self.rgb_host = torch.empty(3 * P, dtype=torch.float32).pin_memory()
         self.graph = None
         self.reqs: list[Request] = []
-        self.slices: list[tuple] = []
+        self.slices: list[tuple] | None = []
         self.event = None
+        self.mode = "batch"
+        self.solo = None     # single-request renderer (_Slot), if the server keeps them
+        self.work = None
 
     def busy(self) -> bool:
         return bool(self.reqs)
@@ -128,7 +134,8 @@ class _BatchCtx:
 class BatchServer:
     def __init__(self, sections, resolutions, n_contexts: int = 3, graphs: bool = True,
                  memory_budget: int | None = None, list_cap: int = 256, batch_ms: float = 4.0,
-                 graph_ms: float = 1.0, keep_results: bool = True, device="cuda"):
+                 graph_ms: float = 1.0, keep_results: bool = True, solo: bool = True,
+                 batch_ms_min: float | None = None, device="cuda"):
         """sections: list of api.Section (resident, spheres); resolutions:
         list of (W, H) buckets.  The contexts share memory_budget (default:
         70% of the free device memory) in equal parts.  A batch takes the
@@ -139,7 +146,14 @@ class BatchServer:
         (persistent grids: launch overhead matters there); a longer one is
         launched directly with grids sized to its work, so that the stages of
         concurrent batches yield SMs block by block and the priority of the
-        earlier batch holds."""
+        earlier batch holds.  With ``solo`` every context also keeps a
+        single-request renderer with a captured graph per (section, bucket,
+        kind): a request admitted alone runs there (the single-request
+        kernels, no work-item table), a batch of two or more through the
+        batched launches; the single-request renderers' memory counts against
+        memory_budget.  With ``batch_ms_min`` the time budget of a batch
+        follows the queue: its estimated GPU time divided among the contexts,
+        clamped to [batch_ms_min, batch_ms]."""
         from . import synthetic as syn
         self.device = torch.device(device)
         self.sections = sections
@@ -148,11 +162,17 @@ class BatchServer:
         self.graphs = graphs
         self.list_cap = int(list_cap)
         self.batch_ms = float(batch_ms)
+        self.batch_ms_min = None if batch_ms_min is None else float(batch_ms_min)
         self.graph_ms = float(graph_ms)
         self.keep_results = keep_results
         free, _ = torch.cuda.mem_get_info(self.device)
+        self._budget_arg = memory_budget
         self.memory_budget = int(memory_budget if memory_budget is not None else 0.7 * free)
         self.n_contexts = int(n_contexts)
+        self.solo = bool(solo)
+        self.solo_off: set = set()     # (section, bucket, kind) that overflowed a solo workspace
+        self.n_solo = 0                # requests served alone / in batched launches
+        self.n_batched = 0
         self.ctxs: list[_BatchCtx] = []
         # tile instances per (section, bucket): measured at warm-up, raised
         # when a batch overflows; GPU milliseconds per (section, bucket, kind)
@@ -246,14 +266,44 @@ class BatchServer:
         self._measure_times(probe, requests)
         del probe
         torch.cuda.synchronize()
+        solos = self._make_solos(requests) if self.solo else [None] * self.n_contexts
         cap = self._capacity(requests)
         self.ctxs = [_BatchCtx(self, cap) for _ in range(self.n_contexts)]
+        for ctx, slot in zip(self.ctxs, solos):
+            ctx.solo = slot
         for ctx in self.ctxs:
             r = requests[0]
             self._launch(ctx, [dataclasses.replace(r, obs=self._dummy_obs(r))], warmup=True)
             ctx.event.synchronize()
             ctx.reqs = []
         torch.cuda.synchronize()
+
+    def _make_solos(self, requests):
+        """One single-request renderer per context, its workspace reserved for
+        the largest request and a graph captured for every (section, bucket,
+        kind) of ``requests``; the memory it takes leaves the contexts'
+        budget (the default budget is taken from the free memory after)."""
+        free0, _ = torch.cuda.mem_get_info(self.device)
+        n_max = max(self.sections[r.section].n for r in requests)
+        i_max = max(self._need(r)["instances"] for r in requests)
+        seen = {}
+        for r in requests:
+            seen.setdefault((r.section, r.bucket, r.kind), r)
+        solos = []
+        for i in range(self.n_contexts):
+            slot = _Slot(self, i)
+            slot.reserve_for(self, n_max, i_max)
+            for r in seen.values():
+                slot.work_for(self, dataclasses.replace(r, obs=self._dummy_obs(r)), slot.stream,
+                              self.graphs)
+            solos.append(slot)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info(self.device)
+        if self._budget_arg is None:
+            self.memory_budget = int(0.7 * free1)
+        else:
+            self.memory_budget = int(self._budget_arg) - max(0, free0 - free1)
+        return solos
 
     def _need_max(self, requests) -> dict:
         needs = [self._need(r) for r in requests]
@@ -266,8 +316,8 @@ class BatchServer:
         return r.obs if r.obs is not None else torch.zeros(4, H, W).pin_memory()
 
     # -- batches -------------------------------------------------------------
-    def _fits(self, ctx, used, need, ms) -> bool:
-        return (used["items"] < ctx.max_items and used["ms"] + ms <= self.batch_ms and
+    def _fits(self, ctx, used, need, ms, budget) -> bool:
+        return (used["items"] < ctx.max_items and used["ms"] + ms <= budget and
                 all(used[k] + need[k] <= ctx.cap[k] for k in ctx.cap))
 
     def _items(self, ctx, reqs):
@@ -334,9 +384,48 @@ class BatchServer:
                                                                 non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(ctx.stream)
-        ctx.reqs, ctx.slices, ctx.event = list(reqs), slices, ev
+        ctx.reqs, ctx.slices, ctx.event, ctx.mode = list(reqs), slices, ev, "batch"
+
+    def _launch_solo(self, ctx, r, level=0):
+        """A lone request on the context's single-request renderer (its
+        graph for the request's section, bucket and kind), on the stream of
+        the given priority level."""
+        ctx.stream = ctx.streams[min(level, len(ctx.streams) - 1)]
+        slot = ctx.solo
+        work = slot.work_for(self, r, ctx.stream, self.graphs)
+        with torch.cuda.stream(ctx.stream):
+            slot.stage_pose(r.pose, work)
+            if r.kind == "track":
+                work.obs.copy_(r.obs, non_blocking=True)
+            if work.graph is not None:
+                work.graph.replay()
+            else:
+                work.run()
+            work.host.copy_(work.rgb if r.kind == "render" else work.out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(ctx.stream)
+        ctx.reqs, ctx.slices, ctx.event, ctx.mode, ctx.work = [r], None, ev, "solo", work
 
     def _finish(self, ctx, now, finished, queue):
+        if ctx.mode == "solo":
+            r = ctx.reqs[0]
+            try:
+                ctx.solo.renderer.status(ctx.stream)
+            except L.VTError as e:
+                if e.status != L.VT_ERR_CAPACITY:
+                    raise
+                # beyond the solo workspace: this kind goes through batches
+                self.solo_off.add((r.section, r.bucket, r.kind))
+                queue.appendleft(r)
+                ctx.reqs = []
+                return
+            r.done = now
+            if self.keep_results:
+                r.result = ctx.work.host.clone()
+            finished.append(r)
+            self.n_solo += 1
+            ctx.reqs = []
+            return
         try:
             ctx.runner.status(ctx.stream)
         except L.VTError as e:
@@ -360,6 +449,7 @@ class BatchServer:
                 else:
                     r.result = ctx.results_host[i].clone()
             finished.append(r)
+        self.n_batched += len(ctx.reqs)
         ctx.reqs = []
 
     def run(self, requests, timeout: float = 600.0):
@@ -393,20 +483,29 @@ class BatchServer:
                     continue
                 used = dict(gaussians=0, pixels=0, tiles=0, views=0, table_rows=0, instances=0,
                             items=0, ms=0.0)
+                budget = self.batch_ms
+                if self.batch_ms_min is not None:
+                    queued = sum(self._ms(q) for q in queue)
+                    budget = min(self.batch_ms, max(self.batch_ms_min, queued / self.n_contexts))
                 take = [queue.popleft()]   # the head always goes (it fits an empty context)
                 for k, v in self._need(take[0]).items():
                     used[k] += v
                 used["items"], used["ms"] = 1, self._ms(take[0])
                 while queue:
                     need, ms = self._need(queue[0]), self._ms(queue[0])
-                    if not self._fits(ctx, used, need, ms):
+                    if not self._fits(ctx, used, need, ms, budget):
                         break
                     for k in need:
                         used[k] += need[k]
                     used["items"] += 1
                     used["ms"] += ms
                     take.append(queue.popleft())
-                self._launch(ctx, take, level=sum(c.busy() for c in self.ctxs))
+                level = sum(c.busy() for c in self.ctxs)
+                if (len(take) == 1 and ctx.solo is not None and
+                        (take[0].section, take[0].bucket, take[0].kind) not in self.solo_off):
+                    self._launch_solo(ctx, take[0], level)
+                else:
+                    self._launch(ctx, take, level=level)
             if all(c.busy() for c in self.ctxs) or (not queue and nxt < len(pending)):
                 time.sleep(20e-6)
         return finished
@@ -417,28 +516,20 @@ class BatchServer:
 
 
 class _Work:
-    """Fixed buffers and (optionally) a captured graph for one
-    (slot, section, bucket, kind)."""
+    """A captured graph (optional) for one (slot, section, bucket, kind); the
+    buffers are the slot's for the (bucket, kind), shared by every section
+    (a slot runs one request at a time)."""
 
     def __init__(self, slot, server, section, bucket, kind):
-        dev = server.device
         W, H = server.resolutions[bucket]
         self.slot, self.kind, self.W, self.H = slot, kind, W, H
         self.K = server.intrinsics[bucket]
         self.sec = server.sections[section]
-        self.pose = torch.zeros(12, dtype=torch.float64, device=dev)
-        self.rgb = torch.empty(3, H, W, device=dev)
-        self.depth = torch.empty(H, W, device=dev)
-        self.sil = torch.empty(H, W, device=dev)
-        self.d_twist = torch.zeros(6, dtype=torch.float64, device=dev)
-        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
-        self.g_rgb = torch.zeros(3, H, W, device=dev)
-        self.g_depth = torch.zeros(H, W, device=dev)
-        self.obs = torch.zeros(4, H, W, device=dev)
-        self.out = torch.zeros(7, dtype=torch.float64, device=dev)   # loss, twist
-        self.host = torch.empty((3, H, W) if kind == "render" else (7,),
-                                dtype=torch.float32 if kind == "render" else torch.float64
-                                ).pin_memory()
+        b = slot.buffers(server.device, bucket, W, H, kind)
+        self.pose, self.rgb, self.depth, self.sil = b["pose"], b["rgb"], b["depth"], b["sil"]
+        self.d_twist, self.d_mat, self.loss = b["d_twist"], b["d_mat"], b["loss"]
+        self.g_rgb, self.g_depth, self.obs = b["g_rgb"], b["g_depth"], b["obs"]
+        self.out, self.host = b["out"], b["host"]
         self.graph = None
 
     def run(self):
@@ -449,9 +540,13 @@ class _Work:
                         sil_min=0.99, rgb_needs_depth=True, d_rgb=self.g_rgb,
                         d_depth=self.g_depth, loss=self.loss)
             self.d_twist.zero_()
-            R.backward(self.g_rgb, self.g_depth, None, pose_grad=True, d_twist=self.d_twist)
+            self.d_mat.zero_()
+            R.backward(self.g_rgb, self.g_depth, None, pose_grad=True, d_twist=self.d_twist,
+                       d_mat=self.d_mat)
+            # the batched form's result layout: loss, dL/dtwist, dL/d[R|t]
             self.out[:1].copy_(self.loss)
-            self.out[1:].copy_(self.d_twist)
+            self.out[1:7].copy_(self.d_twist)
+            self.out[7:].copy_(self.d_mat)
 
 
 class _Slot:
@@ -460,10 +555,71 @@ class _Slot:
         self.stream = torch.cuda.Stream(device=server.device)
         self.renderer = api.Renderer()
         self.works = {}
+        self.bufs = {}
         self.request = None
         self.event = None
         self.reserved = (0, 0, 0)    # Gaussians, pixels, instances
         self.work = None
+        self.pose_host = torch.zeros(12, dtype=torch.float64).pin_memory()
+        self.pose_np = self.pose_host.numpy()
+
+    def buffers(self, dev, bucket, W, H, kind) -> dict:
+        key = (bucket, kind)
+        if key not in self.bufs:
+            f = lambda *shape: torch.zeros(*shape, device=dev)
+            d = lambda n: torch.zeros(n, dtype=torch.float64, device=dev)
+            b = dict(pose=d(12), rgb=f(3, H, W), depth=f(H, W), sil=f(H, W))
+            if kind == "track":
+                b.update(d_twist=d(6), d_mat=d(12), loss=d(1), g_rgb=f(3, H, W),
+                         g_depth=f(H, W), obs=f(4, H, W), out=d(19),
+                         host=torch.empty(19, dtype=torch.float64).pin_memory())
+            else:
+                b.update(d_twist=None, d_mat=None, loss=None, g_rgb=None, g_depth=None,
+                         obs=None, out=None, host=torch.empty(3, H, W).pin_memory())
+            self.bufs[key] = b
+        return self.bufs[key]
+
+    def stage_pose(self, pose, work):
+        """Copies a (3, 4) pose into the work's device pose buffer through the
+        slot's pinned staging buffer (current stream)."""
+        p = np.asarray(pose, np.float64).reshape(3, 4)
+        self.pose_np[:9] = p[:, :3].reshape(9)
+        self.pose_np[9:] = p[:, 3]
+        work.pose.copy_(self.pose_host, non_blocking=True)
+
+    def reserve_for(self, server, n_max, i_max):
+        """Reserves the renderer's workspace for the largest request (captured
+        graphs hold its addresses, so it must not move afterwards) and
+        renders once at the largest size, which allocates the per-pixel
+        lists."""
+        b_max = max(range(len(server.resolutions)),
+                    key=lambda b: server.resolutions[b][0] * server.resolutions[b][1])
+        W, H = server.resolutions[b_max]
+        with torch.cuda.stream(self.stream):
+            self.renderer.reserve(n_max, W, H, i_max)
+            work = _Work(self, server, max(range(len(server.sections)),
+                                           key=lambda s: server.sections[s].n), b_max, "render")
+            work.run()
+        self.reserved = (n_max, W * H, i_max)
+
+    def work_for(self, server, req, stream, graphs: bool):
+        """The slot's work for the request's (section, bucket, kind), created
+        (and its graph captured on ``stream``) on first use."""
+        key = (req.section, req.bucket, req.kind)
+        work = self.works.get(key)
+        if work is None:
+            work = _Work(self, server, req.section, req.bucket, req.kind)
+            self.works[key] = work
+            if graphs:
+                with torch.cuda.stream(stream):
+                    self.stage_pose(req.pose, work)
+                    work.run()                      # warm-up outside the capture
+                    stream.synchronize()
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=stream):
+                        work.run()
+                    work.graph = g
+        return work
 
 
 class SlotServer:
@@ -494,37 +650,18 @@ class SlotServer:
     def _size_slots(self, requests):
         n_max = max(self._need(r)[0] for r in requests)
         i_max = max(self._need(r)[1] for r in requests)
-        b_max = max(range(len(self.resolutions)),
-                    key=lambda b: self.resolutions[b][0] * self.resolutions[b][1])
-        W, H = self.resolutions[b_max]
+        W, H = max(self.resolutions, key=lambda wh: wh[0] * wh[1])
         per_slot = api.L.lib().vt_workspace_bytes(n_max, W, H, i_max) + 8 * 256 * W * H
         usable = max(1, min(len(self.slots), self.memory_budget // max(per_slot, 1)))
         self.slots = self.slots[:usable]
         for slot in self.slots:
-            with torch.cuda.stream(slot.stream):
-                slot.renderer.reserve(n_max, W, H, i_max)
-                # a render at the largest size allocates the per-pixel lists
-                work = _Work(slot, self, max(range(len(self.sections)),
-                                             key=lambda s: self.sections[s].n), b_max, "render")
-                work.run()
-            slot.reserved = (n_max, W * H, i_max)
+            slot.reserve_for(self, n_max, i_max)
         torch.cuda.synchronize()
 
     def _launch(self, slot, req):
-        key = (req.section, req.bucket, req.kind)
-        work = slot.works.get(key)
+        work = slot.work_for(self, req, slot.stream, self.graphs)
         with torch.cuda.stream(slot.stream):
-            if work is None:
-                work = _Work(slot, self, req.section, req.bucket, req.kind)
-                slot.works[key] = work
-                if self.graphs:
-                    work.pose.copy_(api.pose12(req.pose, self.device))
-                    work.run()                      # warm-up outside the capture
-                    g = torch.cuda.CUDAGraph()
-                    with torch.cuda.graph(g, stream=slot.stream):
-                        work.run()
-                    work.graph = g
-            work.pose.copy_(api.pose12(req.pose, self.device), non_blocking=True)
+            slot.stage_pose(req.pose, work)
             if req.kind == "track":           # the request's own observation
                 work.obs.copy_(req.obs, non_blocking=True)
             if work.graph is not None:

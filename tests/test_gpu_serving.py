@@ -61,18 +61,57 @@ def _solo(r):
 
 @pytest.mark.parametrize("graphs", [True, False])
 def test_batched_alone_equals_in_mix(dev, setup, graphs):
+    """Batched launches only: a request gives the same bits as a one-item
+    batch as inside a mix."""
     reqs = _requests(setup)
     server = serving.BatchServer(setup[0], RES, n_contexts=2, graphs=graphs,
-                                 memory_budget=8 << 30)
+                                 memory_budget=8 << 30, solo=False)
     server.warm(reqs)
     done = server.run(reqs)
     assert len(done) == len(reqs) and all(r.done >= r.arrival for r in done)
+    assert server.n_solo == 0 and server.n_batched == len(reqs)
     by_id = {r.rid: r for r in done}
     for r in reqs[:12]:
         (out,) = server.run([_solo(r)])
         assert torch.equal(out.result, by_id[r.rid].result), (r.rid, r.kind)
     s = serving.latency_summary(done, RES)
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def _close_track(a, b):
+    """Tracking results of the single-request kernels against the batched
+    ones: the loss within FP64 rounding of another fixed order of the same
+    block sums, the pose gradient within FP32 rounding (the same terms in the
+    same order; the compiler may contract a product and a sum differently in
+    the two instantiations)."""
+    a, b = a.numpy(), b.numpy()
+    assert a[0] == pytest.approx(b[0], rel=1e-13, abs=1e-300)
+    np.testing.assert_allclose(a[1:7], b[1:7], rtol=1e-6, atol=1e-7 * np.abs(b[1:7]).max())
+    np.testing.assert_allclose(a[7:], b[7:], rtol=1e-6, atol=1e-7 * np.abs(b[7:]).max())
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_lone_requests_take_the_single_request_path(dev, setup, graphs):
+    """With the single-request renderers a request served alone takes them;
+    its colour image equals the batched one bit for bit, its tracking result
+    agrees within rounding."""
+    reqs = _requests(setup)
+    batched = serving.BatchServer(setup[0], RES, n_contexts=2, graphs=graphs,
+                                  memory_budget=8 << 30, solo=False)
+    batched.warm(reqs)
+    server = serving.BatchServer(setup[0], RES, n_contexts=2, graphs=graphs,
+                                 memory_budget=8 << 30)
+    server.warm(reqs)
+    done = server.run(reqs)
+    assert len(done) == len(reqs)
+    for r in reqs[:12]:
+        (a,) = server.run([_solo(r)])
+        (b,) = batched.run([_solo(r)])
+        if r.kind == "render":
+            assert torch.equal(a.result, b.result), r.rid
+        else:
+            _close_track(a.result, b.result)
+    assert server.n_solo >= 12
 
 
 @pytest.mark.parametrize("graphs", [True, False])
@@ -135,14 +174,14 @@ def test_admission_under_a_small_budget(dev, setup):
     sections = setup[0]
     reqs = _requests(setup, n=20, seed=11, rate=1e6)
     server = serving.BatchServer(sections, RES, n_contexts=2, graphs=False,
-                                 memory_budget=600 << 20)
+                                 memory_budget=600 << 20, solo=False)
     server.warm(reqs)
     cap = server.ctxs[0].cap
     done = server.run(reqs)
     assert len(done) == len(reqs)
     small = [r for r in reqs if r.bucket != 1]
     tiny = serving.BatchServer(sections, RES[:1] + [(2000, 2000)] + RES[2:], n_contexts=1,
-                               graphs=False, memory_budget=100 << 20)
+                               graphs=False, memory_budget=100 << 20, solo=False)
     tiny.warm(small)
     big = serving.Request(999, "render", 0, small[0].pose, 1, arrival=0.0)
     with pytest.raises(ValueError):
