@@ -505,9 +505,10 @@ def serving_workload(dev, seed: int = 3):
     return sec16, sec32, poses, res, frames
 
 
-# the served form's smallest batch time budget (the budget follows the queue
-# between this and the server's batch_ms)
-SERVE_BATCH_MS_MIN = 1.0
+# the served form's policy: two batch contexts; the batch time budget follows
+# the queue between 1 ms and the server's batch_ms; shortest estimated
+# request first, except requests older than 15 ms, which go first
+SERVED = dict(n_contexts=2, batch_ms_min=1.0, shortest_first_ms=15.0)
 
 
 def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
@@ -515,8 +516,9 @@ def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
     Poisson requests 70% track / 30% render over 320x240 ... 1920x1080, every
     track request uploading its own observation).  Served form: FP16
     attributes, continuous batching with one launch per stage over the
-    batch, three batch contexts, a lone request on the context's
-    single-request renderer, CUDA graphs.  Baseline: FP32 attributes, one
+    batch, two batch contexts, a lone request on the context's
+    single-request renderer, CUDA graphs, shortest request first within a
+    15 ms wait limit.  Baseline: FP32 attributes, one
     request at a time, eager.  Saturated throughput of each pattern alone
     (FP16, graphs, batching) and of both forms; p50/p99 at 50/80/95% of the
     served form's saturated rate, n_req requests per load point and form,
@@ -530,7 +532,8 @@ def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
     out = {"sections_gaussians": [s.n for s in sec16], "resolutions": res,
            "mix": "70% track (observation uploaded, fwd + Eq. 1 L1 + pose bwd, loss and pose "
                   "gradient to host), 30% render (colour image to host)",
-           "requests_per_load_point": n_req}
+           "requests_per_load_point": n_req,
+           "served_policy": dict(SERVED, batch_ms=4.0, graphs=True, single_request_path=True)}
     req = lambda n, rate, seed: serving.poisson_requests(n, rate, 16, len(res), poses, seed=seed,
                                                          frames=frames)
     forms = {
@@ -539,9 +542,9 @@ def run_serving(dev, n_req: int = 10000, n_burst: int = 1500):
         "fp16_only": lambda: serving.SlotServer(sec16, res, 1, graphs=False, keep_results=False),
         "graphs_only": lambda: serving.SlotServer(sec32, res, 1, graphs=True, keep_results=False),
         "batching_only": lambda: serving.BatchServer(sec32, res, graphs=False, solo=False,
-                                                     keep_results=False),
+                                                     keep_results=False, **SERVED),
         "served_fp16_batched_graphs": lambda: serving.BatchServer(
-            sec16, res, graphs=True, keep_results=False, batch_ms_min=SERVE_BATCH_MS_MIN),
+            sec16, res, graphs=True, keep_results=False, **SERVED),
     }
     warm = req(400, 1e9, 7)
     servers, sat = {}, {}

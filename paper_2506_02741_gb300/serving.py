@@ -70,6 +70,24 @@ def _pad(x: int) -> int:
     return (x + 255) // 256 * 256
 
 
+def batch_budget(queued_ms, n_contexts: int, lo: float | None, hi: float) -> float:
+    """GPU-time budget of the next batch: ``hi``, or with ``lo`` given the
+    queued requests' estimated time divided among the contexts, clamped to
+    [lo, hi]."""
+    if lo is None:
+        return hi
+    return min(hi, max(lo, sum(queued_ms) / max(1, n_contexts)))
+
+
+def admission_order(queue, now: float, ms_of, wait_ms: float) -> list:
+    """The queue in admission order: requests that arrived more than wait_ms
+    before ``now`` (seconds) first, oldest first; then the rest by estimated
+    GPU time (ms_of), shortest first, ties by arrival."""
+    late = now - wait_ms * 1e-3
+    return sorted(queue, key=lambda q: (0, q.arrival, 0.0) if q.arrival < late else
+                  (1, ms_of(q), q.arrival))
+
+
 @contextlib.contextmanager
 def _no_gc():
     """The serving loops hold Python's cyclic garbage collector off while they
@@ -135,7 +153,8 @@ class BatchServer:
     def __init__(self, sections, resolutions, n_contexts: int = 3, graphs: bool = True,
                  memory_budget: int | None = None, list_cap: int = 256, batch_ms: float = 4.0,
                  graph_ms: float = 1.0, keep_results: bool = True, solo: bool = True,
-                 batch_ms_min: float | None = None, device="cuda"):
+                 batch_ms_min: float | None = None, shortest_first_ms: float | None = None,
+                 device="cuda"):
         """sections: list of api.Section (resident, spheres); resolutions:
         list of (W, H) buckets.  The contexts share memory_budget (default:
         70% of the free device memory) in equal parts.  A batch takes the
@@ -153,7 +172,10 @@ class BatchServer:
         batched launches; the single-request renderers' memory counts against
         memory_budget.  With ``batch_ms_min`` the time budget of a batch
         follows the queue: its estimated GPU time divided among the contexts,
-        clamped to [batch_ms_min, batch_ms]."""
+        clamped to [batch_ms_min, batch_ms].  With ``shortest_first_ms`` the
+        queue is served shortest estimated GPU time first, except that the
+        requests which have waited longer than that many milliseconds go
+        first, oldest first (no request waits behind shorter ones for long)."""
         from . import synthetic as syn
         self.device = torch.device(device)
         self.sections = sections
@@ -163,6 +185,7 @@ class BatchServer:
         self.list_cap = int(list_cap)
         self.batch_ms = float(batch_ms)
         self.batch_ms_min = None if batch_ms_min is None else float(batch_ms_min)
+        self.shortest_first_ms = None if shortest_first_ms is None else float(shortest_first_ms)
         self.graph_ms = float(graph_ms)
         self.keep_results = keep_results
         free, _ = torch.cuda.mem_get_info(self.device)
@@ -483,10 +506,11 @@ class BatchServer:
                     continue
                 used = dict(gaussians=0, pixels=0, tiles=0, views=0, table_rows=0, instances=0,
                             items=0, ms=0.0)
-                budget = self.batch_ms
-                if self.batch_ms_min is not None:
-                    queued = sum(self._ms(q) for q in queue)
-                    budget = min(self.batch_ms, max(self.batch_ms_min, queued / self.n_contexts))
+                budget = batch_budget([self._ms(q) for q in queue], self.n_contexts,
+                                      self.batch_ms_min, self.batch_ms)
+                if self.shortest_first_ms is not None and len(queue) > 1:
+                    queue = collections.deque(admission_order(queue, now, self._ms,
+                                                              self.shortest_first_ms))
                 take = [queue.popleft()]   # the head always goes (it fits an empty context)
                 for k, v in self._need(take[0]).items():
                     used[k] += v
