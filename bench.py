@@ -777,6 +777,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # the warm-up steps again in the timed form (graph replays), untimed,
+        # with the clock sampler already running
+        for i in range(args.warmup):
+            frame_for(i)
+            tr.replay()
+        torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         if world > 1:
