@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-mapping", action="store_true", help="skip the FP16/FP32 mapping lines")
     p.add_argument("--mapping-iters", type=int, default=60)
     p.add_argument("--no-serving", action="store_true", help="skip the serving load points")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the head-frame, ellipsoid and large-scene lines")
     p.add_argument("--serving-requests", type=int, default=10000,
                    help="requests per serving load point")
     return p.parse_args()
@@ -84,6 +86,11 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: wait for its first sample so
+            # that its start-up does not fall inside the timed region
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -896,9 +903,10 @@ def main():
     mapping = None
     if rank == 0 and not args.no_mapping:
         mapping = {prec: run_mapping(dev, prec, args.mapping_iters) for prec in ("f16", "f32")}
-    head_frame = run_head_frame(dev) if rank == 0 and not args.no_mapping else None
-    ellipsoids = run_ellipsoids(dev) if rank == 0 and not args.no_mapping else None
-    large = run_large(dev) if rank == 0 and not args.no_mapping else None
+    extras = rank == 0 and not args.no_mapping and not args.no_extras
+    head_frame = run_head_frame(dev) if extras else None
+    ellipsoids = run_ellipsoids(dev) if extras else None
+    large = run_large(dev) if extras else None
 
     serving_line = None
     if rank == 0 and not args.no_serving:
