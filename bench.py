@@ -905,20 +905,24 @@ def main():
                          "frac": n_wi / avg_s / issue_peak}
     roof["timing"] = f"CUDA events around each launch, {n_prof} eager steps of the same workload"
 
+    # the single-GPU figures (mapping, head frame, ellipsoids, large scene,
+    # serving, the host baseline) are taken at N = 1 only: at N > 1 the run
+    # is the replicated tracking step alone
+    single = world == 1
     mapping = None
-    if rank == 0 and not args.no_mapping:
+    if single and not args.no_mapping:
         mapping = {prec: run_mapping(dev, prec, args.mapping_iters) for prec in ("f16", "f32")}
-    extras = rank == 0 and not args.no_mapping and not args.no_extras
+    extras = single and not args.no_mapping and not args.no_extras
     head_frame = run_head_frame(dev) if extras else None
     ellipsoids = run_ellipsoids(dev) if extras else None
     large = run_large(dev) if extras else None
 
     serving_line = None
-    if rank == 0 and not args.no_serving:
+    if single and not args.no_serving:
         serving_line = run_serving(dev, args.serving_requests)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if single and not args.no_cpu_baseline:
         try:
             v, info = oracle_crop_sample(args.cpu_seconds)
             cpu = dict(info, value=v, unit="Mpix/s")
