@@ -83,6 +83,7 @@ struct Status {
     int32_t pad;
     unsigned long long n_instances;
     unsigned long long n_overflow_tiles;
+    uint32_t sort_next[2];   // work counters of the long-list sorts (reset by the tile scan)
 };
 
 // ---------------------------------------------------------------------------

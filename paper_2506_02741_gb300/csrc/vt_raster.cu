@@ -432,6 +432,7 @@ __device__ __forceinline__ void scan_tiles_body(const uint32_t *tile_count, int 
         tile_off[n_tiles] = (uint32_t)carry;
         st->n_instances = carry;
         st->n_overflow_tiles = 0;
+        st->sort_next[0] = st->sort_next[1] = 0u;
         st->flags = carry > cap || carry >= 0xffffffffull ? kFlagCapacity : 0;
     }
 }
@@ -798,15 +799,27 @@ __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_
                                                 uint32_t *sorted, uint8_t *bmask,
                                                 const float4 *geo, const Camera &cam, Status *st,
                                                 int smem_n, int lo, int hi,
-                                                const BatchTable *B = nullptr) {
+                                                const BatchTable *B = nullptr,
+                                                uint32_t *wctr = nullptr) {
     extern __shared__ unsigned long long sm[];
     __shared__ uint32_t red[4][kSortWarps];
+    __shared__ int s_next;
     if (st->flags) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (B) n_tiles = B->n_tiles;
     ItemCursor cur;
-    // grid-stride over tiles: a launch may have fewer blocks than tiles
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    // A launch may have fewer blocks than tiles: blocks stride over the tiles,
+    // or with a work counter take the next tile from it (the long lists vary
+    // in length by 5x: a fixed stride leaves the block with the longest share
+    // running alone at the end).
+    auto next = [&](int t) {
+        if (!wctr) return t + (int)gridDim.x;
+        __syncthreads();   // every thread has read the previous s_next
+        if (tid == 0) s_next = (int)atomicAdd(wctr, 1u);
+        __syncthreads();
+        return s_next;
+    };
+    for (int t = wctr ? next(0) : (int)blockIdx.x; t < n_tiles; t = next(t)) {
         const uint32_t start = tile_off[t];
         const int n = (int)(tile_off[t + 1] - start);
         if (n <= lo || n > hi) continue;   // another launch sorts this size class
@@ -832,19 +845,21 @@ __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_
 // blocks of 512 threads per SM; the long lists (one block per SM) and the
 // lists sorted in global memory (two blocks per SM, shared memory for the
 // histograms only) rank twice.
-#define VT_SORT_KERNEL(name, G, MIN_BLOCKS)                                                      \
+// CTR: the work counter of the launch (-1: blocks stride over the tiles).
+#define VT_SORT_KERNEL(name, G, MIN_BLOCKS, CTR)                                                 \
     __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) name(                            \
         const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,                       \
         unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,       \
         const float4 *geo, Camera cam, Status *st, int smem_n, int lo, int hi) {                 \
         sort_tiles_body<G>(tile_off, n_tiles, bucket, alt, bmask_u, sorted, bmask, geo, cam, st, \
-                           smem_n, lo, hi);                                                      \
+                           smem_n, lo, hi, nullptr,                                              \
+                           CTR < 0 ? nullptr : &st->sort_next[CTR < 0 ? 0 : CTR]);               \
     }
-VT_SORT_KERNEL(k_sort_tiles, 3, 2)
-VT_SORT_KERNEL(k_sort_tiles_mid, 7, 2)
-VT_SORT_KERNEL(k_sort_tiles_large, 12, 2)
-VT_SORT_KERNEL(k_sort_tiles_long, 0, 1)
-VT_SORT_KERNEL(k_sort_tiles_xl, 0, 2)
+VT_SORT_KERNEL(k_sort_tiles, 3, 2, -1)
+VT_SORT_KERNEL(k_sort_tiles_mid, 7, 2, -1)
+VT_SORT_KERNEL(k_sort_tiles_large, 12, 2, -1)
+VT_SORT_KERNEL(k_sort_tiles_long, 0, 1, 0)
+VT_SORT_KERNEL(k_sort_tiles_xl, 0, 2, 1)
 #undef VT_SORT_KERNEL
 
 // Batched forms: the same classes over the tiles of every work item.
