@@ -560,10 +560,24 @@ __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigne
             __syncwarp();
         }
     } else {
+        // without the register cache (the long lists, read from global
+        // memory in the largest class) the keys of the next two groups are
+        // in flight while a group is ranked
+        constexpr bool ahead = G == 0;
+        unsigned long long k1 = ahead && lo + lane < hi ? in[lo + lane] : 0ull;
+        unsigned long long k2 = ahead && lo + 32 + lane < hi ? in[lo + 32 + lane] : 0ull;
         for (int i0 = lo; i0 < hi; i0 += 32) {
             const int i = i0 + lane;
             const bool valid = i < hi;
-            const unsigned d = valid ? (unsigned)(in[i] >> shift) & dmask : 0u;
+            unsigned long long k = 0ull;
+            if (ahead) {
+                k = k1;
+                k1 = k2;
+                k2 = i + 64 < hi ? in[i + 64] : 0ull;
+            } else if (valid) {
+                k = in[i];
+            }
+            const unsigned d = valid ? (unsigned)(k >> shift) & dmask : 0u;
             const unsigned peers = digit_peers(d, nbits, valid);
             if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
             __syncwarp();
@@ -616,15 +630,21 @@ __device__ __forceinline__ void radix_pass(const unsigned long long *in, unsigne
             __syncwarp();
         }
     } else {
+        constexpr bool ahead = G == 0;
+        unsigned long long k1 = ahead && lo + lane < hi ? in[lo + lane] : 0ull;
+        unsigned long long k2 = ahead && lo + 32 + lane < hi ? in[lo + 32 + lane] : 0ull;
         for (int i0 = lo; i0 < hi; i0 += 32) {
             const int i = i0 + lane;
             const bool valid = i < hi;
-            unsigned long long key = 0;
-            unsigned d = 0;
-            if (valid) {
+            unsigned long long key = 0ull;
+            if (ahead) {
+                key = k1;
+                k1 = k2;
+                k2 = i + 64 < hi ? in[i + 64] : 0ull;
+            } else if (valid) {
                 key = in[i];
-                d = (unsigned)(key >> shift) & dmask;
             }
+            const unsigned d = valid ? (unsigned)(key >> shift) & dmask : 0u;
             const unsigned peers = digit_peers(d, nbits, valid);
             if (valid) {
                 const uint32_t pos = h[d] + __popc(peers & lt);
