@@ -883,19 +883,20 @@ VT_SORT_KERNEL(k_sort_tiles_xl, 0, 2, 1)
 #undef VT_SORT_KERNEL
 
 // Batched forms: the same classes over the tiles of every work item.
-#define VT_SORT_KERNEL_B(name, G, MIN_BLOCKS)                                                    \
+#define VT_SORT_KERNEL_B(name, G, MIN_BLOCKS, CTR)                                               \
     __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) name(                            \
         const BatchTable *B, const uint32_t *tile_off, unsigned long long *bucket,               \
         unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,       \
         const float4 *geo, Status *st, int smem_n, int lo, int hi) {                             \
         sort_tiles_body<G>(tile_off, 0, bucket, alt, bmask_u, sorted, bmask, geo, B->it[0].cam,  \
-                           st, smem_n, lo, hi, B);                                               \
+                           st, smem_n, lo, hi, B,                                                \
+                           CTR < 0 ? nullptr : &st->sort_next[CTR < 0 ? 0 : CTR]);               \
     }
-VT_SORT_KERNEL_B(kb_sort_tiles, 3, 2)
-VT_SORT_KERNEL_B(kb_sort_tiles_mid, 7, 2)
-VT_SORT_KERNEL_B(kb_sort_tiles_large, 12, 2)
-VT_SORT_KERNEL_B(kb_sort_tiles_long, 0, 1)
-VT_SORT_KERNEL_B(kb_sort_tiles_xl, 0, 2)
+VT_SORT_KERNEL_B(kb_sort_tiles, 3, 2, -1)
+VT_SORT_KERNEL_B(kb_sort_tiles_mid, 7, 2, -1)
+VT_SORT_KERNEL_B(kb_sort_tiles_large, 12, 2, -1)
+VT_SORT_KERNEL_B(kb_sort_tiles_long, 0, 1, 0)
+VT_SORT_KERNEL_B(kb_sort_tiles_xl, 0, 2, 1)
 #undef VT_SORT_KERNEL_B
 
 }  // namespace vt

@@ -373,5 +373,7 @@ def test_multiroom_large_scene_finite_differences():
         o[li] = v
         fd = (lp - lm) / (2 * e)
         ok += abs(fd - g_want) <= 1e-2 * abs(g_want) + 1e-3 * mag
-    # allow a few of the 64 for a decision the oracle's margins misjudge
+    # allow a few of the 64: where the step +-e moves a decision of the
+    # forward (the 1/255 cut or the termination point depend on o), the
+    # difference quotient is not the derivative
     assert ok >= 60, ok
