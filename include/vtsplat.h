@@ -328,7 +328,7 @@ vt_status vt_masked_l1(vt_ctx *ctx, int32_t W, int32_t H, const float *rgb, cons
  * and the gradient with respect to its camera pose (vt_masked_l1 and
  * vt_render_backward with VT_GRAD_POSE).  Every stage -- view set-up,
  * projection, tile binning, the per-tile sorts, compositing, the loss, the
- * pose backward and the final sums -- runs as one persistent launch over the
+ * pose backward and the final sums -- runs as one launch over the
  * Gaussians, tiles or pixels of all items (item ranges concatenated), so a
  * batch costs the same ~15 launches whatever its size.  The items are read
  * on the device from a work-item table that vt_batch_set writes into pinned

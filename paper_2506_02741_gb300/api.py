@@ -648,7 +648,7 @@ class BatchItem:
 class BatchRunner(Renderer):
     """A context reserved for batched work items (vt_batch_*): every stage
     of all items' renders -- and for tracking items the Eq. 1 loss and the
-    pose gradient -- runs as one persistent launch.  ``set`` stages a batch
+    pose gradient -- runs as one launch over all items.  ``set`` stages a batch
     (host only), ``launch`` enqueues it (capturable in a CUDA graph: the
     work-item table is uploaded inside the launch sequence)."""
 

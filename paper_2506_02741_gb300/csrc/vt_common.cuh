@@ -89,8 +89,9 @@ struct Status {
 // ---------------------------------------------------------------------------
 // Batched launches (vt_batch_*): many independent work items -- one section
 // rendered from one camera each, a tracking item adding the Eq. 1 masked L1
-// loss and the pose gradient -- processed by one persistent launch per
-// stage.  The work-item table lives in device memory (uploaded from pinned
+// loss and the pose gradient -- processed by one launch per stage over all
+// items (grids sized to the batch, or persistent grids inside a graph
+// capture).  The work-item table lives in device memory (uploaded from pinned
 // host memory at the start of the launch sequence), so one captured launch
 // sequence serves any mix of items within the reserved capacity.  The index
 // spaces are concatenated over the items: Gaussians and pixels (each item's
@@ -433,7 +434,7 @@ __global__ void k_view_finalize(SecTable T, const double *pose_copy, const doubl
                                 int n_views);
 __global__ void k_attr_scatter(SecTable T, const float4 *acc4, const float *accr);
 
-// Batched launches (see BatchTable): one persistent launch per stage.
+// Batched launches (see BatchTable): one launch per stage over all items.
 __global__ void kb_setup(const BatchTable *B, ViewXf *views, TabRow *tab, double *pose_copy,
                          uint32_t *tile_count);
 __global__ void kb_preprocess(const BatchTable *B, const ViewXf *views, const TabRow *tab,

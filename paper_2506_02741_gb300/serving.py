@@ -11,8 +11,8 @@ resolution and size on one GPU.
 * Latency runs from arrival to the result being visible on the host (a CUDA
   event after the device-to-host copy, polled without blocking).
 
-BatchServer is the served form: continuous batching with one persistent
-launch per stage (vt_batch_*).  It keeps ``n_contexts`` batch contexts, each
+BatchServer is the served form: continuous batching with one launch per
+stage over all of a batch's items (vt_batch_*).  It keeps ``n_contexts`` batch contexts, each
 with its own stream, workspace and capacity; whenever a context is idle it
 takes queued requests (shortest estimated GPU time first, those waiting
 longer than a limit first of all; or in arrival order) into one batch while
