@@ -66,7 +66,7 @@ enum KernelId {
     K_VIEW_GRADS, K_PRE_AN, K_FWD_AN, K_BWD_LIST_AN, K_BWD_AN, K_CHAIN, K_SHAPE_ADAM,
     K_SORT_XL, K_VIEW_FIN, K_BWD_LIST_POSE, K_BWD_LIST_VIEWS, KB_SETUP, KB_PREPROCESS, KB_SCAN,
     KB_EMIT, KB_SORT, KB_SORT_M, KB_SORT_L, KB_SORT_LONG, KB_SORT_XL, KB_FWD, KB_L1, KB_BWD_LIST,
-    KB_BWD, KB_FINALIZE, K_ADAM_INIT, K_NUM
+    KB_BWD, KB_FINALIZE, K_ADAM_INIT, K_BWD_LIST_POSEMAT, K_NUM
 };
 const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan_tiles",
                                    "k_emit",          "k_sort_tiles",    "k_composite_fwd",
@@ -85,7 +85,8 @@ const char *kKernelNames[K_NUM] = {"k_setup",         "k_preprocess",    "k_scan
                                    "kb_sort_tiles", "kb_sort_tiles_mid", "kb_sort_tiles_large",
                                    "kb_sort_tiles_long", "kb_sort_tiles_xl", "kb_composite_fwd",
                                    "kb_masked_l1", "kb_composite_bwd_list_pose",
-                                   "kb_composite_bwd_pose", "kb_finalize", "k_adam_init"};
+                                   "kb_composite_bwd_pose", "kb_finalize", "k_adam_init",
+                                   "k_composite_bwd_list_posemat"};
 constexpr int kDefaultListCap = 256;  // per-pixel ids kept for the backward
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -790,10 +791,17 @@ vt_status vt_render_backward(vt_ctx *c, const float *dL_drgb, const float *dL_dd
         VT_CUDA(cudaMemsetAsync(c->accr, 0, sizeof(float) * T.n_total, stream), "grad acc reset");
     }
     if (c->used_lists) {
-        LaunchScope ls(c, views ? K_BWD_LIST_VIEWS : (attr ? K_BWD_LIST : K_BWD_LIST_POSE),
+        // the pose alone: without a matrix gradient to return, the twist's six
+        // sums replace the twelve of x g^T and g
+        const bool posemat = d_mat != nullptr;
+        LaunchScope ls(c, views ? K_BWD_LIST_VIEWS
+                                : (attr ? K_BWD_LIST
+                                        : (posemat ? K_BWD_LIST_POSEMAT : K_BWD_LIST_POSE)),
                        stream);
         auto kern = views ? k_composite_bwd_list_views
-                          : (attr ? k_composite_bwd_list : k_composite_bwd_list_pose);
+                          : (attr ? k_composite_bwd_list
+                                  : (posemat ? k_composite_bwd_list_posemat
+                                             : k_composite_bwd_list_pose));
         kern<<<c->n_tiles, kBlockPix, 0, stream>>>(
             T, c->cam, c->geo, c->app, c->pix_nadd, c->pix_T, c->plist, c->list_cap, c->blk_ovf,
             dL_drgb, dL_ddepth, dL_dsil, mode, c->pose_partials, c->acc4, c->accr, c->accg,

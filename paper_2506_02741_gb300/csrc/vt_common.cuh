@@ -401,6 +401,14 @@ __global__ void k_composite_bwd_list_pose(SecTable T, Camera cam, const float4 *
                                           const float *g_depth, const float *g_sil, int mode,
                                           double *pose_partials, float4 *acc4, float *accr,
                                           float4 *accg, const Status *st);
+__global__ void k_composite_bwd_list_posemat(SecTable T, Camera cam, const float4 *geo,
+                                             const float4 *app, const uint32_t *pix_nadd,
+                                             const float *pix_T, const uint2 *plist,
+                                             int plist_cap, const uint32_t *blk_ovf,
+                                             const float *g_rgb, const float *g_depth,
+                                             const float *g_sil, int mode, double *pose_partials,
+                                             float4 *acc4, float *accr, float4 *accg,
+                                             const Status *st);
 __global__ void k_composite_bwd_list_aniso(SecTable T, Camera cam, const float4 *geo,
                                            const float4 *app, const uint32_t *pix_nadd,
                                            const float *pix_T, const uint2 *plist, int plist_cap,

@@ -524,7 +524,10 @@ __device__ __forceinline__ void bwd_advance(BwdPixel &P, const float4 &a, const 
 // and adds its pose terms to acc.  Ti_fwd >= 0 is the forward's transmittance in front
 // of this Gaussian (recorded in the per-pixel list); otherwise it is
 // recovered by division, which accumulates the rounding of every Gaussian
-// behind.
+// behind.  Twist = true accumulates only what the twist gradient needs:
+// acc.a[0..2] = sum (z gy - y gz, x gz - z gx, y gx - x gy) (the
+// antisymmetric part of sum x g^T) and acc.a[3..5] = sum g.
+template <bool Twist = false>
 __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const float4 &g1,
                                          const float4 &a, float t, float du, float dv, float G,
                                          float ah, const Camera &cam, bool want_pose, PoseAcc &acc,
@@ -561,15 +564,24 @@ __device__ __forceinline__ void bwd_pair(BwdPixel &P, const float4 &g0, const fl
         const float uc = (float)__float_as_int(g0.x) + g0.y;
         const float vc = (float)__float_as_int(g0.z) + g0.w;
         const float X[3] = {z * (uc - cam.cx) * ifx, z * (vc - cam.cy) * ify, z};
-        const float Gv[3] = {gx, gy, gz};
+        if constexpr (Twist) {
+            acc.a[0] = __fmaf_rn(-X[1], gz, __fmaf_rn(X[2], gy, acc.a[0]));
+            acc.a[1] = __fmaf_rn(-X[2], gx, __fmaf_rn(X[0], gz, acc.a[1]));
+            acc.a[2] = __fmaf_rn(-X[0], gy, __fmaf_rn(X[1], gx, acc.a[2]));
+            acc.a[3] += gx;
+            acc.a[4] += gy;
+            acc.a[5] += gz;
+        } else {
+            const float Gv[3] = {gx, gy, gz};
 #pragma unroll
-        for (int a_ = 0; a_ < 3; ++a_)
+            for (int a_ = 0; a_ < 3; ++a_)
 #pragma unroll
-            for (int b_ = 0; b_ < 3; ++b_)
-                acc.a[3 * a_ + b_] = __fmaf_rn(X[a_], Gv[b_], acc.a[3 * a_ + b_]);
-        acc.a[9] += gx;
-        acc.a[10] += gy;
-        acc.a[11] += gz;
+                for (int b_ = 0; b_ < 3; ++b_)
+                    acc.a[3 * a_ + b_] = __fmaf_rn(X[a_], Gv[b_], acc.a[3 * a_ + b_]);
+            acc.a[9] += gx;
+            acc.a[10] += gy;
+            acc.a[11] += gz;
+        }
     }
     bwd_advance(P, a, S);
 }
@@ -668,6 +680,31 @@ __device__ __forceinline__ void write_pose_partial(const PoseAcc &acc, double (*
     if (threadIdx.x < 12) {
         double v = 0.0;
         for (int w = 0; w < kBlockPix / 32; ++w) v += s_pose[w][threadIdx.x];
+        pose_partials[(size_t)tile * 12 + threadIdx.x] = v;
+    }
+}
+
+// The same for the twist-only terms (bwd_pair<true>), written in the slots
+// of the full partial that the twist is formed from (k_pose_finalize:
+// dL/dphi = (A21 - A12, A02 - A20, A10 - A01), dL/drho = -s): A21, A02, A10
+// hold the three sums, the other A slots zero, so tiles summed by the full
+// terms (the tile replay) and by these add up in the same slots.
+__device__ __forceinline__ void write_twist_partial(const PoseAcc &acc, double (*s_pose)[12],
+                                                    double *pose_partials, int tile) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const ff v = warp_sum_ff(acc.a[i]);
+        if (lane == 0) s_pose[warp][i] = to_double(v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        // slot -> twist sum: A02 <- 1, A10 <- 2, A21 <- 0, s <- 3..5
+        const int src = threadIdx.x == 2 ? 1 : threadIdx.x == 3 ? 2 : threadIdx.x == 7 ? 0
+                      : threadIdx.x >= 9 ? threadIdx.x - 6 : -1;
+        double v = 0.0;
+        if (src >= 0)
+            for (int w = 0; w < kBlockPix / 32; ++w) v += s_pose[w][src];
         pose_partials[(size_t)tile * 12 + threadIdx.x] = v;
     }
 }
@@ -870,7 +907,7 @@ __global__ void __launch_bounds__(kBlockPix) k_composite_bwd_aniso(
 // ellipsoid records (k_composite_bwd_list_aniso): per-Gaussian accumulation
 // instead of per-lane pose sums.  PoseOnly = true (k_composite_bwd_list_pose)
 // leaves out the per-Gaussian terms, which tracking does not use.
-template <bool Views, bool Aniso, bool PoseOnly = false>
+template <bool Views, bool Aniso, bool PoseOnly = false, bool Twist = false>
 __device__ __forceinline__ void bwd_list_body(
     const SecTable &Tab, const Camera &cam, const float4 *geo, const float4 *app,
     const uint32_t *pix_nadd, const float *pix_T, const uint2 *plist, int plist_cap,
@@ -942,14 +979,19 @@ __device__ __forceinline__ void bwd_list_body(
                                  accg, accm);
         } else {
             float dc0, dc1, dc2, dop, drd, gx, gy, gz;
-            bwd_pair(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2, dop,
-                     drd, want_views, gx, gy, gz, Ti);
+            bwd_pair<Twist>(P, g0, g1, a, t, du, dv, G, ah, cam, want_pose, acc, dc0, dc1, dc2,
+                            dop, drd, want_views, gx, gy, gz, Ti);
             if (!PoseOnly && (want_attr || want_views))
                 add_pair_grads(Tab, g, want_attr, want_views, dc0, dc1, dc2, dop, drd, gx, gy, gz,
                                acc4, accr, accg);
         }
     }
-    if (want_pose && !Aniso) write_pose_partial(acc, s_pose, pose_partials, tile);
+    if (want_pose && !Aniso) {
+        if constexpr (Twist)
+            write_twist_partial(acc, s_pose, pose_partials, tile);
+        else
+            write_pose_partial(acc, s_pose, pose_partials, tile);
+    }
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
@@ -964,6 +1006,20 @@ __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list(
 }
 
 __global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_pose(
+    SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
+    const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *blk_ovf,
+    const float *g_rgb, const float *g_depth, const float *g_sil, int mode,
+    double *pose_partials, float4 *acc4, float *accr, float4 *accg, const Status *st) {
+    __shared__ double s_pose[kBlockPix / 32][12];
+    bwd_list_body<false, false, true, true>(Tab, cam, geo, app, pix_nadd, pix_T, plist,
+                                            plist_cap, blk_ovf, g_rgb, g_depth, g_sil,
+                                            VT_GRAD_POSE, pose_partials, acc4, accr, accg,
+                                            nullptr, st, s_pose, blockIdx.x);
+}
+
+// The pose-only list backward with the matrix gradient too (all twelve sums
+// of x g^T and g), for callers that ask for dL/d[R|t].
+__global__ void __launch_bounds__(kBlockPix, 3) k_composite_bwd_list_posemat(
     SecTable Tab, Camera cam, const float4 *geo, const float4 *app, const uint32_t *pix_nadd,
     const float *pix_T, const uint2 *plist, int plist_cap, const uint32_t *blk_ovf,
     const float *g_rgb, const float *g_depth, const float *g_sil, int mode,

@@ -420,6 +420,29 @@ def test_backward_paths_agree(dev, cap):
     G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", noise=want["mat_noise"])
 
 
+@pytest.mark.parametrize("cap", [0, 3, 256])
+def test_twist_only_backward(dev, cap):
+    """A pose backward asked for the twist alone (no matrix gradient: the
+    tracking iteration) takes the six-sum form of the list backward: its
+    twist agrees with the twelve-sum form's within FP32 rounding and with the
+    oracle's, on list tiles, replayed tiles and a mix of both."""
+    osecs, target, K, W, H = _cases()["qqvga_2views"]()
+    R = api.Renderer()
+    R.set_list_capacity(cap)
+    R, dsecs, out = _render(osecs, target, K, W, H, R=R)
+    ids, cnt = G.decisions(dsecs, api.pose12(target), K, W, H, out=out)
+    gR, gD, _ = _upstream((H, W), 78, 1.0)
+    want = oracle.backward_lists(osecs, target, K, W, H, ids, cnt, g_rgb=gR, g_depth=gD)
+    t = lambda a: torch.from_numpy(a).to(dev)
+    tw = torch.zeros(6, dtype=torch.float64, device=dev)
+    R.backward(t(gR), t(gD), None, pose_grad=True, d_twist=tw)
+    full, _ = R.backward(t(gR), t(gD), None, pose_grad=True)
+    torch.cuda.synchronize()
+    a, b = tw.cpu().numpy(), full.cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+    G.assert_grad_close(a, want["twist"], name="twist", noise=want["twist_noise"])
+
+
 def test_budget_disables_lists(dev):
     osecs, target, K, W, H = _cases()["tiny"]()
     R = api.Renderer()
