@@ -82,6 +82,44 @@ def test_fullsize_crop_parity(cfg):
     G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", noise=want["mat_noise"])
 
 
+def test_4k_render_crop_parity():
+    """The 8-keyframe tracking section rendered at 3832x2156 (4K cut so that
+    the last tile column and row are ragged; the same field of view: 8.3 M
+    pixels, 32,400 tiles, per-pixel lists of 17 GB, so their byte offsets
+    pass 2^31): a crop at the bottom edge, through the ragged tiles, against
+    the oracle along the GPU's decisions, and the pose gradient of an
+    upstream gradient on that crop."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    osec, target = _section(syn.VGA, 8, "f32")
+    sec = G.to_device(osec, "f32")
+    K = syn.scaled_intrinsics(3832, 2156)
+    R = api.Renderer()
+    rgb, depth, sil = R.render([sec], api.pose12(target, dev), K.astuple(), K.W, K.H,
+                               checked=True)
+    assert R.used_lists
+    cw, ch = 96, 80
+    x0, y0 = (K.W - cw) // 2, K.H - ch       # through the ragged last tile row
+    Kc = _crop(K, x0, y0)
+    ids, cnt = G.decisions([sec], api.pose12(target, dev), K.astuple(), K.W, K.H,
+                           out=(rgb, depth, sil), box=(x0, y0, cw, ch))
+    ref = oracle.render_lists([osec], target, Kc, cw, ch, ids, cnt)
+    G.check_decisions(ref, "render_3832x2156")
+    assert float(ref["sil"].mean()) > 0.5        # the crop sees the scene
+    sl = (slice(y0, y0 + ch), slice(x0, x0 + cw))
+    G.assert_forward_close((rgb[:, sl[0], sl[1]], depth[sl], sil[sl]), ref)
+    gR = np.random.default_rng(9).normal(0, 1, (3, ch, cw)).astype(np.float32)
+    want = oracle.backward_lists([osec], target, Kc, cw, ch, ids, cnt, g_rgb=gR)
+    full_gR = torch.zeros(3, K.H, K.W, device=dev)
+    full_gR[:, sl[0], sl[1]] = torch.from_numpy(gR).to(dev)
+    dtw, dmat = R.backward(full_gR, None, None, pose_grad=True)
+    torch.cuda.synchronize()
+    G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist",
+                        noise=want["twist_noise"])
+    G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", noise=want["mat_noise"])
+
+
 def _tile_lists_sorted(R, n, W, H):
     z = R.debug(0, n, np.float32)
     tiles_x = (W + 15) // 16
