@@ -209,6 +209,15 @@ def test_batch_errors(dev, scene):
         B.set(scene["dsecs"], [api.BatchItem(5, False, 16, 16, (10.0, 10.0, 8.0, 8.0),
                                              items[0].pose, torch.zeros(5, 16, 16, device=dev))])
     assert e.value.status == L.VT_ERR_INVALID_ARG
+    # an empty batch and more items than a table holds
+    for bad in ([], items * 65):
+        with pytest.raises(L.VTError) as e:
+            B.set(scene["dsecs"], bad)
+        assert e.value.status == L.VT_ERR_INVALID_ARG, len(bad)
+    # an empty image: refused by the binding's shape check before the call
+    with pytest.raises(ValueError):
+        B.set(scene["dsecs"], [api.BatchItem(0, False, 0, 16, items[0].K, items[0].pose,
+                                             torch.zeros(5, 16, 1, device=dev))])
     small = api.BatchRunner(max_gaussians=1000, max_pixels=1000, max_tiles=10,
                             max_instances=1000, max_views=4, max_table_rows=1000)
     with pytest.raises(L.VTError) as e:
