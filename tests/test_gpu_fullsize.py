@@ -80,6 +80,12 @@ def test_fullsize_crop_parity(cfg):
     G.assert_grad_close(dtw.cpu().numpy(), want["twist"], name="twist",
                         noise=want["twist_noise"])
     G.assert_grad_close(dmat.cpu().numpy(), want["mat"], name="mat", noise=want["mat_noise"])
+    # the tracking iteration's form: the twist alone (six-sum list backward)
+    tw = torch.zeros(6, dtype=torch.float64, device=dev)
+    R.backward(full_gR, full_gD, None, pose_grad=True, d_twist=tw)
+    torch.cuda.synchronize()
+    G.assert_grad_close(tw.cpu().numpy(), want["twist"], name="twist_only",
+                        noise=want["twist_noise"])
 
 
 def test_4k_render_crop_parity():
