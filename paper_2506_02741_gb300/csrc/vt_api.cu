@@ -638,8 +638,9 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         k_emit<<<gblocks, 256, 0, stream>>>(total, c->info, cam, c->tile_cursor, c->bucket,
                                             c->bmask_u, c->status);
     }
-    // fork: the long lists sort on the auxiliary stream (works under graph
-    // capture too: the fork and join events make it a parallel branch)
+    // fork: the long lists and the large class sort on the auxiliary stream,
+    // beside the short classes on the caller's (works under graph capture
+    // too: the fork and join events make it a parallel branch)
     VT_CUDA(cudaEventRecord(c->ev_fork, stream), "sort fork");
     VT_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "sort fork");
     {
@@ -649,6 +650,12 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         k_sort_tiles_long<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, kSortSmemBig);
+    }
+    {
+        LaunchScope ls(c, K_SORT_L, c->aux);
+        k_sort_tiles_large<<<n_tiles, 512, kSortSmemBytes, c->aux>>>(
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN);
     }
     {
         LaunchScope ls(c, K_SORT_XL, c->aux);
@@ -668,12 +675,6 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         k_sort_tiles_mid<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortClassM, kSortClassS, kSortClassM);
-    }
-    {
-        LaunchScope ls(c, K_SORT_L, stream);
-        k_sort_tiles_large<<<n_tiles, 512, kSortSmemBytes, stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN);
     }
     VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
     {
