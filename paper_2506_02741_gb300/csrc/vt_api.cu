@@ -54,6 +54,7 @@ constexpr size_t sort_smem_bytes(int n) { return 2 * (size_t)n * 8 + 16 * 256 * 
 constexpr int kSortSmemN = 6000;
 constexpr size_t kSortSmemBytes = 2 * kSortSmemN * sizeof(unsigned long long) + 16 * 256 * 4;
 constexpr int kSortSmemBig = 13312;
+static_assert(kSortSmemN == kSortLongMin, "the tile scan lists the long-list launches' tiles");
 static_assert(kSortSmemBig < (1 << 24), "shared-memory sorts carry 24-bit bucket positions");
 constexpr size_t kSortSmemBigBytes =
     2 * kSortSmemBig * sizeof(unsigned long long) + 16 * 256 * 4;
@@ -113,6 +114,7 @@ struct vt_ctx {
     float4 *geo = nullptr, *app = nullptr;
     uint4 *info = nullptr;
     uint32_t *tile_count = nullptr, *tile_off = nullptr, *tile_cursor = nullptr;
+    uint32_t *long_tiles = nullptr;   // tiles of the long-list sorts (listed by the tile scan)
     unsigned long long *bucket = nullptr, *alt = nullptr;
     uint32_t *sorted = nullptr;
     uint8_t *bmask = nullptr;         // per sorted entry: 8x4 blocks of the tile it reaches
@@ -224,7 +226,7 @@ size_t arena_bytes_for(int64_t g, int64_t i, int64_t p, int64_t t, int64_t v, in
     b += align_up(sizeof(float4) * 2 * g);               // geo
     b += align_up(sizeof(float4) * g);                   // app
     b += align_up(sizeof(uint4) * g);                    // info
-    b += 3 * align_up(sizeof(uint32_t) * (t + 1));       // tile count/off/cursor
+    b += 4 * align_up(sizeof(uint32_t) * (t + 1));       // tile count/off/cursor, long tiles
     b += 2 * align_up(sizeof(unsigned long long) * i);   // bucket, alt
     b += align_up(sizeof(uint32_t) * i);                 // sorted
     b += 2 * align_up(i);                                // block masks (bucket, sorted)
@@ -277,6 +279,7 @@ vt_status ensure(vt_ctx *c, int64_t g, int64_t i, int64_t p, int64_t t, int64_t 
     c->tile_count = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
     c->tile_off = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
     c->tile_cursor = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
+    c->long_tiles = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (t + 1)));
     c->bucket = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * i));
     c->alt = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * i));
     c->sorted = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * i));
@@ -631,7 +634,8 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
     {
         LaunchScope ls(c, K_SCAN, stream);
         k_scan_tiles<<<1, 1024, 0, stream>>>(c->tile_count, n_tiles, c->tile_off, c->tile_cursor,
-                                             c->status, (unsigned long long)c->cap_i);
+                                             c->status, (unsigned long long)c->cap_i,
+                                             c->long_tiles);
     }
     if (total > 0) {
         LaunchScope ls(c, K_EMIT, stream);
@@ -649,32 +653,32 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         // not hold every SM's shared memory while the others run
         k_sort_tiles_long<<<std::min(n_tiles, c->n_sm), 512, kSortSmemBigBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, kSortSmemBig);
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, kSortSmemBig, c->long_tiles);
     }
     {
         LaunchScope ls(c, K_SORT_L, c->aux);
         k_sort_tiles_large<<<n_tiles, 512, kSortSmemBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN);
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN, c->long_tiles);
     }
     {
         LaunchScope ls(c, K_SORT_XL, c->aux);
         k_sort_tiles_xl<<<std::min(n_tiles, 2 * c->n_sm), 512, kSortHistBytes, c->aux>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemBig, 0x7fffffff);
+            aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemBig, 0x7fffffff, c->long_tiles);
     }
     VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
     {
         LaunchScope ls(c, K_SORT, stream);
         k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassS), stream>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortClassS, 0, kSortClassS);
+            aniso ? nullptr : c->geo, cam, c->status, kSortClassS, 0, kSortClassS, c->long_tiles);
     }
     {
         LaunchScope ls(c, K_SORT_M, stream);
         k_sort_tiles_mid<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortClassM, kSortClassS, kSortClassM);
+            aniso ? nullptr : c->geo, cam, c->status, kSortClassM, kSortClassS, kSortClassM, c->long_tiles);
     }
     VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
     {
@@ -1499,7 +1503,8 @@ vt_status vt_batch_launch(vt_ctx *c, vt_stream stream, vt_event obs_ready) {
     {
         LaunchScope ls(c, KB_SCAN, stream);
         kb_scan_tiles<<<1, 1024, 0, stream>>>(B, c->tile_count, c->tile_off, c->tile_cursor,
-                                              c->status, (unsigned long long)c->bcap_i);
+                                              c->status, (unsigned long long)c->bcap_i,
+                                              c->long_tiles);
     }
     {
         LaunchScope ls(c, KB_EMIT, stream);
@@ -1512,32 +1517,32 @@ vt_status vt_batch_launch(vt_ctx *c, vt_stream stream, vt_event obs_ready) {
         LaunchScope ls(c, KB_SORT_LONG, c->aux);
         kb_sort_tiles_long<<<grid(std::min<int64_t>(H.n_tiles, nsm), 1), 512, kSortSmemBigBytes, c->aux>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
-            kSortSmemBig, kSortSmemN, kSortSmemBig);
+            kSortSmemBig, kSortSmemN, kSortSmemBig, c->long_tiles);
     }
     {
         LaunchScope ls(c, KB_SORT_XL, c->aux);
         kb_sort_tiles_xl<<<grid(std::min<int64_t>(H.n_tiles, 2 * nsm), 2), 512, kSortHistBytes, c->aux>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
-            kSortSmemBig, kSortSmemBig, 0x7fffffff);
+            kSortSmemBig, kSortSmemBig, 0x7fffffff, c->long_tiles);
     }
     VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
     {
         LaunchScope ls(c, KB_SORT, stream);
         kb_sort_tiles<<<grid(H.n_tiles, 4), 512, sort_smem_bytes(kSortClassS), stream>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
-            kSortClassS, 0, kSortClassS);
+            kSortClassS, 0, kSortClassS, c->long_tiles);
     }
     {
         LaunchScope ls(c, KB_SORT_M, stream);
         kb_sort_tiles_mid<<<grid(H.n_tiles, 3), 512, sort_smem_bytes(kSortClassM), stream>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
-            kSortClassM, kSortClassS, kSortClassM);
+            kSortClassM, kSortClassS, kSortClassM, c->long_tiles);
     }
     {
         LaunchScope ls(c, KB_SORT_L, stream);
         kb_sort_tiles_large<<<grid(H.n_tiles, 2), 512, kSortSmemBytes, stream>>>(
             B, c->tile_off, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask, c->geo, c->status,
-            kSortSmemN, kSortClassM, kSortSmemN);
+            kSortSmemN, kSortClassM, kSortSmemN, c->long_tiles);
     }
     VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
     const int cap = c->batch_lists ? c->list_cap : 0;

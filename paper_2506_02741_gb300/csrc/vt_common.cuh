@@ -84,7 +84,12 @@ struct Status {
     unsigned long long n_instances;
     unsigned long long n_overflow_tiles;
     uint32_t sort_next[2];   // work counters of the long-list sorts (reset by the tile scan)
+    uint32_t n_long, pad2;   // tiles listed in long_tiles by the tile scan
 };
+
+// Lists longer than this are sorted by the long-list launches (on chip up to
+// 13,312 entries, beyond in global memory); the tile scan lists their tiles.
+constexpr int kSortLongMin = 6000;
 
 // ---------------------------------------------------------------------------
 // Batched launches (vt_batch_*): many independent work items -- one section
@@ -355,7 +360,8 @@ __global__ void k_preprocess_aniso(SecTable T, Camera cam, const ViewXf *views,
                                    const TabRow *tab, float4 *geo, float4 *app, uint4 *info,
                                    uint32_t *tile_count);
 __global__ void k_scan_tiles(const uint32_t *tile_count, int n_tiles, uint32_t *tile_off,
-                             uint32_t *tile_cursor, Status *st, unsigned long long cap);
+                             uint32_t *tile_cursor, Status *st, unsigned long long cap,
+                             uint32_t *long_tiles);
 __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_cursor,
                        unsigned long long *bucket, uint8_t *bmask_u, const Status *st);
 // Per-tile depth sort, one kernel per list-length class (vt_raster.cu).
@@ -363,7 +369,7 @@ __global__ void k_emit(int64_t n, const uint4 *info, Camera cam, uint32_t *tile_
     __global__ void name(const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,     \
                          unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted,     \
                          uint8_t *bmask, const float4 *geo, Camera cam, Status *st, int smem_n, \
-                         int lo, int hi);
+                         int lo, int hi, const uint32_t *long_tiles);
 VT_DECLARE_SORT(k_sort_tiles)
 VT_DECLARE_SORT(k_sort_tiles_mid)
 VT_DECLARE_SORT(k_sort_tiles_large)
@@ -448,14 +454,16 @@ __global__ void kb_setup(const BatchTable *B, ViewXf *views, TabRow *tab, double
 __global__ void kb_preprocess(const BatchTable *B, const ViewXf *views, const TabRow *tab,
                               float4 *geo, float4 *app, uint4 *info, uint32_t *tile_count);
 __global__ void kb_scan_tiles(const BatchTable *B, const uint32_t *tile_count, uint32_t *tile_off,
-                              uint32_t *tile_cursor, Status *st, unsigned long long cap);
+                              uint32_t *tile_cursor, Status *st, unsigned long long cap,
+                              uint32_t *long_tiles);
 __global__ void kb_emit(const BatchTable *B, const uint4 *info, uint32_t *tile_cursor,
                         unsigned long long *bucket, uint8_t *bmask_u, const Status *st);
 #define VT_DECLARE_SORT_B(name)                                                                  \
     __global__ void name(const BatchTable *B, const uint32_t *tile_off,                          \
                          unsigned long long *bucket, unsigned long long *alt,                    \
                          const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,               \
-                         const float4 *geo, Status *st, int smem_n, int lo, int hi);
+                         const float4 *geo, Status *st, int smem_n, int lo, int hi,      \
+                         const uint32_t *long_tiles);
 VT_DECLARE_SORT_B(kb_sort_tiles)
 VT_DECLARE_SORT_B(kb_sort_tiles_mid)
 VT_DECLARE_SORT_B(kb_sort_tiles_large)

@@ -392,13 +392,21 @@ __global__ void __launch_bounds__(256) kb_preprocess(const BatchTable *Bp, const
 // k_scan_tiles: one block; exclusive prefix sum of the per-tile counts into
 // tile offsets (tile_off[n_tiles] = instance total) and insertion cursors.
 // Flags a capacity shortage instead of letting later kernels overrun.
+// Also lists, in tile order, the tiles whose lists are longer than
+// kSortLongMin (long_tiles[0, st->n_long)): the long-list launches take their
+// tiles from there instead of visiting every tile.
 __device__ __forceinline__ void scan_tiles_body(const uint32_t *tile_count, int n_tiles,
                                                 uint32_t *tile_off, uint32_t *tile_cursor,
-                                                Status *st, unsigned long long cap) {
+                                                Status *st, unsigned long long cap,
+                                                uint32_t *long_tiles) {
     __shared__ unsigned long long warp_sums[32];
     __shared__ unsigned long long carry;
+    __shared__ uint32_t long_warp[32], long_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0;
+    if (tid == 0) {
+        carry = 0;
+        long_carry = 0;
+    }
     __syncthreads();
     for (int base = 0; base < n_tiles; base += 1024) {
         const int i = base + tid;
@@ -424,8 +432,22 @@ __device__ __forceinline__ void scan_tiles_body(const uint32_t *tile_count, int 
             tile_off[i] = (uint32_t)excl;
             tile_cursor[i] = (uint32_t)excl;
         }
+        const bool is_long = i < n_tiles && c > (unsigned long long)kSortLongMin;
+        const unsigned lb = __ballot_sync(kFull, is_long);
+        if (lane == 0) long_warp[warp] = __popc(lb);
+        __syncthreads();
+        if (is_long) {
+            uint32_t pos = long_carry + __popc(lb & ((1u << lane) - 1u));
+            for (int w = 0; w < warp; ++w) pos += long_warp[w];
+            long_tiles[pos] = (uint32_t)i;
+        }
         __syncthreads();
         if (tid == 1023) carry = excl + c;
+        if (tid == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < 32; ++w) tot += long_warp[w];
+            long_carry += tot;
+        }
         __syncthreads();
     }
     if (tid == 0) {
@@ -433,21 +455,24 @@ __device__ __forceinline__ void scan_tiles_body(const uint32_t *tile_count, int 
         st->n_instances = carry;
         st->n_overflow_tiles = 0;
         st->sort_next[0] = st->sort_next[1] = 0u;
+        st->n_long = long_carry;
         st->flags = carry > cap || carry >= 0xffffffffull ? kFlagCapacity : 0;
     }
 }
 
 __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *tile_count, int n_tiles,
                                                      uint32_t *tile_off, uint32_t *tile_cursor,
-                                                     Status *st, unsigned long long cap) {
-    scan_tiles_body(tile_count, n_tiles, tile_off, tile_cursor, st, cap);
+                                                     Status *st, unsigned long long cap,
+                                                     uint32_t *long_tiles) {
+    scan_tiles_body(tile_count, n_tiles, tile_off, tile_cursor, st, cap, long_tiles);
 }
 
 __global__ void __launch_bounds__(1024) kb_scan_tiles(const BatchTable *Bp,
                                                       const uint32_t *tile_count,
                                                       uint32_t *tile_off, uint32_t *tile_cursor,
-                                                      Status *st, unsigned long long cap) {
-    scan_tiles_body(tile_count, Bp->n_tiles, tile_off, tile_cursor, st, cap);
+                                                      Status *st, unsigned long long cap,
+                                                      uint32_t *long_tiles) {
+    scan_tiles_body(tile_count, Bp->n_tiles, tile_off, tile_cursor, st, cap, long_tiles);
 }
 
 // ---------------------------------------------------------------------------
@@ -820,7 +845,8 @@ __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_
                                                 const float4 *geo, const Camera &cam, Status *st,
                                                 int smem_n, int lo, int hi,
                                                 const BatchTable *B = nullptr,
-                                                uint32_t *wctr = nullptr) {
+                                                uint32_t *wctr = nullptr,
+                                                const uint32_t *long_tiles = nullptr) {
     extern __shared__ unsigned long long sm[];
     __shared__ uint32_t red[4][kSortWarps];
     __shared__ int s_next;
@@ -829,17 +855,20 @@ __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_
     if (B) n_tiles = B->n_tiles;
     ItemCursor cur;
     // A launch may have fewer blocks than tiles: blocks stride over the tiles,
-    // or with a work counter take the next tile from it (the long lists vary
-    // in length by 5x: a fixed stride leaves the block with the longest share
-    // running alone at the end).
-    auto next = [&](int t) {
-        if (!wctr) return t + (int)gridDim.x;
+    // or, in the long-list launches, take the next of the tiles the tile scan
+    // listed from a work counter (the long lists vary in length by 5x: a
+    // fixed stride leaves the block with the longest share running alone at
+    // the end).
+    auto next = [&](int j) {
+        if (!wctr) return j + (int)gridDim.x;
         __syncthreads();   // every thread has read the previous s_next
         if (tid == 0) s_next = (int)atomicAdd(wctr, 1u);
         __syncthreads();
         return s_next;
     };
-    for (int t = wctr ? next(0) : (int)blockIdx.x; t < n_tiles; t = next(t)) {
+    const int n_iter = wctr ? (int)st->n_long : n_tiles;
+    for (int j = wctr ? next(0) : (int)blockIdx.x; j < n_iter; j = next(j)) {
+        const int t = wctr ? (int)long_tiles[j] : j;
         const uint32_t start = tile_off[t];
         const int n = (int)(tile_off[t + 1] - start);
         if (n <= lo || n > hi) continue;   // another launch sorts this size class
@@ -870,10 +899,11 @@ __device__ __forceinline__ void sort_tiles_body(const uint32_t *tile_off, int n_
     __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) name(                            \
         const uint32_t *tile_off, int n_tiles, unsigned long long *bucket,                       \
         unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,       \
-        const float4 *geo, Camera cam, Status *st, int smem_n, int lo, int hi) {                 \
+        const float4 *geo, Camera cam, Status *st, int smem_n, int lo, int hi,                   \
+        const uint32_t *long_tiles) {                                                            \
         sort_tiles_body<G>(tile_off, n_tiles, bucket, alt, bmask_u, sorted, bmask, geo, cam, st, \
                            smem_n, lo, hi, nullptr,                                              \
-                           CTR < 0 ? nullptr : &st->sort_next[CTR < 0 ? 0 : CTR]);               \
+                           CTR < 0 ? nullptr : &st->sort_next[CTR < 0 ? 0 : CTR], long_tiles);   \
     }
 VT_SORT_KERNEL(k_sort_tiles, 3, 2, -1)
 VT_SORT_KERNEL(k_sort_tiles_mid, 7, 2, -1)
@@ -887,10 +917,11 @@ VT_SORT_KERNEL(k_sort_tiles_xl, 0, 2, 1)
     __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) name(                            \
         const BatchTable *B, const uint32_t *tile_off, unsigned long long *bucket,               \
         unsigned long long *alt, const uint8_t *bmask_u, uint32_t *sorted, uint8_t *bmask,       \
-        const float4 *geo, Status *st, int smem_n, int lo, int hi) {                             \
+        const float4 *geo, Status *st, int smem_n, int lo, int hi,                               \
+        const uint32_t *long_tiles) {                                                            \
         sort_tiles_body<G>(tile_off, 0, bucket, alt, bmask_u, sorted, bmask, geo, B->it[0].cam,  \
                            st, smem_n, lo, hi, B,                                                \
-                           CTR < 0 ? nullptr : &st->sort_next[CTR < 0 ? 0 : CTR]);               \
+                           CTR < 0 ? nullptr : &st->sort_next[CTR < 0 ? 0 : CTR], long_tiles);   \
     }
 VT_SORT_KERNEL_B(kb_sort_tiles, 3, 2, -1)
 VT_SORT_KERNEL_B(kb_sort_tiles_mid, 7, 2, -1)
