@@ -289,13 +289,18 @@ class BatchServer:
     def warm(self, requests):
         """Measure instance counts, create the contexts, time every kind of
         request once, run one batch on each context and capture its launch
-        graph."""
-        self._measure_instances(requests)
-        probe = _BatchCtx(self, {k: v for k, v in self._need_max(requests).items()})
-        self._measure_times(probe, requests)
+        graph.  Estimates and single-request graphs are made for every
+        (section, bucket, kind), also those the given requests do not use (at
+        a pose of a request of the same section, else of the first request),
+        so that none is missing or captured while requests are served; the
+        contexts' capacities follow the given requests."""
+        every = self._cover(requests)
+        self._measure_instances(every)
+        probe = _BatchCtx(self, {k: v for k, v in self._need_max(every).items()})
+        self._measure_times(probe, every)
         del probe
         torch.cuda.synchronize()
-        solos = self._make_solos(requests) if self.solo else [None] * self.n_contexts
+        solos = self._make_solos(every) if self.solo else [None] * self.n_contexts
         cap = self._capacity(requests)
         self.ctxs = [_BatchCtx(self, cap) for _ in range(self.n_contexts)]
         for ctx, slot in zip(self.ctxs, solos):
@@ -333,6 +338,19 @@ class BatchServer:
         else:
             self.memory_budget = int(self._budget_arg) - max(0, free0 - free1)
         return solos
+
+    def _cover(self, requests) -> list:
+        seen = {(r.section, r.bucket, r.kind) for r in requests}
+        pose_of = {}
+        for r in requests:
+            pose_of.setdefault(r.section, r.pose)
+        extra = []
+        for s in range(len(self.sections)):
+            for b in range(len(self.resolutions)):
+                for kind in ("render", "track"):
+                    if (s, b, kind) not in seen:
+                        extra.append(Request(-1, kind, s, pose_of.get(s, requests[0].pose), b))
+        return list(requests) + extra
 
     def _need_max(self, requests) -> dict:
         needs = [self._need(r) for r in requests]
