@@ -114,6 +114,32 @@ def test_lone_requests_take_the_single_request_path(dev, setup, graphs):
     assert server.n_solo >= 12
 
 
+def test_warm_up_prepares_every_combination(dev, setup):
+    """Warm-up with requests of one section and bucket: time estimates and
+    single-request graphs exist for every (section, bucket, kind), so a
+    request of another combination served alone captures nothing; its
+    result equals the batched path's."""
+    reqs = [r for r in _requests(setup) if r.section == 0 and r.bucket == 0]
+    assert reqs
+    server = serving.BatchServer(setup[0], RES, n_contexts=2, memory_budget=8 << 30)
+    server.warm(reqs)
+    every = {(s, b, k) for s in range(len(setup[0])) for b in range(len(RES))
+             for k in ("render", "track")}
+    assert set(server.ms_est) == every
+    for ctx in server.ctxs:
+        assert set(ctx.solo.works) == every
+        assert all(w.graph is not None for w in ctx.solo.works.values())
+    sections, _, poses, frames = setup
+    other = serving.Request(0, "render", 2, poses[2][1], 1)
+    graphs_before = [id(w.graph) for c in server.ctxs for w in c.solo.works.values()]
+    (a,) = server.run([other])
+    assert [id(w.graph) for c in server.ctxs for w in c.solo.works.values()] == graphs_before
+    batched = serving.BatchServer(setup[0], RES, n_contexts=1, memory_budget=8 << 30, solo=False)
+    batched.warm(reqs)
+    (b,) = batched.run([serving.Request(0, "render", 2, poses[2][1], 1)])
+    assert torch.equal(a.result, b.result)
+
+
 @pytest.mark.parametrize("graphs", [True, False])
 def test_slot_server_alone_equals_in_mix(dev, setup, graphs):
     reqs = _requests(setup, n=30)

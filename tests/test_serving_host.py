@@ -1,6 +1,7 @@
 """Host logic of the batch server that needs no GPU: the admission order
 (shortest estimated request first, requests past the wait limit first and
-oldest first) and the batch time budget that follows the queue."""
+oldest first), the batch time budget that follows the queue, and the set
+of (section, bucket, kind) that warm-up prepares."""
 
 import numpy as np
 import pytest
@@ -47,3 +48,25 @@ def test_admission_order_is_a_permutation():
 ])
 def test_batch_budget(queued, n, lo, hi, want):
     assert serving.batch_budget(queued, n, lo, hi) == pytest.approx(want)
+
+
+def test_warm_up_covers_every_section_bucket_and_kind():
+    """The requests given to warm() plus one request for every (section,
+    bucket, kind) they leave out, at a pose of a given request of the same
+    section, else at the first request's pose."""
+    srv = serving.BatchServer.__new__(serving.BatchServer)
+    srv.sections = [object(), object(), object()]
+    srv.resolutions = [(320, 240), (640, 480)]
+    p0, p2 = np.eye(3, 4), np.eye(3, 4) + 0.5
+    given = [serving.Request(0, "track", 0, p0, 1), serving.Request(1, "render", 2, p2, 0),
+             serving.Request(2, "render", 2, p2 + 1.0, 1)]
+    every = srv._cover(given)
+    assert every[:3] == given
+    keys = [(r.section, r.bucket, r.kind) for r in every]
+    assert len(keys) == len(set(keys)) == 3 * 2 * 2
+    for r in every[3:]:
+        assert r.rid == -1 and r.obs is None
+        want = p2 if r.section == 2 else p0          # section 1 has no request
+        np.testing.assert_array_equal(r.pose, want)
+    # nothing to add when every combination is given
+    assert srv._cover(every) == every
