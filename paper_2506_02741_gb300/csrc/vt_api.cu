@@ -127,8 +127,9 @@ struct vt_ctx {
     double *pose_partials = nullptr, *pose_copy = nullptr;
     uint32_t *blk_ovf = nullptr;      // list overflow flag per 8x4 pixel block
     cudaStream_t aux = nullptr;       // auxiliary stream of the long-list sort
+    cudaStream_t aux2 = nullptr;      // second one: the large class beside the long lists
     int n_sm = 1;                     // SMs of the device
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     double *loss_part = nullptr;      // masked-L1 block partials (separate allocation)
     int64_t loss_cap = 0;             // blocks they hold
     double *view_part = nullptr;      // per-view chunk partials of the view gradients
@@ -371,8 +372,10 @@ vt_status vt_ctx_create(vt_ctx **ctx) {
     if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) !=
             cudaSuccess ||
         cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
         vt_ctx_destroy(c);
         return fail(VT_ERR_CUDA, "vt_ctx_create: cannot create the auxiliary stream");
     }
@@ -405,8 +408,13 @@ void vt_ctx_destroy(vt_ctx *c) {
         cudaStreamSynchronize(c->aux);
         cudaStreamDestroy(c->aux);
     }
+    if (c->aux2) {
+        cudaStreamSynchronize(c->aux2);
+        cudaStreamDestroy(c->aux2);
+    }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
     delete c;
     cudaThreadExchangeStreamCaptureMode(&mode);
 }
@@ -642,11 +650,13 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
         k_emit<<<gblocks, 256, 0, stream>>>(total, c->info, cam, c->tile_cursor, c->bucket,
                                             c->bmask_u, c->status);
     }
-    // fork: the long lists and the large class sort on the auxiliary stream,
-    // beside the short classes on the caller's (works under graph capture
-    // too: the fork and join events make it a parallel branch)
+    // fork: the long lists sort on the auxiliary stream (few blocks: they
+    // leave most SMs free), the large class on the second one, the short
+    // classes on the caller's, all three at once (works under graph capture
+    // too: the fork and join events make them parallel branches)
     VT_CUDA(cudaEventRecord(c->ev_fork, stream), "sort fork");
     VT_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "sort fork");
+    VT_CUDA(cudaStreamWaitEvent(c->aux2, c->ev_fork, 0), "sort fork");
     {
         LaunchScope ls(c, K_SORT_BIG, c->aux);
         // one block per SM at most: these lists are few, and the launch must
@@ -656,11 +666,12 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemN, kSortSmemBig, c->long_tiles);
     }
     {
-        LaunchScope ls(c, K_SORT_L, c->aux);
-        k_sort_tiles_large<<<n_tiles, 512, kSortSmemBytes, c->aux>>>(
+        LaunchScope ls(c, K_SORT_L, c->aux2);
+        k_sort_tiles_large<<<n_tiles, 512, kSortSmemBytes, c->aux2>>>(
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN, c->long_tiles);
     }
+    VT_CUDA(cudaEventRecord(c->ev_join2, c->aux2), "sort join");
     {
         LaunchScope ls(c, K_SORT_XL, c->aux);
         k_sort_tiles_xl<<<std::min(n_tiles, 2 * c->n_sm), 512, kSortHistBytes, c->aux>>>(
@@ -681,6 +692,7 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
             aniso ? nullptr : c->geo, cam, c->status, kSortClassM, kSortClassS, kSortClassM, c->long_tiles);
     }
     VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join, 0), "sort join");
+    VT_CUDA(cudaStreamWaitEvent(stream, c->ev_join2, 0), "sort join");
     {
         LaunchScope ls(c, aniso ? K_FWD_AN : K_FWD, stream);
         auto kern = aniso ? k_composite_fwd_aniso : k_composite_fwd;
