@@ -1,7 +1,8 @@
 """Host logic of bench.py that needs no GPU: the DRAM traffic recorded from
 an ncu capture is reported only while the captured kernel's sources are
 unchanged (hash of the forward part of the compositor source and the common
-header), and a change anywhere in that part makes it unavailable."""
+header), and a change anywhere in that part makes it unavailable; the
+summary of the clock samples taken during the timed region."""
 
 import hashlib
 import importlib.util
@@ -66,3 +67,29 @@ def test_traffic_follows_the_forward_source(tmp_path):
     hdr = root / "paper_2506_02741_gb300" / "csrc" / "vt_common.cuh"
     hdr.write_text(hdr.read_text() + "\n")
     assert b.traffic_for("k_composite_fwd") is None
+
+
+def test_clock_summary_median_and_throttle_reasons():
+    """The clock record of the timed region: median SM clock over the
+    samples, the maximum clock, and every throttle reason seen active in any
+    sample; an empty record says it was not sampled."""
+    b = _bench()
+    s = b.ClockSampler(0)
+    idle = "Not Active"
+    s.lines = [
+        f"2070, 2070, 812.4, 0x0000000000000000, {idle}, {idle}, {idle}, {idle}",
+        f"1980, 2070, 1391.0, 0x0000000000000004, {idle}, {idle}, {idle}, Active",
+        f"2070, 2070, 1200.0, 0x0000000000000000, {idle}, {idle}, {idle}, {idle}",
+        "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",   # unreadable: skipped
+        "2070, 2070",                                                # short: skipped
+    ]
+    got = s.summary()
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
+    s.lines.append(f"1400, 2070, 900.0, 0x0000000000000048, {idle}, Active, {idle}, {idle}")
+    got = s.summary()
+    assert got["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert got["sm_mhz"] == 2025.0 and got["samples"] == 4
+    s.lines = []
+    assert s.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                           "samples": 0}
