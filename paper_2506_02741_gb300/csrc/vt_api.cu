@@ -42,10 +42,11 @@ vt_status cuda_fail(cudaError_t e, const char *what) {
 // Tile lists are sorted in shared memory by size class, each class by a
 // launch whose blocks hold just enough shared memory for its longest list, so
 // that short lists run several blocks per SM (4, 3 and 2 of 228 KB):
-// (0, 1536], (1536, 3584], (3584, kSortSmemN] on the caller's stream; the few
-// longer ones (up to kSortSmemBig in shared memory, one block per SM; beyond
-// that in global memory, two blocks per SM with shared memory for the
-// histograms only) by launches on an auxiliary stream that overlap the
+// (0, 1536], (1536, 3584] on the caller's stream, (3584, kSortSmemN] on a
+// second auxiliary stream (in the batched launches on the caller's stream);
+// the few longer ones (up to kSortSmemBig in shared memory, one block per
+// SM; beyond that in global memory, two blocks per SM with shared memory for
+// the histograms only) by launches on an auxiliary stream that overlap the
 // others.
 constexpr int kSortClassS = 1536, kSortClassM = 3584;
 constexpr size_t sort_smem_bytes(int n) { return 2 * (size_t)n * 8 + 16 * 256 * 4; }
