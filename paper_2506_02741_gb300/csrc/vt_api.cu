@@ -42,8 +42,9 @@ vt_status cuda_fail(cudaError_t e, const char *what) {
 // Tile lists are sorted in shared memory by size class, each class by a
 // launch whose blocks hold just enough shared memory for its longest list, so
 // that short lists run several blocks per SM (4, 3 and 2 of 228 KB):
-// (0, 1536], (1536, 3584] on the caller's stream, (3584, kSortSmemN] on a
-// second auxiliary stream (in the batched launches on the caller's stream);
+// (1536, 3584] on the caller's stream, (3584, kSortSmemN] and then
+// (0, 1536] on a second auxiliary stream (in the batched launches all three
+// on the caller's stream);
 // the few longer ones (up to kSortSmemBig in shared memory, one block per
 // SM; beyond that in global memory, two blocks per SM with shared memory for
 // the histograms only) by launches on an auxiliary stream that overlap the
@@ -652,9 +653,10 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
                                             c->bmask_u, c->status);
     }
     // fork: the long lists sort on the auxiliary stream (few blocks: they
-    // leave most SMs free), the large class on the second one, the short
-    // classes on the caller's, all three at once (works under graph capture
-    // too: the fork and join events make them parallel branches)
+    // leave most SMs free), the large and then the shortest class on the
+    // second one, the middle class on the caller's, all three branches at
+    // once and of similar length (works under graph capture too: the fork
+    // and join events make them parallel branches)
     VT_CUDA(cudaEventRecord(c->ev_fork, stream), "sort fork");
     VT_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "sort fork");
     VT_CUDA(cudaStreamWaitEvent(c->aux2, c->ev_fork, 0), "sort fork");
@@ -672,6 +674,12 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
             c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemN, kSortClassM, kSortSmemN, c->long_tiles);
     }
+    {
+        LaunchScope ls(c, K_SORT, c->aux2);
+        k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassS), c->aux2>>>(
+            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
+            aniso ? nullptr : c->geo, cam, c->status, kSortClassS, 0, kSortClassS, c->long_tiles);
+    }
     VT_CUDA(cudaEventRecord(c->ev_join2, c->aux2), "sort join");
     {
         LaunchScope ls(c, K_SORT_XL, c->aux);
@@ -680,12 +688,6 @@ vt_status vt_render(vt_ctx *c, const vt_section *secs, int32_t n_secs, const dou
             aniso ? nullptr : c->geo, cam, c->status, kSortSmemBig, kSortSmemBig, 0x7fffffff, c->long_tiles);
     }
     VT_CUDA(cudaEventRecord(c->ev_join, c->aux), "sort join");
-    {
-        LaunchScope ls(c, K_SORT, stream);
-        k_sort_tiles<<<n_tiles, 512, sort_smem_bytes(kSortClassS), stream>>>(
-            c->tile_off, n_tiles, c->bucket, c->alt, c->bmask_u, c->sorted, c->bmask,
-            aniso ? nullptr : c->geo, cam, c->status, kSortClassS, 0, kSortClassS, c->long_tiles);
-    }
     {
         LaunchScope ls(c, K_SORT_M, stream);
         k_sort_tiles_mid<<<n_tiles, 512, sort_smem_bytes(kSortClassM), stream>>>(
