@@ -129,7 +129,7 @@ struct vt_ctx {
     double *pose_partials = nullptr, *pose_copy = nullptr;
     uint32_t *blk_ovf = nullptr;      // list overflow flag per 8x4 pixel block
     cudaStream_t aux = nullptr;       // auxiliary stream of the long-list sort
-    cudaStream_t aux2 = nullptr;      // second one: the large class beside the long lists
+    cudaStream_t aux2 = nullptr;      // second one: the large and the shortest class
     int n_sm = 1;                     // SMs of the device
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     double *loss_part = nullptr;      // masked-L1 block partials (separate allocation)
